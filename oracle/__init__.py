@@ -1,0 +1,269 @@
+"""The oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow CPU restatement of the On-the-Fly GS hot path (the 3DGS rasterizer of Sec. III,
+Eq. 1-2, its L1 + D-SSIM loss of Eq. 10, the analytic gradients and Adam) in ``gs_oracle.cpp``,
+and of the progressive schedule (Eq. 3-8) in :mod:`oracle.schedule`.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this package.
+It shares no code with the CUDA library and never imports it.
+
+Arrays are numpy; parameters are component-major ``(59, stride)`` (see ``gs_oracle.cpp``).
+``prec`` selects the instantiation: ``"f32"`` takes every threshold decision in fp32 (the
+precision of the kernels), ``"f64"`` is for finite differences and closed forms.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.cpp")
+_LIB = os.path.join(_HERE, "_build", "libgs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NPARAM = 59
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C++ compiler (plain IEEE arithmetic, no contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           _SRC, "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = ctypes.CDLL(build())
+            _declare(_lib)
+        return _lib
+
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int
+I64 = ctypes.c_int64
+F64 = ctypes.c_double
+
+
+def _declare(L):
+    for suf in ("f32", "f64"):
+        getattr(L, f"orc_project_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32] + [P] * 9
+        getattr(L, f"orc_blend_forward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 12
+        getattr(L, f"orc_blend_backward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 9
+        getattr(L, f"orc_project_backward_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32, P, P]
+        f = getattr(L, f"orc_loss_{suf}")
+        f.argtypes = [I32, I32, P, P, F64, P, F64, P, P]
+        f.restype = F64
+        getattr(L, f"orc_adam_{suf}").argtypes = [P, P, P, P, I64, I64, P, F64, F64, F64, I64]
+        getattr(L, f"orc_sh_eval_{suf}").argtypes = [P, I64, P]
+    L.orc_build_lists.argtypes = [I32, I64, P, P, I32, I32, P, P, P, I64, P, P, P]
+    L.orc_build_lists.restype = I64
+
+
+def _dt(prec):
+    return np.float32 if prec == "f32" else np.float64
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Camera:
+    """Pinhole view: world->camera R (3x3), t (3), focal lengths, principal point, size."""
+
+    def __init__(self, R, t, fx, fy, cx, cy, width, height):
+        self.R = np.asarray(R, dtype=np.float64).reshape(3, 3)
+        self.t = np.asarray(t, dtype=np.float64).reshape(3)
+        self.fx, self.fy, self.cx, self.cy = float(fx), float(fy), float(cx), float(cy)
+        self.width, self.height = int(width), int(height)
+
+    def packed(self):
+        return np.concatenate([self.R.reshape(9), self.t, [self.fx, self.fy, self.cx, self.cy]]).astype(np.float64)
+
+    def grid(self, tw=16, th=16):
+        return (self.width + tw - 1) // tw, (self.height + th - 1) // th
+
+
+def sh_eval(dirs, prec="f64"):
+    dt = _dt(prec)
+    d = _c(dirs, dt).reshape(-1, 3)
+    out = np.zeros((d.shape[0], 16), dt)
+    getattr(lib(), f"orc_sh_eval_{prec}")(_ptr(d), d.shape[0], _ptr(out))
+    return out
+
+
+def project(params, cam: Camera, tile=(16, 16), prec="f32", n=None):
+    """Per-Gaussian projection (mean2d, depth, conic, opacity, rgb, radius, rect, clamp bits)."""
+    dt = _dt(prec)
+    params = _c(params, dt)
+    stride = params.shape[1]
+    n = stride if n is None else n
+    out = dict(mean2d=np.zeros((n, 2), dt), depth=np.zeros(n, dt), conic=np.zeros((n, 3), dt),
+               opacity=np.zeros(n, dt), rgb=np.zeros((n, 3), dt), radius=np.zeros(n, np.int32),
+               rect=np.zeros((n, 4), np.int32), clamp=np.zeros(n, np.uint8), margin=np.zeros(n, dt))
+    camp = cam.packed()
+    getattr(lib(), f"orc_project_{prec}")(
+        _ptr(params), n, stride, _ptr(camp), cam.width, cam.height, tile[0], tile[1],
+        _ptr(out["mean2d"]), _ptr(out["depth"]), _ptr(out["conic"]), _ptr(out["opacity"]),
+        _ptr(out["rgb"]), _ptr(out["radius"]), _ptr(out["rect"]), _ptr(out["clamp"]), _ptr(out["margin"]))
+    return out
+
+
+def build_lists(sizes, mean2d, radius, depth, tile=(16, 16)):
+    """Keys, record indices and per-tile ranges of all views in canonical order.
+
+    ``sizes`` = [(W, H)] per view; ``mean2d`` (V*n, 2) fp32, ``radius`` (V*n,), ``depth`` (V*n,).
+    Record index = view * n + Gaussian id; global tile = view tile base + ty * gx + tx.
+    """
+    V = len(sizes)
+    mean2d = _c(mean2d, np.float32).reshape(-1, 2)
+    radius = _c(radius, np.int32).reshape(-1)
+    depth = _c(depth, np.float32).reshape(-1)
+    n = radius.shape[0] // V
+    Ws = np.array([s[0] for s in sizes], np.int32)
+    Hs = np.array([s[1] for s in sizes], np.int32)
+    tiles = [((w + tile[0] - 1) // tile[0]) * ((h + tile[1] - 1) // tile[1]) for w, h in sizes]
+    ranges = np.zeros((sum(tiles), 2), np.uint32)
+    L = lib()
+    m = L.orc_build_lists(V, n, _ptr(Ws), _ptr(Hs), tile[0], tile[1], _ptr(mean2d), _ptr(radius),
+                          _ptr(depth), 0, None, None, _ptr(ranges))
+    keys = np.zeros(max(m, 1), np.uint64)
+    vals = np.zeros(max(m, 1), np.uint32)
+    L.orc_build_lists(V, n, _ptr(Ws), _ptr(Hs), tile[0], tile[1], _ptr(mean2d), _ptr(radius),
+                      _ptr(depth), m, _ptr(keys), _ptr(vals), _ptr(ranges))
+    base = np.concatenate([[0], np.cumsum(tiles)]).astype(np.int64)
+    return dict(keys=keys[:m], vals=vals[:m], ranges=ranges, tile_base=base, n=n)
+
+
+def blend_forward(cam_size, tile_base, ranges, vals, rec, bg=(0, 0, 0), tile=(16, 16), prec="f32"):
+    """Eq. 2 per pixel.  ``rec`` holds mean2d/conic/opacity/rgb indexed by record index."""
+    dt = _dt(prec)
+    W, H = cam_size
+    img = np.zeros((3, H, W), dt)
+    T = np.zeros((H, W), dt)
+    last = np.zeros((H, W), np.uint32)
+    neval = np.zeros((H, W), np.uint32)
+    gp = np.zeros((H, W), np.uint32)
+    margin = np.zeros((H, W), dt)
+    m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
+    bgv = np.asarray(bg, dt)
+    ranges = _c(ranges, np.uint32)
+    vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    getattr(lib(), f"orc_blend_forward_{prec}")(
+        W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
+        _ptr(rgb), _ptr(bgv), _ptr(img), _ptr(T), _ptr(last), _ptr(neval), _ptr(gp), _ptr(margin))
+    return dict(image=img, T=T, last=last, neval=neval, gp=gp, margin=margin)
+
+
+def blend_backward(cam_size, tile_base, ranges, vals, rec, dimg, grad2d, bg=(0, 0, 0), tile=(16, 16),
+                   prec="f32"):
+    """Accumulate the per-record 2D gradients (9 per record) of one view into ``grad2d``."""
+    dt = _dt(prec)
+    W, H = cam_size
+    m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
+    bgv = np.asarray(bg, dt)
+    d = _c(dimg, dt)
+    assert grad2d.dtype == dt and grad2d.flags.c_contiguous
+    ranges = _c(ranges, np.uint32)
+    vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    getattr(lib(), f"orc_blend_backward_{prec}")(
+        W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
+        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(grad2d))
+    return grad2d
+
+
+def project_backward(params, cam: Camera, grad2d, grads, tile=(16, 16), prec="f32", n=None):
+    """Accumulate into ``grads`` (59, stride) the chain rule of one view's 2D gradients."""
+    dt = _dt(prec)
+    params = _c(params, dt)
+    stride = params.shape[1]
+    n = stride if n is None else n
+    g2 = _c(grad2d, dt)
+    assert grads.dtype == dt and grads.flags.c_contiguous and grads.shape == params.shape
+    camp = cam.packed()
+    getattr(lib(), f"orc_project_backward_{prec}")(
+        _ptr(params), n, stride, _ptr(camp), cam.width, cam.height, tile[0], tile[1], _ptr(g2), _ptr(grads))
+    return grads
+
+
+def loss(img, target, lam=0.2, want_grad=True, grad_scale=1.0, prec="f32"):
+    """(loss, dL/dimg, l1, ssim) of L = (1-lam) L1 + lam (1 - SSIM) for one (3, H, W) view."""
+    dt = _dt(prec)
+    x = _c(img, dt)
+    y = _c(target, dt)
+    _, H, W = x.shape
+    d = np.zeros_like(x) if want_grad else None
+    l1 = ctypes.c_double()
+    ss = ctypes.c_double()
+    val = getattr(lib(), f"orc_loss_{prec}")(W, H, _ptr(x), _ptr(y), float(lam), _ptr(d), float(grad_scale),
+                                           ctypes.byref(l1), ctypes.byref(ss))
+    return val, d, l1.value, ss.value
+
+
+def adam(params, grads, m, v, lrs, step, b1=0.9, b2=0.999, eps=1e-15, n=None, prec="f32"):
+    """In-place Adam over the 59 component rows; ``lrs`` = 6 group learning rates."""
+    dt = _dt(prec)
+    for a in (params, grads, m, v):
+        assert a.dtype == dt and a.flags.c_contiguous
+    stride = params.shape[1]
+    n = stride if n is None else n
+    lr = np.asarray(lrs, np.float64)
+    getattr(lib(), f"orc_adam_{prec}")(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), n, stride, _ptr(lr),
+                                       b1, b2, eps, int(step))
+
+
+def render(params, cams, tile=(16, 16), bg=(0, 0, 0), prec="f32", n=None):
+    """K1-K6 for a batch of views.  Returns the per-view projections, the lists and the images."""
+    dt = _dt(prec)
+    params = _c(params, dt)
+    n = params.shape[1] if n is None else n
+    projs = [project(params, c, tile, prec, n=n) for c in cams]
+    mean2d = np.concatenate([p["mean2d"] for p in projs]).astype(np.float32)
+    radius = np.concatenate([p["radius"] for p in projs])
+    depth = np.concatenate([p["depth"] for p in projs]).astype(np.float32)
+    lists = build_lists([(c.width, c.height) for c in cams], mean2d, radius, depth, tile)
+    rec = {k: np.concatenate([p[k] for p in projs]) for k in ("mean2d", "conic", "opacity", "rgb")}
+    outs = [blend_forward((c.width, c.height), lists["tile_base"][v], lists["ranges"], lists["vals"], rec,
+                          bg, tile, prec) for v, c in enumerate(cams)]
+    return dict(projs=projs, lists=lists, rec=rec, outs=outs, n=n)
+
+
+def loss_and_grad(params, cams, targets, lam=0.2, tile=(16, 16), bg=(0, 0, 0), prec="f32", n=None):
+    """Batched step semantics: loss = mean over views; returns (loss, grads (59, stride), render)."""
+    dt = _dt(prec)
+    params = _c(params, dt)
+    r = render(params, cams, tile, bg, prec, n)
+    n = r["n"]
+    V = len(cams)
+    grad2d = np.zeros((V * n, 9), dt)
+    total = 0.0
+    for v, c in enumerate(cams):
+        val, d, _, _ = loss(r["outs"][v]["image"], targets[v], lam, True, 1.0 / V, prec)
+        total += val / V
+        blend_backward((c.width, c.height), r["lists"]["tile_base"][v], r["lists"]["ranges"], r["lists"]["vals"],
+                       r["rec"], d, grad2d, bg, tile, prec)
+    grads = np.zeros_like(params)
+    for v, c in enumerate(cams):
+        project_backward(params, c, grad2d[v * n:(v + 1) * n], grads, tile, prec, n)
+    r["grad2d"] = grad2d
+    return total, grads, r
+
+
+def pairs(r):
+    """Gaussian-pixel pairs of one forward: per pixel, entries evaluated up to termination."""
+    return int(sum(int(o["neval"].astype(np.int64).sum()) for o in r["outs"]))
