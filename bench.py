@@ -1,0 +1,321 @@
+"""Benchmark of the On-the-Fly GS hot path on GB300.
+
+Workload (one "step" = one pass of the whole hot path): the scene-scale single view -- 200k
+Gaussians in a ring-shaped outdoor-like volume, one 1297 x 840 view, SH degree 3, loss
+0.8 L1 + 0.2 D-SSIM, projection, binning, sort, blend forward, loss, blend backward, projection
+backward and Adam with the per-image learning rate, through the session API (gs_optimize_step),
+replayed from a CUDA graph.  Metric: Gaussian-pixel pairs per second, P counted by the oracle's
+definition (per pixel, list entries evaluated up to its termination), divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+
+--impl reference times the oracle (CPU, fp32, single thread) on the same workload.  Under
+torchrun each rank runs its own independent session (weak scaling, no data exchange); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gsinputs as gi  # noqa: E402
+
+METRIC = "new-image integration latency p50/p99 (s); fwd+bwd Gaussian-pixel pairs/s"
+N_GAUSS = 200_000
+W, H = 1297, 840
+WORKLOAD = "scene-scale single view: 200k Gaussians (ring volume), 1297x840, SH3, 0.8 L1 + 0.2 D-SSIM, fwd+bwd+Adam"
+
+
+def make_workload(seed):
+    p = gi.ring_scene(N_GAUSS, seed=seed, stride=N_GAUSS)
+    cam = gi.ring_camera(0.3 + 0.7 * seed, W, H, 1000.0)
+    tgt = gi.uniform_target(W, H, seed + 1)
+    return p, cam, tgt
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 lane-operations of the blend kernels' arithmetic per Gaussian-pixel pair, counted from the
+# formulas they evaluate (not from compiled code): forward 18 (offset 2, exponent 4, exp 2,
+# alpha 2, cutoffs 2, transmittance 2, colour 4), backward 60 (the forward's alpha path 10,
+# weight/colour-in-front 4, colour behind 6, dL/dalpha 9, colour gradient 3, reciprocal 2,
+# opacity/exponent 3, mean 6, conic 8, transmittance 2, pipeline shifts and selects 7).
+OPS_FWD = 18
+OPS_BWD = 60
+
+
+def roofline(kernel_ms, steps, pairs, m_inst, n, peaks, peaks_kind):
+    """Roofline object for the dominant kernel of the step."""
+    names = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss", "K8 blend bwd",
+             "K9+K10 project bwd + Adam"]
+    per = [k / max(1, steps) for k in kernel_ms]
+    dom = int(np.argmax(per))
+    t = per[dom] * 1e-3
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s (one per lane per clock), in T/s
+    if dom in (5, 7):
+        ops = pairs * (OPS_FWD if dom == 5 else OPS_BWD)
+        ach = ops / t / 1e12
+        return dict(kernel=names[dom], bound="alu", achieved=ach, peak=alu_peak, unit="Tops/s", frac=ach / alu_peak,
+                    traffic=None, peak_source=f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)",
+                    per_kernel_ms={nm: round(x, 4) for nm, x in zip(names, per)})
+    # HBM-bound kernels: algorithmic bytes per launch
+    bytes_ = {0: n * (56 + 8) + 0.5 * n * (192 + 49), 1: n * 8, 2: m_inst * 12 + n * 16, 3: m_inst * 24 * 6,
+              4: m_inst * 8, 6: W * H * 3 * 4 * 6, 8: n * 1416 + m_inst * 48}.get(dom, 0)
+    ach = bytes_ / t / 1e9
+    return dict(kernel=names[dom], bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                frac=ach / peaks["hbm_gbs"], traffic=None, peak_source=peaks_kind,
+                per_kernel_ms={nm: round(x, 4) for nm, x in zip(names, per)})
+
+
+def cpu_baseline_run(steps, warmup, seed=0):
+    """The oracle (fp32, single thread) doing full steps of the same workload."""
+    import oracle
+    from oracle import Camera
+    p, cam, tgt = make_workload(seed)
+    c = Camera(cam["R"], cam["t"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"])
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lrs = [1.6e-4 * 7.0, 5e-3, 1e-3, 0.05, 2.5e-3, 1.25e-4]
+    times, pairs = [], []
+    for s in range(warmup + steps):
+        t0 = time.perf_counter()
+        L, g, r = oracle.loss_and_grad(p, [c], [tgt], lam=0.2, prec="f32")
+        oracle.adam(p, g, m, v, lrs, s + 1, prec="f32")
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            times.append(dt)
+            pairs.append(oracle.pairs(r))
+    return float(np.sum(pairs) / np.sum(times)), float(np.mean(times)), int(np.mean(pairs))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    K, Wm = args.steps, args.warmup
+    # bounded: each step is one full oracle step (~4-5 s on one core)
+    K_eff = min(K, 6)
+    W_eff = min(Wm, 1)
+    val, sec, pairs = cpu_baseline_run(K_eff, W_eff)
+    line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus, "steps": K, "warmup": Wm,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded ring scene; see DESIGN.md)", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
+            "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{K_eff} full oracle steps (after {W_eff} warm-up) of the workload, "
+                                       f"{pairs} pairs each; K capped at 6 to bound CPU time"},
+            "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gs(args):
+    import torch
+    import paper_2503_13086_gb300 as gs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gs.load()
+    p, cam, tgt = make_workload(rank)
+    stream = torch.cuda.Stream()
+    field = gs.Field(stream=stream, scene_extent=7.0, lambda_ssim=0.2, use_graph=1)
+    field.set_gaussians(p)
+    img = field.add_image(cam, tgt)
+    for _ in range(args.warmup):
+        field.optimize_step([img])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    sampler = ClockSampler(local)
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    # --- timed region: K steps, L2 flushed before each, device time per step ---
+    sync_all()
+    field.set_timing(True)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pairs = 0
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        field.optimize_step([img])
+        ev[k][1].record(stream)
+        pairs += field.stats()["last_pairs"]
+    sync_all()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    kms, ksteps = field.kernel_times()
+    field.set_timing(False)
+    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    ms_max = ms
+    pairs_total = pairs
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+        pt = torch.tensor([float(pairs)], device="cuda")
+        torch.distributed.all_reduce(pt)
+        pairs_total = float(pt.item())
+    value = pairs_total / (ms_max * 1e-3)
+
+    # --- end to end through the C ABI: host target (pinned) -> device, step, loss -> host ---
+    tgt_pinned = torch.from_numpy(tgt.reshape(-1)).pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e2e_pairs = 0
+    sync_all()
+    for k in range(args.steps):
+        e2e_ev[k][0].record(stream)
+        field.set_image(img, tgt_pinned)
+        field.optimize_step([img])
+        e2e_ev[k][1].record(stream)
+        e2e_pairs += field.stats()["last_pairs"]
+    sync_all()
+    e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+        pt = torch.tensor([float(e2e_pairs)], device="cuda")
+        torch.distributed.all_reduce(pt)
+        e2e_pairs = pt.item()
+    st = field.stats()
+
+    if rank == 0:
+        peaks, kind = measured_peaks()
+        m_inst = int(st["last_pairs"] > 0) and None
+        # instance count of the last step from a raster forward of the same state (not timed)
+        ras = gs.Raster()
+        P = torch.tensor(field.get_gaussians(), device="cuda")
+        P = torch.nn.functional.pad(P, (0, (-P.shape[1]) % 32))
+        fo = ras.forward(P, N_GAUSS, [cam])
+        m_inst = len(ras.read(9, np.uint32))
+        ras.close()
+        rl = roofline(kms, ksteps, pairs / max(1, args.steps), m_inst, N_GAUSS, peaks, kind)
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
+                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
+                           "instances": m_inst, "pairs_per_step": int(pairs / max(1, args.steps)),
+                           "l2": "flushed before every timed step (256 MiB write, untimed)",
+                           "parallelism": f"{ws} independent session(s), one per GPU",
+                           "graph": True},
+                "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
+                        "h2d_bytes_per_step": int(tgt.nbytes), "d2h_bytes_per_step": 4 + 1024},
+                "gpu_launches": None,
+                "roofline": rl, "clocks": clocks,
+                "wall_s": wall}
+        line["gpu_launches"] = int(ksteps and (13 + 6)) * args.steps
+        if not args.no_cpu_baseline and ws == 1:
+            val, sec, pp = cpu_baseline_run(3, 0)
+            line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                    "sample": f"3 full oracle steps of the workload ({pp} pairs each), fp32, one thread"}
+        print(json.dumps(line))
+    field.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gs(args)
+
+
+if __name__ == "__main__":
+    main()

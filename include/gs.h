@@ -1,0 +1,249 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) hot path of On-the-Fly GS (arxiv 2503.13086).
+ *
+ * On every Local & Semi-Global iteration (Sec. IV-C) the paper optimises a 3D Gaussian
+ * Splatting field (Sec. III, Eq. 1-2) with the original 3DGS rasterizer (Sec. V-A), an
+ * L1 + D-SSIM loss (Eq. 10), a splatting-parallel backward (Sec. IV-D) and Adam whose position
+ * learning rate is the per-image rate of Eq. 6-8.  Each arriving image first extends the field
+ * (Sec. IV-B) and is scheduled by hierarchical image weighting (Eq. 3-4) and the iteration
+ * allocation of Eq. 5.
+ *
+ * Two layers:
+ *   gs_raster_*  stateless rasterizer calls on caller-owned device buffers (forward, loss,
+ *                backward, Adam) for parity checks and autograd wrappers;
+ *   gs_field_* / gs_add_image / gs_select_neighbors / gs_optimize_step / gs_integrate /
+ *                gs_render  a session that keeps the field, its Adam state and the registered
+ *                images resident on the device.
+ *
+ * Conventions
+ *   - Every call returns gs_status; on failure gs_last_error() gives a thread-local message.
+ *     No call aborts the process.  GS_ERR_TIMEOUT means a bounded device-side wait gave up; the
+ *     context stays usable and the affected outputs are unspecified.
+ *   - "device" pointers are CUDA device addresses on the current device, "host" pointers are
+ *     ordinary (preferably pinned) host memory.  The caller owns every pointer it passes; the
+ *     library copies what it keeps before the call returns (host data) or before work queued on
+ *     the stream after the call runs (device data).
+ *   - Stream arguments are cudaStream_t passed as void* (NULL = legacy default stream).  Device
+ *     work is asynchronous on that stream unless a call returns a host value, in which case the
+ *     call synchronises the stream.
+ *   - Gaussian parameters are fp32, component-major with a row stride (a multiple of 32):
+ *       params[c * stride + i], i < n <= stride,
+ *       c = 0..2 mean (x, y, z), 3..5 log-scale, 6..9 quaternion (w, x, y, z, any norm > 0),
+ *       10 opacity logit, 11 + 3 k + ch SH coefficient k = 0..15 of colour channel ch = 0..2.
+ *   - Images are fp32 planar 3 x H x W (CHW), values nominally in [0, 1].  Several views are
+ *     packed back to back in view order.  Per-pixel buffers are H x W per view, packed likewise.
+ *   - Pixel (px, py) is sampled at the continuous image point (px, py); u = fx x/z + cx.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GS_API __attribute__((visibility("default")))
+#else
+#define GS_API
+#endif
+
+#define GS_NUM_PARAMS 59
+#define GS_TILE 16
+
+typedef enum gs_status {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1, /* a pointer, size or id is out of range */
+  GS_ERR_OOM = 2,         /* a device or pinned allocation failed */
+  GS_ERR_BUDGET = 3,      /* the call would exceed the field's hbm_budget_bytes */
+  GS_ERR_CAPACITY = 4,    /* a fixed capacity (views per step, image count) is exceeded */
+  GS_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
+  GS_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired */
+  GS_ERR_STATE = 7        /* call out of order (e.g. backward without a forward) */
+} gs_status;
+
+/* Pinhole camera.  R is the row-major world->camera rotation and t the translation
+ * (x_cam = R x_world + t, OpenCV axes: +z forward, +y down).  fx, fy, cx, cy in pixels. */
+typedef struct gs_camera {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} gs_camera;
+
+/* Thread-local description of the last failure of this thread (never NULL). */
+GS_API const char* gs_last_error(void);
+
+/* Library version string. */
+GS_API const char* gs_version(void);
+
+/* ----------------------------------------------------------------------------------------
+ * Stateless rasterizer (Sec. III Eq. 1-2; Sec. IV-D; Eq. 10).
+ * A gs_raster owns only workspaces (projection records, sorted lists, backward checkpoints);
+ * gs_raster_backward differentiates the most recent gs_raster_forward of the same object.
+ * One gs_raster must not be used from two streams at once.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct gs_raster gs_raster;
+
+GS_API gs_status gs_raster_create(gs_raster** out);
+GS_API gs_status gs_raster_destroy(gs_raster* r);
+
+/* K1-K6 for n_views cameras (host array, n_views <= 32).  Writes, per view packed back to back:
+ *   out_image (device, 3 H W floats per view): sum_i c_i alpha_i T_i + T_final bg,
+ *   out_T     (device, H W floats, nullable): final transmittance,
+ *   out_last  (device, H W uint32): 1 + index in the tile list of the last Gaussian blended,
+ *   out_gp    (device, H W uint32, nullable): number of Gaussians blended into the pixel (G_p of
+ *             Eq. 9).
+ * out_pairs (host, nullable) receives the Gaussian-pixel pairs evaluated: per pixel, the list
+ * entries visited up to and including the one that stopped it.  Synchronises the stream once
+ * to size the instance buffers. */
+GS_API gs_status gs_raster_forward(gs_raster* r, void* stream, const float* params, int64_t n, int64_t stride,
+                            const gs_camera* cams, int n_views, const float bg[3], float* out_image,
+                            float* out_T, uint32_t* out_last, uint32_t* out_gp, uint64_t* out_pairs);
+
+/* K7 on the views of the last forward: L = mean over views of
+ * (1 - lambda_ssim) mean|X - Y| + lambda_ssim (1 - mean SSIM(X, Y)) (11x11 Gaussian window,
+ * sigma 1.5, zero padding).  image/target (device) are packed like out_image.  out_dimage
+ * (device, nullable) receives dL/dimage.  out_loss (host, nullable) receives L and synchronises. */
+GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, const float* target, float lambda_ssim,
+                         float* out_dimage, double* out_loss);
+
+/* K8 + K9: gradients of a scalar loss with respect to the parameters of the last forward,
+ * given dL/dimage (device, packed like out_image).  image and last are the forward's outputs.
+ * out_grads (device, 59 x stride, row stride = stride) is overwritten for i < n.  out_grad2d
+ * (device, nullable, 9 floats per record, record = view * stride + i) receives per view the 2D
+ * gradient (d mean2d x, y; d conic a, b, c; d opacity; d rgb). */
+GS_API gs_status gs_raster_backward(gs_raster* r, void* stream, const float* params, const float* image,
+                             const uint32_t* last, const float* dimage, float* out_grads, float* out_grad2d);
+
+/* K10: Adam (torch.optim.Adam's bias-corrected update) over 59 x stride device arrays.
+ * lr[6] per parameter group: 0 mean, 1 log-scale, 2 quaternion, 3 opacity, 4 SH DC, 5 SH rest.
+ * step >= 1 is the step count used for bias correction. */
+GS_API gs_status gs_adam_step(void* stream, float* params, const float* grads, float* m, float* v, int64_t n,
+                       int64_t stride, const float lr[6], float beta1, float beta2, float eps, int64_t step);
+
+/* Copy a workspace buffer of the last forward to host memory (parity checks).  which:
+ *   0 xyo   (float4 per record: u, v, opacity, 0)   1 conic (float4: -a/2, -b, -c/2, 0)
+ *   2 rgb   (float4: r, g, b, 0)                    3 depth (float)
+ *   4 radius (int32)                                5 rect (uint32 x2: x0|x1<<16, y0|y1<<16)
+ *   6 count (uint32 tiles touched)                  7 offsets (uint32)
+ *   8 keys  (uint64, sorted, m_total of them)       9 values (uint32 record index, sorted)
+ *  10 ranges (uint32 x2 per global tile)           11 clamp bits (uint8)
+ *  12 instance gradients of the last backward (float x12 per instance, emission order)
+ * Records are view * stride + i for the forward's views.  *out_bytes gets the size; with
+ * host_dst == NULL only the size is returned.  Synchronises the raster's stream. */
+GS_API gs_status gs_raster_read(gs_raster* r, int which, void* host_dst, size_t capacity_bytes, size_t* out_bytes);
+
+/* Per-kernel device time (ms) of the raster's last forward + loss + backward when timing is on:
+ * [0] K1 project, [1] K2 scan, [2] K3 emit, [3] K4 sort, [4] K5 ranges, [5] K6 blend forward,
+ * [6] K7 loss, [7] K8 blend backward, [8] K9(+K10) project backward. */
+GS_API gs_status gs_raster_set_timing(gs_raster* r, int enable);
+GS_API gs_status gs_raster_kernel_times(gs_raster* r, float out_ms[9]);
+
+/* ----------------------------------------------------------------------------------------
+ * Session: the field, its Adam state and the registered images stay on the device.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct gs_field gs_field;
+
+typedef struct gs_field_config {
+  int32_t T_I;              /* iterations per arriving image (paper: 200) */
+  int32_t N_m;              /* key images incl. the new one (paper: 10) */
+  int32_t T_a;              /* iterations for an image to be "trained" (Eq. 7; paper: 200) */
+  int32_t batch_views;      /* views per optimisation step in gs_integrate (1 = per-view) */
+  int32_t use_graph;        /* replay each step from a captured CUDA graph */
+  float eta0, etaf;         /* Eq. 6 initial / final position rate (1.6e-4, 1.6e-6) */
+  float lambda_ssim;        /* D-SSIM weight (0.2) */
+  float lr_scale, lr_rot, lr_opacity, lr_sh_dc, lr_sh_rest; /* other Adam groups (3DGS) */
+  float beta1, beta2, adam_eps;
+  float add_dist_thresh;    /* new-point distance test threshold; <= 0: 0.01 x scene extent */
+  float scene_extent;       /* position-rate scale; <= 0: 1.1 x camera spread (at least 1) */
+  float bg[3];
+  uint64_t seed;            /* semi-global selection and slot order (SplitMix64) */
+  uint64_t hbm_budget_bytes;/* 0 = unlimited */
+  int64_t initial_capacity; /* Gaussians */
+} gs_field_config;
+
+/* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2
+ * (3DGS), group rates 5e-3 / 1e-3 / 0.05 / 2.5e-3 / 1.25e-4, Adam (0.9, 0.999, 1e-15). */
+GS_API void gs_field_config_default(gs_field_config* cfg);
+
+GS_API gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out);
+GS_API gs_status gs_field_destroy(gs_field* f);
+
+/* Replace the field's Gaussians (host, component-major, src_stride >= n); Adam state is
+ * zeroed and the Adam step count reset. */
+GS_API gs_status gs_field_set_gaussians(gs_field* f, const float* host_params, int64_t n, int64_t src_stride);
+/* Copy the field's parameters (and optionally Adam m, v; nullable) to host, dst_stride >= n. */
+GS_API gs_status gs_field_get_gaussians(gs_field* f, float* host_params, float* host_m, float* host_v,
+                                 int64_t dst_stride, int64_t* out_n);
+
+/* Register an arriving image (Sec. IV-B): pose and intrinsics, the target image (3 x H x W,
+ * host or device per rgb_on_device), and its sparse points (host: xyz n_pts x 3, rgb n_pts x 3
+ * in [0, 1], track ids n_pts; any may be NULL when n_pts == 0).  Points farther than
+ * add_dist_thresh from every existing sparse point become new Gaussians (3DGS initialisation);
+ * track ids shared with earlier images define the overlap matrix M (shared / min count).
+ * GS_ERR_BUDGET when growing the field would exceed hbm_budget_bytes. */
+GS_API gs_status gs_add_image(gs_field* f, const gs_camera* cam, const float* rgb_chw, int rgb_on_device,
+                       const float* pts_xyz, const float* pts_rgb, int32_t n_pts, const int64_t* pt_track_ids,
+                       int32_t* out_image_id);
+
+/* Replace a registered image's target (and pose when cam != NULL), e.g. a refined pose. */
+GS_API gs_status gs_set_image(gs_field* f, int32_t image_id, const gs_camera* cam, const float* rgb_chw, int rgb_on_device);
+
+/* Eq. 3-4: hierarchical weights from image_id over M; returns image_id first, then up to k
+ * neighbours by decreasing weight (ties: lower id).  out_ids / out_w hold k + 1 entries. */
+GS_API gs_status gs_select_neighbors(gs_field* f, int32_t image_id, int32_t k, int32_t* out_ids, float* out_w,
+                              int32_t* out_n);
+
+/* One optimisation step over n_views registered views (<= 32): render, loss (mean over
+ * views), backward, Adam with the position rate = mean over the views of Eq. 8's rate x scene
+ * extent; then T_j += 1 for every view.  out_loss (host, nullable). */
+GS_API gs_status gs_optimize_step(gs_field* f, const int32_t* view_ids, int32_t n_views, float* out_loss);
+
+typedef struct gs_integrate_stats {
+  int32_t iterations;      /* view-iterations run (T_I) */
+  int32_t steps;           /* optimisation steps (iterations / batch_views, rounded up) */
+  int32_t key_images;      /* N_m actually selected */
+  int32_t new_gaussians;   /* not used by gs_integrate; set by the caller's bookkeeping */
+  double mean_loss;        /* mean of the step losses */
+  uint64_t pairs;          /* Gaussian-pixel pairs of all steps */
+} gs_integrate_stats;
+
+/* Local & Semi-Global optimisation for a new image (Sec. IV-C): Eq. 3-4 weights, Eq. 5
+ * allocation of T_I / 2 iterations over the N_m key images, T_I / 2 spread evenly over the
+ * other registered images (remainder to a seeded random subset), a seeded slot order, and
+ * ceil(T_I / batch_views) calls of the optimisation step. */
+GS_API gs_status gs_integrate(gs_field* f, int32_t image_id, gs_integrate_stats* out_stats);
+
+/* Render the field from any camera: out_rgb_chw (device, 3 x H x W), out_T (device, nullable). */
+GS_API gs_status gs_render(gs_field* f, const gs_camera* cam, float* out_rgb_chw, float* out_T);
+
+typedef struct gs_field_stats {
+  int64_t n_gaussians;
+  int64_t capacity;
+  int64_t n_images;
+  int64_t adam_step;
+  uint64_t bytes_in_use;   /* device bytes owned by the field (parameters, Adam, images, workspaces) */
+  uint64_t last_pairs;     /* Gaussian-pixel pairs of the last step */
+  double last_loss;
+} gs_field_stats;
+GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);
+
+/* Per-image bookkeeping: T_j (iterations trained, Eq. 7) and the overlap row M[image, :]. */
+GS_API gs_status gs_image_info(const gs_field* f, int32_t image_id, int32_t* out_T, float* out_M_row, int32_t row_len);
+
+/* The learning rate of Eq. 8 for image_id under the current T_j (diagnostics and tests). */
+GS_API gs_status gs_image_lr(const gs_field* f, int32_t image_id, float* out_lr);
+
+/* Enable per-kernel timing on the field's steps; gs_field_kernel_times returns the summed
+ * device ms per kernel (same order as gs_raster_kernel_times) and the number of steps. */
+GS_API gs_status gs_field_set_timing(gs_field* f, int enable);
+GS_API gs_status gs_field_kernel_times(gs_field* f, float out_ms[9], int64_t* out_steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -1,0 +1,108 @@
+// gs_device.cuh -- device-side definitions shared by the rasterizer kernels (sm_103a).
+//
+// The hot path of On-the-Fly GS (every Local & Semi-Global iteration, Sec. IV-C) is the 3DGS
+// rasterizer of Sec. III (Eq. 1-2) with the constants of the original 3DGS (Sec. V-A), its
+// L1 + D-SSIM loss (Eq. 10), a splatting-parallel backward (Sec. IV-D) and Adam with the
+// per-image learning rate of Eq. 6-8.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+constexpr int kNumParams = 59;      // mean 3, log-scale 3, quaternion 4, opacity 1, SH 48
+constexpr int kTile = 16;           // tile edge in pixels (16 x 16 = 256 pixels = one CTA)
+constexpr int kTilePix = kTile * kTile;
+constexpr int kChunk = 32;          // Gaussians per backward work item and checkpoint period
+constexpr float kNearZ = 0.2f;      // cull at camera z <= 0.2
+constexpr float kDilate = 0.3f;     // low-pass term added to the 2D covariance diagonal
+constexpr float kFovLim = 1.3f;     // x/z, y/z clamped to 1.3 x half-FOV tangent inside J
+constexpr float kAlphaMax = 0.99f;  // alpha clamp
+constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha cutoff
+constexpr float kTransMin = 1e-4f;  // stop before T would drop below this
+
+// Error bits of Control::error.
+constexpr unsigned kErrTimeout = 1u;     // a bounded spin-wait gave up
+constexpr unsigned kErrOverflow = 2u;    // instance capacity exceeded (step skipped)
+
+// One camera of a step, in device memory.
+struct ViewDev {
+  float R[9];      // world -> camera rotation, row-major
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];  // camera centre in world space, -R^T t
+  float limx, limy;
+  int W, H;        // image size in pixels
+  int gx, gy;      // tile grid
+  long long tile_base;   // first global tile id of this view
+  long long pix_base;    // first pixel of this view in the packed per-pixel buffers
+  long long loss_block_base;  // first loss CTA of this view
+  const float* target;   // target image (3 x H x W) for the loss
+};
+
+// Step control block in device memory, cleared at the start of every step.
+struct Control {
+  unsigned long long m_total;   // instances emitted by the key emission
+  unsigned long long pairs;     // Gaussian-pixel pairs (entries evaluated up to termination)
+  unsigned int overflow;        // instance capacity exceeded
+  unsigned int error;           // kErr* bits
+  unsigned int scan_ticket;
+  unsigned int sort_ticket[8];
+  unsigned int bwd_work;
+  unsigned int loss_done;
+  unsigned int pad;
+  double loss_view[32];         // per-view loss of the last step
+  double loss;                  // batch loss (mean over views)
+};
+
+// Scalars of one step in device memory (so a captured graph picks up new values).
+struct StepParams {
+  int n;                 // live Gaussians
+  int n_views;
+  float bg[3];
+  float lambda_ssim;     // D-SSIM weight of the loss
+  float lr[6];           // learning rate per parameter group
+  float beta1, beta2, eps;
+  float step_size_scale; // 1 / (1 - beta1^t)
+  float bc2_sqrt;        // sqrt(1 - beta2^t)
+  int adam;              // 1: apply Adam, 0: write gradients
+};
+
+// Exponent of the 2D Gaussian at offset (dx, dy) from its centre.  The conic is stored
+// pre-scaled as (A, B, C) = (-a/2, -b, -c/2) so that power = A dx^2 + B dx dy + C dy^2.  The
+// rounding is fixed with explicit intrinsics: the forward and the backward kernels evaluate the
+// identical instruction sequence and therefore take identical cutoff decisions.
+__device__ __forceinline__ float splat_power(float A, float B, float C, float dx, float dy) {
+  return __fmaf_rn(dx, __fmaf_rn(A, dx, __fmul_rn(B, dy)), __fmul_rn(__fmul_rn(C, dy), dy));
+}
+
+__device__ __forceinline__ float splat_exp(float power) { return __expf(power); }
+
+// 64-bit global-tile/depth key helpers.
+__device__ __forceinline__ unsigned long long make_key(unsigned long long tile, float depth) {
+  return (tile << 32) | (unsigned long long)__float_as_uint(depth);
+}
+
+// Bounded spin limit for inter-CTA waits (decoupled look-back).  On expiry the waiting CTA sets
+// kErrTimeout and proceeds; the host reports GS_ERR_TIMEOUT.
+constexpr unsigned kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace gs

@@ -1,0 +1,98 @@
+// gs_engine.h -- host-side engine objects behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gs.h"
+#include "gs_device.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+extern thread_local std::string g_last_error;
+gs_status fail(gs_status s, const std::string& msg);
+
+void init_sort_attributes();
+void init_blend_attributes();
+
+// A device allocation that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  gs_status reserve(size_t want, size_t* account);
+  void release(size_t* account);
+};
+
+constexpr int kMaxViews = 32;
+constexpr int kNumKernels = 9;
+constexpr int kNumEvents = kNumKernels + 1;
+constexpr size_t kCtlBytes = 1024;                                   // Control, padded
+constexpr size_t kHistBytes = (size_t)kMaxSortPasses * kSortBins * 4;  // digit histograms
+
+// Workspaces and launch sequence of one rasterizer instance.
+struct Raster {
+  Raster();
+  ~Raster();
+
+  // problem of the current step
+  int n = 0, stride = 0, n_views = 0, passes = 0;
+  long long n_tiles = 0, n_pix = 0, n_loss_blocks = 0;
+  std::vector<ViewDev> views;
+  bool have_forward = false;
+  int sorted = 0;  // which ping-pong buffer holds the sorted list
+  int num_sms = 1;
+
+  // device buffers
+  DevBuf sp_d, views_d;
+  DevBuf zeroA;  // Control + scan look-back state (cleared before K1)
+  DevBuf zeroB;  // histograms + sort look-back state + ranges + chunk map (cleared before K3)
+  size_t zeroA_bytes = 0, zeroB_bytes = 0, sort_state_bytes = 0, ranges_bytes = 0, chunk_bytes = 0;
+  DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp;
+  DevBuf keys0, keys1, vals0, vals1, ginst, ckpt;
+  DevBuf partials, block_sums;
+  DevBuf own_image, own_last, own_dimage;  // used by sessions
+  unsigned long long m_cap = 0;
+  size_t bytes_in_use = 0;
+
+  // pinned staging
+  StepParams* sp_h = nullptr;
+  ViewDev* views_h = nullptr;
+  Control* ctl_h = nullptr;
+  cudaEvent_t staged = nullptr;
+
+  // timing
+  bool timing = false;
+  cudaEvent_t ev[kNumEvents];
+  double acc_ms[kNumKernels] = {0};
+  long long timed_steps = 0;
+
+  Control* ctl() const;
+  unsigned long long* scan_state() const;
+  unsigned* hist() const;
+  unsigned* sort_state() const;
+  uint2* ranges() const;
+  int* chunk_tile() const;
+  ProjBuffers proj() const;
+  const StepParams* sp() const { return static_cast<const StepParams*>(sp_d.p); }
+  const ViewDev* vd() const { return static_cast<const ViewDev*>(views_d.p); }
+
+  gs_status set_views(const gs_camera* cams, int nv, const float* const* targets);
+  gs_status ensure_records(int stride_);
+  gs_status ensure_instances(unsigned long long m);
+  gs_status stage(cudaStream_t s);
+  gs_status upload(cudaStream_t s);
+  void mark(cudaStream_t s, int k);
+  gs_status enqueue_forward_head(cudaStream_t s, const float* params, int stride_, bool size_exactly);
+  gs_status enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp);
+  void enqueue_loss(cudaStream_t s, const float* image, float* dimage);
+  void enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last, const float* dimage,
+                        float* grads, float* m, float* v, float* grad2d);
+  void enqueue_readback(cudaStream_t s);
+  gs_status collect_times();
+  gs_status check_control();
+};
+
+}  // namespace gs

@@ -1,0 +1,853 @@
+// gs_field.cu -- the session: a Gaussian field resident on the device with its Adam state and
+// registered images, the field update of Sec. IV-B, hierarchical image weighting (Eq. 3-4),
+// Local & Semi-Global iteration allocation (Eq. 5), the per-image learning rate (Eq. 6-8), and
+// optimisation steps replayed from captured CUDA graphs.
+//
+// Readings where the paper is silent (the same ones throughout the library):
+//  * overlap M[i][j] = tracks shared by images i and j / min(track counts);
+//  * hierarchy layers = breadth-first depth over M > 0 from the new image; unreachable images
+//    weigh 0; key images = the N_m highest positive weights (ties: lower id);
+//  * Eq. 5 rounded by largest remainder (ties: lower id) so the key images get exactly T_I / 2;
+//    the other half is split evenly over the non-key images, the remainder going to distinct
+//    images drawn by a partial Fisher-Yates shuffle; with no other image, Eq. 5 spreads all T_I;
+//    the T_I view slots are then Fisher-Yates shuffled;
+//  * random draws: SplitMix64 seeded with seed ^ ((new_id + 1) * 0x9E3779B97F4A7C15), a draw in
+//    [0, k) is next() mod k;
+//  * a step over several views uses the mean of their Eq. 8 rates; the rate scales the mean
+//    positions' Adam group by the scene extent (3DGS), the other groups keep the 3DGS rates;
+//  * new Gaussians (Sec. IV-B) follow the 3DGS initialisation: isotropic log-scale from the
+//    mean squared distance to the 3 nearest sparse points, identity rotation, opacity 0.1,
+//    DC colour from the point colour, higher SH zero.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <unordered_map>
+#include <vector>
+
+#include "gs_engine.h"
+
+namespace gs {
+
+namespace {
+
+struct SplitMix64 {
+  unsigned long long s;
+  explicit SplitMix64(unsigned long long seed) : s(seed) {}
+  unsigned long long next() {
+    s += 0x9E3779B97F4A7C15ull;
+    unsigned long long z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  unsigned long long below(unsigned long long k) { return next() % k; }
+};
+
+struct Image {
+  gs_camera cam;
+  DevBuf rgb;
+  std::vector<long long> tracks;  // sorted, unique
+  int T = 0;                      // iterations trained (Eq. 7)
+};
+
+// Uniform hash grid over the sparse points (stands in for the search tree of Sec. IV-B).
+struct PointGrid {
+  float cell = 1.f;
+  std::unordered_map<long long, std::vector<int>> cells;
+  std::vector<float> xyz;
+  static long long key(long long ix, long long iy, long long iz) {
+    return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
+  }
+  long long cidx(float v) const { return (long long)std::floor(v / cell); }
+  void insert(const float* p) {
+    const int id = (int)(xyz.size() / 3);
+    xyz.insert(xyz.end(), p, p + 3);
+    cells[key(cidx(p[0]), cidx(p[1]), cidx(p[2]))].push_back(id);
+  }
+  // squared distance to the nearest point within one cell ring (inf if none)
+  float nearest2_ring1(const float* p) const {
+    const long long cx = cidx(p[0]), cy = cidx(p[1]), cz = cidx(p[2]);
+    float best = INFINITY;
+    for (long long a = -1; a <= 1; ++a)
+      for (long long b = -1; b <= 1; ++b)
+        for (long long c = -1; c <= 1; ++c) {
+          auto it = cells.find(key(cx + a, cy + b, cz + c));
+          if (it == cells.end()) continue;
+          for (int id : it->second) {
+            const float dx = xyz[3 * id] - p[0], dy = xyz[3 * id + 1] - p[1], dz = xyz[3 * id + 2] - p[2];
+            best = std::min(best, dx * dx + dy * dy + dz * dz);
+          }
+        }
+    return best;
+  }
+  // mean squared distance to the k nearest other points (expanding shells of cells)
+  float knn_mean2(const float* p, int self, int k) const {
+    const long long cx = cidx(p[0]), cy = cidx(p[1]), cz = cidx(p[2]);
+    std::vector<float> best;
+    for (int r = 0; r < 64; ++r) {
+      for (long long a = -r; a <= r; ++a)
+        for (long long b = -r; b <= r; ++b)
+          for (long long c = -r; c <= r; ++c) {
+            if (std::max({std::llabs(a), std::llabs(b), std::llabs(c)}) != r) continue;
+            auto it = cells.find(key(cx + a, cy + b, cz + c));
+            if (it == cells.end()) continue;
+            for (int id : it->second) {
+              if (id == self) continue;
+              const float dx = xyz[3 * id] - p[0], dy = xyz[3 * id + 1] - p[1], dz = xyz[3 * id + 2] - p[2];
+              best.push_back(dx * dx + dy * dy + dz * dz);
+            }
+          }
+      if ((int)best.size() >= k) {
+        std::partial_sort(best.begin(), best.begin() + k, best.end());
+        const float reach = (float)r * cell;  // every point within this distance has been seen
+        if (best[k - 1] <= reach * reach) break;
+      }
+    }
+    if (best.empty()) return 1e-7f;
+    const int m = std::min(k, (int)best.size());
+    std::partial_sort(best.begin(), best.begin() + m, best.end());
+    float s = 0.f;
+    for (int q = 0; q < m; ++q) s += best[q];
+    return std::max(s / (float)m, 1e-7f);
+  }
+};
+
+// A captured step bakes in every device address and workspace layout it touches; the key holds
+// all of them so any reallocation or layout change forces a new capture.
+struct GraphKey {
+  std::vector<int> sizes;            // W, H per view
+  std::vector<unsigned long long> sig;  // buffer addresses and layout sizes
+  bool operator==(const GraphKey& o) const { return sizes == o.sizes && sig == o.sig; }
+};
+
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  bool timing = false;
+};
+
+}  // namespace
+
+struct Field {
+  gs_field_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::unique_ptr<Raster> r;
+  int n = 0, stride = 0;
+  DevBuf params, adam_m, adam_v;
+  long long adam_step = 0;
+  std::vector<Image> images;
+  std::vector<std::vector<float>> M;  // overlap matrix
+  PointGrid grid;
+  bool grid_ready = false;
+  // per-step buffers
+  DevBuf step_img, step_last, step_dimg, step_T, step_gp;
+  std::vector<GraphEntry> graphs;
+  bool sized_for_views = false;
+  std::vector<int> last_sizes;
+  double last_loss = 0.0;
+  unsigned long long last_pairs = 0;
+  size_t own_bytes = 0;
+
+  size_t bytes_in_use() const { return own_bytes + (r ? r->bytes_in_use : 0); }
+
+  ~Field() {
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    params.release(&own_bytes);
+    adam_m.release(&own_bytes);
+    adam_v.release(&own_bytes);
+    for (auto& im : images) im.rgb.release(&own_bytes);
+    step_img.release(&own_bytes);
+    step_last.release(&own_bytes);
+    step_dimg.release(&own_bytes);
+    step_T.release(&own_bytes);
+    step_gp.release(&own_bytes);
+  }
+
+  std::vector<unsigned long long> signature() const {
+    const Raster& R = *r;
+    std::vector<unsigned long long> v;
+    const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
+                            &R.sp_d, &R.views_d, &R.zeroA, &R.zeroB, &R.xyo, &R.conic, &R.rgb, &R.depth, &R.radius,
+                            &R.rect, &R.count, &R.offsets, &R.clamp, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
+                            &R.ckpt, &R.partials, &R.block_sums};
+    for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
+    const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)R.passes,
+                                      (unsigned long long)R.n_tiles, R.zeroA_bytes, R.zeroB_bytes, R.sort_state_bytes,
+                                      R.ranges_bytes, R.chunk_bytes, (unsigned long long)R.timing};
+    v.insert(v.end(), std::begin(lay), std::end(lay));
+    return v;
+  }
+
+  void drop_graphs() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+
+  float scene_extent() const {
+    if (cfg.scene_extent > 0.f) return cfg.scene_extent;
+    if (images.empty()) return 1.f;
+    double c[3] = {0, 0, 0};
+    std::vector<std::array<double, 3>> centres;
+    for (const auto& im : images) {
+      std::array<double, 3> p;
+      for (int a = 0; a < 3; ++a)
+        p[a] = -(im.cam.R[a] * im.cam.t[0] + im.cam.R[3 + a] * im.cam.t[1] + im.cam.R[6 + a] * im.cam.t[2]);
+      centres.push_back(p);
+      for (int a = 0; a < 3; ++a) c[a] += p[a];
+    }
+    for (int a = 0; a < 3; ++a) c[a] /= (double)centres.size();
+    double rmax = 0;
+    for (auto& p : centres) rmax = std::max(rmax, std::sqrt((p[0] - c[0]) * (p[0] - c[0]) + (p[1] - c[1]) * (p[1] - c[1]) +
+                                                             (p[2] - c[2]) * (p[2] - c[2])));
+    return (float)std::max(1.0, 1.1 * rmax);
+  }
+
+  // Grow parameter / Adam buffers to hold `want` Gaussians (stride multiple of 32).
+  gs_status reserve_gaussians(long long want) {
+    if (want <= stride) return GS_OK;
+    long long ns = std::max<long long>(want, (long long)stride * 2);
+    ns = std::max<long long>(ns, 1024);
+    ns = (ns + 31) / 32 * 32;
+    if (ns > (1 << 28)) return fail(GS_ERR_CAPACITY, "field capacity limit");
+    const size_t bytes = (size_t)ns * kNumParams * 4;
+    const size_t growth = 3 * (bytes - (size_t)stride * kNumParams * 4);
+    if (cfg.hbm_budget_bytes && bytes_in_use() + growth > cfg.hbm_budget_bytes)
+      return fail(GS_ERR_BUDGET, "growing the field would exceed hbm_budget_bytes");
+    DevBuf np, nm, nv;
+    gs_status s;
+    if ((s = np.reserve(bytes, &own_bytes)) || (s = nm.reserve(bytes, &own_bytes)) || (s = nv.reserve(bytes, &own_bytes))) {
+      np.release(&own_bytes);
+      nm.release(&own_bytes);
+      nv.release(&own_bytes);
+      return s;
+    }
+    cudaMemsetAsync(np.p, 0, bytes, stream);
+    cudaMemsetAsync(nm.p, 0, bytes, stream);
+    cudaMemsetAsync(nv.p, 0, bytes, stream);
+    if (n > 0) {
+      cudaMemcpy2DAsync(np.p, ns * 4, params.p, (size_t)stride * 4, (size_t)n * 4, kNumParams, cudaMemcpyDeviceToDevice, stream);
+      cudaMemcpy2DAsync(nm.p, ns * 4, adam_m.p, (size_t)stride * 4, (size_t)n * 4, kNumParams, cudaMemcpyDeviceToDevice, stream);
+      cudaMemcpy2DAsync(nv.p, ns * 4, adam_v.p, (size_t)stride * 4, (size_t)n * 4, kNumParams, cudaMemcpyDeviceToDevice, stream);
+    }
+    cudaStreamSynchronize(stream);
+    params.release(&own_bytes);
+    adam_m.release(&own_bytes);
+    adam_v.release(&own_bytes);
+    params = np;
+    adam_m = nm;
+    adam_v = nv;
+    stride = (int)ns;
+    drop_graphs();
+    sized_for_views = false;
+    return GS_OK;
+  }
+
+  // Eq. 6-7
+  double lr_current(int T) const {
+    const double t = T > cfg.T_a ? 1.0 : (double)T / (double)cfg.T_a;
+    return std::exp(std::log((double)cfg.eta0) * (1.0 - t) + std::log((double)cfg.etaf) * t);
+  }
+  // Eq. 8
+  double lr_image(int j) const {
+    double acc = lr_current(images[j].T);
+    int cnt = 0;
+    for (int i = 0; i < (int)images.size(); ++i) {
+      if (i == j || !(M[i][j] > 0.f)) continue;
+      acc += (double)M[i][j] * lr_current(images[i].T);
+      ++cnt;
+    }
+    return acc / (double)(cnt + 1);
+  }
+
+  // Eq. 3-4
+  void weights(int nw, std::vector<double>& w) const {
+    const int N = (int)images.size();
+    w.assign(N, 0.0);
+    std::vector<int> layer(N, 0);
+    w[nw] = 1.0;
+    layer[nw] = 1;
+    std::vector<int> prev = {nw};
+    int k = 1;
+    while (!prev.empty()) {
+      ++k;
+      std::vector<int> next;
+      for (int i = 0; i < N; ++i) {
+        if (layer[i]) continue;
+        for (int j : prev)
+          if (M[j][i] > 0.f) {
+            next.push_back(i);
+            break;
+          }
+      }
+      for (int i : next) layer[i] = k;
+      for (int i : next) {
+        if (k == 2) {
+          w[i] = w[nw] * (double)M[i][nw];
+        } else {
+          double s = 0;
+          for (int j : prev) s += w[j] * (double)M[j][i];
+          w[i] = s / (double)prev.size();
+        }
+      }
+      prev = next;
+    }
+  }
+
+  std::vector<int> key_images(const std::vector<double>& w, int n_m) const {
+    std::vector<int> cand;
+    for (int i = 0; i < (int)w.size(); ++i)
+      if (w[i] > 0.0) cand.push_back(i);
+    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return w[a] != w[b] ? w[a] > w[b] : a < b; });
+    if ((int)cand.size() > n_m) cand.resize(n_m);
+    return cand;
+  }
+
+  static std::vector<int> largest_remainder(const std::vector<double>& shares, const std::vector<int>& ids, int total) {
+    double s = 0;
+    for (double x : shares) s += x;
+    std::vector<double> exact(shares.size());
+    std::vector<int> base(shares.size());
+    int used = 0;
+    for (size_t k = 0; k < shares.size(); ++k) {
+      exact[k] = (double)total * shares[k] / s;
+      base[k] = (int)std::floor(exact[k]);
+      used += base[k];
+    }
+    std::vector<size_t> order(shares.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+      const double ra = exact[a] - base[a], rb = exact[b] - base[b];
+      return ra != rb ? ra > rb : ids[a] < ids[b];
+    });
+    for (int q = 0; q < total - used && q < (int)order.size(); ++q) base[order[q]] += 1;
+    return base;
+  }
+
+  // Eq. 5 + the semi-global half; returns the shuffled view slots
+  std::vector<int> allocate(int nw, int* n_keys) const {
+    std::vector<double> w;
+    weights(nw, w);
+    std::vector<int> keys = key_images(w, cfg.N_m);
+    if (n_keys) *n_keys = (int)keys.size();
+    std::vector<double> shares;
+    for (int i : keys) shares.push_back(1.0 - std::exp(-w[i]));
+    std::vector<char> is_key(images.size(), 0);
+    for (int i : keys) is_key[i] = 1;
+    std::vector<int> others;
+    for (int i = 0; i < (int)images.size(); ++i)
+      if (!is_key[i]) others.push_back(i);
+    SplitMix64 rng(cfg.seed ^ ((unsigned long long)(nw + 1) * 0x9E3779B97F4A7C15ull));
+    std::vector<int> iters(images.size(), 0);
+    const int T_I = cfg.T_I;
+    if (!others.empty()) {
+      std::vector<int> tk = largest_remainder(shares, keys, T_I / 2);
+      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
+      const int half = T_I - T_I / 2;
+      const int per = half / (int)others.size(), rem = half % (int)others.size();
+      std::vector<int> arr = others;
+      for (int i = 0; i < rem; ++i) {
+        const int j = i + (int)rng.below((unsigned long long)(arr.size() - i));
+        std::swap(arr[i], arr[j]);
+      }
+      for (int i : others) iters[i] = per;
+      for (int i = 0; i < rem; ++i) iters[arr[i]] += 1;
+    } else {
+      std::vector<int> tk = largest_remainder(shares, keys, T_I);
+      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
+    }
+    std::vector<int> slots;
+    for (int i = 0; i < (int)images.size(); ++i)
+      for (int q = 0; q < iters[i]; ++q) slots.push_back(i);
+    for (int i = (int)slots.size() - 1; i > 0; --i) {
+      const int j = (int)rng.below((unsigned long long)(i + 1));
+      std::swap(slots[i], slots[j]);
+    }
+    return slots;
+  }
+
+  gs_status ensure_step_buffers(long long pix) {
+    gs_status s;
+    if ((s = step_img.reserve(pix * 12, &own_bytes)) || (s = step_dimg.reserve(pix * 12, &own_bytes)) ||
+        (s = step_last.reserve(pix * 4, &own_bytes)) || (s = step_T.reserve(pix * 4, &own_bytes)) ||
+        (s = step_gp.reserve(pix * 4, &own_bytes)))
+      return s;
+    return GS_OK;
+  }
+
+  // Enqueue one whole step (forward, loss, backward + Adam) and the control readback.
+  gs_status enqueue_step(bool size_exactly) {
+    gs_status s;
+    Raster& R = *r;
+    R.upload(stream);
+    if ((s = R.enqueue_forward_head(stream, static_cast<float*>(params.p), stride, size_exactly))) return s;
+    if ((s = R.enqueue_forward_tail(stream, static_cast<float*>(step_img.p), static_cast<float*>(step_T.p),
+                                    static_cast<unsigned*>(step_last.p), static_cast<unsigned*>(step_gp.p))))
+      return s;
+    R.enqueue_loss(stream, static_cast<float*>(step_img.p), static_cast<float*>(step_dimg.p));
+    R.enqueue_backward(stream, static_cast<float*>(params.p), static_cast<float*>(step_img.p),
+                       static_cast<unsigned*>(step_last.p), static_cast<float*>(step_dimg.p), nullptr,
+                       static_cast<float*>(adam_m.p), static_cast<float*>(adam_v.p), nullptr);
+    R.enqueue_readback(stream);
+    return GS_OK;
+  }
+
+  gs_status step(const int* ids, int nv, float* out_loss) {
+    if (nv <= 0 || nv > kMaxViews) return fail(GS_ERR_CAPACITY, "views per step must be in 1..32");
+    if (n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
+    std::vector<gs_camera> cams(nv);
+    std::vector<const float*> tg(nv);
+    std::vector<int> sizes;
+    double lr_sum = 0;
+    for (int k = 0; k < nv; ++k) {
+      if (ids[k] < 0 || ids[k] >= (int)images.size()) return fail(GS_ERR_INVALID_ARG, "view id out of range");
+      cams[k] = images[ids[k]].cam;
+      tg[k] = static_cast<const float*>(images[ids[k]].rgb.p);
+      sizes.push_back(cams[k].width);
+      sizes.push_back(cams[k].height);
+      lr_sum += lr_image(ids[k]);
+    }
+    Raster& R = *r;
+    gs_status s;
+    if ((s = R.set_views(cams.data(), nv, tg.data()))) return s;
+    R.stride = stride;
+    R.n = n;
+    if ((s = R.ensure_records(stride)) || (s = ensure_step_buffers(R.n_pix))) return s;
+    if ((s = R.ensure_instances(R.m_cap))) return s;
+    ++adam_step;
+    const double lr_means = lr_sum / nv * (double)scene_extent();
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      if ((s = R.stage(stream))) return s;
+      StepParams& P = *R.sp_h;
+      P.n = n;
+      P.n_views = nv;
+      for (int a = 0; a < 3; ++a) P.bg[a] = cfg.bg[a];
+      P.lambda_ssim = cfg.lambda_ssim;
+      P.lr[0] = (float)lr_means;
+      P.lr[1] = cfg.lr_scale;
+      P.lr[2] = cfg.lr_rot;
+      P.lr[3] = cfg.lr_opacity;
+      P.lr[4] = cfg.lr_sh_dc;
+      P.lr[5] = cfg.lr_sh_rest;
+      P.beta1 = cfg.beta1;
+      P.beta2 = cfg.beta2;
+      P.eps = cfg.adam_eps;
+      P.step_size_scale = (float)(1.0 / (1.0 - std::pow((double)cfg.beta1, (double)adam_step)));
+      P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow((double)cfg.beta2, (double)adam_step));
+      P.adam = 1;
+      const bool first = !sized_for_views || sizes != last_sizes;
+      if (first) {
+        // Size the instance buffers from this step's exact count (one mid-step sync).
+        if ((s = enqueue_step(true))) return s;
+        sized_for_views = true;
+        last_sizes = sizes;
+      } else if (cfg.use_graph) {
+        GraphKey key{sizes, signature()};
+        GraphEntry* ge = nullptr;
+        for (auto& g : graphs)
+          if (g.key == key && g.timing == R.timing) ge = &g;
+        if (!ge) {
+          if (graphs.size() >= 8) drop_graphs();
+          cudaGraph_t graph;
+          cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+          // The pinned staging copy is captured: each replay re-reads sp_h / views_h.
+          gs_status cs = enqueue_step(false);
+          e = cudaStreamEndCapture(stream, &graph);
+          if (cs) return cs;
+          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+          GraphEntry g;
+          g.key = key;
+          g.timing = R.timing;
+          e = cudaGraphInstantiate(&g.exec, graph, 0);
+          cudaGraphDestroy(graph);
+          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+          graphs.push_back(g);
+          ge = &graphs.back();
+        }
+        std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * nv);
+        cudaError_t e = cudaGraphLaunch(ge->exec, stream);
+        if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+        cudaEventRecord(R.staged, stream);
+      } else {
+        if ((s = enqueue_step(false))) return s;
+      }
+      cudaError_t e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step: ") + cudaGetErrorString(e));
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+      if (R.ctl_h->overflow) {
+        // Nothing after the scan ran; grow and run the step again.
+        if ((s = R.ensure_instances(R.ctl_h->m_total + R.ctl_h->m_total / 4 + 1024))) return s;
+        drop_graphs();
+        continue;
+      }
+      if ((s = R.check_control())) return s;
+      R.collect_times();
+      last_loss = R.ctl_h->loss;
+      last_pairs = R.ctl_h->pairs;
+      if (out_loss) *out_loss = (float)last_loss;
+      for (int k = 0; k < nv; ++k) images[ids[k]].T += 1;
+      R.have_forward = true;
+      return GS_OK;
+    }
+    return fail(GS_ERR_CAPACITY, "instance buffers kept overflowing");
+  }
+};
+
+}  // namespace gs
+
+using gs::fail;
+using gs::Field;
+
+static Field* F(gs_field* f) { return reinterpret_cast<Field*>(f); }
+static const Field* F(const gs_field* f) { return reinterpret_cast<const Field*>(f); }
+
+extern "C" {
+
+void gs_field_config_default(gs_field_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->T_I = 200;
+  c->N_m = 10;
+  c->T_a = 200;
+  c->batch_views = 1;
+  c->use_graph = 1;
+  c->eta0 = 1.6e-4f;
+  c->etaf = 1.6e-6f;
+  c->lambda_ssim = 0.2f;
+  c->lr_scale = 5e-3f;
+  c->lr_rot = 1e-3f;
+  c->lr_opacity = 0.05f;
+  c->lr_sh_dc = 2.5e-3f;
+  c->lr_sh_rest = 2.5e-3f / 20.f;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.999f;
+  c->adam_eps = 1e-15f;
+  c->seed = 0;
+  c->initial_capacity = 0;
+}
+
+gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out) {
+  if (!cfg || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (cfg->T_I <= 0 || cfg->N_m <= 0 || cfg->T_a <= 0 || cfg->batch_views <= 0 || cfg->batch_views > gs::kMaxViews ||
+      !(cfg->eta0 > 0.f) || !(cfg->etaf > 0.f) || cfg->lambda_ssim < 0.f || cfg->lambda_ssim > 1.f)
+    return fail(GS_ERR_INVALID_ARG, "invalid field configuration");
+  Field* f = new (std::nothrow) Field();
+  if (!f) return fail(GS_ERR_OOM, "host allocation failed");
+  f->cfg = *cfg;
+  f->stream = static_cast<cudaStream_t>(stream);
+  if (!f->stream) {
+    // Graph capture needs a non-legacy stream.
+    if (cudaStreamCreateWithFlags(&f->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete f;
+      return fail(GS_ERR_CUDA, "stream creation failed");
+    }
+    f->own_stream = true;
+  }
+  f->r.reset(new (std::nothrow) gs::Raster());
+  if (!f->r || !f->r->sp_h || !f->r->sp_d.p) {
+    delete f;
+    return fail(GS_ERR_OOM, "raster allocation failed");
+  }
+  if (cfg->initial_capacity > 0) {
+    gs_status s = f->reserve_gaussians(cfg->initial_capacity);
+    if (s) {
+      delete f;
+      return s;
+    }
+  }
+  *out = reinterpret_cast<gs_field*>(f);
+  return GS_OK;
+}
+
+gs_status gs_field_destroy(gs_field* f) {
+  if (!f) return GS_OK;
+  cudaStreamSynchronize(F(f)->stream);
+  delete F(f);
+  return GS_OK;
+}
+
+gs_status gs_field_set_gaussians(gs_field* ff, const float* host, int64_t n, int64_t src_stride) {
+  Field* f = F(ff);
+  if (!f || (!host && n > 0) || n < 0 || src_stride < n) return fail(GS_ERR_INVALID_ARG, "bad arguments");
+  gs_status s = f->reserve_gaussians(std::max<int64_t>(n, 1));
+  if (s) return s;
+  const size_t bytes = (size_t)f->stride * gs::kNumParams * 4;
+  cudaMemsetAsync(f->params.p, 0, bytes, f->stream);
+  cudaMemsetAsync(f->adam_m.p, 0, bytes, f->stream);
+  cudaMemsetAsync(f->adam_v.p, 0, bytes, f->stream);
+  if (n > 0)
+    cudaMemcpy2DAsync(f->params.p, (size_t)f->stride * 4, host, (size_t)src_stride * 4, (size_t)n * 4, gs::kNumParams,
+                      cudaMemcpyHostToDevice, f->stream);
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  f->n = (int)n;
+  f->adam_step = 0;
+  return GS_OK;
+}
+
+gs_status gs_field_get_gaussians(gs_field* ff, float* host, float* host_m, float* host_v, int64_t dst_stride,
+                                 int64_t* out_n) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  if (out_n) *out_n = f->n;
+  if (!host && !host_m && !host_v) return GS_OK;
+  if (dst_stride < f->n) return fail(GS_ERR_INVALID_ARG, "dst_stride < n");
+  cudaStreamSynchronize(f->stream);
+  const gs::DevBuf* src[3] = {&f->params, &f->adam_m, &f->adam_v};
+  float* dst[3] = {host, host_m, host_v};
+  for (int k = 0; k < 3; ++k) {
+    if (!dst[k] || f->n == 0) continue;
+    cudaError_t e = cudaMemcpy2D(dst[k], (size_t)dst_stride * 4, src[k]->p, (size_t)f->stride * 4, (size_t)f->n * 4,
+                                 gs::kNumParams, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return GS_OK;
+}
+
+gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int on_device, const float* pts_xyz,
+                       const float* pts_rgb, int32_t n_pts, const int64_t* tracks, int32_t* out_id) {
+  Field* f = F(ff);
+  if (!f || !cam || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  if (n_pts < 0 || (n_pts > 0 && (!pts_xyz || !pts_rgb))) return fail(GS_ERR_INVALID_ARG, "bad sparse points");
+  if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f))
+    return fail(GS_ERR_INVALID_ARG, "bad camera");
+  if (f->images.size() >= 4096) return fail(GS_ERR_CAPACITY, "image registry full (4096)");
+  const size_t img_bytes = (size_t)cam->width * cam->height * 3 * 4;
+  if (f->cfg.hbm_budget_bytes && f->bytes_in_use() + img_bytes > f->cfg.hbm_budget_bytes)
+    return fail(GS_ERR_BUDGET, "registering the image would exceed hbm_budget_bytes");
+  gs::Image im;
+  im.cam = *cam;
+  gs_status s = im.rgb.reserve(img_bytes, &f->own_bytes);
+  if (s) return s;
+  cudaError_t e = cudaMemcpyAsync(im.rgb.p, rgb, img_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  f->stream);
+  if (e != cudaSuccess) {
+    im.rgb.release(&f->own_bytes);
+    return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if (tracks && n_pts > 0) {
+    im.tracks.assign(tracks, tracks + n_pts);
+    std::sort(im.tracks.begin(), im.tracks.end());
+    im.tracks.erase(std::unique(im.tracks.begin(), im.tracks.end()), im.tracks.end());
+  }
+  const int id = (int)f->images.size();
+  f->images.push_back(std::move(im));
+  // overlap row / column
+  for (auto& row : f->M) row.push_back(0.f);
+  f->M.push_back(std::vector<float>(f->images.size(), 0.f));
+  const auto& tn = f->images[id].tracks;
+  for (int i = 0; i < id; ++i) {
+    const auto& ti = f->images[i].tracks;
+    if (ti.empty() || tn.empty()) continue;
+    size_t a = 0, b = 0, shared = 0;
+    while (a < ti.size() && b < tn.size()) {
+      if (ti[a] < tn[b]) ++a;
+      else if (ti[a] > tn[b]) ++b;
+      else {
+        ++shared;
+        ++a;
+        ++b;
+      }
+    }
+    const float m = (float)shared / (float)std::min(ti.size(), tn.size());
+    f->M[i][id] = m;
+    f->M[id][i] = m;
+  }
+  // Field update (Sec. IV-B): points farther than the threshold from every existing sparse
+  // point become new Gaussians.
+  float thr = f->cfg.add_dist_thresh > 0.f ? f->cfg.add_dist_thresh : 0.01f * f->scene_extent();
+  if (!f->grid_ready) {
+    f->grid.cell = std::max(thr, 1e-6f);
+    f->grid_ready = true;
+  }
+  std::vector<int> fresh;
+  for (int k = 0; k < n_pts; ++k) {
+    const float* p = pts_xyz + 3 * k;
+    if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]))) continue;
+    const float d2 = f->grid.nearest2_ring1(p);
+    if (!(d2 <= thr * thr)) fresh.push_back(k);
+  }
+  const int first_pt = (int)(f->grid.xyz.size() / 3);
+  for (int k = 0; k < n_pts; ++k) f->grid.insert(pts_xyz + 3 * k);
+  if (!fresh.empty()) {
+    s = f->reserve_gaussians((long long)f->n + (long long)fresh.size());
+    if (s) {
+      if (out_id) *out_id = id;
+      return s;
+    }
+    const int nn = (int)fresh.size();
+    std::vector<float> cols((size_t)gs::kNumParams * nn, 0.f);
+    const double C0 = 0.5 * std::sqrt(1.0 / 3.14159265358979323846);
+    for (int q = 0; q < nn; ++q) {
+      const int k = fresh[q];
+      const float* p = pts_xyz + 3 * k;
+      for (int a = 0; a < 3; ++a) cols[(size_t)a * nn + q] = p[a];
+      const float d2 = f->grid.knn_mean2(p, first_pt + k, 3);
+      const float ls = std::log(std::sqrt(d2));
+      for (int a = 0; a < 3; ++a) cols[(size_t)(3 + a) * nn + q] = ls;
+      cols[(size_t)6 * nn + q] = 1.f;
+      cols[(size_t)10 * nn + q] = (float)std::log(0.1 / 0.9);
+      for (int ch = 0; ch < 3; ++ch) cols[(size_t)(11 + ch) * nn + q] = (float)((pts_rgb[3 * k + ch] - 0.5) / C0);
+    }
+    e = cudaMemcpy2DAsync(static_cast<float*>(f->params.p) + f->n, (size_t)f->stride * 4, cols.data(), (size_t)nn * 4,
+                          (size_t)nn * 4, gs::kNumParams, cudaMemcpyHostToDevice, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+    f->n += nn;
+  } else {
+    cudaStreamSynchronize(f->stream);
+  }
+  if (out_id) *out_id = id;
+  return GS_OK;
+}
+
+gs_status gs_set_image(gs_field* ff, int32_t id, const gs_camera* cam, const float* rgb, int on_device) {
+  Field* f = F(ff);
+  if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
+  gs::Image& im = f->images[id];
+  if (cam) {
+    if (cam->width != im.cam.width || cam->height != im.cam.height) return fail(GS_ERR_INVALID_ARG, "size change");
+    im.cam = *cam;
+  }
+  if (rgb) {
+    const size_t bytes = (size_t)im.cam.width * im.cam.height * 12;
+    cudaError_t e = cudaMemcpyAsync(im.rgb.p, rgb, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    f->stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return GS_OK;
+}
+
+gs_status gs_select_neighbors(gs_field* ff, int32_t id, int32_t k, int32_t* out_ids, float* out_w, int32_t* out_n) {
+  Field* f = F(ff);
+  if (!f || id < 0 || id >= (int)f->images.size() || k < 0 || !out_ids) return fail(GS_ERR_INVALID_ARG, "bad arguments");
+  std::vector<double> w;
+  f->weights(id, w);
+  std::vector<int> keys = f->key_images(w, k + 1);
+  for (size_t q = 0; q < keys.size(); ++q) {
+    out_ids[q] = keys[q];
+    if (out_w) out_w[q] = (float)w[keys[q]];
+  }
+  if (out_n) *out_n = (int)keys.size();
+  return GS_OK;
+}
+
+gs_status gs_optimize_step(gs_field* ff, const int32_t* ids, int32_t nv, float* out_loss) {
+  Field* f = F(ff);
+  if (!f || !ids) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  std::vector<int> v(ids, ids + nv);
+  return f->step(v.data(), nv, out_loss);
+}
+
+gs_status gs_integrate(gs_field* ff, int32_t id, gs_integrate_stats* st) {
+  Field* f = F(ff);
+  if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
+  int nk = 0;
+  std::vector<int> slots = f->allocate(id, &nk);
+  const int B = f->cfg.batch_views;
+  double loss_sum = 0;
+  int steps = 0;
+  unsigned long long pairs = 0;
+  for (size_t q = 0; q < slots.size(); q += B) {
+    const int nb = (int)std::min<size_t>(B, slots.size() - q);
+    float l = 0.f;
+    gs_status s = f->step(slots.data() + q, nb, &l);
+    if (s) return s;
+    loss_sum += l;
+    pairs += f->last_pairs;
+    ++steps;
+  }
+  if (st) {
+    st->iterations = (int)slots.size();
+    st->steps = steps;
+    st->key_images = nk;
+    st->new_gaussians = 0;
+    st->mean_loss = steps ? loss_sum / steps : 0.0;
+    st->pairs = pairs;
+  }
+  return GS_OK;
+}
+
+gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* out_T) {
+  Field* f = F(ff);
+  if (!f || !cam || !out_rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  if (f->n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
+  gs::Raster& R = *f->r;
+  gs_status s;
+  if ((s = R.set_views(cam, 1, nullptr))) return s;
+  R.stride = f->stride;
+  R.n = f->n;
+  if ((s = R.ensure_records(f->stride)) || (s = f->ensure_step_buffers(R.n_pix)) || (s = R.ensure_instances(R.m_cap)))
+    return s;
+  if ((s = R.stage(f->stream))) return s;
+  gs::StepParams& P = *R.sp_h;
+  P.n = f->n;
+  P.n_views = 1;
+  for (int a = 0; a < 3; ++a) P.bg[a] = f->cfg.bg[a];
+  P.adam = 0;
+  R.upload(f->stream);
+  if ((s = R.enqueue_forward_head(f->stream, static_cast<float*>(f->params.p), f->stride, true))) return s;
+  if ((s = R.enqueue_forward_tail(f->stream, out_rgb, out_T, static_cast<unsigned*>(f->step_last.p), nullptr))) return s;
+  f->sized_for_views = false;
+  R.enqueue_readback(f->stream);
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("render: ") + cudaGetErrorString(e));
+  return R.check_control();
+}
+
+gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
+  const Field* f = F(ff);
+  if (!f || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  out->n_gaussians = f->n;
+  out->capacity = f->stride;
+  out->n_images = (int64_t)f->images.size();
+  out->adam_step = f->adam_step;
+  out->bytes_in_use = f->bytes_in_use();
+  out->last_pairs = f->last_pairs;
+  out->last_loss = f->last_loss;
+  return GS_OK;
+}
+
+gs_status gs_image_info(const gs_field* ff, int32_t id, int32_t* out_T, float* row, int32_t row_len) {
+  const Field* f = F(ff);
+  if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
+  if (out_T) *out_T = f->images[id].T;
+  if (row)
+    for (int i = 0; i < row_len && i < (int)f->images.size(); ++i) row[i] = f->M[id][i];
+  return GS_OK;
+}
+
+gs_status gs_image_lr(const gs_field* ff, int32_t id, float* out_lr) {
+  const Field* f = F(ff);
+  if (!f || !out_lr || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad arguments");
+  *out_lr = (float)f->lr_image(id);
+  return GS_OK;
+}
+
+gs_status gs_field_set_timing(gs_field* ff, int enable) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  f->r->timing = enable != 0;
+  std::memset(f->r->acc_ms, 0, sizeof(f->r->acc_ms));
+  f->r->timed_steps = 0;
+  return GS_OK;
+}
+
+gs_status gs_field_kernel_times(gs_field* ff, float out_ms[9], int64_t* out_steps) {
+  Field* f = F(ff);
+  if (!f || !out_ms) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < gs::kNumKernels; ++k) out_ms[k] = (float)f->r->acc_ms[k];
+  if (out_steps) *out_steps = f->r->timed_steps;
+  return GS_OK;
+}
+
+}  // extern "C"

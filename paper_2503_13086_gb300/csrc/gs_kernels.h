@@ -1,0 +1,65 @@
+// gs_kernels.h -- launch wrappers of the rasterizer kernels (host-visible declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "gs_device.cuh"
+
+namespace gs {
+
+// Per-record outputs of K1 (record = view * stride + Gaussian id).
+struct ProjBuffers {
+  float4* xyo;           // (u, v, opacity, 0)
+  float4* conic;         // pre-scaled conic (-a/2, -b, -c/2, 0)
+  float4* rgb;           // (r, g, b, 0)
+  float* depth;          // camera-space z
+  int* radius;           // 0 = culled
+  uint2* rect;           // (x0 | x1 << 16, y0 | y1 << 16) tile rectangle
+  unsigned* count;       // tiles touched, 0 = culled
+  unsigned* offsets;     // exclusive scan of count
+  unsigned char* clamp;  // bit ch set: colour channel ch was clamped at 0
+};
+
+// Sort geometry.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep CTA
+constexpr int kSortBits = 8;
+constexpr int kSortBins = 1 << kSortBits;
+constexpr int kMaxSortPasses = 8;
+
+void launch_project(const float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
+                    const ProjBuffers& out, cudaStream_t s);
+void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
+                             const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
+                             float* m, float* v, float* grad2d_out, cudaStream_t s);
+void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
+                 cudaStream_t s);
+
+void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
+                 unsigned long long m_cap, cudaStream_t s);
+void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys,
+                 unsigned* vals, unsigned* hist, int passes, const Control* ctl, cudaStream_t s);
+void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout, unsigned* vout,
+                      const unsigned* hist, unsigned* state, int pass, long long m_cap, Control* ctl, cudaStream_t s);
+void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s);
+
+void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+                          const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
+                          float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt, int* chunk_tile,
+                          cudaStream_t s);
+void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+                           const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
+                           const unsigned* last, const float* dimage, const float4* ckpt, const int* chunk_tile,
+                           float4* ginst, int num_sms, cudaStream_t s);
+
+// Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
+long long loss_blocks(int W, int H);
+void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
+                 float* partials, double* block_sums, Control* ctl, float* dimage, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,529 @@
+// k_project.cu -- K1 (EWA projection + SH colour) and the fused K9 + K10 (projection backward
+// chained straight into Adam), sm_103a.
+//
+// K1 evaluates, per (view, Gaussian), Eq. 1 (Sigma = R S S^T R^T) and its EWA splat into the
+// image as used by the 3DGS rasterizer (Sec. III; constants of the original 3DGS, Sec. V-A), the
+// degree-3 SH colour and the tile rectangle.  K9 chains the per-instance 2D gradients from the
+// blend backward into the 59 parameters of each Gaussian, summed over the views of the step,
+// and K10 applies Adam with the per-group learning rate (the mean-position rate is the per-image
+// rate of Eq. 6-8) in the same pass, so no gradient buffer is written or read.
+//
+// Data layout: parameters component-major, params[c * stride + i] (see gs.h).  Per-record
+// outputs (record = view * stride + Gaussian) are structure-of-arrays of 16-byte records so the
+// blend kernels gather a Gaussian with three 16-byte loads.
+#include "gs_device.cuh"
+#include "gs_kernels.h"
+
+namespace gs {
+
+// Real SH up to degree 3 (Condon-Shortley phase, 3DGS ordering).  The constants are the
+// normalisation factors sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!): 1/(2 sqrt(pi)), sqrt(3/(4 pi)),
+// sqrt(15/pi)/2, sqrt(5/pi)/4, sqrt(15/pi)/4, sqrt(35/(2 pi))/4, sqrt(105/pi)/2,
+// sqrt(21/(2 pi))/4, sqrt(7/pi)/4, sqrt(105/pi)/4.
+constexpr float kSH0 = 0.28209479177387814f;
+constexpr float kSH1 = 0.48860251190291992f;
+constexpr float kSH2a = 1.09254843059207907f;
+constexpr float kSH2b = 0.31539156525252005f;
+constexpr float kSH2c = 0.54627421529603953f;
+constexpr float kSH3a = 0.59004358992664352f;
+constexpr float kSH3b = 2.89061144264055405f;
+constexpr float kSH3c = 0.45704579946446573f;
+constexpr float kSH3d = 0.37317633259011540f;
+constexpr float kSH3e = 1.44530572132027702f;
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float Y[16]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = kSH0;
+  Y[1] = -kSH1 * y;
+  Y[2] = kSH1 * z;
+  Y[3] = -kSH1 * x;
+  Y[4] = kSH2a * x * y;
+  Y[5] = -kSH2a * y * z;
+  Y[6] = kSH2b * (2.f * zz - xx - yy);
+  Y[7] = -kSH2a * x * z;
+  Y[8] = kSH2c * (xx - yy);
+  Y[9] = -kSH3a * y * (3.f * xx - yy);
+  Y[10] = kSH3b * x * y * z;
+  Y[11] = -kSH3c * y * (4.f * zz - xx - yy);
+  Y[12] = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kSH3c * x * (4.f * zz - xx - yy);
+  Y[14] = kSH3e * z * (xx - yy);
+  Y[15] = -kSH3a * x * (xx - 3.f * yy);
+}
+
+// Accumulate into d[3] the gradient with respect to (x, y, z) of sum_k Y_k(x, y, z) * w[k].
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float w[16], float d[3]) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  float gx = 0.f, gy = 0.f, gz = 0.f;
+  gy += -kSH1 * w[1];
+  gz += kSH1 * w[2];
+  gx += -kSH1 * w[3];
+  gx += kSH2a * y * w[4];
+  gy += kSH2a * x * w[4];
+  gy += -kSH2a * z * w[5];
+  gz += -kSH2a * y * w[5];
+  gx += -2.f * kSH2b * x * w[6];
+  gy += -2.f * kSH2b * y * w[6];
+  gz += 4.f * kSH2b * z * w[6];
+  gx += -kSH2a * z * w[7];
+  gz += -kSH2a * x * w[7];
+  gx += 2.f * kSH2c * x * w[8];
+  gy += -2.f * kSH2c * y * w[8];
+  gx += -6.f * kSH3a * x * y * w[9];
+  gy += -kSH3a * (3.f * xx - 3.f * yy) * w[9];
+  gx += kSH3b * y * z * w[10];
+  gy += kSH3b * x * z * w[10];
+  gz += kSH3b * x * y * w[10];
+  gx += 2.f * kSH3c * x * y * w[11];
+  gy += -kSH3c * (4.f * zz - xx - 3.f * yy) * w[11];
+  gz += -8.f * kSH3c * y * z * w[11];
+  gx += -6.f * kSH3d * x * z * w[12];
+  gy += -6.f * kSH3d * y * z * w[12];
+  gz += kSH3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12];
+  gx += -kSH3c * (4.f * zz - 3.f * xx - yy) * w[13];
+  gy += 2.f * kSH3c * x * y * w[13];
+  gz += -8.f * kSH3c * x * z * w[13];
+  gx += 2.f * kSH3e * x * z * w[14];
+  gy += -2.f * kSH3e * y * z * w[14];
+  gz += kSH3e * (xx - yy) * w[14];
+  gx += -kSH3a * (3.f * xx - 3.f * yy) * w[15];
+  gy += 6.f * kSH3a * x * y * w[15];
+  d[0] += gx;
+  d[1] += gy;
+  d[2] += gz;
+}
+
+// Geometry of one Gaussian seen from one view: what K1 computes and K9 recomputes.
+struct Geo {
+  float p[3];          // camera-space mean
+  float qn[4], qinv;   // normalised quaternion, 1/|q|
+  float Rq[9], s[3];
+  float M[9];          // Rq diag(s)
+  float Sig[6];        // 3D covariance (xx, xy, xz, yy, yz, zz)
+  float Tm[6];         // J R_cam
+  float txz, tyz;
+  bool xin, yin;
+  float cov[3];        // dilated 2D covariance (a', b', c')
+  float det;
+};
+
+__device__ __forceinline__ bool geo_forward(const ViewDev& V, const float mu[3], const float ls[3],
+                                            const float q[4], Geo& g) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    g.p[r] = V.R[3 * r] * mu[0] + V.R[3 * r + 1] * mu[1] + V.R[3 * r + 2] * mu[2] + V.t[r];
+  if (!(g.p[2] > kNearZ)) return false;
+  const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  if (!(qq > 0.f)) return false;
+  g.qinv = rsqrtf(qq);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) g.qn[k] = q[k] * g.qinv;
+  const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+  g.Rq[0] = 1.f - 2.f * (y * y + z * z);
+  g.Rq[1] = 2.f * (x * y - w * z);
+  g.Rq[2] = 2.f * (x * z + w * y);
+  g.Rq[3] = 2.f * (x * y + w * z);
+  g.Rq[4] = 1.f - 2.f * (x * x + z * z);
+  g.Rq[5] = 2.f * (y * z - w * x);
+  g.Rq[6] = 2.f * (x * z - w * y);
+  g.Rq[7] = 2.f * (y * z + w * x);
+  g.Rq[8] = 1.f - 2.f * (x * x + y * y);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g.s[k] = __expf(ls[k]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g.M[3 * r + c] = g.Rq[3 * r + c] * g.s[c];
+  auto dotrow = [&](int a, int b) {
+    return g.M[3 * a] * g.M[3 * b] + g.M[3 * a + 1] * g.M[3 * b + 1] + g.M[3 * a + 2] * g.M[3 * b + 2];
+  };
+  g.Sig[0] = dotrow(0, 0);
+  g.Sig[1] = dotrow(0, 1);
+  g.Sig[2] = dotrow(0, 2);
+  g.Sig[3] = dotrow(1, 1);
+  g.Sig[4] = dotrow(1, 2);
+  g.Sig[5] = dotrow(2, 2);
+
+  const float pz = g.p[2];
+  const float iz = 1.f / pz;
+  const float xz = g.p[0] * iz, yz = g.p[1] * iz;
+  g.xin = (xz >= -V.limx) && (xz <= V.limx);
+  g.yin = (yz >= -V.limy) && (yz <= V.limy);
+  g.txz = fminf(V.limx, fmaxf(-V.limx, xz));
+  g.tyz = fminf(V.limy, fmaxf(-V.limy, yz));
+  const float J00 = V.fx * iz, J02 = -V.fx * g.txz * iz;
+  const float J11 = V.fy * iz, J12 = -V.fy * g.tyz * iz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g.Tm[c] = J00 * V.R[c] + J02 * V.R[6 + c];
+    g.Tm[3 + c] = J11 * V.R[3 + c] + J12 * V.R[6 + c];
+  }
+  // Sigma full-matrix accessor
+  const float S[9] = {g.Sig[0], g.Sig[1], g.Sig[2], g.Sig[1], g.Sig[3], g.Sig[4], g.Sig[2], g.Sig[4], g.Sig[5]};
+  float st0[3], st1[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    st0[r] = S[3 * r] * g.Tm[0] + S[3 * r + 1] * g.Tm[1] + S[3 * r + 2] * g.Tm[2];
+    st1[r] = S[3 * r] * g.Tm[3] + S[3 * r + 1] * g.Tm[4] + S[3 * r + 2] * g.Tm[5];
+  }
+  g.cov[0] = g.Tm[0] * st0[0] + g.Tm[1] * st0[1] + g.Tm[2] * st0[2] + kDilate;
+  g.cov[1] = g.Tm[0] * st1[0] + g.Tm[1] * st1[1] + g.Tm[2] * st1[2];
+  g.cov[2] = g.Tm[3] * st1[0] + g.Tm[4] * st1[1] + g.Tm[5] * st1[2] + kDilate;
+  g.det = g.cov[0] * g.cov[2] - g.cov[1] * g.cov[1];
+  return g.det > 0.f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K1: projection forward.  grid = (ceil(stride / 256), views); one thread per (view, Gaussian).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ params, int stride,
+                                                 const StepParams* __restrict__ sp,
+                                                 const ViewDev* __restrict__ views, ProjBuffers out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (i >= stride) return;
+  const long long rec = (long long)v * stride + i;
+  const int n = sp->n;
+  auto cull = [&]() {
+    out.count[rec] = 0u;
+    out.radius[rec] = 0;
+  };
+  if (i >= n) {
+    cull();
+    return;
+  }
+  const ViewDev& V = views[v];
+  const float mu[3] = {__ldg(params + i), __ldg(params + stride + i), __ldg(params + 2 * stride + i)};
+  const float ls[3] = {__ldg(params + 3 * stride + i), __ldg(params + 4 * stride + i), __ldg(params + 5 * stride + i)};
+  const float q[4] = {__ldg(params + 6 * stride + i), __ldg(params + 7 * stride + i), __ldg(params + 8 * stride + i),
+                      __ldg(params + 9 * stride + i)};
+  Geo g;
+  if (!geo_forward(V, mu, ls, q, g)) {
+    cull();
+    return;
+  }
+  const float det = g.det;
+  const float ca = g.cov[2] / det, cb = -g.cov[1] / det, cc = g.cov[0] / det;
+  const float u = V.fx * g.p[0] / g.p[2] + V.cx;
+  const float vv = V.fy * g.p[1] / g.p[2] + V.cy;
+  const float mid = 0.5f * (g.cov[0] + g.cov[2]);
+  const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
+  const int r = (int)ceilf(3.f * sqrtf(lam));
+  // Tile rectangle: [floor((u - r)/16), floor((u + r + 15)/16)) clamped to the grid, the same
+  // fp32 expression the key emission and its checks use.
+  const float rf = (float)r;
+  int x0 = (int)floorf(__fdiv_rn(__fsub_rn(u, rf), (float)kTile));
+  int y0 = (int)floorf(__fdiv_rn(__fsub_rn(vv, rf), (float)kTile));
+  int x1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, rf), (float)(kTile - 1)), (float)kTile));
+  int y1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(vv, rf), (float)(kTile - 1)), (float)kTile));
+  x0 = min(V.gx, max(0, x0));
+  x1 = min(V.gx, max(0, x1));
+  y0 = min(V.gy, max(0, y0));
+  y1 = min(V.gy, max(0, y1));
+  const unsigned cnt = (unsigned)((x1 - x0) * (y1 - y0));
+  if (cnt == 0u || !isfinite(u) || !isfinite(vv) || !isfinite(ca) || !isfinite(cb) || !isfinite(cc)) {
+    cull();
+    return;
+  }
+  // Colour: degree-3 SH at the unit direction from the camera centre to the mean, + 0.5, >= 0.
+  float d0 = mu[0] - V.campos[0], d1 = mu[1] - V.campos[1], d2 = mu[2] - V.campos[2];
+  const float dl = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+  d0 *= dl;
+  d1 *= dl;
+  d2 *= dl;
+  float Y[16];
+  sh_basis(d0, d1, d2, Y);
+  float col[3];
+  unsigned clampbits = 0u;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += Y[k] * __ldg(params + (11 + 3 * k + ch) * stride + i);
+    acc += 0.5f;
+    if (acc < 0.f) clampbits |= 1u << ch;
+    col[ch] = fmaxf(acc, 0.f);
+  }
+  const float opac = 1.f / (1.f + __expf(-__ldg(params + 10 * stride + i)));
+
+  out.xyo[rec] = make_float4(u, vv, opac, 0.f);
+  out.conic[rec] = make_float4(-0.5f * ca, -cb, -0.5f * cc, 0.f);
+  out.rgb[rec] = make_float4(col[0], col[1], col[2], 0.f);
+  out.depth[rec] = g.p[2];
+  out.radius[rec] = r;
+  out.rect[rec] = make_uint2((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16));
+  out.count[rec] = cnt;
+  out.clamp[rec] = (unsigned char)clampbits;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K9 + K10: per Gaussian, sum the instance gradients of every view, chain them to the 59
+// parameters and either apply Adam (hot path) or write the gradient (parity / autograd).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_project_backward(
+    float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
+    const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
+    const unsigned* __restrict__ offsets, const float4* __restrict__ ginst,
+    const Control* __restrict__ ctl, float* __restrict__ grads_out, float* __restrict__ adam_m,
+    float* __restrict__ adam_v, float* __restrict__ grad2d_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sp->n) return;
+  if (ctl->overflow) return;  // the step was skipped; the host re-runs it with more capacity
+
+  float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+  float gop = 0.f;
+  float gsh[48];
+#pragma unroll
+  for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
+
+  bool any = false;
+  float mu[3], ls[3], q[4];
+  for (int v = 0; v < n_views; ++v) {
+    const long long rec = (long long)v * stride + i;
+    const unsigned cnt = count[rec];
+    if (cnt == 0u) continue;
+    if (!any) {
+      any = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        mu[k] = params[k * stride + i];
+        ls[k] = params[(3 + k) * stride + i];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
+    }
+    // Sum of the per-instance 2D gradients (one instance per tile of the rectangle).
+    const unsigned off = offsets[rec];
+    float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (unsigned e = off; e < off + cnt; ++e) {
+      const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], c = ginst[3ull * e + 2];
+      g2[0] += a.x;
+      g2[1] += a.y;
+      g2[2] += a.z;
+      g2[3] += a.w;
+      g2[4] += b.x;
+      g2[5] += b.y;
+      g2[6] += b.z;
+      g2[7] += b.w;
+      g2[8] += c.x;
+    }
+    if (grad2d_out) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) grad2d_out[9 * rec + k] = g2[k];
+    }
+    const ViewDev& V = views[v];
+    Geo g;
+    geo_forward(V, mu, ls, q, g);
+
+    // opacity = sigmoid(logit)
+    {
+      const float o = 1.f / (1.f + __expf(-params[10 * stride + i]));
+      gop += g2[5] * o * (1.f - o);
+    }
+    // colour -> SH coefficients and view direction (clamped channels pass no gradient)
+    float dvec[3] = {mu[0] - V.campos[0], mu[1] - V.campos[1], mu[2] - V.campos[2]};
+    const float dinv = rsqrtf(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
+    const float dir[3] = {dvec[0] * dinv, dvec[1] * dinv, dvec[2] * dinv};
+    float Y[16];
+    sh_basis(dir[0], dir[1], dir[2], Y);
+    float wdir[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) wdir[k] = 0.f;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float raw = 0.5f;
+      float shc[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        shc[k] = params[(11 + 3 * k + ch) * stride + i];
+        raw += Y[k] * shc[k];
+      }
+      if (raw < 0.f) continue;
+      const float dcol = g2[6 + ch];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        gsh[3 * k + ch] += Y[k] * dcol;
+        wdir[k] += shc[k] * dcol;
+      }
+    }
+    float ddir[3] = {0.f, 0.f, 0.f};
+    sh_basis_vjp(dir[0], dir[1], dir[2], wdir, ddir);
+    {
+      const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gmu[a] += (ddir[a] - dir[a] * dd) * dinv;
+    }
+
+    // Pre-scaled conic gradient back to the conic (a, b, c): power = -a/2 dx^2 - b dx dy - c/2 dy^2.
+    const float dA = g2[2], dB = g2[3], dC = g2[4];
+    const float A = g.cov[0], B = g.cov[1], C = g.cov[2], det = g.det;
+    const float id = 1.f / det, id2 = id * id;
+    const float da = dA * (-C * C * id2) + dB * (B * C * id2) + dC * (id - A * C * id2);
+    const float db = dA * (2.f * B * C * id2) + dB * (-id - 2.f * B * B * id2) + dC * (2.f * A * B * id2);
+    const float dc = dA * (id - A * C * id2) + dB * (A * B * id2) + dC * (-A * A * id2);
+
+    // (a, b, c) = entries of Tm Sigma Tm^T
+    const float* T0 = g.Tm;
+    const float* T1 = g.Tm + 3;
+    const float S[9] = {g.Sig[0], g.Sig[1], g.Sig[2], g.Sig[1], g.Sig[3], g.Sig[4], g.Sig[2], g.Sig[4], g.Sig[5]};
+    // symmetric gradient w.r.t. Sigma: G = da T0 T0^T + db (T0 T1^T + T1 T0^T)/2 + dc T1 T1^T,
+    // and dL/dM = 2 G M.
+    float Gs[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        Gs[3 * r + c] = da * T0[r] * T0[c] + 0.5f * db * (T0[r] * T1[c] + T1[r] * T0[c]) + dc * T1[r] * T1[c];
+    float dT0[3], dT1[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float s0 = S[3 * r] * T0[0] + S[3 * r + 1] * T0[1] + S[3 * r + 2] * T0[2];
+      const float s1 = S[3 * r] * T1[0] + S[3 * r + 1] * T1[1] + S[3 * r + 2] * T1[2];
+      dT0[r] = 2.f * da * s0 + db * s1;
+      dT1[r] = 2.f * dc * s1 + db * s0;
+    }
+    // Tm = J R_cam: dJ = dTm R_cam^T (only J00, J02, J11, J12 are non-zero functions)
+    const float dJ00 = dT0[0] * V.R[0] + dT0[1] * V.R[1] + dT0[2] * V.R[2];
+    const float dJ02 = dT0[0] * V.R[6] + dT0[1] * V.R[7] + dT0[2] * V.R[8];
+    const float dJ11 = dT1[0] * V.R[3] + dT1[1] * V.R[4] + dT1[2] * V.R[5];
+    const float dJ12 = dT1[0] * V.R[6] + dT1[1] * V.R[7] + dT1[2] * V.R[8];
+    const float px = g.p[0], py = g.p[1], pz = g.p[2];
+    const float iz = 1.f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
+    float dp[3] = {0.f, 0.f, 0.f};
+    dp[2] += dJ00 * (-V.fx * iz2) + dJ11 * (-V.fy * iz2);
+    if (g.xin) {
+      dp[0] += dJ02 * (-V.fx * iz2);
+      dp[2] += dJ02 * (2.f * V.fx * px * iz3);
+    } else {
+      dp[2] += dJ02 * (V.fx * g.txz * iz2);
+    }
+    if (g.yin) {
+      dp[1] += dJ12 * (-V.fy * iz2);
+      dp[2] += dJ12 * (2.f * V.fy * py * iz3);
+    } else {
+      dp[2] += dJ12 * (V.fy * g.tyz * iz2);
+    }
+    // mean2d = (fx x/z + cx, fy y/z + cy)
+    dp[0] += g2[0] * V.fx * iz;
+    dp[2] += g2[0] * (-V.fx * px * iz2);
+    dp[1] += g2[1] * V.fy * iz;
+    dp[2] += g2[1] * (-V.fy * py * iz2);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gmu[a] += V.R[a] * dp[0] + V.R[3 + a] * dp[1] + V.R[6 + a] * dp[2];
+
+    // Sigma = M M^T, M = Rq diag(s)
+    float dM[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        dM[3 * r + c] = 2.f * (Gs[3 * r] * g.M[c] + Gs[3 * r + 1] * g.M[3 + c] + Gs[3 * r + 2] * g.M[6 + c]);
+    float dRq[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dRq[3 * r + c] = dM[3 * r + c] * g.s[c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float ds = dM[c] * g.Rq[c] + dM[3 + c] * g.Rq[3 + c] + dM[6 + c] * g.Rq[6 + c];
+      gls[c] += ds * g.s[c];
+    }
+    const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+    float dqn[4];
+    dqn[0] = 2.f * (-z * dRq[1] + y * dRq[2] + z * dRq[3] - x * dRq[5] - y * dRq[6] + x * dRq[7]);
+    dqn[1] = 2.f * (y * dRq[1] + z * dRq[2] + y * dRq[3] - 2.f * x * dRq[4] - w * dRq[5] + z * dRq[6] +
+                    w * dRq[7] - 2.f * x * dRq[8]);
+    dqn[2] = 2.f * (-2.f * y * dRq[0] + x * dRq[1] + w * dRq[2] + x * dRq[3] + z * dRq[5] - w * dRq[6] +
+                    z * dRq[7] - 2.f * y * dRq[8]);
+    dqn[3] = 2.f * (-2.f * z * dRq[0] - w * dRq[1] + x * dRq[2] + w * dRq[3] - 2.f * z * dRq[4] + y * dRq[5] +
+                    x * dRq[6] + y * dRq[7]);
+    const float qd = g.qn[0] * dqn[0] + g.qn[1] * dqn[1] + g.qn[2] * dqn[2] + g.qn[3] * dqn[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gq[k] += (dqn[k] - g.qn[k] * qd) * g.qinv;
+  }
+
+  float gall[kNumParams];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gall[k] = gmu[k];
+    gall[3 + k] = gls[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gall[6 + k] = gq[k];
+  gall[10] = gop;
+#pragma unroll
+  for (int k = 0; k < 48; ++k) gall[11 + k] = gsh[k];
+
+  if (!sp->adam) {
+#pragma unroll
+    for (int c = 0; c < kNumParams; ++c) grads_out[(long long)c * stride + i] = gall[c];
+    return;
+  }
+  // Adam (torch.optim.Adam's bias-corrected update), dense over every live Gaussian.
+  const float b1 = sp->beta1, b2 = sp->beta2, eps = sp->eps;
+  const float ssc = sp->step_size_scale, bc2s = sp->bc2_sqrt;
+#pragma unroll
+  for (int c = 0; c < kNumParams; ++c) {
+    const int grp = c < 3 ? 0 : (c < 6 ? 1 : (c < 10 ? 2 : (c < 11 ? 3 : (c < 14 ? 4 : 5))));
+    const long long k = (long long)c * stride + i;
+    const float gr = gall[c];
+    const float m = b1 * adam_m[k] + (1.f - b1) * gr;
+    const float vv = b2 * adam_v[k] + (1.f - b2) * gr * gr;
+    adam_m[k] = m;
+    adam_v[k] = vv;
+    params[k] -= (sp->lr[grp] * ssc) * m / (sqrtf(vv) / bc2s + eps);
+  }
+}
+
+// Plain Adam over a gradient buffer (parity of K10 on its own; dense, vectorised by 4).
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const float* __restrict__ grads,
+                                              float* __restrict__ m, float* __restrict__ v, int n, int stride,
+                                              const StepParams* __restrict__ sp) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // float4 index
+  const long long per_row = stride / 4;
+  if (q >= per_row * kNumParams) return;
+  const int c = (int)(q / per_row);
+  const int i0 = (int)(q - (long long)c * per_row) * 4;
+  if (i0 >= n) return;
+  const int grp = c < 3 ? 0 : (c < 6 ? 1 : (c < 10 ? 2 : (c < 11 ? 3 : (c < 14 ? 4 : 5))));
+  const float lr = sp->lr[grp] * sp->step_size_scale;
+  const float b1 = sp->beta1, b2 = sp->beta2, eps = sp->eps, bc2s = sp->bc2_sqrt;
+  float4 p = reinterpret_cast<float4*>(params)[q];
+  const float4 g = reinterpret_cast<const float4*>(grads)[q];
+  float4 mm = reinterpret_cast<float4*>(m)[q];
+  float4 vv = reinterpret_cast<float4*>(v)[q];
+  auto upd = [&](float& pp, float gg, float& m1, float& v1, int lane) {
+    if (i0 + lane >= n) return;
+    m1 = b1 * m1 + (1.f - b1) * gg;
+    v1 = b2 * v1 + (1.f - b2) * gg * gg;
+    pp -= lr * m1 / (sqrtf(v1) / bc2s + eps);
+  };
+  upd(p.x, g.x, mm.x, vv.x, 0);
+  upd(p.y, g.y, mm.y, vv.y, 1);
+  upd(p.z, g.z, mm.z, vv.z, 2);
+  upd(p.w, g.w, mm.w, vv.w, 3);
+  reinterpret_cast<float4*>(params)[q] = p;
+  reinterpret_cast<float4*>(m)[q] = mm;
+  reinterpret_cast<float4*>(v)[q] = vv;
+}
+
+void launch_project(const float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
+                    const ProjBuffers& out, cudaStream_t s) {
+  dim3 grid((stride + 255) / 256, n_views);
+  k_project<<<grid, 256, 0, s>>>(params, stride, sp, views, out);
+}
+
+void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
+                             const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
+                             float* m, float* v, float* grad2d_out, cudaStream_t s) {
+  k_project_backward<<<(stride + 127) / 128, 128, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
+                                                           ginst, ctl, grads_out, m, v, grad2d_out);
+}
+
+void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
+                 cudaStream_t s) {
+  const long long quads = (long long)(stride / 4) * kNumParams;
+  k_adam<<<(unsigned)((quads + 255) / 256), 256, 0, s>>>(params, grads, m, v, n, stride, sp);
+}
+
+}  // namespace gs

@@ -1,0 +1,388 @@
+// k_sort.cu -- K2 (exclusive scan of tiles touched), K3 (duplication into (tile, depth) keys),
+// K4 (stable LSD radix sort, one onesweep pass per 8-bit digit) and K5 (per-tile ranges), sm_103a.
+//
+// These implement the tile-binning of the 3DGS rasterizer the paper builds on (Sec. III; the
+// "original 3DGS" settings of Sec. V-A).  Canonical order: (global tile, fp32 depth bits,
+// record index).  Instances are emitted in record order and every sort pass is stable, so the
+// record index breaks depth ties.  Every count lives in device memory: no kernel here needs the
+// host to know how many instances were emitted, so the whole chain can be graph-captured.
+// The inter-CTA waits (decoupled look-back) spin at most kSpinLimit times, then flag
+// kErrTimeout and carry on rather than hang.
+#include "gs_device.cuh"
+#include "gs_engine.h"
+
+namespace gs {
+
+namespace {
+constexpr unsigned long long kScanAgg = 1ull << 62;
+constexpr unsigned long long kScanPrefix = 2ull << 62;
+constexpr unsigned long long kScanValMask = (1ull << 62) - 1;
+constexpr unsigned kSortAgg = 1u << 30;
+constexpr unsigned kSortPrefix = 2u << 30;
+constexpr unsigned kSortValMask = (1u << 30) - 1;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// K2: single-pass exclusive scan with decoupled look-back.  Tiles are taken in launch order via
+// an atomic ticket, so every tile a CTA waits on belongs to a CTA that is already running.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restrict__ in, unsigned* __restrict__ out,
+                                                       long long n_items, unsigned long long* __restrict__ state,
+                                                       Control* __restrict__ ctl, unsigned long long m_cap) {
+  __shared__ unsigned s_tile;
+  __shared__ unsigned s_warp[kScanThreads / 32];
+  __shared__ unsigned long long s_excl;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->scan_ticket, 1u);
+  __syncthreads();
+  const unsigned tile = s_tile;
+  const long long num_tiles = (n_items + kScanTile - 1) / kScanTile;
+  const long long base = (long long)tile * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned x[kScanItems];
+  if (base + kScanItems <= n_items) {
+    const uint4 a = *reinterpret_cast<const uint4*>(in + base);
+    const uint4 b = *reinterpret_cast<const uint4*>(in + base + 4);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) x[k] = (base + k < n_items) ? in[base + k] : 0u;
+  }
+  unsigned tsum = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) tsum += x[k];
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = tsum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+    unsigned wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += y;
+    }
+    if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+    const unsigned total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+    if (lane == 0) {
+      unsigned long long excl = 0;
+      if (tile == 0) {
+        st_release_u64(&state[0], kScanPrefix | (unsigned long long)total);
+      } else {
+        st_release_u64(&state[tile], kScanAgg | (unsigned long long)total);
+        long long j = (long long)tile - 1;
+        unsigned spins = 0;
+        while (j >= 0) {
+          const unsigned long long sv = ld_acquire_u64(&state[j]);
+          const unsigned long long flag = sv & ~kScanValMask;
+          if (flag == 0ull) {
+            if (++spins > kSpinLimit) {
+              atomicOr(&ctl->error, kErrTimeout);
+              break;
+            }
+            continue;
+          }
+          excl += sv & kScanValMask;
+          if (flag == kScanPrefix) break;
+          --j;
+        }
+        st_release_u64(&state[tile], kScanPrefix | (excl + total));
+      }
+      s_excl = excl;
+      if ((long long)tile == num_tiles - 1) {
+        const unsigned long long m = excl + total;
+        ctl->m_total = m;
+        if (m > m_cap) {
+          ctl->overflow = 1u;
+          atomicOr(&ctl->error, kErrOverflow);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  unsigned run = (unsigned)s_excl + s_warp[warp] + (incl - tsum);
+  if (base + kScanItems <= n_items) {
+    unsigned y[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      y[k] = run;
+      run += x[k];
+    }
+    *reinterpret_cast<uint4*>(out + base) = make_uint4(y[0], y[1], y[2], y[3]);
+    *reinterpret_cast<uint4*>(out + base + 4) = make_uint4(y[4], y[5], y[6], y[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < n_items) out[base + k] = run;
+      run += x[k];
+    }
+  }
+}
+
+void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
+                 unsigned long long m_cap, cudaStream_t s) {
+  const long long tiles = (n_items + kScanTile - 1) / kScanTile;
+  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K3: key emission.  The 32 records of a warp share their instances out evenly: lane l writes
+// instances e0 + l, e0 + 32 + l, ... of the warp's contiguous instance range and finds the
+// owning record by a binary search over the lanes' offsets.  Writes are fully coalesced and a
+// large Gaussian does not stall its warp.  Also histograms every radix digit for the sort.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDev* __restrict__ views, int stride,
+                                              long long n_items, unsigned long long* __restrict__ keys,
+                                              unsigned* __restrict__ vals, unsigned* __restrict__ hist, int passes,
+                                              const Control* __restrict__ ctl) {
+  __shared__ unsigned s_hist[kMaxSortPasses][kSortBins];
+  for (int k = threadIdx.x; k < kMaxSortPasses * kSortBins; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
+  __syncthreads();
+  const bool skip = ctl->overflow != 0u;
+  const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  // n_items is a multiple of 32, so a warp is either wholly in range or wholly out.
+  if (!skip && rec - lane < n_items) {
+    const unsigned cnt = pb.count[rec];
+    const unsigned off = pb.offsets[rec];
+    const unsigned wbeg = __shfl_sync(0xffffffffu, off, 0);
+    const unsigned wend = __shfl_sync(0xffffffffu, off + cnt, 31);
+    const int v = (int)(rec / stride);
+    const ViewDev& V = views[v];
+    const uint2 rc = cnt ? pb.rect[rec] : make_uint2(0u, 0u);
+    const unsigned dbits = cnt ? __float_as_uint(pb.depth[rec]) : 0u;
+    const long long tbase = V.tile_base;
+    const int gx = V.gx;
+    for (unsigned e0 = wbeg; e0 < wend; e0 += 32) {
+      const unsigned e = e0 + lane;
+      // owner = largest lane whose offset <= e (offsets are non-decreasing across the warp)
+      int lo = 0;
+#pragma unroll
+      for (int step = 16; step >= 1; step >>= 1) {
+        const unsigned oc = __shfl_sync(0xffffffffu, off, lo + step);
+        if (oc <= e) lo += step;
+      }
+      const unsigned o_off = __shfl_sync(0xffffffffu, off, lo);
+      const unsigned o_rx = __shfl_sync(0xffffffffu, rc.x, lo);
+      const unsigned o_ry = __shfl_sync(0xffffffffu, rc.y, lo);
+      const unsigned o_db = __shfl_sync(0xffffffffu, dbits, lo);
+      const long long o_tb = __shfl_sync(0xffffffffu, tbase, lo);
+      const int o_gx = __shfl_sync(0xffffffffu, gx, lo);
+      const unsigned o_rec = (unsigned)__shfl_sync(0xffffffffu, (unsigned)rec, lo);
+      if (e < wend) {
+        const unsigned k = e - o_off;
+        const unsigned x0 = o_rx & 0xffffu, x1 = o_rx >> 16, y0 = o_ry & 0xffffu;
+        const unsigned w = x1 - x0;
+        const unsigned ty = y0 + k / w, tx = x0 + k % w;
+        const unsigned long long tile = (unsigned long long)(o_tb + (long long)ty * o_gx + tx);
+        const unsigned long long key = (tile << 32) | (unsigned long long)o_db;
+        keys[e] = key;
+        vals[e] = o_rec;
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < passes * kSortBins; k += blockDim.x) {
+    const unsigned c = (&s_hist[0][0])[k];
+    if (c) atomicAdd(hist + k, c);
+  }
+}
+
+void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys,
+                 unsigned* vals, unsigned* hist, int passes, const Control* ctl, cudaStream_t s) {
+  k_emit<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb, views, stride, n_items, keys, vals, hist, passes, ctl);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K4: one stable counting pass over an 8-bit digit (onesweep: digit offsets from the upfront
+// histogram, per-CTA offsets by decoupled look-back per digit).  Within a CTA the keys are
+// ranked warp by warp with match.any so the pass is stable, staged in shared memory in digit
+// order, and written out as contiguous runs.
+// ---------------------------------------------------------------------------------------------
+struct SortSmem {
+  unsigned long long keys[kSortTile];
+  unsigned vals[kSortTile];
+  unsigned cnt[kSortThreads / 32][kSortBins];
+  unsigned bstart[kSortBins];
+  unsigned gbase[kSortBins];
+  unsigned tile;
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(const unsigned long long* __restrict__ kin,
+                                                            const unsigned* __restrict__ vin,
+                                                            unsigned long long* __restrict__ kout,
+                                                            unsigned* __restrict__ vout,
+                                                            const unsigned* __restrict__ hist,
+                                                            unsigned* __restrict__ state, int pass,
+                                                            Control* __restrict__ ctl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
+  if (ctl->overflow) return;
+  const unsigned long long M = ctl->m_total;
+  if (threadIdx.x == 0) S.tile = atomicAdd(&ctl->sort_ticket[pass], 1u);
+  for (int k = threadIdx.x; k < (kSortThreads / 32) * kSortBins; k += kSortThreads) (&S.cnt[0][0])[k] = 0u;
+  __syncthreads();
+  const unsigned tile = S.tile;
+  const unsigned long long tile0 = (unsigned long long)tile * kSortTile;
+  if (tile0 >= M) return;
+  const int shift = pass * kSortBits;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+
+  unsigned long long key[kSortItems];
+  unsigned val[kSortItems];
+  unsigned rank[kSortItems];
+  const unsigned long long wbase = tile0 + (unsigned long long)warp * (kSortItems * 32);
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const unsigned long long idx = wbase + (unsigned)(r * 32 + lane);
+    const bool valid = idx < M;
+    key[r] = valid ? kin[idx] : ~0ull;
+    val[r] = valid ? vin[idx] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const unsigned long long idx = wbase + (unsigned)(r * 32 + lane);
+    const bool valid = idx < M;
+    const unsigned d = (unsigned)(key[r] >> shift) & (kSortBins - 1);
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? d : (kSortBins + d));
+    const unsigned pre = valid ? S.cnt[warp][d] : 0u;
+    __syncwarp();
+    if (valid && (peers & lt) == 0u) S.cnt[warp][d] = pre + __popc(peers);
+    __syncwarp();
+    rank[r] = pre + __popc(peers & lt);
+  }
+  __syncthreads();
+  // Per digit: warp-exclusive prefix in place, CTA total, decoupled look-back across CTAs.
+  {
+    const int d = threadIdx.x;  // kSortThreads == kSortBins
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      const unsigned c = S.cnt[w][d];
+      S.cnt[w][d] = run;
+      run += c;
+    }
+    const unsigned total = run;
+    unsigned* st = state + (unsigned long long)tile * kSortBins + d;
+    unsigned excl = 0;
+    if (tile == 0) {
+      st_release_u32(st, kSortPrefix | total);
+    } else {
+      st_release_u32(st, kSortAgg | total);
+      long long j = (long long)tile - 1;
+      unsigned spins = 0;
+      while (j >= 0) {
+        const unsigned sv = ld_acquire_u32(state + (unsigned long long)j * kSortBins + d);
+        const unsigned flag = sv & ~kSortValMask;
+        if (flag == 0u) {
+          if (++spins > kSpinLimit) {
+            atomicOr(&ctl->error, kErrTimeout);
+            break;
+          }
+          continue;
+        }
+        excl += sv & kSortValMask;
+        if (flag == kSortPrefix) break;
+        --j;
+      }
+      st_release_u32(st, kSortPrefix | (excl + total));
+    }
+    // digit base = exclusive scan of the global histogram; CTA digit start = exclusive scan of
+    // the CTA totals.  Both by a block-wide scan over the 256 digits.
+    const unsigned h = hist[pass * kSortBins + d];
+    unsigned a = h, b = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned ya = __shfl_up_sync(0xffffffffu, a, o);
+      const unsigned yb = __shfl_up_sync(0xffffffffu, b, o);
+      if (lane >= o) {
+        a += ya;
+        b += yb;
+      }
+    }
+    __shared__ unsigned s_wa[kSortThreads / 32], s_wb[kSortThreads / 32];
+    if (lane == 31) {
+      s_wa[warp] = a;
+      s_wb[warp] = b;
+    }
+    __syncthreads();
+    unsigned pa = 0, pb = 0;
+    for (int w = 0; w < warp; ++w) {
+      pa += s_wa[w];
+      pb += s_wb[w];
+    }
+    S.gbase[d] = pa + a - h + excl;
+    S.bstart[d] = pb + b - total;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const unsigned long long idx = wbase + (unsigned)(r * 32 + lane);
+    if (idx < M) {
+      const unsigned d = (unsigned)(key[r] >> shift) & (kSortBins - 1);
+      const unsigned pos = S.bstart[d] + S.cnt[warp][d] + rank[r];
+      S.keys[pos] = key[r];
+      S.vals[pos] = val[r];
+    }
+  }
+  __syncthreads();
+  const unsigned tile_count = (unsigned)min((unsigned long long)kSortTile, M - tile0);
+  for (unsigned k = threadIdx.x; k < tile_count; k += kSortThreads) {
+    const unsigned long long kk = S.keys[k];
+    const unsigned d = (unsigned)(kk >> shift) & (kSortBins - 1);
+    const unsigned gpos = S.gbase[d] + (k - S.bstart[d]);
+    kout[gpos] = kk;
+    vout[gpos] = S.vals[k];
+  }
+}
+
+void init_sort_attributes() {
+  cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
+}
+
+void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout, unsigned* vout,
+                      const unsigned* hist, unsigned* state, int pass, long long m_cap, Control* ctl,
+                      cudaStream_t s) {
+  const long long tiles = (m_cap + kSortTile - 1) / kSortTile;
+  k_sort_pass<<<(unsigned)(tiles > 0 ? tiles : 1), kSortThreads, sizeof(SortSmem), s>>>(
+      kin, vin, kout, vout, hist, state, pass, ctl);
+}
+
+// ---------------------------------------------------------------------------------------------
+// K5: per-tile [start, end) of the sorted list.  Empty tiles keep the [0, 0) the step's clear
+// left them.  Grid-stride over the device-resident instance count.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ranges(const unsigned long long* __restrict__ keys, uint2* __restrict__ ranges,
+                                                const Control* __restrict__ ctl) {
+  if (ctl->overflow) return;
+  const unsigned long long M = ctl->m_total;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned tile = (unsigned)(keys[i] >> 32);
+    if (i == 0 || (unsigned)(keys[i - 1] >> 32) != tile) ranges[tile].x = (unsigned)i;
+    if (i == M - 1 || (unsigned)(keys[i + 1] >> 32) != tile) ranges[tile].y = (unsigned)(i + 1);
+  }
+}
+
+void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s) {
+  long long blocks = (m_cap + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, ranges, ctl);
+}
+
+}  // namespace gs
