@@ -125,8 +125,9 @@ GS_API gs_status gs_adam_step(void* stream, float* params, const float* grads, f
                        int64_t stride, const float lr[6], float beta1, float beta2, float eps, int64_t step);
 
 /* Copy a workspace buffer of the last forward to host memory (parity checks).  which:
- *   0 xyo   (float4 per record: u, v, opacity, 0)   1 conic (float4: -a/2, -b, -c/2, 0)
- *   2 rgb   (float4: r, g, b, 0)                    3 depth (float)
+ *   0 mean  (float4 per record: u, v, ex, ey: the 1/255 cutoff box half extents)
+ *   1 conic (float4: -a/2, -b, -c/2, -ln(255 opacity))
+ *   2 rgb   (float4: r, g, b, opacity)              3 depth (float)
  *   4 radius (int32)                                5 rect (uint32 x2: x0|x1<<16, y0|y1<<16)
  *   6 count (uint32 tiles touched)                  7 offsets (uint32)
  *   8 keys  (uint64, sorted, m_total of them)       9 values (uint32 record index, sorted)
@@ -236,6 +237,13 @@ GS_API gs_status gs_image_info(const gs_field* f, int32_t image_id, int32_t* out
 
 /* The learning rate of Eq. 8 for image_id under the current T_j (diagnostics and tests). */
 GS_API gs_status gs_image_lr(const gs_field* f, int32_t image_id, float* out_lr);
+
+/* Device-side checkpoint of the trainable state: parameters, Adam moments and step count, and
+ * each image's iteration count T_j.  gs_field_restore returns the field to the last snapshot
+ * (Gaussians added since are dropped; registered images are kept).  GS_ERR_STATE if no
+ * snapshot exists.  The snapshot lives in device memory owned by the field. */
+GS_API gs_status gs_field_snapshot(gs_field* f);
+GS_API gs_status gs_field_restore(gs_field* f);
 
 /* Enable per-kernel timing on the field's steps; gs_field_kernel_times returns the summed
  * device ms per kernel (same order as gs_raster_kernel_times) and the number of steps. */

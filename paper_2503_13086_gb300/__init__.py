@@ -112,6 +112,8 @@ SYMBOLS = {
     "gs_field_stats_get": ([P, P], I32),
     "gs_image_info": ([P, I32, P, P, I32], I32),
     "gs_image_lr": ([P, I32, P], I32),
+    "gs_field_snapshot": ([P], I32),
+    "gs_field_restore": ([P], I32),
     "gs_field_set_timing": ([P, ctypes.c_int], I32),
     "gs_field_kernel_times": ([P, P, P], I32),
 }
@@ -409,6 +411,12 @@ class Field:
         out = ctypes.c_float()
         _check(self._lib.gs_image_lr(self._h, int(image_id), ctypes.byref(out)))
         return float(out.value)
+
+    def snapshot(self):
+        _check(self._lib.gs_field_snapshot(self._h))
+
+    def restore(self):
+        _check(self._lib.gs_field_restore(self._h))
 
     def set_timing(self, on=True):
         _check(self._lib.gs_field_set_timing(self._h, 1 if on else 0))

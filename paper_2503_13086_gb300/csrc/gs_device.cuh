@@ -15,6 +15,7 @@ constexpr int kNumParams = 59;      // mean 3, log-scale 3, quaternion 4, opacit
 constexpr int kTile = 16;           // tile edge in pixels (16 x 16 = 256 pixels = one CTA)
 constexpr int kTilePix = kTile * kTile;
 constexpr int kChunk = 32;          // Gaussians per backward work item and checkpoint period
+constexpr int kMaxStepViews = 32;   // views of one step
 constexpr float kNearZ = 0.2f;      // cull at camera z <= 0.2
 constexpr float kDilate = 0.3f;     // low-pass term added to the 2D covariance diagonal
 constexpr float kFovLim = 1.3f;     // x/z, y/z clamped to 1.3 x half-FOV tangent inside J
@@ -50,8 +51,10 @@ struct Control {
   unsigned int scan_ticket;
   unsigned int sort_ticket[8];
   unsigned int bwd_work;
+  unsigned int fwd_work;
   unsigned int loss_done;
   unsigned int pad;
+  unsigned int order_count[32];  // tiles per list-length bucket (long-first schedule)
   double loss_view[32];         // per-view loss of the last step
   double loss;                  // batch loss (mean over views)
 };

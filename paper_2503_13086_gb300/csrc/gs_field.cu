@@ -151,6 +151,11 @@ struct Field {
   double last_loss = 0.0;
   unsigned long long last_pairs = 0;
   size_t own_bytes = 0;
+  // snapshot (gs_field_snapshot / gs_field_restore)
+  DevBuf snap_p, snap_m, snap_v;
+  int snap_n = -1, snap_stride = 0;
+  long long snap_step = 0;
+  std::vector<int> snap_T;
 
   size_t bytes_in_use() const { return own_bytes + (r ? r->bytes_in_use : 0); }
 
@@ -167,6 +172,9 @@ struct Field {
     step_dimg.release(&own_bytes);
     step_T.release(&own_bytes);
     step_gp.release(&own_bytes);
+    snap_p.release(&own_bytes);
+    snap_m.release(&own_bytes);
+    snap_v.release(&own_bytes);
   }
 
   std::vector<unsigned long long> signature() const {
@@ -175,7 +183,7 @@ struct Field {
     const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
                             &R.sp_d, &R.views_d, &R.zeroA, &R.zeroB, &R.xyo, &R.conic, &R.rgb, &R.depth, &R.radius,
                             &R.rect, &R.count, &R.offsets, &R.clamp, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
-                            &R.ckpt, &R.partials, &R.block_sums};
+                            &R.ckpt, &R.cmask, &R.order, &R.partials, &R.block_sums};
     for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
     const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)R.passes,
                                       (unsigned long long)R.n_tiles, R.zeroA_bytes, R.zeroB_bytes, R.sort_state_bytes,
@@ -830,6 +838,52 @@ gs_status gs_image_lr(const gs_field* ff, int32_t id, float* out_lr) {
   const Field* f = F(ff);
   if (!f || !out_lr || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad arguments");
   *out_lr = (float)f->lr_image(id);
+  return GS_OK;
+}
+
+gs_status gs_field_snapshot(gs_field* ff) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  const size_t bytes = (size_t)f->stride * gs::kNumParams * 4;
+  if (f->cfg.hbm_budget_bytes && f->snap_p.bytes < bytes &&
+      f->bytes_in_use() + 3 * (bytes - f->snap_p.bytes) > f->cfg.hbm_budget_bytes)
+    return fail(GS_ERR_BUDGET, "a snapshot would exceed hbm_budget_bytes");
+  gs_status s;
+  if ((s = f->snap_p.reserve(bytes, &f->own_bytes)) || (s = f->snap_m.reserve(bytes, &f->own_bytes)) ||
+      (s = f->snap_v.reserve(bytes, &f->own_bytes)))
+    return s;
+  if (bytes) {
+    cudaMemcpyAsync(f->snap_p.p, f->params.p, bytes, cudaMemcpyDeviceToDevice, f->stream);
+    cudaMemcpyAsync(f->snap_m.p, f->adam_m.p, bytes, cudaMemcpyDeviceToDevice, f->stream);
+    cudaMemcpyAsync(f->snap_v.p, f->adam_v.p, bytes, cudaMemcpyDeviceToDevice, f->stream);
+  }
+  f->snap_n = f->n;
+  f->snap_stride = f->stride;
+  f->snap_step = f->adam_step;
+  f->snap_T.clear();
+  for (auto& im : f->images) f->snap_T.push_back(im.T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  return GS_OK;
+}
+
+gs_status gs_field_restore(gs_field* ff) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  if (f->snap_n < 0) return fail(GS_ERR_STATE, "no snapshot");
+  // the field may have grown (stride) since the snapshot: copy rows with their pitches
+  const gs::DevBuf* src[3] = {&f->snap_p, &f->snap_m, &f->snap_v};
+  gs::DevBuf* dst[3] = {&f->params, &f->adam_m, &f->adam_v};
+  for (int k = 0; k < 3; ++k) {
+    if (f->snap_n == 0) continue;
+    cudaMemcpy2DAsync(dst[k]->p, (size_t)f->stride * 4, src[k]->p, (size_t)f->snap_stride * 4, (size_t)f->snap_n * 4,
+                      gs::kNumParams, cudaMemcpyDeviceToDevice, f->stream);
+  }
+  f->n = f->snap_n;
+  f->adam_step = f->snap_step;
+  for (size_t j = 0; j < f->images.size(); ++j) f->images[j].T = j < f->snap_T.size() ? f->snap_T[j] : 0;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
   return GS_OK;
 }
 

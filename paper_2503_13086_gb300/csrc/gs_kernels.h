@@ -10,9 +10,9 @@ namespace gs {
 
 // Per-record outputs of K1 (record = view * stride + Gaussian id).
 struct ProjBuffers {
-  float4* xyo;           // (u, v, opacity, 0)
-  float4* conic;         // pre-scaled conic (-a/2, -b, -c/2, 0)
-  float4* rgb;           // (r, g, b, 0)
+  float4* xyo;           // (u, v, ex, ey): mean and half extents of the 1/255 cutoff box
+  float4* conic;         // pre-scaled conic (-a/2, -b, -c/2) and thr = -ln(255 opacity)
+  float4* rgb;           // (r, g, b, opacity)
   float* depth;          // camera-space z
   int* radius;           // 0 = culled
   uint2* rect;           // (x0 | x1 << 16, y0 | y1 << 16) tile rectangle
@@ -48,14 +48,15 @@ void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsign
                       const unsigned* hist, unsigned* state, int pass, long long m_cap, Control* ctl, cudaStream_t s);
 void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s);
 
+void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const Control* ctl, cudaStream_t s);
 void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
-                          float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt, int* chunk_tile,
-                          cudaStream_t s);
+                          const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
+                          unsigned* cmask, int* chunk_tile, int num_sms, cudaStream_t s);
 void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
-                           const unsigned* last, const float* dimage, const float4* ckpt, const int* chunk_tile,
-                           float4* ginst, int num_sms, cudaStream_t s);
+                           const unsigned* last, const float* dimage, const float4* ckpt, const unsigned* cmask,
+                           const int* chunk_tile, float4* ginst, int num_sms, cudaStream_t s);
 
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);

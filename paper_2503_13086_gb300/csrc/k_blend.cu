@@ -1,20 +1,29 @@
 // k_blend.cu -- K6 (front-to-back alpha blending, Eq. 2) and K8 (its splatting-parallel
 // backward, Sec. IV-D), sm_103a.
 //
-// K6: one CTA per 16 x 16 tile (all views' tiles in one grid), one pixel per thread.  The
-// tile's sorted Gaussians are staged through shared memory in batches; a pixel stops before the
-// Gaussian that would take its transmittance below 1e-4 and the CTA leaves the batch loop as
-// soon as every pixel has stopped (__syncthreads_count).  Every 32 list entries each live pixel
-// stores a checkpoint (T, accumulated colour) so the backward can start any 32-entry chunk
-// without re-walking the list.
+// K6: persistent CTAs of 256 threads (one 16 x 16 tile at a time, one pixel per thread, each
+// warp an 8 x 4 pixel block) take tiles longest-list first, so the few very long tiles do not
+// end up as the tail of the launch.  The tile's sorted Gaussians are staged through shared
+// memory in batches of 256 and walked in chunks of 32.  Per chunk a cheap pass first marks the
+// candidates: a warp skips a Gaussian outright when the bounding box of its 1/255 cutoff ellipse
+// misses the warp's block (a warp-uniform branch), otherwise each pixel tests its exponent
+// against -ln(255 opacity).  These iterations are independent, so they pipeline; only
+// candidates then run the sequential part (exp, alpha, early stop, blending).
+// Per (pixel, chunk) K6 stores the transmittance and colour at the chunk start and a 32-bit mask
+// of the Gaussians actually blended; the CTA leaves the batch loop once every pixel has stopped
+// (__syncthreads_count).
 //
-// K8: splatting-parallel gradient accumulation (the paper adopts it from Taming 3DGS to remove
-// the serialized per-pixel atomics of the original backward).  A persistent warp takes one
-// (tile, 32-entry chunk) at a time.  Lane l owns Gaussian l of the chunk and keeps its nine
-// gradient sums in registers; the tile's live pixels stream through the warp as a skewed
-// pipeline (at step s lane l works on pixel s - l), the running (T, colour-in-front) state of a
-// pixel passing from lane to lane by one shuffle.  Each instance's gradient is written once,
-// to its own slot, with no atomics, so the result is deterministic.
+// K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
+// Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
+// (tile, 32-entry chunk), one warp each, taken from a global counter.  The warp compacts the
+// tile's pixels whose mask for this chunk is non-empty and takes them 32 at a time: each lane
+// restarts its pixel from the checkpoint and walks only the Gaussians it blended, in order, with
+// exactly the forward's transmittance (the colour behind a Gaussian is the rendered colour minus
+// the colour accumulated in front of it), recording per (pixel, Gaussian) pair its slot in a
+// list sorted by Gaussian (slots from per-Gaussian ballots).  Then all 32 lanes take consecutive
+// pairs, compute the nine gradient terms, and a segmented warp scan sums each Gaussian's run.
+// No atomics and a fixed summation order: the gradient is deterministic.  Each instance's
+// gradient is written once, to its own slot.
 #include "gs_device.cuh"
 #include "gs_engine.h"
 
@@ -22,6 +31,7 @@ namespace gs {
 
 namespace {
 constexpr int kBlendBatch = 256;
+static_assert(kBlendBatch % kChunk == 0, "batches hold whole chunks");
 
 __device__ __forceinline__ int view_of_tile(const ViewDev* __restrict__ views, int n_views, long long t) {
   int v = 0;
@@ -29,145 +39,263 @@ __device__ __forceinline__ int view_of_tile(const ViewDev* __restrict__ views, i
   return v;
 }
 
+// Pixel slot s (0..255) of a tile -> offset in the tile: warp w = s / 32 covers the 8 x 4 block
+// at (8 (w % 2), 4 (w / 2)), lane l its pixel (l % 8, l / 8).  K6 and K8 share this mapping.
+__device__ __forceinline__ void slot_xy(int s, int& ox, int& oy) {
+  const int w = s >> 5, l = s & 31;
+  ox = ((w & 1) << 3) + (l & 7);
+  oy = ((w >> 1) << 2) + (l >> 3);
+}
+
+// Chunk id of a tile's chunk 0: unique over tiles and < (instances / 32) + tiles + 1.
 __device__ __forceinline__ long long chunk_base(unsigned start, long long tile) {
   return (long long)(start >> 5) + tile;
 }
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
+// Tile order for K6: buckets by floor(log2(list length)), longest bucket first (one CTA).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, long long n_tiles,
+                                                     int* __restrict__ order, const Control* __restrict__ ctl) {
+  __shared__ unsigned s_cnt[32];
+  __shared__ unsigned s_base[32];
+  if (ctl->overflow) return;
+  if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  for (long long t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    const unsigned L = ranges[t].y - ranges[t].x;
+    const int b = L ? 32 - __clz(L) : 0;  // 0 = empty, else 1 + floor(log2 L), at most 31
+    atomicAdd(&s_cnt[min(b, 31)], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int b = 31; b >= 0; --b) {
+      s_base[b] = run;
+      run += s_cnt[b];
+    }
+  }
+  __syncthreads();
+  for (long long t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    const unsigned L = ranges[t].y - ranges[t].x;
+    const int b = L ? 32 - __clz(L) : 0;
+    order[atomicAdd(&s_base[min(b, 31)], 1u)] = (int)t;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // K6
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTilePix) k_blend_forward(
-    const ViewDev* __restrict__ views, int n_views, const uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
+    const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
     const unsigned* __restrict__ vals, const ProjBuffers pb, const StepParams* __restrict__ sp,
-    Control* __restrict__ ctl, float* __restrict__ image, float* __restrict__ Tout, unsigned* __restrict__ last_out,
-    unsigned* __restrict__ gp_out, float4* __restrict__ ckpt, int* __restrict__ chunk_tile) {
+    Control* __restrict__ ctl, const int* __restrict__ order, float* __restrict__ image, float* __restrict__ Tout,
+    unsigned* __restrict__ last_out, unsigned* __restrict__ gp_out, float4* __restrict__ ckpt,
+    unsigned* __restrict__ cmask, int* __restrict__ chunk_tile) {
   __shared__ float4 s_xyo[kBlendBatch];
   __shared__ float4 s_con[kBlendBatch];
   __shared__ float4 s_rgb[kBlendBatch];
   __shared__ unsigned long long s_pairs[kTilePix / 32];
+  __shared__ int s_item;
   if (ctl->overflow) return;
-  const long long t = blockIdx.x;
-  const int v = view_of_tile(views, n_views, t);
-  const ViewDev& V = views[v];
-  const long long local = t - V.tile_base;
-  const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
   const int tid = threadIdx.x;
-  const int px = tx * kTile + (tid & (kTile - 1));
-  const int py = ty * kTile + (tid / kTile);
-  const bool inside = px < V.W && py < V.H;
-  const float pxf = (float)px, pyf = (float)py;
-
-  const uint2 rg = ranges[t];
-  const unsigned start = rg.x;
-  const int L = (int)(rg.y - rg.x);
-  const long long cb = chunk_base(start, t);
-  for (int k = tid; k < (L + kChunk - 1) / kChunk; k += kTilePix) chunk_tile[cb + k] = (int)(t + 1);
-
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-  unsigned last = 0u, gp = 0u;
-  unsigned neval = (unsigned)L;
-  bool done = !inside;
-  for (int b0 = 0; b0 < L; b0 += kBlendBatch) {
-    if (__syncthreads_count(done) == kTilePix) break;
-    const int j = b0 + tid;
-    if (j < L) {
-      const unsigned rec = vals[start + j];
-      s_xyo[tid] = pb.xyo[rec];
-      s_con[tid] = pb.conic[rec];
-      s_rgb[tid] = pb.rgb[rec];
-    }
+  const float bg0 = sp->bg[0], bg1 = sp->bg[1], bg2 = sp->bg[2];
+  unsigned long long my_pairs = 0;
+  for (;;) {
     __syncthreads();
-    if (!done) {
+    if (tid == 0) s_item = (int)atomicAdd(&ctl->fwd_work, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_tiles) break;
+    const long long t = order[item];
+    const int v = view_of_tile(views, n_views, t);
+    const ViewDev& V = views[v];
+    const long long local = t - V.tile_base;
+    const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
+    int ox, oy;
+    slot_xy(tid, ox, oy);
+    const int px = tx * kTile + ox;
+    const int py = ty * kTile + oy;
+    const bool inside = px < V.W && py < V.H;
+    const float pxf = (float)px, pyf = (float)py;
+    // centre of this warp's 8 x 4 block (pixel centres span 7 x 3 pixels around it)
+    const float bcx = (float)(tx * kTile + (((tid >> 5) & 1) << 3)) + 3.5f;
+    const float bcy = (float)(ty * kTile + ((tid >> 6) << 2)) + 1.5f;
+
+    const uint2 rg = ranges[t];
+    const unsigned start = rg.x;
+    const int L = (int)(rg.y - rg.x);
+    const long long cb = chunk_base(start, t);
+    for (int k = tid; k < (L + kChunk - 1) / kChunk; k += kTilePix) chunk_tile[cb + k] = (int)(t + 1);
+
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    unsigned last = 0u, gp = 0u;
+    unsigned neval = (unsigned)L;
+    bool done = !inside;
+    for (int b0 = 0; b0 < L; b0 += kBlendBatch) {
+      if (__syncthreads_count(done) == kTilePix) break;
+      const int j = b0 + tid;
+      if (j < L) {
+        const unsigned rec = vals[start + j];
+        s_xyo[tid] = pb.xyo[rec];
+        s_con[tid] = pb.conic[rec];
+        s_rgb[tid] = pb.rgb[rec];
+      }
+      __syncthreads();
+      if (done) continue;
       const int nb = min(kBlendBatch, L - b0);
-      for (int jj = 0; jj < nb; ++jj) {
-        const int jg = b0 + jj;
-        if ((jg & (kChunk - 1)) == 0 && jg > 0)
-          ckpt[(cb + (jg >> 5)) * kTilePix + tid] = make_float4(T, C0, C1, C2);
-        const float4 xy = s_xyo[jj];
-        const float4 co = s_con[jj];
-        const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
-        const float power = splat_power(co.x, co.y, co.z, dx, dy);
-        if (power > 0.f) continue;
-        const float alpha = fminf(kAlphaMax, __fmul_rn(xy.z, splat_exp(power)));
-        if (alpha < kAlphaMin) continue;
-        const float testT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        if (testT < kTransMin) {
-          done = true;
-          neval = (unsigned)jg + 1u;
-          break;
+      for (int c0 = 0; c0 < nb; c0 += kChunk) {
+        const int jg0 = b0 + c0;
+        const long long chunk = cb + (jg0 >> 5);
+        if (jg0 > 0) ckpt[chunk * kTilePix + tid] = make_float4(T, C0, C1, C2);
+        const int ce = min(kChunk, nb - c0);
+        // candidates: alpha may reach 1/255 (independent iterations -> pipelined)
+        unsigned cand = 0u;
+#pragma unroll 8
+        for (int q = 0; q < kChunk; ++q) {
+          if (q < ce) {
+            const float4 xy = s_xyo[c0 + q];
+            // warp-uniform: does the cutoff box reach this warp's block at all?
+            if (fabsf(xy.x - bcx) <= xy.z + 3.5f && fabsf(xy.y - bcy) <= xy.w + 1.5f) {
+              const float4 co = s_con[c0 + q];
+              const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
+              if (!(power > 0.f) && power >= co.w) cand |= 1u << q;
+            }
+          }
         }
-        const float4 c = s_rgb[jj];
-        const float w = __fmul_rn(alpha, T);
-        C0 = __fmaf_rn(c.x, w, C0);
-        C1 = __fmaf_rn(c.y, w, C1);
-        C2 = __fmaf_rn(c.z, w, C2);
-        T = testT;
-        last = (unsigned)jg + 1u;
-        ++gp;
+        unsigned mask = 0u;
+        while (cand) {
+          const int q = __ffs(cand) - 1;
+          cand &= cand - 1u;
+          const float4 xy = s_xyo[c0 + q];
+          const float4 co = s_con[c0 + q];
+          const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
+          const float4 c = s_rgb[c0 + q];
+          const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, splat_exp(power)));
+          if (alpha < kAlphaMin) continue;
+          const float testT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          if (testT < kTransMin) {
+            done = true;
+            neval = (unsigned)(jg0 + q) + 1u;
+            break;
+          }
+          const float w = __fmul_rn(alpha, T);
+          C0 = __fmaf_rn(c.x, w, C0);
+          C1 = __fmaf_rn(c.y, w, C1);
+          C2 = __fmaf_rn(c.z, w, C2);
+          T = testT;
+          last = (unsigned)(jg0 + q) + 1u;
+          ++gp;
+          mask |= 1u << q;
+        }
+        cmask[chunk * kTilePix + tid] = mask;
+        if (done) break;
       }
     }
-  }
-  unsigned long long my_pairs = 0;
-  if (inside) {
-    const long long HW = (long long)V.W * V.H;
-    const long long pix = (long long)py * V.W + px;
-    float* img = image + 3 * V.pix_base;
-    img[pix] = C0 + T * sp->bg[0];
-    img[HW + pix] = C1 + T * sp->bg[1];
-    img[2 * HW + pix] = C2 + T * sp->bg[2];
-    const long long gpix = V.pix_base + pix;
-    if (Tout) Tout[gpix] = T;
-    last_out[gpix] = last;
-    if (gp_out) gp_out[gpix] = gp;
-    my_pairs = neval;
+    if (inside) {
+      const long long HW = (long long)V.W * V.H;
+      const long long pix = (long long)py * V.W + px;
+      float* img = image + 3 * V.pix_base;
+      img[pix] = C0 + T * bg0;
+      img[HW + pix] = C1 + T * bg1;
+      img[2 * HW + pix] = C2 + T * bg2;
+      const long long gpix = V.pix_base + pix;
+      if (Tout) Tout[gpix] = T;
+      last_out[gpix] = last;
+      if (gp_out) gp_out[gpix] = gp;
+      my_pairs += neval;
+    }
   }
   // Gaussian-pixel pairs by definition: entries evaluated per pixel up to its termination.
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+  __syncthreads();
   if ((tid & 31) == 0) s_pairs[tid >> 5] = my_pairs;
   __syncthreads();
   if (tid == 0) {
     unsigned long long s = 0;
 #pragma unroll
     for (int w = 0; w < kTilePix / 32; ++w) s += s_pairs[w];
-    atomicAdd(&ctl->pairs, s);
+    if (s) atomicAdd(&ctl->pairs, s);
   }
+}
+
+void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const Control* ctl, cudaStream_t s) {
+  if (n_tiles <= 0) return;
+  k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order, ctl);
 }
 
 void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
-                          float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt, int* chunk_tile,
-                          cudaStream_t s) {
+                          const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
+                          unsigned* cmask, int* chunk_tile, int num_sms, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  k_blend_forward<<<(unsigned)n_tiles, kTilePix, 0, s>>>(views, n_views, ranges, vals, pb, sp, ctl, image, T, last,
-                                                          gp, ckpt, chunk_tile);
+  long long grid = (long long)num_sms * 6;
+  if (grid > n_tiles) grid = n_tiles;
+  k_blend_forward<<<(unsigned)grid, kTilePix, 0, s>>>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image,
+                                                       T, last, gp, ckpt, cmask, chunk_tile);
 }
 
 // ---------------------------------------------------------------------------------------------
 // K8
 // ---------------------------------------------------------------------------------------------
-constexpr int kBwdWarps = 8;
+constexpr int kBwdWarps = 4;
+constexpr int kMaxPairs = kChunk * 32;  // a round: 32 pixels x 32 Gaussians at most
 
-struct BwdWarpSmem {
-  float4 a[kTilePix];   // (dL/dC r, g, b, bits: pixel index | (entries of this chunk it reaches) << 8)
-  float4 b[kTilePix];   // (rendered C r, g, b incl. background, 0)
-  float4 c[kTilePix];   // checkpoint (T, colour in front) at the chunk start
+struct BwdWarp {
+  float4 a[kChunk], b[kChunk], c[kChunk];  // the chunk's Gaussians (records A, B, C)
+  float acc[9][kChunk];                    // their gradient sums
+  uint2 act[kTilePix];                     // compacted (slot, mask) of the pixels to visit
+  unsigned ball[kChunk];                   // per Gaussian: which lanes of the round blended it
+  unsigned seg[kChunk];                    // per Gaussian: start of its run in the pair list
+  float4 pix[32];                          // per lane of the round: dL/dC (3), pixel x | y << 16
+  float pT[kMaxPairs];                     // per pair: transmittance in front of the Gaussian
+  float pD[kMaxPairs];                     // per pair: dL/dC . (colour behind the Gaussian)
+  unsigned short pid[kMaxPairs];           // per pair: lane | Gaussian << 8
 };
+
+// Gradient terms of one (pixel, Gaussian) pair: d mean2d (2), d conic a, b, c, d opacity, d rgb.
+__device__ __forceinline__ void pair_grad(const float4& xy, const float4& co, const float4& c, float pxf, float pyf,
+                                          float T, float DS, float d0, float d1, float d2, float g[9]) {
+  const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
+  const float power = splat_power(co.x, co.y, co.z, dx, dy);
+  const float G = splat_exp(power);
+  const float oG = __fmul_rn(c.w, G);
+  const float alpha = fminf(kAlphaMax, oG);
+  const float w = __fmul_rn(alpha, T);
+  // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha))
+  const float dalpha = T * (c.x * d0 + c.y * d1 + c.z * d2) - DS * __fdividef(1.f, 1.f - alpha);
+  g[6] = w * d0;
+  g[7] = w * d1;
+  g[8] = w * d2;
+  if (!(oG > kAlphaMax)) {
+    g[5] = dalpha * G;
+    const float dpow = dalpha * alpha;
+    g[0] = dpow * (2.f * co.x * dx + co.y * dy);
+    g[1] = dpow * (co.y * dx + 2.f * co.z * dy);
+    g[2] = dpow * (-0.5f * dx * dx);
+    g[3] = dpow * (-dx * dy);
+    g[4] = dpow * (-0.5f * dy * dy);
+  } else {
+    g[0] = g[1] = g[2] = g[3] = g[4] = g[5] = 0.f;
+  }
+}
 
 __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
     const unsigned* __restrict__ vals, const ProjBuffers pb, Control* __restrict__ ctl,
     const float* __restrict__ image, const unsigned* __restrict__ last_in, const float* __restrict__ dimage,
-    const float4* __restrict__ ckpt, const int* __restrict__ chunk_tile, float4* __restrict__ ginst) {
+    const float4* __restrict__ ckpt, const unsigned* __restrict__ cmask, const int* __restrict__ chunk_tile,
+    float4* __restrict__ ginst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BwdWarpSmem& S = reinterpret_cast<BwdWarpSmem*>(smem_raw)[warp];
+  BwdWarp& S = reinterpret_cast<BwdWarp*>(smem_raw)[warp];
   if (ctl->overflow) return;
   const unsigned long long M = ctl->m_total;
   const long long n_ids = (long long)(M >> 5) + n_tiles + 1;
   const unsigned lt = (1u << lane) - 1u;
-
+  const unsigned le = lt | (1u << lane);
   for (;;) {
     long long id = 0;
     if (lane == 0) id = (long long)atomicAdd(&ctl->bwd_work, 1u);
@@ -186,111 +314,148 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const ViewDev& V = views[v];
     const long long local = t - V.tile_base;
     const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
+    const long long cid = chunk_base(start, t) + k;
 
-    // Lane l's Gaussian and the slot of its instance gradient.
-    float4 xy = make_float4(0.f, 0.f, 0.f, 0.f), co = xy, col = xy;
     unsigned long long e = 0;
     if (lane < cnt) {
       const unsigned rec = vals[start + base + lane];
-      xy = pb.xyo[rec];
-      co = pb.conic[rec];
-      col = pb.rgb[rec];
+      S.a[lane] = pb.xyo[rec];
+      S.b[lane] = pb.conic[rec];
+      S.c[lane] = pb.rgb[rec];
       const uint2 rc = pb.rect[rec];
       const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu;
       e = (unsigned long long)pb.offsets[rec] + (unsigned long long)((ty - (int)y0) * (int)(x1 - x0) + (tx - (int)x0));
     }
-
-    // Stage the pixels of the tile that reach this chunk (last contributor beyond its start).
-    const long long HW = (long long)V.W * V.H;
-    const float* img = image + 3 * V.pix_base;
-    const float* dimg = dimage + 3 * V.pix_base;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) S.acc[c][lane] = 0.f;
+    // compact the pixels that blended at least one Gaussian of this chunk
     int n_act = 0;
-    for (int p0 = 0; p0 < kTilePix; p0 += 32) {
-      const int p = p0 + lane;
-      const int px = tx * kTile + (p & (kTile - 1)), py = ty * kTile + p / kTile;
+#pragma unroll
+    for (int r = 0; r < kTilePix / 32; ++r) {
+      const int slot = r * 32 + lane;
+      int ox, oy;
+      slot_xy(slot, ox, oy);
+      const int px = tx * kTile + ox, py = ty * kTile + oy;
       const bool inside = px < V.W && py < V.H;
-      const long long pix = (long long)py * V.W + px;
-      const unsigned lp = inside ? last_in[V.pix_base + pix] : 0u;
-      const bool act = lp > (unsigned)base;
-      const unsigned ball = __ballot_sync(0xffffffffu, act);
-      if (act) {
-        const int slot = n_act + __popc(ball & lt);
-        const unsigned reach = min(lp - (unsigned)base, (unsigned)kChunk);
-        S.a[slot] = make_float4(dimg[pix], dimg[HW + pix], dimg[2 * HW + pix],
-                                __uint_as_float((unsigned)p | (reach << 8)));
-        S.b[slot] = make_float4(img[pix], img[HW + pix], img[2 * HW + pix], 0.f);
-        S.c[slot] = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[(chunk_base(start, t) + k) * kTilePix + p];
-      }
+      const unsigned lp = inside ? last_in[V.pix_base + (long long)py * V.W + px] : 0u;
+      const unsigned mask = lp > (unsigned)base ? cmask[cid * kTilePix + slot] : 0u;
+      const unsigned ball = __ballot_sync(0xffffffffu, mask != 0u);
+      if (mask) S.act[n_act + __popc(ball & lt)] = make_uint2((unsigned)slot, mask);
       n_act += __popc(ball);
     }
     __syncwarp();
-
-    float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_o = 0.f, g_r = 0.f, g_g = 0.f, g_bl = 0.f;
-    float T = 1.f, F0 = 0.f, F1 = 0.f, F2 = 0.f;  // state of the pixel this lane holds
-    const float A2 = co.x, B2 = co.y, C2 = co.z;   // pre-scaled conic (-a/2, -b, -c/2)
-    const float opac = xy.z;
-    for (int s = 0; s < n_act + kChunk - 1; ++s) {
-      // Shift the pipeline by one lane; lane 0 takes the next pixel's checkpoint.
-      float iT = __shfl_up_sync(0xffffffffu, T, 1);
-      float i0 = __shfl_up_sync(0xffffffffu, F0, 1);
-      float i1 = __shfl_up_sync(0xffffffffu, F1, 1);
-      float i2 = __shfl_up_sync(0xffffffffu, F2, 1);
-      const int q = s - lane;
-      if (lane == 0 && q < n_act) {
-        const float4 c = S.c[q];
-        iT = c.x;
-        i0 = c.y;
-        i1 = c.z;
-        i2 = c.w;
+    const long long HW = (long long)V.W * V.H;
+    const float* img = image + 3 * V.pix_base;
+    const float* dimg = dimage + 3 * V.pix_base;
+    for (int r0 = 0; r0 < n_act; r0 += 32) {
+      const int i = r0 + lane;
+      const uint2 pm = i < n_act ? S.act[i] : make_uint2(0u, 0u);
+      unsigned mask = pm.y;
+      // (1) where each (pixel, Gaussian) pair of this round goes: pairs sorted by Gaussian, and
+      //     by lane within a Gaussian
+      unsigned myball = 0u;
+#pragma unroll
+      for (int q = 0; q < kChunk; ++q) {
+        const unsigned b = __ballot_sync(0xffffffffu, (mask >> q) & 1u);
+        if (lane == q) myball = b;
       }
-      T = iT;
-      F0 = i0;
-      F1 = i1;
-      F2 = i2;
-      if (q < 0 || q >= n_act || lane >= cnt) continue;
-      const float4 pa = S.a[q];
-      const unsigned bits = __float_as_uint(pa.w);
-      const int p = (int)(bits & 0xffu);
-      if (lane >= (int)(bits >> 8)) continue;  // this pixel stopped before Gaussian `lane`
-      const float pxf = (float)(tx * kTile + (p & (kTile - 1)));
-      const float pyf = (float)(ty * kTile + p / kTile);
-      const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
-      const float power = splat_power(A2, B2, C2, dx, dy);
-      if (power > 0.f) continue;
-      const float G = splat_exp(power);
-      const float oG = __fmul_rn(opac, G);
-      const float alpha = fminf(kAlphaMax, oG);
-      if (alpha < kAlphaMin) continue;
-      const float w = __fmul_rn(alpha, T);
-      const float n0 = __fmaf_rn(col.x, w, F0);
-      const float n1 = __fmaf_rn(col.y, w, F1);
-      const float n2 = __fmaf_rn(col.z, w, F2);
-      const float4 pbv = S.b[q];
-      // colour behind this Gaussian (later Gaussians plus background): C_pixel - front incl.
-      const float inv = __fdividef(1.f, 1.f - alpha);
-      const float dalpha = pa.x * (col.x * T - (pbv.x - n0) * inv) + pa.y * (col.y * T - (pbv.y - n1) * inv) +
-                           pa.z * (col.z * T - (pbv.z - n2) * inv);
-      g_r += w * pa.x;
-      g_g += w * pa.y;
-      g_bl += w * pa.z;
-      if (!(oG > kAlphaMax)) {
-        g_o += dalpha * G;
-        const float dpow = dalpha * alpha;
-        g_u += dpow * (2.f * A2 * dx + B2 * dy);
-        g_v += dpow * (B2 * dx + 2.f * C2 * dy);
-        g_a += dpow * (-0.5f * dx * dx);
-        g_b += dpow * (-dx * dy);
-        g_c += dpow * (-0.5f * dy * dy);
+      const unsigned mycnt = __popc(myball);
+      unsigned incl = mycnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-      F0 = n0;
-      F1 = n1;
-      F2 = n2;
+      const int n_pairs = (int)__shfl_sync(0xffffffffu, incl, 31);
+      S.ball[lane] = myball;
+      S.seg[lane] = incl - mycnt;
+      // (2) each lane walks the Gaussians its pixel blended, in order, with the forward's exact
+      //     transmittance, and records (T, dL/dC . behind) per pair
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+      int px = 0, py = 0;
+      if (mask) {
+        int ox, oy;
+        slot_xy((int)pm.x, ox, oy);
+        px = tx * kTile + ox;
+        py = ty * kTile + oy;
+        const long long pix = (long long)py * V.W + px;
+        d0 = dimg[pix];
+        d1 = dimg[HW + pix];
+        d2 = dimg[2 * HW + pix];
+      }
+      S.pix[lane] = make_float4(d0, d1, d2, __uint_as_float((unsigned)px | ((unsigned)py << 16)));
+      __syncwarp();
+      if (mask) {
+        const long long pix = (long long)py * V.W + px;
+        const float4 ck = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[cid * kTilePix + pm.x];
+        float T = ck.x, F0 = ck.y, F1 = ck.z, F2 = ck.w;
+        const float P0 = img[pix], P1 = img[HW + pix], P2 = img[2 * HW + pix];
+        const float pxf = (float)px, pyf = (float)py;
+        while (mask) {
+          const int q = __ffs(mask) - 1;
+          mask &= mask - 1u;
+          const float4 xy = S.a[q];
+          const float4 co = S.b[q];
+          const float4 c = S.c[q];
+          const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
+          const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, splat_exp(power)));
+          const float w = __fmul_rn(alpha, T);
+          const float n0 = __fmaf_rn(c.x, w, F0);
+          const float n1 = __fmaf_rn(c.y, w, F1);
+          const float n2 = __fmaf_rn(c.z, w, F2);
+          // colour behind = rendered colour (incl. background) - colour in front incl. this one
+          const int pos = (int)S.seg[q] + __popc(S.ball[q] & lt);
+          S.pT[pos] = T;
+          S.pD[pos] = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
+          S.pid[pos] = (unsigned short)(lane | (q << 8));
+          T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          F0 = n0;
+          F1 = n1;
+          F2 = n2;
+        }
+      }
+      __syncwarp();
+      // (3) all lanes take consecutive pairs; a segmented scan sums each Gaussian's run
+      for (int j0 = 0; j0 < n_pairs; j0 += 32) {
+        const int j = j0 + lane;
+        float g[9];
+        int q = 255 + lane;  // distinct sentinel for idle lanes
+        if (j < n_pairs) {
+          const unsigned idw = S.pid[j];
+          const int pl = (int)(idw & 255u);
+          q = (int)(idw >> 8);
+          const float4 pp = S.pix[pl];
+          const unsigned xyb = __float_as_uint(pp.w);
+          pair_grad(S.a[q], S.b[q], S.c[q], (float)(xyb & 0xffffu), (float)(xyb >> 16), S.pT[j], S.pD[j], pp.x, pp.y,
+                    pp.z, g);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) g[c] = 0.f;
+        }
+        const int qp = __shfl_up_sync(0xffffffffu, q, 1);
+        const int qn = __shfl_down_sync(0xffffffffu, q, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || qp != q);
+        const int first = 31 - __clz(heads & le);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            const float y = __shfl_up_sync(0xffffffffu, g[c], o);
+            if (lane - o >= first) g[c] += y;
+          }
+        }
+        if (j < n_pairs && (lane == 31 || qn != q)) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) S.acc[c][q] += g[c];
+        }
+        __syncwarp();
+      }
     }
+    __syncwarp();
     if (lane < cnt) {
-      ginst[3 * e] = make_float4(g_u, g_v, g_a, g_b);
-      ginst[3 * e + 1] = make_float4(g_c, g_o, g_r, g_g);
-      ginst[3 * e + 2] = make_float4(g_bl, 0.f, 0.f, 0.f);
+      ginst[3 * e] = make_float4(S.acc[0][lane], S.acc[1][lane], S.acc[2][lane], S.acc[3][lane]);
+      ginst[3 * e + 1] = make_float4(S.acc[4][lane], S.acc[5][lane], S.acc[6][lane], S.acc[7][lane]);
+      ginst[3 * e + 2] = make_float4(S.acc[8][lane], 0.f, 0.f, 0.f);
     }
     __syncwarp();
   }
@@ -298,16 +463,15 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
 
 void init_blend_attributes() {
   cudaFuncSetAttribute(k_blend_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(BwdWarpSmem) * kBwdWarps));
+                       (int)(sizeof(BwdWarp) * kBwdWarps));
 }
 
 void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
-                           const unsigned* last, const float* dimage, const float4* ckpt, const int* chunk_tile,
-                           float4* ginst, int num_sms, cudaStream_t s) {
-  const int smem = (int)(sizeof(BwdWarpSmem) * kBwdWarps);
-  k_blend_backward<<<num_sms * 2, kBwdWarps * 32, smem, s>>>(views, n_views, n_tiles, ranges, vals, pb, ctl, image,
-                                                              last, dimage, ckpt, chunk_tile, ginst);
+                           const unsigned* last, const float* dimage, const float4* ckpt, const unsigned* cmask,
+                           const int* chunk_tile, float4* ginst, int num_sms, cudaStream_t s) {
+  k_blend_backward<<<num_sms * 3, kBwdWarps * 32, sizeof(BwdWarp) * kBwdWarps, s>>>(
+      views, n_views, n_tiles, ranges, vals, pb, ctl, image, last, dimage, ckpt, cmask, chunk_tile, ginst);
 }
 
 }  // namespace gs

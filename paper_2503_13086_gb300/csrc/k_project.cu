@@ -245,10 +245,19 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ param
     col[ch] = fmaxf(acc, 0.f);
   }
   const float opac = 1.f / (1.f + __expf(-__ldg(params + 10 * stride + i)));
-
-  out.xyo[rec] = make_float4(u, vv, opac, 0.f);
-  out.conic[rec] = make_float4(-0.5f * ca, -cb, -0.5f * cc, 0.f);
-  out.rgb[rec] = make_float4(col[0], col[1], col[2], 0.f);
+  // alpha = opacity * exp(power) reaches 1/255 only where power >= thr = -ln(255 opacity), i.e.
+  // inside the ellipse d^T conic d <= 2 ln(255 opacity); its axis-aligned half extents are
+  // sqrt(2 ln(255 opacity) cov_xx), sqrt(.. cov_yy).  Widened by 0.1 % + 0.01 px so no pixel the
+  // blend would accept lies outside (a culling bound only; it decides nothing by itself).
+  const float thr = -logf(255.f * opac);
+  float ex = -1e30f, ey = -1e30f;
+  if (thr < 0.f) {
+    ex = sqrtf(-2.f * thr * g.cov[0]) * 1.001f + 0.01f;
+    ey = sqrtf(-2.f * thr * g.cov[2]) * 1.001f + 0.01f;
+  }
+  out.xyo[rec] = make_float4(u, vv, ex, ey);
+  out.conic[rec] = make_float4(-0.5f * ca, -cb, -0.5f * cc, thr);
+  out.rgb[rec] = make_float4(col[0], col[1], col[2], opac);
   out.depth[rec] = g.p[2];
   out.radius[rec] = r;
   out.rect[rec] = make_uint2((unsigned)x0 | ((unsigned)x1 << 16), (unsigned)y0 | ((unsigned)y1 << 16));
@@ -259,52 +268,175 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ param
 // ---------------------------------------------------------------------------------------------
 // K9 + K10: per Gaussian, sum the instance gradients of every view, chain them to the 59
 // parameters and either apply Adam (hot path) or write the gradient (parity / autograd).
+// Streaming layout: the geometry is chained view by view; what the 48 SH coefficients need
+// (view direction, masked colour gradient, 1/|mu - camera|) is kept per view, and the SH rows
+// are then updated one coefficient at a time, so a thread never holds all 59 gradients.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_project_backward(
+template <int K>
+__device__ __forceinline__ void sh_term(float x, float y, float z, float& Y, float& gx, float& gy, float& gz) {
+  const float xx = x * x, yy = y * y, zz = z * z;
+  switch (K) {
+    case 0: Y = kSH0; gx = gy = gz = 0.f; break;
+    case 1: Y = -kSH1 * y; gx = 0.f; gy = -kSH1; gz = 0.f; break;
+    case 2: Y = kSH1 * z; gx = 0.f; gy = 0.f; gz = kSH1; break;
+    case 3: Y = -kSH1 * x; gx = -kSH1; gy = 0.f; gz = 0.f; break;
+    case 4: Y = kSH2a * x * y; gx = kSH2a * y; gy = kSH2a * x; gz = 0.f; break;
+    case 5: Y = -kSH2a * y * z; gx = 0.f; gy = -kSH2a * z; gz = -kSH2a * y; break;
+    case 6: Y = kSH2b * (2.f * zz - xx - yy); gx = -2.f * kSH2b * x; gy = -2.f * kSH2b * y; gz = 4.f * kSH2b * z; break;
+    case 7: Y = -kSH2a * x * z; gx = -kSH2a * z; gy = 0.f; gz = -kSH2a * x; break;
+    case 8: Y = kSH2c * (xx - yy); gx = 2.f * kSH2c * x; gy = -2.f * kSH2c * y; gz = 0.f; break;
+    case 9: Y = -kSH3a * y * (3.f * xx - yy); gx = -6.f * kSH3a * x * y; gy = -kSH3a * (3.f * xx - 3.f * yy); gz = 0.f; break;
+    case 10: Y = kSH3b * x * y * z; gx = kSH3b * y * z; gy = kSH3b * x * z; gz = kSH3b * x * y; break;
+    case 11:
+      Y = -kSH3c * y * (4.f * zz - xx - yy);
+      gx = 2.f * kSH3c * x * y; gy = -kSH3c * (4.f * zz - xx - 3.f * yy); gz = -8.f * kSH3c * y * z;
+      break;
+    case 12:
+      Y = kSH3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      gx = -6.f * kSH3d * x * z; gy = -6.f * kSH3d * y * z; gz = kSH3d * (6.f * zz - 3.f * xx - 3.f * yy);
+      break;
+    case 13:
+      Y = -kSH3c * x * (4.f * zz - xx - yy);
+      gx = -kSH3c * (4.f * zz - 3.f * xx - yy); gy = 2.f * kSH3c * x * y; gz = -8.f * kSH3c * x * z;
+      break;
+    case 14: Y = kSH3e * z * (xx - yy); gx = 2.f * kSH3e * x * z; gy = -2.f * kSH3e * y * z; gz = kSH3e * (xx - yy); break;
+    default: Y = -kSH3a * x * (xx - 3.f * yy); gx = -kSH3a * (3.f * xx - 3.f * yy); gy = 6.f * kSH3a * x * y; gz = 0.f; break;
+  }
+}
+
+struct AdamArgs {
+  float* params;
+  float* m;
+  float* v;
+  float* grads_out;
+  int stride;
+  int adam;
+  float b1, b2, eps, ssc, bc2s;
+  float lr[6];
+};
+
+// Adam (or gradient write) for n consecutive component rows c0..c0+n-1 of Gaussian i, with
+// every load issued before the first store so the rows stream concurrently.
+template <int N>
+__device__ __forceinline__ void apply_rows(const AdamArgs& A, int c0, const int* grp, int i, const float* g,
+                                           const float* pcur) {
+  if (!A.adam) {
+#pragma unroll
+    for (int r = 0; r < N; ++r) A.grads_out[(long long)(c0 + r) * A.stride + i] = g[r];
+    return;
+  }
+  float m[N], v[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const long long k = (long long)(c0 + r) * A.stride + i;
+    m[r] = A.m[k];
+    v[r] = A.v[k];
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const long long k = (long long)(c0 + r) * A.stride + i;
+    const float mm = A.b1 * m[r] + (1.f - A.b1) * g[r];
+    const float vv = A.b2 * v[r] + (1.f - A.b2) * g[r] * g[r];
+    A.m[k] = mm;
+    A.v[k] = vv;
+    A.params[k] = pcur[r] - (A.lr[grp[r]] * A.ssc) * mm / (sqrtf(vv) / A.bc2s + A.eps);
+  }
+}
+
+// Four SH coefficients (12 rows) K0..K0+3: gradient sum over the visible views, the direction
+// gradient they feed, and the update.
+template <int K0>
+__device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, const float (*vdir)[3],
+                                         const float (*vcol)[3], float (*vdd)[3]) {
+  float p[12];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) p[r] = A.params[(long long)(11 + 3 * K0 + r) * A.stride + i];
+  float g[12];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) g[r] = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < nvis; ++j) {
+    const float x = vdir[j][0], y = vdir[j][1], z = vdir[j][2];
+    const float c0 = vcol[j][0], c1 = vcol[j][1], c2 = vcol[j][2];
+    float Y[4], gx[4], gy[4], gz[4];
+    sh_term<K0 + 0>(x, y, z, Y[0], gx[0], gy[0], gz[0]);
+    sh_term<K0 + 1>(x, y, z, Y[1], gx[1], gy[1], gz[1]);
+    sh_term<K0 + 2>(x, y, z, Y[2], gx[2], gy[2], gz[2]);
+    sh_term<K0 + 3>(x, y, z, Y[3], gx[3], gy[3], gz[3]);
+    float ddx = 0.f, ddy = 0.f, ddz = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      g[3 * kk + 0] += Y[kk] * c0;
+      g[3 * kk + 1] += Y[kk] * c1;
+      g[3 * kk + 2] += Y[kk] * c2;
+      const float w = p[3 * kk] * c0 + p[3 * kk + 1] * c1 + p[3 * kk + 2] * c2;
+      ddx += gx[kk] * w;
+      ddy += gy[kk] * w;
+      ddz += gz[kk] * w;
+    }
+    vdd[j][0] += ddx;
+    vdd[j][1] += ddy;
+    vdd[j][2] += ddz;
+  }
+  int grp[12];
+#pragma unroll
+  for (int r = 0; r < 12; ++r) grp[r] = (K0 == 0 && r < 3) ? 4 : 5;
+  apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
+}
+
+__global__ void __launch_bounds__(256, 2) k_project_backward(
     float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
-    const unsigned* __restrict__ offsets, const float4* __restrict__ ginst,
-    const Control* __restrict__ ctl, float* __restrict__ grads_out, float* __restrict__ adam_m,
-    float* __restrict__ adam_v, float* __restrict__ grad2d_out) {
+    const unsigned* __restrict__ offsets, const unsigned char* __restrict__ clampbits,
+    const float4* __restrict__ ginst, const Control* __restrict__ ctl, float* __restrict__ grads_out,
+    float* __restrict__ adam_m, float* __restrict__ adam_v, float* __restrict__ grad2d_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sp->n) return;
   if (ctl->overflow) return;  // the step was skipped; the host re-runs it with more capacity
 
+  AdamArgs A;
+  A.params = params;
+  A.m = adam_m;
+  A.v = adam_v;
+  A.grads_out = grads_out;
+  A.stride = stride;
+  A.adam = sp->adam;
+  A.b1 = sp->beta1;
+  A.b2 = sp->beta2;
+  A.eps = sp->eps;
+  A.ssc = sp->step_size_scale;
+  A.bc2s = sp->bc2_sqrt;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.lr[k] = sp->lr[k];
+
+  float mu[3], ls[3], q[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = params[k * stride + i];
+    ls[k] = params[(3 + k) * stride + i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
+  const float logit = params[10 * stride + i];
+
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gop = 0.f;
-  float gsh[48];
-#pragma unroll
-  for (int k = 0; k < 48; ++k) gsh[k] = 0.f;
-
-  bool any = false;
-  float mu[3], ls[3], q[4];
+  // per visible view: direction, masked colour gradient, 1/|d|, and the direction gradient
+  float vdir[kMaxStepViews][3], vcol[kMaxStepViews][3], vinv[kMaxStepViews], vdd[kMaxStepViews][3];
+  int nvis = 0;
+  float o = 0.f;
+  bool have_o = false;
+#pragma unroll 1
   for (int v = 0; v < n_views; ++v) {
     const long long rec = (long long)v * stride + i;
     const unsigned cnt = count[rec];
     if (cnt == 0u) continue;
-    if (!any) {
-      any = true;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        mu[k] = params[k * stride + i];
-        ls[k] = params[(3 + k) * stride + i];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
-    }
-    // Sum of the per-instance 2D gradients (one instance per tile of the rectangle).
     const unsigned off = offsets[rec];
     float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (unsigned e = off; e < off + cnt; ++e) {
       const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], c = ginst[3ull * e + 2];
-      g2[0] += a.x;
-      g2[1] += a.y;
-      g2[2] += a.z;
-      g2[3] += a.w;
-      g2[4] += b.x;
-      g2[5] += b.y;
-      g2[6] += b.z;
-      g2[7] += b.w;
+      g2[0] += a.x; g2[1] += a.y; g2[2] += a.z; g2[3] += a.w;
+      g2[4] += b.x; g2[5] += b.y; g2[6] += b.z; g2[7] += b.w;
       g2[8] += c.x;
     }
     if (grad2d_out) {
@@ -313,61 +445,40 @@ __global__ void __launch_bounds__(128) k_project_backward(
     }
     const ViewDev& V = views[v];
     Geo g;
-    geo_forward(V, mu, ls, q, g);
+    if (!geo_forward(V, mu, ls, q, g)) continue;
 
-    // opacity = sigmoid(logit)
-    {
-      const float o = 1.f / (1.f + __expf(-params[10 * stride + i]));
-      gop += g2[5] * o * (1.f - o);
+    if (!have_o) {
+      o = 1.f / (1.f + __expf(-logit));
+      have_o = true;
     }
-    // colour -> SH coefficients and view direction (clamped channels pass no gradient)
-    float dvec[3] = {mu[0] - V.campos[0], mu[1] - V.campos[1], mu[2] - V.campos[2]};
-    const float dinv = rsqrtf(dvec[0] * dvec[0] + dvec[1] * dvec[1] + dvec[2] * dvec[2]);
-    const float dir[3] = {dvec[0] * dinv, dvec[1] * dinv, dvec[2] * dinv};
-    float Y[16];
-    sh_basis(dir[0], dir[1], dir[2], Y);
-    float wdir[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) wdir[k] = 0.f;
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      float raw = 0.5f;
-      float shc[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        shc[k] = params[(11 + 3 * k + ch) * stride + i];
-        raw += Y[k] * shc[k];
-      }
-      if (raw < 0.f) continue;
-      const float dcol = g2[6 + ch];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        gsh[3 * k + ch] += Y[k] * dcol;
-        wdir[k] += shc[k] * dcol;
-      }
-    }
-    float ddir[3] = {0.f, 0.f, 0.f};
-    sh_basis_vjp(dir[0], dir[1], dir[2], wdir, ddir);
-    {
-      const float dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) gmu[a] += (ddir[a] - dir[a] * dd) * dinv;
-    }
+    gop += g2[5] * o * (1.f - o);
+
+    // view direction and the colour gradient of the unclamped channels, kept for the SH rows
+    const float d0 = mu[0] - V.campos[0], d1 = mu[1] - V.campos[1], d2 = mu[2] - V.campos[2];
+    const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    const unsigned cb = clampbits[rec];
+    vdir[nvis][0] = d0 * dinv;
+    vdir[nvis][1] = d1 * dinv;
+    vdir[nvis][2] = d2 * dinv;
+    vcol[nvis][0] = (cb & 1u) ? 0.f : g2[6];
+    vcol[nvis][1] = (cb & 2u) ? 0.f : g2[7];
+    vcol[nvis][2] = (cb & 4u) ? 0.f : g2[8];
+    vinv[nvis] = dinv;
+    vdd[nvis][0] = vdd[nvis][1] = vdd[nvis][2] = 0.f;
+    ++nvis;
 
     // Pre-scaled conic gradient back to the conic (a, b, c): power = -a/2 dx^2 - b dx dy - c/2 dy^2.
     const float dA = g2[2], dB = g2[3], dC = g2[4];
-    const float A = g.cov[0], B = g.cov[1], C = g.cov[2], det = g.det;
+    const float A_ = g.cov[0], B_ = g.cov[1], C_ = g.cov[2], det = g.det;
     const float id = 1.f / det, id2 = id * id;
-    const float da = dA * (-C * C * id2) + dB * (B * C * id2) + dC * (id - A * C * id2);
-    const float db = dA * (2.f * B * C * id2) + dB * (-id - 2.f * B * B * id2) + dC * (2.f * A * B * id2);
-    const float dc = dA * (id - A * C * id2) + dB * (A * B * id2) + dC * (-A * A * id2);
+    const float da = dA * (-C_ * C_ * id2) + dB * (B_ * C_ * id2) + dC * (id - A_ * C_ * id2);
+    const float db = dA * (2.f * B_ * C_ * id2) + dB * (-id - 2.f * B_ * B_ * id2) + dC * (2.f * A_ * B_ * id2);
+    const float dc = dA * (id - A_ * C_ * id2) + dB * (A_ * B_ * id2) + dC * (-A_ * A_ * id2);
 
     // (a, b, c) = entries of Tm Sigma Tm^T
     const float* T0 = g.Tm;
     const float* T1 = g.Tm + 3;
     const float S[9] = {g.Sig[0], g.Sig[1], g.Sig[2], g.Sig[1], g.Sig[3], g.Sig[4], g.Sig[2], g.Sig[4], g.Sig[5]};
-    // symmetric gradient w.r.t. Sigma: G = da T0 T0^T + db (T0 T1^T + T1 T0^T)/2 + dc T1 T1^T,
-    // and dL/dM = 2 G M.
     float Gs[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -382,7 +493,6 @@ __global__ void __launch_bounds__(128) k_project_backward(
       dT0[r] = 2.f * da * s0 + db * s1;
       dT1[r] = 2.f * dc * s1 + db * s0;
     }
-    // Tm = J R_cam: dJ = dTm R_cam^T (only J00, J02, J11, J12 are non-zero functions)
     const float dJ00 = dT0[0] * V.R[0] + dT0[1] * V.R[1] + dT0[2] * V.R[2];
     const float dJ02 = dT0[0] * V.R[6] + dT0[1] * V.R[7] + dT0[2] * V.R[8];
     const float dJ11 = dT1[0] * V.R[3] + dT1[1] * V.R[4] + dT1[2] * V.R[5];
@@ -403,7 +513,6 @@ __global__ void __launch_bounds__(128) k_project_backward(
     } else {
       dp[2] += dJ12 * (V.fy * g.tyz * iz2);
     }
-    // mean2d = (fx x/z + cx, fy y/z + cy)
     dp[0] += g2[0] * V.fx * iz;
     dp[2] += g2[0] * (-V.fx * px * iz2);
     dp[1] += g2[1] * V.fy * iz;
@@ -411,7 +520,6 @@ __global__ void __launch_bounds__(128) k_project_backward(
 #pragma unroll
     for (int a = 0; a < 3; ++a) gmu[a] += V.R[a] * dp[0] + V.R[3 + a] * dp[1] + V.R[6 + a] * dp[2];
 
-    // Sigma = M M^T, M = Rq diag(s)
     float dM[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -442,37 +550,23 @@ __global__ void __launch_bounds__(128) k_project_backward(
     for (int k = 0; k < 4; ++k) gq[k] += (dqn[k] - g.qn[k] * qd) * g.qinv;
   }
 
-  float gall[kNumParams];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gall[k] = gmu[k];
-    gall[3 + k] = gls[k];
-  }
-#pragma unroll
-  for (int k = 0; k < 4; ++k) gall[6 + k] = gq[k];
-  gall[10] = gop;
-#pragma unroll
-  for (int k = 0; k < 48; ++k) gall[11 + k] = gsh[k];
+  // SH rows, four coefficients (12 rows) at a time; accumulates the direction gradient.
+  sh_group<0>(A, i, nvis, vdir, vcol, vdd);
+  sh_group<4>(A, i, nvis, vdir, vcol, vdd);
+  sh_group<8>(A, i, nvis, vdir, vcol, vdd);
+  sh_group<12>(A, i, nvis, vdir, vcol, vdd);
 
-  if (!sp->adam) {
+  // direction = (mu - c)/|mu - c|  ->  mean
+#pragma unroll 1
+  for (int j = 0; j < nvis; ++j) {
+    const float dd = vdir[j][0] * vdd[j][0] + vdir[j][1] * vdd[j][1] + vdir[j][2] * vdd[j][2];
 #pragma unroll
-    for (int c = 0; c < kNumParams; ++c) grads_out[(long long)c * stride + i] = gall[c];
-    return;
+    for (int a = 0; a < 3; ++a) gmu[a] += (vdd[j][a] - vdir[j][a] * dd) * vinv[j];
   }
-  // Adam (torch.optim.Adam's bias-corrected update), dense over every live Gaussian.
-  const float b1 = sp->beta1, b2 = sp->beta2, eps = sp->eps;
-  const float ssc = sp->step_size_scale, bc2s = sp->bc2_sqrt;
-#pragma unroll
-  for (int c = 0; c < kNumParams; ++c) {
-    const int grp = c < 3 ? 0 : (c < 6 ? 1 : (c < 10 ? 2 : (c < 11 ? 3 : (c < 14 ? 4 : 5))));
-    const long long k = (long long)c * stride + i;
-    const float gr = gall[c];
-    const float m = b1 * adam_m[k] + (1.f - b1) * gr;
-    const float vv = b2 * adam_v[k] + (1.f - b2) * gr * gr;
-    adam_m[k] = m;
-    adam_v[k] = vv;
-    params[k] -= (sp->lr[grp] * ssc) * m / (sqrtf(vv) / bc2s + eps);
-  }
+  const float gg[11] = {gmu[0], gmu[1], gmu[2], gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
+  const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
+  const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};
+  apply_rows<11>(A, 0, grp, i, gg, pc);
 }
 
 // Plain Adam over a gradient buffer (parity of K10 on its own; dense, vectorised by 4).
@@ -516,8 +610,8 @@ void launch_project(const float* params, int stride, int n_views, const StepPara
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
                              const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
                              float* m, float* v, float* grad2d_out, cudaStream_t s) {
-  k_project_backward<<<(stride + 127) / 128, 128, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
-                                                           ginst, ctl, grads_out, m, v, grad2d_out);
+  k_project_backward<<<(stride + 255) / 256, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
+                                                           pb.clamp, ginst, ctl, grads_out, m, v, grad2d_out);
 }
 
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,

@@ -22,7 +22,7 @@ def gpu_forward(ras, params_np, n, cams, bg=(0.0, 0.0, 0.0)):
     xyo = ras.read(0, np.float32).reshape(recs, 4)
     con = ras.read(1, np.float32).reshape(recs, 4)
     rgb = ras.read(2, np.float32).reshape(recs, 4)
-    rec = dict(mean2d=np.ascontiguousarray(xyo[:, :2]), opacity=np.ascontiguousarray(xyo[:, 2]),
+    rec = dict(mean2d=np.ascontiguousarray(xyo[:, :2]), opacity=np.ascontiguousarray(rgb[:, 3]),
                conic=np.ascontiguousarray(np.stack([-2 * con[:, 0], -con[:, 1], -2 * con[:, 2]], 1)),
                rgb=np.ascontiguousarray(rgb[:, :3]))
     radius = ras.read(4, np.int32)

@@ -1,0 +1,172 @@
+"""Session layer through the C ABI: optimisation step vs the oracle's step, graph replay vs
+eager launch, snapshot/restore, the schedule (Eq. 3-8) vs the oracle's schedule, and the field
+update of Sec. IV-B (new-point test and 3DGS initialisation)."""
+import math
+
+import numpy as np
+import pytest
+
+import gsinputs as gi
+import oracle
+from helpers import config1, ocam
+from oracle import schedule as sch
+
+pytestmark = pytest.mark.gpu
+
+LRS_REST = [5e-3, 1e-3, 0.05, 2.5e-3, 2.5e-3 / 20]
+C0 = 0.5 * math.sqrt(1.0 / math.pi)
+
+
+def make_field(**kw):
+    import paper_2503_13086_gb300 as gs
+    kw.setdefault("scene_extent", 1.0)
+    return gs.Field(**kw)
+
+
+def test_step_matches_oracle_step():
+    p, cams, tg = config1(seed=4)
+    f = make_field(use_graph=0)
+    f.set_gaussians(p)
+    img = f.add_image(cams[0], tg[0])
+    lr = f.image_lr(img)
+    assert lr == pytest.approx(1.6e-4, rel=1e-6)  # Eq. 6-8: T = 0, no overlapping image
+    loss = f.optimize_step([img])
+    got = f.get_gaussians()
+    L, g, _ = oracle.loss_and_grad(p, [ocam(cams[0])], tg, lam=0.2, prec="f32")
+    ref = p.copy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    oracle.adam(ref, g, m, v, [lr * 1.0] + LRS_REST, 1, prec="f32")
+    assert abs(loss - L) <= 1e-5 * max(1.0, abs(L))
+    groups = [(0, 3, lr), (3, 6, 5e-3), (6, 10, 1e-3), (10, 11, 0.05), (11, 14, 2.5e-3), (14, 59, 1.25e-4)]
+    for a, b, lrg in groups:
+        d = np.abs(got[a:b] - ref[a:b, :got.shape[1]])
+        # a first Adam step moves each parameter by ~lr * sign(g): only gradients too small to
+        # have a stable sign may differ
+        bad = d > 1e-3 * lrg + 1e-6
+        assert bad.mean() < 2e-3, (a, b, bad.mean())
+    f.close()
+
+
+def test_graph_replay_equals_eager():
+    p, cams, tg = config1(seed=5)
+    res = []
+    for use_graph in (1, 0):
+        f = make_field(use_graph=use_graph)
+        f.set_gaussians(p)
+        img = f.add_image(cams[0], tg[0])
+        losses = [f.optimize_step([img]) for _ in range(4)]
+        res.append((losses, f.get_gaussians(with_adam=True)))
+        f.close()
+    assert res[0][0] == res[1][0]
+    for a, b in zip(res[0][1], res[1][1]):
+        assert np.array_equal(a, b)
+
+
+def test_snapshot_restore():
+    p, cams, tg = config1(seed=6)
+    f = make_field()
+    f.set_gaussians(p)
+    img = f.add_image(cams[0], tg[0])
+    f.optimize_step([img])
+    f.snapshot()
+    s0 = f.get_gaussians(with_adam=True)
+    T0, _ = f.image_info(img, 1)
+    l1 = [f.optimize_step([img]) for _ in range(2)]
+    assert not np.array_equal(f.get_gaussians(), s0[0])
+    f.restore()
+    s1 = f.get_gaussians(with_adam=True)
+    for a, b in zip(s0, s1):
+        assert np.array_equal(a, b)
+    assert f.image_info(img, 1)[0] == T0
+    l2 = [f.optimize_step([img]) for _ in range(2)]
+    assert l1 == l2  # deterministic replay from the snapshot
+    f.close()
+
+
+def test_schedule_matches_oracle():
+    """Golden 5-image overlap example: weights (Eq. 3-4), allocation (Eq. 5 + semi-global) and the
+    per-image learning rate (Eq. 6-8) of the C++ session against the oracle's schedule."""
+    T_I, N_m, seed = 21, 3, 11  # odd: the semi-global remainder exercises the seeded draw
+    f = make_field(T_I=T_I, N_m=N_m, T_a=200, seed=seed, use_graph=0)
+    p = gi.cube_scene(512, seed=1, stride=512)
+    f.set_gaussians(p)
+    tracks = [np.arange(1, 11), np.arange(6, 16), np.arange(11, 21), np.arange(16, 26), np.arange(30, 36)]
+    W, H = 64, 48
+    for k, tr in enumerate(tracks):
+        cam = gi.identity_camera(W, H, 64.0)
+        cam["t"] = np.array([0.05 * k, 0.0, 0.0])
+        f.add_image(cam, gi.uniform_target(W, H, k), pts_xyz=np.zeros((len(tr), 3)) + 100.0 + k,
+                    pts_rgb=np.full((len(tr), 3), 0.5), tracks=tr)
+    M = sch.overlap_matrix(tracks)
+    for i in range(5):
+        assert np.allclose(f.image_info(i, 5)[1], M[i], atol=1e-7)
+    ids, w = f.select_neighbors(3, 4)
+    wref, _ = sch.hierarchical_weights(M, 3)
+    assert ids == [3, 2, 1, 0]
+    assert np.allclose(w, [wref[i] for i in ids], atol=1e-7)
+    # integrate image 3 and compare T_j with the oracle's allocation
+    n_before = f.stats()["n_gaussians"]
+    st = f.integrate(3)
+    keys, iters, slots = sch.allocate(wref, N_m, T_I, list(range(5)), 3, seed)
+    assert st["iterations"] == T_I and st["key_images"] == len(keys)
+    Ts = [f.image_info(i, 5)[0] for i in range(5)]
+    assert Ts == [iters[i] for i in range(5)]
+    for i in range(5):
+        ref = sch.lr_image(i, M, Ts, 200, 1.6e-4, 1.6e-6)
+        assert f.image_lr(i) == pytest.approx(ref, rel=1e-5)
+    assert f.stats()["n_gaussians"] == n_before
+    f.close()
+
+
+def test_field_update_adds_far_points_with_3dgs_init():
+    thr = 0.05
+    f = make_field(add_dist_thresh=thr, use_graph=0)
+    rng = np.random.default_rng(3)
+    W, H = 48, 32
+    cam = gi.identity_camera(W, H, 48.0)
+    pts1 = rng.uniform(-0.5, 0.5, (200, 3)) + [0, 0, 3]
+    col1 = rng.uniform(0, 1, (200, 3))
+    f.add_image(cam, gi.uniform_target(W, H, 1), pts1, col1, np.arange(200))
+    n1 = f.stats()["n_gaussians"]
+    # first image: no existing points, every point becomes a Gaussian
+    assert n1 == 200
+    near = pts1[:50] + rng.normal(0, 0.005, (50, 3))        # within thr of an existing point
+    far = rng.uniform(-0.5, 0.5, (80, 3)) + [0, 0, 6]        # far from everything
+    pts2 = np.concatenate([near, far])
+    col2 = rng.uniform(0, 1, (130, 3))
+    f.add_image(cam, gi.uniform_target(W, H, 2), pts2, col2, np.arange(100, 230))
+    d_exist = np.sqrt(((pts2[:, None, :] - pts1[None, :, :]) ** 2).sum(-1)).min(1)
+    is_new = d_exist > thr
+    got = f.get_gaussians()
+    assert got.shape[1] == 200 + is_new.sum()
+    new = got[:, 200:]
+    allp = np.concatenate([pts1, pts2]).astype(np.float32)
+    idx = np.nonzero(is_new)[0]
+    assert np.allclose(new[0:3].T, pts2[idx], atol=1e-6)
+    for q, k in enumerate(idx):
+        d2 = ((allp - pts2[k].astype(np.float32)) ** 2).sum(1)
+        d2[200 + k] = np.inf
+        mean3 = np.sort(d2)[:3].mean()
+        assert new[3, q] == pytest.approx(math.log(math.sqrt(max(mean3, 1e-7))), abs=1e-4)
+    assert np.allclose(new[6], 1.0) and np.allclose(new[7:10], 0.0)
+    assert np.allclose(new[10], math.log(0.1 / 0.9), atol=1e-6)
+    assert np.allclose(new[11:14].T, (col2[idx] - 0.5) / C0, atol=1e-5)
+    assert np.allclose(new[14:59], 0.0)
+    # overlap from shared tracks: 100 of 200 tracks of image 0 are in image 1 (130 tracks)
+    assert f.image_info(0, 2)[1][1] == pytest.approx(100 / 130, rel=1e-6)
+    f.close()
+
+
+def test_budget_and_bad_arguments():
+    import paper_2503_13086_gb300 as gs
+    f = make_field(hbm_budget_bytes=1 << 20)
+    with pytest.raises(gs.GSError) as e:
+        f.set_gaussians(gi.cube_scene(100000, seed=0, stride=100000))
+    assert e.value.status == 3  # GS_ERR_BUDGET
+    f.close()
+    f = make_field()
+    with pytest.raises(gs.GSError) as e:
+        f.optimize_step([0])
+    assert e.value.status in (1, 7)
+    f.close()
