@@ -250,6 +250,27 @@ GS_API gs_status gs_field_restore(gs_field* f);
 GS_API gs_status gs_field_set_timing(gs_field* f, int enable);
 GS_API gs_status gs_field_kernel_times(gs_field* f, float out_ms[9], int64_t* out_steps);
 
+/* ----------------------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is a deployment variant.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Exclusive prefix sum of n uint32 tile counts (the scan K2 runs inside gs_raster_forward),
+ * for callers that cannot allocate device memory: code running while another component owns the
+ * device allocator, or on a path where an allocation's implicit synchronisation is not allowed.
+ * It calls no cudaMalloc, cudaFree or allocating library routine; its scratch is a 65 KiB array
+ * in the library's own device memory, which every GPU that loads the library keeps until exit.
+ *   counts      (device, n uint32, 16-byte aligned)          input
+ *   out_offsets (device, n uint32, 16-byte aligned)          out_offsets[i] = sum of counts[0..i)
+ *   out_total   (device, one uint64, nullable)               sum of all counts
+ * n may be 0 .. 2^24 (GS_ERR_CAPACITY beyond); the sum must fit in 32 bits for the offsets.
+ * Asynchronous on stream.  The first call on a device also looks up the scratch array's device
+ * address; make that first call before any stream capture.  All calls share the one scratch
+ * array: calls that can overlap on the GPU (other streams, other threads) race and give wrong
+ * results, so serialise them.  The look-back waits are bounded; if one gives up, the offsets are
+ * unspecified (no error is reported, as nothing is read back). */
+GS_API gs_status gs_scan_noalloc(void* stream, const uint32_t* counts, int64_t n, uint32_t* out_offsets,
+                                 uint64_t* out_total);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,7 @@ SYMBOLS = {
     "gs_field_restore": ([P], I32),
     "gs_field_set_timing": ([P, ctypes.c_int], I32),
     "gs_field_kernel_times": ([P, P, P], I32),
+    "gs_scan_noalloc": ([P, P, I64, P, P], I32),
 }
 
 KERNEL_NAMES = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss",
