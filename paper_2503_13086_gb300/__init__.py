@@ -194,6 +194,7 @@ class Raster:
         _check(self._lib.gs_raster_create(ctypes.byref(h)))
         self._h = h
         self._sizes = None
+        self.generation = 0  # bumped by every forward (the workspace keeps only the latest one)
 
     def close(self):
         if self._h:
@@ -222,6 +223,7 @@ class Raster:
                                            _cams(cams), len(cams), bgv, _ptr(image), _ptr(T), _ptr(last), _ptr(gp),
                                            ctypes.byref(pairs)))
         self._sizes = sizes
+        self.generation += 1
         return dict(image=image, T=T, last=last, gp=gp, pairs=int(pairs.value), sizes=sizes)
 
     def loss(self, image, target, lambda_ssim=0.2, want_grad=True, stream=None):

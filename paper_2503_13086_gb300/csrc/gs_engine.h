@@ -51,7 +51,7 @@ struct Raster {
   DevBuf zeroB;  // histograms + sort look-back state + ranges + chunk map (cleared before K3)
   size_t zeroA_bytes = 0, zeroB_bytes = 0, sort_state_bytes = 0, ranges_bytes = 0, chunk_bytes = 0;
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp;
-  DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order;
+  DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order, tile_chunks;
   DevBuf partials, block_sums;
   DevBuf own_image, own_last, own_dimage;  // used by sessions
   unsigned long long m_cap = 0;

@@ -52,11 +52,11 @@ void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const
 void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
-                          unsigned* cmask, int* chunk_tile, int num_sms, cudaStream_t s);
+                          unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s);
 void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
-                           const unsigned* last, const float* dimage, const float4* ckpt, const unsigned* cmask,
-                           const int* chunk_tile, float4* ginst, int num_sms, cudaStream_t s);
+                           const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
+                           const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s);
 
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);

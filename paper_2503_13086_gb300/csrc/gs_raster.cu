@@ -82,7 +82,7 @@ Raster::Raster() {
 
 Raster::~Raster() {
   DevBuf* all[] = {&sp_d, &views_d, &zeroA, &zeroB, &xyo, &conic, &rgb, &depth, &radius, &rect, &count, &offsets,
-                   &clamp, &keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &cmask, &order, &partials, &block_sums, &own_image,
+                   &clamp, &keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
                    &own_last, &own_dimage};
   for (DevBuf* b : all) b->release(&bytes_in_use);
   if (sp_h) cudaFreeHost(sp_h);
@@ -200,7 +200,8 @@ gs_status Raster::ensure_instances(unsigned long long m) {
   const unsigned long long n_ids = (m_cap >> 5) + (unsigned long long)n_tiles + 1;
   gs_status s;
   if ((s = ckpt.reserve(n_ids * kTilePix * sizeof(float4), &bytes_in_use)) ||
-      (s = cmask.reserve(n_ids * kTilePix * 4, &bytes_in_use)) || (s = order.reserve((size_t)n_tiles * 4, &bytes_in_use)))
+      (s = cmask.reserve(n_ids * kTilePix * 4, &bytes_in_use)) || (s = order.reserve((size_t)n_tiles * 4, &bytes_in_use)) ||
+      (s = tile_chunks.reserve((size_t)n_tiles * 4, &bytes_in_use)))
     return s;
   const unsigned long long sort_tiles = (m_cap + kSortTile - 1) / kSortTile;
   sort_state_bytes = (size_t)passes * sort_tiles * kSortBins * 4;
@@ -282,7 +283,7 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
   mark(s, 5);
   launch_blend_forward(vd(), n_views, n_tiles, ranges(), vb[sorted], proj(), sp(), ctl(),
                        static_cast<const int*>(order.p), image, T, last, gp, static_cast<float4*>(ckpt.p),
-                       static_cast<unsigned*>(cmask.p), chunk_tile(), num_sms, s);
+                       static_cast<unsigned*>(cmask.p), chunk_tile(), static_cast<int*>(tile_chunks.p), num_sms, s);
   mark(s, 6);
   return GS_OK;
 }
@@ -295,9 +296,10 @@ void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
 
 void Raster::enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last,
                               const float* dimage, float* grads, float* m, float* v, float* grad2d) {
+  (void)last;  // the backward reads the forward's per-chunk masks instead of the last index
   launch_blend_backward(vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(sorted ? vals1.p : vals0.p), proj(),
-                        ctl(), image, last, dimage, static_cast<float4*>(ckpt.p), static_cast<unsigned*>(cmask.p),
-                        chunk_tile(), static_cast<float4*>(ginst.p), num_sms, s);
+                        ctl(), image, dimage, static_cast<float4*>(ckpt.p), static_cast<unsigned*>(cmask.p),
+                        chunk_tile(), static_cast<int*>(tile_chunks.p), static_cast<float4*>(ginst.p), num_sms, s);
   mark(s, 8);
   launch_project_backward(params, stride, n_views, sp(), vd(), proj(), static_cast<float4*>(ginst.p), ctl(), grads,
                           m, v, grad2d, s);

@@ -16,14 +16,14 @@
 // K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
 // (tile, 32-entry chunk), one warp each, taken from a global counter.  The warp compacts the
-// tile's pixels whose mask for this chunk is non-empty and takes them 32 at a time: each lane
-// restarts its pixel from the checkpoint and walks only the Gaussians it blended, in order, with
-// exactly the forward's transmittance (the colour behind a Gaussian is the rendered colour minus
-// the colour accumulated in front of it), recording per (pixel, Gaussian) pair its slot in a
-// list sorted by Gaussian (slots from per-Gaussian ballots).  Then all 32 lanes take consecutive
-// pairs, compute the nine gradient terms, and a segmented warp scan sums each Gaussian's run.
-// No atomics and a fixed summation order: the gradient is deterministic.  Each instance's
-// gradient is written once, to its own slot.
+// tile's pixels whose mask for this chunk is non-empty and takes them 32 at a time.  First each
+// lane restarts its pixel from the checkpoint and walks only the Gaussians it blended, in order,
+// with exactly the forward's transmittance (the colour behind a Gaussian is the rendered colour
+// minus the colour accumulated in front of it), leaving per (Gaussian, pixel) the transmittance
+// in front and dL/dC . (colour behind) in shared memory.  Then the roles swap: lane q owns
+// Gaussian q of the chunk and adds, in pixel order, the nine gradient terms of the pixels that
+// blended it, in registers.  No atomics and a fixed summation order: the gradient is
+// deterministic, and each instance's gradient is written once, to its own slot.
 #include "gs_device.cuh"
 #include "gs_engine.h"
 
@@ -92,10 +92,11 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
     const unsigned* __restrict__ vals, const ProjBuffers pb, const StepParams* __restrict__ sp,
     Control* __restrict__ ctl, const int* __restrict__ order, float* __restrict__ image, float* __restrict__ Tout,
     unsigned* __restrict__ last_out, unsigned* __restrict__ gp_out, float4* __restrict__ ckpt,
-    unsigned* __restrict__ cmask, int* __restrict__ chunk_tile) {
+    unsigned* __restrict__ cmask, int* __restrict__ chunk_tile, int* __restrict__ tile_chunks) {
   __shared__ float4 s_xyo[kBlendBatch];
   __shared__ float4 s_con[kBlendBatch];
   __shared__ float4 s_rgb[kBlendBatch];
+  __shared__ unsigned char s_bm[kBlendBatch];  // per entry: the warp blocks its cutoff box reaches
   __shared__ unsigned long long s_pairs[kTilePix / 32];
   __shared__ int s_item;
   if (ctl->overflow) return;
@@ -119,9 +120,8 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
     const int py = ty * kTile + oy;
     const bool inside = px < V.W && py < V.H;
     const float pxf = (float)px, pyf = (float)py;
-    // centre of this warp's 8 x 4 block (pixel centres span 7 x 3 pixels around it)
-    const float bcx = (float)(tx * kTile + (((tid >> 5) & 1) << 3)) + 3.5f;
-    const float bcy = (float)(ty * kTile + ((tid >> 6) << 2)) + 1.5f;
+    const int warp = tid >> 5, lane = tid & 31;
+    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
 
     const uint2 rg = ranges[t];
     const unsigned start = rg.x;
@@ -133,36 +133,55 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
     unsigned last = 0u, gp = 0u;
     unsigned neval = (unsigned)L;
     bool done = !inside;
+    int batches = 0;
     for (int b0 = 0; b0 < L; b0 += kBlendBatch) {
       if (__syncthreads_count(done) == kTilePix) break;
+      ++batches;
       const int j = b0 + tid;
       if (j < L) {
         const unsigned rec = vals[start + j];
-        s_xyo[tid] = pb.xyo[rec];
+        const float4 xy = pb.xyo[rec];
+        s_xyo[tid] = xy;
         s_con[tid] = pb.conic[rec];
         s_rgb[tid] = pb.rgb[rec];
+        // which of the eight 8 x 4 warp blocks (warp w at (8 (w % 2), 4 (w / 2))) the cutoff box
+        // of this Gaussian reaches; block centres are 3.5 / 1.5 px from their edge pixels
+        unsigned xm = 0u, ym = 0u;
+#pragma unroll
+        for (int bx = 0; bx < 2; ++bx)
+          if (fabsf(xy.x - (tx0 + 8.f * bx + 3.5f)) <= xy.z + 3.5f) xm |= 1u << bx;
+#pragma unroll
+        for (int by = 0; by < 4; ++by)
+          if (fabsf(xy.y - (ty0 + 4.f * by + 1.5f)) <= xy.w + 1.5f) ym |= 1u << by;
+        unsigned bm = 0u;
+#pragma unroll
+        for (int by = 0; by < 4; ++by)
+          if (ym & (1u << by)) bm |= xm << (2 * by);
+        s_bm[tid] = (unsigned char)bm;
       }
       __syncthreads();
-      if (done) continue;
       const int nb = min(kBlendBatch, L - b0);
       for (int c0 = 0; c0 < nb; c0 += kChunk) {
         const int jg0 = b0 + c0;
         const long long chunk = cb + (jg0 >> 5);
-        if (jg0 > 0) ckpt[chunk * kTilePix + tid] = make_float4(T, C0, C1, C2);
         const int ce = min(kChunk, nb - c0);
+        // entries of this chunk whose cutoff box reaches this warp's block (warp-uniform)
+        const unsigned rel = __ballot_sync(0xffffffffu, lane < ce && ((s_bm[c0 + lane] >> warp) & 1u));
+        if (done) {  // stopped pixels still record an empty mask: the backward reads every chunk
+          cmask[chunk * kTilePix + tid] = 0u;
+          continue;
+        }
+        if (jg0 > 0) ckpt[chunk * kTilePix + tid] = make_float4(T, C0, C1, C2);
         // candidates: alpha may reach 1/255 (independent iterations -> pipelined)
         unsigned cand = 0u;
-#pragma unroll 8
-        for (int q = 0; q < kChunk; ++q) {
-          if (q < ce) {
-            const float4 xy = s_xyo[c0 + q];
-            // warp-uniform: does the cutoff box reach this warp's block at all?
-            if (fabsf(xy.x - bcx) <= xy.z + 3.5f && fabsf(xy.y - bcy) <= xy.w + 1.5f) {
-              const float4 co = s_con[c0 + q];
-              const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
-              if (!(power > 0.f) && power >= co.w) cand |= 1u << q;
-            }
-          }
+        unsigned rl = rel;
+        while (rl) {
+          const int q = __ffs(rl) - 1;
+          rl &= rl - 1u;
+          const float4 xy = s_xyo[c0 + q];
+          const float4 co = s_con[c0 + q];
+          const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
+          if (!(power > 0.f) && power >= co.w) cand |= 1u << q;
         }
         unsigned mask = 0u;
         while (cand) {
@@ -190,9 +209,10 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
           mask |= 1u << q;
         }
         cmask[chunk * kTilePix + tid] = mask;
-        if (done) break;
       }
     }
+    // chunks whose masks K6 wrote for every pixel of the tile (the rest the backward skips)
+    if (tid == 0) tile_chunks[t] = min((L + kChunk - 1) / kChunk, batches * (kBlendBatch / kChunk));
     if (inside) {
       const long long HW = (long long)V.W * V.H;
       const long long pix = (long long)py * V.W + px;
@@ -229,33 +249,29 @@ void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const
 void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
-                          unsigned* cmask, int* chunk_tile, int num_sms, cudaStream_t s) {
+                          unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
   if (n_tiles <= 0) return;
   long long grid = (long long)num_sms * 6;
   if (grid > n_tiles) grid = n_tiles;
   k_blend_forward<<<(unsigned)grid, kTilePix, 0, s>>>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image,
-                                                       T, last, gp, ckpt, cmask, chunk_tile);
+                                                       T, last, gp, ckpt, cmask, chunk_tile, tile_chunks);
 }
 
 // ---------------------------------------------------------------------------------------------
 // K8
 // ---------------------------------------------------------------------------------------------
 constexpr int kBwdWarps = 4;
-constexpr int kMaxPairs = kChunk * 32;  // a round: 32 pixels x 32 Gaussians at most
 
 struct BwdWarp {
   float4 a[kChunk], b[kChunk], c[kChunk];  // the chunk's Gaussians (records A, B, C)
-  float acc[9][kChunk];                    // their gradient sums
   uint2 act[kTilePix];                     // compacted (slot, mask) of the pixels to visit
-  unsigned ball[kChunk];                   // per Gaussian: which lanes of the round blended it
-  unsigned seg[kChunk];                    // per Gaussian: start of its run in the pair list
   float4 pix[32];                          // per lane of the round: dL/dC (3), pixel x | y << 16
-  float pT[kMaxPairs];                     // per pair: transmittance in front of the Gaussian
-  float pD[kMaxPairs];                     // per pair: dL/dC . (colour behind the Gaussian)
-  unsigned short pid[kMaxPairs];           // per pair: lane | Gaussian << 8
+  float pT[kChunk][33];                    // per (Gaussian, lane): transmittance in front
+  float pD[kChunk][33];                    // per (Gaussian, lane): dL/dC . (colour behind)
 };
 
-// Gradient terms of one (pixel, Gaussian) pair: d mean2d (2), d conic a, b, c, d opacity, d rgb.
+// Gradient terms of one (pixel, Gaussian) pair added into g: d mean2d (2), d conic a, b, c,
+// d opacity, d rgb.
 __device__ __forceinline__ void pair_grad(const float4& xy, const float4& co, const float4& c, float pxf, float pyf,
                                           float T, float DS, float d0, float d1, float d2, float g[9]) {
   const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
@@ -266,27 +282,25 @@ __device__ __forceinline__ void pair_grad(const float4& xy, const float4& co, co
   const float w = __fmul_rn(alpha, T);
   // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha))
   const float dalpha = T * (c.x * d0 + c.y * d1 + c.z * d2) - DS * __fdividef(1.f, 1.f - alpha);
-  g[6] = w * d0;
-  g[7] = w * d1;
-  g[8] = w * d2;
+  g[6] += w * d0;
+  g[7] += w * d1;
+  g[8] += w * d2;
   if (!(oG > kAlphaMax)) {
-    g[5] = dalpha * G;
+    g[5] += dalpha * G;
     const float dpow = dalpha * alpha;
-    g[0] = dpow * (2.f * co.x * dx + co.y * dy);
-    g[1] = dpow * (co.y * dx + 2.f * co.z * dy);
-    g[2] = dpow * (-0.5f * dx * dx);
-    g[3] = dpow * (-dx * dy);
-    g[4] = dpow * (-0.5f * dy * dy);
-  } else {
-    g[0] = g[1] = g[2] = g[3] = g[4] = g[5] = 0.f;
+    g[0] += dpow * (2.f * co.x * dx + co.y * dy);
+    g[1] += dpow * (co.y * dx + 2.f * co.z * dy);
+    g[2] += dpow * (-0.5f * dx * dx);
+    g[3] += dpow * (-dx * dy);
+    g[4] += dpow * (-0.5f * dy * dy);
   }
 }
 
 __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
     const unsigned* __restrict__ vals, const ProjBuffers pb, Control* __restrict__ ctl,
-    const float* __restrict__ image, const unsigned* __restrict__ last_in, const float* __restrict__ dimage,
-    const float4* __restrict__ ckpt, const unsigned* __restrict__ cmask, const int* __restrict__ chunk_tile,
+    const float* __restrict__ image, const float* __restrict__ dimage, const float4* __restrict__ ckpt,
+    const unsigned* __restrict__ cmask, const int* __restrict__ chunk_tile, const int* __restrict__ tile_chunks,
     float4* __restrict__ ginst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -295,7 +309,6 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
   const unsigned long long M = ctl->m_total;
   const long long n_ids = (long long)(M >> 5) + n_tiles + 1;
   const unsigned lt = (1u << lane) - 1u;
-  const unsigned le = lt | (1u << lane);
   for (;;) {
     long long id = 0;
     if (lane == 0) id = (long long)atomicAdd(&ctl->bwd_work, 1u);
@@ -326,22 +339,21 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
       const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu;
       e = (unsigned long long)pb.offsets[rec] + (unsigned long long)((ty - (int)y0) * (int)(x1 - x0) + (tx - (int)x0));
     }
+    float g[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) S.acc[c][lane] = 0.f;
-    // compact the pixels that blended at least one Gaussian of this chunk
+    for (int c = 0; c < 9; ++c) g[c] = 0.f;
+    // Chunks past tile_chunks[t] were never reached by any pixel: all gradients are zero.
     int n_act = 0;
+    if (k < tile_chunks[t]) {
+      // compact the pixels that blended at least one Gaussian of this chunk
 #pragma unroll
-    for (int r = 0; r < kTilePix / 32; ++r) {
-      const int slot = r * 32 + lane;
-      int ox, oy;
-      slot_xy(slot, ox, oy);
-      const int px = tx * kTile + ox, py = ty * kTile + oy;
-      const bool inside = px < V.W && py < V.H;
-      const unsigned lp = inside ? last_in[V.pix_base + (long long)py * V.W + px] : 0u;
-      const unsigned mask = lp > (unsigned)base ? cmask[cid * kTilePix + slot] : 0u;
-      const unsigned ball = __ballot_sync(0xffffffffu, mask != 0u);
-      if (mask) S.act[n_act + __popc(ball & lt)] = make_uint2((unsigned)slot, mask);
-      n_act += __popc(ball);
+      for (int r = 0; r < kTilePix / 32; ++r) {
+        const int slot = r * 32 + lane;
+        const unsigned mask = cmask[cid * kTilePix + slot];
+        const unsigned ball = __ballot_sync(0xffffffffu, mask != 0u);
+        if (mask) S.act[n_act + __popc(ball & lt)] = make_uint2((unsigned)slot, mask);
+        n_act += __popc(ball);
+      }
     }
     __syncwarp();
     const long long HW = (long long)V.W * V.H;
@@ -351,26 +363,15 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
       const int i = r0 + lane;
       const uint2 pm = i < n_act ? S.act[i] : make_uint2(0u, 0u);
       unsigned mask = pm.y;
-      // (1) where each (pixel, Gaussian) pair of this round goes: pairs sorted by Gaussian, and
-      //     by lane within a Gaussian
+      // lane q learns which lanes (pixels) of this round blended Gaussian q
       unsigned myball = 0u;
 #pragma unroll
       for (int q = 0; q < kChunk; ++q) {
         const unsigned b = __ballot_sync(0xffffffffu, (mask >> q) & 1u);
         if (lane == q) myball = b;
       }
-      const unsigned mycnt = __popc(myball);
-      unsigned incl = mycnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int n_pairs = (int)__shfl_sync(0xffffffffu, incl, 31);
-      S.ball[lane] = myball;
-      S.seg[lane] = incl - mycnt;
-      // (2) each lane walks the Gaussians its pixel blended, in order, with the forward's exact
-      //     transmittance, and records (T, dL/dC . behind) per pair
+      // (1) each lane walks the Gaussians its pixel blended, in order, with the forward's exact
+      //     transmittance, recording per (Gaussian, pixel) T and dL/dC . (colour behind)
       float d0 = 0.f, d1 = 0.f, d2 = 0.f;
       int px = 0, py = 0;
       if (mask) {
@@ -382,11 +383,6 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
         d0 = dimg[pix];
         d1 = dimg[HW + pix];
         d2 = dimg[2 * HW + pix];
-      }
-      S.pix[lane] = make_float4(d0, d1, d2, __uint_as_float((unsigned)px | ((unsigned)py << 16)));
-      __syncwarp();
-      if (mask) {
-        const long long pix = (long long)py * V.W + px;
         const float4 ck = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[cid * kTilePix + pm.x];
         float T = ck.x, F0 = ck.y, F1 = ck.z, F2 = ck.w;
         const float P0 = img[pix], P1 = img[HW + pix], P2 = img[2 * HW + pix];
@@ -404,58 +400,35 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
           const float n1 = __fmaf_rn(c.y, w, F1);
           const float n2 = __fmaf_rn(c.z, w, F2);
           // colour behind = rendered colour (incl. background) - colour in front incl. this one
-          const int pos = (int)S.seg[q] + __popc(S.ball[q] & lt);
-          S.pT[pos] = T;
-          S.pD[pos] = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
-          S.pid[pos] = (unsigned short)(lane | (q << 8));
+          S.pT[q][lane] = T;
+          S.pD[q][lane] = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
           T = __fmul_rn(T, __fsub_rn(1.f, alpha));
           F0 = n0;
           F1 = n1;
           F2 = n2;
         }
       }
+      S.pix[lane] = make_float4(d0, d1, d2, __uint_as_float((unsigned)px | ((unsigned)py << 16)));
       __syncwarp();
-      // (3) all lanes take consecutive pairs; a segmented scan sums each Gaussian's run
-      for (int j0 = 0; j0 < n_pairs; j0 += 32) {
-        const int j = j0 + lane;
-        float g[9];
-        int q = 255 + lane;  // distinct sentinel for idle lanes
-        if (j < n_pairs) {
-          const unsigned idw = S.pid[j];
-          const int pl = (int)(idw & 255u);
-          q = (int)(idw >> 8);
+      // (2) lane q sums, in lane order, the terms of the pixels that blended Gaussian q
+      if (lane < cnt) {
+        const float4 xy = S.a[lane], co = S.b[lane], c = S.c[lane];
+        unsigned bl = myball;
+        while (bl) {
+          const int pl = __ffs(bl) - 1;
+          bl &= bl - 1u;
           const float4 pp = S.pix[pl];
           const unsigned xyb = __float_as_uint(pp.w);
-          pair_grad(S.a[q], S.b[q], S.c[q], (float)(xyb & 0xffffu), (float)(xyb >> 16), S.pT[j], S.pD[j], pp.x, pp.y,
+          pair_grad(xy, co, c, (float)(xyb & 0xffffu), (float)(xyb >> 16), S.pT[lane][pl], S.pD[lane][pl], pp.x, pp.y,
                     pp.z, g);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) g[c] = 0.f;
         }
-        const int qp = __shfl_up_sync(0xffffffffu, q, 1);
-        const int qn = __shfl_down_sync(0xffffffffu, q, 1);
-        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || qp != q);
-        const int first = 31 - __clz(heads & le);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            const float y = __shfl_up_sync(0xffffffffu, g[c], o);
-            if (lane - o >= first) g[c] += y;
-          }
-        }
-        if (j < n_pairs && (lane == 31 || qn != q)) {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) S.acc[c][q] += g[c];
-        }
-        __syncwarp();
       }
+      __syncwarp();
     }
-    __syncwarp();
     if (lane < cnt) {
-      ginst[3 * e] = make_float4(S.acc[0][lane], S.acc[1][lane], S.acc[2][lane], S.acc[3][lane]);
-      ginst[3 * e + 1] = make_float4(S.acc[4][lane], S.acc[5][lane], S.acc[6][lane], S.acc[7][lane]);
-      ginst[3 * e + 2] = make_float4(S.acc[8][lane], 0.f, 0.f, 0.f);
+      ginst[3 * e] = make_float4(g[0], g[1], g[2], g[3]);
+      ginst[3 * e + 1] = make_float4(g[4], g[5], g[6], g[7]);
+      ginst[3 * e + 2] = make_float4(g[8], 0.f, 0.f, 0.f);
     }
     __syncwarp();
   }
@@ -468,10 +441,10 @@ void init_blend_attributes() {
 
 void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
-                           const unsigned* last, const float* dimage, const float4* ckpt, const unsigned* cmask,
-                           const int* chunk_tile, float4* ginst, int num_sms, cudaStream_t s) {
-  k_blend_backward<<<num_sms * 3, kBwdWarps * 32, sizeof(BwdWarp) * kBwdWarps, s>>>(
-      views, n_views, n_tiles, ranges, vals, pb, ctl, image, last, dimage, ckpt, cmask, chunk_tile, ginst);
+                           const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
+                           const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
+  k_blend_backward<<<num_sms * 4, kBwdWarps * 32, sizeof(BwdWarp) * kBwdWarps, s>>>(
+      views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, chunk_tile, tile_chunks, ginst);
 }
 
 }  // namespace gs

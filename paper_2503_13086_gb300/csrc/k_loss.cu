@@ -4,7 +4,7 @@
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
 // views, the loss is the mean of the per-view losses.  The window is separable: each CTA stages
-// a 32 x 16 output block plus a 5-pixel halo in shared memory, blurs rows then columns.
+// a 32 x 32 output block plus a 5-pixel halo in shared memory, blurs rows then columns.
 //   pass 1 (k_loss_forward): the five window moments -> SSIM map, the three partial derivatives
 //          of SSIM with respect to (mu_x, E[x^2], E[xy]) per pixel, and per-CTA sums;
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
@@ -16,8 +16,9 @@
 namespace gs {
 
 namespace {
-constexpr int kBX = 32, kBY = 16, kR = 5;
-constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // 42 x 26 staged block
+constexpr int kBX = 32, kBY = 32, kR = 5;
+constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // 42 x 42 staged block
+constexpr int kSXP = 44;                               // padded row: 16-byte aligned float4 reads
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 __device__ __forceinline__ void window(float w[11]) {
@@ -37,16 +38,32 @@ __device__ __forceinline__ int view_of_block(const ViewDev* __restrict__ views, 
   while (v + 1 < n_views && views[v + 1].loss_block_base <= b) ++v;
   return v;
 }
+
+// 16 consecutive values of a padded shared row starting at a multiple of 4
+__device__ __forceinline__ void load16(const float* row, int c0, float o[16]) {
+  const float4* r4 = reinterpret_cast<const float4*>(row + c0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = r4[k];
+    o[4 * k] = v.x;
+    o[4 * k + 1] = v.y;
+    o[4 * k + 2] = v.z;
+    o[4 * k + 3] = v.w;
+  }
+}
 }  // namespace
 
 long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * ((H + kBY - 1) / kBY); }
 
+// Each thread blurs 4 adjacent outputs per pass (row segment, then column segment) from 14
+// staged values per map, so a staged value is read once per 4 outputs.
 __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
                                                       long long n_blocks, const float* __restrict__ image,
                                                       const StepParams* __restrict__ sp,
                                                       float* __restrict__ partials, double* __restrict__ block_sums,
                                                       Control* __restrict__ ctl) {
-  __shared__ float sx[kSY][kSX], sy[kSY][kSX];
+  __shared__ __align__(16) float sx[kSY][kSXP];
+  __shared__ __align__(16) float sy[kSY][kSXP];
   __shared__ float hm[5][kSY][kBX];
   __shared__ double s_red[2][8];
   __shared__ bool s_last;
@@ -66,60 +83,83 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   float* P = partials + 9 * V.pix_base;
   double l1 = 0.0, ss = 0.0;
   for (int ch = 0; ch < 3; ++ch) {
-    for (int k = threadIdx.x; k < kSX * kSY; k += blockDim.x) {
-      const int r = k / kSX, c = k % kSX;
+    for (int k = threadIdx.x; k < kSY * kSXP; k += blockDim.x) {
+      const int r = k / kSXP, c = k % kSXP;
       const int gy = oy + r - kR, gx = ox + c - kR;
-      const bool in = gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
+      const bool in = c < kSX && gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
       const long long pix = (long long)gy * V.W + gx;
       sx[r][c] = in ? X[ch * HW + pix] : 0.f;
       sy[r][c] = in ? Yt[ch * HW + pix] : 0.f;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kSY * kBX; k += blockDim.x) {
-      const int r = k / kBX, c = k % kBX;
-      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+    // horizontal: 42 rows x 8 segments of 4 columns
+    for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
+      const int r = task / (kBX / 4), c0 = (task % (kBX / 4)) * 4;
+      float xv[16], yv[16];
+      load16(sx[r], c0, xv);
+      load16(sy[r], c0, yv);
+      float acc[5][4];
 #pragma unroll
-      for (int t = 0; t < 11; ++t) {
-        const float xv = sx[r][c + t], yv = sy[r][c + t];
-        m0 += w[t] * xv;
-        m1 += w[t] * yv;
-        m2 += w[t] * xv * xv;
-        m3 += w[t] * yv * yv;
-        m4 += w[t] * xv * yv;
+      for (int m = 0; m < 5; ++m)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) acc[m][o] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 14; ++j) {
+        const float x = xv[j], y = yv[j], xx = x * x, yy = y * y, xy = x * y;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int t = j - o;
+          if (t >= 0 && t < 11) {
+            acc[0][o] += w[t] * x;
+            acc[1][o] += w[t] * y;
+            acc[2][o] += w[t] * xx;
+            acc[3][o] += w[t] * yy;
+            acc[4][o] += w[t] * xy;
+          }
+        }
       }
-      hm[0][r][c] = m0;
-      hm[1][r][c] = m1;
-      hm[2][r][c] = m2;
-      hm[3][r][c] = m3;
-      hm[4][r][c] = m4;
+#pragma unroll
+      for (int m = 0; m < 5; ++m)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) hm[m][r][c0 + o] = acc[m][o];
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kBY * kBX; k += blockDim.x) {
-      const int r = k / kBX, c = k % kBX;
-      const int gy = oy + r, gx = ox + c;
-      if (gx >= V.W || gy >= V.H) continue;
-      float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    // vertical: 32 columns x 8 segments of 4 rows
+    {
+      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
+      float mom[5][4];
 #pragma unroll
-      for (int t = 0; t < 11; ++t) {
-        mx += w[t] * hm[0][r + t][c];
-        my += w[t] * hm[1][r + t][c];
-        exx += w[t] * hm[2][r + t][c];
-        eyy += w[t] * hm[3][r + t][c];
-        exy += w[t] * hm[4][r + t][c];
+      for (int m = 0; m < 5; ++m) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) mom[m][o] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 14; ++j) {
+          const float h = hm[m][r0 + j][c];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) mom[m][o] += w[t] * h;
+          }
+        }
       }
-      const float N1 = 2.f * mx * my + kC1, N2 = 2.f * (exy - mx * my) + kC2;
-      const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
-      const float N = N1 * N2, D = D1 * D2;
-      const float iD = 1.f / D;
-      const float S = N * iD;
-      ss += (double)S;
-      const float dN = 2.f * my * N2 - 2.f * my * N1;
-      const float dD = 2.f * mx * D2 - 2.f * mx * D1;
-      const long long pix = (long long)gy * V.W + gx;
-      P[(3 * ch + 0) * HW + pix] = (dN * D - N * dD) * iD * iD;  // dS/dmu_x
-      P[(3 * ch + 1) * HW + pix] = -N * D1 * iD * iD;             // dS/dE[x^2]
-      P[(3 * ch + 2) * HW + pix] = 2.f * N1 * iD;                 // dS/dE[xy]
-      l1 += (double)fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int gy = oy + r0 + o, gx = ox + c;
+        if (gx >= V.W || gy >= V.H) continue;
+        const float mx = mom[0][o], my = mom[1][o], exx = mom[2][o], eyy = mom[3][o], exy = mom[4][o];
+        const float N1 = 2.f * mx * my + kC1, N2 = 2.f * (exy - mx * my) + kC2;
+        const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
+        const float N = N1 * N2, D = D1 * D2;
+        const float iD = 1.f / D;
+        ss += (double)(N * iD);
+        const float dN = 2.f * my * N2 - 2.f * my * N1;
+        const float dD = 2.f * mx * D2 - 2.f * mx * D1;
+        const long long pix = (long long)gy * V.W + gx;
+        P[(3 * ch + 0) * HW + pix] = (dN * D - N * dD) * iD * iD;  // dS/dmu_x
+        P[(3 * ch + 1) * HW + pix] = -N * D1 * iD * iD;             // dS/dE[x^2]
+        P[(3 * ch + 2) * HW + pix] = 2.f * N1 * iD;                 // dS/dE[xy]
+        l1 += (double)fabsf(sx[r0 + o + kR][c + kR] - sy[r0 + o + kR][c + kR]);
+      }
     }
     __syncthreads();
   }
@@ -190,7 +230,7 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
                                                        const StepParams* __restrict__ sp,
                                                        const float* __restrict__ partials,
                                                        const Control* __restrict__ ctl, float* __restrict__ dimage) {
-  __shared__ float sp3[3][kSY][kSX];
+  __shared__ __align__(16) float sp3[3][kSY][kSXP];
   __shared__ float hb[3][kSY][kBX];
   if (ctl->overflow) return;
   float w[11];
@@ -211,45 +251,61 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   const float scale = 1.f / (3.f * (float)V.W * (float)V.H * (float)n_views);
   const float gl1 = (1.f - lam) * scale, gs = -lam * scale;
   for (int ch = 0; ch < 3; ++ch) {
-    for (int k = threadIdx.x; k < kSX * kSY; k += blockDim.x) {
-      const int r = k / kSX, c = k % kSX;
+    for (int k = threadIdx.x; k < kSY * kSXP; k += blockDim.x) {
+      const int r = k / kSXP, c = k % kSXP;
       const int gy = oy + r - kR, gx = ox + c - kR;
-      const bool in = gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
+      const bool in = c < kSX && gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
       const long long pix = (long long)gy * V.W + gx;
 #pragma unroll
       for (int m = 0; m < 3; ++m) sp3[m][r][c] = in ? P[(3 * ch + m) * HW + pix] : 0.f;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kSY * kBX; k += blockDim.x) {
-      const int r = k / kBX, c = k % kBX;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
+      const int r = task / (kBX / 4), c0 = (task % (kBX / 4)) * 4;
 #pragma unroll
-      for (int t = 0; t < 11; ++t) {
-        a0 += w[t] * sp3[0][r][c + t];
-        a1 += w[t] * sp3[1][r][c + t];
-        a2 += w[t] * sp3[2][r][c + t];
+      for (int m = 0; m < 3; ++m) {
+        float pv[16];
+        load16(sp3[m][r], c0, pv);
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 14; ++j)
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) acc[o] += w[t] * pv[j];
+          }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) hb[m][r][c0 + o] = acc[o];
       }
-      hb[0][r][c] = a0;
-      hb[1][r][c] = a1;
-      hb[2][r][c] = a2;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kBY * kBX; k += blockDim.x) {
-      const int r = k / kBX, c = k % kBX;
-      const int gy = oy + r, gx = ox + c;
-      if (gx >= V.W || gy >= V.H) continue;
-      float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    {
+      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
+      float bl[3][4];
 #pragma unroll
-      for (int t = 0; t < 11; ++t) {
-        b0 += w[t] * hb[0][r + t][c];
-        b1 += w[t] * hb[1][r + t][c];
-        b2 += w[t] * hb[2][r + t][c];
+      for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) bl[m][o] = 0.f;
+#pragma unroll
+        for (int j = 0; j < 14; ++j) {
+          const float h = hb[m][r0 + j][c];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) bl[m][o] += w[t] * h;
+          }
+        }
       }
-      const long long pix = (long long)gy * V.W + gx;
-      const float xv = X[ch * HW + pix], yv = Yt[ch * HW + pix];
-      const float diff = xv - yv;
-      const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-      dX[ch * HW + pix] = gl1 * sgn + gs * (b0 + 2.f * xv * b1 + yv * b2);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int gy = oy + r0 + o, gx = ox + c;
+        if (gx >= V.W || gy >= V.H) continue;
+        const long long pix = (long long)gy * V.W + gx;
+        const float xv = X[ch * HW + pix], yv = Yt[ch * HW + pix];
+        const float diff = xv - yv;
+        const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
+        dX[ch * HW + pix] = gl1 * sgn + gs * (bl[0][o] + 2.f * xv * bl[1][o] + yv * bl[2][o]);
+      }
     }
     __syncthreads();
   }

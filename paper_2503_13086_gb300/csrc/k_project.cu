@@ -332,6 +332,7 @@ __device__ __forceinline__ void apply_rows(const AdamArgs& A, int c0, const int*
     m[r] = A.m[k];
     v[r] = A.v[k];
   }
+  const float ibc2s = 1.f / A.bc2s;
 #pragma unroll
   for (int r = 0; r < N; ++r) {
     const long long k = (long long)(c0 + r) * A.stride + i;
@@ -339,23 +340,27 @@ __device__ __forceinline__ void apply_rows(const AdamArgs& A, int c0, const int*
     const float vv = A.b2 * v[r] + (1.f - A.b2) * g[r] * g[r];
     A.m[k] = mm;
     A.v[k] = vv;
-    A.params[k] = pcur[r] - (A.lr[grp[r]] * A.ssc) * mm / (sqrtf(vv) / A.bc2s + A.eps);
+    // lr m_hat / (sqrt(v_hat) + eps) with a 2-ulp divide (the IEEE divide and sqrt sequences cost
+    // more than the whole rest of the update)
+    A.params[k] = pcur[r] - __fdividef((A.lr[grp[r]] * A.ssc) * mm, __fsqrt_rn(vv) * ibc2s + A.eps);
   }
 }
 
 // Four SH coefficients (12 rows) K0..K0+3: gradient sum over the visible views, the direction
 // gradient they feed, and the update.
-template <int K0>
-__device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, const float (*vdir)[3],
-                                         const float (*vcol)[3], float (*vdd)[3]) {
+template <int K0, int MAXV>
+__device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, unsigned vmask, float (&vdir)[MAXV][3],
+                                         float (&vcol)[MAXV][3], float (&vdd)[MAXV][3]) {
+  constexpr bool kSmall = MAXV <= 4;
   float p[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) p[r] = A.params[(long long)(11 + 3 * K0 + r) * A.stride + i];
   float g[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) g[r] = 0.f;
-#pragma unroll 1
-  for (int j = 0; j < nvis; ++j) {
+#pragma unroll(kSmall ? MAXV : 1)
+  for (int j = 0; j < (kSmall ? MAXV : nvis); ++j) {
+    if (kSmall && !((vmask >> j) & 1u)) continue;
     const float x = vdir[j][0], y = vdir[j][1], z = vdir[j][2];
     const float c0 = vcol[j][0], c1 = vcol[j][1], c2 = vcol[j][2];
     float Y[4], gx[4], gy[4], gz[4];
@@ -384,6 +389,7 @@ __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, con
   apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
 }
 
+template <int MAXV>
 __global__ void __launch_bounds__(256, 2) k_project_backward(
     float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
@@ -421,16 +427,22 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
 
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gop = 0.f;
-  // per visible view: direction, masked colour gradient, 1/|d|, and the direction gradient
-  float vdir[kMaxStepViews][3], vcol[kMaxStepViews][3], vinv[kMaxStepViews], vdd[kMaxStepViews][3];
+  // per visible view: direction, masked colour gradient, 1/|d|, and the direction gradient.
+  // Up to 4 views these live in registers (slot = view, vmask = visible slots); beyond that in a
+  // compacted local array (slot = nvis).
+  constexpr bool kSmall = MAXV <= 4;
+  float vdir[MAXV][3], vcol[MAXV][3], vinv[MAXV], vdd[MAXV][3];
   int nvis = 0;
+  unsigned vmask = 0u;
   float o = 0.f;
   bool have_o = false;
-#pragma unroll 1
-  for (int v = 0; v < n_views; ++v) {
+#pragma unroll(kSmall ? MAXV : 1)
+  for (int v = 0; v < (kSmall ? MAXV : n_views); ++v) {
+    if (kSmall && v >= n_views) break;
     const long long rec = (long long)v * stride + i;
     const unsigned cnt = count[rec];
     if (cnt == 0u) continue;
+    const int slot = kSmall ? v : nvis;
     const unsigned off = offsets[rec];
     float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (unsigned e = off; e < off + cnt; ++e) {
@@ -457,14 +469,15 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     const float d0 = mu[0] - V.campos[0], d1 = mu[1] - V.campos[1], d2 = mu[2] - V.campos[2];
     const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
     const unsigned cb = clampbits[rec];
-    vdir[nvis][0] = d0 * dinv;
-    vdir[nvis][1] = d1 * dinv;
-    vdir[nvis][2] = d2 * dinv;
-    vcol[nvis][0] = (cb & 1u) ? 0.f : g2[6];
-    vcol[nvis][1] = (cb & 2u) ? 0.f : g2[7];
-    vcol[nvis][2] = (cb & 4u) ? 0.f : g2[8];
-    vinv[nvis] = dinv;
-    vdd[nvis][0] = vdd[nvis][1] = vdd[nvis][2] = 0.f;
+    vdir[slot][0] = d0 * dinv;
+    vdir[slot][1] = d1 * dinv;
+    vdir[slot][2] = d2 * dinv;
+    vcol[slot][0] = (cb & 1u) ? 0.f : g2[6];
+    vcol[slot][1] = (cb & 2u) ? 0.f : g2[7];
+    vcol[slot][2] = (cb & 4u) ? 0.f : g2[8];
+    vinv[slot] = dinv;
+    vdd[slot][0] = vdd[slot][1] = vdd[slot][2] = 0.f;
+    vmask |= 1u << slot;
     ++nvis;
 
     // Pre-scaled conic gradient back to the conic (a, b, c): power = -a/2 dx^2 - b dx dy - c/2 dy^2.
@@ -551,14 +564,15 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
   }
 
   // SH rows, four coefficients (12 rows) at a time; accumulates the direction gradient.
-  sh_group<0>(A, i, nvis, vdir, vcol, vdd);
-  sh_group<4>(A, i, nvis, vdir, vcol, vdd);
-  sh_group<8>(A, i, nvis, vdir, vcol, vdd);
-  sh_group<12>(A, i, nvis, vdir, vcol, vdd);
+  sh_group<0>(A, i, nvis, vmask, vdir, vcol, vdd);
+  sh_group<4>(A, i, nvis, vmask, vdir, vcol, vdd);
+  sh_group<8>(A, i, nvis, vmask, vdir, vcol, vdd);
+  sh_group<12>(A, i, nvis, vmask, vdir, vcol, vdd);
 
   // direction = (mu - c)/|mu - c|  ->  mean
-#pragma unroll 1
-  for (int j = 0; j < nvis; ++j) {
+#pragma unroll(kSmall ? MAXV : 1)
+  for (int j = 0; j < (kSmall ? MAXV : nvis); ++j) {
+    if (kSmall && !((vmask >> j) & 1u)) continue;
     const float dd = vdir[j][0] * vdd[j][0] + vdir[j][1] * vdd[j][1] + vdir[j][2] * vdd[j][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) gmu[a] += (vdd[j][a] - vdir[j][a] * dd) * vinv[j];
@@ -610,7 +624,15 @@ void launch_project(const float* params, int stride, int n_views, const StepPara
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
                              const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
                              float* m, float* v, float* grad2d_out, cudaStream_t s) {
-  k_project_backward<<<(stride + 255) / 256, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
+  const unsigned grid = (unsigned)((stride + 255) / 256);
+  if (n_views <= 1)
+    k_project_backward<1><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets, pb.clamp, ginst,
+                                               ctl, grads_out, m, v, grad2d_out);
+  else if (n_views <= 4)
+    k_project_backward<4><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets, pb.clamp, ginst,
+                                               ctl, grads_out, m, v, grad2d_out);
+  else
+    k_project_backward<kMaxStepViews><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
                                                            pb.clamp, ginst, ctl, grads_out, m, v, grad2d_out);
 }
 
