@@ -132,3 +132,41 @@ def batched_views(n_views=9, seed=0, f=1000.0):
         theta = base + 0.12 * (k - n_views // 2)
         cams.append(ring_camera(theta, W, H, f, jitter=0.05, rng=rng))
     return cams
+
+
+def random_walk_cameras(n, seed=0, W=1297, H=840, f=1000.0, radius=7.0, overlap=(0.6, 0.8), reverse_p=0.1):
+    """Cameras on the ring looking inward; consecutive frames overlap 60-80 % of the horizontal
+    field of view (the heading moves by (1 - overlap) x FOV), with occasional reversals."""
+    rng = np.random.default_rng(seed)
+    fov = 2.0 * np.arctan(W / (2.0 * f))
+    theta = rng.uniform(0, 2 * np.pi)
+    direction = 1.0
+    cams = []
+    for k in range(n):
+        if k > 0:
+            if rng.uniform() < reverse_p:
+                direction = -direction
+            theta += direction * (1.0 - rng.uniform(*overlap)) * fov
+        cams.append(ring_camera(theta, W, H, f, radius=radius, jitter=0.03, rng=rng))
+    return cams
+
+
+def sparse_points(gt_params, n_gt, cam, n_pts, seed=0, noise=0.01):
+    """Synthetic sparse points of one image (stand-in for an SfM front end): ground-truth means
+    visible in the camera's frustum, n_pts of them at random, plus N(0, noise) jitter; colour is
+    the ground-truth DC colour; the track id is the ground-truth index."""
+    rng = np.random.default_rng(seed)
+    mu = gt_params[0:3, :n_gt].T.astype(np.float64)
+    pc = mu @ np.asarray(cam["R"]).T + np.asarray(cam["t"])
+    z = pc[:, 2]
+    ok = z > 0.2
+    u = cam["fx"] * pc[:, 0] / np.where(ok, z, 1.0) + cam["cx"]
+    v = cam["fy"] * pc[:, 1] / np.where(ok, z, 1.0) + cam["cy"]
+    ok &= (u >= 0) & (u < cam["width"]) & (v >= 0) & (v < cam["height"])
+    ids = np.nonzero(ok)[0]
+    if len(ids) > n_pts:
+        ids = np.sort(rng.choice(ids, n_pts, replace=False))
+    xyz = (mu[ids] + rng.normal(0.0, noise, (len(ids), 3))).astype(np.float32)
+    c0 = 0.5 * np.sqrt(1.0 / np.pi)
+    rgb = np.clip(gt_params[11:14, ids].T * c0 + 0.5, 0.0, 1.0).astype(np.float32)
+    return xyz, rgb, ids.astype(np.int64)

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -14,6 +15,7 @@ namespace gs {
 
 extern thread_local std::string g_last_error;
 gs_status fail(gs_status s, const std::string& msg);
+std::mutex& alloc_capture_mutex();
 
 void init_sort_attributes();
 void init_blend_attributes();

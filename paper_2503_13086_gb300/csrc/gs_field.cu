@@ -463,11 +463,13 @@ struct Field {
         if (!ge) {
           if (graphs.size() >= 8) drop_graphs();
           cudaGraph_t graph;
+          std::unique_lock<std::mutex> lock(alloc_capture_mutex());
           cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
           if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
           // The pinned staging copy is captured: each replay re-reads sp_h / views_h.
           gs_status cs = enqueue_step(false);
           e = cudaStreamEndCapture(stream, &graph);
+          lock.unlock();
           if (cs) return cs;
           if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
           GraphEntry g;

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "gs_engine.h"
@@ -11,6 +12,13 @@ namespace gs {
 
 thread_local std::string g_last_error;
 
+// Device allocations and frees (which may synchronise the device) never run while another
+// session captures a step into a CUDA graph: both take this lock.
+std::mutex& alloc_capture_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 gs_status fail(gs_status s, const std::string& msg) {
   g_last_error = msg;
   return s;
@@ -18,6 +26,7 @@ gs_status fail(gs_status s, const std::string& msg) {
 
 gs_status DevBuf::reserve(size_t want, size_t* account) {
   if (want <= bytes) return GS_OK;
+  std::lock_guard<std::mutex> lock(alloc_capture_mutex());
   if (p) {
     cudaFree(p);
     if (account) *account -= bytes;
@@ -38,6 +47,11 @@ gs_status DevBuf::reserve(size_t want, size_t* account) {
 }
 
 void DevBuf::release(size_t* account) {
+  if (!p) {
+    bytes = 0;
+    return;
+  }
+  std::lock_guard<std::mutex> lock(alloc_capture_mutex());
   if (p) {
     cudaFree(p);
     if (account) *account -= bytes;

@@ -1,0 +1,182 @@
+"""Streaming sessions and the serving loop through the C ABI.
+
+* the GPU-driven streaming run ends within 0.1 dB PSNR of an oracle-driven run of the same reduced
+  session (same inputs, same schedule, targets rendered by the oracle);
+* the plain per-view path and the batched graph-replayed path both integrate every arrival;
+* a scene gives bitwise-identical results served alone and served concurrently with others,
+  including when the HBM budget defers one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gsinputs as gi
+import oracle
+from oracle import schedule as sch
+from helpers import ocam
+
+pytestmark = pytest.mark.gpu
+
+C0 = 0.5 * math.sqrt(1.0 / math.pi)
+
+
+def reduced_session(seed=0, n_images=5, W=64, H=48, n_gt=3000, n_pts=300):
+    gt = gi.cube_scene(n_gt, seed=seed, stride=n_gt + (-n_gt) % 32, half=0.8, logscale=(-3.0, 0.3))
+    cams = []
+    for k in range(n_images):
+        R, t = gi.look_at([0.25 * (k - n_images // 2), 0.0, -0.5], [0.0, 0.0, 3.0])
+        cams.append(gi.camera_dict(R, t, 60.0, 60.0, W / 2.0, H / 2.0, W, H))
+    targets = [oracle.render(gt, [ocam(c)], prec="f32", n=n_gt)["outs"][0]["image"].astype(np.float32) for c in cams]
+    pts = [gi.sparse_points(gt, n_gt, c, n_pts, seed=seed * 100 + k) for k, c in enumerate(cams)]
+    return gt, cams, targets, pts
+
+
+class OracleSession:
+    """The same session driven by the oracle: field update (brute force), Eq. 3-8 schedule, steps."""
+
+    def __init__(self, T_I, N_m, T_a, seed, thr, extent, lam=0.2):
+        self.T_I, self.N_m, self.T_a, self.seed, self.thr, self.extent, self.lam = T_I, N_m, T_a, seed, thr, extent, lam
+        self.p = np.zeros((59, 0), np.float32)
+        self.m = np.zeros_like(self.p)
+        self.v = np.zeros_like(self.p)
+        self.step_count = 0
+        self.sparse = np.zeros((0, 3), np.float64)
+        self.cams, self.targets, self.tracks, self.T = [], [], [], []
+
+    def add_image(self, cam, target, xyz, rgb, tracks):
+        xyz64 = xyz.astype(np.float64)
+        if len(self.sparse):
+            d = np.sqrt(((xyz64[:, None, :] - self.sparse[None]) ** 2).sum(-1)).min(1)
+            new = d > self.thr
+        else:
+            new = np.ones(len(xyz), bool)
+        allp = np.concatenate([self.sparse, xyz64])
+        base = len(self.sparse)
+        cols = []
+        for k in np.nonzero(new)[0]:
+            d2 = ((allp.astype(np.float32) - xyz[k]) ** 2).sum(1)
+            d2[base + k] = np.inf
+            mean3 = max(float(np.sort(d2)[:3].mean()), 1e-7)
+            c = np.zeros(59, np.float32)
+            c[0:3] = xyz[k]
+            c[3:6] = math.log(math.sqrt(mean3))
+            c[6] = 1.0
+            c[10] = math.log(0.1 / 0.9)
+            c[11:14] = (rgb[k] - 0.5) / C0
+            cols.append(c)
+        if cols:
+            add = np.stack(cols, 1)
+            self.p = np.concatenate([self.p, add], 1)
+            self.m = np.concatenate([self.m, np.zeros_like(add)], 1)
+            self.v = np.concatenate([self.v, np.zeros_like(add)], 1)
+        self.sparse = allp
+        self.cams.append(cam)
+        self.targets.append(target)
+        self.tracks.append(set(int(t) for t in tracks))
+        self.T.append(0)
+        return len(self.cams) - 1
+
+    def integrate(self, new):
+        M = sch.overlap_matrix(self.tracks)
+        w, _ = sch.hierarchical_weights(M, new)
+        keys, iters, slots = sch.allocate(w, self.N_m, self.T_I, list(range(len(self.cams))), new, self.seed)
+        for j in slots:
+            lr = sch.lr_image(j, M, self.T, self.T_a, 1.6e-4, 1.6e-6) * self.extent
+            n = self.p.shape[1]
+            stride = n + (-n) % 32
+            P = np.zeros((59, stride), np.float32)
+            P[:, :n] = self.p
+            L, g, _ = oracle.loss_and_grad(P, [ocam(self.cams[j])], [self.targets[j]], lam=self.lam, prec="f32", n=n)
+            self.step_count += 1
+            p, m, v = (np.ascontiguousarray(a) for a in (self.p, self.m, self.v))
+            gg = np.ascontiguousarray(g[:, :n])
+            oracle.adam(p, gg, m, v, [lr, 5e-3, 1e-3, 0.05, 2.5e-3, 2.5e-3 / 20], self.step_count, prec="f32")
+            self.p, self.m, self.v = p, m, v
+            self.T[j] += 1
+
+
+def psnr_oracle(params, cams, targets):
+    n = params.shape[1]
+    stride = n + (-n) % 32
+    P = np.zeros((59, stride), np.float32)
+    P[:, :n] = params
+    vals = []
+    for c, t in zip(cams, targets):
+        img = oracle.render(P, [ocam(c)], prec="f32", n=n)["outs"][0]["image"]
+        mse = float(np.mean((np.clip(img, 0, 1) - t) ** 2))
+        vals.append(10 * math.log10(1.0 / mse))
+    return float(np.mean(vals))
+
+
+def test_streaming_psnr_matches_oracle_driven_run():
+    from paper_2503_13086_gb300.streaming import StreamingSession
+    gt, cams, targets, pts = reduced_session()
+    cfg = dict(T_I=8, N_m=3, T_a=16, seed=5, add_dist_thresh=0.05, scene_extent=2.0, batch_views=1, use_graph=1)
+    sess = StreamingSession(**cfg)
+    ors = OracleSession(T_I=8, N_m=3, T_a=16, seed=5, thr=0.05, extent=2.0)
+    for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
+        sess.arrive(c, t, xyz, rgb, tr)
+        j = ors.add_image(c, t, xyz, rgb, tr)
+        ors.integrate(j)
+    gpu_params = sess.field.get_gaussians()
+    assert gpu_params.shape == ors.p.shape
+    p_gpu = psnr_oracle(gpu_params, cams, targets)
+    p_orc = psnr_oracle(ors.p, cams, targets)
+    assert abs(p_gpu - p_orc) <= 0.1, (p_gpu, p_orc)
+    lat = sess.latency()
+    assert lat["n"] == len(cams) and lat["p99"] >= lat["p50"] > 0
+    sess.close()
+
+
+@pytest.mark.parametrize("batch,graph", [(1, 0), (4, 1)])
+def test_plain_and_batched_paths_integrate_every_arrival(batch, graph):
+    from paper_2503_13086_gb300.streaming import StreamingSession
+    gt = gi.ring_scene(20000, seed=3, stride=20000)
+    cams = gi.random_walk_cameras(6, seed=4, W=160, H=104, f=125.0)
+    import paper_2503_13086_gb300 as gs
+    tgt_field = gs.Field(scene_extent=7.0)
+    tgt_field.set_gaussians(gt)
+    targets = [tgt_field.render(c) for c in cams]
+    tgt_field.close()
+    sess = StreamingSession(T_I=24, N_m=4, batch_views=batch, use_graph=graph, scene_extent=7.0, seed=1)
+    for k, (c, t) in enumerate(zip(cams, targets)):
+        xyz, rgb, tr = gi.sparse_points(gt, 20000, c, 1500, seed=k)
+        r = sess.arrive(c, t, xyz, rgb, tr)
+        assert r["iterations"] == 24 and r["steps"] == -(-24 // batch)
+    assert sess.field.stats()["n_images"] == 6
+    assert np.isfinite(sess.psnr(cams, targets))
+    sess.close()
+
+
+def small_scene_requests(seed, n_images=4, W=96, H=64):
+    gt = gi.ring_scene(8000, seed=seed, stride=8000)
+    cams = gi.random_walk_cameras(n_images, seed=seed + 10, W=W, H=H, f=75.0)
+    tg = [gi.uniform_target(W, H, seed * 10 + k) for k in range(n_images)]
+    reqs = []
+    for k, c in enumerate(cams):
+        xyz, rgb, tr = gi.sparse_points(gt, 8000, c, 800, seed=seed * 10 + k)
+        reqs.append((0.002 * k, dict(cam=c, target=tg[k], pts_xyz=xyz, pts_rgb=rgb, tracks=tr)))
+    return reqs
+
+
+def test_serving_results_same_alone_and_in_the_mix():
+    from paper_2503_13086_gb300.serving import Scene, Server
+    cfg = dict(T_I=12, N_m=3, batch_views=2, use_graph=1, scene_extent=7.0, seed=2)
+    scenes = {s: small_scene_requests(s) for s in (1, 2, 3)}
+    alone = {}
+    for sid, reqs in scenes.items():
+        srv = Server(hbm_budget_bytes=8 << 30, session_budget_bytes=2 << 30, max_active=1)
+        alone[sid] = srv.run([Scene(sid, reqs, cfg)], keep_fields=True)[sid]["state"]
+    srv = Server(hbm_budget_bytes=8 << 30, session_budget_bytes=2 << 30, max_active=3)
+    mix = srv.run([Scene(sid, reqs, cfg) for sid, reqs in scenes.items()], keep_fields=True)
+    for sid in scenes:
+        for a, b in zip(alone[sid], mix[sid]["state"]):
+            assert np.array_equal(a, b)
+    # a budget for two sessions defers the third, which still gives the same result
+    srv = Server(hbm_budget_bytes=4 << 30, session_budget_bytes=2 << 30, max_active=4)
+    mix2 = srv.run([Scene(sid, reqs, cfg) for sid, reqs in scenes.items()], keep_fields=True)
+    assert any(ev == "defer" for _, ev, _ in srv.log)
+    for sid in scenes:
+        for a, b in zip(alone[sid], mix2[sid]["state"]):
+            assert np.array_equal(a, b)
