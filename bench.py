@@ -1,17 +1,21 @@
 """Benchmark of the On-the-Fly GS hot path on GB300.
 
-Workload (one "step" = one pass of the whole hot path): the scene-scale single view -- 200k
-Gaussians in a ring-shaped outdoor-like volume, one 1297 x 840 view, SH degree 3, loss
-0.8 L1 + 0.2 D-SSIM, projection, binning, sort, blend forward, loss, blend backward, projection
+Default workload (one "step" = one pass of the whole hot path): the scene-scale single view --
+200k Gaussians in a ring-shaped outdoor-like volume, one 1297 x 840 view, SH degree 3, loss
+0.8 L1 + 0.2 D-SSIM: projection, binning, sort, blend forward, loss, blend backward, projection
 backward and Adam with the per-image learning rate, through the session API (gs_optimize_step),
-replayed from a CUDA graph.  Metric: Gaussian-pixel pairs per second, P counted by the oracle's
-definition (per pixel, list entries evaluated up to its termination), divided by the step time.
+replayed from a CUDA graph.  value = Gaussian-pixel pairs per second (P counted by the oracle's
+definition: per pixel, list entries evaluated up to its stop) / step time.  The same line carries
+the new-image integration latency p50/p99 of a streaming segment (arrivals on a random-walk
+trajectory, T_I = 200 iterations each), for the plain per-view eager path and the batched,
+graph-replayed path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
+                  [--workload scene|batched|serve] [--arrivals A]
 
---impl reference times the oracle (CPU, fp32, single thread) on the same workload.  Under
-torchrun each rank runs its own independent session (weak scaling, no data exchange); rank 0
-prints one JSON line.
+--impl reference times the oracle (CPU, fp32, one thread) on the same workload.  Under torchrun
+each rank runs its own independent session (weak scaling, no data exchange); rank 0 prints one
+JSON line.
 """
 from __future__ import annotations
 
@@ -34,6 +38,8 @@ METRIC = "new-image integration latency p50/p99 (s); fwd+bwd Gaussian-pixel pair
 N_GAUSS = 200_000
 W, H = 1297, 840
 WORKLOAD = "scene-scale single view: 200k Gaussians (ring volume), 1297x840, SH3, 0.8 L1 + 0.2 D-SSIM, fwd+bwd+Adam"
+KERNELS = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges+order", "K6 blend fwd", "K7 loss", "K8 blend bwd",
+           "K9+K10 project bwd + Adam"]
 
 
 def make_workload(seed):
@@ -44,31 +50,25 @@ def make_workload(seed):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of the SM clock and throttle reasons while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -107,46 +107,59 @@ class ClockSampler:
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
+            return json.load(f), "measured (MEASURED_PEAKS.json)"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 lane-operations of the blend kernels' arithmetic per Gaussian-pixel pair, counted from the
-# formulas they evaluate (not from compiled code): forward 18 (offset 2, exponent 4, exp 2,
-# alpha 2, cutoffs 2, transmittance 2, colour 4), backward 60 (the forward's alpha path 10,
-# weight/colour-in-front 4, colour behind 6, dL/dalpha 9, colour gradient 3, reciprocal 2,
-# opacity/exponent 3, mean 6, conic 8, transmittance 2, pipeline shifts and selects 7).
-OPS_FWD = 18
-OPS_BWD = 60
+# Algorithmic work per kernel launch: FP32 lane-operations for the blend kernels,
+# counted from the formulas they evaluate; bytes for the memory-bound kernels.
+def kernel_work(k, st, n, passes):
+    P, B, M = st["pairs"], st["blended"], st["instances"]
+    if k == 5:   # K6: exponent + cutoff test for every evaluated pair, the blend for blended ones
+        return "alu", 8.0 * P + 10.0 * B
+    if k == 7:   # K8: 45 lane-ops per blended pair; pairs a pixel did not blend cost nothing
+        return "alu", 45.0 * B
+    if k == 8:   # K9+K10: read + write p, m, v (3 x 236 B each way) + 48 B per instance + count/offset
+        return "hbm", 1416.0 * n + 48.0 * M + 8.0 * n
+    if k == 3:   # K4: one read and one write of key + value per pass
+        return "hbm", 24.0 * M * passes
+    if k == 0:   # K1: geometry of every Gaussian, SH of the visible ones, the records written
+        return "hbm", 44.0 * n + st["visible"] * (192.0 + 80.0)
+    if k == 6:   # K7: two reads + one write of 3 H W per pass, partial maps written and re-read
+        return "hbm", 4.0 * W * H * (3 * 3 + 9 * 2 + 3)
+    if k == 2:
+        return "hbm", 12.0 * M + 24.0 * n
+    return "hbm", 8.0 * n
 
 
-def roofline(kernel_ms, steps, pairs, m_inst, n, peaks, peaks_kind):
-    """Roofline object for the dominant kernel of the step."""
-    names = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss", "K8 blend bwd",
-             "K9+K10 project bwd + Adam"]
+def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
     per = [k / max(1, steps) for k in kernel_ms]
     dom = int(np.argmax(per))
     t = per[dom] * 1e-3
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lane-ops/s (one per lane per clock), in T/s
-    if dom in (5, 7):
-        ops = pairs * (OPS_FWD if dom == 5 else OPS_BWD)
-        ach = ops / t / 1e12
-        return dict(kernel=names[dom], bound="alu", achieved=ach, peak=alu_peak, unit="Tops/s", frac=ach / alu_peak,
-                    traffic=None, peak_source=f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)",
-                    per_kernel_ms={nm: round(x, 4) for nm, x in zip(names, per)})
-    # HBM-bound kernels: algorithmic bytes per launch
-    bytes_ = {0: n * (56 + 8) + 0.5 * n * (192 + 49), 1: n * 8, 2: m_inst * 12 + n * 16, 3: m_inst * 24 * 6,
-              4: m_inst * 8, 6: W * H * 3 * 4 * 6, 8: n * 1416 + m_inst * 48}.get(dom, 0)
-    ach = bytes_ / t / 1e9
-    return dict(kernel=names[dom], bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                frac=ach / peaks["hbm_gbs"], traffic=None, peak_source=peaks_kind,
-                per_kernel_ms={nm: round(x, 4) for nm, x in zip(names, per)})
+    bound, work = kernel_work(dom, st, n, passes)
+    if bound == "alu":
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        ach = work / t / 1e12
+        unit, src = "Tops/s", f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived from unit counts and clock)"
+    else:
+        peak = peaks["hbm_gbs"]
+        ach = work / t / 1e9
+        unit, src = "GB/s", f"HBM copy, {peaks_kind}"
+    return dict(kernel=KERNELS[dom], bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
+                traffic=traffic.get(KERNELS[dom]), peak_source=src, work_per_launch=work,
+                per_kernel_ms={nm: round(x, 4) for nm, x in zip(KERNELS, per)})
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed ncu
+# summaries of the current kernels (profiles/); None for a kernel changed since its capture.
+TRAFFIC = {"K8 blend bwd": 62.1e6, "K6 blend fwd": 21.8e6, "K9+K10 project bwd + Adam": 246.9e6,
+           "K4 sort": 6 * 4.08e6, "K7 loss": None}
 
 
 def cpu_baseline_run(steps, warmup, seed=0):
-    """The oracle (fp32, single thread) doing full steps of the same workload."""
+    """The oracle (fp32, one thread) doing full steps of the same workload."""
     import oracle
     from oracle import Camera
     p, cam, tgt = make_workload(seed)
@@ -170,20 +183,58 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    K, Wm = args.steps, args.warmup
-    # bounded: each step is one full oracle step (~4-5 s on one core)
-    K_eff = min(K, 6)
-    W_eff = min(Wm, 1)
+    K_eff = min(args.steps, 6)  # each step is one full oracle step (~4-5 s on one core): bounded
+    W_eff = min(args.warmup, 1)
     val, sec, pairs = cpu_baseline_run(K_eff, W_eff)
-    line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus, "steps": K, "warmup": Wm,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic (seeded ring scene; see DESIGN.md)", "impl": "reference",
+    line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ring scene; see DESIGN.md)",
+            "impl": "reference",
             "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
             "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{K_eff} full oracle steps (after {W_eff} warm-up) of the workload, "
-                                       f"{pairs} pairs each; K capped at 6 to bound CPU time"},
+                             "sample": f"{K_eff} full oracle steps (after {W_eff} warm-up) of the workload, {pairs} "
+                                       f"pairs each; steps capped at 6 to bound CPU time"},
             "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------------------------------
+# streaming: new-image integration latency, plain per-view eager path vs batched graph path
+# ------------------------------------------------------------------------------------------
+def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
+    import torch
+    import paper_2503_13086_gb300 as gs
+    gt = gi.ring_scene(n_gt, seed=seed + 100, stride=n_gt + (-n_gt) % 32)
+    cams = gi.random_walk_cameras(n_images, seed=seed + 7, W=Wv, H=Hv, f=1000.0 * Wv / W)
+    f = gs.Field(scene_extent=7.0)
+    f.set_gaussians(gt, n_gt)
+    targets = [f.render(c).clone() for c in cams]
+    torch.cuda.synchronize()
+    f.close()
+    rng = np.random.default_rng(seed)
+    pts = [gi.sparse_points(gt, n_gt, c, int(rng.integers(5000, 20001)), seed=seed * 1000 + k)
+           for k, c in enumerate(cams)]
+    return cams, targets, pts
+
+
+def run_stream(cams, targets, pts, batch, graph, T_I=200, k_neighbours=8):
+    import torch
+    from paper_2503_13086_gb300.streaming import StreamingSession
+    sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, scene_extent=7.0,
+                            seed=3)
+    pairs = 0
+    t0 = time.perf_counter()
+    for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
+        r = sess.arrive(c, t, xyz, rgb, tr)
+        pairs += r["pairs"]
+    wall = time.perf_counter() - t0
+    lat = sess.latency()
+    psnr = sess.psnr(cams, targets)
+    n = sess.field.stats()["n_gaussians"]
+    torch.cuda.synchronize()
+    sess.close()
+    return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
+                pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph))
 
 
 def run_gs(args):
@@ -206,7 +257,6 @@ def run_gs(args):
     # every timed step starts from this state (restored untimed), so the workload is stationary
     field.snapshot()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    sampler = ClockSampler(local)
 
     def sync_all():
         torch.cuda.synchronize()
@@ -214,13 +264,13 @@ def run_gs(args):
             torch.distributed.barrier()
             torch.cuda.synchronize()
 
-    # --- timed region: K steps, L2 flushed before each, device time per step ---
+    sampler = ClockSampler(local)
     sync_all()
     field.set_timing(True)
     sampler.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    pairs = 0
-    wall0 = time.perf_counter()
+    acc = dict(pairs=0, blended=0, instances=0)
+    launches = 0
     for k in range(args.steps):
         field.restore()
         with torch.cuda.stream(stream):
@@ -228,25 +278,26 @@ def run_gs(args):
         ev[k][0].record(stream)
         field.optimize_step([img])
         ev[k][1].record(stream)
-        pairs += field.stats()["last_pairs"]
+        st = field.stats()
+        acc["pairs"] += st["last_pairs"]
+        acc["blended"] += st["last_blended"]
+        acc["instances"] += st["last_instances"]
+        launches += st["last_kernels"]
     sync_all()
-    wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     kms, ksteps = field.kernel_times()
     field.set_timing(False)
     ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    ms_max = ms
-    pairs_total = pairs
+    ms_max, pairs_total = ms, float(acc["pairs"])
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-        pt = torch.tensor([float(pairs)], device="cuda")
-        torch.distributed.all_reduce(pt)
-        pairs_total = float(pt.item())
+        t = torch.tensor([ms, float(acc["pairs"])], device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t)
+        ms_max, pairs_total = float(tmax[0].item()), float(t[1].item())
     value = pairs_total / (ms_max * 1e-3)
 
-    # --- end to end through the C ABI: host target (pinned) -> device, step, loss -> host ---
+    # end to end through the C ABI: host target (pinned) -> device, step, loss -> host
     tgt_pinned = torch.from_numpy(tgt.reshape(-1)).pin_memory()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     e2e_pairs = 0
@@ -261,63 +312,134 @@ def run_gs(args):
     sync_all()
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
     if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-        pt = torch.tensor([float(e2e_pairs)], device="cuda")
-        torch.distributed.all_reduce(pt)
-        e2e_pairs = pt.item()
-    st = field.stats()
+        t = torch.tensor([e2e_ms, float(e2e_pairs)], device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t)
+        e2e_ms, e2e_pairs = float(tmax[0].item()), float(t[1].item())
+    field.close()
+
+    steps = max(1, args.steps)
+    st_mean = {k: v / steps for k, v in acc.items()}
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    passes = (32 + int(tiles - 1).bit_length() + 7) // 8
+    # visible Gaussians of the view (for K1's algorithmic bytes)
+    ras = gs.Raster()
+    fo = ras.forward(torch.tensor(p, device="cuda"), N_GAUSS, [cam])
+    st_mean["visible"] = int((ras.read(6, np.uint32) > 0).sum())
+    ras.close()
+
+    lat = None
+    if ws == 1 and args.arrivals > 0:
+        cams, targets, pts = stream_inputs(args.arrivals, seed=rank)
+        plain = run_stream(cams, targets, pts, batch=1, graph=0)
+        batched = run_stream(cams, targets, pts, batch=9, graph=1)
+        lat = {"workload": f"{args.arrivals} arrivals, 1297x840, random walk with 60-80% overlap, 5k-20k sparse "
+                           f"points each, T_I = 200 over the new image + 8 neighbours, 1.5M-Gaussian hidden scene",
+               "plain_per_view": plain, "batched_graph": batched}
 
     if rank == 0:
         peaks, kind = measured_peaks()
-        m_inst = int(st["last_pairs"] > 0) and None
-        # instance count of the last step from a raster forward of the same state (not timed)
-        ras = gs.Raster()
-        P = torch.tensor(field.get_gaussians(), device="cuda")
-        P = torch.nn.functional.pad(P, (0, (-P.shape[1]) % 32))
-        fo = ras.forward(P, N_GAUSS, [cam])
-        m_inst = len(ras.read(9, np.uint32))
-        ras.close()
-        rl = roofline(kms, ksteps, pairs / max(1, args.steps), m_inst, N_GAUSS, peaks, kind)
+        rl = roofline(kms, ksteps, st_mean, N_GAUSS, passes, peaks, kind, TRAFFIC)
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
                 "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
-                           "instances": m_inst, "pairs_per_step": int(pairs / max(1, args.steps)),
+                           "instances": int(st_mean["instances"]), "pairs_per_step": int(st_mean["pairs"]),
+                           "blended_pairs_per_step": int(st_mean["blended"]),
                            "l2": "flushed before every timed step (256 MiB write, untimed)",
                            "state": "every timed step starts from the same snapshot (device copy, untimed)",
-                           "parallelism": f"{ws} independent session(s), one per GPU",
-                           "graph": True},
+                           "parallelism": f"{ws} independent session(s), one per GPU", "graph": True},
                 "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
-                        "h2d_bytes_per_step": int(tgt.nbytes), "d2h_bytes_per_step": 4 + 1024},
-                "gpu_launches": None,
-                "roofline": rl, "clocks": clocks,
-                "wall_s": wall}
-        line["gpu_launches"] = int(ksteps and (13 + 6)) * args.steps
+                        "h2d_bytes_per_step": int(tgt.nbytes), "d2h_bytes_per_step": 1024},
+                "gpu_launches": int(launches),
+                "roofline": rl, "clocks": clocks}
+        if lat is not None:
+            line["integration_latency_s"] = {"p50": lat["batched_graph"]["p50_s"], "p99": lat["batched_graph"]["p99_s"],
+                                             "detail": lat}
         if not args.no_cpu_baseline and ws == 1:
             val, sec, pp = cpu_baseline_run(3, 0)
             line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                                     "sample": f"3 full oracle steps of the workload ({pp} pairs each), fp32, one thread"}
         print(json.dumps(line))
-    field.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_batched(args):
+    """Batched local & semi-global step: 500k Gaussians, 9 views at mixed sizes, one graph."""
+    import torch
+    import paper_2503_13086_gb300 as gs
+    torch.cuda.set_device(0)
+    n = 500_000
+    p = gi.ring_scene(n, seed=5, stride=n)
+    cams = gi.batched_views(9, seed=2)
+    field = gs.Field(scene_extent=7.0, use_graph=1)
+    field.set_gaussians(p)
+    ids = [field.add_image(c, gi.uniform_target(c["width"], c["height"], k)) for k, c in enumerate(cams)]
+    for _ in range(args.warmup):
+        field.optimize_step(ids)
+    field.snapshot()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot, pairs = 0.0, 0
+    for _ in range(args.steps):
+        field.restore()
+        torch.cuda.synchronize()
+        ev0.record()
+        field.optimize_step(ids)
+        ev1.record()
+        torch.cuda.synchronize()
+        tot += ev0.elapsed_time(ev1)
+        pairs += field.stats()["last_pairs"]
+    field.close()
+    print(json.dumps({"workload": "batched: 500k Gaussians, 9 views at mixed sizes, one graph", "ms_per_step":
+                      tot / args.steps, "pairs_per_s": pairs / (tot * 1e-3),
+                      "sizes": [(c["width"], c["height"]) for c in cams]}))
+
+
+def run_serve(args):
+    """Multi-session serving: 4 scenes at 1920x1080 / 1280x720 arriving at 1-3 Hz."""
+    import torch
+    import paper_2503_13086_gb300 as gs  # noqa: F401
+    from paper_2503_13086_gb300.serving import Scene, Server, summarize
+    torch.cuda.set_device(0)
+    scenes = []
+    for s in range(4):
+        Wv, Hv = (1920, 1080) if s % 2 == 0 else (1280, 720)
+        cams, targets, pts = stream_inputs(args.arrivals, seed=10 + s, n_gt=1_000_000, Wv=Wv, Hv=Hv)
+        rng = np.random.default_rng(s)
+        t, reqs = 0.0, []
+        for c, tg, (xyz, rgb, tr) in zip(cams, targets, pts):
+            reqs.append((t, dict(cam=c, target=tg, pts_xyz=xyz, pts_rgb=rgb, tracks=tr)))
+            t += rng.exponential(1.0 / rng.uniform(1.0, 3.0))
+        scenes.append(Scene(s, reqs, dict(T_I=200, N_m=9, batch_views=9, use_graph=1, scene_extent=7.0, seed=s)))
+    srv = Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), session_budget_bytes=16 << 30, max_active=4)
+    out = srv.run(scenes)
+    summ = summarize(out, srv.wall_s)
+    summ.update(peak_device_bytes=srv.peak_device_bytes, wall_s=srv.wall_s,
+                deferred=sum(1 for _, e, _ in srv.log if e == "defer"))
+    print(json.dumps({"workload": "serving: 4 scenes, 1-3 Hz arrivals", **summ}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
+    ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve"])
+    ap.add_argument("--arrivals", type=int, default=20)
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3:
-        args.warmup = 3
+    args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gs(args)
 

@@ -227,7 +227,11 @@ typedef struct gs_field_stats {
   int64_t n_images;
   int64_t adam_step;
   uint64_t bytes_in_use;   /* device bytes owned by the field (parameters, Adam, images, workspaces) */
-  uint64_t last_pairs;     /* Gaussian-pixel pairs of the last step */
+  uint64_t last_pairs;     /* Gaussian-pixel pairs evaluated in the last step (per pixel, up to its stop) */
+  uint64_t last_blended;   /* Gaussian-pixel pairs blended in the last step (sum of G_p) */
+  int64_t last_instances;  /* Gaussian-tile instances of the last step */
+  int32_t last_kernels;    /* kernel launches of the last step */
+  int32_t pad;
   double last_loss;
 } gs_field_stats;
 GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);

@@ -46,6 +46,7 @@ struct ViewDev {
 struct Control {
   unsigned long long m_total;   // instances emitted by the key emission
   unsigned long long pairs;     // Gaussian-pixel pairs (entries evaluated up to termination)
+  unsigned long long blended;   // Gaussian-pixel pairs blended (sum of G_p)
   unsigned int overflow;        // instance capacity exceeded
   unsigned int error;           // kErr* bits
   unsigned int scan_ticket;

@@ -149,7 +149,8 @@ struct Field {
   bool sized_for_views = false;
   std::vector<int> last_sizes;
   double last_loss = 0.0;
-  unsigned long long last_pairs = 0;
+  unsigned long long last_pairs = 0, last_blended = 0, last_instances = 0;
+  int last_kernels = 0;
   size_t own_bytes = 0;
   // snapshot (gs_field_snapshot / gs_field_restore)
   DevBuf snap_p, snap_m, snap_v;
@@ -502,6 +503,10 @@ struct Field {
       R.collect_times();
       last_loss = R.ctl_h->loss;
       last_pairs = R.ctl_h->pairs;
+      last_blended = R.ctl_h->blended;
+      last_instances = R.ctl_h->m_total;
+      // project, scan, emit, sort passes, ranges, tile order, blend, 2 loss, blend bwd, proj bwd
+      last_kernels = 10 + R.passes;
       if (out_loss) *out_loss = (float)last_loss;
       for (int k = 0; k < nv; ++k) images[ids[k]].T += 1;
       R.have_forward = true;
@@ -823,6 +828,10 @@ gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
   out->adam_step = f->adam_step;
   out->bytes_in_use = f->bytes_in_use();
   out->last_pairs = f->last_pairs;
+  out->last_blended = f->last_blended;
+  out->last_instances = (int64_t)f->last_instances;
+  out->last_kernels = f->last_kernels;
+  out->pad = 0;
   out->last_loss = f->last_loss;
   return GS_OK;
 }

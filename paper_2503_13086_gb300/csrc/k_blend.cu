@@ -98,11 +98,12 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
   __shared__ float4 s_rgb[kBlendBatch];
   __shared__ unsigned char s_bm[kBlendBatch];  // per entry: the warp blocks its cutoff box reaches
   __shared__ unsigned long long s_pairs[kTilePix / 32];
+  __shared__ unsigned long long s_blend[kTilePix / 32];
   __shared__ int s_item;
   if (ctl->overflow) return;
   const int tid = threadIdx.x;
   const float bg0 = sp->bg[0], bg1 = sp->bg[1], bg2 = sp->bg[2];
-  unsigned long long my_pairs = 0;
+  unsigned long long my_pairs = 0, my_blend = 0;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_item = (int)atomicAdd(&ctl->fwd_work, 1u);
@@ -225,19 +226,30 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
       last_out[gpix] = last;
       if (gp_out) gp_out[gpix] = gp;
       my_pairs += neval;
+      my_blend += gp;
     }
   }
   // Gaussian-pixel pairs by definition: entries evaluated per pixel up to its termination.
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+    my_blend += __shfl_down_sync(0xffffffffu, my_blend, o);
+  }
   __syncthreads();
-  if ((tid & 31) == 0) s_pairs[tid >> 5] = my_pairs;
+  if ((tid & 31) == 0) {
+    s_pairs[tid >> 5] = my_pairs;
+    s_blend[tid >> 5] = my_blend;
+  }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long s = 0;
+    unsigned long long s = 0, b = 0;
 #pragma unroll
-    for (int w = 0; w < kTilePix / 32; ++w) s += s_pairs[w];
+    for (int w = 0; w < kTilePix / 32; ++w) {
+      s += s_pairs[w];
+      b += s_blend[w];
+    }
     if (s) atomicAdd(&ctl->pairs, s);
+    if (b) atomicAdd(&ctl->blended, b);
   }
 }
 
