@@ -217,11 +217,11 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
     return cams, targets, pts
 
 
-def run_stream(cams, targets, pts, batch, graph, T_I=200, k_neighbours=8):
+def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
-    sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, scene_extent=7.0,
-                            seed=3)
+    sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
+                            scene_extent=7.0, seed=3)
     pairs = 0
     t0 = time.perf_counter()
     for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
@@ -234,7 +234,7 @@ def run_stream(cams, targets, pts, batch, graph, T_I=200, k_neighbours=8):
     torch.cuda.synchronize()
     sess.close()
     return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
-                pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph))
+                pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn)
 
 
 def run_gs(args):
@@ -332,11 +332,12 @@ def run_gs(args):
     lat = None
     if ws == 1 and args.arrivals > 0:
         cams, targets, pts = stream_inputs(args.arrivals, seed=rank)
-        plain = run_stream(cams, targets, pts, batch=1, graph=0)
-        batched = run_stream(cams, targets, pts, batch=9, graph=1)
+        plain = run_stream(cams, targets, pts, batch=1, graph=0, asyn=1)
+        graphed = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16)
+        batched = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16)
         lat = {"workload": f"{args.arrivals} arrivals, 1297x840, random walk with 60-80% overlap, 5k-20k sparse "
                            f"points each, T_I = 200 over the new image + 8 neighbours, 1.5M-Gaussian hidden scene",
-               "plain_per_view": plain, "batched_graph": batched}
+               "plain_per_view": plain, "graph_async_per_view": graphed, "batched_graph": batched}
 
     if rank == 0:
         peaks, kind = measured_peaks()
@@ -356,8 +357,10 @@ def run_gs(args):
                 "gpu_launches": int(launches),
                 "roofline": rl, "clocks": clocks}
         if lat is not None:
-            line["integration_latency_s"] = {"p50": lat["batched_graph"]["p50_s"], "p99": lat["batched_graph"]["p99_s"],
-                                             "detail": lat}
+            # headline: the per-view path (the paper's one-image-per-iteration semantics, so the same
+            # PSNR as the plain path) replayed from graphs with 16 steps between host syncs
+            line["integration_latency_s"] = {"p50": lat["graph_async_per_view"]["p50_s"],
+                                             "p99": lat["graph_async_per_view"]["p99_s"], "detail": lat}
         if not args.no_cpu_baseline and ws == 1:
             val, sec, pp = cpu_baseline_run(3, 0)
             line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",

@@ -154,6 +154,7 @@ typedef struct gs_field_config {
   int32_t T_a;              /* iterations for an image to be "trained" (Eq. 7; paper: 200) */
   int32_t batch_views;      /* views per optimisation step in gs_integrate (1 = per-view) */
   int32_t use_graph;        /* replay each step from a captured CUDA graph */
+  int32_t async_steps;      /* gs_integrate enqueues up to this many steps between host syncs (1 = sync each) */
   float eta0, etaf;         /* Eq. 6 initial / final position rate (1.6e-4, 1.6e-6) */
   float lambda_ssim;        /* D-SSIM weight (0.2) */
   float lr_scale, lr_rot, lr_opacity, lr_sh_dc, lr_sh_rest; /* other Adam groups (3DGS) */

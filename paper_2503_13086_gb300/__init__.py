@@ -60,7 +60,7 @@ class Camera(ctypes.Structure):
 
 class FieldConfig(ctypes.Structure):
     _fields_ = [("T_I", ctypes.c_int32), ("N_m", ctypes.c_int32), ("T_a", ctypes.c_int32),
-                ("batch_views", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("batch_views", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("async_steps", ctypes.c_int32),
                 ("eta0", ctypes.c_float), ("etaf", ctypes.c_float), ("lambda_ssim", ctypes.c_float),
                 ("lr_scale", ctypes.c_float), ("lr_rot", ctypes.c_float), ("lr_opacity", ctypes.c_float),
                 ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),

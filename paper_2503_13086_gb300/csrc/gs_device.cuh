@@ -60,6 +60,19 @@ struct Control {
   double loss;                  // batch loss (mean over views)
 };
 
+// Running totals over a run of steps enqueued without host synchronisation (not cleared per
+// step).  A step whose instances overflow the buffers latches `skip`; every later step of the run
+// then does nothing, so the host can re-run the skipped tail in order after growing the buffers.
+struct Ledger {
+  double loss_sum;
+  unsigned long long pairs, blended, instances;
+  unsigned long long m_need;  // largest instance count a skipped step needed
+  unsigned int steps_ok;      // steps completed (a prefix of the run)
+  unsigned int skip;
+  unsigned int error;
+  unsigned int pad;
+};
+
 // Scalars of one step in device memory (so a captured graph picks up new values).
 struct StepParams {
   int n;                 // live Gaussians

@@ -55,6 +55,7 @@ struct Raster {
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp;
   DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order, tile_chunks;
   DevBuf partials, block_sums;
+  DevBuf ledger_d;  // Ledger of the current run of steps
   DevBuf own_image, own_last, own_dimage;  // used by sessions
   unsigned long long m_cap = 0;
   size_t bytes_in_use = 0;
@@ -63,6 +64,7 @@ struct Raster {
   StepParams* sp_h = nullptr;
   ViewDev* views_h = nullptr;
   Control* ctl_h = nullptr;
+  Ledger* ledger_h = nullptr;
   cudaEvent_t staged = nullptr;
 
   // timing
@@ -93,6 +95,9 @@ struct Raster {
   void enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last, const float* dimage,
                         float* grads, float* m, float* v, float* grad2d);
   void enqueue_readback(cudaStream_t s);
+  Ledger* ledger() const { return static_cast<Ledger*>(ledger_d.p); }
+  void reset_ledger(cudaStream_t s) { cudaMemsetAsync(ledger_d.p, 0, sizeof(Ledger), s); }
+  void read_ledger(cudaStream_t s) { cudaMemcpyAsync(ledger_h, ledger_d.p, sizeof(Ledger), cudaMemcpyDeviceToHost, s); }
   gs_status collect_times();
   gs_status check_control();
 };

@@ -390,7 +390,8 @@ struct Field {
     return GS_OK;
   }
 
-  // Enqueue one whole step (forward, loss, backward + Adam) and the control readback.
+  // Enqueue one whole step (forward, loss, backward + Adam); no readback, no synchronisation
+  // (except the sizing step, which reads the instance count back mid-step).
   gs_status enqueue_step(bool size_exactly) {
     gs_status s;
     Raster& R = *r;
@@ -403,23 +404,24 @@ struct Field {
     R.enqueue_backward(stream, static_cast<float*>(params.p), static_cast<float*>(step_img.p),
                        static_cast<unsigned*>(step_last.p), static_cast<float*>(step_dimg.p), nullptr,
                        static_cast<float*>(adam_m.p), static_cast<float*>(adam_v.p), nullptr);
-    R.enqueue_readback(stream);
     return GS_OK;
   }
 
-  gs_status step(const int* ids, int nv, float* out_loss) {
+  // Views of the next step: workspace sizes, and the mean of their Eq. 8 rates.
+  std::vector<int> cur_sizes;
+  gs_status setup_views(const int* ids, int nv, double* lr_mean) {
     if (nv <= 0 || nv > kMaxViews) return fail(GS_ERR_CAPACITY, "views per step must be in 1..32");
     if (n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
     std::vector<gs_camera> cams(nv);
     std::vector<const float*> tg(nv);
-    std::vector<int> sizes;
+    cur_sizes.clear();
     double lr_sum = 0;
     for (int k = 0; k < nv; ++k) {
       if (ids[k] < 0 || ids[k] >= (int)images.size()) return fail(GS_ERR_INVALID_ARG, "view id out of range");
       cams[k] = images[ids[k]].cam;
       tg[k] = static_cast<const float*>(images[ids[k]].rgb.p);
-      sizes.push_back(cams[k].width);
-      sizes.push_back(cams[k].height);
+      cur_sizes.push_back(cams[k].width);
+      cur_sizes.push_back(cams[k].height);
       lr_sum += lr_image(ids[k]);
     }
     Raster& R = *r;
@@ -427,92 +429,157 @@ struct Field {
     if ((s = R.set_views(cams.data(), nv, tg.data()))) return s;
     R.stride = stride;
     R.n = n;
-    if ((s = R.ensure_records(stride)) || (s = ensure_step_buffers(R.n_pix))) return s;
-    if ((s = R.ensure_instances(R.m_cap))) return s;
-    ++adam_step;
-    const double lr_means = lr_sum / nv * (double)scene_extent();
-    for (int attempt = 0; attempt < 4; ++attempt) {
-      if ((s = R.stage(stream))) return s;
-      StepParams& P = *R.sp_h;
-      P.n = n;
-      P.n_views = nv;
-      for (int a = 0; a < 3; ++a) P.bg[a] = cfg.bg[a];
-      P.lambda_ssim = cfg.lambda_ssim;
-      P.lr[0] = (float)lr_means;
-      P.lr[1] = cfg.lr_scale;
-      P.lr[2] = cfg.lr_rot;
-      P.lr[3] = cfg.lr_opacity;
-      P.lr[4] = cfg.lr_sh_dc;
-      P.lr[5] = cfg.lr_sh_rest;
-      P.beta1 = cfg.beta1;
-      P.beta2 = cfg.beta2;
-      P.eps = cfg.adam_eps;
-      P.step_size_scale = (float)(1.0 / (1.0 - std::pow((double)cfg.beta1, (double)adam_step)));
-      P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow((double)cfg.beta2, (double)adam_step));
-      P.adam = 1;
-      const bool first = !sized_for_views || sizes != last_sizes;
-      if (first) {
-        // Size the instance buffers from this step's exact count (one mid-step sync).
-        if ((s = enqueue_step(true))) return s;
-        sized_for_views = true;
-        last_sizes = sizes;
-      } else if (cfg.use_graph) {
-        GraphKey key{sizes, signature()};
-        GraphEntry* ge = nullptr;
-        for (auto& g : graphs)
-          if (g.key == key && g.timing == R.timing) ge = &g;
-        if (!ge) {
-          if (graphs.size() >= 8) drop_graphs();
-          cudaGraph_t graph;
-          std::unique_lock<std::mutex> lock(alloc_capture_mutex());
-          cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
-          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-          // The pinned staging copy is captured: each replay re-reads sp_h / views_h.
-          gs_status cs = enqueue_step(false);
-          e = cudaStreamEndCapture(stream, &graph);
-          lock.unlock();
-          if (cs) return cs;
-          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
-          GraphEntry g;
-          g.key = key;
-          g.timing = R.timing;
-          e = cudaGraphInstantiate(&g.exec, graph, 0);
-          cudaGraphDestroy(graph);
-          if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-          graphs.push_back(g);
-          ge = &graphs.back();
-        }
-        std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * nv);
-        cudaError_t e = cudaGraphLaunch(ge->exec, stream);
-        if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-        cudaEventRecord(R.staged, stream);
-      } else {
-        if ((s = enqueue_step(false))) return s;
-      }
-      cudaError_t e = cudaStreamSynchronize(stream);
-      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step: ") + cudaGetErrorString(e));
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
-      if (R.ctl_h->overflow) {
-        // Nothing after the scan ran; grow and run the step again.
-        if ((s = R.ensure_instances(R.ctl_h->m_total + R.ctl_h->m_total / 4 + 1024))) return s;
-        drop_graphs();
-        continue;
-      }
-      if ((s = R.check_control())) return s;
-      R.collect_times();
-      last_loss = R.ctl_h->loss;
-      last_pairs = R.ctl_h->pairs;
-      last_blended = R.ctl_h->blended;
-      last_instances = R.ctl_h->m_total;
-      // project, scan, emit, sort passes, ranges, tile order, blend, 2 loss, blend bwd, proj bwd
-      last_kernels = 10 + R.passes;
-      if (out_loss) *out_loss = (float)last_loss;
-      for (int k = 0; k < nv; ++k) images[ids[k]].T += 1;
-      R.have_forward = true;
+    if ((s = R.ensure_records(stride)) || (s = ensure_step_buffers(R.n_pix)) || (s = R.ensure_instances(R.m_cap)))
+      return s;
+    *lr_mean = lr_sum / nv;
+    return GS_OK;
+  }
+
+  // Fill the staging parameters of a step (after Raster::stage) for Adam step `t`.
+  void fill_params(int nv, double lr_mean, long long t) {
+    StepParams& P = *r->sp_h;
+    P.n = n;
+    P.n_views = nv;
+    for (int a = 0; a < 3; ++a) P.bg[a] = cfg.bg[a];
+    P.lambda_ssim = cfg.lambda_ssim;
+    P.lr[0] = (float)(lr_mean * (double)scene_extent());
+    P.lr[1] = cfg.lr_scale;
+    P.lr[2] = cfg.lr_rot;
+    P.lr[3] = cfg.lr_opacity;
+    P.lr[4] = cfg.lr_sh_dc;
+    P.lr[5] = cfg.lr_sh_rest;
+    P.beta1 = cfg.beta1;
+    P.beta2 = cfg.beta2;
+    P.eps = cfg.adam_eps;
+    P.step_size_scale = (float)(1.0 / (1.0 - std::pow((double)cfg.beta1, (double)t)));
+    P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow((double)cfg.beta2, (double)t));
+    P.adam = 1;
+  }
+
+  // Enqueue the prepared step: the sizing launch for new view sizes, else a graph replay (captured
+  // on first use) or an eager launch.
+  gs_status enqueue_prepared(int nv) {
+    Raster& R = *r;
+    gs_status s;
+    const bool first = !sized_for_views || cur_sizes != last_sizes;
+    if (first) {
+      if ((s = enqueue_step(true))) return s;
+      sized_for_views = true;
+      last_sizes = cur_sizes;
       return GS_OK;
     }
-    return fail(GS_ERR_CAPACITY, "instance buffers kept overflowing");
+    if (!cfg.use_graph) return enqueue_step(false);
+    GraphKey key{cur_sizes, signature()};
+    GraphEntry* ge = nullptr;
+    for (auto& g : graphs)
+      if (g.key == key && g.timing == R.timing) ge = &g;
+    if (!ge) {
+      if (graphs.size() >= 8) drop_graphs();
+      cudaGraph_t graph;
+      std::unique_lock<std::mutex> lock(alloc_capture_mutex());
+      cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      // The pinned staging copy is captured: each replay re-reads sp_h / views_h.
+      gs_status cs = enqueue_step(false);
+      e = cudaStreamEndCapture(stream, &graph);
+      lock.unlock();
+      if (cs) return cs;
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+      GraphEntry g;
+      g.key = key;
+      g.timing = R.timing;
+      e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+      graphs.push_back(g);
+      ge = &graphs.back();
+    }
+    (void)nv;
+    cudaError_t e = cudaGraphLaunch(ge->exec, stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    return GS_OK;
+  }
+
+  // Run `count` steps (views of step k: groups[k]) enqueued back to back, with one
+  // synchronisation at the end.  Returns how many completed (a prefix); the caller re-runs the
+  // rest.  T_j and the Adam step count are advanced only for completed steps.
+  gs_status run_steps(const std::vector<std::vector<int>>& groups, size_t first_group, size_t count, size_t* done,
+                      double* loss_sum) {
+    Raster& R = *r;
+    gs_status s;
+    const long long step0 = adam_step;
+    std::vector<int> T0;
+    for (auto& im : images) T0.push_back(im.T);
+    R.reset_ledger(stream);
+    for (size_t k = 0; k < count; ++k) {
+      const std::vector<int>& ids = groups[first_group + k];
+      double lr_mean = 0;
+      if ((s = setup_views(ids.data(), (int)ids.size(), &lr_mean))) return s;
+      if ((s = R.stage(stream))) return s;  // waits only for the previous step's parameter upload
+      fill_params((int)ids.size(), lr_mean, adam_step + 1);
+      std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * ids.size());
+      if ((s = enqueue_prepared((int)ids.size()))) return s;
+      ++adam_step;
+      for (int id : ids) images[id].T += 1;  // tentative: Eq. 7 counts for the next steps' rates
+    }
+    R.read_ledger(stream);
+    R.enqueue_readback(stream);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step: ") + cudaGetErrorString(e));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    const Ledger& Lg = *R.ledger_h;
+    if (Lg.error & kErrTimeout) return fail(GS_ERR_TIMEOUT, "a device-side wait (decoupled look-back) timed out");
+    const size_t ok = std::min<size_t>(Lg.steps_ok, count);
+    // commit the completed prefix only
+    adam_step = step0 + (long long)ok;
+    for (size_t j = 0; j < images.size(); ++j) images[j].T = j < T0.size() ? T0[j] : 0;
+    for (size_t k = 0; k < ok; ++k)
+      for (int id : groups[first_group + k]) images[id].T += 1;
+    if (ok < count) {
+      // a step overflowed the instance buffers: grow them for the next try
+      if ((s = R.ensure_instances(Lg.m_need + Lg.m_need / 4 + 1024))) return s;
+      drop_graphs();
+    }
+    *done = ok;
+    *loss_sum += Lg.loss_sum;
+    last_pairs = ok ? Lg.pairs / ok : 0;
+    last_blended = ok ? Lg.blended / ok : 0;
+    last_instances = ok ? Lg.instances / ok : 0;
+    last_kernels = 10 + R.passes;
+    sum_pairs += Lg.pairs;
+    if (ok == count && count > 0) {
+      last_loss = R.ctl_h->loss;
+      R.collect_times();
+      R.have_forward = true;
+    }
+    return GS_OK;
+  }
+
+  // Steps in runs of up to `chunk`, re-running whatever an overflow skipped.
+  gs_status run_all(const std::vector<std::vector<int>>& groups, size_t chunk, double* loss_sum) {
+    size_t g = 0;
+    int stalls = 0;
+    while (g < groups.size()) {
+      size_t done = 0;
+      gs_status s = run_steps(groups, g, std::min(chunk, groups.size() - g), &done, loss_sum);
+      if (s) return s;
+      g += done;
+      stalls = done ? 0 : stalls + 1;
+      if (stalls > 3) return fail(GS_ERR_CAPACITY, "instance buffers kept overflowing");
+    }
+    return GS_OK;
+  }
+
+  unsigned long long sum_pairs = 0;
+
+  gs_status step(const int* ids, int nv, float* out_loss) {
+    std::vector<std::vector<int>> groups(1, std::vector<int>(ids, ids + nv));
+    double loss_sum = 0;
+    gs_status s = run_all(groups, 1, &loss_sum);
+    if (s) return s;
+    if (out_loss) *out_loss = (float)last_loss;
+    return GS_OK;
   }
 };
 
@@ -534,6 +601,7 @@ void gs_field_config_default(gs_field_config* c) {
   c->T_a = 200;
   c->batch_views = 1;
   c->use_graph = 1;
+  c->async_steps = 16;
   c->eta0 = 1.6e-4f;
   c->etaf = 1.6e-6f;
   c->lambda_ssim = 0.2f;
@@ -769,25 +837,21 @@ gs_status gs_integrate(gs_field* ff, int32_t id, gs_integrate_stats* st) {
   int nk = 0;
   std::vector<int> slots = f->allocate(id, &nk);
   const int B = f->cfg.batch_views;
+  std::vector<std::vector<int>> groups;
+  for (size_t q = 0; q < slots.size(); q += B)
+    groups.emplace_back(slots.begin() + q, slots.begin() + std::min(slots.size(), q + (size_t)B));
+  const size_t chunk = f->cfg.async_steps > 0 ? (size_t)f->cfg.async_steps : 1;
+  const unsigned long long pairs0 = f->sum_pairs;
   double loss_sum = 0;
-  int steps = 0;
-  unsigned long long pairs = 0;
-  for (size_t q = 0; q < slots.size(); q += B) {
-    const int nb = (int)std::min<size_t>(B, slots.size() - q);
-    float l = 0.f;
-    gs_status s = f->step(slots.data() + q, nb, &l);
-    if (s) return s;
-    loss_sum += l;
-    pairs += f->last_pairs;
-    ++steps;
-  }
+  gs_status s = f->run_all(groups, chunk, &loss_sum);
+  if (s) return s;
   if (st) {
     st->iterations = (int)slots.size();
-    st->steps = steps;
+    st->steps = (int)groups.size();
     st->key_images = nk;
     st->new_gaussians = 0;
-    st->mean_loss = steps ? loss_sum / steps : 0.0;
-    st->pairs = pairs;
+    st->mean_loss = groups.empty() ? 0.0 : loss_sum / (double)groups.size();
+    st->pairs = f->sum_pairs - pairs0;
   }
   return GS_OK;
 }
@@ -809,6 +873,7 @@ gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* o
   P.n_views = 1;
   for (int a = 0; a < 3; ++a) P.bg[a] = f->cfg.bg[a];
   P.adam = 0;
+  R.reset_ledger(f->stream);
   R.upload(f->stream);
   if ((s = R.enqueue_forward_head(f->stream, static_cast<float*>(f->params.p), f->stride, true))) return s;
   if ((s = R.enqueue_forward_tail(f->stream, out_rgb, out_T, static_cast<unsigned*>(f->step_last.p), nullptr))) return s;

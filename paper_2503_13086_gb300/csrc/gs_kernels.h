@@ -41,7 +41,7 @@ void launch_adam(float* params, const float* grads, float* m, float* v, int n, i
                  cudaStream_t s);
 
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
-                 unsigned long long m_cap, cudaStream_t s);
+                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s);
 void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys,
                  unsigned* vals, unsigned* hist, int passes, const Control* ctl, cudaStream_t s);
 void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout, unsigned* vout,
@@ -61,6 +61,6 @@ void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles,
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
-                 float* partials, double* block_sums, Control* ctl, float* dimage, cudaStream_t s);
+                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s);
 
 }  // namespace gs

@@ -64,7 +64,7 @@ extern "C" GS_API gs_status gs_scan_noalloc(void* stream, const uint32_t* counts
   // the previous call's tickets, totals and look-back flags must not leak into this one
   e = cudaMemsetAsync(base, 0, kCtlBytes + (size_t)tiles * 8, s);
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  if (n > 0) launch_scan(counts, out_offsets, n, state, ctl, ~0ull, s);
+  if (n > 0) launch_scan(counts, out_offsets, n, state, ctl, ~0ull, nullptr, s);
   if (out_total) {
     e = cudaMemcpyAsync(out_total, &ctl->m_total, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));

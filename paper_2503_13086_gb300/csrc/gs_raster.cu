@@ -28,6 +28,8 @@ gs_status DevBuf::reserve(size_t want, size_t* account) {
   if (want <= bytes) return GS_OK;
   std::lock_guard<std::mutex> lock(alloc_capture_mutex());
   if (p) {
+    // steps enqueued earlier may still use the old buffer
+    cudaDeviceSynchronize();
     cudaFree(p);
     if (account) *account -= bytes;
     p = nullptr;
@@ -53,6 +55,7 @@ void DevBuf::release(size_t* account) {
   }
   std::lock_guard<std::mutex> lock(alloc_capture_mutex());
   if (p) {
+    cudaDeviceSynchronize();
     cudaFree(p);
     if (account) *account -= bytes;
   }
@@ -86,22 +89,27 @@ Raster::Raster() {
   cudaMallocHost(&sp_h, sizeof(StepParams));
   cudaMallocHost(&views_h, sizeof(ViewDev) * kMaxViews);
   cudaMallocHost(&ctl_h, sizeof(Control));
+  cudaMallocHost(&ledger_h, sizeof(Ledger));
   std::memset(sp_h, 0, sizeof(StepParams));
   std::memset(ctl_h, 0, sizeof(Control));
+  std::memset(ledger_h, 0, sizeof(Ledger));
   cudaEventCreateWithFlags(&staged, cudaEventDisableTiming);
   for (int k = 0; k < kNumEvents; ++k) cudaEventCreate(&ev[k]);
   sp_d.reserve(sizeof(StepParams), &bytes_in_use);
   views_d.reserve(sizeof(ViewDev) * kMaxViews, &bytes_in_use);
+  ledger_d.reserve(sizeof(Ledger), &bytes_in_use);
+  cudaMemset(ledger_d.p, 0, sizeof(Ledger));
 }
 
 Raster::~Raster() {
-  DevBuf* all[] = {&sp_d, &views_d, &zeroA, &zeroB, &xyo, &conic, &rgb, &depth, &radius, &rect, &count, &offsets,
+  DevBuf* all[] = {&sp_d, &views_d, &ledger_d, &zeroA, &zeroB, &xyo, &conic, &rgb, &depth, &radius, &rect, &count, &offsets,
                    &clamp, &keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
                    &own_last, &own_dimage};
   for (DevBuf* b : all) b->release(&bytes_in_use);
   if (sp_h) cudaFreeHost(sp_h);
   if (views_h) cudaFreeHost(views_h);
   if (ctl_h) cudaFreeHost(ctl_h);
+  if (ledger_h) cudaFreeHost(ledger_h);
   cudaEventDestroy(staged);
   for (int k = 0; k < kNumEvents; ++k) cudaEventDestroy(ev[k]);
 }
@@ -251,9 +259,10 @@ gs_status Raster::stage(cudaStream_t s) {
 gs_status Raster::upload(cudaStream_t s) {
   cudaMemcpyAsync(sp_d.p, sp_h, sizeof(StepParams), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(views_d.p, views_h, sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, s);
-  // Outside a capture, mark when the staging buffers may be reused; a captured step is marked
-  // by its caller after the graph launch.
-  if (!capturing(s)) cudaEventRecord(staged, s);
+  // Mark when the staging buffers may be overwritten for the next step: right after these
+  // copies, also inside a captured step (an event node of the graph).
+  if (capturing(s)) cudaEventRecordWithFlags(staged, s, cudaEventRecordExternal);
+  else cudaEventRecord(staged, s);
   return GS_OK;
 }
 
@@ -263,7 +272,7 @@ gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int 
   launch_project(params, stride_, n_views, sp(), vd(), proj(), s);
   mark(s, 1);
   const long long n_items = (long long)n_views * stride_;
-  launch_scan(proj().count, proj().offsets, n_items, scan_state(), ctl(), size_exactly ? ~0ull : m_cap, s);
+  launch_scan(proj().count, proj().offsets, n_items, scan_state(), ctl(), size_exactly ? ~0ull : m_cap, ledger(), s);
   mark(s, 2);
   if (size_exactly) {
     cudaMemcpyAsync(ctl_h, ctl(), sizeof(Control), cudaMemcpyDeviceToHost, s);
@@ -304,7 +313,7 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
 
 void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
   launch_loss(vd(), n_views, n_loss_blocks, image, sp(), static_cast<float*>(partials.p),
-              static_cast<double*>(block_sums.p), ctl(), dimage, s);
+              static_cast<double*>(block_sums.p), ctl(), ledger(), dimage, s);
   mark(s, 7);
 }
 
@@ -389,6 +398,7 @@ gs_status gs_raster_forward(gs_raster* rr, void* stream, const float* params, in
   P.n_views = n_views;
   for (int k = 0; k < 3; ++k) P.bg[k] = bg ? bg[k] : 0.f;
   P.adam = 0;
+  r->reset_ledger(s);
   r->upload(s);
   if ((st = r->enqueue_forward_head(s, params, (int)stride, true))) return st;
   if ((st = r->ensure_instances(r->m_cap))) return st;

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
                                                       long long n_blocks, const float* __restrict__ image,
                                                       const StepParams* __restrict__ sp,
                                                       float* __restrict__ partials, double* __restrict__ block_sums,
-                                                      Control* __restrict__ ctl) {
+                                                      Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
   __shared__ __align__(16) float sx[kSY][kSXP];
   __shared__ __align__(16) float sy[kSY][kSXP];
   __shared__ float hm[5][kSY][kBX];
@@ -222,7 +222,17 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
       total += lv;
     }
   }
-  if (threadIdx.x == 0) ctl->loss = total / (double)n_views;
+  if (threadIdx.x == 0) {
+    ctl->loss = total / (double)n_views;
+    if (ledger) {  // this step is complete up to Adam, which cannot fail any more
+      ledger->loss_sum += ctl->loss;
+      ledger->pairs += ctl->pairs;
+      ledger->blended += ctl->blended;
+      ledger->instances += ctl->m_total;
+      ledger->steps_ok += 1u;
+      ledger->error |= ctl->error;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict__ views, int n_views,
@@ -312,9 +322,10 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
 }
 
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
-                 float* partials, double* block_sums, Control* ctl, float* dimage, cudaStream_t s) {
+                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s) {
   if (n_blocks <= 0) return;
-  k_loss_forward<<<(unsigned)n_blocks, 256, 0, s>>>(views, n_views, n_blocks, image, sp, partials, block_sums, ctl);
+  k_loss_forward<<<(unsigned)n_blocks, 256, 0, s>>>(views, n_views, n_blocks, image, sp, partials, block_sums, ctl,
+                                                     ledger);
   if (dimage)
     k_loss_backward<<<(unsigned)n_blocks, 256, 0, s>>>(views, n_views, image, sp, partials, ctl, dimage);
 }

@@ -34,7 +34,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restrict__ in, unsigned* __restrict__ out,
                                                        long long n_items, unsigned long long* __restrict__ state,
-                                                       Control* __restrict__ ctl, unsigned long long m_cap) {
+                                                       Control* __restrict__ ctl, unsigned long long m_cap,
+                                                       Ledger* __restrict__ ledger) {
   __shared__ unsigned s_tile;
   __shared__ unsigned s_warp[kScanThreads / 32];
   __shared__ unsigned long long s_excl;
@@ -104,9 +105,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
       if ((long long)tile == num_tiles - 1) {
         const unsigned long long m = excl + total;
         ctl->m_total = m;
-        if (m > m_cap) {
+        // an overflow skips this step; an earlier skipped step of the run skips it too
+        if (m > m_cap || (ledger && ledger->skip)) {
           ctl->overflow = 1u;
           atomicOr(&ctl->error, kErrOverflow);
+          if (ledger) {
+            ledger->skip = 1u;
+            if (m > ledger->m_need) ledger->m_need = m;
+          }
         }
       }
     }
@@ -132,9 +138,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
 }
 
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
-                 unsigned long long m_cap, cudaStream_t s) {
+                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s) {
   const long long tiles = (n_items + kScanTile - 1) / kScanTile;
-  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap);
+  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap, ledger);
 }
 
 // ---------------------------------------------------------------------------------------------
