@@ -234,6 +234,7 @@ typedef struct gs_field_stats {
   int32_t last_kernels;    /* kernel launches of the last step */
   int32_t pad;
   double last_loss;
+  double last_load_std;    /* Eq. 9 L_load of the last step's first view set: std of G_p over pixels with G_p > 0 */
 } gs_field_stats;
 GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);
 

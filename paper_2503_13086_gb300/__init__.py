@@ -78,7 +78,7 @@ class FieldStats(ctypes.Structure):
     _fields_ = [("n_gaussians", ctypes.c_int64), ("capacity", ctypes.c_int64), ("n_images", ctypes.c_int64),
                 ("adam_step", ctypes.c_int64), ("bytes_in_use", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_blended", ctypes.c_uint64), ("last_instances", ctypes.c_int64), ("last_kernels", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("last_loss", ctypes.c_double)]
+                ("pad", ctypes.c_int32), ("last_loss", ctypes.c_double), ("last_load_std", ctypes.c_double)]
 
 
 P = ctypes.c_void_p

@@ -47,6 +47,8 @@ struct Control {
   unsigned long long m_total;   // instances emitted by the key emission
   unsigned long long pairs;     // Gaussian-pixel pairs (entries evaluated up to termination)
   unsigned long long blended;   // Gaussian-pixel pairs blended (sum of G_p)
+  unsigned long long gp_pixels; // pixels with G_p > 0 (the "visible range" of Eq. 9)
+  unsigned long long gp_sq;     // sum of G_p^2 over those pixels
   unsigned int overflow;        // instance capacity exceeded
   unsigned int error;           // kErr* bits
   unsigned int scan_ticket;
@@ -67,6 +69,7 @@ struct Ledger {
   double loss_sum;
   unsigned long long pairs, blended, instances;
   unsigned long long m_need;  // largest instance count a skipped step needed
+  unsigned long long last_gp_sum, last_gp_pixels, last_gp_sq;  // G_p moments of the last completed step
   unsigned int steps_ok;      // steps completed (a prefix of the run)
   unsigned int skip;
   unsigned int error;

@@ -150,6 +150,7 @@ struct Field {
   std::vector<int> last_sizes;
   double last_loss = 0.0;
   unsigned long long last_pairs = 0, last_blended = 0, last_instances = 0;
+  double last_load_std = 0.0;
   int last_kernels = 0;
   size_t own_bytes = 0;
   // snapshot (gs_field_snapshot / gs_field_restore)
@@ -548,6 +549,11 @@ struct Field {
     last_instances = ok ? Lg.instances / ok : 0;
     last_kernels = 10 + R.passes;
     sum_pairs += Lg.pairs;
+    if (ok && Lg.last_gp_pixels) {  // Eq. 9: std of G_p over the pixels some Gaussian reaches
+      const double mean = (double)Lg.last_gp_sum / (double)Lg.last_gp_pixels;
+      const double var = (double)Lg.last_gp_sq / (double)Lg.last_gp_pixels - mean * mean;
+      last_load_std = std::sqrt(std::max(0.0, var));
+    }
     if (ok == count && count > 0) {
       last_loss = R.ctl_h->loss;
       R.collect_times();
@@ -898,6 +904,7 @@ gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
   out->last_kernels = f->last_kernels;
   out->pad = 0;
   out->last_loss = f->last_loss;
+  out->last_load_std = f->last_load_std;
   return GS_OK;
 }
 

@@ -99,11 +99,12 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
   __shared__ unsigned char s_bm[kBlendBatch];  // per entry: the warp blocks its cutoff box reaches
   __shared__ unsigned long long s_pairs[kTilePix / 32];
   __shared__ unsigned long long s_blend[kTilePix / 32];
+  __shared__ unsigned long long s_gpn[kTilePix / 32], s_gpsq[kTilePix / 32];
   __shared__ int s_item;
   if (ctl->overflow) return;
   const int tid = threadIdx.x;
   const float bg0 = sp->bg[0], bg1 = sp->bg[1], bg2 = sp->bg[2];
-  unsigned long long my_pairs = 0, my_blend = 0;
+  unsigned long long my_pairs = 0, my_blend = 0, my_gpn = 0, my_gpsq = 0;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_item = (int)atomicAdd(&ctl->fwd_work, 1u);
@@ -227,6 +228,10 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
       if (gp_out) gp_out[gpix] = gp;
       my_pairs += neval;
       my_blend += gp;
+      if (gp) {
+        my_gpn += 1;
+        my_gpsq += (unsigned long long)gp * gp;
+      }
     }
   }
   // Gaussian-pixel pairs by definition: entries evaluated per pixel up to its termination.
@@ -234,22 +239,32 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
   for (int o = 16; o > 0; o >>= 1) {
     my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
     my_blend += __shfl_down_sync(0xffffffffu, my_blend, o);
+    my_gpn += __shfl_down_sync(0xffffffffu, my_gpn, o);
+    my_gpsq += __shfl_down_sync(0xffffffffu, my_gpsq, o);
   }
   __syncthreads();
   if ((tid & 31) == 0) {
     s_pairs[tid >> 5] = my_pairs;
     s_blend[tid >> 5] = my_blend;
+    s_gpn[tid >> 5] = my_gpn;
+    s_gpsq[tid >> 5] = my_gpsq;
   }
   __syncthreads();
   if (tid == 0) {
-    unsigned long long s = 0, b = 0;
+    unsigned long long s = 0, b = 0, gn = 0, gq = 0;
 #pragma unroll
     for (int w = 0; w < kTilePix / 32; ++w) {
       s += s_pairs[w];
       b += s_blend[w];
+      gn += s_gpn[w];
+      gq += s_gpsq[w];
     }
     if (s) atomicAdd(&ctl->pairs, s);
     if (b) atomicAdd(&ctl->blended, b);
+    if (gn) {
+      atomicAdd(&ctl->gp_pixels, gn);
+      atomicAdd(&ctl->gp_sq, gq);
+    }
   }
 }
 

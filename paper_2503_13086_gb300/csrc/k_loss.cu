@@ -231,6 +231,9 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
       ledger->instances += ctl->m_total;
       ledger->steps_ok += 1u;
       ledger->error |= ctl->error;
+      ledger->last_gp_sum = ctl->blended;
+      ledger->last_gp_pixels = ctl->gp_pixels;
+      ledger->last_gp_sq = ctl->gp_sq;
     }
   }
 }

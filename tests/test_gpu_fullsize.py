@@ -1,0 +1,69 @@
+"""Parity at the bench's full size (200k Gaussians in the ring scene, one 1297 x 840 view, L1 +
+0.2 D-SSIM), in the launch configuration the bench times: bit-exact binning, pixels, loss and
+gradients against the oracle, and the Eq. 9 G_p statistic."""
+import numpy as np
+import pytest
+
+import gsinputs as gi
+import oracle
+from helpers import gpu_forward, grad_close, ocam, split_views
+
+pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
+
+
+def test_scene_scale_parity():
+    import torch
+    import paper_2503_13086_gb300 as gs
+    n = 200_000
+    p = gi.ring_scene(n, seed=0, stride=n)
+    cam = gi.ring_camera(0.3, 1297, 840, 1000.0)
+    tgt = gi.uniform_target(1297, 840, 1)
+    ras = gs.Raster()
+    g = gpu_forward(ras, p, n, [cam])
+    sizes = [(1297, 840)]
+    L = oracle.build_lists(sizes, g["rec"]["mean2d"], g["radius"], g["depth"])
+    assert len(g["keys"]) == len(L["keys"]) > 300_000
+    assert np.array_equal(g["keys"], L["keys"]) and np.array_equal(g["vals"], L["vals"])
+    assert np.array_equal(g["ranges"], L["ranges"])
+    o = oracle.blend_forward((1297, 840), 0, L["ranges"], L["vals"], g["rec"], prec="f32")
+    img = g["out"]["image"].cpu().numpy().reshape(3, 840, 1297)
+    clean = o["margin"] > TIE
+    assert clean.mean() > 0.999
+    assert np.abs(img - o["image"])[:, clean].max() <= 1e-4
+    gp = g["out"]["gp"].cpu().numpy().view(np.uint32).reshape(840, 1297)
+    assert np.array_equal(gp[clean], o["gp"][clean])
+    # loss and dL/dimage
+    T = torch.tensor(tgt.reshape(-1), device="cuda")
+    loss, dimg = ras.loss(g["out"]["image"], T, 0.2)
+    ref, d_ref, _, _ = oracle.loss(img, tgt, 0.2, True, 1.0, prec="f32")
+    assert abs(loss - ref) <= 1e-5 * abs(ref)
+    assert grad_close(dimg.cpu().numpy().reshape(1, -1), d_ref.reshape(1, -1)).mean() == 0.0
+    # gradients
+    grads, _ = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg)
+    g2 = np.zeros((n, 9), np.float32)
+    oracle.blend_backward((1297, 840), 0, L["ranges"], L["vals"], g["rec"], dimg.cpu().numpy().reshape(3, 840, 1297),
+                          g2, prec="f32")
+    g_ref = np.zeros_like(p)
+    oracle.project_backward(p, ocam(cam), g2, g_ref, prec="f32", n=n)
+    bad = grad_close(grads.cpu().numpy()[:, :n], g_ref[:, :n])
+    assert bad.mean() < 1e-3, bad.sum(axis=1)
+    ras.close()
+
+
+def test_load_balance_statistic_matches_oracle():
+    """Eq. 9: std of G_p over the pixels some Gaussian reaches, for the step's forward."""
+    import paper_2503_13086_gb300 as gs
+    n = 4096
+    p = gi.cube_scene(n, seed=9, stride=n)
+    cam = gi.identity_camera(256, 256, 256.0)
+    f = gs.Field(scene_extent=1.0)
+    f.set_gaussians(p)
+    img = f.add_image(cam, gi.uniform_target(256, 256, 3))
+    f.optimize_step([img])
+    got = f.stats()["last_load_std"]
+    gp = oracle.render(p, [ocam(cam)], prec="f32", n=n)["outs"][0]["gp"].astype(np.float64)
+    ref = float(np.std(gp[gp > 0]))
+    assert got == pytest.approx(ref, rel=1e-3)
+    f.close()
