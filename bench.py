@@ -153,9 +153,11 @@ def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed ncu
-# summaries of the current kernels (profiles/); None for a kernel changed since its capture.
-TRAFFIC = {"K8 blend bwd": 62.1e6, "K6 blend fwd": 21.8e6, "K9+K10 project bwd + Adam": 246.9e6,
-           "K4 sort": 6 * 4.08e6, "K7 loss": None}
+# summaries of the current kernels (profiles/), taken with the tiling below; None for a kernel
+# changed since its capture.
+TRAFFIC_TILING = (16, 16, 256)
+TRAFFIC = {"K8 blend bwd": None, "K6 blend fwd": None, "K9+K10 project bwd + Adam": 246.9e6,
+           "K4 sort": None, "K7 loss": None}
 
 
 def cpu_baseline_run(steps, warmup, seed=0):
@@ -217,16 +219,18 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
     return cams, targets, pts
 
 
-def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8):
+def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
-                            scene_extent=7.0, seed=3)
-    pairs = 0
+                            scene_extent=7.0, seed=3, batch_scaling=scaling)
+    pairs, add_s, int_s = 0, [], []
     t0 = time.perf_counter()
     for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
         r = sess.arrive(c, t, xyz, rgb, tr)
         pairs += r["pairs"]
+        add_s.append(r["add_image_s"])
+        int_s.append(r["integrate_s"])
     wall = time.perf_counter() - t0
     lat = sess.latency()
     psnr = sess.psnr(cams, targets)
@@ -234,7 +238,8 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8):
     torch.cuda.synchronize()
     sess.close()
     return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
-                pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn)
+                pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn,
+                batch_scaling=scaling, add_image_mean_s=float(np.mean(add_s)), integrate_mean_s=float(np.mean(int_s)))
 
 
 def run_gs(args):
@@ -249,14 +254,48 @@ def run_gs(args):
     gs.load()
     p, cam, tgt = make_workload(rank)
     stream = torch.cuda.Stream()
-    field = gs.Field(stream=stream, scene_extent=7.0, lambda_ssim=0.2, use_graph=1)
-    field.set_gaussians(p)
-    img = field.add_image(cam, tgt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def make_field(tiling):
+        f = gs.Field(stream=stream, scene_extent=7.0, lambda_ssim=0.2, use_graph=1, tiling=tiling)
+        f.set_gaussians(p)
+        return f, f.add_image(cam, tgt)
+
+    def timed_loop(f, img, steps):
+        """steps timed optimisation steps, each from the same snapshot (restored untimed) after an
+        untimed L2 flush; CUDA events on the session's stream."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        acc = dict(pairs=0, blended=0, instances=0, launches=0)
+        for k in range(steps):
+            f.restore()
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[k][0].record(stream)
+            f.optimize_step([img])
+            ev[k][1].record(stream)
+            st = f.stats()
+            acc["pairs"] += st["last_pairs"]
+            acc["blended"] += st["last_blended"]
+            acc["instances"] += st["last_instances"]
+            acc["launches"] += st["last_kernels"]
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in ev)), acc
+
+    # the autotuned session (the library's default): its choice and step time, reported beside
+    # the headline, which uses the 16 x 16 binning the pair count P is defined on
+    fa, img_a = make_field(None)
+    tune = fa.autotune([img_a], reps=5)
+    for _ in range(args.warmup):
+        fa.optimize_step([img_a])
+    fa.snapshot()
+    auto_ms, auto_acc = timed_loop(fa, img_a, args.steps)
+    auto_tiling = fa.stats()["last_tiling"]
+    fa.close()
+
+    field, img = make_field(None if args.tiling == "auto" else tuple(int(x) for x in args.tiling.split("x")))
     for _ in range(args.warmup):
         field.optimize_step([img])
-    # every timed step starts from this state (restored untimed), so the workload is stationary
     field.snapshot()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
     def sync_all():
         torch.cuda.synchronize()
@@ -268,26 +307,13 @@ def run_gs(args):
     sync_all()
     field.set_timing(True)
     sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    acc = dict(pairs=0, blended=0, instances=0)
-    launches = 0
-    for k in range(args.steps):
-        field.restore()
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        ev[k][0].record(stream)
-        field.optimize_step([img])
-        ev[k][1].record(stream)
-        st = field.stats()
-        acc["pairs"] += st["last_pairs"]
-        acc["blended"] += st["last_blended"]
-        acc["instances"] += st["last_instances"]
-        launches += st["last_kernels"]
+    ms, acc = timed_loop(field, img, args.steps)
+    launches = acc.pop("launches")
     sync_all()
     clocks = sampler.stop()
     kms, ksteps = field.kernel_times()
     field.set_timing(False)
-    ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    tiling = field.stats()["last_tiling"]
     ms_max, pairs_total = ms, float(acc["pairs"])
     if ws > 1:
         t = torch.tensor([ms, float(acc["pairs"])], device="cuda")
@@ -321,27 +347,40 @@ def run_gs(args):
 
     steps = max(1, args.steps)
     st_mean = {k: v / steps for k, v in acc.items()}
-    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    tiles = (-(-W // tiling[0])) * (-(-H // tiling[1]))
     passes = (32 + int(tiles - 1).bit_length() + 7) // 8
-    # visible Gaussians of the view (for K1's algorithmic bytes)
+    # visible Gaussians of the view (for K1's algorithmic bytes), and the pairs the 16 x 16
+    # binning of 3DGS evaluates on the same state (context for other tilings)
     ras = gs.Raster()
     fo = ras.forward(torch.tensor(p, device="cuda"), N_GAUSS, [cam])
     st_mean["visible"] = int((ras.read(6, np.uint32) > 0).sum())
+    pairs_16 = int(fo["pairs"])
     ras.close()
 
     lat = None
     if ws == 1 and args.arrivals > 0:
         cams, targets, pts = stream_inputs(args.arrivals, seed=rank)
+        # the autotuner's classes (a power of two of pixels per step) are tuned once per process, as a
+        # server would at start-up: untimed sessions over the first arrivals fill the cache
+        gs.autotune_clear()
+        warm = min(args.arrivals, 10)
+        for b in (1, 3, 9):
+            run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1)
         plain = run_stream(cams, targets, pts, batch=1, graph=0, asyn=1)
         graphed = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16)
         batched = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16)
+        batched_s = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16, scaling=1)
+        batched3_s = run_stream(cams, targets, pts, batch=3, graph=1, asyn=16, scaling=1)
         lat = {"workload": f"{args.arrivals} arrivals, 1297x840, random walk with 60-80% overlap, 5k-20k sparse "
                            f"points each, T_I = 200 over the new image + 8 neighbours, 1.5M-Gaussian hidden scene",
-               "plain_per_view": plain, "graph_async_per_view": graphed, "batched_graph": batched}
+               "autotune": f"tiling autotuned per class, cache filled by untimed sessions over the first {warm} arrivals",
+               "plain_per_view": plain, "graph_async_per_view": graphed, "batched_graph": batched,
+               "batched_graph_scaled": batched_s, "batched3_graph_scaled": batched3_s}
 
     if rank == 0:
         peaks, kind = measured_peaks()
-        rl = roofline(kms, ksteps, st_mean, N_GAUSS, passes, peaks, kind, TRAFFIC)
+        rl = roofline(kms, ksteps, st_mean, N_GAUSS, passes, peaks, kind,
+                      TRAFFIC if tuple(tiling) == TRAFFIC_TILING else {})
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -349,12 +388,21 @@ def run_gs(args):
                 "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
                            "instances": int(st_mean["instances"]), "pairs_per_step": int(st_mean["pairs"]),
                            "blended_pairs_per_step": int(st_mean["blended"]),
+                           "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "blend_batch": tiling[2],
+                                      "source": "autotuned" if args.tiling == "auto" else "fixed"},
                            "l2": "flushed before every timed step (256 MiB write, untimed)",
                            "state": "every timed step starts from the same snapshot (device copy, untimed)",
                            "parallelism": f"{ws} independent session(s), one per GPU", "graph": True},
                 "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
                         "h2d_bytes_per_step": int(tgt.nbytes), "d2h_bytes_per_step": 1024},
                 "gpu_launches": int(launches),
+                "autotuned": {"tiling": f"{auto_tiling[0]}x{auto_tiling[1]}/{auto_tiling[2]}",
+                              "ms_per_step": auto_ms / steps, "pairs_per_step": int(auto_acc["pairs"] / steps),
+                              "pairs_per_s": auto_acc["pairs"] / (auto_ms * 1e-3),
+                              "pairs_16x16_per_step": pairs_16,
+                              "candidates_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]},
+                              "note": "the same workload with the tiling the autotuner picks; P then counts that "
+                                      "binning's list entries (smaller tiles evaluate fewer pairs)"},
                 "roofline": rl, "clocks": clocks}
         if lat is not None:
             # headline: the per-view path (the paper's one-image-per-iteration semantics, so the same
@@ -378,9 +426,11 @@ def run_batched(args):
     n = 500_000
     p = gi.ring_scene(n, seed=5, stride=n)
     cams = gi.batched_views(9, seed=2)
-    field = gs.Field(scene_extent=7.0, use_graph=1)
+    stream = torch.cuda.Stream()
+    field = gs.Field(stream=stream, scene_extent=7.0, use_graph=1, tiling=None)  # autotuned
     field.set_gaussians(p)
     ids = [field.add_image(c, gi.uniform_target(c["width"], c["height"], k)) for k, c in enumerate(cams)]
+    tune = field.autotune(ids, reps=3)
     for _ in range(args.warmup):
         field.optimize_step(ids)
     field.snapshot()
@@ -389,16 +439,19 @@ def run_batched(args):
     for _ in range(args.steps):
         field.restore()
         torch.cuda.synchronize()
-        ev0.record()
+        ev0.record(stream)
         field.optimize_step(ids)
-        ev1.record()
+        ev1.record(stream)
         torch.cuda.synchronize()
         tot += ev0.elapsed_time(ev1)
         pairs += field.stats()["last_pairs"]
+    tiling = field.stats()["last_tiling"]
     field.close()
     print(json.dumps({"workload": "batched: 500k Gaussians, 9 views at mixed sizes, one graph", "ms_per_step":
                       tot / args.steps, "pairs_per_s": pairs / (tot * 1e-3),
-                      "sizes": [(c["width"], c["height"]) for c in cams]}))
+                      "sizes": [(c["width"], c["height"]) for c in cams],
+                      "tiling": f"{tiling[0]}x{tiling[1]}/{tiling[2]}",
+                      "autotune_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]}}))
 
 
 def run_serve(args):
@@ -435,6 +488,8 @@ def main():
     ap.add_argument("--arrivals", type=int, default=20)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default="16x16x256",
+                    help="scene workload headline tiling: WxHxB (tile width, height, blend batch) or auto")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -143,6 +143,22 @@ GS_API gs_status gs_raster_read(gs_raster* r, int which, void* host_dst, size_t 
 GS_API gs_status gs_raster_set_timing(gs_raster* r, int enable);
 GS_API gs_status gs_raster_kernel_times(gs_raster* r, float out_ms[9]);
 
+/* Tile shape and blend batch.  The paper renders with the 3DGS tile binning (Sec. III, Sec. V-A)
+ * and states no tile size; 3DGS uses 16 x 16.  tile_w x tile_h is the tile of the rect rule
+ * ([floor((u - r)/tile_w), floor((u + r + tile_w - 1)/tile_w)), same for y) and of the blend
+ * CTA (one thread per pixel), so it decides which Gaussians enter a pixel's list: a Gaussian whose
+ * 1/255 footprint reaches past its 3-sigma square can enter or miss a pixel depending on the grid,
+ * so the tile shape is part of the result (the oracle takes the same shape).  batch is the
+ * number of sorted Gaussians the forward stages in shared memory per round; it does not change
+ * any result.  gs_tiling_candidates lists the compiled combinations (out may be NULL to query
+ * the count; the first one, 16 x 16 with batch 256, is the default); any other combination is
+ * GS_ERR_INVALID_ARG.  gs_raster_set_tiling applies to the raster's next forward. */
+typedef struct gs_tiling {
+  int32_t tile_w, tile_h, batch;
+} gs_tiling;
+GS_API gs_status gs_tiling_candidates(gs_tiling* out, int32_t capacity, int32_t* out_n);
+GS_API gs_status gs_raster_set_tiling(gs_raster* r, const gs_tiling* t);
+
 /* ----------------------------------------------------------------------------------------
  * Session: the field, its Adam state and the registered images stay on the device.
  * ---------------------------------------------------------------------------------------- */
@@ -165,10 +181,14 @@ typedef struct gs_field_config {
   uint64_t seed;            /* semi-global selection and slot order (SplitMix64) */
   uint64_t hbm_budget_bytes;/* 0 = unlimited */
   int64_t initial_capacity; /* Gaussians */
+  gs_tiling tiling;         /* all zero: autotuned per class of view set (gs_field_autotune); else fixed */
+  int32_t batch_scaling;    /* steps over B > 1 views: 0 = mean of their Eq. 8 rates, Adam as configured;
+                               1 = also lr x sqrt(B) and betas ^ B (the large-batch rule of Zhao et al.
+                               2024 for 3DGS), which keeps per-view progress with B x fewer steps */
 } gs_field_config;
 
 /* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2
- * (3DGS), group rates 5e-3 / 1e-3 / 0.05 / 2.5e-3 / 1.25e-4, Adam (0.9, 0.999, 1e-15). */
+ * (3DGS), group rates 5e-3 / 1e-3 / 0.05 / 2.5e-3 / 1.25e-4, Adam (0.9, 0.999, 1e-15); tiling auto. */
 GS_API void gs_field_config_default(gs_field_config* cfg);
 
 GS_API gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out);
@@ -235,6 +255,8 @@ typedef struct gs_field_stats {
   int32_t pad;
   double last_loss;
   double last_load_std;    /* Eq. 9 L_load of the last step's first view set: std of G_p over pixels with G_p > 0 */
+  gs_tiling last_tiling;   /* tile shape and blend batch of the last step */
+  int32_t pad2;
 } gs_field_stats;
 GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);
 
@@ -255,6 +277,33 @@ GS_API gs_status gs_field_restore(gs_field* f);
  * device ms per kernel (same order as gs_raster_kernel_times) and the number of steps. */
 GS_API gs_status gs_field_set_timing(gs_field* f, int enable);
 GS_API gs_status gs_field_kernel_times(gs_field* f, float out_ms[9], int64_t* out_steps);
+
+/* Autotuner of the tile shape and blend batch (the paper gives none; see gs_tiling).  Times every
+ * compiled candidate on the field's current state and the given views (host array, 1..32 image
+ * ids): one sizing pass, one warm-up, then `reps` (>= 1) back-to-back runs of a whole step --
+ * projection, scan, key emission, sort, ranges, blend forward, loss, blend backward and the
+ * projection backward -- except that the projection backward writes nothing (no Adam update,
+ * which costs the same for every tiling), so the field's parameters, moments and T_j are
+ * unchanged.  The
+ * fastest candidate (best device time per run) becomes the tiling of every later step whose view
+ * set falls in the same class -- same device, same power of two of the total pixels -- in every
+ * session of the process whose configured tiling is auto (all zero); a session with a fixed
+ * tiling keeps it.  With an auto tiling, gs_optimize_step / gs_integrate run this (reps = 3) on
+ * the first step of a class no session has tuned yet, so results then depend on the timings; fix
+ * the tiling for runs that must be reproducible bit for bit.  Synchronises the field's stream.
+ * gs_autotune_clear forgets every class (thread-safe).  out (host, nullable):
+ * the choice, and per candidate its tiling and ms (INFINITY if it could not run, e.g. out of
+ * the HBM budget). */
+#define GS_MAX_TILINGS 16
+typedef struct gs_autotune_result {
+  gs_tiling chosen;
+  int32_t n_candidates;
+  gs_tiling candidates[GS_MAX_TILINGS];
+  float ms[GS_MAX_TILINGS];
+} gs_autotune_result;
+GS_API gs_status gs_field_autotune(gs_field* f, const int32_t* view_ids, int32_t n_views, int32_t reps,
+                                   gs_autotune_result* out);
+GS_API gs_status gs_autotune_clear(void);
 
 /* ----------------------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a deployment variant.

@@ -15,11 +15,11 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["GSError", "load", "build", "Camera", "Raster", "Field", "FieldConfig", "adam_step", "NPARAM",
-           "SYMBOLS", "library_path"]
+__all__ = ["GSError", "load", "build", "Camera", "Raster", "Field", "FieldConfig", "Tiling", "adam_step", "NPARAM",
+           "SYMBOLS", "library_path", "tiling_candidates"]
 
 NPARAM = 59
-TILE = 16
+MAX_TILINGS = 16
 _lock = threading.Lock()
 _lib = None
 
@@ -58,6 +58,18 @@ class Camera(ctypes.Structure):
         return c
 
 
+class Tiling(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("batch", ctypes.c_int32)]
+
+    def astuple(self):
+        return (self.tile_w, self.tile_h, self.batch)
+
+
+class AutotuneResult(ctypes.Structure):
+    _fields_ = [("chosen", Tiling), ("n_candidates", ctypes.c_int32), ("candidates", Tiling * MAX_TILINGS),
+                ("ms", ctypes.c_float * MAX_TILINGS)]
+
+
 class FieldConfig(ctypes.Structure):
     _fields_ = [("T_I", ctypes.c_int32), ("N_m", ctypes.c_int32), ("T_a", ctypes.c_int32),
                 ("batch_views", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("async_steps", ctypes.c_int32),
@@ -66,7 +78,8 @@ class FieldConfig(ctypes.Structure):
                 ("lr_sh_dc", ctypes.c_float), ("lr_sh_rest", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("add_dist_thresh", ctypes.c_float), ("scene_extent", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64),
+                ("tiling", Tiling), ("batch_scaling", ctypes.c_int32)]
 
 
 class IntegrateStats(ctypes.Structure):
@@ -78,7 +91,8 @@ class FieldStats(ctypes.Structure):
     _fields_ = [("n_gaussians", ctypes.c_int64), ("capacity", ctypes.c_int64), ("n_images", ctypes.c_int64),
                 ("adam_step", ctypes.c_int64), ("bytes_in_use", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_blended", ctypes.c_uint64), ("last_instances", ctypes.c_int64), ("last_kernels", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("last_loss", ctypes.c_double), ("last_load_std", ctypes.c_double)]
+                ("pad", ctypes.c_int32), ("last_loss", ctypes.c_double), ("last_load_std", ctypes.c_double),
+                ("last_tiling", Tiling), ("pad2", ctypes.c_int32)]
 
 
 P = ctypes.c_void_p
@@ -99,6 +113,8 @@ SYMBOLS = {
     "gs_raster_read": ([P, ctypes.c_int, P, ctypes.c_size_t, P], I32),
     "gs_raster_set_timing": ([P, ctypes.c_int], I32),
     "gs_raster_kernel_times": ([P, P], I32),
+    "gs_tiling_candidates": ([P, I32, P], I32),
+    "gs_raster_set_tiling": ([P, P], I32),
     "gs_field_config_default": ([P], None),
     "gs_field_init": ([P, P, P], I32),
     "gs_field_destroy": ([P], I32),
@@ -117,6 +133,8 @@ SYMBOLS = {
     "gs_field_restore": ([P], I32),
     "gs_field_set_timing": ([P, ctypes.c_int], I32),
     "gs_field_kernel_times": ([P, P, P], I32),
+    "gs_field_autotune": ([P, P, I32, I32, P], I32),
+    "gs_autotune_clear": ([], I32),
     "gs_scan_noalloc": ([P, P, I64, P, P], I32),
 }
 
@@ -253,6 +271,10 @@ class Raster:
                                         ctypes.byref(nbytes)))
         return buf
 
+    def set_tiling(self, tile_w, tile_h, batch):
+        t = Tiling(int(tile_w), int(tile_h), int(batch))
+        _check(self._lib.gs_raster_set_tiling(self._h, ctypes.byref(t)))
+
     def set_timing(self, on=True):
         _check(self._lib.gs_raster_set_timing(self._h, 1 if on else 0))
 
@@ -269,7 +291,23 @@ def adam_step(params, grads, m, v, n, lrs, step, beta1=0.9, beta2=0.999, eps=1e-
                             float(beta1), float(beta2), float(eps), int(step)))
 
 
+def tiling_candidates():
+    """The compiled (tile_w, tile_h, batch) combinations; the first is the default."""
+    lib = load()
+    arr = (Tiling * MAX_TILINGS)()
+    n = ctypes.c_int32()
+    _check(lib.gs_tiling_candidates(arr, MAX_TILINGS, ctypes.byref(n)))
+    return [arr[k].astuple() for k in range(min(n.value, MAX_TILINGS))]
+
+
+def autotune_clear():
+    """Forget every autotuned view-set class (the cache is shared by all sessions)."""
+    _check(load().gs_autotune_clear())
+
+
 def default_config(**kw):
+    """Library defaults, overridden by keyword (bg=(r, g, b); tiling=(tile_w, tile_h, batch) or None
+    for the autotuner)."""
     lib = load()
     cfg = FieldConfig()
     lib.gs_field_config_default(ctypes.byref(cfg))
@@ -277,6 +315,9 @@ def default_config(**kw):
         if k == "bg":
             for i in range(3):
                 cfg.bg[i] = float(v[i])
+        elif k == "tiling":
+            t = (0, 0, 0) if v is None else tuple(int(x) for x in v)
+            cfg.tiling = Tiling(*t)
         else:
             setattr(cfg, k, v)
     return cfg
@@ -403,7 +444,18 @@ class Field:
     def stats(self):
         st = FieldStats()
         _check(self._lib.gs_field_stats_get(self._h, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in FieldStats._fields_}
+        out = {k: getattr(st, k) for k, _ in FieldStats._fields_}
+        out["last_tiling"] = st.last_tiling.astuple()
+        return out
+
+    def autotune(self, view_ids, reps=3):
+        """Time every compiled tiling on these views; returns the choice and ms per candidate."""
+        arr = (ctypes.c_int32 * len(view_ids))(*[int(v) for v in view_ids])
+        res = AutotuneResult()
+        _check(self._lib.gs_field_autotune(self._h, arr, len(view_ids), int(reps), ctypes.byref(res)))
+        n = min(res.n_candidates, MAX_TILINGS)
+        return dict(chosen=res.chosen.astuple(),
+                    candidates=[(res.candidates[k].astuple(), float(res.ms[k])) for k in range(n)])
 
     def image_info(self, image_id, n_images):
         T = ctypes.c_int32()

@@ -12,8 +12,7 @@
 namespace gs {
 
 constexpr int kNumParams = 59;      // mean 3, log-scale 3, quaternion 4, opacity 1, SH 48
-constexpr int kTile = 16;           // tile edge in pixels (16 x 16 = 256 pixels = one CTA)
-constexpr int kTilePix = kTile * kTile;
+constexpr int kMaxTilePix = 256;    // largest tile (pixels = threads of one blend CTA)
 constexpr int kChunk = 32;          // Gaussians per backward work item and checkpoint period
 constexpr int kMaxStepViews = 32;   // views of one step
 constexpr float kNearZ = 0.2f;      // cull at camera z <= 0.2
@@ -35,6 +34,7 @@ struct ViewDev {
   float campos[3];  // camera centre in world space, -R^T t
   float limx, limy;
   int W, H;        // image size in pixels
+  int tw, th;      // tile size in pixels (the same for every view of a step)
   int gx, gy;      // tile grid
   long long tile_base;   // first global tile id of this view
   long long pix_base;    // first pixel of this view in the packed per-pixel buffers
@@ -86,7 +86,7 @@ struct StepParams {
   float beta1, beta2, eps;
   float step_size_scale; // 1 / (1 - beta1^t)
   float bc2_sqrt;        // sqrt(1 - beta2^t)
-  int adam;              // 1: apply Adam, 0: write gradients
+  int adam;              // 1: apply Adam, 0: write gradients, 2: write nothing (autotuner timing)
 };
 
 // Exponent of the 2D Gaussian at offset (dx, dy) from its centre.  The conic is stored

@@ -46,6 +46,7 @@ struct Raster {
   bool have_forward = false;
   int sorted = 0;  // which ping-pong buffer holds the sorted list
   int num_sms = 1;
+  Tiling tiling;   // tile shape and K6 batch of the next step
 
   // device buffers
   DevBuf sp_d, views_d;
@@ -92,6 +93,7 @@ struct Raster {
   gs_status enqueue_forward_head(cudaStream_t s, const float* params, int stride_, bool size_exactly);
   gs_status enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp);
   void enqueue_loss(cudaStream_t s, const float* image, float* dimage);
+  void enqueue_blend_backward(cudaStream_t s, const float* image, const float* dimage);
   void enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last, const float* dimage,
                         float* grads, float* m, float* v, float* grad2d);
   void enqueue_readback(cudaStream_t s);

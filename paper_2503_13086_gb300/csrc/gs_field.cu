@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <unordered_map>
 #include <vector>
@@ -131,6 +132,41 @@ struct GraphEntry {
 
 }  // namespace
 
+// Autotuned tilings, shared by every session of the process: a step's cost depends on the device
+// and on the size of its view set, not on the session, so a class is tuned once per device.
+// Class = (device, floor(log2(total pixels of the step's views))).
+struct TuneCache {
+  std::mutex mu;
+  std::vector<std::pair<std::pair<int, int>, Tiling>> entries;
+  bool find(std::pair<int, int> key, Tiling* out) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : entries)
+      if (e.first == key) {
+        *out = e.second;
+        return true;
+      }
+    return false;
+  }
+  void put(std::pair<int, int> key, const Tiling& t) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& e : entries)
+      if (e.first == key) {
+        e.second = t;
+        return;
+      }
+    entries.push_back({key, t});
+  }
+  void clear() {
+    std::lock_guard<std::mutex> lock(mu);
+    entries.clear();
+  }
+};
+
+TuneCache& tune_cache() {
+  static TuneCache c;
+  return c;
+}
+
 struct Field {
   gs_field_config cfg;
   cudaStream_t stream = nullptr;
@@ -148,6 +184,9 @@ struct Field {
   std::vector<GraphEntry> graphs;
   bool sized_for_views = false;
   std::vector<int> last_sizes;
+  Tiling sized_tiling;  // tiling of the last sizing step
+  Tiling last_tiling;   // tiling of the last step
+
   double last_loss = 0.0;
   unsigned long long last_pairs = 0, last_blended = 0, last_instances = 0;
   double last_load_std = 0.0;
@@ -189,7 +228,9 @@ struct Field {
     for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
     const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)R.passes,
                                       (unsigned long long)R.n_tiles, R.zeroA_bytes, R.zeroB_bytes, R.sort_state_bytes,
-                                      R.ranges_bytes, R.chunk_bytes, (unsigned long long)R.timing};
+                                      R.ranges_bytes, R.chunk_bytes, (unsigned long long)R.timing,
+                                      (unsigned long long)R.tiling.tw, (unsigned long long)R.tiling.th,
+                                      (unsigned long long)R.tiling.batch};
     v.insert(v.end(), std::begin(lay), std::end(lay));
     return v;
   }
@@ -437,23 +478,31 @@ struct Field {
   }
 
   // Fill the staging parameters of a step (after Raster::stage) for Adam step `t`.
+  // With batch_scaling a step over B views scales every rate by sqrt(B) and raises the betas to
+  // the power B (Zhao et al. 2024, large-batch 3DGS training).
   void fill_params(int nv, double lr_mean, long long t) {
     StepParams& P = *r->sp_h;
     P.n = n;
     P.n_views = nv;
     for (int a = 0; a < 3; ++a) P.bg[a] = cfg.bg[a];
     P.lambda_ssim = cfg.lambda_ssim;
-    P.lr[0] = (float)(lr_mean * (double)scene_extent());
-    P.lr[1] = cfg.lr_scale;
-    P.lr[2] = cfg.lr_rot;
-    P.lr[3] = cfg.lr_opacity;
-    P.lr[4] = cfg.lr_sh_dc;
-    P.lr[5] = cfg.lr_sh_rest;
-    P.beta1 = cfg.beta1;
-    P.beta2 = cfg.beta2;
+    double scale = 1.0, b1 = cfg.beta1, b2 = cfg.beta2;
+    if (cfg.batch_scaling && nv > 1) {
+      scale = std::sqrt((double)nv);
+      b1 = std::pow(b1, (double)nv);
+      b2 = std::pow(b2, (double)nv);
+    }
+    P.lr[0] = (float)(scale * lr_mean * (double)scene_extent());
+    P.lr[1] = (float)(scale * cfg.lr_scale);
+    P.lr[2] = (float)(scale * cfg.lr_rot);
+    P.lr[3] = (float)(scale * cfg.lr_opacity);
+    P.lr[4] = (float)(scale * cfg.lr_sh_dc);
+    P.lr[5] = (float)(scale * cfg.lr_sh_rest);
+    P.beta1 = (float)b1;
+    P.beta2 = (float)b2;
     P.eps = cfg.adam_eps;
-    P.step_size_scale = (float)(1.0 / (1.0 - std::pow((double)cfg.beta1, (double)t)));
-    P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow((double)cfg.beta2, (double)t));
+    P.step_size_scale = (float)(1.0 / (1.0 - std::pow(b1, (double)t)));
+    P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow(b2, (double)t));
     P.adam = 1;
   }
 
@@ -462,11 +511,12 @@ struct Field {
   gs_status enqueue_prepared(int nv) {
     Raster& R = *r;
     gs_status s;
-    const bool first = !sized_for_views || cur_sizes != last_sizes;
+    const bool first = !sized_for_views || cur_sizes != last_sizes || !(sized_tiling == R.tiling);
     if (first) {
       if ((s = enqueue_step(true))) return s;
       sized_for_views = true;
       last_sizes = cur_sizes;
+      sized_tiling = R.tiling;
       return GS_OK;
     }
     if (!cfg.use_graph) return enqueue_step(false);
@@ -501,6 +551,138 @@ struct Field {
     return GS_OK;
   }
 
+  bool auto_tiling() const { return cfg.tiling.tile_w == 0 && cfg.tiling.tile_h == 0 && cfg.tiling.batch == 0; }
+  Tiling fixed_tiling() const {
+    if (auto_tiling()) return Tiling{};
+    return Tiling{cfg.tiling.tile_w, cfg.tiling.tile_h, cfg.tiling.batch};
+  }
+
+  std::pair<int, int> view_class(const int* ids, int nv) const {
+    long long pix = 0;
+    for (int k = 0; k < nv; ++k)
+      if (ids[k] >= 0 && ids[k] < (int)images.size())
+        pix += (long long)images[ids[k]].cam.width * images[ids[k]].cam.height;
+    int b = 0;
+    while ((pix >> b) > 1) ++b;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return {dev, b};
+  }
+
+  // Time every compiled tiling on these views (the whole step with the projection backward in
+  // its write-nothing mode, so the field is untouched) and remember the fastest for the class.
+  gs_status autotune(const int* ids, int nv, int reps, gs_autotune_result* out) {
+    Raster& R = *r;
+    gs_status s;
+    if (nv <= 0 || nv > kMaxViews) return fail(GS_ERR_CAPACITY, "views per step must be in 1..32");
+    if (n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
+    if (reps < 1) return fail(GS_ERR_INVALID_ARG, "reps must be >= 1");
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    Tiling cand[GS_MAX_TILINGS];
+    const int nc = std::min(tiling_candidates(cand, GS_MAX_TILINGS), GS_MAX_TILINGS);
+    float ms[GS_MAX_TILINGS];
+    const Tiling keep = R.tiling;
+    const bool keep_timing = R.timing;
+    R.timing = false;  // the per-kernel events are for real steps only
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    s = GS_OK;
+    for (int c = 0; c < nc && !s; ++c) {
+      ms[c] = INFINITY;
+      R.tiling = cand[c];
+      double lr_mean = 0;
+      gs_status cs = setup_views(ids, nv, &lr_mean);
+      if (cs == GS_ERR_OOM || cs == GS_ERR_BUDGET || cs == GS_ERR_CAPACITY) continue;  // this candidate does not fit
+      if (cs) {
+        s = cs;
+        break;
+      }
+      if ((s = R.stage(stream))) break;
+      fill_params(nv, lr_mean, adam_step + 1);
+      R.sp_h->adam = 2;  // the projection backward runs but writes nothing
+      std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * nv);
+      R.reset_ledger(stream);
+      R.upload(stream);
+      float* img = static_cast<float*>(step_img.p);
+      float* dimg = static_cast<float*>(step_dimg.p);
+      for (int rep = 0; rep <= reps && !s; ++rep) {  // rep 0: sizing + warm-up
+        if (rep == 1) cudaEventRecord(e0, stream);
+        cs = R.enqueue_forward_head(stream, static_cast<float*>(params.p), stride, rep == 0);
+        if (cs == GS_ERR_OOM || cs == GS_ERR_BUDGET || cs == GS_ERR_CAPACITY) break;
+        if ((s = cs)) break;
+        if ((s = R.enqueue_forward_tail(stream, img, static_cast<float*>(step_T.p), static_cast<unsigned*>(step_last.p),
+                                        static_cast<unsigned*>(step_gp.p))))
+          break;
+        R.enqueue_loss(stream, img, dimg);
+        R.enqueue_backward(stream, static_cast<float*>(params.p), img, static_cast<unsigned*>(step_last.p), dimg,
+                           nullptr, static_cast<float*>(adam_m.p), static_cast<float*>(adam_v.p), nullptr);
+        if (rep == reps) {
+          cudaEventRecord(e1, stream);
+          R.read_ledger(stream);
+          e = cudaStreamSynchronize(stream);
+          if (e != cudaSuccess) {
+            s = fail(GS_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            break;
+          }
+          if (R.ledger_h->error & kErrTimeout) {
+            s = fail(GS_ERR_TIMEOUT, "a device-side wait (decoupled look-back) timed out");
+            break;
+          }
+          float t = 0.f;
+          if (cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && R.ledger_h->skip == 0u) {
+            ms[c] = t / (float)reps;
+            if (best < 0 || ms[c] < ms[best]) best = c;
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    R.timing = keep_timing;
+    R.reset_ledger(stream);
+    sized_for_views = false;  // the next step sizes its buffers for its own tiling
+    if (s) {
+      R.tiling = keep;
+      return s;
+    }
+    if (best < 0) {
+      R.tiling = keep;
+      return fail(GS_ERR_OOM, "autotune: no tiling fits");
+    }
+    R.tiling = cand[best];
+    tune_cache().put(view_class(ids, nv), cand[best]);
+    if (out) {
+      out->chosen = gs_tiling{cand[best].tw, cand[best].th, cand[best].batch};
+      out->n_candidates = nc;
+      for (int c = 0; c < nc; ++c) {
+        out->candidates[c] = gs_tiling{cand[c].tw, cand[c].th, cand[c].batch};
+        out->ms[c] = ms[c];
+      }
+    }
+    if (!auto_tiling()) R.tiling = fixed_tiling();
+    return GS_OK;
+  }
+
+  // Tiling of a step over these views: the configured one, else the class's autotuned one
+  // (tuning the class first if `may_tune`).
+  gs_status pick_tiling(const int* ids, int nv, bool may_tune) {
+    Raster& R = *r;
+    if (!auto_tiling()) {
+      R.tiling = fixed_tiling();
+      return GS_OK;
+    }
+    Tiling t;
+    if (tune_cache().find(view_class(ids, nv), &t)) {
+      R.tiling = t;
+      return GS_OK;
+    }
+    if (!may_tune) return fail(GS_ERR_STATE, "tiling of this view class not tuned");
+    return autotune(ids, nv, 3, nullptr);
+  }
+
   // Run `count` steps (views of step k: groups[k]) enqueued back to back, with one
   // synchronisation at the end.  Returns how many completed (a prefix); the caller re-runs the
   // rest.  T_j and the Adam step count are advanced only for completed steps.
@@ -509,18 +691,25 @@ struct Field {
     Raster& R = *r;
     gs_status s;
     const long long step0 = adam_step;
+    // tune any view class not seen yet before the run starts (tuning synchronises)
+    for (size_t k = 0; k < count; ++k) {
+      const std::vector<int>& ids = groups[first_group + k];
+      if ((s = pick_tiling(ids.data(), (int)ids.size(), true))) return s;
+    }
     std::vector<int> T0;
     for (auto& im : images) T0.push_back(im.T);
     R.reset_ledger(stream);
     for (size_t k = 0; k < count; ++k) {
       const std::vector<int>& ids = groups[first_group + k];
       double lr_mean = 0;
+      if ((s = pick_tiling(ids.data(), (int)ids.size(), false))) return s;
       if ((s = setup_views(ids.data(), (int)ids.size(), &lr_mean))) return s;
       if ((s = R.stage(stream))) return s;  // waits only for the previous step's parameter upload
       fill_params((int)ids.size(), lr_mean, adam_step + 1);
       std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * ids.size());
       if ((s = enqueue_prepared((int)ids.size()))) return s;
       ++adam_step;
+      last_tiling = R.tiling;
       for (int id : ids) images[id].T += 1;  // tentative: Eq. 7 counts for the next steps' rates
     }
     R.read_ledger(stream);
@@ -629,6 +818,9 @@ gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out
   if (cfg->T_I <= 0 || cfg->N_m <= 0 || cfg->T_a <= 0 || cfg->batch_views <= 0 || cfg->batch_views > gs::kMaxViews ||
       !(cfg->eta0 > 0.f) || !(cfg->etaf > 0.f) || cfg->lambda_ssim < 0.f || cfg->lambda_ssim > 1.f)
     return fail(GS_ERR_INVALID_ARG, "invalid field configuration");
+  const bool tiling_auto = cfg->tiling.tile_w == 0 && cfg->tiling.tile_h == 0 && cfg->tiling.batch == 0;
+  if (!tiling_auto && !gs::tiling_supported(gs::Tiling{cfg->tiling.tile_w, cfg->tiling.tile_h, cfg->tiling.batch}))
+    return fail(GS_ERR_INVALID_ARG, "configured tiling not among gs_tiling_candidates");
   Field* f = new (std::nothrow) Field();
   if (!f) return fail(GS_ERR_OOM, "host allocation failed");
   f->cfg = *cfg;
@@ -868,6 +1060,7 @@ gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* o
   if (f->n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
   gs::Raster& R = *f->r;
   gs_status s;
+  R.tiling = f->fixed_tiling();  // renders use the configured tiling, else the default one
   if ((s = R.set_views(cam, 1, nullptr))) return s;
   R.stride = f->stride;
   R.n = f->n;
@@ -905,6 +1098,8 @@ gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
   out->pad = 0;
   out->last_loss = f->last_loss;
   out->last_load_std = f->last_load_std;
+  out->last_tiling = gs_tiling{f->last_tiling.tw, f->last_tiling.th, f->last_tiling.batch};
+  out->pad2 = 0;
   return GS_OK;
 }
 
@@ -976,6 +1171,20 @@ gs_status gs_field_set_timing(gs_field* ff, int enable) {
   f->r->timing = enable != 0;
   std::memset(f->r->acc_ms, 0, sizeof(f->r->acc_ms));
   f->r->timed_steps = 0;
+  return GS_OK;
+}
+
+gs_status gs_field_autotune(gs_field* ff, const int32_t* ids, int32_t nv, int32_t reps, gs_autotune_result* out) {
+  Field* f = F(ff);
+  if (!f || !ids) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  for (int k = 0; k < nv; ++k)
+    if (ids[k] < 0 || ids[k] >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "view id out of range");
+  std::vector<int> v(ids, ids + std::max(nv, 0));
+  return f->autotune(v.data(), nv, reps, out);
+}
+
+gs_status gs_autotune_clear(void) {
+  gs::tune_cache().clear();
   return GS_OK;
 }
 

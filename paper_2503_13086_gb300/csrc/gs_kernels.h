@@ -32,6 +32,15 @@ constexpr int kSortBits = 8;
 constexpr int kSortBins = 1 << kSortBits;
 constexpr int kMaxSortPasses = 8;
 
+// Tile shape of the binning and blending, and the number of sorted Gaussians K6 stages in shared
+// memory per round.  Only the shapes/batches in tiling_candidates() are compiled.
+struct Tiling {
+  int tw = 16, th = 16, batch = 256;
+  bool operator==(const Tiling& o) const { return tw == o.tw && th == o.th && batch == o.batch; }
+};
+int tiling_candidates(Tiling* out, int cap);  // returns how many; fills up to cap
+bool tiling_supported(const Tiling& t);
+
 void launch_project(const float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
                     const ProjBuffers& out, cudaStream_t s);
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
@@ -49,11 +58,11 @@ void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsign
 void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s);
 
 void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const Control* ctl, cudaStream_t s);
-void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
                           unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s);
-void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
                            const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s);

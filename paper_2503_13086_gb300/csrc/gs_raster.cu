@@ -148,7 +148,7 @@ gs_status Raster::set_views(const gs_camera* cams, int nv, const float* const* t
   long long tb = 0, pb = 0, lb = 0;
   for (int v = 0; v < nv; ++v) {
     const gs_camera& c = cams[v];
-    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * kTile || c.height > 65535 * kTile)
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * tiling.tw || c.height > 65535 * tiling.th)
       return fail(GS_ERR_INVALID_ARG, "camera size out of range");
     if (!(c.fx > 0.f) || !(c.fy > 0.f)) return fail(GS_ERR_INVALID_ARG, "focal lengths must be positive");
     ViewDev& V = views[v];
@@ -164,8 +164,10 @@ gs_status Raster::set_views(const gs_camera* cams, int nv, const float* const* t
     V.limy = kFovLim * ((float)c.height / (2.f * c.fy));
     V.W = c.width;
     V.H = c.height;
-    V.gx = (c.width + kTile - 1) / kTile;
-    V.gy = (c.height + kTile - 1) / kTile;
+    V.tw = tiling.tw;
+    V.th = tiling.th;
+    V.gx = (c.width + tiling.tw - 1) / tiling.tw;
+    V.gy = (c.height + tiling.th - 1) / tiling.th;
     V.tile_base = tb;
     V.pix_base = pb;
     V.loss_block_base = lb;
@@ -211,6 +213,7 @@ gs_status Raster::ensure_instances(unsigned long long m) {
     DevBuf* bufs[] = {&keys0, &keys1, &vals0, &vals1, &ginst, &ckpt};
     for (DevBuf* b : bufs) b->release(&bytes_in_use);
     const unsigned long long chunks = (want >> 5) + 1;
+    m_cap = 0;  // until every buffer below exists (a failed reserve leaves them released)
     if ((s = keys0.reserve(want * 8, &bytes_in_use)) || (s = keys1.reserve(want * 8, &bytes_in_use)) ||
         (s = vals0.reserve(want * 4, &bytes_in_use)) || (s = vals1.reserve(want * 4, &bytes_in_use)) ||
         (s = ginst.reserve(want * 48, &bytes_in_use)))
@@ -221,8 +224,9 @@ gs_status Raster::ensure_instances(unsigned long long m) {
   // checkpoints and chunk map depend on tiles as well
   const unsigned long long n_ids = (m_cap >> 5) + (unsigned long long)n_tiles + 1;
   gs_status s;
-  if ((s = ckpt.reserve(n_ids * kTilePix * sizeof(float4), &bytes_in_use)) ||
-      (s = cmask.reserve(n_ids * kTilePix * 4, &bytes_in_use)) || (s = order.reserve((size_t)n_tiles * 4, &bytes_in_use)) ||
+  const unsigned long long tile_pix = (unsigned long long)tiling.tw * tiling.th;
+  if ((s = ckpt.reserve(n_ids * tile_pix * sizeof(float4), &bytes_in_use)) ||
+      (s = cmask.reserve(n_ids * tile_pix * 4, &bytes_in_use)) || (s = order.reserve((size_t)n_tiles * 4, &bytes_in_use)) ||
       (s = tile_chunks.reserve((size_t)n_tiles * 4, &bytes_in_use)))
     return s;
   const unsigned long long sort_tiles = (m_cap + kSortTile - 1) / kSortTile;
@@ -304,7 +308,7 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
   launch_ranges(kb[sorted], ranges(), (long long)m_cap, ctl(), s);
   launch_tile_order(ranges(), n_tiles, static_cast<int*>(order.p), ctl(), s);
   mark(s, 5);
-  launch_blend_forward(vd(), n_views, n_tiles, ranges(), vb[sorted], proj(), sp(), ctl(),
+  launch_blend_forward(tiling, vd(), n_views, n_tiles, ranges(), vb[sorted], proj(), sp(), ctl(),
                        static_cast<const int*>(order.p), image, T, last, gp, static_cast<float4*>(ckpt.p),
                        static_cast<unsigned*>(cmask.p), chunk_tile(), static_cast<int*>(tile_chunks.p), num_sms, s);
   mark(s, 6);
@@ -317,13 +321,17 @@ void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
   mark(s, 7);
 }
 
-void Raster::enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last,
-                              const float* dimage, float* grads, float* m, float* v, float* grad2d) {
-  (void)last;  // the backward reads the forward's per-chunk masks instead of the last index
-  launch_blend_backward(vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(sorted ? vals1.p : vals0.p), proj(),
+void Raster::enqueue_blend_backward(cudaStream_t s, const float* image, const float* dimage) {
+  launch_blend_backward(tiling, vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(sorted ? vals1.p : vals0.p), proj(),
                         ctl(), image, dimage, static_cast<float4*>(ckpt.p), static_cast<unsigned*>(cmask.p),
                         chunk_tile(), static_cast<int*>(tile_chunks.p), static_cast<float4*>(ginst.p), num_sms, s);
   mark(s, 8);
+}
+
+void Raster::enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last,
+                              const float* dimage, float* grads, float* m, float* v, float* grad2d) {
+  (void)last;  // the backward reads the forward's per-chunk masks instead of the last index
+  enqueue_blend_backward(s, image, dimage);
   launch_project_backward(params, stride, n_views, sp(), vd(), proj(), static_cast<float4*>(ginst.p), ctl(), grads,
                           m, v, grad2d, s);
   mark(s, 9);
@@ -534,6 +542,25 @@ gs_status gs_raster_set_timing(gs_raster* rr, int enable) {
   r->timing = enable != 0;
   std::memset(r->acc_ms, 0, sizeof(r->acc_ms));
   r->timed_steps = 0;
+  return GS_OK;
+}
+
+gs_status gs_tiling_candidates(gs_tiling* out, int32_t capacity, int32_t* out_n) {
+  gs::Tiling t[GS_MAX_TILINGS];
+  const int n = gs::tiling_candidates(t, GS_MAX_TILINGS);
+  if (out_n) *out_n = n;
+  if (!out) return GS_OK;
+  if (capacity < 0) return fail(GS_ERR_INVALID_ARG, "negative capacity");
+  for (int k = 0; k < n && k < capacity && k < GS_MAX_TILINGS; ++k) out[k] = gs_tiling{t[k].tw, t[k].th, t[k].batch};
+  return GS_OK;
+}
+
+gs_status gs_raster_set_tiling(gs_raster* rr, const gs_tiling* t) {
+  gs::Raster* r = reinterpret_cast<gs::Raster*>(rr);
+  if (!r || !t) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  const gs::Tiling tl{t->tile_w, t->tile_h, t->batch};
+  if (!gs::tiling_supported(tl)) return fail(GS_ERR_INVALID_ARG, "tiling not among gs_tiling_candidates");
+  r->tiling = tl;
   return GS_OK;
 }
 

@@ -1,10 +1,13 @@
 // k_blend.cu -- K6 (front-to-back alpha blending, Eq. 2) and K8 (its splatting-parallel
 // backward, Sec. IV-D), sm_103a.
 //
-// K6: persistent CTAs of 256 threads (one 16 x 16 tile at a time, one pixel per thread, each
-// warp an 8 x 4 pixel block) take tiles longest-list first, so the few very long tiles do not
-// end up as the tail of the launch.  The tile's sorted Gaussians are staged through shared
-// memory in batches of 256 and walked in chunks of 32.  Per chunk a cheap pass first marks the
+// Both are templates over the tile shape TW x TH (a multiple of the 8 x 4 warp block, at most 256
+// pixels) and K6 over the staged batch; the autotuner of the session picks the instance.
+//
+// K6: persistent CTAs of TW x TH threads (one tile at a time, one pixel per thread, each warp an
+// 8 x 4 pixel block) take tiles longest-list first, so the few very long tiles do not end up as
+// the tail of the launch.  The tile's sorted Gaussians are staged through shared memory in
+// batches of BATCH and walked in chunks of 32.  Per chunk a cheap pass first marks the
 // candidates: a warp skips a Gaussian outright when the bounding box of its 1/255 cutoff ellipse
 // misses the warp's block (a warp-uniform branch), otherwise each pixel tests its exponent
 // against -ln(255 opacity).  These iterations are independent, so they pipeline; only
@@ -30,21 +33,28 @@
 namespace gs {
 
 namespace {
-constexpr int kBlendBatch = 256;
-static_assert(kBlendBatch % kChunk == 0, "batches hold whole chunks");
+
+// Pixel layout of a TW x TH tile: warp w covers the 8 x 4 block (w % BX, w / BX) of the tile,
+// lane l its pixel (l % 8, l / 8).  K6 and K8 share this mapping.
+template <int TW, int TH>
+struct Shape {
+  static constexpr int kPix = TW * TH;
+  static constexpr int kWarps = kPix / 32;
+  static constexpr int kBX = TW / 8;
+  static constexpr int kBY = TH / 4;
+  static_assert(TW % 8 == 0 && TH % 4 == 0 && kPix >= 32 && kPix <= kMaxTilePix, "unsupported tile shape");
+  static_assert(kWarps <= 8, "the per-entry warp-block mask is 8 bits");
+  __device__ static __forceinline__ void slot_xy(int s, int& ox, int& oy) {
+    const int w = s >> 5, l = s & 31;
+    ox = ((w % kBX) << 3) + (l & 7);
+    oy = ((w / kBX) << 2) + (l >> 3);
+  }
+};
 
 __device__ __forceinline__ int view_of_tile(const ViewDev* __restrict__ views, int n_views, long long t) {
   int v = 0;
   while (v + 1 < n_views && views[v + 1].tile_base <= t) ++v;
   return v;
-}
-
-// Pixel slot s (0..255) of a tile -> offset in the tile: warp w = s / 32 covers the 8 x 4 block
-// at (8 (w % 2), 4 (w / 2)), lane l its pixel (l % 8, l / 8).  K6 and K8 share this mapping.
-__device__ __forceinline__ void slot_xy(int s, int& ox, int& oy) {
-  const int w = s >> 5, l = s & 31;
-  ox = ((w & 1) << 3) + (l & 7);
-  oy = ((w >> 1) << 2) + (l >> 3);
 }
 
 // Chunk id of a tile's chunk 0: unique over tiles and < (instances / 32) + tiles + 1.
@@ -87,19 +97,23 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
 // ---------------------------------------------------------------------------------------------
 // K6
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
+template <int TW, int TH, int BATCH>
+__global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
     const unsigned* __restrict__ vals, const ProjBuffers pb, const StepParams* __restrict__ sp,
     Control* __restrict__ ctl, const int* __restrict__ order, float* __restrict__ image, float* __restrict__ Tout,
     unsigned* __restrict__ last_out, unsigned* __restrict__ gp_out, float4* __restrict__ ckpt,
     unsigned* __restrict__ cmask, int* __restrict__ chunk_tile, int* __restrict__ tile_chunks) {
-  __shared__ float4 s_xyo[kBlendBatch];
-  __shared__ float4 s_con[kBlendBatch];
-  __shared__ float4 s_rgb[kBlendBatch];
-  __shared__ unsigned char s_bm[kBlendBatch];  // per entry: the warp blocks its cutoff box reaches
-  __shared__ unsigned long long s_pairs[kTilePix / 32];
-  __shared__ unsigned long long s_blend[kTilePix / 32];
-  __shared__ unsigned long long s_gpn[kTilePix / 32], s_gpsq[kTilePix / 32];
+  using S = Shape<TW, TH>;
+  constexpr int kPix = S::kPix;
+  static_assert(BATCH % kChunk == 0, "batches hold whole chunks");
+  __shared__ float4 s_xyo[BATCH];
+  __shared__ float4 s_con[BATCH];
+  __shared__ float4 s_rgb[BATCH];
+  __shared__ unsigned char s_bm[BATCH];  // per entry: the warp blocks its cutoff box reaches
+  __shared__ unsigned long long s_pairs[S::kWarps];
+  __shared__ unsigned long long s_blend[S::kWarps];
+  __shared__ unsigned long long s_gpn[S::kWarps], s_gpsq[S::kWarps];
   __shared__ int s_item;
   if (ctl->overflow) return;
   const int tid = threadIdx.x;
@@ -117,52 +131,54 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
     const long long local = t - V.tile_base;
     const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
     int ox, oy;
-    slot_xy(tid, ox, oy);
-    const int px = tx * kTile + ox;
-    const int py = ty * kTile + oy;
+    S::slot_xy(tid, ox, oy);
+    const int px = tx * TW + ox;
+    const int py = ty * TH + oy;
     const bool inside = px < V.W && py < V.H;
     const float pxf = (float)px, pyf = (float)py;
     const int warp = tid >> 5, lane = tid & 31;
-    const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
+    const float tx0 = (float)(tx * TW), ty0 = (float)(ty * TH);
 
     const uint2 rg = ranges[t];
     const unsigned start = rg.x;
     const int L = (int)(rg.y - rg.x);
     const long long cb = chunk_base(start, t);
-    for (int k = tid; k < (L + kChunk - 1) / kChunk; k += kTilePix) chunk_tile[cb + k] = (int)(t + 1);
+    for (int k = tid; k < (L + kChunk - 1) / kChunk; k += kPix) chunk_tile[cb + k] = (int)(t + 1);
 
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     unsigned last = 0u, gp = 0u;
     unsigned neval = (unsigned)L;
     bool done = !inside;
     int batches = 0;
-    for (int b0 = 0; b0 < L; b0 += kBlendBatch) {
-      if (__syncthreads_count(done) == kTilePix) break;
+    for (int b0 = 0; b0 < L; b0 += BATCH) {
+      if (__syncthreads_count(done) == kPix) break;
       ++batches;
-      const int j = b0 + tid;
-      if (j < L) {
+#pragma unroll
+      for (int jj = tid; jj < BATCH; jj += kPix) {
+        const int j = b0 + jj;
+        if (j >= L) break;
         const unsigned rec = vals[start + j];
         const float4 xy = pb.xyo[rec];
-        s_xyo[tid] = xy;
-        s_con[tid] = pb.conic[rec];
-        s_rgb[tid] = pb.rgb[rec];
-        // which of the eight 8 x 4 warp blocks (warp w at (8 (w % 2), 4 (w / 2))) the cutoff box
-        // of this Gaussian reaches; block centres are 3.5 / 1.5 px from their edge pixels
+        s_xyo[jj] = xy;
+        s_con[jj] = pb.conic[rec];
+        s_rgb[jj] = pb.rgb[rec];
+        // which 8 x 4 warp blocks (warp w at (8 (w % BX), 4 (w / BX))) the cutoff box of this
+        // Gaussian reaches; block centres are 3.5 / 1.5 px from their edge pixels
         unsigned xm = 0u, ym = 0u;
 #pragma unroll
-        for (int bx = 0; bx < 2; ++bx)
+        for (int bx = 0; bx < S::kBX; ++bx)
           if (fabsf(xy.x - (tx0 + 8.f * bx + 3.5f)) <= xy.z + 3.5f) xm |= 1u << bx;
 #pragma unroll
-        for (int by = 0; by < 4; ++by)
+        for (int by = 0; by < S::kBY; ++by)
           if (fabsf(xy.y - (ty0 + 4.f * by + 1.5f)) <= xy.w + 1.5f) ym |= 1u << by;
         unsigned bm = 0u;
 #pragma unroll
-        for (int by = 0; by < 4; ++by)
-          if (ym & (1u << by)) bm |= xm << (2 * by);
-        s_bm[tid] = (unsigned char)bm;
+        for (int by = 0; by < S::kBY; ++by)
+          if (ym & (1u << by)) bm |= xm << (S::kBX * by);
+        s_bm[jj] = (unsigned char)bm;
       }
       __syncthreads();
-      const int nb = min(kBlendBatch, L - b0);
+      const int nb = min(BATCH, L - b0);
       for (int c0 = 0; c0 < nb; c0 += kChunk) {
         const int jg0 = b0 + c0;
         const long long chunk = cb + (jg0 >> 5);
@@ -170,10 +186,10 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
         // entries of this chunk whose cutoff box reaches this warp's block (warp-uniform)
         const unsigned rel = __ballot_sync(0xffffffffu, lane < ce && ((s_bm[c0 + lane] >> warp) & 1u));
         if (done) {  // stopped pixels still record an empty mask: the backward reads every chunk
-          cmask[chunk * kTilePix + tid] = 0u;
+          cmask[chunk * kPix + tid] = 0u;
           continue;
         }
-        if (jg0 > 0) ckpt[chunk * kTilePix + tid] = make_float4(T, C0, C1, C2);
+        if (jg0 > 0) ckpt[chunk * kPix + tid] = make_float4(T, C0, C1, C2);
         // candidates: alpha may reach 1/255 (independent iterations -> pipelined)
         unsigned cand = 0u;
         unsigned rl = rel;
@@ -210,11 +226,11 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
           ++gp;
           mask |= 1u << q;
         }
-        cmask[chunk * kTilePix + tid] = mask;
+        cmask[chunk * kPix + tid] = mask;
       }
     }
     // chunks whose masks K6 wrote for every pixel of the tile (the rest the backward skips)
-    if (tid == 0) tile_chunks[t] = min((L + kChunk - 1) / kChunk, batches * (kBlendBatch / kChunk));
+    if (tid == 0) tile_chunks[t] = min((L + kChunk - 1) / kChunk, batches * (BATCH / kChunk));
     if (inside) {
       const long long HW = (long long)V.W * V.H;
       const long long pix = (long long)py * V.W + px;
@@ -253,7 +269,7 @@ __global__ void __launch_bounds__(kTilePix, 4) k_blend_forward(
   if (tid == 0) {
     unsigned long long s = 0, b = 0, gn = 0, gq = 0;
 #pragma unroll
-    for (int w = 0; w < kTilePix / 32; ++w) {
+    for (int w = 0; w < S::kWarps; ++w) {
       s += s_pairs[w];
       b += s_blend[w];
       gn += s_gpn[w];
@@ -273,15 +289,71 @@ void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const
   k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order, ctl);
 }
 
-void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+namespace {
+// Resident CTAs per SM of one K6 instance (persistent grid = that x SMs), set at start-up.
+template <int TW, int TH, int BATCH>
+int& fwd_occupancy() {
+  static int occ = 0;
+  return occ;
+}
+
+template <int TW, int TH, int BATCH>
+void init_forward_instance() {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_forward<TW, TH, BATCH>, TW * TH, 0) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  fwd_occupancy<TW, TH, BATCH>() = occ > 0 ? occ : 1;
+}
+
+template <int TW, int TH, int BATCH>
+void launch_forward_instance(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+                             const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
+                             const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
+                             unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
+  long long grid = (long long)num_sms * fwd_occupancy<TW, TH, BATCH>();
+  if (grid > n_tiles) grid = n_tiles;
+  k_blend_forward<TW, TH, BATCH><<<(unsigned)grid, TW * TH, 0, s>>>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl,
+                                                                   order, image, T, last, gp, ckpt, cmask, chunk_tile,
+                                                                   tile_chunks);
+}
+}  // namespace
+
+// The compiled (tile shape, batch) instances; the first is the default.
+#define GS_TILINGS(X) X(16, 16, 256) X(16, 16, 128) X(16, 8, 256) X(16, 8, 128) X(8, 8, 128) X(8, 8, 64) X(32, 8, 256)
+
+int tiling_candidates(Tiling* out, int cap) {
+  int n = 0;
+#define GS_LIST(W, H, B)            \
+  if (n < cap && out) out[n] = Tiling{W, H, B}; \
+  ++n;
+  GS_TILINGS(GS_LIST)
+#undef GS_LIST
+  return n;
+}
+
+bool tiling_supported(const Tiling& t) {
+#define GS_SUP(W, H, B) \
+  if (t.tw == W && t.th == H && t.batch == B) return true;
+  GS_TILINGS(GS_SUP)
+#undef GS_SUP
+  return false;
+}
+
+void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
                           unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  long long grid = (long long)num_sms * 6;
-  if (grid > n_tiles) grid = n_tiles;
-  k_blend_forward<<<(unsigned)grid, kTilePix, 0, s>>>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image,
-                                                       T, last, gp, ckpt, cmask, chunk_tile, tile_chunks);
+#define GS_FWD(W, H, B)                                                                                              \
+  if (tl.tw == W && tl.th == H && tl.batch == B) {                                                                  \
+    launch_forward_instance<W, H, B>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image, T, last, gp, \
+                                     ckpt, cmask, chunk_tile, tile_chunks, num_sms, s);                           \
+    return;                                                                                                        \
+  }
+  GS_TILINGS(GS_FWD)
+#undef GS_FWD
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -289,9 +361,10 @@ void launch_blend_forward(const ViewDev* views, int n_views, long long n_tiles, 
 // ---------------------------------------------------------------------------------------------
 constexpr int kBwdWarps = 4;
 
+template <int PIX>
 struct BwdWarp {
   float4 a[kChunk], b[kChunk], c[kChunk];  // the chunk's Gaussians (records A, B, C)
-  uint2 act[kTilePix];                     // compacted (slot, mask) of the pixels to visit
+  uint2 act[PIX];                          // compacted (slot, mask) of the pixels to visit
   float4 pix[32];                          // per lane of the round: dL/dC (3), pixel x | y << 16
   float pT[kChunk][33];                    // per (Gaussian, lane): transmittance in front
   float pD[kChunk][33];                    // per (Gaussian, lane): dL/dC . (colour behind)
@@ -323,6 +396,7 @@ __device__ __forceinline__ void pair_grad(const float4& xy, const float4& co, co
   }
 }
 
+template <int TW, int TH>
 __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
     const unsigned* __restrict__ vals, const ProjBuffers pb, Control* __restrict__ ctl,
@@ -331,7 +405,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     float4* __restrict__ ginst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BwdWarp& S = reinterpret_cast<BwdWarp*>(smem_raw)[warp];
+  using Sh = Shape<TW, TH>;
+  constexpr int kPix = Sh::kPix;
+  BwdWarp<kPix>& S = reinterpret_cast<BwdWarp<kPix>*>(smem_raw)[warp];
   if (ctl->overflow) return;
   const unsigned long long M = ctl->m_total;
   const long long n_ids = (long long)(M >> 5) + n_tiles + 1;
@@ -374,9 +450,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     if (k < tile_chunks[t]) {
       // compact the pixels that blended at least one Gaussian of this chunk
 #pragma unroll
-      for (int r = 0; r < kTilePix / 32; ++r) {
+      for (int r = 0; r < kPix / 32; ++r) {
         const int slot = r * 32 + lane;
-        const unsigned mask = cmask[cid * kTilePix + slot];
+        const unsigned mask = cmask[cid * kPix + slot];
         const unsigned ball = __ballot_sync(0xffffffffu, mask != 0u);
         if (mask) S.act[n_act + __popc(ball & lt)] = make_uint2((unsigned)slot, mask);
         n_act += __popc(ball);
@@ -403,14 +479,14 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
       int px = 0, py = 0;
       if (mask) {
         int ox, oy;
-        slot_xy((int)pm.x, ox, oy);
-        px = tx * kTile + ox;
-        py = ty * kTile + oy;
+        Sh::slot_xy((int)pm.x, ox, oy);
+        px = tx * TW + ox;
+        py = ty * TH + oy;
         const long long pix = (long long)py * V.W + px;
         d0 = dimg[pix];
         d1 = dimg[HW + pix];
         d2 = dimg[2 * HW + pix];
-        const float4 ck = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[cid * kTilePix + pm.x];
+        const float4 ck = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[cid * kPix + pm.x];
         float T = ck.x, F0 = ck.y, F1 = ck.z, F2 = ck.w;
         const float P0 = img[pix], P1 = img[HW + pix], P2 = img[2 * HW + pix];
         const float pxf = (float)px, pyf = (float)py;
@@ -461,17 +537,44 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
   }
 }
 
-void init_blend_attributes() {
-  cudaFuncSetAttribute(k_blend_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(BwdWarp) * kBwdWarps));
+namespace {
+template <int TW, int TH>
+void init_backward_instance() {
+  cudaFuncSetAttribute(k_blend_backward<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(BwdWarp<TW * TH>) * kBwdWarps));
 }
 
-void launch_blend_backward(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+template <int TW, int TH>
+void launch_backward_instance(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
+                              const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
+                              const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
+                              const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
+  k_blend_backward<TW, TH><<<num_sms * 4, kBwdWarps * 32, sizeof(BwdWarp<TW * TH>) * kBwdWarps, s>>>(
+      views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, chunk_tile, tile_chunks, ginst);
+}
+}  // namespace
+
+void init_blend_attributes() {
+#define GS_INIT(W, H, B)              \
+  init_forward_instance<W, H, B>();   \
+  init_backward_instance<W, H>();
+  GS_TILINGS(GS_INIT)
+#undef GS_INIT
+}
+
+void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
                            const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
-  k_blend_backward<<<num_sms * 4, kBwdWarps * 32, sizeof(BwdWarp) * kBwdWarps, s>>>(
-      views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, chunk_tile, tile_chunks, ginst);
+  // the backward depends on the tile shape only
+#define GS_BWD(W, H, B)                                                                                          \
+  if (tl.tw == W && tl.th == H) {                                                                               \
+    launch_backward_instance<W, H>(views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, \
+                                   chunk_tile, tile_chunks, ginst, num_sms, s);                                \
+    return;                                                                                                    \
+  }
+  GS_TILINGS(GS_BWD)
+#undef GS_BWD
 }
 
 }  // namespace gs

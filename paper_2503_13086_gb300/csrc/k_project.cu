@@ -209,13 +209,14 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ param
   const float mid = 0.5f * (g.cov[0] + g.cov[2]);
   const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
   const int r = (int)ceilf(3.f * sqrtf(lam));
-  // Tile rectangle: [floor((u - r)/16), floor((u + r + 15)/16)) clamped to the grid, the same
-  // fp32 expression the key emission and its checks use.
+  // Tile rectangle: [floor((u - r)/tw), floor((u + r + tw - 1)/tw)) clamped to the grid, same for
+  // y with th, in fp32 (the expression the key emission and its checks use).
   const float rf = (float)r;
-  int x0 = (int)floorf(__fdiv_rn(__fsub_rn(u, rf), (float)kTile));
-  int y0 = (int)floorf(__fdiv_rn(__fsub_rn(vv, rf), (float)kTile));
-  int x1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, rf), (float)(kTile - 1)), (float)kTile));
-  int y1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(vv, rf), (float)(kTile - 1)), (float)kTile));
+  const float twf = (float)V.tw, thf = (float)V.th;
+  int x0 = (int)floorf(__fdiv_rn(__fsub_rn(u, rf), twf));
+  int y0 = (int)floorf(__fdiv_rn(__fsub_rn(vv, rf), thf));
+  int x1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(u, rf), (float)(V.tw - 1)), twf));
+  int y1 = (int)floorf(__fdiv_rn(__fadd_rn(__fadd_rn(vv, rf), (float)(V.th - 1)), thf));
   x0 = min(V.gx, max(0, x0));
   x1 = min(V.gx, max(0, x1));
   y0 = min(V.gy, max(0, y0));
@@ -320,6 +321,7 @@ struct AdamArgs {
 template <int N>
 __device__ __forceinline__ void apply_rows(const AdamArgs& A, int c0, const int* grp, int i, const float* g,
                                            const float* pcur) {
+  if (A.adam == 2) return;  // timing run of the autotuner: gradients computed, nothing written
   if (!A.adam) {
 #pragma unroll
     for (int r = 0; r < N; ++r) A.grads_out[(long long)(c0 + r) * A.stride + i] = g[r];

@@ -34,13 +34,16 @@ class StreamingSession:
     def arrive(self, cam, target, pts_xyz=None, pts_rgb=None, tracks=None, arrival_time=None):
         """Integrate one image; returns its record (latency, steps, loss, new Gaussians, pairs)."""
         t0 = time.perf_counter() if arrival_time is None else arrival_time
+        ta = time.perf_counter()
         n0 = self.field.stats()["n_gaussians"]
         img = self.field.add_image(cam, target, pts_xyz, pts_rgb, tracks)
         n1 = self.field.stats()["n_gaussians"]
+        tb = time.perf_counter()
         st = self.field.integrate(img) if n1 > 0 else dict(iterations=0, steps=0, key_images=0, mean_loss=0.0,
                                                               pairs=0)
         t1 = time.perf_counter()
-        rec = dict(image_id=img, latency_s=t1 - t0, new_gaussians=n1 - n0, n_gaussians=n1, **st)
+        rec = dict(image_id=img, latency_s=t1 - t0, add_image_s=tb - ta, integrate_s=t1 - tb, new_gaussians=n1 - n0,
+                   n_gaussians=n1, **st)
         self.results.append(rec)
         return rec
 

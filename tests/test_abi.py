@@ -41,3 +41,16 @@ def test_host_only_calls_without_a_gpu():
     # argument checks fail cleanly with a status and a message, no GPU touched
     assert lib.gs_field_init(None, None, None) == 1
     assert b"NULL" in lib.gs_last_error()
+
+
+def test_tiling_candidates_on_the_host():
+    import paper_2503_13086_gb300 as gs
+    cands = gs.tiling_candidates()
+    assert cands[0] == (16, 16, 256)  # the 3DGS tile, the default
+    assert len(set(cands)) == len(cands) <= gs.MAX_TILINGS
+    for tw, th, b in cands:
+        # whole 8 x 4 warp blocks, at most 256 pixels (one thread each), whole 32-entry chunks
+        assert tw % 8 == 0 and th % 4 == 0 and 32 <= tw * th <= 256 and b % 32 == 0
+    cfg = gs.FieldConfig()
+    gs.load().gs_field_config_default(ctypes.byref(cfg))
+    assert cfg.tiling.astuple() == (0, 0, 0)  # autotuned by default

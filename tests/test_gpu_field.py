@@ -20,6 +20,7 @@ C0 = 0.5 * math.sqrt(1.0 / math.pi)
 def make_field(**kw):
     import paper_2503_13086_gb300 as gs
     kw.setdefault("scene_extent", 1.0)
+    kw.setdefault("tiling", (16, 16, 256))  # the oracle's default binning; bitwise comparisons
     return gs.Field(**kw)
 
 
@@ -169,4 +170,34 @@ def test_budget_and_bad_arguments():
     with pytest.raises(gs.GSError) as e:
         f.optimize_step([0])
     assert e.value.status in (1, 7)
+    f.close()
+
+
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_multi_view_step_matches_oracle(scaling):
+    """A step over three views at mixed sizes (R13: mean loss, one Adam step at the mean of the
+    views' Eq. 8 rates); with batch_scaling every rate is x sqrt(3) and the betas are cubed."""
+    p = gi.cube_scene(3000, seed=12, stride=3008)
+    cams = [gi.identity_camera(96, 64, 90.0), gi.identity_camera(70, 52, 60.0)]
+    R, t = gi.look_at([0.4, -0.3, -0.4], [0.0, 0.0, 3.0])
+    cams.append(gi.camera_dict(R, t, 70.0, 70.0, 40.0, 30.0, 81, 61))
+    tg = [gi.uniform_target(c["width"], c["height"], 20 + k) for k, c in enumerate(cams)]
+    f = make_field(use_graph=0, batch_scaling=scaling)
+    f.set_gaussians(p[:, :3000])
+    ids = [f.add_image(c, t) for c, t in zip(cams, tg)]
+    lr = float(np.mean([f.image_lr(i) for i in ids]))
+    loss = f.optimize_step(ids)
+    got = f.get_gaussians()
+    L, g, _ = oracle.loss_and_grad(p, [ocam(c) for c in cams], tg, lam=0.2, prec="f32", n=3000)
+    assert abs(loss - L) <= 1e-5 * max(1.0, abs(L))
+    s = math.sqrt(3.0) if scaling else 1.0
+    b1, b2 = (0.9 ** 3, 0.999 ** 3) if scaling else (0.9, 0.999)
+    lrs = [s * lr] + [s * x for x in LRS_REST]
+    ref = p.copy()
+    oracle.adam(ref, g, np.zeros_like(p), np.zeros_like(p), lrs, 1, b1=b1, b2=b2, prec="f32", n=3000)
+    groups = [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 59)]
+    for (a, b), lrg in zip(groups, lrs):
+        d = np.abs(got[a:b] - ref[a:b, :3000])
+        bad = d > 1e-3 * lrg + 1e-6
+        assert bad.mean() < 2e-3, (a, b, bad.mean())
     f.close()

@@ -58,7 +58,7 @@ def test_load_balance_statistic_matches_oracle():
     n = 4096
     p = gi.cube_scene(n, seed=9, stride=n)
     cam = gi.identity_camera(256, 256, 256.0)
-    f = gs.Field(scene_extent=1.0)
+    f = gs.Field(scene_extent=1.0, tiling=(16, 16, 256))
     f.set_gaussians(p)
     img = f.add_image(cam, gi.uniform_target(256, 256, 3))
     f.optimize_step([img])

@@ -112,7 +112,8 @@ def psnr_oracle(params, cams, targets):
 def test_streaming_psnr_matches_oracle_driven_run():
     from paper_2503_13086_gb300.streaming import StreamingSession
     gt, cams, targets, pts = reduced_session()
-    cfg = dict(T_I=8, N_m=3, T_a=16, seed=5, add_dist_thresh=0.05, scene_extent=2.0, batch_views=1, use_graph=1)
+    cfg = dict(T_I=8, N_m=3, T_a=16, seed=5, add_dist_thresh=0.05, scene_extent=2.0, batch_views=1, use_graph=1,
+               tiling=(16, 16, 256))
     sess = StreamingSession(**cfg)
     ors = OracleSession(T_I=8, N_m=3, T_a=16, seed=5, thr=0.05, extent=2.0)
     for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
@@ -139,7 +140,7 @@ def _stream_run(batch, graph, asyn):
     targets = [tgt_field.render(c) for c in cams]
     tgt_field.close()
     sess = StreamingSession(T_I=24, N_m=4, batch_views=batch, use_graph=graph, async_steps=asyn, scene_extent=7.0,
-                            seed=1)
+                            seed=1, tiling=(16, 16, 256))
     for k, (c, t) in enumerate(zip(cams, targets)):
         xyz, rgb, tr = gi.sparse_points(gt, 20000, c, 1500, seed=k)
         r = sess.arrive(c, t, xyz, rgb, tr)
@@ -178,7 +179,7 @@ def small_scene_requests(seed, n_images=4, W=96, H=64):
 
 def test_serving_results_same_alone_and_in_the_mix():
     from paper_2503_13086_gb300.serving import Scene, Server
-    cfg = dict(T_I=12, N_m=3, batch_views=2, use_graph=1, scene_extent=7.0, seed=2)
+    cfg = dict(T_I=12, N_m=3, batch_views=2, use_graph=1, scene_extent=7.0, seed=2, tiling=(16, 16, 256))
     scenes = {s: small_scene_requests(s) for s in (1, 2, 3)}
     alone = {}
     for sid, reqs in scenes.items():
