@@ -19,6 +19,7 @@ std::mutex& alloc_capture_mutex();
 
 void init_sort_attributes();
 void init_blend_attributes();
+void init_loss_attributes();
 
 // A device allocation that only grows.
 struct DevBuf {

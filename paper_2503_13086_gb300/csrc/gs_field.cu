@@ -54,68 +54,6 @@ struct Image {
   int T = 0;                      // iterations trained (Eq. 7)
 };
 
-// Uniform hash grid over the sparse points (stands in for the search tree of Sec. IV-B).
-struct PointGrid {
-  float cell = 1.f;
-  std::unordered_map<long long, std::vector<int>> cells;
-  std::vector<float> xyz;
-  static long long key(long long ix, long long iy, long long iz) {
-    return ((ix & 0x1FFFFF) << 42) | ((iy & 0x1FFFFF) << 21) | (iz & 0x1FFFFF);
-  }
-  long long cidx(float v) const { return (long long)std::floor(v / cell); }
-  void insert(const float* p) {
-    const int id = (int)(xyz.size() / 3);
-    xyz.insert(xyz.end(), p, p + 3);
-    cells[key(cidx(p[0]), cidx(p[1]), cidx(p[2]))].push_back(id);
-  }
-  // squared distance to the nearest point within one cell ring (inf if none)
-  float nearest2_ring1(const float* p) const {
-    const long long cx = cidx(p[0]), cy = cidx(p[1]), cz = cidx(p[2]);
-    float best = INFINITY;
-    for (long long a = -1; a <= 1; ++a)
-      for (long long b = -1; b <= 1; ++b)
-        for (long long c = -1; c <= 1; ++c) {
-          auto it = cells.find(key(cx + a, cy + b, cz + c));
-          if (it == cells.end()) continue;
-          for (int id : it->second) {
-            const float dx = xyz[3 * id] - p[0], dy = xyz[3 * id + 1] - p[1], dz = xyz[3 * id + 2] - p[2];
-            best = std::min(best, dx * dx + dy * dy + dz * dz);
-          }
-        }
-    return best;
-  }
-  // mean squared distance to the k nearest other points (expanding shells of cells)
-  float knn_mean2(const float* p, int self, int k) const {
-    const long long cx = cidx(p[0]), cy = cidx(p[1]), cz = cidx(p[2]);
-    std::vector<float> best;
-    for (int r = 0; r < 64; ++r) {
-      for (long long a = -r; a <= r; ++a)
-        for (long long b = -r; b <= r; ++b)
-          for (long long c = -r; c <= r; ++c) {
-            if (std::max({std::llabs(a), std::llabs(b), std::llabs(c)}) != r) continue;
-            auto it = cells.find(key(cx + a, cy + b, cz + c));
-            if (it == cells.end()) continue;
-            for (int id : it->second) {
-              if (id == self) continue;
-              const float dx = xyz[3 * id] - p[0], dy = xyz[3 * id + 1] - p[1], dz = xyz[3 * id + 2] - p[2];
-              best.push_back(dx * dx + dy * dy + dz * dz);
-            }
-          }
-      if ((int)best.size() >= k) {
-        std::partial_sort(best.begin(), best.begin() + k, best.end());
-        const float reach = (float)r * cell;  // every point within this distance has been seen
-        if (best[k - 1] <= reach * reach) break;
-      }
-    }
-    if (best.empty()) return 1e-7f;
-    const int m = std::min(k, (int)best.size());
-    std::partial_sort(best.begin(), best.begin() + m, best.end());
-    float s = 0.f;
-    for (int q = 0; q < m; ++q) s += best[q];
-    return std::max(s / (float)m, 1e-7f);
-  }
-};
-
 // A captured step bakes in every device address and workspace layout it touches; the key holds
 // all of them so any reallocation or layout change forces a new capture.
 struct GraphKey {
@@ -177,8 +115,13 @@ struct Field {
   long long adam_step = 0;
   std::vector<Image> images;
   std::vector<std::vector<float>> M;  // overlap matrix
-  PointGrid grid;
+  // sparse points of all registered images, hashed by cells (the field update of Sec. IV-B)
+  DevBuf pts_xyz, pts_next, grid_keys, grid_head, new_rgb, far_flags, far_off, far_count;
+  long long n_points = 0;
+  unsigned grid_slots = 0;
+  float grid_cell = 1.f;
   bool grid_ready = false;
+  unsigned* count_h = nullptr;  // pinned
   // per-step buffers
   DevBuf step_img, step_last, step_dimg, step_T, step_gp;
   std::vector<GraphEntry> graphs;
@@ -216,6 +159,67 @@ struct Field {
     snap_p.release(&own_bytes);
     snap_m.release(&own_bytes);
     snap_v.release(&own_bytes);
+    DevBuf* pts[] = {&pts_xyz, &pts_next, &grid_keys, &grid_head, &new_rgb, &far_flags, &far_off, &far_count};
+    for (DevBuf* b : pts) b->release(&own_bytes);
+    if (count_h) cudaFreeHost(count_h);
+  }
+
+  PointGridDev grid_dev() const {
+    PointGridDev g;
+    g.xyz = static_cast<const float*>(pts_xyz.p);
+    g.keys = static_cast<unsigned long long*>(grid_keys.p);
+    g.head = static_cast<int*>(grid_head.p);
+    g.next = static_cast<const int*>(pts_next.p);
+    g.mask = grid_slots ? grid_slots - 1u : 0u;
+    g.cell = grid_cell;
+    return g;
+  }
+
+  // Room for `want` sparse points: the point arrays keep their contents; a larger hash table is
+  // rebuilt from every point registered so far.
+  gs_status reserve_points(long long want) {
+    gs_status s;
+    if ((long long)(pts_xyz.bytes / 12) < want) {
+      const long long cap = std::max<long long>(want, std::max<long long>(2 * (long long)(pts_xyz.bytes / 12), 65536));
+      const size_t grow = (size_t)cap * 16 - pts_xyz.bytes - pts_next.bytes;
+      if (cfg.hbm_budget_bytes && bytes_in_use() + grow > cfg.hbm_budget_bytes)
+        return fail(GS_ERR_BUDGET, "registering the sparse points would exceed hbm_budget_bytes");
+      DevBuf nx, nn;
+      if ((s = nx.reserve((size_t)cap * 12, &own_bytes)) || (s = nn.reserve((size_t)cap * 4, &own_bytes))) {
+        nx.release(&own_bytes);
+        nn.release(&own_bytes);
+        return s;
+      }
+      if (n_points > 0) {
+        cudaMemcpyAsync(nx.p, pts_xyz.p, (size_t)n_points * 12, cudaMemcpyDeviceToDevice, stream);
+        cudaMemcpyAsync(nn.p, pts_next.p, (size_t)n_points * 4, cudaMemcpyDeviceToDevice, stream);
+      }
+      cudaStreamSynchronize(stream);
+      pts_xyz.release(&own_bytes);
+      pts_next.release(&own_bytes);
+      pts_xyz = nx;
+      pts_next = nn;
+    }
+    if ((long long)grid_slots < 2 * want) {
+      unsigned long long slots = 1024;
+      while ((long long)slots < 2 * want) slots <<= 1;
+      if (slots > (1ull << 31)) return fail(GS_ERR_CAPACITY, "too many sparse points");
+      const size_t bytes = (size_t)slots * 12;
+      const size_t have = grid_keys.bytes + grid_head.bytes;
+      if (cfg.hbm_budget_bytes && bytes > have && bytes_in_use() + (bytes - have) > cfg.hbm_budget_bytes)
+        return fail(GS_ERR_BUDGET, "growing the point grid would exceed hbm_budget_bytes");
+      grid_keys.release(&own_bytes);
+      grid_head.release(&own_bytes);
+      if ((s = grid_keys.reserve((size_t)slots * 8, &own_bytes)) || (s = grid_head.reserve((size_t)slots * 4, &own_bytes))) {
+        grid_slots = 0;
+        return s;
+      }
+      grid_slots = (unsigned)slots;
+      cudaMemsetAsync(grid_keys.p, 0xFF, (size_t)slots * 8, stream);
+      cudaMemsetAsync(grid_head.p, 0xFF, (size_t)slots * 4, stream);
+      launch_insert_points(grid_dev(), static_cast<int*>(pts_next.p), 0, n_points, stream);
+    }
+    return GS_OK;
   }
 
   std::vector<unsigned long long> signature() const {
@@ -943,47 +947,57 @@ gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int
     f->M[i][id] = m;
     f->M[id][i] = m;
   }
-  // Field update (Sec. IV-B): points farther than the threshold from every existing sparse
-  // point become new Gaussians.
+  // Field update (Sec. IV-B), on the device: points farther than the threshold from every earlier
+  // sparse point become new Gaussians (3DGS initialisation); all of the image's points then join
+  // the sparse set.
   float thr = f->cfg.add_dist_thresh > 0.f ? f->cfg.add_dist_thresh : 0.01f * f->scene_extent();
   if (!f->grid_ready) {
-    f->grid.cell = std::max(thr, 1e-6f);
+    f->grid_cell = std::max(thr, 1e-6f);
     f->grid_ready = true;
   }
-  std::vector<int> fresh;
-  for (int k = 0; k < n_pts; ++k) {
-    const float* p = pts_xyz + 3 * k;
-    if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]))) continue;
-    const float d2 = f->grid.nearest2_ring1(p);
-    if (!(d2 <= thr * thr)) fresh.push_back(k);
-  }
-  const int first_pt = (int)(f->grid.xyz.size() / 3);
-  for (int k = 0; k < n_pts; ++k) f->grid.insert(pts_xyz + 3 * k);
-  if (!fresh.empty()) {
-    s = f->reserve_gaussians((long long)f->n + (long long)fresh.size());
-    if (s) {
+  if (n_pts > 0) {
+    if (!f->count_h && cudaMallocHost(&f->count_h, sizeof(unsigned)) != cudaSuccess) {
+      f->count_h = nullptr;
+      return fail(GS_ERR_OOM, "pinned allocation failed");
+    }
+    if ((s = f->reserve_points(f->n_points + n_pts)) || (s = f->new_rgb.reserve((size_t)n_pts * 12, &f->own_bytes)) ||
+        (s = f->far_flags.reserve((size_t)n_pts * 4, &f->own_bytes)) ||
+        (s = f->far_off.reserve((size_t)n_pts * 4, &f->own_bytes)) || (s = f->far_count.reserve(4, &f->own_bytes))) {
       if (out_id) *out_id = id;
       return s;
     }
-    const int nn = (int)fresh.size();
-    std::vector<float> cols((size_t)gs::kNumParams * nn, 0.f);
-    const double C0 = 0.5 * std::sqrt(1.0 / 3.14159265358979323846);
-    for (int q = 0; q < nn; ++q) {
-      const int k = fresh[q];
-      const float* p = pts_xyz + 3 * k;
-      for (int a = 0; a < 3; ++a) cols[(size_t)a * nn + q] = p[a];
-      const float d2 = f->grid.knn_mean2(p, first_pt + k, 3);
-      const float ls = std::log(std::sqrt(d2));
-      for (int a = 0; a < 3; ++a) cols[(size_t)(3 + a) * nn + q] = ls;
-      cols[(size_t)6 * nn + q] = 1.f;
-      cols[(size_t)10 * nn + q] = (float)std::log(0.1 / 0.9);
-      for (int ch = 0; ch < 3; ++ch) cols[(size_t)(11 + ch) * nn + q] = (float)((pts_rgb[3 * k + ch] - 0.5) / C0);
+    float* xyz_new = static_cast<float*>(f->pts_xyz.p) + 3 * f->n_points;
+    cudaMemcpyAsync(xyz_new, pts_xyz, (size_t)n_pts * 12, cudaMemcpyHostToDevice, f->stream);
+    cudaMemcpyAsync(f->new_rgb.p, pts_rgb, (size_t)n_pts * 12, cudaMemcpyHostToDevice, f->stream);
+    const gs::PointGridDev g = f->grid_dev();
+    const int ring = (int)std::min(16.f, std::max(1.f, std::ceil(thr / f->grid_cell)));
+    unsigned* far = static_cast<unsigned*>(f->far_flags.p);
+    unsigned* off = static_cast<unsigned*>(f->far_off.p);
+    gs::launch_far_points(g, xyz_new, n_pts, thr * thr, ring, far, f->stream);
+    gs::launch_insert_points(g, static_cast<int*>(f->pts_next.p), f->n_points, n_pts, f->stream);
+    gs::launch_scan_flags(far, n_pts, off, static_cast<unsigned*>(f->far_count.p), f->stream);
+    cudaMemcpyAsync(f->count_h, f->far_count.p, sizeof(unsigned), cudaMemcpyDeviceToHost, f->stream);
+    e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("field update: ") + cudaGetErrorString(e));
+    const long long first_pt = f->n_points;
+    f->n_points += n_pts;
+    const unsigned fresh = *f->count_h;
+    if (fresh > 0) {
+      s = f->reserve_gaussians((long long)f->n + (long long)fresh);
+      if (s) {
+        if (out_id) *out_id = id;
+        return s;
+      }
+      const double C0 = 0.5 * std::sqrt(1.0 / 3.14159265358979323846);
+      gs::launch_init_gaussians(f->grid_dev(), xyz_new, static_cast<const float*>(f->new_rgb.p), n_pts, first_pt, far,
+                                off, static_cast<float*>(f->params.p), static_cast<float*>(f->adam_m.p),
+                                static_cast<float*>(f->adam_v.p), f->stride, f->n, (float)std::log(0.1 / 0.9), C0,
+                                f->stream);
+      e = cudaStreamSynchronize(f->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("field update: ") + cudaGetErrorString(e));
+      f->n += (int)fresh;
     }
-    e = cudaMemcpy2DAsync(static_cast<float*>(f->params.p) + f->n, (size_t)f->stride * 4, cols.data(), (size_t)nn * 4,
-                          (size_t)nn * 4, gs::kNumParams, cudaMemcpyHostToDevice, f->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
-    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
-    f->n += nn;
   } else {
     cudaStreamSynchronize(f->stream);
   }

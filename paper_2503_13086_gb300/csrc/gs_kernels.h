@@ -67,6 +67,23 @@ void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, 
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
                            const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s);
 
+// Field update (Sec. IV-B): the registered sparse points, hashed by cubic cells.
+struct PointGridDev {
+  const float* xyz;           // 3 floats per point
+  unsigned long long* keys;   // per slot: cell key, ~0 = empty
+  int* head;                  // per slot: first point of the cell, -1 = none
+  const int* next;            // per point: next point of its cell, -1 = end
+  unsigned mask;              // slots - 1 (slots a power of two, at least twice the points)
+  float cell;                 // cell edge
+};
+void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float thr2, int ring, unsigned* far,
+                       cudaStream_t s);
+void launch_insert_points(const PointGridDev& g, int* next, long long first, long long count, cudaStream_t s);
+void launch_scan_flags(const unsigned* far, int n, unsigned* offsets, unsigned* count, cudaStream_t s);
+void launch_init_gaussians(const PointGridDev& g, const float* xyz, const float* rgb, int n_new, long long self0,
+                           const unsigned* far, const unsigned* offsets, float* params, float* m, float* v, int stride,
+                           int n0, float opacity_logit, double sh_c0, cudaStream_t s);
+
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,

@@ -77,6 +77,7 @@ static void init_attributes_once() {
   if (done) return;
   init_sort_attributes();
   init_blend_attributes();
+  init_loss_attributes();
   done = true;
 }
 

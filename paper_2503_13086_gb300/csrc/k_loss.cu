@@ -4,14 +4,16 @@
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
 // views, the loss is the mean of the per-view losses.  The window is separable: each CTA stages
-// a 32 x 32 output block plus a 5-pixel halo in shared memory, blurs rows then columns.
+// a 32 x 32 output block plus a 5-pixel halo in shared memory, blurs rows then columns.  The
+// staging is asynchronous (cp.async, zero-filled outside the image) and double-buffered: the
+// next channel's block is in flight while the current one is blurred.
 //   pass 1 (k_loss_forward): the five window moments -> SSIM map, the three partial derivatives
 //          of SSIM with respect to (mu_x, E[x^2], E[xy]) per pixel, and per-CTA sums;
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
 //          symmetric, so the adjoint of the blur is the blur) gives dL/dx.
 // The last CTA of pass 1 reduces the per-CTA sums in a fixed order: the loss is deterministic.
 #include "gs_device.cuh"
-#include "gs_kernels.h"
+#include "gs_engine.h"
 
 namespace gs {
 
@@ -39,6 +41,39 @@ __device__ __forceinline__ int view_of_block(const ViewDev* __restrict__ views, 
   return v;
 }
 
+// 4-byte asynchronous copy global -> shared; ok == false writes 0 (reads nothing).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = ok ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage MAPS planes (W x H each) of the 42 x 42 block at (ox - 5, oy - 5) into dst[m] (rows of
+// kSXP floats); outside the image (and the pad columns) become 0.  Warp w takes rows w, w + 8,
+// ...; its lanes the columns.
+template <int MAPS>
+__device__ __forceinline__ void stage_block(float (*dst)[kSY][kSXP], const float* const (&src)[MAPS], int ox, int oy,
+                                            int W, int H) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < kSY; r += 8) {
+    const int gy = oy + r - kR;
+    const bool row_ok = gy >= 0 && gy < H;
+    for (int c = lane; c < kSXP; c += 32) {
+      const int gx = ox + c - kR;
+      const bool ok = row_ok && c < kSX && gx >= 0 && gx < W;
+      const long long pix = ok ? (long long)gy * W + gx : 0;
+#pragma unroll
+      for (int m = 0; m < MAPS; ++m) cp_async4(&dst[m][r][c], src[m] + pix, ok);
+    }
+  }
+  cp_async_commit();
+}
+
 // 16 consecutive values of a padded shared row starting at a multiple of 4
 __device__ __forceinline__ void load16(const float* row, int c0, float o[16]) {
   const float4* r4 = reinterpret_cast<const float4*>(row + c0);
@@ -57,14 +92,22 @@ long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * 
 
 // Each thread blurs 4 adjacent outputs per pass (row segment, then column segment) from 14
 // staged values per map, so a staged value is read once per 4 outputs.
+struct LossFwdSmem {
+  float in[2][2][kSY][kSXP];  // [buffer][x / y][row][col]
+  float hm[5][kSY][kBX];      // row-blurred moments
+};
+struct LossBwdSmem {
+  float in[2][3][kSY][kSXP];  // [buffer][partial][row][col]
+  float hb[3][kSY][kBX];
+};
+
 __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
                                                       long long n_blocks, const float* __restrict__ image,
                                                       const StepParams* __restrict__ sp,
                                                       float* __restrict__ partials, double* __restrict__ block_sums,
                                                       Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
-  __shared__ __align__(16) float sx[kSY][kSXP];
-  __shared__ __align__(16) float sy[kSY][kSXP];
-  __shared__ float hm[5][kSY][kBX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LossFwdSmem& S = *reinterpret_cast<LossFwdSmem*>(smem_raw);
   __shared__ double s_red[2][8];
   __shared__ bool s_last;
   if (ctl->overflow) return;
@@ -79,22 +122,28 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   const int ox = bx * kBX, oy = by * kBY;
   const long long HW = (long long)V.W * V.H;
   const float* X = image + 3 * V.pix_base;
-  const float* Yt = V.target;
   float* P = partials + 9 * V.pix_base;
+  const float* Yt = V.target;
   double l1 = 0.0, ss = 0.0;
+  {
+    const float* const src[2] = {X, Yt};
+    stage_block<2>(S.in[0], src, ox, oy, V.W, V.H);
+  }
   for (int ch = 0; ch < 3; ++ch) {
-    for (int k = threadIdx.x; k < kSY * kSXP; k += blockDim.x) {
-      const int r = k / kSXP, c = k % kSXP;
-      const int gy = oy + r - kR, gx = ox + c - kR;
-      const bool in = c < kSX && gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
-      const long long pix = (long long)gy * V.W + gx;
-      sx[r][c] = in ? X[ch * HW + pix] : 0.f;
-      sy[r][c] = in ? Yt[ch * HW + pix] : 0.f;
+    const int cur = ch & 1;
+    if (ch < 2) {
+      const float* const src[2] = {X + (ch + 1) * HW, Yt + (ch + 1) * HW};
+      stage_block<2>(S.in[cur ^ 1], src, ox, oy, V.W, V.H);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    float (*sx)[kSXP] = S.in[cur][0];
+    float (*sy)[kSXP] = S.in[cur][1];
     // horizontal: 42 rows x 8 segments of 4 columns
     for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
-      const int r = task / (kBX / 4), c0 = (task % (kBX / 4)) * 4;
+      const int r = task >> 3, c0 = (task & 7) * 4;
       float xv[16], yv[16];
       load16(sx[r], c0, xv);
       load16(sy[r], c0, yv);
@@ -121,7 +170,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
 #pragma unroll
       for (int m = 0; m < 5; ++m)
 #pragma unroll
-        for (int o = 0; o < 4; ++o) hm[m][r][c0 + o] = acc[m][o];
+        for (int o = 0; o < 4; ++o) S.hm[m][r][c0 + o] = acc[m][o];
     }
     __syncthreads();
     // vertical: 32 columns x 8 segments of 4 rows
@@ -134,7 +183,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
         for (int o = 0; o < 4; ++o) mom[m][o] = 0.f;
 #pragma unroll
         for (int j = 0; j < 14; ++j) {
-          const float h = hm[m][r0 + j][c];
+          const float h = S.hm[m][r0 + j][c];
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             const int t = j - o;
@@ -142,6 +191,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
           }
         }
       }
+      float l1c = 0.f, ssc = 0.f;  // at most 4 terms per thread and channel: float is exact enough
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         const int gy = oy + r0 + o, gx = ox + c;
@@ -151,15 +201,17 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
         const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
         const float N = N1 * N2, D = D1 * D2;
         const float iD = 1.f / D;
-        ss += (double)(N * iD);
+        ssc += N * iD;
         const float dN = 2.f * my * N2 - 2.f * my * N1;
         const float dD = 2.f * mx * D2 - 2.f * mx * D1;
         const long long pix = (long long)gy * V.W + gx;
         P[(3 * ch + 0) * HW + pix] = (dN * D - N * dD) * iD * iD;  // dS/dmu_x
         P[(3 * ch + 1) * HW + pix] = -N * D1 * iD * iD;             // dS/dE[x^2]
         P[(3 * ch + 2) * HW + pix] = 2.f * N1 * iD;                 // dS/dE[xy]
-        l1 += (double)fabsf(sx[r0 + o + kR][c + kR] - sy[r0 + o + kR][c + kR]);
+        l1c += fabsf(sx[r0 + o + kR][c + kR] - sy[r0 + o + kR][c + kR]);
       }
+      l1 += (double)l1c;
+      ss += (double)ssc;
     }
     __syncthreads();
   }
@@ -243,8 +295,8 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
                                                        const StepParams* __restrict__ sp,
                                                        const float* __restrict__ partials,
                                                        const Control* __restrict__ ctl, float* __restrict__ dimage) {
-  __shared__ __align__(16) float sp3[3][kSY][kSXP];
-  __shared__ float hb[3][kSY][kBX];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LossBwdSmem& S = *reinterpret_cast<LossBwdSmem*>(smem_raw);
   if (ctl->overflow) return;
   float w[11];
   window(w);
@@ -263,22 +315,26 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   const float lam = sp->lambda_ssim;
   const float scale = 1.f / (3.f * (float)V.W * (float)V.H * (float)n_views);
   const float gl1 = (1.f - lam) * scale, gs = -lam * scale;
+  {
+    const float* const src[3] = {P, P + HW, P + 2 * HW};
+    stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);
+  }
   for (int ch = 0; ch < 3; ++ch) {
-    for (int k = threadIdx.x; k < kSY * kSXP; k += blockDim.x) {
-      const int r = k / kSXP, c = k % kSXP;
-      const int gy = oy + r - kR, gx = ox + c - kR;
-      const bool in = c < kSX && gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
-      const long long pix = (long long)gy * V.W + gx;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) sp3[m][r][c] = in ? P[(3 * ch + m) * HW + pix] : 0.f;
+    const int cur = ch & 1;
+    if (ch < 2) {
+      const float* const src[3] = {P + (3 * ch + 3) * HW, P + (3 * ch + 4) * HW, P + (3 * ch + 5) * HW};
+      stage_block<3>(S.in[cur ^ 1], src, ox, oy, V.W, V.H);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
     for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
-      const int r = task / (kBX / 4), c0 = (task % (kBX / 4)) * 4;
+      const int r = task >> 3, c0 = (task & 7) * 4;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         float pv[16];
-        load16(sp3[m][r], c0, pv);
+        load16(S.in[cur][m][r], c0, pv);
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < 14; ++j)
@@ -288,7 +344,7 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
             if (t >= 0 && t < 11) acc[o] += w[t] * pv[j];
           }
 #pragma unroll
-        for (int o = 0; o < 4; ++o) hb[m][r][c0 + o] = acc[o];
+        for (int o = 0; o < 4; ++o) S.hb[m][r][c0 + o] = acc[o];
       }
     }
     __syncthreads();
@@ -301,7 +357,7 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
         for (int o = 0; o < 4; ++o) bl[m][o] = 0.f;
 #pragma unroll
         for (int j = 0; j < 14; ++j) {
-          const float h = hb[m][r0 + j][c];
+          const float h = S.hb[m][r0 + j][c];
 #pragma unroll
           for (int o = 0; o < 4; ++o) {
             const int t = j - o;
@@ -324,13 +380,19 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   }
 }
 
+void init_loss_attributes() {
+  cudaFuncSetAttribute(k_loss_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossFwdSmem));
+  cudaFuncSetAttribute(k_loss_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossBwdSmem));
+}
+
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
                  float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s) {
   if (n_blocks <= 0) return;
-  k_loss_forward<<<(unsigned)n_blocks, 256, 0, s>>>(views, n_views, n_blocks, image, sp, partials, block_sums, ctl,
-                                                     ledger);
+  k_loss_forward<<<(unsigned)n_blocks, 256, sizeof(LossFwdSmem), s>>>(views, n_views, n_blocks, image, sp, partials,
+                                                                        block_sums, ctl, ledger);
   if (dimage)
-    k_loss_backward<<<(unsigned)n_blocks, 256, 0, s>>>(views, n_views, image, sp, partials, ctl, dimage);
+    k_loss_backward<<<(unsigned)n_blocks, 256, sizeof(LossBwdSmem), s>>>(views, n_views, image, sp, partials, ctl,
+                                                                         dimage);
 }
 
 }  // namespace gs

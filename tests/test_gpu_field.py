@@ -201,3 +201,63 @@ def test_multi_view_step_matches_oracle(scaling):
         bad = d > 1e-3 * lrg + 1e-6
         assert bad.mean() < 2e-3, (a, b, bad.mean())
     f.close()
+
+
+def test_field_update_at_scale_matches_brute_force():
+    """Four images of 30 000 sparse points each (the point arrays and the hash table grow and are
+    rebuilt on the way): the far test against every earlier point and the 3-nearest initial scale
+    against a k-d tree in float64, away from distances within 1e-5 of the threshold."""
+    from scipy.spatial import cKDTree
+    thr = 0.02
+    f = make_field(add_dist_thresh=thr, use_graph=0)
+    rng = np.random.default_rng(7)
+    cam = gi.identity_camera(48, 32, 48.0)
+    allp = np.zeros((0, 3), np.float32)
+    n_g = 0
+    for k in range(4):
+        pts = rng.uniform(-1.0, 1.0, (30000, 3)).astype(np.float32) + np.float32([0, 0, 3])
+        col = rng.uniform(0, 1, (30000, 3)).astype(np.float32)
+        if len(allp):
+            d, _ = cKDTree(allp.astype(np.float64)).query(pts.astype(np.float64), k=1)
+        else:
+            d = np.full(len(pts), np.inf)
+        far = d > thr
+        tie = np.abs(d - thr) <= 1e-5 * thr
+        f.add_image(cam, gi.uniform_target(48, 32, k), pts, col, np.arange(30000) + 30000 * k)
+        got = f.get_gaussians()
+        added = got.shape[1] - n_g
+        assert abs(added - int(far.sum())) <= int(tie.sum()), (k, added, int(far.sum()))
+        allp = np.concatenate([allp, pts])
+        if not tie.any():
+            new = got[:, n_g:]
+            idx = np.nonzero(far)[0]
+            assert np.allclose(new[0:3].T, pts[idx])
+            dd, _ = cKDTree(allp.astype(np.float64)).query(pts[idx].astype(np.float64), k=4)
+            ref = np.log(np.sqrt(np.maximum((dd[:, 1:] ** 2).mean(1), 1e-7)))
+            assert np.allclose(new[3], ref, atol=1e-4), np.abs(new[3] - ref).max()
+            assert np.allclose(new[11:14].T, (col[idx] - 0.5) / C0, atol=1e-5)
+        n_g = got.shape[1]
+    f.close()
+
+
+def test_new_gaussians_start_with_zero_adam_moments_after_restore():
+    thr = 0.05
+    f = make_field(add_dist_thresh=thr, use_graph=0)
+    rng = np.random.default_rng(4)
+    cam = gi.identity_camera(64, 48, 64.0)
+    pts1 = rng.uniform(-0.5, 0.5, (300, 3)).astype(np.float32) + np.float32([0, 0, 3])
+    img = f.add_image(cam, gi.uniform_target(64, 48, 1), pts1, rng.uniform(0, 1, (300, 3)), np.arange(300))
+    f.snapshot()
+    pts2 = rng.uniform(-0.5, 0.5, (200, 3)).astype(np.float32) + np.float32([0, 0, 5])
+    f.add_image(cam, gi.uniform_target(64, 48, 2), pts2, rng.uniform(0, 1, (200, 3)), np.arange(300, 500))
+    for _ in range(3):
+        f.optimize_step([img])
+    _, m, v = f.get_gaussians(with_adam=True)
+    assert np.abs(m[:, 300:]).max() > 0  # the Gaussians past the snapshot have moments now
+    f.restore()
+    pts3 = rng.uniform(-0.5, 0.5, (150, 3)).astype(np.float32) + np.float32([0, 0, 8])
+    f.add_image(cam, gi.uniform_target(64, 48, 3), pts3, rng.uniform(0, 1, (150, 3)), np.arange(500, 650))
+    p, m, v = f.get_gaussians(with_adam=True)
+    assert p.shape[1] == 450
+    assert np.all(m[:, 300:] == 0) and np.all(v[:, 300:] == 0)
+    f.close()
