@@ -20,13 +20,15 @@
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
 // (tile, 32-entry chunk), one warp each, taken from a global counter.  The warp compacts the
 // tile's pixels whose mask for this chunk is non-empty and takes them 32 at a time.  First each
-// lane restarts its pixel from the checkpoint and walks only the Gaussians it blended, in order,
-// with exactly the forward's transmittance (the colour behind a Gaussian is the rendered colour
-// minus the colour accumulated in front of it), leaving per (Gaussian, pixel) the transmittance
-// in front and dL/dC . (colour behind) in shared memory.  Then the roles swap: lane q owns
-// Gaussian q of the chunk and adds, in pixel order, the nine gradient terms of the pixels that
-// blended it, in registers.  No atomics and a fixed summation order: the gradient is
-// deterministic, and each instance's gradient is written once, to its own slot.
+// lane restarts its pixel from the checkpoint.  The lanes then walk the union of their pixels'
+// blended Gaussians in list order, three Gaussians at a time: a lane computes its pixel's nine
+// gradient terms for each (zero where it did not blend it) and advances its transmittance and
+// front colour exactly as the forward did (the colour behind a Gaussian is the rendered colour
+// minus the colour accumulated in front of it); the 27 terms are summed over the 32 pixels through
+// shared memory in a fixed order and added to the Gaussians' running sums.  A round's pixels share
+// few Gaussians (about 9 of 32), each blended by many of them, so this keeps more lanes busy than
+// one lane per Gaussian.  No atomics: the gradient is deterministic, and each instance's gradient
+// is written once, to its own slot.
 #include "gs_device.cuh"
 #include "gs_engine.h"
 
@@ -360,41 +362,15 @@ void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, l
 // K8
 // ---------------------------------------------------------------------------------------------
 constexpr int kBwdWarps = 4;
+constexpr int kGroup = 3;  // Gaussians whose gradient terms are summed together (3 x 9 <= 32 lanes)
 
 template <int PIX>
 struct BwdWarp {
   float4 a[kChunk], b[kChunk], c[kChunk];  // the chunk's Gaussians (records A, B, C)
   uint2 act[PIX];                          // compacted (slot, mask) of the pixels to visit
-  float4 pix[32];                          // per lane of the round: dL/dC (3), pixel x | y << 16
-  float pT[kChunk][33];                    // per (Gaussian, lane): transmittance in front
-  float pD[kChunk][33];                    // per (Gaussian, lane): dL/dC . (colour behind)
+  float red[32][33];                       // per lane: the 27 terms of a group of 3 Gaussians
+  float acc[kChunk][9];                    // per Gaussian of the chunk: running gradient sums
 };
-
-// Gradient terms of one (pixel, Gaussian) pair added into g: d mean2d (2), d conic a, b, c,
-// d opacity, d rgb.
-__device__ __forceinline__ void pair_grad(const float4& xy, const float4& co, const float4& c, float pxf, float pyf,
-                                          float T, float DS, float d0, float d1, float d2, float g[9]) {
-  const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
-  const float power = splat_power(co.x, co.y, co.z, dx, dy);
-  const float G = splat_exp(power);
-  const float oG = __fmul_rn(c.w, G);
-  const float alpha = fminf(kAlphaMax, oG);
-  const float w = __fmul_rn(alpha, T);
-  // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha))
-  const float dalpha = T * (c.x * d0 + c.y * d1 + c.z * d2) - DS * __fdividef(1.f, 1.f - alpha);
-  g[6] += w * d0;
-  g[7] += w * d1;
-  g[8] += w * d2;
-  if (!(oG > kAlphaMax)) {
-    g[5] += dalpha * G;
-    const float dpow = dalpha * alpha;
-    g[0] += dpow * (2.f * co.x * dx + co.y * dy);
-    g[1] += dpow * (co.y * dx + 2.f * co.z * dy);
-    g[2] += dpow * (-0.5f * dx * dx);
-    g[3] += dpow * (-dx * dy);
-    g[4] += dpow * (-0.5f * dy * dy);
-  }
-}
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
@@ -442,9 +418,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
       const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu;
       e = (unsigned long long)pb.offsets[rec] + (unsigned long long)((ty - (int)y0) * (int)(x1 - x0) + (tx - (int)x0));
     }
-    float g[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) g[c] = 0.f;
+    for (int c = 0; c < 9; ++c) S.acc[lane][c] = 0.f;
     // Chunks past tile_chunks[t] were never reached by any pixel: all gradients are zero.
     int n_act = 0;
     if (k < tile_chunks[t]) {
@@ -465,73 +440,102 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     for (int r0 = 0; r0 < n_act; r0 += 32) {
       const int i = r0 + lane;
       const uint2 pm = i < n_act ? S.act[i] : make_uint2(0u, 0u);
-      unsigned mask = pm.y;
-      // lane q learns which lanes (pixels) of this round blended Gaussian q
-      unsigned myball = 0u;
-#pragma unroll
-      for (int q = 0; q < kChunk; ++q) {
-        const unsigned b = __ballot_sync(0xffffffffu, (mask >> q) & 1u);
-        if (lane == q) myball = b;
-      }
-      // (1) each lane walks the Gaussians its pixel blended, in order, with the forward's exact
-      //     transmittance, recording per (Gaussian, pixel) T and dL/dC . (colour behind)
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-      int px = 0, py = 0;
+      const unsigned mask = pm.y;
+      // this lane's pixel: dL/dC, the rendered colour, and the state at the chunk start
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, P0 = 0.f, P1 = 0.f, P2 = 0.f;
+      float T = 1.f, F0 = 0.f, F1 = 0.f, F2 = 0.f, pxf = 0.f, pyf = 0.f;
       if (mask) {
         int ox, oy;
         Sh::slot_xy((int)pm.x, ox, oy);
-        px = tx * TW + ox;
-        py = ty * TH + oy;
+        const int px = tx * TW + ox, py = ty * TH + oy;
         const long long pix = (long long)py * V.W + px;
         d0 = dimg[pix];
         d1 = dimg[HW + pix];
         d2 = dimg[2 * HW + pix];
-        const float4 ck = k == 0 ? make_float4(1.f, 0.f, 0.f, 0.f) : ckpt[cid * kPix + pm.x];
-        float T = ck.x, F0 = ck.y, F1 = ck.z, F2 = ck.w;
-        const float P0 = img[pix], P1 = img[HW + pix], P2 = img[2 * HW + pix];
-        const float pxf = (float)px, pyf = (float)py;
-        while (mask) {
-          const int q = __ffs(mask) - 1;
-          mask &= mask - 1u;
-          const float4 xy = S.a[q];
-          const float4 co = S.b[q];
-          const float4 c = S.c[q];
-          const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
-          const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, splat_exp(power)));
-          const float w = __fmul_rn(alpha, T);
-          const float n0 = __fmaf_rn(c.x, w, F0);
-          const float n1 = __fmaf_rn(c.y, w, F1);
-          const float n2 = __fmaf_rn(c.z, w, F2);
-          // colour behind = rendered colour (incl. background) - colour in front incl. this one
-          S.pT[q][lane] = T;
-          S.pD[q][lane] = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
-          T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          F0 = n0;
-          F1 = n1;
-          F2 = n2;
+        P0 = img[pix];
+        P1 = img[HW + pix];
+        P2 = img[2 * HW + pix];
+        if (k > 0) {
+          const float4 ck = ckpt[cid * kPix + pm.x];
+          T = ck.x;
+          F0 = ck.y;
+          F1 = ck.z;
+          F2 = ck.w;
         }
+        pxf = (float)px;
+        pyf = (float)py;
       }
-      S.pix[lane] = make_float4(d0, d1, d2, __uint_as_float((unsigned)px | ((unsigned)py << 16)));
-      __syncwarp();
-      // (2) lane q sums, in lane order, the terms of the pixels that blended Gaussian q
-      if (lane < cnt) {
-        const float4 xy = S.a[lane], co = S.b[lane], c = S.c[lane];
-        unsigned bl = myball;
-        while (bl) {
-          const int pl = __ffs(bl) - 1;
-          bl &= bl - 1u;
-          const float4 pp = S.pix[pl];
-          const unsigned xyb = __float_as_uint(pp.w);
-          pair_grad(xy, co, c, (float)(xyb & 0xffffu), (float)(xyb >> 16), S.pT[lane][pl], S.pD[lane][pl], pp.x, pp.y,
-                    pp.z, g);
+      // The round's pixels walk the union of their Gaussians in list order, three at a time:
+      // each lane computes its pair's nine gradient terms (zero if it did not blend that
+      // Gaussian) and advances its own transmittance exactly as the forward did; the 27 terms of
+      // a group are then summed over the 32 pixels through shared memory (fixed order).
+      unsigned uni = __reduce_or_sync(0xffffffffu, mask);
+      while (uni) {
+        float g[kGroup * 9];
+#pragma unroll
+        for (int j = 0; j < kGroup * 9; ++j) g[j] = 0.f;
+        int qs[kGroup];
+        int ng = 0;
+#pragma unroll
+        for (int gi = 0; gi < kGroup; ++gi) {
+          qs[gi] = 0;
+          if (!uni) break;
+          const int q = __ffs(uni) - 1;
+          uni &= uni - 1u;
+          qs[gi] = q;
+          ng = gi + 1;
+          if ((mask >> q) & 1u) {
+            const float4 xy = S.a[q], co = S.b[q], c = S.c[q];
+            const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
+            const float G = splat_exp(splat_power(co.x, co.y, co.z, dx, dy));
+            const float oG = __fmul_rn(c.w, G);
+            const float alpha = fminf(kAlphaMax, oG);
+            const float w = __fmul_rn(alpha, T);
+            const float n0 = __fmaf_rn(c.x, w, F0);
+            const float n1 = __fmaf_rn(c.y, w, F1);
+            const float n2 = __fmaf_rn(c.z, w, F2);
+            // colour behind = rendered colour (incl. background) - colour in front incl. this one
+            const float DS = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
+            // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha))
+            const float dalpha = T * (c.x * d0 + c.y * d1 + c.z * d2) - DS * __fdividef(1.f, 1.f - alpha);
+            g[9 * gi + 6] = w * d0;
+            g[9 * gi + 7] = w * d1;
+            g[9 * gi + 8] = w * d2;
+            if (!(oG > kAlphaMax)) {
+              g[9 * gi + 5] = dalpha * G;
+              const float dpow = dalpha * alpha;
+              g[9 * gi + 0] = dpow * (2.f * co.x * dx + co.y * dy);
+              g[9 * gi + 1] = dpow * (co.y * dx + 2.f * co.z * dy);
+              g[9 * gi + 2] = dpow * (-0.5f * dx * dx);
+              g[9 * gi + 3] = dpow * (-dx * dy);
+              g[9 * gi + 4] = dpow * (-0.5f * dy * dy);
+            }
+            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            F0 = n0;
+            F1 = n1;
+            F2 = n2;
+          }
         }
+#pragma unroll
+        for (int j = 0; j < kGroup * 9; ++j) S.red[lane][j] = g[j];
+        __syncwarp();
+        if (lane < 9 * ng) {
+          float sum = 0.f;
+#pragma unroll 8
+          for (int l = 0; l < 32; ++l) sum += S.red[l][lane];
+          const int gi = lane / 9;
+          const int q = gi == 0 ? qs[0] : (gi == 1 ? qs[1] : qs[2]);
+          S.acc[q][lane - 9 * gi] += sum;
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
+    __syncwarp();
     if (lane < cnt) {
-      ginst[3 * e] = make_float4(g[0], g[1], g[2], g[3]);
-      ginst[3 * e + 1] = make_float4(g[4], g[5], g[6], g[7]);
-      ginst[3 * e + 2] = make_float4(g[8], 0.f, 0.f, 0.f);
+      const float* a = S.acc[lane];
+      ginst[3 * e] = make_float4(a[0], a[1], a[2], a[3]);
+      ginst[3 * e + 1] = make_float4(a[4], a[5], a[6], a[7]);
+      ginst[3 * e + 2] = make_float4(a[8], 0.f, 0.f, 0.f);
     }
     __syncwarp();
   }
@@ -539,9 +543,22 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
 
 namespace {
 template <int TW, int TH>
+int& bwd_occupancy() {
+  static int occ = 0;
+  return occ;
+}
+
+template <int TW, int TH>
 void init_backward_instance() {
-  cudaFuncSetAttribute(k_blend_backward<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(sizeof(BwdWarp<TW * TH>) * kBwdWarps));
+  const int smem = (int)(sizeof(BwdWarp<TW * TH>) * kBwdWarps);
+  cudaFuncSetAttribute(k_blend_backward<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_backward<TW, TH>, kBwdWarps * 32, smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    occ = 0;
+  }
+  bwd_occupancy<TW, TH>() = occ > 0 ? occ : 1;
 }
 
 template <int TW, int TH>
@@ -549,7 +566,8 @@ void launch_backward_instance(const ViewDev* views, int n_views, long long n_til
                               const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                               const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
                               const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
-  k_blend_backward<TW, TH><<<num_sms * 4, kBwdWarps * 32, sizeof(BwdWarp<TW * TH>) * kBwdWarps, s>>>(
+  k_blend_backward<TW, TH><<<num_sms * bwd_occupancy<TW, TH>(), kBwdWarps * 32, sizeof(BwdWarp<TW * TH>) * kBwdWarps,
+                             s>>>(
       views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, chunk_tile, tile_chunks, ginst);
 }
 }  // namespace
