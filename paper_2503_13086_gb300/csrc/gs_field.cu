@@ -227,7 +227,7 @@ struct Field {
     std::vector<unsigned long long> v;
     const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
                             &R.sp_d, &R.views_d, &R.zeroA, &R.zeroB, &R.xyo, &R.conic, &R.rgb, &R.depth, &R.radius,
-                            &R.rect, &R.count, &R.offsets, &R.clamp, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
+                            &R.rect, &R.count, &R.offsets, &R.clamp, &R.g2s, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
                             &R.ckpt, &R.cmask, &R.order, &R.tile_chunks, &R.partials, &R.block_sums};
     for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
     const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)R.passes,
@@ -740,7 +740,7 @@ struct Field {
     last_pairs = ok ? Lg.pairs / ok : 0;
     last_blended = ok ? Lg.blended / ok : 0;
     last_instances = ok ? Lg.instances / ok : 0;
-    last_kernels = 10 + R.passes;
+    last_kernels = kStepLaunchesBase + R.passes;
     sum_pairs += Lg.pairs;
     if (ok && Lg.last_gp_pixels) {  // Eq. 9: std of G_p over the pixels some Gaussian reaches
       const double mean = (double)Lg.last_gp_sum / (double)Lg.last_gp_pixels;

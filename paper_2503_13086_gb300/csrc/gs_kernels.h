@@ -43,9 +43,11 @@ bool tiling_supported(const Tiling& t);
 
 void launch_project(const float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
                     const ProjBuffers& out, cudaStream_t s);
+// K9a (per-record sums of the instance gradients, into g2s: 9 planes of views x stride floats) and
+// K9 + K10.
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
-                             const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
-                             float* m, float* v, float* grad2d_out, cudaStream_t s);
+                             const ProjBuffers& pb, const float4* ginst, float* g2s, const Control* ctl,
+                             float* grads_out, float* m, float* v, float* grad2d_out, cudaStream_t s);
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
                  cudaStream_t s);
 

@@ -104,7 +104,7 @@ Raster::Raster() {
 
 Raster::~Raster() {
   DevBuf* all[] = {&sp_d, &views_d, &ledger_d, &zeroA, &zeroB, &xyo, &conic, &rgb, &depth, &radius, &rect, &count, &offsets,
-                   &clamp, &keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
+                   &clamp, &g2s, &keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
                    &own_last, &own_dimage};
   for (DevBuf* b : all) b->release(&bytes_in_use);
   if (sp_h) cudaFreeHost(sp_h);
@@ -194,7 +194,7 @@ gs_status Raster::ensure_records(int stride_) {
       (s = rgb.reserve(recs * 16, &bytes_in_use)) || (s = depth.reserve(recs * 4, &bytes_in_use)) ||
       (s = radius.reserve(recs * 4, &bytes_in_use)) || (s = rect.reserve(recs * 8, &bytes_in_use)) ||
       (s = count.reserve(recs * 4, &bytes_in_use)) || (s = offsets.reserve(recs * 4, &bytes_in_use)) ||
-      (s = clamp.reserve(recs, &bytes_in_use)))
+      (s = clamp.reserve(recs, &bytes_in_use)) || (s = g2s.reserve(recs * 36, &bytes_in_use)))
     return s;
   const long long scan_tiles = (recs + kScanTile - 1) / kScanTile;
   if ((s = zeroA.reserve(kCtlBytes + scan_tiles * 8, &bytes_in_use))) return s;
@@ -333,8 +333,8 @@ void Raster::enqueue_backward(cudaStream_t s, float* params, const float* image,
                               const float* dimage, float* grads, float* m, float* v, float* grad2d) {
   (void)last;  // the backward reads the forward's per-chunk masks instead of the last index
   enqueue_blend_backward(s, image, dimage);
-  launch_project_backward(params, stride, n_views, sp(), vd(), proj(), static_cast<float4*>(ginst.p), ctl(), grads,
-                          m, v, grad2d, s);
+  launch_project_backward(params, stride, n_views, sp(), vd(), proj(), static_cast<float4*>(ginst.p),
+                          static_cast<float*>(g2s.p), ctl(), grads, m, v, grad2d, s);
   mark(s, 9);
 }
 

@@ -391,13 +391,169 @@ __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, uns
   apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
 }
 
+// K9a: per record (view, Gaussian), the sum of its instances' nine gradients.  A record's instances
+// are contiguous (its tiles, in emission order), so a warp takes the instances of its 32 records
+// as one contiguous run, 32 at a time (coalesced), and adds each lane's instance into its owner's
+// sum by a segmented scan over the lanes; the segment's last lane adds the total into the owner's
+// accumulator in shared memory (one writer per owner and round, rounds in order: deterministic).
+// Output: g2s, 9 planes of n_items floats (record-major inside a plane); grad2d (nullable) the same
+// sums as 9 consecutive floats per record.
+__global__ void __launch_bounds__(256) k_record_grads(const unsigned* __restrict__ count,
+                                                      const unsigned* __restrict__ offsets,
+                                                      const float4* __restrict__ ginst, long long n_items,
+                                                      const Control* __restrict__ ctl, float* __restrict__ g2s,
+                                                      float* __restrict__ grad2d) {
+  __shared__ float s_acc[8][9][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl->overflow || rec - lane >= n_items) return;  // warp-uniform: n_items is a multiple of 32
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s_acc[warp][k][lane] = 0.f;
+  const unsigned cnt = count[rec];
+  const unsigned off = offsets[rec];
+  const unsigned wbeg = __shfl_sync(0xffffffffu, off, 0);
+  const unsigned wend = __shfl_sync(0xffffffffu, off + cnt, 31);
+  __syncwarp();
+  for (unsigned e0 = wbeg; e0 < wend; e0 += 32) {
+    const unsigned e = e0 + lane;
+    // owner = largest lane whose offset is <= e
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const unsigned oc = __shfl_sync(0xffffffffu, off, owner + step);
+      if (oc <= e) owner += step;
+    }
+    float x[9];
+    if (e < wend) {
+      const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], c = ginst[3ull * e + 2];
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+      x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+      x[8] = c.x;
+    } else {
+      owner = 32;  // past the run: a segment of its own
+#pragma unroll
+      for (int k = 0; k < 9; ++k) x[k] = 0.f;
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int od = __shfl_up_sync(0xffffffffu, owner, d);
+      const bool same = lane >= d && od == owner;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const float y = __shfl_up_sync(0xffffffffu, x[k], d);
+        if (same) x[k] += y;
+      }
+    }
+    const int next_owner = __shfl_down_sync(0xffffffffu, owner, 1);
+    if (owner < 32 && (lane == 31 || next_owner != owner)) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) s_acc[warp][k][owner] += x[k];
+    }
+    __syncwarp();
+  }
+  const long long n_rec = n_items;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float v = s_acc[warp][k][lane];
+    g2s[k * n_rec + rec] = v;
+    if (grad2d) grad2d[9 * rec + k] = v;
+  }
+}
+
+// Chain rule of one view's 2D gradient (d mean2d, d pre-scaled conic; g2[0..4]) back to the mean,
+// the log-scales and the quaternion (accumulated into gmu, gls, gq).
+__device__ __forceinline__ void geo_backward(const ViewDev& V, const Geo& g, const float g2[9], float gmu[3],
+                                             float gls[3], float gq[4]) {
+  // Pre-scaled conic gradient back to the conic (a, b, c): power = -a/2 dx^2 - b dx dy - c/2 dy^2.
+  const float dA = g2[2], dB = g2[3], dC = g2[4];
+  const float A_ = g.cov[0], B_ = g.cov[1], C_ = g.cov[2], det = g.det;
+  const float id = 1.f / det, id2 = id * id;
+  const float da = dA * (-C_ * C_ * id2) + dB * (B_ * C_ * id2) + dC * (id - A_ * C_ * id2);
+  const float db = dA * (2.f * B_ * C_ * id2) + dB * (-id - 2.f * B_ * B_ * id2) + dC * (2.f * A_ * B_ * id2);
+  const float dc = dA * (id - A_ * C_ * id2) + dB * (A_ * B_ * id2) + dC * (-A_ * A_ * id2);
+
+  // (a, b, c) = entries of Tm Sigma Tm^T
+  const float* T0 = g.Tm;
+  const float* T1 = g.Tm + 3;
+  const float S[9] = {g.Sig[0], g.Sig[1], g.Sig[2], g.Sig[1], g.Sig[3], g.Sig[4], g.Sig[2], g.Sig[4], g.Sig[5]};
+  float Gs[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      Gs[3 * r + c] = da * T0[r] * T0[c] + 0.5f * db * (T0[r] * T1[c] + T1[r] * T0[c]) + dc * T1[r] * T1[c];
+  float dT0[3], dT1[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float s0 = S[3 * r] * T0[0] + S[3 * r + 1] * T0[1] + S[3 * r + 2] * T0[2];
+    const float s1 = S[3 * r] * T1[0] + S[3 * r + 1] * T1[1] + S[3 * r + 2] * T1[2];
+    dT0[r] = 2.f * da * s0 + db * s1;
+    dT1[r] = 2.f * dc * s1 + db * s0;
+  }
+  const float dJ00 = dT0[0] * V.R[0] + dT0[1] * V.R[1] + dT0[2] * V.R[2];
+  const float dJ02 = dT0[0] * V.R[6] + dT0[1] * V.R[7] + dT0[2] * V.R[8];
+  const float dJ11 = dT1[0] * V.R[3] + dT1[1] * V.R[4] + dT1[2] * V.R[5];
+  const float dJ12 = dT1[0] * V.R[6] + dT1[1] * V.R[7] + dT1[2] * V.R[8];
+  const float px = g.p[0], py = g.p[1], pz = g.p[2];
+  const float iz = 1.f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
+  float dp[3] = {0.f, 0.f, 0.f};
+  dp[2] += dJ00 * (-V.fx * iz2) + dJ11 * (-V.fy * iz2);
+  if (g.xin) {
+    dp[0] += dJ02 * (-V.fx * iz2);
+    dp[2] += dJ02 * (2.f * V.fx * px * iz3);
+  } else {
+    dp[2] += dJ02 * (V.fx * g.txz * iz2);
+  }
+  if (g.yin) {
+    dp[1] += dJ12 * (-V.fy * iz2);
+    dp[2] += dJ12 * (2.f * V.fy * py * iz3);
+  } else {
+    dp[2] += dJ12 * (V.fy * g.tyz * iz2);
+  }
+  dp[0] += g2[0] * V.fx * iz;
+  dp[2] += g2[0] * (-V.fx * px * iz2);
+  dp[1] += g2[1] * V.fy * iz;
+  dp[2] += g2[1] * (-V.fy * py * iz2);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gmu[a] += V.R[a] * dp[0] + V.R[3 + a] * dp[1] + V.R[6 + a] * dp[2];
+
+  float dM[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dM[3 * r + c] = 2.f * (Gs[3 * r] * g.M[c] + Gs[3 * r + 1] * g.M[3 + c] + Gs[3 * r + 2] * g.M[6 + c]);
+  float dRq[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dRq[3 * r + c] = dM[3 * r + c] * g.s[c];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float ds = dM[c] * g.Rq[c] + dM[3 + c] * g.Rq[3 + c] + dM[6 + c] * g.Rq[6 + c];
+    gls[c] += ds * g.s[c];
+  }
+  const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
+  float dqn[4];
+  dqn[0] = 2.f * (-z * dRq[1] + y * dRq[2] + z * dRq[3] - x * dRq[5] - y * dRq[6] + x * dRq[7]);
+  dqn[1] = 2.f * (y * dRq[1] + z * dRq[2] + y * dRq[3] - 2.f * x * dRq[4] - w * dRq[5] + z * dRq[6] +
+                  w * dRq[7] - 2.f * x * dRq[8]);
+  dqn[2] = 2.f * (-2.f * y * dRq[0] + x * dRq[1] + w * dRq[2] + x * dRq[3] + z * dRq[5] - w * dRq[6] +
+                  z * dRq[7] - 2.f * y * dRq[8]);
+  dqn[3] = 2.f * (-2.f * z * dRq[0] - w * dRq[1] + x * dRq[2] + w * dRq[3] - 2.f * z * dRq[4] + y * dRq[5] +
+                  x * dRq[6] + y * dRq[7]);
+  const float qd = g.qn[0] * dqn[0] + g.qn[1] * dqn[1] + g.qn[2] * dqn[2] + g.qn[3] * dqn[3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) gq[k] += (dqn[k] - g.qn[k] * qd) * g.qinv;
+}
+
 template <int MAXV>
 __global__ void __launch_bounds__(256, 2) k_project_backward(
     float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
-    const unsigned* __restrict__ offsets, const unsigned char* __restrict__ clampbits,
-    const float4* __restrict__ ginst, const Control* __restrict__ ctl, float* __restrict__ grads_out,
-    float* __restrict__ adam_m, float* __restrict__ adam_v, float* __restrict__ grad2d_out) {
+    const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
+    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+  const long long n_rec = (long long)n_views * stride;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sp->n) return;
   if (ctl->overflow) return;  // the step was skipped; the host re-runs it with more capacity
@@ -445,18 +601,9 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     const unsigned cnt = count[rec];
     if (cnt == 0u) continue;
     const int slot = kSmall ? v : nvis;
-    const unsigned off = offsets[rec];
-    float g2[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (unsigned e = off; e < off + cnt; ++e) {
-      const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], c = ginst[3ull * e + 2];
-      g2[0] += a.x; g2[1] += a.y; g2[2] += a.z; g2[3] += a.w;
-      g2[4] += b.x; g2[5] += b.y; g2[6] += b.z; g2[7] += b.w;
-      g2[8] += c.x;
-    }
-    if (grad2d_out) {
+    float g2[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) grad2d_out[9 * rec + k] = g2[k];
-    }
+    for (int k = 0; k < 9; ++k) g2[k] = g2s[k * n_rec + rec];
     const ViewDev& V = views[v];
     Geo g;
     if (!geo_forward(V, mu, ls, q, g)) continue;
@@ -482,87 +629,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     vmask |= 1u << slot;
     ++nvis;
 
-    // Pre-scaled conic gradient back to the conic (a, b, c): power = -a/2 dx^2 - b dx dy - c/2 dy^2.
-    const float dA = g2[2], dB = g2[3], dC = g2[4];
-    const float A_ = g.cov[0], B_ = g.cov[1], C_ = g.cov[2], det = g.det;
-    const float id = 1.f / det, id2 = id * id;
-    const float da = dA * (-C_ * C_ * id2) + dB * (B_ * C_ * id2) + dC * (id - A_ * C_ * id2);
-    const float db = dA * (2.f * B_ * C_ * id2) + dB * (-id - 2.f * B_ * B_ * id2) + dC * (2.f * A_ * B_ * id2);
-    const float dc = dA * (id - A_ * C_ * id2) + dB * (A_ * B_ * id2) + dC * (-A_ * A_ * id2);
-
-    // (a, b, c) = entries of Tm Sigma Tm^T
-    const float* T0 = g.Tm;
-    const float* T1 = g.Tm + 3;
-    const float S[9] = {g.Sig[0], g.Sig[1], g.Sig[2], g.Sig[1], g.Sig[3], g.Sig[4], g.Sig[2], g.Sig[4], g.Sig[5]};
-    float Gs[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        Gs[3 * r + c] = da * T0[r] * T0[c] + 0.5f * db * (T0[r] * T1[c] + T1[r] * T0[c]) + dc * T1[r] * T1[c];
-    float dT0[3], dT1[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const float s0 = S[3 * r] * T0[0] + S[3 * r + 1] * T0[1] + S[3 * r + 2] * T0[2];
-      const float s1 = S[3 * r] * T1[0] + S[3 * r + 1] * T1[1] + S[3 * r + 2] * T1[2];
-      dT0[r] = 2.f * da * s0 + db * s1;
-      dT1[r] = 2.f * dc * s1 + db * s0;
-    }
-    const float dJ00 = dT0[0] * V.R[0] + dT0[1] * V.R[1] + dT0[2] * V.R[2];
-    const float dJ02 = dT0[0] * V.R[6] + dT0[1] * V.R[7] + dT0[2] * V.R[8];
-    const float dJ11 = dT1[0] * V.R[3] + dT1[1] * V.R[4] + dT1[2] * V.R[5];
-    const float dJ12 = dT1[0] * V.R[6] + dT1[1] * V.R[7] + dT1[2] * V.R[8];
-    const float px = g.p[0], py = g.p[1], pz = g.p[2];
-    const float iz = 1.f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
-    float dp[3] = {0.f, 0.f, 0.f};
-    dp[2] += dJ00 * (-V.fx * iz2) + dJ11 * (-V.fy * iz2);
-    if (g.xin) {
-      dp[0] += dJ02 * (-V.fx * iz2);
-      dp[2] += dJ02 * (2.f * V.fx * px * iz3);
-    } else {
-      dp[2] += dJ02 * (V.fx * g.txz * iz2);
-    }
-    if (g.yin) {
-      dp[1] += dJ12 * (-V.fy * iz2);
-      dp[2] += dJ12 * (2.f * V.fy * py * iz3);
-    } else {
-      dp[2] += dJ12 * (V.fy * g.tyz * iz2);
-    }
-    dp[0] += g2[0] * V.fx * iz;
-    dp[2] += g2[0] * (-V.fx * px * iz2);
-    dp[1] += g2[1] * V.fy * iz;
-    dp[2] += g2[1] * (-V.fy * py * iz2);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) gmu[a] += V.R[a] * dp[0] + V.R[3 + a] * dp[1] + V.R[6 + a] * dp[2];
-
-    float dM[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        dM[3 * r + c] = 2.f * (Gs[3 * r] * g.M[c] + Gs[3 * r + 1] * g.M[3 + c] + Gs[3 * r + 2] * g.M[6 + c]);
-    float dRq[9];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) dRq[3 * r + c] = dM[3 * r + c] * g.s[c];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float ds = dM[c] * g.Rq[c] + dM[3 + c] * g.Rq[3 + c] + dM[6 + c] * g.Rq[6 + c];
-      gls[c] += ds * g.s[c];
-    }
-    const float w = g.qn[0], x = g.qn[1], y = g.qn[2], z = g.qn[3];
-    float dqn[4];
-    dqn[0] = 2.f * (-z * dRq[1] + y * dRq[2] + z * dRq[3] - x * dRq[5] - y * dRq[6] + x * dRq[7]);
-    dqn[1] = 2.f * (y * dRq[1] + z * dRq[2] + y * dRq[3] - 2.f * x * dRq[4] - w * dRq[5] + z * dRq[6] +
-                    w * dRq[7] - 2.f * x * dRq[8]);
-    dqn[2] = 2.f * (-2.f * y * dRq[0] + x * dRq[1] + w * dRq[2] + x * dRq[3] + z * dRq[5] - w * dRq[6] +
-                    z * dRq[7] - 2.f * y * dRq[8]);
-    dqn[3] = 2.f * (-2.f * z * dRq[0] - w * dRq[1] + x * dRq[2] + w * dRq[3] - 2.f * z * dRq[4] + y * dRq[5] +
-                    x * dRq[6] + y * dRq[7]);
-    const float qd = g.qn[0] * dqn[0] + g.qn[1] * dqn[1] + g.qn[2] * dqn[2] + g.qn[3] * dqn[3];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) gq[k] += (dqn[k] - g.qn[k] * qd) * g.qinv;
+    geo_backward(V, g, g2, gmu, gls, gq);
   }
 
   // SH rows, four coefficients (12 rows) at a time; accumulates the direction gradient.
@@ -583,6 +650,120 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
   const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
   const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};
   apply_rows<11>(A, 0, grp, i, gg, pc);
+}
+
+// One SH coefficient K of one view: its three gradient rows (colour gradient x Y_K(dir)) into
+// shared memory, and its share of the direction gradient (grad Y_K . (coefficient . colour grad)).
+template <int K>
+__device__ __forceinline__ void sh_view(const float* __restrict__ params, int stride, int i, float x, float y, float z,
+                                        const float c[3], float* __restrict__ gsh, float dd[3]) {
+  float Y, gx, gy, gz;
+  sh_term<K>(x, y, z, Y, gx, gy, gz);
+  float w = 0.f;
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) {
+    gsh[(3 * K + ch) * 256] += Y * c[ch];
+    w += __ldg(params + (long long)(11 + 3 * K + ch) * stride + i) * c[ch];
+  }
+  dd[0] += gx * w;
+  dd[1] += gy * w;
+  dd[2] += gz * w;
+}
+
+template <int K>
+__device__ __forceinline__ void sh_views(const float* __restrict__ params, int stride, int i, float x, float y, float z,
+                                         const float c[3], float* __restrict__ gsh, float dd[3]) {
+  sh_view<K>(params, stride, i, x, y, z, c, gsh, dd);
+  if constexpr (K + 1 < 16) sh_views<K + 1>(params, stride, i, x, y, z, c, gsh, dd);
+}
+
+// K9 + K10 for steps over several views: the views are taken one at a time, each one's SH rows
+// summed straight into per-thread shared-memory accumulators (48 rows) and its direction gradient
+// folded into the mean at once, so no per-view state is kept in registers or local memory.
+__global__ void __launch_bounds__(256, 2) k_project_backward_views(
+    float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
+    const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
+    const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
+    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+  const long long n_rec = (long long)n_views * stride;
+  __shared__ float s_gsh[48 * 256];  // [row][thread]
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sp->n) return;
+  if (ctl->overflow) return;
+  float* gsh = s_gsh + threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < 48; ++r) gsh[r * 256] = 0.f;
+
+  AdamArgs A;
+  A.params = params;
+  A.m = adam_m;
+  A.v = adam_v;
+  A.grads_out = grads_out;
+  A.stride = stride;
+  A.adam = sp->adam;
+  A.b1 = sp->beta1;
+  A.b2 = sp->beta2;
+  A.eps = sp->eps;
+  A.ssc = sp->step_size_scale;
+  A.bc2s = sp->bc2_sqrt;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.lr[k] = sp->lr[k];
+
+  float mu[3], ls[3], q[4];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mu[k] = params[k * stride + i];
+    ls[k] = params[(3 + k) * stride + i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
+  const float logit = params[10 * stride + i];
+  const float o = 1.f / (1.f + __expf(-logit));
+
+  float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+  float gop = 0.f;
+  for (int v = 0; v < n_views; ++v) {
+    const long long rec = (long long)v * stride + i;
+    const unsigned cnt = count[rec];
+    if (cnt == 0u) continue;
+    float g2[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g2[k] = g2s[k * n_rec + rec];
+    const ViewDev& V = views[v];
+    // colour: SH rows and the direction gradient of this view
+    const float d0 = mu[0] - V.campos[0], d1 = mu[1] - V.campos[1], d2 = mu[2] - V.campos[2];
+    const float dinv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    const float x = d0 * dinv, y = d1 * dinv, z = d2 * dinv;
+    const unsigned cb = clampbits[rec];
+    const float col[3] = {(cb & 1u) ? 0.f : g2[6], (cb & 2u) ? 0.f : g2[7], (cb & 4u) ? 0.f : g2[8]};
+    float dd[3] = {0.f, 0.f, 0.f};
+    sh_views<0>(params, stride, i, x, y, z, col, gsh, dd);
+    const float ddot = x * dd[0] + y * dd[1] + z * dd[2];
+    gmu[0] += (dd[0] - x * ddot) * dinv;
+    gmu[1] += (dd[1] - y * ddot) * dinv;
+    gmu[2] += (dd[2] - z * ddot) * dinv;
+    // geometry
+    Geo g;
+    if (!geo_forward(V, mu, ls, q, g)) continue;
+    gop += g2[5] * o * (1.f - o);
+    geo_backward(V, g, g2, gmu, gls, gq);
+  }
+  const float gg[11] = {gmu[0], gmu[1], gmu[2], gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
+  const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
+  const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};
+  apply_rows<11>(A, 0, grp, i, gg, pc);
+#pragma unroll
+  for (int g0 = 0; g0 < 48; g0 += 12) {
+    float p12[12], g12[12];
+    int grp12[12];
+#pragma unroll
+    for (int r = 0; r < 12; ++r) {
+      p12[r] = params[(long long)(11 + g0 + r) * stride + i];
+      g12[r] = gsh[(g0 + r) * 256];
+      grp12[r] = (g0 + r) < 3 ? 4 : 5;
+    }
+    apply_rows<12>(A, 11 + g0, grp12, i, g12, p12);
+  }
 }
 
 // Plain Adam over a gradient buffer (parity of K10 on its own; dense, vectorised by 4).
@@ -624,18 +805,19 @@ void launch_project(const float* params, int stride, int n_views, const StepPara
 }
 
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
-                             const ProjBuffers& pb, const float4* ginst, const Control* ctl, float* grads_out,
-                             float* m, float* v, float* grad2d_out, cudaStream_t s) {
+                             const ProjBuffers& pb, const float4* ginst, float* g2s, const Control* ctl,
+                             float* grads_out, float* m, float* v, float* grad2d_out, cudaStream_t s) {
+  const long long n_items = (long long)n_views * stride;
+  if (n_items > 0)
+    k_record_grads<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, ginst, n_items, ctl, g2s,
+                                                                     grad2d_out);
   const unsigned grid = (unsigned)((stride + 255) / 256);
   if (n_views <= 1)
-    k_project_backward<1><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets, pb.clamp, ginst,
-                                               ctl, grads_out, m, v, grad2d_out);
-  else if (n_views <= 4)
-    k_project_backward<4><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets, pb.clamp, ginst,
-                                               ctl, grads_out, m, v, grad2d_out);
+    k_project_backward<1><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.clamp, g2s, ctl,
+                                               grads_out, m, v);
   else
-    k_project_backward<kMaxStepViews><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.offsets,
-                                                           pb.clamp, ginst, ctl, grads_out, m, v, grad2d_out);
+    k_project_backward_views<<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.clamp, g2s, ctl,
+                                                  grads_out, m, v);
 }
 
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
