@@ -94,11 +94,14 @@ long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * 
 // staged values per map, so a staged value is read once per 4 outputs.
 struct LossFwdSmem {
   float in[2][2][kSY][kSXP];  // [buffer][x / y][row][col]
-  float hm[5][kSY][kBX];      // row-blurred moments
+  float2 hxy[kSY][kBX + 1];   // row-blurred (E[x], E[y])
+  float2 hq[kSY][kBX + 1];    // row-blurred (E[x^2], E[y^2])
+  float hc[kSY][kBX + 1];     // row-blurred E[xy]
 };
 struct LossBwdSmem {
   float in[2][3][kSY][kSXP];  // [buffer][partial][row][col]
-  float hb[3][kSY][kBX];
+  float2 hab[kSY][kBX + 1];   // row-blurred (dS/dmu_x, dS/dE[x^2])
+  float hc[kSY][kBX + 1];     // row-blurred dS/dE[xy]
 };
 
 __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
@@ -113,6 +116,9 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   if (ctl->overflow) return;
   float w[11];
   window(w);
+  float2 w2[11];
+#pragma unroll
+  for (int t = 0; t < 11; ++t) w2[t] = make_float2(w[t], w[t]);
   const long long b = blockIdx.x;
   const int v = view_of_block(views, n_views, b);
   const ViewDev& V = views[v];
@@ -141,53 +147,66 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
     __syncthreads();
     float (*sx)[kSXP] = S.in[cur][0];
     float (*sy)[kSXP] = S.in[cur][1];
-    // horizontal: 42 rows x 8 segments of 4 columns
+    // horizontal: 42 rows x 8 segments of 4 columns; x and y (and x^2 and y^2) share the window
+    // weights, so they are blurred as pairs with the packed FP32x2 FMA of sm_100+
     for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
       const int r = task >> 3, c0 = (task & 7) * 4;
       float xv[16], yv[16];
       load16(sx[r], c0, xv);
       load16(sy[r], c0, yv);
-      float acc[5][4];
+      float2 axy[4], aq[4];
+      float ac[4];
 #pragma unroll
-      for (int m = 0; m < 5; ++m)
-#pragma unroll
-        for (int o = 0; o < 4; ++o) acc[m][o] = 0.f;
+      for (int o = 0; o < 4; ++o) {
+        axy[o] = make_float2(0.f, 0.f);
+        aq[o] = make_float2(0.f, 0.f);
+        ac[o] = 0.f;
+      }
 #pragma unroll
       for (int j = 0; j < 14; ++j) {
-        const float x = xv[j], y = yv[j], xx = x * x, yy = y * y, xy = x * y;
+        const float2 v = make_float2(xv[j], yv[j]);
+        const float2 v2 = __fmul2_rn(v, v);
+        const float c = xv[j] * yv[j];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           const int t = j - o;
           if (t >= 0 && t < 11) {
-            acc[0][o] += w[t] * x;
-            acc[1][o] += w[t] * y;
-            acc[2][o] += w[t] * xx;
-            acc[3][o] += w[t] * yy;
-            acc[4][o] += w[t] * xy;
+            axy[o] = __ffma2_rn(w2[t], v, axy[o]);
+            aq[o] = __ffma2_rn(w2[t], v2, aq[o]);
+            ac[o] = fmaf(w[t], c, ac[o]);
           }
         }
       }
 #pragma unroll
-      for (int m = 0; m < 5; ++m)
-#pragma unroll
-        for (int o = 0; o < 4; ++o) S.hm[m][r][c0 + o] = acc[m][o];
+      for (int o = 0; o < 4; ++o) {
+        S.hxy[r][c0 + o] = axy[o];
+        S.hq[r][c0 + o] = aq[o];
+        S.hc[r][c0 + o] = ac[o];
+      }
     }
     __syncthreads();
     // vertical: 32 columns x 8 segments of 4 rows
     {
       const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
-      float mom[5][4];
+      float2 mxy[4], mq[4];
+      float mc[4];
 #pragma unroll
-      for (int m = 0; m < 5; ++m) {
+      for (int o = 0; o < 4; ++o) {
+        mxy[o] = make_float2(0.f, 0.f);
+        mq[o] = make_float2(0.f, 0.f);
+        mc[o] = 0.f;
+      }
 #pragma unroll
-        for (int o = 0; o < 4; ++o) mom[m][o] = 0.f;
+      for (int j = 0; j < 14; ++j) {
+        const float2 hxy = S.hxy[r0 + j][c], hq = S.hq[r0 + j][c];
+        const float hc = S.hc[r0 + j][c];
 #pragma unroll
-        for (int j = 0; j < 14; ++j) {
-          const float h = S.hm[m][r0 + j][c];
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            const int t = j - o;
-            if (t >= 0 && t < 11) mom[m][o] += w[t] * h;
+        for (int o = 0; o < 4; ++o) {
+          const int t = j - o;
+          if (t >= 0 && t < 11) {
+            mxy[o] = __ffma2_rn(w2[t], hxy, mxy[o]);
+            mq[o] = __ffma2_rn(w2[t], hq, mq[o]);
+            mc[o] = fmaf(w[t], hc, mc[o]);
           }
         }
       }
@@ -196,7 +215,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
       for (int o = 0; o < 4; ++o) {
         const int gy = oy + r0 + o, gx = ox + c;
         if (gx >= V.W || gy >= V.H) continue;
-        const float mx = mom[0][o], my = mom[1][o], exx = mom[2][o], eyy = mom[3][o], exy = mom[4][o];
+        const float mx = mxy[o].x, my = mxy[o].y, exx = mq[o].x, eyy = mq[o].y, exy = mc[o];
         const float N1 = 2.f * mx * my + kC1, N2 = 2.f * (exy - mx * my) + kC2;
         const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
         const float N = N1 * N2, D = D1 * D2;
@@ -300,6 +319,9 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   if (ctl->overflow) return;
   float w[11];
   window(w);
+  float2 w2[11];
+#pragma unroll
+  for (int t = 0; t < 11; ++t) w2[t] = make_float2(w[t], w[t]);
   const long long b = blockIdx.x;
   const int v = view_of_block(views, n_views, b);
   const ViewDev& V = views[v];
@@ -329,39 +351,68 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
       cp_async_wait<0>();
     }
     __syncthreads();
+    // this thread's four output pixels: fetch the render and target now, used after the blur
+    const int vc = threadIdx.x % kBX, vr0 = (threadIdx.x / kBX) * 4;
+    float xo[4], yo[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      const int gy = oy + vr0 + o, gx = ox + vc;
+      const bool in = gx < V.W && gy < V.H;
+      const long long pix = in ? (long long)gy * V.W + gx : 0;
+      xo[o] = in ? X[ch * HW + pix] : 0.f;
+      yo[o] = in ? Yt[ch * HW + pix] : 0.f;
+    }
     for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
       const int r = task >> 3, c0 = (task & 7) * 4;
+      float av[16], bv[16], cv[16];
+      load16(S.in[cur][0][r], c0, av);
+      load16(S.in[cur][1][r], c0, bv);
+      load16(S.in[cur][2][r], c0, cv);
+      float2 aab[4];
+      float ac[4];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        float pv[16];
-        load16(S.in[cur][m][r], c0, pv);
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int o = 0; o < 4; ++o) {
+        aab[o] = make_float2(0.f, 0.f);
+        ac[o] = 0.f;
+      }
 #pragma unroll
-        for (int j = 0; j < 14; ++j)
+      for (int j = 0; j < 14; ++j) {
+        const float2 v = make_float2(av[j], bv[j]);
 #pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            const int t = j - o;
-            if (t >= 0 && t < 11) acc[o] += w[t] * pv[j];
+        for (int o = 0; o < 4; ++o) {
+          const int t = j - o;
+          if (t >= 0 && t < 11) {
+            aab[o] = __ffma2_rn(w2[t], v, aab[o]);
+            ac[o] = fmaf(w[t], cv[j], ac[o]);
           }
+        }
+      }
 #pragma unroll
-        for (int o = 0; o < 4; ++o) S.hb[m][r][c0 + o] = acc[o];
+      for (int o = 0; o < 4; ++o) {
+        S.hab[r][c0 + o] = aab[o];
+        S.hc[r][c0 + o] = ac[o];
       }
     }
     __syncthreads();
     {
-      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
-      float bl[3][4];
+      const int c = vc, r0 = vr0;
+      float2 bab[4];
+      float bc[4];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
+      for (int o = 0; o < 4; ++o) {
+        bab[o] = make_float2(0.f, 0.f);
+        bc[o] = 0.f;
+      }
 #pragma unroll
-        for (int o = 0; o < 4; ++o) bl[m][o] = 0.f;
+      for (int j = 0; j < 14; ++j) {
+        const float2 h = S.hab[r0 + j][c];
+        const float hc = S.hc[r0 + j][c];
 #pragma unroll
-        for (int j = 0; j < 14; ++j) {
-          const float h = S.hb[m][r0 + j][c];
-#pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            const int t = j - o;
-            if (t >= 0 && t < 11) bl[m][o] += w[t] * h;
+        for (int o = 0; o < 4; ++o) {
+          const int t = j - o;
+          if (t >= 0 && t < 11) {
+            bab[o] = __ffma2_rn(w2[t], h, bab[o]);
+            bc[o] = fmaf(w[t], hc, bc[o]);
           }
         }
       }
@@ -370,10 +421,10 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
         const int gy = oy + r0 + o, gx = ox + c;
         if (gx >= V.W || gy >= V.H) continue;
         const long long pix = (long long)gy * V.W + gx;
-        const float xv = X[ch * HW + pix], yv = Yt[ch * HW + pix];
+        const float xv = xo[o], yv = yo[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        dX[ch * HW + pix] = gl1 * sgn + gs * (bl[0][o] + 2.f * xv * bl[1][o] + yv * bl[2][o]);
+        dX[ch * HW + pix] = gl1 * sgn + gs * (bab[o].x + 2.f * xv * bab[o].y + yv * bc[o]);
       }
     }
     __syncthreads();
