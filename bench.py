@@ -219,11 +219,13 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
     return cams, targets, pts
 
 
-def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0):
+def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
                             scene_extent=7.0, seed=3, batch_scaling=scaling)
+    if kernel_times:
+        sess.field.set_timing(True)
     pairs, add_s, int_s = 0, [], []
     t0 = time.perf_counter()
     for c, t, (xyz, rgb, tr) in zip(cams, targets, pts):
@@ -235,11 +237,16 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, 
     lat = sess.latency()
     psnr = sess.psnr(cams, targets)
     n = sess.field.stats()["n_gaussians"]
+    kt = None
+    if kernel_times:
+        kms, ksteps = sess.field.kernel_times()
+        kt = {nm: round(x / max(1, ksteps), 4) for nm, x in zip(KERNELS, kms)}
     torch.cuda.synchronize()
     sess.close()
     return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
                 pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn,
-                batch_scaling=scaling, add_image_mean_s=float(np.mean(add_s)), integrate_mean_s=float(np.mean(int_s)))
+                batch_scaling=scaling, add_image_mean_s=float(np.mean(add_s)), integrate_mean_s=float(np.mean(int_s)),
+                **({"kernel_ms_per_step": kt} if kt else {}))
 
 
 def run_gs(args):
@@ -374,13 +381,15 @@ def run_gs(args):
             run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1)
         plain = run_stream(cams, targets, pts, batch=1, graph=0, asyn=1)
         graphed = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16)
+        graphed_k = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16, kernel_times=True)
         batched = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16)
         batched_s = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16, scaling=1)
         batched3_s = run_stream(cams, targets, pts, batch=3, graph=1, asyn=16, scaling=1)
         lat = {"workload": f"{args.arrivals} arrivals, 1297x840, random walk with 60-80% overlap, 5k-20k sparse "
                            f"points each, T_I = 200 over the new image + 8 neighbours, 1.5M-Gaussian hidden scene",
                "autotune": f"tiling autotuned per class, cache filled by untimed sessions over the first {warm} arrivals",
-               "plain_per_view": plain, "graph_async_per_view": graphed, "batched_graph": batched,
+               "plain_per_view": plain, "graph_async_per_view": graphed,
+               "kernel_ms_per_step_graph_async": graphed_k["kernel_ms_per_step"], "batched_graph": batched,
                "batched_graph_scaled": batched_s, "batched3_graph_scaled": batched3_s}
 
     if rank == 0:

@@ -51,6 +51,8 @@ struct Control {
   unsigned long long gp_sq;     // sum of G_p^2 over those pixels
   unsigned int overflow;        // instance capacity exceeded
   unsigned int error;           // kErr* bits
+  unsigned int dmax;            // largest fp32 depth bits of a record with instances
+  unsigned int dnot;            // ~ smallest such bits (so that the cleared 0 is neutral)
   unsigned int scan_ticket;
   unsigned int sort_ticket[8];
   unsigned int bwd_work;
@@ -99,9 +101,22 @@ __device__ __forceinline__ float splat_power(float A, float B, float C, float dx
 
 __device__ __forceinline__ float splat_exp(float power) { return __expf(power); }
 
-// 64-bit global-tile/depth key helpers.
-__device__ __forceinline__ unsigned long long make_key(unsigned long long tile, float depth) {
-  return (tile << 32) | (unsigned long long)__float_as_uint(depth);
+// Sort key layout of a step: (global tile << D) | (fp32 depth bits - smallest depth bits of the
+// step), D the bits that difference needs (positive floats order like their bits, so the
+// difference keeps the order); and the 8-bit passes the tile_bits + D key bits need.
+struct KeyLayout {
+  int D;
+  int passes;
+  unsigned dmin;
+};
+__device__ __forceinline__ KeyLayout key_layout(const Control* ctl, int tile_bits) {
+  KeyLayout k;
+  const unsigned dmax = ctl->dmax, dnot = ctl->dnot;
+  k.dmin = ~dnot;
+  const unsigned span = (dmax | dnot) ? dmax - k.dmin : 0u;
+  k.D = span ? 32 - __clz(span) : 0;
+  k.passes = (tile_bits + k.D + 7) / 8;
+  return k;
 }
 
 // Bounded spin limit for inter-CTA waits (decoupled look-back).  On expiry the waiting CTA sets

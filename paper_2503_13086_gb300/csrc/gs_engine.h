@@ -44,11 +44,10 @@ struct Raster {
   ~Raster();
 
   // problem of the current step
-  int n = 0, stride = 0, n_views = 0, passes = 0;
+  int n = 0, stride = 0, n_views = 0, passes = 0, tile_bits = 0;
   long long n_tiles = 0, n_pix = 0, n_loss_blocks = 0;
   std::vector<ViewDev> views;
   bool have_forward = false;
-  int sorted = 0;  // which ping-pong buffer holds the sorted list
   int num_sms = 1;
   Tiling tiling;   // tile shape and K6 batch of the next step
 

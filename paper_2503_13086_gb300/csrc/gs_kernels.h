@@ -52,12 +52,15 @@ void launch_adam(float* params, const float* grads, float* m, float* v, int n, i
                  cudaStream_t s);
 
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
-                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s);
-void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys,
-                 unsigned* vals, unsigned* hist, int passes, const Control* ctl, cudaStream_t s);
-void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout, unsigned* vout,
-                      const unsigned* hist, unsigned* state, int pass, long long m_cap, Control* ctl, cudaStream_t s);
-void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s);
+                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth = nullptr);
+void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
+                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* hist, int tile_bits,
+                 const Control* ctl, cudaStream_t s);
+void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long long* keys1, unsigned* vals1,
+                      const unsigned* hist, unsigned* state, int pass, int tile_bits, long long m_cap, Control* ctl,
+                      cudaStream_t s);
+void launch_ranges(const unsigned long long* keys, uint2* ranges, int tile_bits, long long m_cap, const Control* ctl,
+                   cudaStream_t s);
 
 void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const Control* ctl, cudaStream_t s);
 void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,

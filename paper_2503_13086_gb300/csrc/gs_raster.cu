@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "gs_engine.h"
 
@@ -181,7 +182,8 @@ gs_status Raster::set_views(const gs_camera* cams, int nv, const float* const* t
   n_tiles = tb;
   n_pix = pb;
   n_loss_blocks = lb;
-  passes = (32 + bits_for(n_tiles - 1) + kSortBits - 1) / kSortBits;
+  tile_bits = bits_for(n_tiles - 1);
+  passes = (32 + tile_bits + kSortBits - 1) / kSortBits;  // at most; the step may need fewer
   if (passes > kMaxSortPasses) return fail(GS_ERR_CAPACITY, "too many tiles");
   return GS_OK;
 }
@@ -277,7 +279,8 @@ gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int 
   launch_project(params, stride_, n_views, sp(), vd(), proj(), s);
   mark(s, 1);
   const long long n_items = (long long)n_views * stride_;
-  launch_scan(proj().count, proj().offsets, n_items, scan_state(), ctl(), size_exactly ? ~0ull : m_cap, ledger(), s);
+  launch_scan(proj().count, proj().offsets, n_items, scan_state(), ctl(), size_exactly ? ~0ull : m_cap, ledger(), s,
+              proj().depth);
   mark(s, 2);
   if (size_exactly) {
     cudaMemcpyAsync(ctl_h, ctl(), sizeof(Control), cudaMemcpyDeviceToHost, s);
@@ -295,21 +298,21 @@ gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int 
 gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp) {
   cudaMemsetAsync(zeroB.p, 0, zeroB_bytes, s);
   const long long n_items = (long long)n_views * stride;
-  launch_emit(proj(), vd(), stride, n_items, static_cast<unsigned long long*>(keys0.p), static_cast<unsigned*>(vals0.p),
-              hist(), passes, ctl(), s);
+  unsigned long long* k0 = static_cast<unsigned long long*>(keys0.p);
+  unsigned long long* k1 = static_cast<unsigned long long*>(keys1.p);
+  unsigned* v0 = static_cast<unsigned*>(vals0.p);
+  unsigned* v1 = static_cast<unsigned*>(vals1.p);
+  launch_emit(proj(), vd(), stride, n_items, k0, v0, k1, v1, hist(), tile_bits, ctl(), s);
   mark(s, 3);
-  unsigned long long* kb[2] = {static_cast<unsigned long long*>(keys0.p), static_cast<unsigned long long*>(keys1.p)};
-  unsigned* vb[2] = {static_cast<unsigned*>(vals0.p), static_cast<unsigned*>(vals1.p)};
   const unsigned long long sort_tiles = (m_cap + kSortTile - 1) / kSortTile;
-  for (int p = 0; p < passes; ++p)
-    launch_sort_pass(kb[p & 1], vb[p & 1], kb[(p + 1) & 1], vb[(p + 1) & 1], hist(),
-                     sort_state() + (size_t)p * sort_tiles * kSortBins, p, (long long)m_cap, ctl(), s);
-  sorted = passes & 1;
+  for (int p = 0; p < passes; ++p)  // passes the step does not need return at once; the list ends in buffer 0
+    launch_sort_pass(k0, v0, k1, v1, hist(), sort_state() + (size_t)p * sort_tiles * kSortBins, p, tile_bits,
+                     (long long)m_cap, ctl(), s);
   mark(s, 4);
-  launch_ranges(kb[sorted], ranges(), (long long)m_cap, ctl(), s);
+  launch_ranges(k0, ranges(), tile_bits, (long long)m_cap, ctl(), s);
   launch_tile_order(ranges(), n_tiles, static_cast<int*>(order.p), ctl(), s);
   mark(s, 5);
-  launch_blend_forward(tiling, vd(), n_views, n_tiles, ranges(), vb[sorted], proj(), sp(), ctl(),
+  launch_blend_forward(tiling, vd(), n_views, n_tiles, ranges(), v0, proj(), sp(), ctl(),
                        static_cast<const int*>(order.p), image, T, last, gp, static_cast<float4*>(ckpt.p),
                        static_cast<unsigned*>(cmask.p), chunk_tile(), static_cast<int*>(tile_chunks.p), num_sms, s);
   mark(s, 6);
@@ -323,7 +326,7 @@ void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
 }
 
 void Raster::enqueue_blend_backward(cudaStream_t s, const float* image, const float* dimage) {
-  launch_blend_backward(tiling, vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(sorted ? vals1.p : vals0.p), proj(),
+  launch_blend_backward(tiling, vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(vals0.p), proj(),
                         ctl(), image, dimage, static_cast<float4*>(ckpt.p), static_cast<unsigned*>(cmask.p),
                         chunk_tile(), static_cast<int*>(tile_chunks.p), static_cast<float4*>(ginst.p), num_sms, s);
   mark(s, 8);
@@ -520,8 +523,8 @@ gs_status gs_raster_read(gs_raster* rr, int which, void* host_dst, size_t capaci
     case 5: src = r->rect.p; bytes = recs * 8; break;
     case 6: src = r->count.p; bytes = recs * 4; break;
     case 7: src = r->offsets.p; bytes = recs * 4; break;
-    case 8: src = r->sorted ? r->keys1.p : r->keys0.p; bytes = M * 8; break;
-    case 9: src = r->sorted ? r->vals1.p : r->vals0.p; bytes = M * 4; break;
+    case 8: bytes = M * 8; break;  // assembled below: the sort keeps only the depth bits that vary
+    case 9: src = r->vals0.p; bytes = M * 4; break;
     case 10: src = r->ranges(); bytes = (size_t)r->n_tiles * 8; break;
     case 11: src = r->clamp.p; bytes = recs; break;
     case 12: src = r->ginst.p; bytes = M * 48; break;
@@ -530,6 +533,24 @@ gs_status gs_raster_read(gs_raster* rr, int which, void* host_dst, size_t capaci
   if (out_bytes) *out_bytes = bytes;
   if (!host_dst) return GS_OK;
   if (capacity < bytes) return fail(GS_ERR_INVALID_ARG, "host buffer too small");
+  if (which == 8) {
+    // the sorted (global tile << 32 | fp32 depth bits) keys, in list order
+    std::vector<unsigned> v(M);
+    std::vector<uint2> rg((size_t)r->n_tiles);
+    std::vector<float> depth(recs);
+    if ((M && cudaMemcpy(v.data(), r->vals0.p, M * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (r->n_tiles && cudaMemcpy(rg.data(), r->ranges(), rg.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (recs && cudaMemcpy(depth.data(), r->depth.p, recs * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
+      return fail(GS_ERR_CUDA, "reading the tile lists failed");
+    unsigned long long* out = static_cast<unsigned long long*>(host_dst);
+    for (size_t t = 0; t < rg.size(); ++t)
+      for (unsigned i = rg[t].x; i < rg[t].y && i < M; ++i) {
+        unsigned bits = 0;
+        std::memcpy(&bits, &depth[v[i]], 4);
+        out[i] = ((unsigned long long)t << 32) | bits;
+      }
+    return GS_OK;
+  }
   if (bytes) {
     e = cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));

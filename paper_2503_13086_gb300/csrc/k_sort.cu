@@ -4,7 +4,9 @@
 // These implement the tile-binning of the 3DGS rasterizer the paper builds on (Sec. III; the
 // "original 3DGS" settings of Sec. V-A).  Canonical order: (global tile, fp32 depth bits,
 // record index).  Instances are emitted in record order and every sort pass is stable, so the
-// record index breaks depth ties.  Every count lives in device memory: no kernel here needs the
+// record index breaks depth ties.  The key holds only the depth bits that vary within the step
+// (their range comes out of the scan), so a step usually needs 5 passes of 8 bits instead of 6; the
+// number of passes is decided on the device and the passes always end in buffer 0.  Every count lives in device memory: no kernel here needs the
 // host to know how many instances were emitted, so the whole chain can be graph-captured.
 // The inter-CTA waits (decoupled look-back) spin at most kSpinLimit times, then flag
 // kErrTimeout and carry on rather than hang.
@@ -35,7 +37,7 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restrict__ in, unsigned* __restrict__ out,
                                                        long long n_items, unsigned long long* __restrict__ state,
                                                        Control* __restrict__ ctl, unsigned long long m_cap,
-                                                       Ledger* __restrict__ ledger) {
+                                                       Ledger* __restrict__ ledger, const float* __restrict__ depth) {
   __shared__ unsigned s_tile;
   __shared__ unsigned s_warp[kScanThreads / 32];
   __shared__ unsigned long long s_excl;
@@ -57,8 +59,24 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
   unsigned tsum = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) tsum += x[k];
-  // block-wide exclusive scan of the per-thread sums
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (depth) {  // range of the depth bits of the records with instances (the sort key layout)
+    unsigned dmax = 0u, dnot = 0u;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (x[k]) {
+        const unsigned b = __float_as_uint(depth[base + k]);
+        dmax = max(dmax, b);
+        dnot = max(dnot, ~b);
+      }
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    dnot = __reduce_max_sync(0xffffffffu, dnot);
+    if (lane == 0 && (dmax | dnot)) {
+      atomicMax(&ctl->dmax, dmax);
+      atomicMax(&ctl->dnot, dnot);
+    }
+  }
+  // block-wide exclusive scan of the per-thread sums
   unsigned incl = tsum;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -138,9 +156,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
 }
 
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
-                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s) {
+                 unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth) {
   const long long tiles = (n_items + kScanTile - 1) / kScanTile;
-  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap, ledger);
+  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap, ledger, depth);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -150,8 +168,9 @@ void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned 
 // large Gaussian does not stall its warp.  Also histograms every radix digit for the sort.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDev* __restrict__ views, int stride,
-                                              long long n_items, unsigned long long* __restrict__ keys,
-                                              unsigned* __restrict__ vals, unsigned* __restrict__ hist, int passes,
+                                              long long n_items, unsigned long long* __restrict__ keys0,
+                                              unsigned* __restrict__ vals0, unsigned long long* __restrict__ keys1,
+                                              unsigned* __restrict__ vals1, unsigned* __restrict__ hist, int tile_bits,
                                               const Control* __restrict__ ctl) {
   __shared__ unsigned s_hist[kMaxSortPasses][kSortBins];
   for (int k = threadIdx.x; k < kMaxSortPasses * kSortBins; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
@@ -159,6 +178,12 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
   const bool skip = ctl->overflow != 0u;
   const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  // the passes end in buffer 0: start in buffer (passes & 1)
+  const KeyLayout kl = key_layout(ctl, tile_bits);
+  const int passes = kl.passes;
+  const int depth_passes = min(passes, kl.D / kSortBits);
+  unsigned long long* __restrict__ keys = (passes & 1) ? keys1 : keys0;
+  unsigned* __restrict__ vals = (passes & 1) ? vals1 : vals0;
   // n_items is a multiple of 32, so a warp is either wholly in range or wholly out.
   if (!skip && rec - lane < n_items) {
     const unsigned cnt = pb.count[rec];
@@ -169,6 +194,11 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
     const ViewDev& V = views[v];
     const uint2 rc = cnt ? pb.rect[rec] : make_uint2(0u, 0u);
     const unsigned dbits = cnt ? __float_as_uint(pb.depth[rec]) : 0u;
+    // passes whose digit lies inside the depth part of the key: every instance of a record has the
+    // record's digit, so the record adds its instance count once
+    if (cnt)
+      for (int p = 0; p < depth_passes; ++p)
+        atomicAdd(&s_hist[p][((dbits - kl.dmin) >> (p * kSortBits)) & (kSortBins - 1)], cnt);
     const long long tbase = V.tile_base;
     const int gx = V.gx;
     for (unsigned e0 = wbeg; e0 < wend; e0 += 32) {
@@ -193,10 +223,13 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
         const unsigned w = x1 - x0;
         const unsigned ty = y0 + k / w, tx = x0 + k % w;
         const unsigned long long tile = (unsigned long long)(o_tb + (long long)ty * o_gx + tx);
-        const unsigned long long key = (tile << 32) | (unsigned long long)o_db;
+        const unsigned long long key = (tile << kl.D) | (unsigned long long)(o_db - kl.dmin);
         keys[e] = key;
         vals[e] = o_rec;
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
+        // digit histograms of the passes that see tile bits (the depth-only ones are added per
+        // record below)
+        for (int p = depth_passes; p < passes; ++p)
+          atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
       }
     }
   }
@@ -207,9 +240,11 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
   }
 }
 
-void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys,
-                 unsigned* vals, unsigned* hist, int passes, const Control* ctl, cudaStream_t s) {
-  k_emit<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb, views, stride, n_items, keys, vals, hist, passes, ctl);
+void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
+                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* hist, int tile_bits,
+                 const Control* ctl, cudaStream_t s) {
+  k_emit<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb, views, stride, n_items, keys0, vals0, keys1, vals1, hist,
+                                                           tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -227,16 +262,24 @@ struct SortSmem {
   unsigned tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(const unsigned long long* __restrict__ kin,
-                                                            const unsigned* __restrict__ vin,
-                                                            unsigned long long* __restrict__ kout,
-                                                            unsigned* __restrict__ vout,
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(unsigned long long* __restrict__ keys0,
+                                                            unsigned* __restrict__ vals0,
+                                                            unsigned long long* __restrict__ keys1,
+                                                            unsigned* __restrict__ vals1,
                                                             const unsigned* __restrict__ hist,
-                                                            unsigned* __restrict__ state, int pass,
+                                                            unsigned* __restrict__ state, int pass, int tile_bits,
                                                             Control* __restrict__ ctl) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
   if (ctl->overflow) return;
+  // passes beyond the step's key bits do nothing; pass j reads buffer (passes - j) & 1
+  const int passes = key_layout(ctl, tile_bits).passes;
+  if (pass >= passes) return;
+  const bool from1 = ((passes - pass) & 1) != 0;
+  const unsigned long long* __restrict__ kin = from1 ? keys1 : keys0;
+  const unsigned* __restrict__ vin = from1 ? vals1 : vals0;
+  unsigned long long* __restrict__ kout = from1 ? keys0 : keys1;
+  unsigned* __restrict__ vout = from1 ? vals0 : vals1;
   const unsigned long long M = ctl->m_total;
   if (threadIdx.x == 0) S.tile = atomicAdd(&ctl->sort_ticket[pass], 1u);
   for (int k = threadIdx.x; k < (kSortThreads / 32) * kSortBins; k += kSortThreads) (&S.cnt[0][0])[k] = 0u;
@@ -360,12 +403,12 @@ void init_sort_attributes() {
   cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SortSmem));
 }
 
-void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsigned long long* kout, unsigned* vout,
-                      const unsigned* hist, unsigned* state, int pass, long long m_cap, Control* ctl,
+void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long long* keys1, unsigned* vals1,
+                      const unsigned* hist, unsigned* state, int pass, int tile_bits, long long m_cap, Control* ctl,
                       cudaStream_t s) {
   const long long tiles = (m_cap + kSortTile - 1) / kSortTile;
   k_sort_pass<<<(unsigned)(tiles > 0 ? tiles : 1), kSortThreads, sizeof(SortSmem), s>>>(
-      kin, vin, kout, vout, hist, state, pass, ctl);
+      keys0, vals0, keys1, vals1, hist, state, pass, tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -373,22 +416,24 @@ void launch_sort_pass(const unsigned long long* kin, const unsigned* vin, unsign
 // left them.  Grid-stride over the device-resident instance count.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ranges(const unsigned long long* __restrict__ keys, uint2* __restrict__ ranges,
-                                                const Control* __restrict__ ctl) {
+                                                int tile_bits, const Control* __restrict__ ctl) {
   if (ctl->overflow) return;
   const unsigned long long M = ctl->m_total;
+  const int D = key_layout(ctl, tile_bits).D;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < M;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned tile = (unsigned)(keys[i] >> 32);
-    if (i == 0 || (unsigned)(keys[i - 1] >> 32) != tile) ranges[tile].x = (unsigned)i;
-    if (i == M - 1 || (unsigned)(keys[i + 1] >> 32) != tile) ranges[tile].y = (unsigned)(i + 1);
+    const unsigned tile = (unsigned)(keys[i] >> D);
+    if (i == 0 || (unsigned)(keys[i - 1] >> D) != tile) ranges[tile].x = (unsigned)i;
+    if (i == M - 1 || (unsigned)(keys[i + 1] >> D) != tile) ranges[tile].y = (unsigned)(i + 1);
   }
 }
 
-void launch_ranges(const unsigned long long* keys, uint2* ranges, long long m_cap, const Control* ctl, cudaStream_t s) {
+void launch_ranges(const unsigned long long* keys, uint2* ranges, int tile_bits, long long m_cap, const Control* ctl,
+                   cudaStream_t s) {
   long long blocks = (m_cap + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, ranges, ctl);
+  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, ranges, tile_bits, ctl);
 }
 
 }  // namespace gs
