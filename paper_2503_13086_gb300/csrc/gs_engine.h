@@ -30,9 +30,9 @@ struct DevBuf {
 };
 
 constexpr int kMaxViews = 32;
-// kernel launches of one optimisation step besides the sort passes: K1, K2, K3, K5 x 2, K6, K7 x 2,
-// K8, K9a, K9
-constexpr int kStepLaunchesBase = 11;
+// kernel launches of one optimisation step besides the sort passes: K1, K2, K3 x 2, K5 x 2, K6,
+// K7 x 2, K8, K9a x 2, K9
+constexpr int kStepLaunchesBase = 13;
 constexpr int kNumKernels = 9;
 constexpr int kNumEvents = kNumKernels + 1;
 constexpr size_t kCtlBytes = 1024;                                   // Control, padded
@@ -58,6 +58,7 @@ struct Raster {
   size_t zeroA_bytes = 0, zeroB_bytes = 0, sort_state_bytes = 0, ranges_bytes = 0, chunk_bytes = 0;
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp, g2s;
   DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order, tile_chunks;
+  DevBuf inst_rec, block_owner, carry;  // instance -> record, owner of every 256th instance, K9a partials
   DevBuf partials, block_sums;
   DevBuf ledger_d;  // Ledger of the current run of steps
   DevBuf own_image, own_last, own_dimage;  // used by sessions

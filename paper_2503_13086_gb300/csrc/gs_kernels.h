@@ -46,16 +46,17 @@ void launch_project(const float* params, int stride, int n_views, const StepPara
 // K9a (per-record sums of the instance gradients, into g2s: 9 planes of views x stride floats) and
 // K9 + K10.
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
-                             const ProjBuffers& pb, const float4* ginst, float* g2s, const Control* ctl,
-                             float* grads_out, float* m, float* v, float* grad2d_out, cudaStream_t s);
+                             const ProjBuffers& pb, const float4* ginst, const unsigned* inst_rec, float* carry,
+                             long long m_cap, float* g2s, const Control* ctl, float* grads_out, float* m, float* v,
+                             float* grad2d_out, int num_sms, cudaStream_t s);
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
                  cudaStream_t s);
 
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
                  unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth = nullptr);
 void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
-                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* hist, int tile_bits,
-                 const Control* ctl, cudaStream_t s);
+                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* block_owner,
+                 unsigned* hist, int tile_bits, int num_sms, const Control* ctl, cudaStream_t s);
 void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long long* keys1, unsigned* vals1,
                       const unsigned* hist, unsigned* state, int pass, int tile_bits, long long m_cap, Control* ctl,
                       cudaStream_t s);

@@ -391,72 +391,93 @@ __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, uns
   apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
 }
 
-// K9a: per record (view, Gaussian), the sum of its instances' nine gradients.  A record's instances
-// are contiguous (its tiles, in emission order), so a warp takes the instances of its 32 records
-// as one contiguous run, 32 at a time (coalesced), and adds each lane's instance into its owner's
-// sum by a segmented scan over the lanes; the segment's last lane adds the total into the owner's
-// accumulator in shared memory (one writer per owner and round, rounds in order: deterministic).
-// Output: g2s, 9 planes of n_items floats (record-major inside a plane); grad2d (nullable) the same
-// sums as 9 consecutive floats per record.
-__global__ void __launch_bounds__(256) k_record_grads(const unsigned* __restrict__ count,
-                                                      const unsigned* __restrict__ offsets,
-                                                      const float4* __restrict__ ginst, long long n_items,
-                                                      const Control* __restrict__ ctl, float* __restrict__ g2s,
-                                                      float* __restrict__ grad2d) {
-  __shared__ float s_acc[8][9][33];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ctl->overflow || rec - lane >= n_items) return;  // warp-uniform: n_items is a multiple of 32
-#pragma unroll
-  for (int k = 0; k < 9; ++k) s_acc[warp][k][lane] = 0.f;
-  const unsigned cnt = count[rec];
-  const unsigned off = offsets[rec];
-  const unsigned wbeg = __shfl_sync(0xffffffffu, off, 0);
-  const unsigned wend = __shfl_sync(0xffffffffu, off + cnt, 31);
-  __syncwarp();
-  for (unsigned e0 = wbeg; e0 < wend; e0 += 32) {
-    const unsigned e = e0 + lane;
-    // owner = largest lane whose offset is <= e
-    int owner = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-      const unsigned oc = __shfl_sync(0xffffffffu, off, owner + step);
-      if (oc <= e) owner += step;
-    }
+// K9a: per record (view, Gaussian), the sum of its instances' nine gradients (a reduce by key over
+// the instances, whose records are non-decreasing in emission order).  Warps take 32-instance
+// chunks (coalesced) and sum each record's run inside the chunk by a segmented scan over the
+// lanes.  A run that lies inside one chunk is the record's sum; a run cut by a chunk boundary is
+// a partial: the chunk's first run (record started earlier) goes to head[chunk], its last run
+// (record continues) to tail[chunk]; k_inst_carry adds, per record that spans chunks, its tail
+// partial, the middle chunks' heads and the last chunk's head, in chunk order (deterministic).
+// Output: g2s, 9 planes of n_rec floats; grad2d (nullable) the same as 9 floats per record.
+__global__ void __launch_bounds__(256) k_inst_reduce(const unsigned* __restrict__ inst_rec,
+                                                     const float4* __restrict__ ginst,
+                                                     const unsigned* __restrict__ count,
+                                                     const unsigned* __restrict__ offsets, long long n_rec,
+                                                     const Control* __restrict__ ctl, float* __restrict__ g2s,
+                                                     float* __restrict__ grad2d, float* __restrict__ head,
+                                                     float* __restrict__ tail) {
+  if (ctl->overflow) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long M = ctl->m_total;
+  const unsigned long long n_chunks = (M + 31) >> 5;
+  const unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long n_warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long c = w0; c < n_chunks; c += n_warps) {
+    const unsigned long long e = (c << 5) + lane;
+    const bool valid = e < M;
+    const unsigned r = valid ? inst_rec[e] : 0xffffffffu;
     float x[9];
-    if (e < wend) {
-      const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], c = ginst[3ull * e + 2];
+    if (valid) {
+      const float4 a = ginst[3ull * e], b = ginst[3ull * e + 1], cc = ginst[3ull * e + 2];
       x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
       x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-      x[8] = c.x;
+      x[8] = cc.x;
     } else {
-      owner = 32;  // past the run: a segment of its own
 #pragma unroll
       for (int k = 0; k < 9; ++k) x[k] = 0.f;
     }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      const int od = __shfl_up_sync(0xffffffffu, owner, d);
-      const bool same = lane >= d && od == owner;
+      const unsigned rd = __shfl_up_sync(0xffffffffu, r, d);
+      const bool same = lane >= d && rd == r;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const float y = __shfl_up_sync(0xffffffffu, x[k], d);
         if (same) x[k] += y;
       }
     }
-    const int next_owner = __shfl_down_sync(0xffffffffu, owner, 1);
-    if (owner < 32 && (lane == 31 || next_owner != owner)) {
+    const unsigned r_next = __shfl_down_sync(0xffffffffu, r, 1);
+    if (valid && (lane == 31 || r_next != r)) {
+      const unsigned long long off = offsets[r], cnt = count[r];
+      const bool begins = off >= (c << 5);
+      const bool ends = off + cnt - 1 == e;
+      if (begins && ends) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) s_acc[warp][k][owner] += x[k];
+        for (int k = 0; k < 9; ++k) {
+          g2s[k * n_rec + r] = x[k];
+          if (grad2d) grad2d[9ull * r + k] = x[k];
+        }
+      } else {
+        float* dst = (begins ? tail : head) + 9 * c;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dst[k] = x[k];
+      }
     }
-    __syncwarp();
   }
-  const long long n_rec = n_items;
+}
+
+__global__ void __launch_bounds__(256) k_inst_carry(const unsigned* __restrict__ count,
+                                                    const unsigned* __restrict__ offsets, long long n_rec,
+                                                    const Control* __restrict__ ctl, const float* __restrict__ head,
+                                                    const float* __restrict__ tail, float* __restrict__ g2s,
+                                                    float* __restrict__ grad2d) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl->overflow || r >= n_rec) return;
+  const unsigned long long cnt = count[r];
+  if (!cnt) return;
+  const unsigned long long off = offsets[r];
+  const unsigned long long c0 = off >> 5, c1 = (off + cnt - 1) >> 5;
+  if (c0 == c1) return;  // summed inside one chunk
+  float x[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) x[k] = tail[9 * c0 + k];
+  for (unsigned long long c = c0 + 1; c <= c1; ++c)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) x[k] += head[9 * c + k];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    const float v = s_acc[warp][k][lane];
-    g2s[k * n_rec + rec] = v;
-    if (grad2d) grad2d[9 * rec + k] = v;
+    g2s[k * n_rec + r] = x[k];
+    if (grad2d) grad2d[9ull * r + k] = x[k];
   }
 }
 
@@ -805,12 +826,18 @@ void launch_project(const float* params, int stride, int n_views, const StepPara
 }
 
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
-                             const ProjBuffers& pb, const float4* ginst, float* g2s, const Control* ctl,
-                             float* grads_out, float* m, float* v, float* grad2d_out, cudaStream_t s) {
-  const long long n_items = (long long)n_views * stride;
-  if (n_items > 0)
-    k_record_grads<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, ginst, n_items, ctl, g2s,
-                                                                     grad2d_out);
+                             const ProjBuffers& pb, const float4* ginst, const unsigned* inst_rec, float* carry,
+                             long long m_cap, float* g2s, const Control* ctl, float* grads_out, float* m, float* v,
+                             float* grad2d_out, int num_sms, cudaStream_t s) {
+  const long long n_rec = (long long)n_views * stride;
+  if (n_rec > 0) {
+    float* head = carry;
+    float* tail = carry + 9 * ((m_cap + 31) / 32 + 1);
+    k_inst_reduce<<<(unsigned)(num_sms * 8), 256, 0, s>>>(inst_rec, ginst, pb.count, pb.offsets, n_rec, ctl, g2s,
+                                                         grad2d_out, head, tail);
+    k_inst_carry<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, n_rec, ctl, head, tail, g2s,
+                                                                 grad2d_out);
+  }
   const unsigned grid = (unsigned)((stride + 255) / 256);
   if (n_views <= 1)
     k_project_backward<1><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.clamp, g2s, ctl,

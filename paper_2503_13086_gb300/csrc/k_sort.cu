@@ -162,74 +162,71 @@ void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned 
 }
 
 // ---------------------------------------------------------------------------------------------
-// K3: key emission.  The 32 records of a warp share their instances out evenly: lane l writes
-// instances e0 + l, e0 + 32 + l, ... of the warp's contiguous instance range and finds the
-// owning record by a binary search over the lanes' offsets.  Writes are fully coalesced and a
-// large Gaussian does not stall its warp.  Also histograms every radix digit for the sort.
+// K3: duplication into (tile, depth) keys, one thread per instance.  The owner record of
+// instance e is the last record whose offset is <= e; block_owner[b] holds the owner of instance
+// 256 b, so each thread binary-searches only the records between two block owners.  Also
+// histograms every radix digit for the sort (the passes whose digit lies in the depth part of the
+// key once per record, through the thread of its first instance).
 // ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_block_owner(const unsigned* __restrict__ count,
+                                                     const unsigned* __restrict__ offsets, long long n_items,
+                                                     unsigned* __restrict__ block_owner,
+                                                     const Control* __restrict__ ctl) {
+  const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctl->overflow || rec >= n_items) return;
+  const unsigned cnt = count[rec];
+  if (!cnt) return;
+  const unsigned long long off = offsets[rec], end = off + cnt;
+  for (unsigned long long b = (off + 255) >> 8; (b << 8) < end; ++b) block_owner[b] = (unsigned)rec;
+}
+
 __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDev* __restrict__ views, int stride,
                                               long long n_items, unsigned long long* __restrict__ keys0,
                                               unsigned* __restrict__ vals0, unsigned long long* __restrict__ keys1,
-                                              unsigned* __restrict__ vals1, unsigned* __restrict__ hist, int tile_bits,
-                                              const Control* __restrict__ ctl) {
+                                              unsigned* __restrict__ vals1, unsigned* __restrict__ inst_rec,
+                                              const unsigned* __restrict__ block_owner, unsigned* __restrict__ hist,
+                                              int tile_bits, const Control* __restrict__ ctl) {
   __shared__ unsigned s_hist[kMaxSortPasses][kSortBins];
   for (int k = threadIdx.x; k < kMaxSortPasses * kSortBins; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
   __syncthreads();
-  const bool skip = ctl->overflow != 0u;
-  const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
   // the passes end in buffer 0: start in buffer (passes & 1)
   const KeyLayout kl = key_layout(ctl, tile_bits);
   const int passes = kl.passes;
   const int depth_passes = min(passes, kl.D / kSortBits);
   unsigned long long* __restrict__ keys = (passes & 1) ? keys1 : keys0;
   unsigned* __restrict__ vals = (passes & 1) ? vals1 : vals0;
-  // n_items is a multiple of 32, so a warp is either wholly in range or wholly out.
-  if (!skip && rec - lane < n_items) {
-    const unsigned cnt = pb.count[rec];
-    const unsigned off = pb.offsets[rec];
-    const unsigned wbeg = __shfl_sync(0xffffffffu, off, 0);
-    const unsigned wend = __shfl_sync(0xffffffffu, off + cnt, 31);
-    const int v = (int)(rec / stride);
-    const ViewDev& V = views[v];
-    const uint2 rc = cnt ? pb.rect[rec] : make_uint2(0u, 0u);
-    const unsigned dbits = cnt ? __float_as_uint(pb.depth[rec]) : 0u;
-    // passes whose digit lies inside the depth part of the key: every instance of a record has the
-    // record's digit, so the record adds its instance count once
-    if (cnt)
-      for (int p = 0; p < depth_passes; ++p)
-        atomicAdd(&s_hist[p][((dbits - kl.dmin) >> (p * kSortBits)) & (kSortBins - 1)], cnt);
-    const long long tbase = V.tile_base;
-    const int gx = V.gx;
-    for (unsigned e0 = wbeg; e0 < wend; e0 += 32) {
-      const unsigned e = e0 + lane;
-      // owner = largest lane whose offset <= e (offsets are non-decreasing across the warp)
-      int lo = 0;
-#pragma unroll
-      for (int step = 16; step >= 1; step >>= 1) {
-        const unsigned oc = __shfl_sync(0xffffffffu, off, lo + step);
-        if (oc <= e) lo += step;
+  if (!ctl->overflow) {
+    const unsigned long long M = ctl->m_total;
+    const unsigned long long nblk = (M + 255) >> 8;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < M;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+      const unsigned long long b = e >> 8;
+      unsigned lo = block_owner[b];
+      unsigned hi = b + 1 < nblk ? block_owner[b + 1] : (unsigned)(n_items - 1);
+      while (lo < hi) {
+        const unsigned mid = lo + ((hi - lo + 1) >> 1);
+        if (pb.offsets[mid] <= e) lo = mid;
+        else hi = mid - 1;
       }
-      const unsigned o_off = __shfl_sync(0xffffffffu, off, lo);
-      const unsigned o_rx = __shfl_sync(0xffffffffu, rc.x, lo);
-      const unsigned o_ry = __shfl_sync(0xffffffffu, rc.y, lo);
-      const unsigned o_db = __shfl_sync(0xffffffffu, dbits, lo);
-      const long long o_tb = __shfl_sync(0xffffffffu, tbase, lo);
-      const int o_gx = __shfl_sync(0xffffffffu, gx, lo);
-      const unsigned o_rec = (unsigned)__shfl_sync(0xffffffffu, (unsigned)rec, lo);
-      if (e < wend) {
-        const unsigned k = e - o_off;
-        const unsigned x0 = o_rx & 0xffffu, x1 = o_rx >> 16, y0 = o_ry & 0xffffu;
-        const unsigned w = x1 - x0;
-        const unsigned ty = y0 + k / w, tx = x0 + k % w;
-        const unsigned long long tile = (unsigned long long)(o_tb + (long long)ty * o_gx + tx);
-        const unsigned long long key = (tile << kl.D) | (unsigned long long)(o_db - kl.dmin);
-        keys[e] = key;
-        vals[e] = o_rec;
-        // digit histograms of the passes that see tile bits (the depth-only ones are added per
-        // record below)
-        for (int p = depth_passes; p < passes; ++p)
-          atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
+      const unsigned rec = lo;
+      const unsigned k = (unsigned)(e - pb.offsets[rec]);
+      const uint2 rc = pb.rect[rec];
+      const unsigned db = __float_as_uint(pb.depth[rec]);
+      const ViewDev& V = views[rec / (unsigned)stride];
+      const unsigned x0 = rc.x & 0xffffu, x1 = rc.x >> 16, y0 = rc.y & 0xffffu;
+      const unsigned w = x1 - x0;
+      const unsigned ty = y0 + k / w, tx = x0 + k % w;
+      const unsigned long long tile = (unsigned long long)(V.tile_base + (long long)ty * V.gx + tx);
+      const unsigned long long key = (tile << kl.D) | (unsigned long long)(db - kl.dmin);
+      keys[e] = key;
+      vals[e] = rec;
+      inst_rec[e] = rec;
+      for (int p = depth_passes; p < passes; ++p)
+        atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
+      if (k == 0) {  // every instance of the record has the record's depth digits
+        const unsigned cnt = pb.count[rec];
+        for (int p = 0; p < depth_passes; ++p)
+          atomicAdd(&s_hist[p][((db - kl.dmin) >> (p * kSortBits)) & (kSortBins - 1)], cnt);
       }
     }
   }
@@ -241,10 +238,12 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
 }
 
 void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
-                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* hist, int tile_bits,
-                 const Control* ctl, cudaStream_t s) {
-  k_emit<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb, views, stride, n_items, keys0, vals0, keys1, vals1, hist,
-                                                           tile_bits, ctl);
+                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* block_owner,
+                 unsigned* hist, int tile_bits, int num_sms, const Control* ctl, cudaStream_t s) {
+  if (n_items <= 0) return;
+  k_block_owner<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, n_items, block_owner, ctl);
+  k_emit<<<(unsigned)(num_sms * 8), 256, 0, s>>>(pb, views, stride, n_items, keys0, vals0, keys1, vals1, inst_rec,
+                                                 block_owner, hist, tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
