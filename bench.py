@@ -156,8 +156,8 @@ def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
 # summaries of the current kernels (profiles/), taken with the tiling below; None for a kernel
 # changed since its capture.
 TRAFFIC_TILING = (16, 16, 256)
-TRAFFIC = {"K8 blend bwd": 62.4e6, "K6 blend fwd": 21.8e6, "K9+K10 project bwd + Adam": None,
-           "K4 sort": None, "K7 loss": 94.7e6}
+TRAFFIC = {"K8 blend bwd": 62.1e6, "K6 blend fwd": 20.9e6, "K9+K10 project bwd + Adam": 256.6e6,
+           "K4 sort": 5 * 4.1e6, "K7 loss": None}
 
 
 def cpu_baseline_run(steps, warmup, seed=0):
@@ -203,7 +203,7 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 # streaming: new-image integration latency, plain per-view eager path vs batched graph path
 # ------------------------------------------------------------------------------------------
-def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
+def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H, pts_range=(5000, 20001)):
     import torch
     import paper_2503_13086_gb300 as gs
     gt = gi.ring_scene(n_gt, seed=seed + 100, stride=n_gt + (-n_gt) % 32)
@@ -214,7 +214,7 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H):
     torch.cuda.synchronize()
     f.close()
     rng = np.random.default_rng(seed)
-    pts = [gi.sparse_points(gt, n_gt, c, int(rng.integers(5000, 20001)), seed=seed * 1000 + k)
+    pts = [gi.sparse_points(gt, n_gt, c, int(rng.integers(*pts_range)), seed=seed * 1000 + k)
            for k, c in enumerate(cams)]
     return cams, targets, pts
 
@@ -464,7 +464,9 @@ def run_batched(args):
 
 
 def run_serve(args):
-    """Multi-session serving: 4 scenes at 1920x1080 / 1280x720 arriving at 1-3 Hz."""
+    """Multi-session serving: 4 scenes at 1920x1080 / 1280x720 arriving at 1-3 Hz (seeded Poisson),
+    each growing by up to args.serve_points new Gaussians per arrival; sessions are admitted and
+    deferred by the HBM budget."""
     import torch
     import paper_2503_13086_gb300 as gs  # noqa: F401
     from paper_2503_13086_gb300.serving import Scene, Server, summarize
@@ -472,19 +474,31 @@ def run_serve(args):
     scenes = []
     for s in range(4):
         Wv, Hv = (1920, 1080) if s % 2 == 0 else (1280, 720)
-        cams, targets, pts = stream_inputs(args.arrivals, seed=10 + s, n_gt=1_000_000, Wv=Wv, Hv=Hv)
+        cams, targets, pts = stream_inputs(args.arrivals, seed=10 + s, n_gt=args.serve_gt, Wv=Wv, Hv=Hv,
+                                           pts_range=(args.serve_points // 2, args.serve_points + 1))
         rng = np.random.default_rng(s)
         t, reqs = 0.0, []
         for c, tg, (xyz, rgb, tr) in zip(cams, targets, pts):
             reqs.append((t, dict(cam=c, target=tg, pts_xyz=xyz, pts_rgb=rgb, tracks=tr)))
             t += rng.exponential(1.0 / rng.uniform(1.0, 3.0))
-        scenes.append(Scene(s, reqs, dict(T_I=200, N_m=9, batch_views=9, use_graph=1, scene_extent=7.0, seed=s)))
-    srv = Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), session_budget_bytes=16 << 30, max_active=4)
+        scenes.append(Scene(s, reqs, dict(T_I=200, N_m=9, batch_views=args.serve_batch, batch_scaling=1,
+                                          use_graph=1, scene_extent=7.0, seed=s,
+                                          add_dist_thresh=args.serve_thresh)))
+    torch.cuda.synchronize()
+    srv = Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
+                 session_budget_bytes=int(args.serve_session_gb * (1 << 30)), max_active=4)
     out = srv.run(scenes)
     summ = summarize(out, srv.wall_s)
     summ.update(peak_device_bytes=srv.peak_device_bytes, wall_s=srv.wall_s,
-                deferred=sum(1 for _, e, _ in srv.log if e == "defer"))
-    print(json.dumps({"workload": "serving: 4 scenes, 1-3 Hz arrivals", **summ}))
+                deferred=sum(1 for _, e, _ in srv.log if e == "defer"),
+                n_gaussians={sid: r["stats"]["n_gaussians"] for sid, r in out.items()},
+                bytes_in_use={sid: r["stats"]["bytes_in_use"] for sid, r in out.items()},
+                config={"arrivals_per_scene": args.arrivals, "points_per_arrival": [args.serve_points // 2,
+                                                                                     args.serve_points],
+                        "gt_gaussians": args.serve_gt, "batch_views": args.serve_batch, "batch_scaling": 1,
+                        "new_point_threshold": args.serve_thresh,
+                        "hbm_budget_gb": args.serve_budget_gb, "session_budget_gb": args.serve_session_gb})
+    print(json.dumps({"workload": "serving: 4 scenes, 1920x1080 and 1280x720, 1-3 Hz arrivals", **summ}))
 
 
 def main():
@@ -496,6 +510,11 @@ def main():
     ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve"])
     ap.add_argument("--arrivals", type=int, default=20)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
+    ap.add_argument("--serve-session-gb", type=float, default=16.0)
+    ap.add_argument("--serve-points", type=int, default=150_000)
+    ap.add_argument("--serve-gt", type=int, default=4_000_000)
+    ap.add_argument("--serve-batch", type=int, default=3)
+    ap.add_argument("--serve-thresh", type=float, default=0.005)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune-report", action="store_true",
                     help="skip the timed run of the autotuned session (profiling runs)")
