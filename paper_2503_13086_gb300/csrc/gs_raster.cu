@@ -84,6 +84,8 @@ static void init_attributes_once() {
 
 Raster::Raster() {
   init_attributes_once();
+  Tiling first;
+  if (tiling_candidates(&first, 1) > 0) tiling = first;  // the default is the first compiled tiling
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
