@@ -185,6 +185,11 @@ typedef struct gs_field_config {
   int32_t batch_scaling;    /* steps over B > 1 views: 0 = mean of their Eq. 8 rates, Adam as configured;
                                1 = also lr x sqrt(B) and betas ^ B (the large-batch rule of Zhao et al.
                                2024 for 3DGS), which keeps per-view progress with B x fewer steps */
+  float lambda_l1;          /* Eq. 10 L1 weight; -1 = 1 - lambda_ssim (3DGS: 0.8) */
+  float lambda_load;        /* Eq. 10 weight of L_load (Eq. 9, std of G_p over the pixels some Gaussian
+                               reaches, all views of the step); G_p is a count, so the term enters the
+                               reported loss only and has no gradient.  The paper's preset:
+                               lambda_l1 0.47, lambda_ssim 0.12, lambda_load 0.41.  Default 0. */
 } gs_field_config;
 
 /* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2

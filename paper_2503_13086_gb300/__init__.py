@@ -79,7 +79,8 @@ class FieldConfig(ctypes.Structure):
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
                 ("add_dist_thresh", ctypes.c_float), ("scene_extent", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64),
-                ("tiling", Tiling), ("batch_scaling", ctypes.c_int32)]
+                ("tiling", Tiling), ("batch_scaling", ctypes.c_int32), ("lambda_l1", ctypes.c_float),
+                ("lambda_load", ctypes.c_float)]
 
 
 class IntegrateStats(ctypes.Structure):

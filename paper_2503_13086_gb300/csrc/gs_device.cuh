@@ -84,6 +84,8 @@ struct StepParams {
   int n_views;
   float bg[3];
   float lambda_ssim;     // D-SSIM weight of the loss
+  float lambda_l1;       // L1 weight of the loss
+  float lambda_load;     // weight of L_load (Eq. 9) in the reported loss (no gradient)
   float lr[6];           // learning rate per parameter group
   float beta1, beta2, eps;
   float step_size_scale; // 1 / (1 - beta1^t)

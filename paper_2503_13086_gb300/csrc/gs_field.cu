@@ -491,6 +491,8 @@ struct Field {
     P.n_views = nv;
     for (int a = 0; a < 3; ++a) P.bg[a] = cfg.bg[a];
     P.lambda_ssim = cfg.lambda_ssim;
+    P.lambda_l1 = cfg.lambda_l1 >= 0.f ? cfg.lambda_l1 : 1.f - cfg.lambda_ssim;
+    P.lambda_load = cfg.lambda_load;
     double scale = 1.0, b1 = cfg.beta1, b2 = cfg.beta2;
     if (cfg.batch_scaling && nv > 1) {
       scale = std::sqrt((double)nv);
@@ -805,6 +807,8 @@ void gs_field_config_default(gs_field_config* c) {
   c->eta0 = 1.6e-4f;
   c->etaf = 1.6e-6f;
   c->lambda_ssim = 0.2f;
+  c->lambda_l1 = -1.f;  // 1 - lambda_ssim
+  c->lambda_load = 0.f;
   c->lr_scale = 5e-3f;
   c->lr_rot = 1e-3f;
   c->lr_opacity = 0.05f;
@@ -821,7 +825,8 @@ gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out
   if (!cfg || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   if (cfg->T_I <= 0 || cfg->N_m <= 0 || cfg->T_a <= 0 || cfg->batch_views <= 0 || cfg->batch_views > gs::kMaxViews ||
-      !(cfg->eta0 > 0.f) || !(cfg->etaf > 0.f) || cfg->lambda_ssim < 0.f || cfg->lambda_ssim > 1.f)
+      !(cfg->eta0 > 0.f) || !(cfg->etaf > 0.f) || cfg->lambda_ssim < 0.f || cfg->lambda_ssim > 1.f ||
+      !(cfg->lambda_load >= 0.f) || !(cfg->lambda_l1 >= 0.f || cfg->lambda_l1 == -1.f))
     return fail(GS_ERR_INVALID_ARG, "invalid field configuration");
   const bool tiling_auto = cfg->tiling.tile_w == 0 && cfg->tiling.tile_h == 0 && cfg->tiling.batch == 0;
   if (!tiling_auto && !gs::tiling_supported(gs::Tiling{cfg->tiling.tile_w, cfg->tiling.tile_h, cfg->tiling.batch}))

@@ -444,6 +444,8 @@ gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const 
   gs_status st;
   if ((st = r->stage(s))) return st;
   r->sp_h->lambda_ssim = lambda_ssim;
+  r->sp_h->lambda_l1 = 1.f - lambda_ssim;
+  r->sp_h->lambda_load = 0.f;
   r->upload(s);
   r->enqueue_loss(s, image, out_dimage);
   cudaError_t e = cudaGetLastError();

@@ -1,5 +1,5 @@
-// k_loss.cu -- K7: L = (1 - lambda) L1 + lambda (1 - SSIM) of Eq. 10 (its L1 and SSIM terms),
-// and dL/d(render), sm_103a.
+// k_loss.cu -- K7: L = lambda_1 L1 + lambda_ssim (1 - SSIM) (+ lambda_load L_load, a value without
+// gradient) of Eq. 10, and dL/d(render), sm_103a.
 //
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const double lam = (double)sp->lambda_ssim;
+  const double lam = (double)sp->lambda_ssim, lam1 = (double)sp->lambda_l1;
   double total = 0.0;
   for (int vv = 0; vv < n_views; ++vv) {
     const ViewDev& U = views[vv];
@@ -288,13 +288,21 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
         Cs += s_red[1][k];
       }
       const double cntp = 3.0 * (double)U.W * (double)U.H;
-      const double lv = (1.0 - lam) * (A / cntp) + lam * (1.0 - Cs / cntp);
+      const double lv = lam1 * (A / cntp) + lam * (1.0 - Cs / cntp);
       if (vv < 32) ctl->loss_view[vv] = lv;
       total += lv;
     }
   }
   if (threadIdx.x == 0) {
-    ctl->loss = total / (double)n_views;
+    double loss = total / (double)n_views;
+    // Eq. 9-10: + lambda_load std(G_p) over the pixels some Gaussian reaches (all views of the step);
+    // G_p is a count, so this term has no gradient
+    if (sp->lambda_load != 0.f && ctl->gp_pixels) {
+      const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
+      const double var = (double)ctl->gp_sq / np - mean * mean;
+      loss += (double)sp->lambda_load * sqrt(var > 0.0 ? var : 0.0);
+    }
+    ctl->loss = loss;
     if (ledger) {  // this step is complete up to Adam, which cannot fail any more
       ledger->loss_sum += ctl->loss;
       ledger->pairs += ctl->pairs;
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   float* dX = dimage + 3 * V.pix_base;
   const float lam = sp->lambda_ssim;
   const float scale = 1.f / (3.f * (float)V.W * (float)V.H * (float)n_views);
-  const float gl1 = (1.f - lam) * scale, gs = -lam * scale;
+  const float gl1 = sp->lambda_l1 * scale, gs = -lam * scale;
   {
     const float* const src[3] = {P, P + HW, P + 2 * HW};
     stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);

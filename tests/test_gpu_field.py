@@ -261,3 +261,29 @@ def test_new_gaussians_start_with_zero_adam_moments_after_restore():
     assert p.shape[1] == 450
     assert np.all(m[:, 300:] == 0) and np.all(v[:, 300:] == 0)
     f.close()
+
+
+def test_paper_loss_preset_with_the_load_term():
+    """Eq. 10 with the paper's weights: 0.47 L1 + 0.12 D-SSIM + 0.41 L_load, L_load = std of G_p
+    over the pixels some Gaussian reaches (Eq. 9); G_p is a count, so the load term changes the
+    reported loss but not the gradient."""
+    p, cams, tg = config1(seed=7)
+    f = make_field(use_graph=0, lambda_l1=0.47, lambda_ssim=0.12, lambda_load=0.41)
+    f.set_gaussians(p)
+    img = f.add_image(cams[0], tg[0])
+    lr = f.image_lr(img)
+    loss = f.optimize_step([img])
+    got = f.get_gaussians()
+    # 0.47 L1 + 0.12 D-SSIM = 0.59 ((1 - l) L1 + l D-SSIM) with l = 0.12 / 0.59
+    L, g, r = oracle.loss_and_grad(p, [ocam(cams[0])], tg, lam=0.12 / 0.59, prec="f32")
+    gp = r["outs"][0]["gp"].astype(np.float64)
+    ref_loss = 0.59 * L + 0.41 * float(np.std(gp[gp > 0]))
+    assert abs(loss - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss)), (loss, ref_loss)
+    ref = p.copy()
+    oracle.adam(ref, (g * 0.59).astype(np.float32), np.zeros_like(p), np.zeros_like(p), [lr] + LRS_REST, 1,
+                prec="f32")
+    groups = [(0, 3, lr), (3, 6, 5e-3), (6, 10, 1e-3), (10, 11, 0.05), (11, 14, 2.5e-3), (14, 59, 1.25e-4)]
+    for a, b, lrg in groups:
+        bad = np.abs(got[a:b] - ref[a:b, :got.shape[1]]) > 1e-3 * lrg + 1e-6
+        assert bad.mean() < 2e-3, (a, b, bad.mean())
+    f.close()
