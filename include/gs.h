@@ -61,7 +61,8 @@ typedef enum gs_status {
   GS_ERR_CAPACITY = 4,    /* a fixed capacity (views per step, image count) is exceeded */
   GS_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
   GS_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired */
-  GS_ERR_STATE = 7        /* call out of order (e.g. backward without a forward) */
+  GS_ERR_STATE = 7,       /* call out of order (e.g. backward without a forward) */
+  GS_ERR_IO = 8           /* a file could not be written or read, or is not a saved field */
 } gs_status;
 
 /* Pinhole camera.  R is the row-major world->camera rotation and t the translation
@@ -244,6 +245,15 @@ typedef struct gs_integrate_stats {
  * ceil(T_I / batch_views) calls of the optimisation step. */
 GS_API gs_status gs_integrate(gs_field* f, int32_t image_id, gs_integrate_stats* out_stats);
 
+/* Phase 1 of the method (Sec. IV-A, the initial training before images stream in; the paper: the
+ * first 30 images, 2000 iterations, "all other settings" of 3DGS): `iterations` view-iterations over
+ * the registered images, batch_views per step, each view drawn uniformly from them (SplitMix64
+ * seeded with seed ^ 0x5048415345310000, a draw in [0, n) is next() mod n).  The position rate is
+ * 3DGS's exponential schedule, exp((1 - u) ln eta0 + u ln etaf) with u = min(step / max_steps, 1)
+ * over the phase-1 steps (3DGS: max_steps 30000), times the scene extent; the other groups keep
+ * their rates.  T_j counts these iterations (Eq. 7).  out_stats as for gs_integrate. */
+GS_API gs_status gs_initial_training(gs_field* f, int32_t iterations, int32_t max_steps, gs_integrate_stats* out_stats);
+
 /* Render the field from any camera: out_rgb_chw (device, 3 x H x W), out_T (device, nullable). */
 GS_API gs_status gs_render(gs_field* f, const gs_camera* cam, float* out_rgb_chw, float* out_T);
 
@@ -277,6 +287,18 @@ GS_API gs_status gs_image_lr(const gs_field* f, int32_t image_id, float* out_lr)
  * snapshot exists.  The snapshot lives in device memory owned by the field. */
 GS_API gs_status gs_field_snapshot(gs_field* f);
 GS_API gs_status gs_field_restore(gs_field* f);
+
+/* Checkpoint / resume of a whole session in a file (the paper keeps the field and optimiser state
+ * of a session; Sec. IV).  gs_field_save writes the configuration, the Gaussians with their Adam
+ * moments and step count, every registered image (camera, pixels, sparse-point tracks, T_j), the
+ * overlap matrix and the sparse points of the field update; it synchronises the field's stream.
+ * gs_field_load creates a new field from such a file on `stream` (NULL: a stream of its own); a
+ * session resumed from a file continues exactly as the saved one would (with a fixed tiling: bit
+ * for bit).  Not saved: the snapshot of gs_field_snapshot, timing state, autotuned tilings.
+ * Errors: GS_ERR_IO (file, format), GS_ERR_OOM / GS_ERR_BUDGET as for the calls that build a
+ * field. */
+GS_API gs_status gs_field_save(gs_field* f, const char* path);
+GS_API gs_status gs_field_load(const char* path, void* stream, gs_field** out);
 
 /* Enable per-kernel timing on the field's steps; gs_field_kernel_times returns the summed
  * device ms per kernel (same order as gs_raster_kernel_times) and the number of steps. */

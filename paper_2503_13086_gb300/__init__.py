@@ -126,6 +126,7 @@ SYMBOLS = {
     "gs_select_neighbors": ([P, I32, I32, P, P, P], I32),
     "gs_optimize_step": ([P, P, I32, P], I32),
     "gs_integrate": ([P, I32, P], I32),
+    "gs_initial_training": ([P, I32, I32, P], I32),
     "gs_render": ([P, P, P, P], I32),
     "gs_field_stats_get": ([P, P], I32),
     "gs_image_info": ([P, I32, P, P, I32], I32),
@@ -136,6 +137,8 @@ SYMBOLS = {
     "gs_field_kernel_times": ([P, P, P], I32),
     "gs_field_autotune": ([P, P, I32, I32, P], I32),
     "gs_autotune_clear": ([], I32),
+    "gs_field_save": ([P, ctypes.c_char_p], I32),
+    "gs_field_load": ([ctypes.c_char_p, P, P], I32),
     "gs_scan_noalloc": ([P, P, I64, P, P], I32),
 }
 
@@ -343,6 +346,24 @@ class Field:
             self._lib.gs_field_destroy(self._h)
             self._h = None
 
+    def save(self, path):
+        """Checkpoint the whole session to a file (see gs_field_save)."""
+        _check(self._lib.gs_field_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A new session resumed from a file written by save()."""
+        self = cls.__new__(cls)
+        self._lib = load()
+        _torch()
+        h = ctypes.c_void_p()
+        self._stream_obj = stream
+        sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+        _check(self._lib.gs_field_load(os.fsencode(path), sp, ctypes.byref(h)))
+        self._h = h
+        self.config = None
+        return self
+
     def __del__(self):
         try:
             self.close()
@@ -431,6 +452,12 @@ class Field:
         _check(self._lib.gs_integrate(self._h, int(image_id), ctypes.byref(st)))
         return dict(iterations=st.iterations, steps=st.steps, key_images=st.key_images, mean_loss=st.mean_loss,
                     pairs=int(st.pairs))
+
+    def initial_training(self, iterations, max_steps=30000):
+        """Phase 1: iterations over the registered images with 3DGS's position-rate schedule."""
+        st = IntegrateStats()
+        _check(self._lib.gs_initial_training(self._h, int(iterations), int(max_steps), ctypes.byref(st)))
+        return dict(iterations=st.iterations, steps=st.steps, mean_loss=st.mean_loss, pairs=int(st.pairs))
 
     def render(self, cam, want_T=False):
         torch = _torch()

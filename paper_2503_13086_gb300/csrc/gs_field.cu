@@ -711,6 +711,7 @@ struct Field {
       double lr_mean = 0;
       if ((s = pick_tiling(ids.data(), (int)ids.size(), false))) return s;
       if ((s = setup_views(ids.data(), (int)ids.size(), &lr_mean))) return s;
+      if (lr_override) lr_mean = (*lr_override)[first_group + k];
       if ((s = R.stage(stream))) return s;  // waits only for the previous step's parameter upload
       fill_params((int)ids.size(), lr_mean, adam_step + 1);
       std::memcpy(R.views_h, R.views.data(), sizeof(ViewDev) * ids.size());
@@ -774,6 +775,7 @@ struct Field {
   }
 
   unsigned long long sum_pairs = 0;
+  const std::vector<double>* lr_override = nullptr;  // per step of a run: the position rate before x extent
 
   gs_status step(const int* ids, int nv, float* out_loss) {
     std::vector<std::vector<int>> groups(1, std::vector<int>(ids, ids + nv));
@@ -1074,6 +1076,41 @@ gs_status gs_integrate(gs_field* ff, int32_t id, gs_integrate_stats* st) {
   return GS_OK;
 }
 
+gs_status gs_initial_training(gs_field* ff, int32_t iterations, int32_t max_steps, gs_integrate_stats* st) {
+  Field* f = F(ff);
+  if (!f || iterations < 0 || max_steps <= 0) return fail(GS_ERR_INVALID_ARG, "bad arguments");
+  if (f->images.empty()) return fail(GS_ERR_STATE, "no registered image");
+  // views drawn uniformly by SplitMix64; 3DGS's exponential position-rate schedule over max_steps
+  gs::SplitMix64 rng(f->cfg.seed ^ 0x5048415345310000ull);
+  const int B = f->cfg.batch_views;
+  const int n_img = (int)f->images.size();
+  std::vector<std::vector<int>> groups;
+  std::vector<double> lrs;
+  for (int done = 0; done < iterations; done += B) {
+    std::vector<int> ids;
+    for (int k = 0; k < B && done + k < iterations; ++k) ids.push_back((int)rng.below((unsigned long long)n_img));
+    const double u = std::min(1.0, (double)groups.size() / (double)max_steps);
+    lrs.push_back(std::exp(std::log((double)f->cfg.eta0) * (1.0 - u) + std::log((double)f->cfg.etaf) * u));
+    groups.push_back(std::move(ids));
+  }
+  const size_t chunk = f->cfg.async_steps > 0 ? (size_t)f->cfg.async_steps : 1;
+  const unsigned long long pairs0 = f->sum_pairs;
+  double loss_sum = 0;
+  f->lr_override = &lrs;
+  gs_status s = f->run_all(groups, chunk, &loss_sum);
+  f->lr_override = nullptr;
+  if (s) return s;
+  if (st) {
+    st->iterations = iterations;
+    st->steps = (int)groups.size();
+    st->key_images = 0;
+    st->new_gaussians = 0;
+    st->mean_loss = groups.empty() ? 0.0 : loss_sum / (double)groups.size();
+    st->pairs = f->sum_pairs - pairs0;
+  }
+  return GS_OK;
+}
+
 gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* out_T) {
   Field* f = F(ff);
   if (!f || !cam || !out_rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
@@ -1217,3 +1254,171 @@ gs_status gs_field_kernel_times(gs_field* ff, float out_ms[9], int64_t* out_step
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Checkpoint / resume of a session in a file.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+struct FileHeader {
+  char magic[8];
+  uint32_t version, cfg_bytes, camera_bytes, nparams;
+};
+constexpr char kMagic[8] = {'G', 'S', 'F', 'I', 'E', 'L', 'D', '1'};
+
+struct File {
+  FILE* f = nullptr;
+  bool ok = true;
+  ~File() {
+    if (f) fclose(f);
+  }
+  void put(const void* p, size_t n) {
+    if (ok && n && fwrite(p, 1, n, f) != n) ok = false;
+  }
+  void get(void* p, size_t n) {
+    if (ok && n && fread(p, 1, n, f) != n) ok = false;
+  }
+  template <class T>
+  void put(const T& v) {
+    put(&v, sizeof(T));
+  }
+  template <class T>
+  void get(T& v) {
+    get(&v, sizeof(T));
+  }
+};
+
+}  // namespace
+
+extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
+  Field* f = F(ff);
+  if (!f || !path) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  File out;
+  out.f = fopen(path, "wb");
+  if (!out.f) return fail(GS_ERR_IO, std::string("cannot write ") + path);
+  FileHeader h;
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.cfg_bytes = sizeof(gs_field_config);
+  h.camera_bytes = sizeof(gs_camera);
+  h.nparams = gs::kNumParams;
+  out.put(h);
+  out.put(f->cfg);
+  out.put((int64_t)f->n);
+  out.put((int64_t)f->adam_step);
+  out.put((int32_t)f->images.size());
+  std::vector<float> buf;
+  for (const auto& im : f->images) {
+    out.put(im.cam);
+    out.put((int32_t)im.T);
+    out.put((int64_t)im.tracks.size());
+    out.put(im.tracks.data(), im.tracks.size() * sizeof(long long));
+    buf.resize((size_t)3 * im.cam.width * im.cam.height);
+    if (cudaMemcpy(buf.data(), im.rgb.p, buf.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(GS_ERR_CUDA, "reading an image back failed");
+    out.put(buf.data(), buf.size() * 4);
+  }
+  for (const auto& row : f->M) out.put(row.data(), row.size() * 4);
+  out.put((int64_t)f->n_points);
+  out.put(f->grid_cell);
+  out.put((int32_t)f->grid_ready);
+  buf.resize((size_t)3 * f->n_points);
+  if (f->n_points && cudaMemcpy(buf.data(), f->pts_xyz.p, buf.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(GS_ERR_CUDA, "reading the sparse points back failed");
+  out.put(buf.data(), buf.size() * 4);
+  const gs::DevBuf* src[3] = {&f->params, &f->adam_m, &f->adam_v};
+  buf.resize((size_t)gs::kNumParams * f->n);
+  for (const gs::DevBuf* b : src) {
+    if (f->n && cudaMemcpy2D(buf.data(), (size_t)f->n * 4, b->p, (size_t)f->stride * 4, (size_t)f->n * 4, gs::kNumParams,
+                             cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(GS_ERR_CUDA, "reading the Gaussians back failed");
+    out.put(buf.data(), buf.size() * 4);
+  }
+  if (!out.ok) return fail(GS_ERR_IO, std::string("short write to ") + path);
+  return GS_OK;
+}
+
+extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** out_field) {
+  if (!path || !out_field) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  *out_field = nullptr;
+  File in;
+  in.f = fopen(path, "rb");
+  if (!in.f) return fail(GS_ERR_IO, std::string("cannot read ") + path);
+  FileHeader h;
+  in.get(h);
+  if (!in.ok || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || h.cfg_bytes != sizeof(gs_field_config) ||
+      h.camera_bytes != sizeof(gs_camera) || h.nparams != (uint32_t)gs::kNumParams)
+    return fail(GS_ERR_IO, std::string(path) + " is not a saved field of this library");
+  gs_field_config cfg;
+  in.get(cfg);
+  int64_t n = 0, adam_step = 0;
+  int32_t n_images = 0;
+  in.get(n);
+  in.get(adam_step);
+  in.get(n_images);
+  if (!in.ok || n < 0 || n_images < 0 || n_images > 4096) return fail(GS_ERR_IO, "corrupt field file");
+  gs_field* ffield = nullptr;
+  gs_status s = gs_field_init(&cfg, stream, &ffield);
+  if (s) return s;
+  std::unique_ptr<Field> f(F(ffield));
+  std::vector<float> buf;
+  for (int32_t k = 0; k < n_images; ++k) {
+    gs::Image im;
+    int32_t T = 0;
+    int64_t nt = 0;
+    in.get(im.cam);
+    in.get(T);
+    in.get(nt);
+    if (!in.ok || nt < 0 || im.cam.width <= 0 || im.cam.height <= 0) return fail(GS_ERR_IO, "corrupt field file");
+    im.T = T;
+    im.tracks.resize((size_t)nt);
+    in.get(im.tracks.data(), (size_t)nt * sizeof(long long));
+    buf.resize((size_t)3 * im.cam.width * im.cam.height);
+    in.get(buf.data(), buf.size() * 4);
+    if (!in.ok) return fail(GS_ERR_IO, "corrupt field file");
+    if ((s = im.rgb.reserve(buf.size() * 4, &f->own_bytes))) return s;
+    if (cudaMemcpy(im.rgb.p, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(GS_ERR_CUDA, "uploading an image failed");
+    f->images.push_back(std::move(im));
+  }
+  f->M.assign(n_images, std::vector<float>(n_images, 0.f));
+  for (auto& row : f->M) in.get(row.data(), row.size() * 4);
+  int64_t n_points = 0;
+  int32_t grid_ready = 0;
+  in.get(n_points);
+  in.get(f->grid_cell);
+  in.get(grid_ready);
+  if (!in.ok || n_points < 0) return fail(GS_ERR_IO, "corrupt field file");
+  buf.resize((size_t)3 * n_points);
+  in.get(buf.data(), buf.size() * 4);
+  if (!in.ok) return fail(GS_ERR_IO, "corrupt field file");
+  f->grid_ready = grid_ready != 0;
+  if (n_points > 0) {
+    if ((s = f->reserve_points(n_points))) return s;
+    if (cudaMemcpy(f->pts_xyz.p, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(GS_ERR_CUDA, "uploading the sparse points failed");
+    f->n_points = n_points;
+    gs::launch_insert_points(f->grid_dev(), static_cast<int*>(f->pts_next.p), 0, n_points, f->stream);
+  }
+  if ((s = f->reserve_gaussians(std::max<int64_t>(n, 1)))) return s;
+  gs::DevBuf* dst[3] = {&f->params, &f->adam_m, &f->adam_v};
+  buf.resize((size_t)gs::kNumParams * n);
+  for (gs::DevBuf* b : dst) {
+    in.get(buf.data(), buf.size() * 4);
+    if (!in.ok) return fail(GS_ERR_IO, "corrupt field file");
+    cudaMemsetAsync(b->p, 0, (size_t)f->stride * gs::kNumParams * 4, f->stream);
+    if (n && cudaMemcpy2DAsync(b->p, (size_t)f->stride * 4, buf.data(), (size_t)n * 4, (size_t)n * 4, gs::kNumParams,
+                               cudaMemcpyHostToDevice, f->stream) != cudaSuccess)
+      return fail(GS_ERR_CUDA, "uploading the Gaussians failed");
+    cudaStreamSynchronize(f->stream);
+  }
+  f->n = (int)n;
+  f->adam_step = adam_step;
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  *out_field = reinterpret_cast<gs_field*>(f.release());
+  return GS_OK;
+}

@@ -54,3 +54,15 @@ def test_tiling_candidates_on_the_host():
     cfg = gs.FieldConfig()
     gs.load().gs_field_config_default(ctypes.byref(cfg))
     assert cfg.tiling.astuple() == (0, 0, 0)  # autotuned by default
+
+
+def test_loading_a_file_that_is_not_a_field_fails_cleanly(tmp_path):
+    import paper_2503_13086_gb300 as gs
+    lib = gs.load()
+    junk = tmp_path / "junk.gsf"
+    junk.write_bytes(b"not a field" * 10)
+    h = ctypes.c_void_p()
+    assert lib.gs_field_load(str(junk).encode(), None, ctypes.byref(h)) == 8  # GS_ERR_IO
+    assert b"not a saved field" in lib.gs_last_error()
+    assert lib.gs_field_load(str(tmp_path / "missing.gsf").encode(), None, ctypes.byref(h)) == 8
+    assert not h.value

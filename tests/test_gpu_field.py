@@ -287,3 +287,80 @@ def test_paper_loss_preset_with_the_load_term():
         bad = np.abs(got[a:b] - ref[a:b, :got.shape[1]]) > 1e-3 * lrg + 1e-6
         assert bad.mean() < 2e-3, (a, b, bad.mean())
     f.close()
+
+
+def test_session_checkpoint_and_resume_continue_bit_for_bit(tmp_path):
+    """A session saved to a file after three arrivals and resumed in a new field integrates the next
+    arrivals exactly as the uninterrupted session (fixed tiling)."""
+    import paper_2503_13086_gb300 as gs
+    gt = gi.ring_scene(20000, seed=3, stride=20000)
+    cams = gi.random_walk_cameras(5, seed=4, W=160, H=104, f=125.0)
+    rng = np.random.default_rng(0)
+    tgt = [gi.uniform_target(160, 104, 40 + k) for k in range(5)]
+    pts = [gi.sparse_points(gt, 20000, c, 1500, seed=k) for k, c in enumerate(cams)]
+    f = make_field(T_I=16, N_m=3, scene_extent=7.0, seed=3, add_dist_thresh=0.05)
+
+    def arrive(field, k):
+        xyz, rgb, tr = pts[k]
+        img = field.add_image(cams[k], tgt[k], xyz, rgb, tr)
+        field.integrate(img)
+
+    for k in range(3):
+        arrive(f, k)
+    path = str(tmp_path / "session.gsf")
+    f.save(path)
+    g = gs.Field.load(path)
+    a0 = f.get_gaussians(with_adam=True)
+    b0 = g.get_gaussians(with_adam=True)
+    for x, y in zip(a0, b0):
+        assert np.array_equal(x, y)
+    for k in (3, 4):
+        arrive(f, k)
+        arrive(g, k)
+    for x, y in zip(f.get_gaussians(with_adam=True), g.get_gaussians(with_adam=True)):
+        assert np.array_equal(x, y)
+    sf, sg = f.stats(), g.stats()
+    assert sf["adam_step"] == sg["adam_step"] and sf["n_images"] == sg["n_images"] == 5
+    assert [f.image_info(i, 5) for i in range(5)] == [g.image_info(i, 5) for i in range(5)]
+    f.close()
+    g.close()
+
+
+def test_initial_training_draws_views_and_follows_the_3dgs_rate():
+    """Phase 1 (Sec. IV-A): the views come from SplitMix64 (seed ^ 0x5048415345310000, next() mod n)
+    and the position rate from 3DGS's exponential schedule, not from Eq. 8: after one ordinary step
+    has made every image 'trained' (T_j >= T_a = 1, Eq. 8 would give eta_f), the first phase-1 step
+    still uses eta_0 x extent."""
+    p = gi.cube_scene(3000, seed=13, stride=3008)
+    cams = [gi.identity_camera(64, 48, 60.0) for _ in range(3)]
+    for k, c in enumerate(cams):
+        c["t"] = np.array([0.03 * k, 0.0, 0.0])
+    tg = [gi.uniform_target(64, 48, 50 + k) for k in range(3)]
+    f = make_field(use_graph=0, T_a=1, seed=21)
+    f.set_gaussians(p[:, :3000])
+    ids = [f.add_image(c, t) for c, t in zip(cams, tg)]
+    f.optimize_step(ids)  # T_j = 1 for all three
+    assert f.image_lr(0) == pytest.approx(1.6e-6, rel=1e-5)
+    p1, m1, v1 = f.get_gaussians(with_adam=True)
+    rng = sch.SplitMix64(21 ^ 0x5048415345310000)
+    draws = [rng.below(3) for _ in range(5)]
+    st = f.initial_training(1, max_steps=30000)
+    assert st["iterations"] == 1 and st["steps"] == 1
+    got = f.get_gaussians()
+    P1 = np.zeros((59, 3008), np.float32)
+    P1[:, :3000] = p1
+    _, g, _ = oracle.loss_and_grad(P1, [ocam(cams[draws[0]])], [tg[draws[0]]], lam=0.2, prec="f32", n=3000)
+    M1 = np.zeros_like(P1)
+    V1 = np.zeros_like(P1)
+    M1[:, :3000] = m1
+    V1[:, :3000] = v1
+    ref = P1.copy()
+    oracle.adam(ref, g, M1, V1, [1.6e-4] + LRS_REST, 2, prec="f32", n=3000)
+    d = np.abs(got[0:3] - ref[0:3, :3000])
+    assert (d > 1e-3 * 1.6e-4 + 1e-6).mean() < 2e-3
+    # the rest of the phase: T_j counts follow the same draws
+    f.initial_training(4, max_steps=30000)
+    counts = [1 + draws[:5].count(i) for i in range(3)]
+    assert [f.image_info(i, 3)[0] for i in range(3)] == counts
+    assert f.stats()["adam_step"] == 6
+    f.close()
