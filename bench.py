@@ -219,11 +219,12 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H, pts_range=(5000,
     return cams, targets, pts
 
 
-def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False):
+def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False,
+               thresh=0.0):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
-                            scene_extent=7.0, seed=3, batch_scaling=scaling)
+                            scene_extent=7.0, seed=3, batch_scaling=scaling, add_dist_thresh=thresh)
     if kernel_times:
         sess.field.set_timing(True)
     pairs, add_s, int_s = 0, [], []
@@ -463,6 +464,28 @@ def run_batched(args):
                       "autotune_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]}}))
 
 
+def run_stream_long(args):
+    """The streaming session at full length: 150 arrivals at 1297 x 840 on a random walk, 5k-20k
+    sparse points each, new points kept down to 0.005 from the field so it grows to ~1.5M Gaussians;
+    the per-view graph-replayed path and the 3-view batched path."""
+    import torch
+    import paper_2503_13086_gb300 as gs
+    torch.cuda.set_device(0)
+    cams, targets, pts = stream_inputs(args.arrivals, seed=0, n_gt=4_000_000)
+    gs.autotune_clear()
+    warm = min(args.arrivals, 10)
+    for b in (1, 3):
+        run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1,
+                   thresh=0.005)
+    res = {}
+    for name, b in (("graph_async_per_view", 1), ("batched3_graph_scaled", 3)):
+        r = run_stream(cams, targets, pts, batch=b, graph=1, asyn=16, scaling=1, thresh=0.005)
+        res[name] = r
+    print(json.dumps({"workload": f"streaming: {args.arrivals} arrivals, 1297x840, random walk 60-80% overlap, "
+                                  f"5k-20k sparse points each, new-point threshold 0.005, T_I = 200 over the new "
+                                  f"image + 8 neighbours, 4M-Gaussian hidden scene", **res}))
+
+
 def run_serve(args):
     """Multi-session serving: 4 scenes at 1920x1080 / 1280x720 arriving at 1-3 Hz (seeded Poisson),
     each growing by up to args.serve_points new Gaussians per arrival; sessions are admitted and
@@ -507,7 +530,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve"])
+    ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve", "stream"])
     ap.add_argument("--arrivals", type=int, default=20)
     ap.add_argument("--serve-budget-gb", type=float, default=40.0)
     ap.add_argument("--serve-session-gb", type=float, default=16.0)
@@ -528,6 +551,8 @@ def main():
         run_batched(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "stream":
+        run_stream_long(args)
     else:
         run_gs(args)
 

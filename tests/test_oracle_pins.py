@@ -524,3 +524,66 @@ def test_schedule_invariants():
     # the rate falls as the image is trained (Sec. IV-C)
     rates = [sch.lr_current(t, 200, 1.6e-4, 1.6e-6) for t in range(0, 250, 10)]
     assert all(a >= b for a, b in zip(rates, rates[1:]))
+
+
+# ---------------------------------------------------------------------------------------------
+# 3DGS adaptive density control (oracle/densify.py)
+# ---------------------------------------------------------------------------------------------
+def test_splitmix64_published_vector():
+    """SplitMix64 seeded with 1234567: the first five outputs of the published reference."""
+    from oracle import densify as dn
+    from oracle import schedule as sch
+    ref = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+           16408922859458223821]
+    assert [dn.splitmix64_hash((1234567 + k * dn.GOLDEN) % (1 << 64)) for k in range(5)] == ref
+    r = sch.SplitMix64(1234567)
+    assert [r.next() for _ in range(5)] == ref
+
+
+def test_densify_normals_are_standard():
+    from oracle import densify as dn
+    z = np.array([dn.normal(3, 1, i, c, a) for i in range(2000) for c in range(2) for a in range(3)], np.float64)
+    assert abs(z.mean()) < 0.03 and abs(z.std() - 1.0) < 0.03
+    assert abs(np.mean(z ** 4) - 3.0) < 0.2  # Gaussian kurtosis
+
+
+def test_view_space_norm_closed_form():
+    from oracle import densify as dn
+    assert dn.view_space_norm(3.0 / 960.0, 4.0 / 540.0, 1920, 1080) == pytest.approx(5.0, rel=1e-6)
+
+
+def test_densify_hand_example():
+    """Four Gaussians, extent 10 (clone limit log 0.1, prune limit log 1.0): A hot and small (clone),
+    B hot and large and rotated 90 degrees about z (split), C cold and transparent (pruned), D cold
+    and huge (pruned).  Output: A, A's clone, B's two children; only A keeps its moments."""
+    from oracle import densify as dn
+    n = 4
+    p = np.zeros((59, n), np.float32)
+    p[0:3] = [[0, 1, 2, 3], [0, 0, 0, 0], [5, 5, 5, 5]]
+    p[3:6, 0] = np.log(0.05)
+    p[3:6, 1] = np.log([0.5, 0.2, 0.1])
+    p[3:6, 2] = np.log(0.05)
+    p[3:6, 3] = np.log(2.0)
+    p[6, :] = 1.0
+    c45 = np.float32(np.sqrt(0.5))
+    p[6, 1], p[9, 1] = c45, c45  # 90 degrees about z: (x, y, z) -> (-y, x, z)
+    p[10, :] = 2.0
+    p[10, 2] = -8.0  # opacity 3.4e-4 < 0.005
+    p[11:59] = 0.1
+    m = np.full_like(p, 0.5)
+    v = np.full_like(p, 0.25)
+    accum = np.array([3e-3, 3e-3, 1e-5, 1e-5], np.float32)
+    count = np.array([10, 10, 10, 10], np.float32)
+    P, M, V, info = dn.densify(p, m, v, n, accum, count, extent=10.0, seed=7, rnd=2)
+    assert info == dict(cloned=1, split=1, pruned=2, kept=1, n=4)
+    assert np.array_equal(P[:, 0], p[:, 0]) and np.array_equal(P[:, 1], p[:, 0])
+    assert np.all(M[:, 0] == 0.5) and np.all(V[:, 0] == 0.25)
+    assert np.all(M[:, 1:] == 0) and np.all(V[:, 1:] == 0)
+    s = np.array([0.5, 0.2, 0.1])
+    for c in range(2):
+        z = np.array([float(dn.normal(7, 2, 1, c, a)) for a in range(3)])
+        local = s * z
+        expect = np.array([1.0, 0.0, 5.0]) + np.array([-local[1], local[0], local[2]])
+        assert np.allclose(P[0:3, 2 + c], expect, atol=1e-5)
+        assert np.allclose(P[3:6, 2 + c], np.log(s / 1.6), atol=1e-6)
+        assert np.array_equal(P[6:59, 2 + c], p[6:59, 1])
