@@ -191,6 +191,7 @@ typedef struct gs_field_config {
                                reaches, all views of the step); G_p is a count, so the term enters the
                                reported loss only and has no gradient.  The paper's preset:
                                lambda_l1 0.47, lambda_ssim 0.12, lambda_load 0.41.  Default 0. */
+  int32_t densify_stats;    /* 1: every step accumulates the statistics gs_field_densify uses */
 } gs_field_config;
 
 /* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2
@@ -288,10 +289,31 @@ GS_API gs_status gs_image_lr(const gs_field* f, int32_t image_id, float* out_lr)
 GS_API gs_status gs_field_snapshot(gs_field* f);
 GS_API gs_status gs_field_restore(gs_field* f);
 
+/* Adaptive density control of the original 3DGS (kept among "all other settings" of 3DGS, Sec.
+ * V-A; 3DGS Sec. 5.2).  With densify_stats set, every step adds, per Gaussian and per view in
+ * which it has instances, the norm of its view-space mean gradient (the pixel-space gradient
+ * scaled by (W/2, H/2)) and a count.  gs_field_densify then clones every Gaussian whose mean norm
+ * is >= grad_thresh and whose largest scale is <= percent_dense x extent, splits the larger ones
+ * into 2 children (mean + R(q) (s * z), z standard normal from a counter-based generator, every
+ * log-scale lowered by log 1.6), prunes every result with opacity < min_opacity or largest scale
+ * > max_scale x extent, orders the field as kept originals, clones, children, gives the new
+ * Gaussians zero Adam moments and clears the statistics.  extent = the configured scene extent
+ * (1.1 x camera spread by default).  3DGS's values: 2e-4, 0.01, 0.005, 0.1.  Synchronises. */
+typedef struct gs_densify_params {
+  float grad_thresh, percent_dense, min_opacity, max_scale;
+} gs_densify_params;
+typedef struct gs_densify_result {
+  int64_t n_before, n_after, cloned, split, pruned;
+} gs_densify_result;
+GS_API gs_status gs_field_densify(gs_field* f, const gs_densify_params* p, gs_densify_result* out);
+/* The accumulated statistics (host arrays of n floats each; either may be NULL). */
+GS_API gs_status gs_field_densify_stats(gs_field* f, float* host_norm_sum, float* host_count);
+
 /* Checkpoint / resume of a whole session in a file (the paper keeps the field and optimiser state
  * of a session; Sec. IV).  gs_field_save writes the configuration, the Gaussians with their Adam
  * moments and step count, every registered image (camera, pixels, sparse-point tracks, T_j), the
- * overlap matrix and the sparse points of the field update; it synchronises the field's stream.
+ * overlap matrix, the sparse points of the field update and the densification statistics and
+ * round count; it synchronises the field's stream.
  * gs_field_load creates a new field from such a file on `stream` (NULL: a stream of its own); a
  * session resumed from a file continues exactly as the saved one would (with a fixed tiling: bit
  * for bit).  Not saved: the snapshot of gs_field_snapshot, timing state, autotuned tilings.

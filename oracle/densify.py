@@ -18,7 +18,8 @@ silent (the kernels follow the same ones):
 * order: kept originals, then clones, then children (by original, child 0 before child 1); the
   Adam moments of clones and children are 0, the kept originals keep theirs;
 * the decisions compare log-scales and opacity logits against thresholds taken to the log / logit
-  domain in float64 and rounded to float32, so both sides decide on the same float32 values;
+  domain in float64 from the float32 settings and extent, then rounded to float32, so both sides
+  decide on the same float32 values;
 * the normals z: for split round r, original i, child c, axis a: k = (2 i + c) 3 + a, two
   SplitMix64 outputs h(base + 2k), h(base + 2k + 1) with base = seed ^ (r * 0x9E3779B97F4A7C15)
   give u1 = ((h1 >> 11) + 1) / 2^53, u2 = (h2 >> 11) / 2^53 and z = sqrt(-2 ln u1) cos(2 pi u2)
@@ -69,6 +70,9 @@ def quat_to_rot(q):
 
 
 def thresholds(extent, grad_thresh=2e-4, percent_dense=0.01, min_opacity=0.005, max_scale=0.1):
+    # the settings and the extent are float32 values; the products and logs are taken in float64
+    f = lambda x: float(np.float32(x))
+    extent, percent_dense, min_opacity, max_scale = f(extent), f(percent_dense), f(min_opacity), f(max_scale)
     return dict(grad=np.float32(grad_thresh),
                 ls_dense=np.float32(math.log(percent_dense * extent)),
                 ls_big=np.float32(math.log(max_scale * extent)),

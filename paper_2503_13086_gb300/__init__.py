@@ -80,7 +80,17 @@ class FieldConfig(ctypes.Structure):
                 ("add_dist_thresh", ctypes.c_float), ("scene_extent", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64),
                 ("tiling", Tiling), ("batch_scaling", ctypes.c_int32), ("lambda_l1", ctypes.c_float),
-                ("lambda_load", ctypes.c_float)]
+                ("lambda_load", ctypes.c_float), ("densify_stats", ctypes.c_int32)]
+
+
+class DensifyParams(ctypes.Structure):
+    _fields_ = [("grad_thresh", ctypes.c_float), ("percent_dense", ctypes.c_float), ("min_opacity", ctypes.c_float),
+                ("max_scale", ctypes.c_float)]
+
+
+class DensifyResult(ctypes.Structure):
+    _fields_ = [("n_before", ctypes.c_int64), ("n_after", ctypes.c_int64), ("cloned", ctypes.c_int64),
+                ("split", ctypes.c_int64), ("pruned", ctypes.c_int64)]
 
 
 class IntegrateStats(ctypes.Structure):
@@ -140,6 +150,8 @@ SYMBOLS = {
     "gs_field_save": ([P, ctypes.c_char_p], I32),
     "gs_field_load": ([ctypes.c_char_p, P, P], I32),
     "gs_scan_noalloc": ([P, P, I64, P, P], I32),
+    "gs_field_densify": ([P, P, P], I32),
+    "gs_field_densify_stats": ([P, P, P], I32),
 }
 
 KERNEL_NAMES = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss",
@@ -458,6 +470,22 @@ class Field:
         st = IntegrateStats()
         _check(self._lib.gs_initial_training(self._h, int(iterations), int(max_steps), ctypes.byref(st)))
         return dict(iterations=st.iterations, steps=st.steps, mean_loss=st.mean_loss, pairs=int(st.pairs))
+
+    def densify(self, grad_thresh=2e-4, percent_dense=0.01, min_opacity=0.005, max_scale=0.1):
+        """3DGS's clone / split / prune on the accumulated statistics (needs densify_stats=1)."""
+        prm = DensifyParams(grad_thresh, percent_dense, min_opacity, max_scale)
+        res = DensifyResult()
+        _check(self._lib.gs_field_densify(self._h, ctypes.byref(prm), ctypes.byref(res)))
+        return {k: getattr(res, k) for k, _ in DensifyResult._fields_}
+
+    def densify_stats(self):
+        """(norm sums, counts) accumulated since the last densification, numpy (n,) each."""
+        n = self.stats()["n_gaussians"]
+        a = np.zeros(max(n, 1), np.float32)
+        c = np.zeros(max(n, 1), np.float32)
+        _check(self._lib.gs_field_densify_stats(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                c.ctypes.data_as(ctypes.c_void_p)))
+        return a[:n], c[:n]
 
     def render(self, cam, want_T=False):
         torch = _torch()

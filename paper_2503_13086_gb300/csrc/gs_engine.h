@@ -50,6 +50,7 @@ struct Raster {
   bool have_forward = false;
   int num_sms = 1;
   Tiling tiling;   // tile shape and K6 batch of the next step
+  float* dstat = nullptr;  // densification statistics (2 rows of stride floats), nullptr: off
 
   // device buffers
   DevBuf sp_d, views_d;

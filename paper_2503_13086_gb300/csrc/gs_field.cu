@@ -112,6 +112,9 @@ struct Field {
   std::unique_ptr<Raster> r;
   int n = 0, stride = 0;
   DevBuf params, adam_m, adam_v;
+  DevBuf dstat;  // densification statistics: norm sums, counts (2 rows of stride)
+  DevBuf dens_tmp;
+  long long densify_round = 0;
   long long adam_step = 0;
   std::vector<Image> images;
   std::vector<std::vector<float>> M;  // overlap matrix
@@ -150,6 +153,8 @@ struct Field {
     params.release(&own_bytes);
     adam_m.release(&own_bytes);
     adam_v.release(&own_bytes);
+    dstat.release(&own_bytes);
+    dens_tmp.release(&own_bytes);
     for (auto& im : images) im.rgb.release(&own_bytes);
     step_img.release(&own_bytes);
     step_last.release(&own_bytes);
@@ -225,13 +230,13 @@ struct Field {
   std::vector<unsigned long long> signature() const {
     const Raster& R = *r;
     std::vector<unsigned long long> v;
-    const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
+    const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &dstat, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
                             &R.sp_d, &R.views_d, &R.zeroA, &R.zeroB, &R.xyo, &R.conic, &R.rgb, &R.depth, &R.radius,
                             &R.rect, &R.count, &R.offsets, &R.clamp, &R.g2s, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
                             &R.inst_rec, &R.block_owner, &R.carry,
                             &R.ckpt, &R.cmask, &R.order, &R.tile_chunks, &R.partials, &R.block_sums};
     for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
-    const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)R.passes,
+    const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)(uintptr_t)R.dstat, (unsigned long long)R.passes,
                                       (unsigned long long)R.n_tiles, R.zeroA_bytes, R.zeroB_bytes, R.sort_state_bytes,
                                       R.ranges_bytes, R.chunk_bytes, (unsigned long long)R.timing,
                                       (unsigned long long)R.tiling.tw, (unsigned long long)R.tiling.th,
@@ -292,13 +297,25 @@ struct Field {
       cudaMemcpy2DAsync(nm.p, ns * 4, adam_m.p, (size_t)stride * 4, (size_t)n * 4, kNumParams, cudaMemcpyDeviceToDevice, stream);
       cudaMemcpy2DAsync(nv.p, ns * 4, adam_v.p, (size_t)stride * 4, (size_t)n * 4, kNumParams, cudaMemcpyDeviceToDevice, stream);
     }
+    DevBuf nd;
+    if ((s = nd.reserve((size_t)ns * 8, &own_bytes))) {
+      np.release(&own_bytes);
+      nm.release(&own_bytes);
+      nv.release(&own_bytes);
+      return s;
+    }
+    cudaMemsetAsync(nd.p, 0, (size_t)ns * 8, stream);
+    if (n > 0 && dstat.p)
+      cudaMemcpy2DAsync(nd.p, ns * 4, dstat.p, (size_t)stride * 4, (size_t)n * 4, 2, cudaMemcpyDeviceToDevice, stream);
     cudaStreamSynchronize(stream);
     params.release(&own_bytes);
     adam_m.release(&own_bytes);
     adam_v.release(&own_bytes);
+    dstat.release(&own_bytes);
     params = np;
     adam_m = nm;
     adam_v = nv;
+    dstat = nd;
     stride = (int)ns;
     drop_graphs();
     sized_for_views = false;
@@ -476,6 +493,7 @@ struct Field {
     if ((s = R.set_views(cams.data(), nv, tg.data()))) return s;
     R.stride = stride;
     R.n = n;
+    R.dstat = cfg.densify_stats ? static_cast<float*>(dstat.p) : nullptr;
     if ((s = R.ensure_records(stride)) || (s = ensure_step_buffers(R.n_pix)) || (s = R.ensure_instances(R.m_cap)))
       return s;
     *lr_mean = lr_sum / nv;
@@ -744,7 +762,7 @@ struct Field {
     last_pairs = ok ? Lg.pairs / ok : 0;
     last_blended = ok ? Lg.blended / ok : 0;
     last_instances = ok ? Lg.instances / ok : 0;
-    last_kernels = kStepLaunchesBase + R.passes;
+    last_kernels = kStepLaunchesBase + R.passes + (R.dstat ? 1 : 0);
     sum_pairs += Lg.pairs;
     if (ok && Lg.last_gp_pixels) {  // Eq. 9: std of G_p over the pixels some Gaussian reaches
       const double mean = (double)Lg.last_gp_sum / (double)Lg.last_gp_pixels;
@@ -877,6 +895,7 @@ gs_status gs_field_set_gaussians(gs_field* ff, const float* host, int64_t n, int
   cudaMemsetAsync(f->params.p, 0, bytes, f->stream);
   cudaMemsetAsync(f->adam_m.p, 0, bytes, f->stream);
   cudaMemsetAsync(f->adam_v.p, 0, bytes, f->stream);
+  cudaMemsetAsync(f->dstat.p, 0, (size_t)f->stride * 8, f->stream);
   if (n > 0)
     cudaMemcpy2DAsync(f->params.p, (size_t)f->stride * 4, host, (size_t)src_stride * 4, (size_t)n * 4, gs::kNumParams,
                       cudaMemcpyHostToDevice, f->stream);
@@ -1111,6 +1130,103 @@ gs_status gs_initial_training(gs_field* ff, int32_t iterations, int32_t max_step
   return GS_OK;
 }
 
+gs_status gs_field_densify_stats(gs_field* ff, float* host_sum, float* host_count) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  const float* d = static_cast<const float*>(f->dstat.p);
+  if (f->n > 0 && host_sum && cudaMemcpy(host_sum, d, (size_t)f->n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(GS_ERR_CUDA, "reading the statistics failed");
+  if (f->n > 0 && host_count &&
+      cudaMemcpy(host_count, d + f->stride, (size_t)f->n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(GS_ERR_CUDA, "reading the statistics failed");
+  return GS_OK;
+}
+
+gs_status gs_field_densify(gs_field* ff, const gs_densify_params* prm, gs_densify_result* out) {
+  Field* f = F(ff);
+  if (!f || !prm) return fail(GS_ERR_INVALID_ARG, "NULL argument");
+  if (!(prm->grad_thresh >= 0.f) || !(prm->percent_dense > 0.f) || !(prm->min_opacity > 0.f) ||
+      !(prm->min_opacity < 1.f) || !(prm->max_scale > 0.f))
+    return fail(GS_ERR_INVALID_ARG, "bad densification parameters");
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  const int n = f->n;
+  gs_densify_result res{n, n, 0, 0, 0};
+  if (n > 0) {
+    const double extent = (double)f->scene_extent();
+    gs::DensifyThresholds th;
+    th.grad = prm->grad_thresh;
+    th.ls_dense = (float)std::log((double)prm->percent_dense * extent);
+    th.ls_big = (float)std::log((double)prm->max_scale * extent);
+    th.logit_min = (float)std::log((double)prm->min_opacity / (1.0 - (double)prm->min_opacity));
+    th.ls_shrink = (float)std::log(1.6);
+    th.seed_base = f->cfg.seed ^ ((unsigned long long)f->densify_round * 0x9E3779B97F4A7C15ull);
+    // scratch: counts a, b, c; offsets a, b, c; totals (3) + candidates (2)
+    gs_status s = f->dens_tmp.reserve((size_t)6 * n * 4 + 64, &f->own_bytes);
+    if (s) return s;
+    unsigned* tmp = static_cast<unsigned*>(f->dens_tmp.p);
+    unsigned *ca = tmp, *cb = tmp + n, *cc = tmp + 2 * (size_t)n;
+    unsigned *oa = tmp + 3 * (size_t)n, *ob = tmp + 4 * (size_t)n, *oc = tmp + 5 * (size_t)n;
+    unsigned* tot = tmp + 6 * (size_t)n;  // [0..2] totals, [3..4] clone / split candidates
+    cudaMemsetAsync(tot, 0, 64, f->stream);
+    gs::launch_densify_count(n, f->stride, static_cast<const float*>(f->params.p), static_cast<const float*>(f->dstat.p),
+                             th, ca, cb, cc, tot + 3, f->stream);
+    gs::launch_scan_flags(ca, n, oa, tot, f->stream);
+    gs::launch_scan_flags(cb, n, ob, tot + 1, f->stream);
+    gs::launch_scan_flags(cc, n, oc, tot + 2, f->stream);
+    unsigned h[5];
+    e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
+    const long long n2 = (long long)h[0] + h[1] + h[2];
+    const long long stride2 = std::max<long long>(1024, (std::max<long long>(n2, 1) + 31) / 32 * 32);
+    const size_t bytes = (size_t)stride2 * gs::kNumParams * 4;
+    if (f->cfg.hbm_budget_bytes && f->bytes_in_use() + 3 * bytes > f->cfg.hbm_budget_bytes + 3 * f->params.bytes)
+      return fail(GS_ERR_BUDGET, "densification would exceed hbm_budget_bytes");
+    gs::DevBuf np, nm, nv, nd;
+    if ((s = np.reserve(bytes, &f->own_bytes)) || (s = nm.reserve(bytes, &f->own_bytes)) ||
+        (s = nv.reserve(bytes, &f->own_bytes)) || (s = nd.reserve((size_t)stride2 * 8, &f->own_bytes))) {
+      np.release(&f->own_bytes);
+      nm.release(&f->own_bytes);
+      nv.release(&f->own_bytes);
+      nd.release(&f->own_bytes);
+      return s;
+    }
+    cudaMemsetAsync(np.p, 0, bytes, f->stream);
+    cudaMemsetAsync(nm.p, 0, bytes, f->stream);
+    cudaMemsetAsync(nv.p, 0, bytes, f->stream);
+    cudaMemsetAsync(nd.p, 0, (size_t)stride2 * 8, f->stream);
+    gs::launch_densify_write(n, f->stride, static_cast<const float*>(f->params.p), static_cast<const float*>(f->adam_m.p),
+                             static_cast<const float*>(f->adam_v.p), static_cast<const float*>(f->dstat.p), th, oa, ob,
+                             oc, tot, (int)stride2, static_cast<float*>(np.p), static_cast<float*>(nm.p),
+                             static_cast<float*>(nv.p), f->stream);
+    e = cudaStreamSynchronize(f->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("densify: ") + cudaGetErrorString(e));
+    f->params.release(&f->own_bytes);
+    f->adam_m.release(&f->own_bytes);
+    f->adam_v.release(&f->own_bytes);
+    f->dstat.release(&f->own_bytes);
+    f->params = np;
+    f->adam_m = nm;
+    f->adam_v = nv;
+    f->dstat = nd;
+    f->stride = (int)stride2;
+    f->n = (int)n2;
+    f->drop_graphs();
+    f->sized_for_views = false;
+    ++f->densify_round;
+    res.n_after = n2;
+    res.cloned = h[1];
+    res.split = h[4];
+    res.pruned = (long long)n + h[3] + 2ll * h[4] - n2 - h[4];  // results made minus results kept
+  }
+  if (out) *out = res;
+  return GS_OK;
+}
+
 gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* out_T) {
   Field* f = F(ff);
   if (!f || !cam || !out_rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
@@ -1216,6 +1332,7 @@ gs_status gs_field_restore(gs_field* ff) {
   }
   f->n = f->snap_n;
   f->adam_step = f->snap_step;
+  cudaMemsetAsync(f->dstat.p, 0, (size_t)f->stride * 8, f->stream);  // statistics are not part of a snapshot
   for (size_t j = 0; j < f->images.size(); ++j) f->images[j].T = j < f->snap_T.size() ? f->snap_T[j] : 0;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
@@ -1300,7 +1417,7 @@ extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
   if (!out.f) return fail(GS_ERR_IO, std::string("cannot write ") + path);
   FileHeader h;
   std::memcpy(h.magic, kMagic, 8);
-  h.version = 1;
+  h.version = 2;
   h.cfg_bytes = sizeof(gs_field_config);
   h.camera_bytes = sizeof(gs_camera);
   h.nparams = gs::kNumParams;
@@ -1336,6 +1453,12 @@ extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
       return fail(GS_ERR_CUDA, "reading the Gaussians back failed");
     out.put(buf.data(), buf.size() * 4);
   }
+  out.put((int64_t)f->densify_round);
+  buf.resize((size_t)2 * f->n);
+  if (f->n && cudaMemcpy2D(buf.data(), (size_t)f->n * 4, f->dstat.p, (size_t)f->stride * 4, (size_t)f->n * 4, 2,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(GS_ERR_CUDA, "reading the densification statistics back failed");
+  out.put(buf.data(), buf.size() * 4);
   if (!out.ok) return fail(GS_ERR_IO, std::string("short write to ") + path);
   return GS_OK;
 }
@@ -1348,7 +1471,7 @@ extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** ou
   if (!in.f) return fail(GS_ERR_IO, std::string("cannot read ") + path);
   FileHeader h;
   in.get(h);
-  if (!in.ok || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || h.cfg_bytes != sizeof(gs_field_config) ||
+  if (!in.ok || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 || h.cfg_bytes != sizeof(gs_field_config) ||
       h.camera_bytes != sizeof(gs_camera) || h.nparams != (uint32_t)gs::kNumParams)
     return fail(GS_ERR_IO, std::string(path) + " is not a saved field of this library");
   gs_field_config cfg;
@@ -1414,6 +1537,15 @@ extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** ou
       return fail(GS_ERR_CUDA, "uploading the Gaussians failed");
     cudaStreamSynchronize(f->stream);
   }
+  int64_t densify_round = 0;
+  in.get(densify_round);
+  buf.resize((size_t)2 * n);
+  in.get(buf.data(), buf.size() * 4);
+  if (!in.ok || densify_round < 0) return fail(GS_ERR_IO, "corrupt field file");
+  if (n && cudaMemcpy2D(f->dstat.p, (size_t)f->stride * 4, buf.data(), (size_t)n * 4, (size_t)n * 4, 2,
+                        cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(GS_ERR_CUDA, "uploading the densification statistics failed");
+  f->densify_round = densify_round;
   f->n = (int)n;
   f->adam_step = adam_step;
   cudaError_t e = cudaStreamSynchronize(f->stream);

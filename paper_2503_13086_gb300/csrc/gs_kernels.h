@@ -90,6 +90,23 @@ void launch_init_gaussians(const PointGridDev& g, const float* xyz, const float*
                            const unsigned* far, const unsigned* offsets, float* params, float* m, float* v, int stride,
                            int n0, float opacity_logit, double sh_c0, cudaStream_t s);
 
+// 3DGS adaptive density control (k_densify.cu).
+struct DensifyThresholds {
+  float grad;       // mean view-space gradient norm that makes a Gaussian clone or split
+  float ls_dense;   // log(percent_dense x extent): clone at or below, split above
+  float ls_big;     // log(max_scale x extent): pruned above
+  float logit_min;  // logit(min_opacity): pruned below
+  float ls_shrink;  // log(1.6): what a split lowers every log-scale by
+  unsigned long long seed_base;  // seed ^ (round x 0x9E3779B97F4A7C15)
+};
+void launch_densify_stats(int n, int stride, int n_views, const ViewDev* views, const unsigned* count,
+                          const float* g2s, const Control* ctl, float* dstat, cudaStream_t s);
+void launch_densify_count(int n, int stride, const float* params, const float* dstat, const DensifyThresholds& th,
+                          unsigned* ca, unsigned* cb, unsigned* cc, unsigned* cand, cudaStream_t s);
+void launch_densify_write(int n, int stride, const float* params, const float* m, const float* v, const float* dstat,
+                          const DensifyThresholds& th, const unsigned* oa, const unsigned* ob, const unsigned* oc,
+                          const unsigned* totals, int stride2, float* p2, float* m2, float* v2, cudaStream_t s);
+
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,

@@ -344,6 +344,8 @@ void Raster::enqueue_backward(cudaStream_t s, float* params, const float* image,
   launch_project_backward(params, stride, n_views, sp(), vd(), proj(), static_cast<float4*>(ginst.p),
                           static_cast<const unsigned*>(inst_rec.p), static_cast<float*>(carry.p), (long long)m_cap,
                           static_cast<float*>(g2s.p), ctl(), grads, m, v, grad2d, num_sms, s);
+  if (dstat)
+    launch_densify_stats(n, stride, n_views, vd(), proj().count, static_cast<const float*>(g2s.p), ctl(), dstat, s);
   mark(s, 9);
 }
 
