@@ -120,6 +120,8 @@ struct Field {
   std::vector<std::vector<float>> M;  // overlap matrix
   // sparse points of all registered images, hashed by cells (the field update of Sec. IV-B)
   DevBuf pts_xyz, pts_next, grid_keys, grid_head, new_rgb, far_flags, far_off, far_count;
+  // the same points in cells of kCoarseCells x grid_cell, for the 3-NN search where points are sparse
+  DevBuf pts_next_c, grid_keys_c, grid_head_c;
   long long n_points = 0;
   unsigned grid_slots = 0;
   float grid_cell = 1.f;
@@ -164,20 +166,27 @@ struct Field {
     snap_p.release(&own_bytes);
     snap_m.release(&own_bytes);
     snap_v.release(&own_bytes);
-    DevBuf* pts[] = {&pts_xyz, &pts_next, &grid_keys, &grid_head, &new_rgb, &far_flags, &far_off, &far_count};
+    DevBuf* pts[] = {&pts_xyz,   &pts_next,  &grid_keys,  &grid_head,   &new_rgb,
+                     &far_flags, &far_off,   &far_count,  &pts_next_c,  &grid_keys_c, &grid_head_c};
     for (DevBuf* b : pts) b->release(&own_bytes);
     if (count_h) cudaFreeHost(count_h);
   }
 
-  PointGridDev grid_dev() const {
+  PointGridDev grid_dev(bool coarse = false) const {
     PointGridDev g;
     g.xyz = static_cast<const float*>(pts_xyz.p);
-    g.keys = static_cast<unsigned long long*>(grid_keys.p);
-    g.head = static_cast<int*>(grid_head.p);
-    g.next = static_cast<const int*>(pts_next.p);
+    g.keys = static_cast<unsigned long long*>((coarse ? grid_keys_c : grid_keys).p);
+    g.head = static_cast<int*>((coarse ? grid_head_c : grid_head).p);
+    g.next = static_cast<const int*>((coarse ? pts_next_c : pts_next).p);
     g.mask = grid_slots ? grid_slots - 1u : 0u;
-    g.cell = grid_cell;
+    g.cell = coarse ? gs::kCoarseCells * grid_cell : grid_cell;
     return g;
+  }
+
+  // Points first..first+count-1 into both grids.
+  void insert_points(long long first, long long count) {
+    launch_insert_points(grid_dev(false), static_cast<int*>(pts_next.p), first, count, stream);
+    launch_insert_points(grid_dev(true), static_cast<int*>(pts_next_c.p), first, count, stream);
   }
 
   // Room for `want` sparse points: the point arrays keep their contents; a larger hash table is
@@ -186,43 +195,52 @@ struct Field {
     gs_status s;
     if ((long long)(pts_xyz.bytes / 12) < want) {
       const long long cap = std::max<long long>(want, std::max<long long>(2 * (long long)(pts_xyz.bytes / 12), 65536));
-      const size_t grow = (size_t)cap * 16 - pts_xyz.bytes - pts_next.bytes;
+      const size_t grow = (size_t)cap * 20 - pts_xyz.bytes - pts_next.bytes - pts_next_c.bytes;
       if (cfg.hbm_budget_bytes && bytes_in_use() + grow > cfg.hbm_budget_bytes)
         return fail(GS_ERR_BUDGET, "registering the sparse points would exceed hbm_budget_bytes");
-      DevBuf nx, nn;
-      if ((s = nx.reserve((size_t)cap * 12, &own_bytes)) || (s = nn.reserve((size_t)cap * 4, &own_bytes))) {
+      DevBuf nx, nn, nc;
+      if ((s = nx.reserve((size_t)cap * 12, &own_bytes)) || (s = nn.reserve((size_t)cap * 4, &own_bytes)) ||
+          (s = nc.reserve((size_t)cap * 4, &own_bytes))) {
         nx.release(&own_bytes);
         nn.release(&own_bytes);
+        nc.release(&own_bytes);
         return s;
       }
       if (n_points > 0) {
         cudaMemcpyAsync(nx.p, pts_xyz.p, (size_t)n_points * 12, cudaMemcpyDeviceToDevice, stream);
         cudaMemcpyAsync(nn.p, pts_next.p, (size_t)n_points * 4, cudaMemcpyDeviceToDevice, stream);
+        cudaMemcpyAsync(nc.p, pts_next_c.p, (size_t)n_points * 4, cudaMemcpyDeviceToDevice, stream);
       }
       cudaStreamSynchronize(stream);
       pts_xyz.release(&own_bytes);
       pts_next.release(&own_bytes);
+      pts_next_c.release(&own_bytes);
       pts_xyz = nx;
       pts_next = nn;
+      pts_next_c = nc;
     }
     if ((long long)grid_slots < 2 * want) {
       unsigned long long slots = 1024;
       while ((long long)slots < 2 * want) slots <<= 1;
       if (slots > (1ull << 31)) return fail(GS_ERR_CAPACITY, "too many sparse points");
-      const size_t bytes = (size_t)slots * 12;
-      const size_t have = grid_keys.bytes + grid_head.bytes;
+      const size_t bytes = (size_t)slots * 24;
+      const size_t have = grid_keys.bytes + grid_head.bytes + grid_keys_c.bytes + grid_head_c.bytes;
       if (cfg.hbm_budget_bytes && bytes > have && bytes_in_use() + (bytes - have) > cfg.hbm_budget_bytes)
         return fail(GS_ERR_BUDGET, "growing the point grid would exceed hbm_budget_bytes");
-      grid_keys.release(&own_bytes);
-      grid_head.release(&own_bytes);
-      if ((s = grid_keys.reserve((size_t)slots * 8, &own_bytes)) || (s = grid_head.reserve((size_t)slots * 4, &own_bytes))) {
+      DevBuf* tables[] = {&grid_keys, &grid_head, &grid_keys_c, &grid_head_c};
+      for (DevBuf* b : tables) b->release(&own_bytes);
+      if ((s = grid_keys.reserve((size_t)slots * 8, &own_bytes)) || (s = grid_head.reserve((size_t)slots * 4, &own_bytes)) ||
+          (s = grid_keys_c.reserve((size_t)slots * 8, &own_bytes)) ||
+          (s = grid_head_c.reserve((size_t)slots * 4, &own_bytes))) {
         grid_slots = 0;
         return s;
       }
       grid_slots = (unsigned)slots;
       cudaMemsetAsync(grid_keys.p, 0xFF, (size_t)slots * 8, stream);
       cudaMemsetAsync(grid_head.p, 0xFF, (size_t)slots * 4, stream);
-      launch_insert_points(grid_dev(), static_cast<int*>(pts_next.p), 0, n_points, stream);
+      cudaMemsetAsync(grid_keys_c.p, 0xFF, (size_t)slots * 8, stream);
+      cudaMemsetAsync(grid_head_c.p, 0xFF, (size_t)slots * 4, stream);
+      insert_points(0, n_points);
     }
     return GS_OK;
   }
@@ -1001,7 +1019,7 @@ gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int
     unsigned* far = static_cast<unsigned*>(f->far_flags.p);
     unsigned* off = static_cast<unsigned*>(f->far_off.p);
     gs::launch_far_points(g, xyz_new, n_pts, thr * thr, ring, far, f->stream);
-    gs::launch_insert_points(g, static_cast<int*>(f->pts_next.p), f->n_points, n_pts, f->stream);
+    f->insert_points(f->n_points, n_pts);
     gs::launch_scan_flags(far, n_pts, off, static_cast<unsigned*>(f->far_count.p), f->stream);
     cudaMemcpyAsync(f->count_h, f->far_count.p, sizeof(unsigned), cudaMemcpyDeviceToHost, f->stream);
     e = cudaStreamSynchronize(f->stream);
@@ -1016,7 +1034,7 @@ gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int
         return s;
       }
       const double C0 = 0.5 * std::sqrt(1.0 / 3.14159265358979323846);
-      gs::launch_init_gaussians(f->grid_dev(), xyz_new, static_cast<const float*>(f->new_rgb.p), n_pts, first_pt, far,
+      gs::launch_init_gaussians(f->grid_dev(false), f->grid_dev(true), xyz_new, static_cast<const float*>(f->new_rgb.p), n_pts, first_pt, far,
                                 off, static_cast<float*>(f->params.p), static_cast<float*>(f->adam_m.p),
                                 static_cast<float*>(f->adam_v.p), f->stride, f->n, (float)std::log(0.1 / 0.9), C0,
                                 f->stream);
@@ -1523,7 +1541,7 @@ extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** ou
     if (cudaMemcpy(f->pts_xyz.p, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(GS_ERR_CUDA, "uploading the sparse points failed");
     f->n_points = n_points;
-    gs::launch_insert_points(f->grid_dev(), static_cast<int*>(f->pts_next.p), 0, n_points, f->stream);
+    f->insert_points(0, n_points);
   }
   if ((s = f->reserve_gaussians(std::max<int64_t>(n, 1)))) return s;
   gs::DevBuf* dst[3] = {&f->params, &f->adam_m, &f->adam_v};

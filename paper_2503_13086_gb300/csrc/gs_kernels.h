@@ -26,7 +26,7 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
+constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep CTA
 constexpr int kSortBits = 8;
 constexpr int kSortBins = 1 << kSortBits;
@@ -74,6 +74,7 @@ void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, 
                            const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s);
 
 // Field update (Sec. IV-B): the registered sparse points, hashed by cubic cells.
+constexpr float kCoarseCells = 4.f;  // coarse grid cell edge in fine cells (3-NN search)
 struct PointGridDev {
   const float* xyz;           // 3 floats per point
   unsigned long long* keys;   // per slot: cell key, ~0 = empty
@@ -86,7 +87,7 @@ void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float
                        cudaStream_t s);
 void launch_insert_points(const PointGridDev& g, int* next, long long first, long long count, cudaStream_t s);
 void launch_scan_flags(const unsigned* far, int n, unsigned* offsets, unsigned* count, cudaStream_t s);
-void launch_init_gaussians(const PointGridDev& g, const float* xyz, const float* rgb, int n_new, long long self0,
+void launch_init_gaussians(const PointGridDev& g, const PointGridDev& gc, const float* xyz, const float* rgb, int n_new, long long self0,
                            const unsigned* far, const unsigned* offsets, float* params, float* m, float* v, int stride,
                            int n0, float opacity_logit, double sh_c0, cudaStream_t s);
 

@@ -12,6 +12,10 @@
 //         the mean squared distance to its 3 nearest other points (shells of cells, stopping once
 //         the third nearest is closer than the searched reach), identity rotation, opacity 0.1,
 //         DC colour from the point colour, higher SH zero; its Adam moments are zeroed.
+// The points are hashed twice: in cells of the threshold (the far test, and the 3-NN search for
+// its first shells) and in cells kCoarseCells times larger, where the 3-NN search restarts when
+// the first shells do not settle it, so a sparse neighbourhood costs a few coarse shells instead
+// of thousands of empty fine cells.
 // Squared distances are formed with explicit round-to-nearest operations (no contraction), so
 // the decisions are the same on every host and device.
 #include "gs_engine.h"
@@ -21,7 +25,8 @@ namespace gs {
 namespace {
 
 constexpr unsigned long long kEmptyCell = ~0ull;
-constexpr int kMaxShells = 64;  // kNN search bound (cells); beyond it the points found are used
+constexpr int kMaxShells = 64;   // kNN search bound (coarse cells); beyond it the points found are used
+constexpr int kFineShells = 3;   // fine-grid shells tried first
 
 __device__ __forceinline__ long long cell_of(float v, float cell) {
   return (long long)floorf(__fdiv_rn(v, cell));
@@ -58,6 +63,46 @@ __device__ __forceinline__ int cell_head(const PointGridDev& g, unsigned long lo
     s = (s + 1u) & g.mask;
   }
   return -1;
+}
+
+// The three smallest squared distances from p to the grid's points other than `self` (b0 <= b1 <=
+// b2, INFINITY where fewer), searching shells 0..max_shells-1 of cells around p's cell and stopping
+// once the third is within the searched reach.  Returns the number of points seen, or -(seen + 1)
+// when the shells ran out before the answer was settled.
+__device__ __forceinline__ int knn3(const PointGridDev& g, const float* p, long long self, int max_shells, float& b0,
+                                    float& b1, float& b2) {
+  const long long cx = cell_of(p[0], g.cell), cy = cell_of(p[1], g.cell), cz = cell_of(p[2], g.cell);
+  b0 = b1 = b2 = INFINITY;
+  int found = 0;
+  for (int r = 0; r < max_shells; ++r) {
+    for (int a = -r; a <= r; ++a)
+      for (int b = -r; b <= r; ++b) {
+        const bool face = (a == -r || a == r || b == -r || b == r);
+        const int cstep = face ? 1 : (r > 0 ? 2 * r : 1);  // inside the square only the two caps
+        for (int c = -r; c <= r; c += cstep)
+          for (int id = cell_head(g, cell_key(cx + a, cy + b, cz + c)); id >= 0; id = g.next[id]) {
+            if (id == self) continue;
+            const float d = dist2(g.xyz + 3ll * id, p[0], p[1], p[2]);
+            ++found;
+            if (d < b2) {
+              if (d < b1) {
+                b2 = b1;
+                if (d < b0) {
+                  b1 = b0;
+                  b0 = d;
+                } else {
+                  b1 = d;
+                }
+              } else {
+                b2 = d;
+              }
+            }
+          }
+      }
+    const float reach = __fmul_rn((float)r, g.cell);  // every point this close has been seen
+    if (found >= 3 && b2 <= __fmul_rn(reach, reach)) return found;
+  }
+  return -found - 1;
 }
 
 }  // namespace
@@ -146,7 +191,7 @@ __global__ void __launch_bounds__(1024) k_scan_flags(const unsigned* __restrict_
 }
 
 // K11d
-__global__ void __launch_bounds__(128) k_init_gaussians(PointGridDev g, const float* __restrict__ xyz,
+__global__ void __launch_bounds__(128) k_init_gaussians(PointGridDev g, PointGridDev gc, const float* __restrict__ xyz,
                                                         const float* __restrict__ rgb, int n_new, long long self0,
                                                         const unsigned* __restrict__ far,
                                                         const unsigned* __restrict__ offsets, float* __restrict__ params,
@@ -156,37 +201,10 @@ __global__ void __launch_bounds__(128) k_init_gaussians(PointGridDev g, const fl
   if (k >= n_new || !far[k]) return;
   const float* p = xyz + 3ll * k;
   const long long self = self0 + k;
-  const long long cx = cell_of(p[0], g.cell), cy = cell_of(p[1], g.cell), cz = cell_of(p[2], g.cell);
-  float b0 = INFINITY, b1 = INFINITY, b2 = INFINITY;  // the three smallest, ascending
-  int found = 0;
-  for (int r = 0; r < kMaxShells; ++r) {
-    for (int a = -r; a <= r; ++a)
-      for (int b = -r; b <= r; ++b) {
-        const bool face = (a == -r || a == r || b == -r || b == r);
-        const int cstep = face ? 1 : (r > 0 ? 2 * r : 1);  // inside the square only the two caps
-        for (int c = -r; c <= r; c += cstep)
-          for (int id = cell_head(g, cell_key(cx + a, cy + b, cz + c)); id >= 0; id = g.next[id]) {
-            if (id == self) continue;
-            const float d = dist2(g.xyz + 3ll * id, p[0], p[1], p[2]);
-            ++found;
-            if (d < b2) {
-              if (d < b1) {
-                b2 = b1;
-                if (d < b0) {
-                  b1 = b0;
-                  b0 = d;
-                } else {
-                  b1 = d;
-                }
-              } else {
-                b2 = d;
-              }
-            }
-          }
-      }
-    const float reach = __fmul_rn((float)r, g.cell);  // every point this close has been seen
-    if (found >= 3 && b2 <= __fmul_rn(reach, reach)) break;
-  }
+  float b0, b1, b2;
+  int found = knn3(g, p, self, kFineShells, b0, b1, b2);
+  if (found < 0) found = knn3(gc, p, self, kMaxShells, b0, b1, b2);
+  if (found < 0) found = -found - 1;  // shell limit reached: the points found are used
   float d2 = 1e-7f;
   if (found > 0) {
     const int m = found < 3 ? found : 3;
@@ -231,11 +249,11 @@ void launch_scan_flags(const unsigned* far, int n, unsigned* offsets, unsigned* 
   k_scan_flags<<<1, 1024, 0, s>>>(far, n, offsets, count);
 }
 
-void launch_init_gaussians(const PointGridDev& g, const float* xyz, const float* rgb, int n_new, long long self0,
+void launch_init_gaussians(const PointGridDev& g, const PointGridDev& gc, const float* xyz, const float* rgb, int n_new, long long self0,
                            const unsigned* far, const unsigned* offsets, float* params, float* m, float* v, int stride,
                            int n0, float opacity_logit, double sh_c0, cudaStream_t s) {
   if (n_new <= 0) return;
-  k_init_gaussians<<<(n_new + 127) / 128, 128, 0, s>>>(g, xyz, rgb, n_new, self0, far, offsets, params, m, v, stride,
+  k_init_gaussians<<<(n_new + 127) / 128, 128, 0, s>>>(g, gc, xyz, rgb, n_new, self0, far, offsets, params, m, v, stride,
                                                        n0, opacity_logit, sh_c0);
 }
 
