@@ -220,11 +220,12 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H, pts_range=(5000,
 
 
 def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False,
-               thresh=0.0):
+               thresh=0.0, sparse=0):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
-                            scene_extent=7.0, seed=3, batch_scaling=scaling, add_dist_thresh=thresh)
+                            scene_extent=7.0, seed=3, batch_scaling=scaling, add_dist_thresh=thresh,
+                            sparse_adam=sparse)
     if kernel_times:
         sess.field.set_timing(True)
     pairs, add_s, int_s = 0, [], []
@@ -246,7 +247,8 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, 
     sess.close()
     return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
                 pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn,
-                batch_scaling=scaling, add_image_mean_s=float(np.mean(add_s)), integrate_mean_s=float(np.mean(int_s)),
+                batch_scaling=scaling, sparse_adam=bool(sparse), add_image_mean_s=float(np.mean(add_s)),
+                integrate_mean_s=float(np.mean(int_s)),
                 **({"kernel_ms_per_step": kt} if kt else {}))
 
 
@@ -467,7 +469,8 @@ def run_batched(args):
 def run_stream_long(args):
     """The streaming session at full length: 150 arrivals at 1297 x 840 on a random walk, 5k-20k
     sparse points each, new points kept down to 0.005 from the field so it grows to ~1.5M Gaussians;
-    the per-view graph-replayed path and the 3-view batched path."""
+    the per-view graph-replayed path (dense and sparse Adam; per-kernel times recorded by events in the
+    replayed graphs) and the 3-view batched path."""
     import torch
     import paper_2503_13086_gb300 as gs
     torch.cuda.set_device(0)
@@ -478,8 +481,10 @@ def run_stream_long(args):
         run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1,
                    thresh=0.005)
     res = {}
-    for name, b in (("graph_async_per_view", 1), ("batched3_graph_scaled", 3)):
-        r = run_stream(cams, targets, pts, batch=b, graph=1, asyn=16, scaling=1, thresh=0.005)
+    for name, b, sp in (("graph_async_per_view", 1, 0), ("batched3_graph_scaled", 3, 0),
+                        ("graph_async_per_view_sparse_adam", 1, 1)):
+        r = run_stream(cams, targets, pts, batch=b, graph=1, asyn=16, scaling=1, thresh=0.005, sparse=sp,
+                       kernel_times=(b == 1))
         res[name] = r
     print(json.dumps({"workload": f"streaming: {args.arrivals} arrivals, 1297x840, random walk 60-80% overlap, "
                                   f"5k-20k sparse points each, new-point threshold 0.005, T_I = 200 over the new "

@@ -192,6 +192,9 @@ typedef struct gs_field_config {
                                reported loss only and has no gradient.  The paper's preset:
                                lambda_l1 0.47, lambda_ssim 0.12, lambda_load 0.41.  Default 0. */
   int32_t densify_stats;    /* 1: every step accumulates the statistics gs_field_densify uses */
+  int32_t sparse_adam;      /* 1: a step's Adam updates only the Gaussians with instances in one of
+                               its views (later 3DGS releases' sparse Adam; bias correction by the
+                               field's step count); 0 (default): all, as the original dense Adam */
 } gs_field_config;
 
 /* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2

@@ -80,7 +80,8 @@ class FieldConfig(ctypes.Structure):
                 ("add_dist_thresh", ctypes.c_float), ("scene_extent", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64),
                 ("tiling", Tiling), ("batch_scaling", ctypes.c_int32), ("lambda_l1", ctypes.c_float),
-                ("lambda_load", ctypes.c_float), ("densify_stats", ctypes.c_int32)]
+                ("lambda_load", ctypes.c_float), ("densify_stats", ctypes.c_int32),
+                ("sparse_adam", ctypes.c_int32)]
 
 
 class DensifyParams(ctypes.Structure):

@@ -91,6 +91,7 @@ struct StepParams {
   float step_size_scale; // 1 / (1 - beta1^t)
   float bc2_sqrt;        // sqrt(1 - beta2^t)
   int adam;              // 1: apply Adam, 0: write gradients, 2: write nothing (autotuner timing)
+  int sparse;            // with adam == 1: only Gaussians with instances in a view of the step
 };
 
 // Exponent of the 2D Gaussian at offset (dx, dy) from its centre.  The conic is stored

@@ -547,6 +547,7 @@ struct Field {
     P.step_size_scale = (float)(1.0 / (1.0 - std::pow(b1, (double)t)));
     P.bc2_sqrt = (float)std::sqrt(1.0 - std::pow(b2, (double)t));
     P.adam = 1;
+    P.sparse = cfg.sparse_adam ? 1 : 0;
   }
 
   // Enqueue the prepared step: the sizing launch for new view sizes, else a graph replay (captured

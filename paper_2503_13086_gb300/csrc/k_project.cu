@@ -652,6 +652,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
 
     geo_backward(V, g, g2, gmu, gls, gq);
   }
+  if (nvis == 0 && A.adam == 1 && sp->sparse) return;  // sparse Adam: not seen by the step
 
   // SH rows, four coefficients (12 rows) at a time; accumulates the direction gradient.
   sh_group<0>(A, i, nvis, vmask, vdir, vcol, vdd);
@@ -743,10 +744,12 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
 
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gop = 0.f;
+  bool seen = false;
   for (int v = 0; v < n_views; ++v) {
     const long long rec = (long long)v * stride + i;
     const unsigned cnt = count[rec];
     if (cnt == 0u) continue;
+    seen = true;
     float g2[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) g2[k] = g2s[k * n_rec + rec];
@@ -769,6 +772,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
     gop += g2[5] * o * (1.f - o);
     geo_backward(V, g, g2, gmu, gls, gq);
   }
+  if (!seen && A.adam == 1 && sp->sparse) return;  // sparse Adam: not seen by the step
   const float gg[11] = {gmu[0], gmu[1], gmu[2], gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
   const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
   const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};

@@ -261,7 +261,7 @@ struct SortSmem {
   unsigned tile;
 };
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(unsigned long long* __restrict__ keys0,
+__global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsigned long long* __restrict__ keys0,
                                                             unsigned* __restrict__ vals0,
                                                             unsigned long long* __restrict__ keys1,
                                                             unsigned* __restrict__ vals1,

@@ -364,3 +364,36 @@ def test_initial_training_draws_views_and_follows_the_3dgs_rate():
     assert [f.image_info(i, 3)[0] for i in range(3)] == counts
     assert f.stats()["adam_step"] == 6
     f.close()
+
+
+def test_sparse_adam_updates_only_the_gaussians_a_step_sees():
+    """sparse_adam: Gaussians without instances in the step's views keep parameters and moments
+    bit for bit; the others take the dense step's update."""
+    p, cams, tg = config1(seed=8)
+    p = p.copy()
+    p[0, ::5] += 3.0  # push a fifth of the cube out of the view
+    f = make_field(use_graph=0, sparse_adam=1)
+    f.set_gaussians(p)
+    img = f.add_image(cams[0], tg[0])
+    lr = f.image_lr(img)
+    loss = f.optimize_step([img])
+    got, gm, gv = f.get_gaussians(with_adam=True)
+    L, g, r = oracle.loss_and_grad(p, [ocam(cams[0])], tg, lam=0.2, prec="f32")
+    rect = r["projs"][0]["rect"]
+    seen = ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]) > 0) & (r["projs"][0]["radius"] > 0)
+    assert 0.3 < seen.mean() < 0.95
+    ref = p.copy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    oracle.adam(ref, g, m, v, [lr] + LRS_REST, 1, prec="f32")
+    assert abs(loss - L) <= 1e-5 * max(1.0, abs(L))
+    assert np.array_equal(got[:, ~seen], p[:, ~seen])
+    assert not gm[:, ~seen].any() and not gv[:, ~seen].any()
+    groups = [(0, 3, lr), (3, 6, 5e-3), (6, 10, 1e-3), (10, 11, 0.05), (11, 14, 2.5e-3), (14, 59, 1.25e-4)]
+    for a, b, lrg in groups:
+        d = np.abs(got[a:b, seen] - ref[a:b, seen])
+        bad = d > 1e-3 * lrg + 1e-6
+        assert bad.mean() < 2e-3, (a, b, bad.mean())
+    f.optimize_step([img])  # the unseen ones stay put on later steps too
+    assert np.array_equal(f.get_gaussians()[:, ~seen], p[:, ~seen])
+    f.close()
