@@ -22,6 +22,30 @@ constexpr float kAlphaMax = 0.99f;  // alpha clamp
 constexpr float kAlphaMin = 1.0f / 255.0f;  // alpha cutoff
 constexpr float kTransMin = 1e-4f;  // stop before T would drop below this
 
+// Programmatic dependent launch.  The step's kernels are launched with programmatic stream
+// serialisation (launch_dep): a kernel's CTAs may be scheduled while its predecessor is still
+// running, so every such kernel first waits, in every thread, until the predecessor grid has
+// completed and its writes are visible (dep_wait, before reading anything), then lets its own
+// successor be scheduled (dep_release).  Outside such a launch both are no-ops.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 // Error bits of Control::error.
 constexpr unsigned kErrTimeout = 1u;     // a bounded spin-wait gave up
 constexpr unsigned kErrOverflow = 2u;    // instance capacity exceeded (step skipped)

@@ -57,6 +57,7 @@ struct Raster {
   DevBuf zeroA;  // Control + scan look-back state (cleared before K1)
   DevBuf zeroB;  // histograms + sort look-back state + ranges + chunk map (cleared before K3)
   size_t zeroA_bytes = 0, zeroB_bytes = 0, sort_state_bytes = 0, ranges_bytes = 0, chunk_bytes = 0;
+  bool zeroB_pending = true;  // zeroB still to be cleared by the forward tail
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp, g2s;
   DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order, tile_chunks;
   DevBuf inst_rec, block_owner, carry;  // instance -> record, owner of every 256th instance, K9a partials

@@ -279,6 +279,10 @@ gs_status Raster::upload(cudaStream_t s) {
 
 gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int stride_, bool size_exactly) {
   cudaMemsetAsync(zeroA.p, 0, zeroA_bytes, s);
+  // zeroB is cleared here too unless the sizing below may reallocate it, so that the kernels from
+  // K1 on follow one another with no other node between them (programmatic dependent launch)
+  zeroB_pending = size_exactly;
+  if (!size_exactly) cudaMemsetAsync(zeroB.p, 0, zeroB_bytes, s);
   mark(s, 0);
   launch_project(params, stride_, n_views, sp(), vd(), proj(), s);
   mark(s, 1);
@@ -300,7 +304,8 @@ gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int 
 }
 
 gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp) {
-  cudaMemsetAsync(zeroB.p, 0, zeroB_bytes, s);
+  if (zeroB_pending) cudaMemsetAsync(zeroB.p, 0, zeroB_bytes, s);
+  zeroB_pending = false;
   const long long n_items = (long long)n_views * stride;
   unsigned long long* k0 = static_cast<unsigned long long*>(keys0.p);
   unsigned long long* k1 = static_cast<unsigned long long*>(keys1.p);

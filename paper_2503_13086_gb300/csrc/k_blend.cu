@@ -70,6 +70,8 @@ __device__ __forceinline__ long long chunk_base(unsigned start, long long tile) 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, long long n_tiles,
                                                      int* __restrict__ order, const Control* __restrict__ ctl) {
+  dep_wait();
+  dep_release();
   __shared__ unsigned s_cnt[32];
   __shared__ unsigned s_base[32];
   if (ctl->overflow) return;
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     Control* __restrict__ ctl, const int* __restrict__ order, float* __restrict__ image, float* __restrict__ Tout,
     unsigned* __restrict__ last_out, unsigned* __restrict__ gp_out, float4* __restrict__ ckpt,
     unsigned* __restrict__ cmask, int* __restrict__ chunk_tile, int* __restrict__ tile_chunks) {
+  dep_wait();
+  dep_release();
   using S = Shape<TW, TH>;
   constexpr int kPix = S::kPix;
   static_assert(BATCH % kChunk == 0, "batches hold whole chunks");
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
 
 void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const Control* ctl, cudaStream_t s) {
   if (n_tiles <= 0) return;
-  k_tile_order<<<1, 1024, 0, s>>>(ranges, n_tiles, order, ctl);
+  launch_dep(k_tile_order, dim3(1), dim3(1024), 0, s, ranges, n_tiles, order, ctl);
 }
 
 namespace {
@@ -316,9 +320,8 @@ void launch_forward_instance(const ViewDev* views, int n_views, long long n_tile
                              unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
   long long grid = (long long)num_sms * fwd_occupancy<TW, TH, BATCH>();
   if (grid > n_tiles) grid = n_tiles;
-  k_blend_forward<TW, TH, BATCH><<<(unsigned)grid, TW * TH, 0, s>>>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl,
-                                                                   order, image, T, last, gp, ckpt, cmask, chunk_tile,
-                                                                   tile_chunks);
+  launch_dep(k_blend_forward<TW, TH, BATCH>, dim3((unsigned)grid), dim3(TW * TH), 0, s, views, n_views, n_tiles, ranges,
+      vals, pb, sp, ctl, order, image, T, last, gp, ckpt, cmask, chunk_tile, tile_chunks);
 }
 }  // namespace
 
@@ -379,6 +382,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const float* __restrict__ image, const float* __restrict__ dimage, const float4* __restrict__ ckpt,
     const unsigned* __restrict__ cmask, const int* __restrict__ chunk_tile, const int* __restrict__ tile_chunks,
     float4* __restrict__ ginst) {
+  dep_wait();
+  dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   using Sh = Shape<TW, TH>;
@@ -566,9 +571,9 @@ void launch_backward_instance(const ViewDev* views, int n_views, long long n_til
                               const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                               const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
                               const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
-  k_blend_backward<TW, TH><<<num_sms * bwd_occupancy<TW, TH>(), kBwdWarps * 32, sizeof(BwdWarp<TW * TH>) * kBwdWarps,
-                             s>>>(
-      views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, chunk_tile, tile_chunks, ginst);
+  launch_dep(k_blend_backward<TW, TH>, dim3(num_sms * bwd_occupancy<TW, TH>()), dim3(kBwdWarps * 32),
+      sizeof(BwdWarp<TW * TH>) * kBwdWarps, s, views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt,
+      cmask, chunk_tile, tile_chunks, ginst);
 }
 }  // namespace
 

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(256) k_densify_stats(int n, int stride, int n_
                                                        const unsigned* __restrict__ count,
                                                        const float* __restrict__ g2s, const Control* __restrict__ ctl,
                                                        float* __restrict__ dstat) {
+  dep_wait();
+  dep_release();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || ctl->overflow) return;
   const long long n_rec = (long long)n_views * stride;
@@ -153,7 +155,8 @@ __global__ void __launch_bounds__(256) k_densify_write(int n, int stride, const 
 void launch_densify_stats(int n, int stride, int n_views, const ViewDev* views, const unsigned* count,
                           const float* g2s, const Control* ctl, float* dstat, cudaStream_t s) {
   if (n <= 0) return;
-  k_densify_stats<<<(n + 255) / 256, 256, 0, s>>>(n, stride, n_views, views, count, g2s, ctl, dstat);
+  launch_dep(k_densify_stats, dim3((n + 255) / 256), dim3(256), 0, s, n, stride, n_views, views, count, g2s, ctl,
+      dstat);
 }
 
 void launch_densify_count(int n, int stride, const float* params, const float* dstat, const DensifyThresholds& th,

@@ -109,6 +109,8 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
                                                       const StepParams* __restrict__ sp,
                                                       float* __restrict__ partials, double* __restrict__ block_sums,
                                                       Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
+  dep_wait();
+  dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LossFwdSmem& S = *reinterpret_cast<LossFwdSmem*>(smem_raw);
   __shared__ double s_red[2][8];
@@ -322,6 +324,8 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
                                                        const StepParams* __restrict__ sp,
                                                        const float* __restrict__ partials,
                                                        const Control* __restrict__ ctl, float* __restrict__ dimage) {
+  dep_wait();
+  dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LossBwdSmem& S = *reinterpret_cast<LossBwdSmem*>(smem_raw);
   if (ctl->overflow) return;
@@ -447,11 +451,11 @@ void init_loss_attributes() {
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
                  float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s) {
   if (n_blocks <= 0) return;
-  k_loss_forward<<<(unsigned)n_blocks, 256, sizeof(LossFwdSmem), s>>>(views, n_views, n_blocks, image, sp, partials,
-                                                                        block_sums, ctl, ledger);
+  launch_dep(k_loss_forward, dim3((unsigned)n_blocks), dim3(256), sizeof(LossFwdSmem), s, views, n_views, n_blocks,
+      image, sp, partials, block_sums, ctl, ledger);
   if (dimage)
-    k_loss_backward<<<(unsigned)n_blocks, 256, sizeof(LossBwdSmem), s>>>(views, n_views, image, sp, partials, ctl,
-                                                                         dimage);
+    launch_dep(k_loss_backward, dim3((unsigned)n_blocks), dim3(256), sizeof(LossBwdSmem), s, views, n_views, image, sp,
+        partials, ctl, dimage);
 }
 
 }  // namespace gs

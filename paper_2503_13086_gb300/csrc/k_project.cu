@@ -179,6 +179,8 @@ __device__ __forceinline__ bool geo_forward(const ViewDev& V, const float mu[3],
 __global__ void __launch_bounds__(256) k_project(const float* __restrict__ params, int stride,
                                                  const StepParams* __restrict__ sp,
                                                  const ViewDev* __restrict__ views, ProjBuffers out) {
+  dep_wait();
+  dep_release();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y;
   if (i >= stride) return;
@@ -406,6 +408,8 @@ __global__ void __launch_bounds__(256) k_inst_reduce(const unsigned* __restrict_
                                                      const Control* __restrict__ ctl, float* __restrict__ g2s,
                                                      float* __restrict__ grad2d, float* __restrict__ head,
                                                      float* __restrict__ tail) {
+  dep_wait();
+  dep_release();
   if (ctl->overflow) return;
   const int lane = threadIdx.x & 31;
   const unsigned long long M = ctl->m_total;
@@ -461,6 +465,8 @@ __global__ void __launch_bounds__(256) k_inst_carry(const unsigned* __restrict__
                                                     const Control* __restrict__ ctl, const float* __restrict__ head,
                                                     const float* __restrict__ tail, float* __restrict__ g2s,
                                                     float* __restrict__ grad2d) {
+  dep_wait();
+  dep_release();
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ctl->overflow || r >= n_rec) return;
   const unsigned long long cnt = count[r];
@@ -574,6 +580,8 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
     const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
     float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+  dep_wait();
+  dep_release();
   const long long n_rec = (long long)n_views * stride;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sp->n) return;
@@ -707,6 +715,8 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
     const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
     float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+  dep_wait();
+  dep_release();
   const long long n_rec = (long long)n_views * stride;
   __shared__ float s_gsh[48 * 256];  // [row][thread]
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -826,7 +836,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ params, const 
 void launch_project(const float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
                     const ProjBuffers& out, cudaStream_t s) {
   dim3 grid((stride + 255) / 256, n_views);
-  k_project<<<grid, 256, 0, s>>>(params, stride, sp, views, out);
+  launch_dep(k_project, dim3(grid), dim3(256), 0, s, params, stride, sp, views, out);
 }
 
 void launch_project_backward(float* params, int stride, int n_views, const StepParams* sp, const ViewDev* views,
@@ -837,18 +847,18 @@ void launch_project_backward(float* params, int stride, int n_views, const StepP
   if (n_rec > 0) {
     float* head = carry;
     float* tail = carry + 9 * ((m_cap + 31) / 32 + 1);
-    k_inst_reduce<<<(unsigned)(num_sms * 8), 256, 0, s>>>(inst_rec, ginst, pb.count, pb.offsets, n_rec, ctl, g2s,
-                                                         grad2d_out, head, tail);
-    k_inst_carry<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, n_rec, ctl, head, tail, g2s,
-                                                                 grad2d_out);
+    launch_dep(k_inst_reduce, dim3((unsigned)(num_sms * 8)), dim3(256), 0, s, inst_rec, ginst, pb.count, pb.offsets,
+        n_rec, ctl, g2s, grad2d_out, head, tail);
+    launch_dep(k_inst_carry, dim3((unsigned)((n_rec + 255) / 256)), dim3(256), 0, s, pb.count, pb.offsets, n_rec, ctl,
+        head, tail, g2s, grad2d_out);
   }
   const unsigned grid = (unsigned)((stride + 255) / 256);
   if (n_views <= 1)
-    k_project_backward<1><<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.clamp, g2s, ctl,
-                                               grads_out, m, v);
+    launch_dep(k_project_backward<1>, dim3(grid), dim3(256), 0, s, params, stride, sp, views, n_views, pb.count,
+        pb.clamp, g2s, ctl, grads_out, m, v);
   else
-    k_project_backward_views<<<grid, 256, 0, s>>>(params, stride, sp, views, n_views, pb.count, pb.clamp, g2s, ctl,
-                                                  grads_out, m, v);
+    launch_dep(k_project_backward_views, dim3(grid), dim3(256), 0, s, params, stride, sp, views, n_views, pb.count,
+        pb.clamp, g2s, ctl, grads_out, m, v);
 }
 
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,

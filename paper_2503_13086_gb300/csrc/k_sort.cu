@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
                                                        long long n_items, unsigned long long* __restrict__ state,
                                                        Control* __restrict__ ctl, unsigned long long m_cap,
                                                        Ledger* __restrict__ ledger, const float* __restrict__ depth) {
+  dep_wait();
+  dep_release();
   __shared__ unsigned s_tile;
   __shared__ unsigned s_warp[kScanThreads / 32];
   __shared__ unsigned long long s_excl;
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
 void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned long long* state, Control* ctl,
                  unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth) {
   const long long tiles = (n_items + kScanTile - 1) / kScanTile;
-  k_scan<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n_items, state, ctl, m_cap, ledger, depth);
+  launch_dep(k_scan, dim3((unsigned)tiles), dim3(kScanThreads), 0, s, in, out, n_items, state, ctl, m_cap, ledger,
+      depth);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -172,6 +175,8 @@ __global__ void __launch_bounds__(256) k_block_owner(const unsigned* __restrict_
                                                      const unsigned* __restrict__ offsets, long long n_items,
                                                      unsigned* __restrict__ block_owner,
                                                      const Control* __restrict__ ctl) {
+  dep_wait();
+  dep_release();
   const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (ctl->overflow || rec >= n_items) return;
   const unsigned cnt = count[rec];
@@ -186,6 +191,8 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
                                               unsigned* __restrict__ vals1, unsigned* __restrict__ inst_rec,
                                               const unsigned* __restrict__ block_owner, unsigned* __restrict__ hist,
                                               int tile_bits, const Control* __restrict__ ctl) {
+  dep_wait();
+  dep_release();
   __shared__ unsigned s_hist[kMaxSortPasses][kSortBins];
   for (int k = threadIdx.x; k < kMaxSortPasses * kSortBins; k += blockDim.x) (&s_hist[0][0])[k] = 0u;
   __syncthreads();
@@ -241,9 +248,10 @@ void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long l
                  unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* block_owner,
                  unsigned* hist, int tile_bits, int num_sms, const Control* ctl, cudaStream_t s) {
   if (n_items <= 0) return;
-  k_block_owner<<<(unsigned)((n_items + 255) / 256), 256, 0, s>>>(pb.count, pb.offsets, n_items, block_owner, ctl);
-  k_emit<<<(unsigned)(num_sms * 8), 256, 0, s>>>(pb, views, stride, n_items, keys0, vals0, keys1, vals1, inst_rec,
-                                                 block_owner, hist, tile_bits, ctl);
+  launch_dep(k_block_owner, dim3((unsigned)((n_items + 255) / 256)), dim3(256), 0, s, pb.count, pb.offsets, n_items,
+      block_owner, ctl);
+  launch_dep(k_emit, dim3((unsigned)(num_sms * 8)), dim3(256), 0, s, pb, views, stride, n_items, keys0, vals0, keys1,
+      vals1, inst_rec, block_owner, hist, tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -268,6 +276,8 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
                                                             const unsigned* __restrict__ hist,
                                                             unsigned* __restrict__ state, int pass, int tile_bits,
                                                             Control* __restrict__ ctl) {
+  dep_wait();
+  dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SortSmem& S = *reinterpret_cast<SortSmem*>(smem_raw);
   if (ctl->overflow) return;
@@ -406,8 +416,8 @@ void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long 
                       const unsigned* hist, unsigned* state, int pass, int tile_bits, long long m_cap, Control* ctl,
                       cudaStream_t s) {
   const long long tiles = (m_cap + kSortTile - 1) / kSortTile;
-  k_sort_pass<<<(unsigned)(tiles > 0 ? tiles : 1), kSortThreads, sizeof(SortSmem), s>>>(
-      keys0, vals0, keys1, vals1, hist, state, pass, tile_bits, ctl);
+  launch_dep(k_sort_pass, dim3((unsigned)(tiles > 0 ? tiles : 1)), dim3(kSortThreads), sizeof(SortSmem), s, keys0,
+      vals0, keys1, vals1, hist, state, pass, tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -416,6 +426,8 @@ void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_ranges(const unsigned long long* __restrict__ keys, uint2* __restrict__ ranges,
                                                 int tile_bits, const Control* __restrict__ ctl) {
+  dep_wait();
+  dep_release();
   if (ctl->overflow) return;
   const unsigned long long M = ctl->m_total;
   const int D = key_layout(ctl, tile_bits).D;
@@ -432,7 +444,7 @@ void launch_ranges(const unsigned long long* keys, uint2* ranges, int tile_bits,
   long long blocks = (m_cap + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_ranges<<<(unsigned)blocks, 256, 0, s>>>(keys, ranges, tile_bits, ctl);
+  launch_dep(k_ranges, dim3((unsigned)blocks), dim3(256), 0, s, keys, ranges, tile_bits, ctl);
 }
 
 }  // namespace gs
