@@ -12,6 +12,8 @@
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
 //          symmetric, so the adjoint of the blur is the blur) gives dL/dx.
 // The last CTA of pass 1 reduces the per-CTA sums in a fixed order: the loss is deterministic.
+#include <cmath>
+
 #include "gs_device.cuh"
 #include "gs_engine.h"
 
@@ -23,17 +25,12 @@ constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // 42 x 42 staged block
 constexpr int kSXP = 44;                               // padded row: 16-byte aligned float4 reads
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
-__device__ __forceinline__ void window(float w[11]) {
-  float s = 0.f;
-#pragma unroll
-  for (int k = 0; k < 11; ++k) {
-    const float d = (float)(k - kR);
-    w[k] = expf(-d * d / (2.f * 1.5f * 1.5f));
-    s += w[k];
-  }
-#pragma unroll
-  for (int k = 0; k < 11; ++k) w[k] /= s;
-}
+// The normalised window w[k] = exp(-d^2 / (2 1.5^2)) / sum, d = k - 5, set once by the host (in
+// double, rounded to float), held twice for the packed FP32x2 FMAs: c_w2[k] = (w[k], w[k]).
+__constant__ float2 c_w2[11];
+// (w[t], w[t - 1]) for t = 0..11 (0 outside the window): the weights of one input at two adjacent
+// outputs, for blurring a single map two outputs per packed FMA
+__constant__ float2 c_wp[12];
 
 __device__ __forceinline__ int view_of_block(const ViewDev* __restrict__ views, int n_views, long long b) {
   int v = 0;
@@ -54,44 +51,36 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Stage MAPS planes (W x H each) of the 42 x 42 block at (ox - 5, oy - 5) into dst[m] (rows of
-// kSXP floats); outside the image (and the pad columns) become 0.  Warp w takes rows w, w + 8,
-// ...; its lanes the columns.
+// kSXP floats); outside the image (and the pad columns) become 0.  A task is 4 consecutive
+// columns of one row (the rows of an image of any width are not 16-byte aligned, so the copies
+// are 4-byte ones; the row and bounds arithmetic is shared by the four).
 template <int MAPS>
 __device__ __forceinline__ void stage_block(float (*dst)[kSY][kSXP], const float* const (&src)[MAPS], int ox, int oy,
                                             int W, int H) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < kSY; r += 8) {
-    const int gy = oy + r - kR;
+  constexpr int kGroups = kSXP / 4;
+  for (int task = threadIdx.x; task < kSY * kGroups; task += blockDim.x) {
+    const int r = task / kGroups, c0 = (task - r * kGroups) * 4;
+    const int gy = oy + r - kR, gx0 = ox + c0 - kR;
     const bool row_ok = gy >= 0 && gy < H;
-    for (int c = lane; c < kSXP; c += 32) {
-      const int gx = ox + c - kR;
-      const bool ok = row_ok && c < kSX && gx >= 0 && gx < W;
-      const long long pix = ok ? (long long)gy * W + gx : 0;
+    const long long rowbase = row_ok ? (long long)gy * W : 0;
 #pragma unroll
-      for (int m = 0; m < MAPS; ++m) cp_async4(&dst[m][r][c], src[m] + pix, ok);
+    for (int i = 0; i < 4; ++i) {
+      const int gx = gx0 + i;
+      const bool ok = row_ok && c0 + i < kSX && gx >= 0 && gx < W;
+      const long long pix = ok ? rowbase + gx : 0;
+#pragma unroll
+      for (int m = 0; m < MAPS; ++m) cp_async4(&dst[m][r][c0 + i], src[m] + pix, ok);
     }
   }
   cp_async_commit();
 }
 
-// 16 consecutive values of a padded shared row starting at a multiple of 4
-__device__ __forceinline__ void load16(const float* row, int c0, float o[16]) {
-  const float4* r4 = reinterpret_cast<const float4*>(row + c0);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float4 v = r4[k];
-    o[4 * k] = v.x;
-    o[4 * k + 1] = v.y;
-    o[4 * k + 2] = v.z;
-    o[4 * k + 3] = v.w;
-  }
-}
 }  // namespace
 
 long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * ((H + kBY - 1) / kBY); }
 
-// Each thread blurs 4 adjacent outputs per pass (row segment, then column segment) from 14
-// staged values per map, so a staged value is read once per 4 outputs.
+// The row pass blurs 8 adjacent outputs per thread from 18 staged values per map, the column pass
+// 4 from 14, so a staged value is read once per 8 (4) outputs.
 struct LossFwdSmem {
   float in[2][2][kSY][kSXP];  // [buffer][x / y][row][col]
   float2 hxy[kSY][kBX + 1];   // row-blurred (E[x], E[y])
@@ -116,11 +105,6 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   __shared__ double s_red[2][8];
   __shared__ bool s_last;
   if (ctl->overflow) return;
-  float w[11];
-  window(w);
-  float2 w2[11];
-#pragma unroll
-  for (int t = 0; t < 11; ++t) w2[t] = make_float2(w[t], w[t]);
   const long long b = blockIdx.x;
   const int v = view_of_block(views, n_views, b);
   const ViewDev& V = views[v];
@@ -149,69 +133,91 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
     __syncthreads();
     float (*sx)[kSXP] = S.in[cur][0];
     float (*sy)[kSXP] = S.in[cur][1];
-    // horizontal: 42 rows x 8 segments of 4 columns; x and y (and x^2 and y^2) share the window
-    // weights, so they are blurred as pairs with the packed FP32x2 FMA of sm_100+
-    for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
-      const int r = task >> 3, c0 = (task & 7) * 4;
-      float xv[16], yv[16];
-      load16(sx[r], c0, xv);
-      load16(sy[r], c0, yv);
-      float2 axy[4], aq[4];
-      float ac[4];
+    // horizontal: 42 rows x 4 segments of 8 columns, one per thread.  x and y (and x^2 and y^2)
+    // share the window weights, so they are blurred as pairs with the packed FP32x2 FMA of sm_100+;
+    // xy is blurred two adjacent outputs per packed FMA.
+    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += blockDim.x) {
+      const int r = task >> 2, c0 = (task & 3) * 8;
+      const float* rx = sx[r] + c0;
+      const float* ry = sy[r] + c0;
+      float2 axy[8], aq[8], ac[4];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < 8; ++o) {
         axy[o] = make_float2(0.f, 0.f);
         aq[o] = make_float2(0.f, 0.f);
-        ac[o] = 0.f;
       }
 #pragma unroll
-      for (int j = 0; j < 14; ++j) {
-        const float2 v = make_float2(xv[j], yv[j]);
-        const float2 v2 = __fmul2_rn(v, v);
-        const float c = xv[j] * yv[j];
+      for (int k = 0; k < 4; ++k) ac[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int t = j - o;
-          if (t >= 0 && t < 11) {
-            axy[o] = __ffma2_rn(w2[t], v, axy[o]);
-            aq[o] = __ffma2_rn(w2[t], v2, aq[o]);
-            ac[o] = fmaf(w[t], c, ac[o]);
+      for (int j4 = 0; j4 < 20; j4 += 4) {  // inputs c0 .. c0 + 17 (+ 2 zero pad columns)
+        const float4 X4 = *reinterpret_cast<const float4*>(rx + j4);
+        const float4 Y4 = *reinterpret_cast<const float4*>(ry + j4);
+        const float xs[4] = {X4.x, X4.y, X4.z, X4.w}, ys[4] = {Y4.x, Y4.y, Y4.z, Y4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j4 + u;
+          if (j >= 18) break;
+          const float2 v = make_float2(xs[u], ys[u]);
+          const float2 v2 = __fmul2_rn(v, v);
+          const float c = xs[u] * ys[u];
+          const float2 cc = make_float2(c, c);
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) {
+              axy[o] = __ffma2_rn(c_w2[t], v, axy[o]);
+              aq[o] = __ffma2_rn(c_w2[t], v2, aq[o]);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int t = j - 2 * k;
+            if (t >= 0 && t <= 11) ac[k] = __ffma2_rn(c_wp[t], cc, ac[k]);
           }
         }
       }
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < 8; ++o) {
         S.hxy[r][c0 + o] = axy[o];
         S.hq[r][c0 + o] = aq[o];
-        S.hc[r][c0 + o] = ac[o];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        S.hc[r][c0 + 2 * k] = ac[k].x;
+        S.hc[r][c0 + 2 * k + 1] = ac[k].y;
       }
     }
     __syncthreads();
     // vertical: 32 columns x 8 segments of 4 rows
     {
       const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
-      float2 mxy[4], mq[4];
-      float mc[4];
+      float2 mxy[4], mq[4], mc2[2];
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         mxy[o] = make_float2(0.f, 0.f);
         mq[o] = make_float2(0.f, 0.f);
-        mc[o] = 0.f;
       }
+      mc2[0] = mc2[1] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < 14; ++j) {
         const float2 hxy = S.hxy[r0 + j][c], hq = S.hq[r0 + j][c];
         const float hc = S.hc[r0 + j][c];
+        const float2 hcc = make_float2(hc, hc);
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           const int t = j - o;
           if (t >= 0 && t < 11) {
-            mxy[o] = __ffma2_rn(w2[t], hxy, mxy[o]);
-            mq[o] = __ffma2_rn(w2[t], hq, mq[o]);
-            mc[o] = fmaf(w[t], hc, mc[o]);
+            mxy[o] = __ffma2_rn(c_w2[t], hxy, mxy[o]);
+            mq[o] = __ffma2_rn(c_w2[t], hq, mq[o]);
           }
         }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int t = j - 2 * k;
+          if (t >= 0 && t <= 11) mc2[k] = __ffma2_rn(c_wp[t], hcc, mc2[k]);
+        }
       }
+      const float mc[4] = {mc2[0].x, mc2[0].y, mc2[1].x, mc2[1].y};
       float l1c = 0.f, ssc = 0.f;  // at most 4 terms per thread and channel: float is exact enough
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
@@ -329,11 +335,6 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LossBwdSmem& S = *reinterpret_cast<LossBwdSmem*>(smem_raw);
   if (ctl->overflow) return;
-  float w[11];
-  window(w);
-  float2 w2[11];
-#pragma unroll
-  for (int t = 0; t < 11; ++t) w2[t] = make_float2(w[t], w[t]);
   const long long b = blockIdx.x;
   const int v = view_of_block(views, n_views, b);
   const ViewDev& V = views[v];
@@ -374,60 +375,73 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
       xo[o] = in ? X[ch * HW + pix] : 0.f;
       yo[o] = in ? Yt[ch * HW + pix] : 0.f;
     }
-    for (int task = threadIdx.x; task < kSY * (kBX / 4); task += blockDim.x) {
-      const int r = task >> 3, c0 = (task & 7) * 4;
-      float av[16], bv[16], cv[16];
-      load16(S.in[cur][0][r], c0, av);
-      load16(S.in[cur][1][r], c0, bv);
-      load16(S.in[cur][2][r], c0, cv);
-      float2 aab[4];
-      float ac[4];
+    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += blockDim.x) {
+      const int r = task >> 2, c0 = (task & 3) * 8;
+      const float* ra = S.in[cur][0][r] + c0;
+      const float* rb = S.in[cur][1][r] + c0;
+      const float* rc = S.in[cur][2][r] + c0;
+      float2 aab[8], ac[4];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        aab[o] = make_float2(0.f, 0.f);
-        ac[o] = 0.f;
-      }
+      for (int o = 0; o < 8; ++o) aab[o] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 14; ++j) {
-        const float2 v = make_float2(av[j], bv[j]);
+      for (int k = 0; k < 4; ++k) ac[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int t = j - o;
-          if (t >= 0 && t < 11) {
-            aab[o] = __ffma2_rn(w2[t], v, aab[o]);
-            ac[o] = fmaf(w[t], cv[j], ac[o]);
+      for (int j4 = 0; j4 < 20; j4 += 4) {
+        const float4 A4 = *reinterpret_cast<const float4*>(ra + j4);
+        const float4 B4 = *reinterpret_cast<const float4*>(rb + j4);
+        const float4 C4 = *reinterpret_cast<const float4*>(rc + j4);
+        const float as[4] = {A4.x, A4.y, A4.z, A4.w}, bs[4] = {B4.x, B4.y, B4.z, B4.w};
+        const float cs[4] = {C4.x, C4.y, C4.z, C4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j4 + u;
+          if (j >= 18) break;
+          const float2 v = make_float2(as[u], bs[u]);
+          const float2 cc = make_float2(cs[u], cs[u]);
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int t = j - o;
+            if (t >= 0 && t < 11) aab[o] = __ffma2_rn(c_w2[t], v, aab[o]);
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int t = j - 2 * k;
+            if (t >= 0 && t <= 11) ac[k] = __ffma2_rn(c_wp[t], cc, ac[k]);
           }
         }
       }
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        S.hab[r][c0 + o] = aab[o];
-        S.hc[r][c0 + o] = ac[o];
+      for (int o = 0; o < 8; ++o) S.hab[r][c0 + o] = aab[o];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        S.hc[r][c0 + 2 * k] = ac[k].x;
+        S.hc[r][c0 + 2 * k + 1] = ac[k].y;
       }
     }
     __syncthreads();
     {
       const int c = vc, r0 = vr0;
-      float2 bab[4];
-      float bc[4];
+      float2 bab[4], bc2[2];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        bab[o] = make_float2(0.f, 0.f);
-        bc[o] = 0.f;
-      }
+      for (int o = 0; o < 4; ++o) bab[o] = make_float2(0.f, 0.f);
+      bc2[0] = bc2[1] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < 14; ++j) {
         const float2 h = S.hab[r0 + j][c];
         const float hc = S.hc[r0 + j][c];
+        const float2 hcc = make_float2(hc, hc);
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           const int t = j - o;
-          if (t >= 0 && t < 11) {
-            bab[o] = __ffma2_rn(w2[t], h, bab[o]);
-            bc[o] = fmaf(w[t], hc, bc[o]);
-          }
+          if (t >= 0 && t < 11) bab[o] = __ffma2_rn(c_w2[t], h, bab[o]);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int t = j - 2 * k;
+          if (t >= 0 && t <= 11) bc2[k] = __ffma2_rn(c_wp[t], hcc, bc2[k]);
         }
       }
+      const float bc[4] = {bc2[0].x, bc2[0].y, bc2[1].x, bc2[1].y};
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
         const int gy = oy + r0 + o, gx = ox + c;
@@ -444,6 +458,22 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
 }
 
 void init_loss_attributes() {
+  float w[11];
+  float2 w2[11];
+  double sum = 0.0, e[11];
+  for (int k = 0; k < 11; ++k) {
+    const double d = (double)(k - kR);
+    e[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
+    sum += e[k];
+  }
+  for (int k = 0; k < 11; ++k) {
+    w[k] = (float)(e[k] / sum);
+    w2[k] = make_float2(w[k], w[k]);
+  }
+  float2 wp[12];
+  for (int t = 0; t < 12; ++t) wp[t] = make_float2(t <= 10 ? w[t] : 0.f, t >= 1 ? w[t - 1] : 0.f);
+  cudaMemcpyToSymbol(c_w2, w2, sizeof(w2));
+  cudaMemcpyToSymbol(c_wp, wp, sizeof(wp));
   cudaFuncSetAttribute(k_loss_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossFwdSmem));
   cudaFuncSetAttribute(k_loss_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossBwdSmem));
 }
