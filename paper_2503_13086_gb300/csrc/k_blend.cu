@@ -19,13 +19,15 @@
 // K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
 // (tile, 32-entry chunk), one warp each, taken from a global counter.  The warp compacts the
-// tile's pixels whose mask for this chunk is non-empty and takes them 32 at a time.  First each
-// lane restarts its pixel from the checkpoint.  The lanes then walk the union of their pixels'
-// blended Gaussians in list order, three Gaussians at a time: a lane computes its pixel's nine
-// gradient terms for each (zero where it did not blend it) and advances its transmittance and
-// front colour exactly as the forward did (the colour behind a Gaussian is the rendered colour
-// minus the colour accumulated in front of it); the 27 terms are summed over the 32 pixels through
-// shared memory in a fixed order and added to the Gaussians' running sums.  A round's pixels share
+// tile's pixels whose mask for this chunk is non-empty and takes them 64 at a time, two per lane
+// held as the halves of packed FP32x2 values (sm_100's FFMA2 / FMUL2 / FADD2 work on both at
+// once).  First each lane restarts its pixels from the checkpoint.  The lanes then walk the union
+// of their pixels' blended Gaussians in list order, three Gaussians at a time: a lane computes its
+// pixels' nine gradient terms for each (a pixel that did not blend it takes G = 0, which leaves
+// its state unchanged and its terms zero) and advances transmittance and front colour exactly as
+// the forward did (the colour behind a Gaussian is the rendered colour minus the colour
+// accumulated in front of it); it adds its two pixels' terms, and the 27 terms are summed over the
+// lanes through shared memory in a fixed order and added to the Gaussians' running sums.  A round's pixels share
 // few Gaussians (about 9 of 32), each blended by many of them, so this keeps more lanes busy than
 // one lane per Gaussian.  No atomics: the gradient is deterministic, and each instance's gradient
 // is written once, to its own slot.
@@ -442,87 +444,131 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const long long HW = (long long)V.W * V.H;
     const float* img = image + 3 * V.pix_base;
     const float* dimg = dimage + 3 * V.pix_base;
-    for (int r0 = 0; r0 < n_act; r0 += 32) {
-      const int i = r0 + lane;
-      const uint2 pm = i < n_act ? S.act[i] : make_uint2(0u, 0u);
-      const unsigned mask = pm.y;
-      // this lane's pixel: dL/dC, the rendered colour, and the state at the chunk start
-      float d0 = 0.f, d1 = 0.f, d2 = 0.f, P0 = 0.f, P1 = 0.f, P2 = 0.f;
-      float T = 1.f, F0 = 0.f, F1 = 0.f, F2 = 0.f, pxf = 0.f, pyf = 0.f;
-      if (mask) {
-        int ox, oy;
-        Sh::slot_xy((int)pm.x, ox, oy);
-        const int px = tx * TW + ox, py = ty * TH + oy;
-        const long long pix = (long long)py * V.W + px;
-        d0 = dimg[pix];
-        d1 = dimg[HW + pix];
-        d2 = dimg[2 * HW + pix];
-        P0 = img[pix];
-        P1 = img[HW + pix];
-        P2 = img[2 * HW + pix];
-        if (k > 0) {
-          const float4 ck = ckpt[cid * kPix + pm.x];
-          T = ck.x;
-          F0 = ck.y;
-          F1 = ck.z;
-          F2 = ck.w;
-        }
-        pxf = (float)px;
-        pyf = (float)py;
-      }
-      // The round's pixels walk the union of their Gaussians in list order, three at a time:
-      // each lane computes its pair's nine gradient terms (zero if it did not blend that
-      // Gaussian) and advances its own transmittance exactly as the forward did; the 27 terms of
-      // a group are then summed over the 32 pixels through shared memory (fixed order).
-      unsigned uni = __reduce_or_sync(0xffffffffu, mask);
-      while (uni) {
-        float g[kGroup * 9];
+    for (int r0 = 0; r0 < n_act; r0 += 64) {
+      // this lane's two pixels (act[r0 + lane], act[r0 + 32 + lane]), packed as (.x, .y): dL/dC, the
+      // rendered colour, the state at the chunk start, minus the pixel coordinates
+      const uint2 pa = r0 + lane < n_act ? S.act[r0 + lane] : make_uint2(0u, 0u);
+      const uint2 pb2 = r0 + 32 + lane < n_act ? S.act[r0 + 32 + lane] : make_uint2(0u, 0u);
+      const unsigned ma = pa.y, mb = pb2.y;
+      float2 d0, d1, d2, P0, P1, P2, T, F0, F1, F2, npx, npy;
+      {
+        float st[2][12];
 #pragma unroll
-        for (int j = 0; j < kGroup * 9; ++j) g[j] = 0.f;
+        for (int h = 0; h < 2; ++h) {
+          const uint2 pm = h ? pb2 : pa;
+          float* q = st[h];
+          q[0] = q[1] = q[2] = q[3] = q[4] = q[5] = 0.f;
+          q[6] = 1.f;
+          q[7] = q[8] = q[9] = q[10] = q[11] = 0.f;
+          if (pm.y) {
+            int ox, oy;
+            Sh::slot_xy((int)pm.x, ox, oy);
+            const int px = tx * TW + ox, py = ty * TH + oy;
+            const long long pix = (long long)py * V.W + px;
+            q[0] = dimg[pix];
+            q[1] = dimg[HW + pix];
+            q[2] = dimg[2 * HW + pix];
+            q[3] = img[pix];
+            q[4] = img[HW + pix];
+            q[5] = img[2 * HW + pix];
+            if (k > 0) {
+              const float4 ck = ckpt[cid * kPix + pm.x];
+              q[6] = ck.x;
+              q[7] = ck.y;
+              q[8] = ck.z;
+              q[9] = ck.w;
+            }
+            q[10] = -(float)px;
+            q[11] = -(float)py;
+          }
+        }
+        d0 = make_float2(st[0][0], st[1][0]);
+        d1 = make_float2(st[0][1], st[1][1]);
+        d2 = make_float2(st[0][2], st[1][2]);
+        P0 = make_float2(st[0][3], st[1][3]);
+        P1 = make_float2(st[0][4], st[1][4]);
+        P2 = make_float2(st[0][5], st[1][5]);
+        T = make_float2(st[0][6], st[1][6]);
+        F0 = make_float2(st[0][7], st[1][7]);
+        F1 = make_float2(st[0][8], st[1][8]);
+        F2 = make_float2(st[0][9], st[1][9]);
+        npx = make_float2(st[0][10], st[1][10]);
+        npy = make_float2(st[0][11], st[1][11]);
+      }
+      const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
+      // The round's pixels walk the union of their Gaussians in list order, three at a time.  A
+      // pixel that did not blend a Gaussian takes it with G = 0: alpha = 0 leaves its
+      // transmittance and front colour exactly as they were and zeroes its nine terms, so the walk
+      // has no per-pixel branch.  Each lane adds its two pixels' terms; the 27 terms of a group are
+      // then summed over the lanes through shared memory (fixed order).
+      unsigned uni = __reduce_or_sync(0xffffffffu, ma | mb);
+      while (uni) {
         int qs[kGroup];
         int ng = 0;
 #pragma unroll
         for (int gi = 0; gi < kGroup; ++gi) {
           qs[gi] = 0;
-          if (!uni) break;
-          const int q = __ffs(uni) - 1;
-          uni &= uni - 1u;
-          qs[gi] = q;
-          ng = gi + 1;
-          if ((mask >> q) & 1u) {
-            const float4 xy = S.a[q], co = S.b[q], c = S.c[q];
-            const float dx = __fsub_rn(xy.x, pxf), dy = __fsub_rn(xy.y, pyf);
-            const float G = splat_exp(splat_power(co.x, co.y, co.z, dx, dy));
-            const float oG = __fmul_rn(c.w, G);
-            const float alpha = fminf(kAlphaMax, oG);
-            const float w = __fmul_rn(alpha, T);
-            const float n0 = __fmaf_rn(c.x, w, F0);
-            const float n1 = __fmaf_rn(c.y, w, F1);
-            const float n2 = __fmaf_rn(c.z, w, F2);
-            // colour behind = rendered colour (incl. background) - colour in front incl. this one
-            const float DS = d0 * (P0 - n0) + d1 * (P1 - n1) + d2 * (P2 - n2);
-            // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha))
-            const float dalpha = T * (c.x * d0 + c.y * d1 + c.z * d2) - DS * __fdividef(1.f, 1.f - alpha);
-            g[9 * gi + 6] = w * d0;
-            g[9 * gi + 7] = w * d1;
-            g[9 * gi + 8] = w * d2;
-            if (!(oG > kAlphaMax)) {
-              g[9 * gi + 5] = dalpha * G;
-              const float dpow = dalpha * alpha;
-              g[9 * gi + 0] = dpow * (2.f * co.x * dx + co.y * dy);
-              g[9 * gi + 1] = dpow * (co.y * dx + 2.f * co.z * dy);
-              g[9 * gi + 2] = dpow * (-0.5f * dx * dx);
-              g[9 * gi + 3] = dpow * (-dx * dy);
-              g[9 * gi + 4] = dpow * (-0.5f * dy * dy);
-            }
-            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            F0 = n0;
-            F1 = n1;
-            F2 = n2;
-          }
-        }
+          float g[9];
 #pragma unroll
-        for (int j = 0; j < kGroup * 9; ++j) S.red[lane][j] = g[j];
+          for (int j = 0; j < 9; ++j) g[j] = 0.f;
+          if (uni) {
+            const int q = __ffs(uni) - 1;
+            uni &= uni - 1u;
+            qs[gi] = q;
+            ng = gi + 1;
+            const bool ba = (ma >> q) & 1u, bb = (mb >> q) & 1u;
+            if (ba || bb) {
+              const float4 xy = S.a[q], co = S.b[q], c = S.c[q];
+              const float2 dx = __fadd2_rn(make_float2(xy.x, xy.x), npx);
+              const float2 dy = __fadd2_rn(make_float2(xy.y, xy.y), npy);
+              const float2 A2 = make_float2(co.x, co.x), B2 = make_float2(co.y, co.y), C2 = make_float2(co.z, co.z);
+              // the forward's exponent, rounding step for rounding step (splat_power)
+              const float2 pw =
+                  __ffma2_rn(dx, __ffma2_rn(A2, dx, __fmul2_rn(B2, dy)), __fmul2_rn(__fmul2_rn(C2, dy), dy));
+              const float2 G = make_float2(ba ? splat_exp(pw.x) : 0.f, bb ? splat_exp(pw.y) : 0.f);
+              const float2 oG = __fmul2_rn(make_float2(c.w, c.w), G);
+              const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
+              const float2 w = __fmul2_rn(alpha, T);
+              const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z);
+              const float2 n0 = __ffma2_rn(cx, w, F0);
+              const float2 n1 = __ffma2_rn(cy, w, F1);
+              const float2 n2 = __ffma2_rn(cz, w, F2);
+              // colour behind = rendered colour (incl. background) - colour in front incl. this one
+              const float2 behind2 = __fmul2_rn(d2, __ffma2_rn(n2, neg2, P2));
+              const float2 DS = __ffma2_rn(d0, __ffma2_rn(n0, neg2, P0), __ffma2_rn(d1, __ffma2_rn(n1, neg2, P1), behind2));
+              // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha)); no gradient to the
+              // opacity and footprint where alpha was clamped
+              const float2 cd = __ffma2_rn(cx, d0, __ffma2_rn(cy, d1, __fmul2_rn(cz, d2)));
+              const float2 ninv = make_float2(-__fdividef(1.f, 1.f - alpha.x), -__fdividef(1.f, 1.f - alpha.y));
+              float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T, cd));
+              dal.x = oG.x > kAlphaMax ? 0.f : dal.x;
+              dal.y = oG.y > kAlphaMax ? 0.f : dal.y;
+              const float2 w0 = __fmul2_rn(w, d0), w1 = __fmul2_rn(w, d1), w2 = __fmul2_rn(w, d2);
+              const float2 g5 = __fmul2_rn(dal, G);
+              const float2 dpow = __fmul2_rn(dal, alpha);
+              const float2 ex = __ffma2_rn(make_float2(2.f * co.x, 2.f * co.x), dx, __fmul2_rn(B2, dy));
+              const float2 ey = __ffma2_rn(B2, dx, __fmul2_rn(make_float2(2.f * co.z, 2.f * co.z), dy));
+              const float2 pdx = __fmul2_rn(dpow, dx), pdy = __fmul2_rn(dpow, dy);
+              const float2 g0 = __fmul2_rn(dpow, ex), g1 = __fmul2_rn(dpow, ey);
+              const float2 g2 = __fmul2_rn(pdx, dx), g3 = __fmul2_rn(pdx, dy), g4 = __fmul2_rn(pdy, dy);
+              g[0] = g0.x + g0.y;
+              g[1] = g1.x + g1.y;
+              g[2] = -0.5f * (g2.x + g2.y);
+              g[3] = -(g3.x + g3.y);
+              g[4] = -0.5f * (g4.x + g4.y);
+              g[5] = g5.x + g5.y;
+              g[6] = w0.x + w0.y;
+              g[7] = w1.x + w1.y;
+              g[8] = w2.x + w2.y;
+              T = __fmul2_rn(T, __ffma2_rn(alpha, neg2, one2));
+              F0 = n0;
+              F1 = n1;
+              F2 = n2;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 9; ++j) S.red[lane][9 * gi + j] = g[j];
+        }
         __syncwarp();
         if (lane < 9 * ng) {
           float sum = 0.f;
