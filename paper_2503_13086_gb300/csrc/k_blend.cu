@@ -19,14 +19,14 @@
 // K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
 // (tile, 32-entry chunk), one warp each, taken from a global counter.  The warp compacts the
-// tile's pixels whose mask for this chunk is non-empty and takes them 64 at a time, two per lane
-// held as the halves of packed FP32x2 values (sm_100's FFMA2 / FMUL2 / FADD2 work on both at
-// once).  First each lane restarts its pixels from the checkpoint.  The lanes then walk the union
+// tile's pixels whose mask for this chunk is non-empty and takes them 128 at a time, four per
+// lane held as the halves of two packed FP32x2 values (sm_100's FFMA2 / FMUL2 / FADD2 work on both
+// halves at once).  First each lane restarts its pixels from the checkpoint.  The lanes then walk the union
 // of their pixels' blended Gaussians in list order, three Gaussians at a time: a lane computes its
 // pixels' nine gradient terms for each (a pixel that did not blend it takes G = 0, which leaves
 // its state unchanged and its terms zero) and advances transmittance and front colour exactly as
 // the forward did (the colour behind a Gaussian is the rendered colour minus the colour
-// accumulated in front of it); it adds its two pixels' terms, and the 27 terms are summed over the
+// accumulated in front of it); it adds its pixels' terms, and the 27 terms are summed over the
 // lanes through shared memory in a fixed order and added to the Gaussians' running sums.  A round's pixels share
 // few Gaussians (about 9 of 32), each blended by many of them, so this keeps more lanes busy than
 // one lane per Gaussian.  No atomics: the gradient is deterministic, and each instance's gradient
@@ -368,6 +368,7 @@ void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, l
 // ---------------------------------------------------------------------------------------------
 constexpr int kBwdWarps = 4;
 constexpr int kGroup = 3;  // Gaussians whose gradient terms are summed together (3 x 9 <= 32 lanes)
+constexpr int kBwdPairs = 2;  // packed pixel pairs per lane (4 pixels, 128 per round)
 
 template <int PIX>
 struct BwdWarp {
@@ -444,18 +445,23 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const long long HW = (long long)V.W * V.H;
     const float* img = image + 3 * V.pix_base;
     const float* dimg = dimage + 3 * V.pix_base;
-    for (int r0 = 0; r0 < n_act; r0 += 64) {
-      // this lane's two pixels (act[r0 + lane], act[r0 + 32 + lane]), packed as (.x, .y): dL/dC, the
-      // rendered colour, the state at the chunk start, minus the pixel coordinates
-      const uint2 pa = r0 + lane < n_act ? S.act[r0 + lane] : make_uint2(0u, 0u);
-      const uint2 pb2 = r0 + 32 + lane < n_act ? S.act[r0 + 32 + lane] : make_uint2(0u, 0u);
-      const unsigned ma = pa.y, mb = pb2.y;
-      float2 d0, d1, d2, P0, P1, P2, T, F0, F1, F2, npx, npy;
-      {
+    for (int r0 = 0; r0 < n_act; r0 += 64 * kBwdPairs) {
+      // this lane's pixels act[r0 + 32 h + lane], h = 0 .. 2 kBwdPairs - 1, pair p holding pixels
+      // 2p (.x) and 2p + 1 (.y): dL/dC, the rendered colour, the state at the chunk start, minus
+      // the pixel coordinates
+      unsigned mk[2 * kBwdPairs];
+      float2 d0[kBwdPairs], d1[kBwdPairs], d2[kBwdPairs], P0[kBwdPairs], P1[kBwdPairs], P2[kBwdPairs];
+      float2 T[kBwdPairs], F0[kBwdPairs], F1[kBwdPairs], F2[kBwdPairs], npx[kBwdPairs], npy[kBwdPairs];
+      unsigned any = 0u;
+#pragma unroll
+      for (int pp = 0; pp < kBwdPairs; ++pp) {
         float st[2][12];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint2 pm = h ? pb2 : pa;
+          const int i = r0 + 32 * (2 * pp + h) + lane;
+          const uint2 pm = i < n_act ? S.act[i] : make_uint2(0u, 0u);
+          mk[2 * pp + h] = pm.y;
+          any |= pm.y;
           float* q = st[h];
           q[0] = q[1] = q[2] = q[3] = q[4] = q[5] = 0.f;
           q[6] = 1.f;
@@ -482,26 +488,26 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
             q[11] = -(float)py;
           }
         }
-        d0 = make_float2(st[0][0], st[1][0]);
-        d1 = make_float2(st[0][1], st[1][1]);
-        d2 = make_float2(st[0][2], st[1][2]);
-        P0 = make_float2(st[0][3], st[1][3]);
-        P1 = make_float2(st[0][4], st[1][4]);
-        P2 = make_float2(st[0][5], st[1][5]);
-        T = make_float2(st[0][6], st[1][6]);
-        F0 = make_float2(st[0][7], st[1][7]);
-        F1 = make_float2(st[0][8], st[1][8]);
-        F2 = make_float2(st[0][9], st[1][9]);
-        npx = make_float2(st[0][10], st[1][10]);
-        npy = make_float2(st[0][11], st[1][11]);
+        d0[pp] = make_float2(st[0][0], st[1][0]);
+        d1[pp] = make_float2(st[0][1], st[1][1]);
+        d2[pp] = make_float2(st[0][2], st[1][2]);
+        P0[pp] = make_float2(st[0][3], st[1][3]);
+        P1[pp] = make_float2(st[0][4], st[1][4]);
+        P2[pp] = make_float2(st[0][5], st[1][5]);
+        T[pp] = make_float2(st[0][6], st[1][6]);
+        F0[pp] = make_float2(st[0][7], st[1][7]);
+        F1[pp] = make_float2(st[0][8], st[1][8]);
+        F2[pp] = make_float2(st[0][9], st[1][9]);
+        npx[pp] = make_float2(st[0][10], st[1][10]);
+        npy[pp] = make_float2(st[0][11], st[1][11]);
       }
       const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
       // The round's pixels walk the union of their Gaussians in list order, three at a time.  A
       // pixel that did not blend a Gaussian takes it with G = 0: alpha = 0 leaves its
       // transmittance and front colour exactly as they were and zeroes its nine terms, so the walk
-      // has no per-pixel branch.  Each lane adds its two pixels' terms; the 27 terms of a group are
+      // has no per-pixel branch.  Each lane adds its pixels' terms; the 27 terms of a group are
       // then summed over the lanes through shared memory (fixed order).
-      unsigned uni = __reduce_or_sync(0xffffffffu, ma | mb);
+      unsigned uni = __reduce_or_sync(0xffffffffu, any);
       while (uni) {
         int qs[kGroup];
         int ng = 0;
@@ -516,54 +522,58 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
             uni &= uni - 1u;
             qs[gi] = q;
             ng = gi + 1;
-            const bool ba = (ma >> q) & 1u, bb = (mb >> q) & 1u;
-            if (ba || bb) {
-              const float4 xy = S.a[q], co = S.b[q], c = S.c[q];
-              const float2 dx = __fadd2_rn(make_float2(xy.x, xy.x), npx);
-              const float2 dy = __fadd2_rn(make_float2(xy.y, xy.y), npy);
-              const float2 A2 = make_float2(co.x, co.x), B2 = make_float2(co.y, co.y), C2 = make_float2(co.z, co.z);
+            const float4 xy = S.a[q], co = S.b[q], c = S.c[q];
+            const float2 A2 = make_float2(co.x, co.x), B2 = make_float2(co.y, co.y), C2 = make_float2(co.z, co.z);
+            const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z);
+            const float2 A2x2 = make_float2(2.f * co.x, 2.f * co.x), C2x2 = make_float2(2.f * co.z, 2.f * co.z);
+#pragma unroll
+            for (int pp = 0; pp < kBwdPairs; ++pp) {
+              const bool ba = (mk[2 * pp] >> q) & 1u, bb = (mk[2 * pp + 1] >> q) & 1u;
+              if (!(ba || bb)) continue;
+              const float2 dx = __fadd2_rn(make_float2(xy.x, xy.x), npx[pp]);
+              const float2 dy = __fadd2_rn(make_float2(xy.y, xy.y), npy[pp]);
               // the forward's exponent, rounding step for rounding step (splat_power)
               const float2 pw =
                   __ffma2_rn(dx, __ffma2_rn(A2, dx, __fmul2_rn(B2, dy)), __fmul2_rn(__fmul2_rn(C2, dy), dy));
               const float2 G = make_float2(ba ? splat_exp(pw.x) : 0.f, bb ? splat_exp(pw.y) : 0.f);
               const float2 oG = __fmul2_rn(make_float2(c.w, c.w), G);
               const float2 alpha = make_float2(fminf(kAlphaMax, oG.x), fminf(kAlphaMax, oG.y));
-              const float2 w = __fmul2_rn(alpha, T);
-              const float2 cx = make_float2(c.x, c.x), cy = make_float2(c.y, c.y), cz = make_float2(c.z, c.z);
-              const float2 n0 = __ffma2_rn(cx, w, F0);
-              const float2 n1 = __ffma2_rn(cy, w, F1);
-              const float2 n2 = __ffma2_rn(cz, w, F2);
+              const float2 w = __fmul2_rn(alpha, T[pp]);
+              const float2 n0 = __ffma2_rn(cx, w, F0[pp]);
+              const float2 n1 = __ffma2_rn(cy, w, F1[pp]);
+              const float2 n2 = __ffma2_rn(cz, w, F2[pp]);
               // colour behind = rendered colour (incl. background) - colour in front incl. this one
-              const float2 behind2 = __fmul2_rn(d2, __ffma2_rn(n2, neg2, P2));
-              const float2 DS = __ffma2_rn(d0, __ffma2_rn(n0, neg2, P0), __ffma2_rn(d1, __ffma2_rn(n1, neg2, P1), behind2));
+              const float2 behind2 = __fmul2_rn(d2[pp], __ffma2_rn(n2, neg2, P2[pp]));
+              const float2 DS = __ffma2_rn(d0[pp], __ffma2_rn(n0, neg2, P0[pp]),
+                                           __ffma2_rn(d1[pp], __ffma2_rn(n1, neg2, P1[pp]), behind2));
               // dL/dalpha = sum_ch dL/dC_ch (c_ch T - behind_ch / (1 - alpha)); no gradient to the
               // opacity and footprint where alpha was clamped
-              const float2 cd = __ffma2_rn(cx, d0, __ffma2_rn(cy, d1, __fmul2_rn(cz, d2)));
+              const float2 cd = __ffma2_rn(cx, d0[pp], __ffma2_rn(cy, d1[pp], __fmul2_rn(cz, d2[pp])));
               const float2 ninv = make_float2(-__fdividef(1.f, 1.f - alpha.x), -__fdividef(1.f, 1.f - alpha.y));
-              float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T, cd));
+              float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T[pp], cd));
               dal.x = oG.x > kAlphaMax ? 0.f : dal.x;
               dal.y = oG.y > kAlphaMax ? 0.f : dal.y;
-              const float2 w0 = __fmul2_rn(w, d0), w1 = __fmul2_rn(w, d1), w2 = __fmul2_rn(w, d2);
+              const float2 w0 = __fmul2_rn(w, d0[pp]), w1 = __fmul2_rn(w, d1[pp]), w2 = __fmul2_rn(w, d2[pp]);
               const float2 g5 = __fmul2_rn(dal, G);
               const float2 dpow = __fmul2_rn(dal, alpha);
-              const float2 ex = __ffma2_rn(make_float2(2.f * co.x, 2.f * co.x), dx, __fmul2_rn(B2, dy));
-              const float2 ey = __ffma2_rn(B2, dx, __fmul2_rn(make_float2(2.f * co.z, 2.f * co.z), dy));
+              const float2 ex = __ffma2_rn(A2x2, dx, __fmul2_rn(B2, dy));
+              const float2 ey = __ffma2_rn(B2, dx, __fmul2_rn(C2x2, dy));
               const float2 pdx = __fmul2_rn(dpow, dx), pdy = __fmul2_rn(dpow, dy);
               const float2 g0 = __fmul2_rn(dpow, ex), g1 = __fmul2_rn(dpow, ey);
               const float2 g2 = __fmul2_rn(pdx, dx), g3 = __fmul2_rn(pdx, dy), g4 = __fmul2_rn(pdy, dy);
-              g[0] = g0.x + g0.y;
-              g[1] = g1.x + g1.y;
-              g[2] = -0.5f * (g2.x + g2.y);
-              g[3] = -(g3.x + g3.y);
-              g[4] = -0.5f * (g4.x + g4.y);
-              g[5] = g5.x + g5.y;
-              g[6] = w0.x + w0.y;
-              g[7] = w1.x + w1.y;
-              g[8] = w2.x + w2.y;
-              T = __fmul2_rn(T, __ffma2_rn(alpha, neg2, one2));
-              F0 = n0;
-              F1 = n1;
-              F2 = n2;
+              g[0] += g0.x + g0.y;
+              g[1] += g1.x + g1.y;
+              g[2] -= 0.5f * (g2.x + g2.y);
+              g[3] -= g3.x + g3.y;
+              g[4] -= 0.5f * (g4.x + g4.y);
+              g[5] += g5.x + g5.y;
+              g[6] += w0.x + w0.y;
+              g[7] += w1.x + w1.y;
+              g[8] += w2.x + w2.y;
+              T[pp] = __fmul2_rn(T[pp], __ffma2_rn(alpha, neg2, one2));
+              F0[pp] = n0;
+              F1[pp] = n1;
+              F2[pp] = n2;
             }
           }
 #pragma unroll
