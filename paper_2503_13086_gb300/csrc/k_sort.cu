@@ -97,30 +97,38 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
     }
     if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
     const unsigned total = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
-    if (lane == 0) {
-      unsigned long long excl = 0;
-      if (tile == 0) {
-        st_release_u64(&state[0], kScanPrefix | (unsigned long long)total);
-      } else {
-        st_release_u64(&state[tile], kScanAgg | (unsigned long long)total);
-        long long j = (long long)tile - 1;
-        unsigned spins = 0;
-        while (j >= 0) {
-          const unsigned long long sv = ld_acquire_u64(&state[j]);
-          const unsigned long long flag = sv & ~kScanValMask;
-          if (flag == 0ull) {
-            if (++spins > kSpinLimit) {
-              atomicOr(&ctl->error, kErrTimeout);
-              break;
-            }
-            continue;
-          }
-          excl += sv & kScanValMask;
-          if (flag == kScanPrefix) break;
-          --j;
+    // decoupled look-back by the whole warp: lane l reads the status of tile j - l, so one round
+    // trip covers up to 32 predecessors
+    unsigned long long excl = 0;
+    if (tile == 0) {
+      if (lane == 0) st_relaxed_u64(&state[0], kScanPrefix | (unsigned long long)total);
+    } else {
+      if (lane == 0) st_relaxed_u64(&state[tile], kScanAgg | (unsigned long long)total);
+      long long j = (long long)tile - 1;
+      unsigned spins = 0;
+      for (;;) {
+        const long long idx = j - lane;
+        const unsigned long long sv = idx >= 0 ? ld_relaxed_u64(&state[idx]) : kScanPrefix;
+        const unsigned long long flag = sv & ~kScanValMask;
+        const unsigned notready = __ballot_sync(0xffffffffu, flag == 0ull);
+        const unsigned isprefix = __ballot_sync(0xffffffffu, flag == kScanPrefix);
+        const unsigned stop = notready | isprefix;
+        const int first = stop ? __ffs(stop) - 1 : 32;  // lanes below it hold aggregates
+        const bool take = lane < first || (lane == first && ((isprefix >> lane) & 1u));
+        unsigned long long v = take ? (sv & kScanValMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (first < 32 && ((isprefix >> first) & 1u)) break;
+        j -= first;
+        if (first < 32 && ++spins > kSpinLimit) {
+          if (lane == 0) atomicOr(&ctl->error, kErrTimeout);
+          break;
         }
-        st_release_u64(&state[tile], kScanPrefix | (excl + total));
       }
+      if (lane == 0) st_relaxed_u64(&state[tile], kScanPrefix | (excl + total));
+    }
+    if (lane == 0) {
       s_excl = excl;
       if ((long long)tile == num_tiles - 1) {
         const unsigned long long m = excl + total;
@@ -338,26 +346,40 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
     unsigned* st = state + (unsigned long long)tile * kSortBins + d;
     unsigned excl = 0;
     if (tile == 0) {
-      st_release_u32(st, kSortPrefix | total);
+      st_relaxed_u32(st, kSortPrefix | total);
     } else {
-      st_release_u32(st, kSortAgg | total);
+      st_relaxed_u32(st, kSortAgg | total);
+      // look-back over windows of kLookBack predecessors (their loads in flight together)
+      constexpr int kLookBack = 8;
       long long j = (long long)tile - 1;
       unsigned spins = 0;
-      while (j >= 0) {
-        const unsigned sv = ld_acquire_u32(state + (unsigned long long)j * kSortBins + d);
-        const unsigned flag = sv & ~kSortValMask;
-        if (flag == 0u) {
-          if (++spins > kSpinLimit) {
-            atomicOr(&ctl->error, kErrTimeout);
-            break;
+      bool done = false;
+      while (!done) {
+        unsigned sv[kLookBack];
+#pragma unroll
+        for (int w = 0; w < kLookBack; ++w)
+          sv[w] = j - w >= 0 ? ld_relaxed_u32(state + (unsigned long long)(j - w) * kSortBins + d) : kSortPrefix;
+        int used = 0;
+        bool wait = false;
+#pragma unroll
+        for (int w = 0; w < kLookBack; ++w) {
+          if (done || wait) continue;
+          const unsigned flag = sv[w] & ~kSortValMask;
+          if (flag == 0u) {
+            wait = true;
+            continue;
           }
-          continue;
+          excl += sv[w] & kSortValMask;
+          ++used;
+          if (flag == kSortPrefix) done = true;
         }
-        excl += sv & kSortValMask;
-        if (flag == kSortPrefix) break;
-        --j;
+        j -= used;
+        if (wait && ++spins > kSpinLimit) {
+          atomicOr(&ctl->error, kErrTimeout);
+          break;
+        }
       }
-      st_release_u32(st, kSortPrefix | (excl + total));
+      st_relaxed_u32(st, kSortPrefix | (excl + total));
     }
     // digit base = exclusive scan of the global histogram; CTA digit start = exclusive scan of
     // the CTA totals.  Both by a block-wide scan over the 256 digits.
