@@ -60,7 +60,7 @@ struct Raster {
   bool zeroB_pending = true;  // zeroB still to be cleared by the forward tail
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp, g2s;
   DevBuf keys0, keys1, vals0, vals1, ginst, ckpt, cmask, order, tile_chunks;
-  DevBuf inst_rec, block_owner, carry;  // instance -> record, owner of every 256th instance, K9a partials
+  DevBuf inst_rec, carry;  // instance -> record, K9a partials
   DevBuf partials, block_sums;
   DevBuf ledger_d;  // Ledger of the current run of steps
   DevBuf own_image, own_last, own_dimage;  // used by sessions

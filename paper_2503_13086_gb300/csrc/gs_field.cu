@@ -251,7 +251,7 @@ struct Field {
     const DevBuf* bufs[] = {&params, &adam_m, &adam_v, &dstat, &step_img, &step_dimg, &step_last, &step_T, &step_gp,
                             &R.sp_d, &R.views_d, &R.zeroA, &R.zeroB, &R.xyo, &R.conic, &R.rgb, &R.depth, &R.radius,
                             &R.rect, &R.count, &R.offsets, &R.clamp, &R.g2s, &R.keys0, &R.keys1, &R.vals0, &R.vals1, &R.ginst,
-                            &R.inst_rec, &R.block_owner, &R.carry,
+                            &R.inst_rec, &R.carry,
                             &R.ckpt, &R.cmask, &R.order, &R.tile_chunks, &R.partials, &R.block_sums};
     for (const DevBuf* b : bufs) v.push_back((unsigned long long)(uintptr_t)b->p);
     const unsigned long long lay[] = {(unsigned long long)stride, R.m_cap, (unsigned long long)(uintptr_t)R.dstat, (unsigned long long)R.passes,

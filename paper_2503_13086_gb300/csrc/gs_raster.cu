@@ -107,7 +107,7 @@ Raster::Raster() {
 
 Raster::~Raster() {
   DevBuf* all[] = {&sp_d, &views_d, &ledger_d, &zeroA, &zeroB, &xyo, &conic, &rgb, &depth, &radius, &rect, &count, &offsets,
-                   &clamp, &g2s, &keys0, &keys1, &vals0, &vals1, &ginst, &inst_rec, &block_owner, &carry, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
+                   &clamp, &g2s, &keys0, &keys1, &vals0, &vals1, &ginst, &inst_rec, &carry, &ckpt, &cmask, &order, &tile_chunks, &partials, &block_sums, &own_image,
                    &own_last, &own_dimage};
   for (DevBuf* b : all) b->release(&bytes_in_use);
   if (sp_h) cudaFreeHost(sp_h);
@@ -215,14 +215,13 @@ gs_status Raster::ensure_instances(unsigned long long m) {
     if (want > (1ull << 31)) return fail(GS_ERR_CAPACITY, "more than 2^31 Gaussian-tile instances");
     gs_status s;
     // free first so the peak does not hold old and new copies
-    DevBuf* bufs[] = {&keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &inst_rec, &block_owner, &carry};
+    DevBuf* bufs[] = {&keys0, &keys1, &vals0, &vals1, &ginst, &ckpt, &inst_rec, &carry};
     for (DevBuf* b : bufs) b->release(&bytes_in_use);
     const unsigned long long chunks = (want >> 5) + 1;
     m_cap = 0;  // until every buffer below exists (a failed reserve leaves them released)
     if ((s = keys0.reserve(want * 8, &bytes_in_use)) || (s = keys1.reserve(want * 8, &bytes_in_use)) ||
         (s = vals0.reserve(want * 4, &bytes_in_use)) || (s = vals1.reserve(want * 4, &bytes_in_use)) ||
         (s = ginst.reserve(want * 48, &bytes_in_use)) || (s = inst_rec.reserve(want * 4, &bytes_in_use)) ||
-        (s = block_owner.reserve(((want + 255) / 256 + 2) * 4, &bytes_in_use)) ||
         (s = carry.reserve(2 * 9 * 4 * ((want + 31) / 32 + 1), &bytes_in_use)))
       return s;
     (void)chunks;
@@ -312,7 +311,7 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
   unsigned* v0 = static_cast<unsigned*>(vals0.p);
   unsigned* v1 = static_cast<unsigned*>(vals1.p);
   launch_emit(proj(), vd(), stride, n_items, k0, v0, k1, v1, static_cast<unsigned*>(inst_rec.p),
-              static_cast<unsigned*>(block_owner.p), hist(), tile_bits, num_sms, ctl(), s);
+              hist(), tile_bits, num_sms, ctl(), s);
   mark(s, 3);
   const unsigned long long sort_tiles = (m_cap + kSortTile - 1) / kSortTile;
   for (int p = 0; p < passes; ++p)  // passes the step does not need return at once; the list ends in buffer 0

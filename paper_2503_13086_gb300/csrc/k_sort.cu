@@ -173,31 +173,42 @@ void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned 
 }
 
 // ---------------------------------------------------------------------------------------------
-// K3: duplication into (tile, depth) keys, one thread per instance.  The owner record of
-// instance e is the last record whose offset is <= e; block_owner[b] holds the owner of instance
-// 256 b, so each thread binary-searches only the records between two block owners.  Also
-// histograms every radix digit for the sort (the passes whose digit lies in the depth part of the
-// key once per record, through the thread of its first instance).
+// K3: duplication into (tile, depth) keys, one thread per instance.  First every record writes
+// its index over its instances' slots of inst_rec (a record with more than kFillAlone instances is
+// written by its whole warp, so one large Gaussian does not serialise a warp); then each instance reads
+// its owner from there (one coalesced load) and writes its key.  Also histograms every radix digit
+// for the sort (the passes whose digit lies in the depth part of the key once per record, through
+// the thread of its first instance).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_block_owner(const unsigned* __restrict__ count,
-                                                     const unsigned* __restrict__ offsets, long long n_items,
-                                                     unsigned* __restrict__ block_owner,
-                                                     const Control* __restrict__ ctl) {
+constexpr unsigned kFillAlone = 4;  // larger records are written by their whole warp
+__global__ void __launch_bounds__(256) k_fill_owner(const unsigned* __restrict__ count,
+                                                    const unsigned* __restrict__ offsets, long long n_items,
+                                                    unsigned* __restrict__ inst_rec, const Control* __restrict__ ctl) {
   dep_wait();
   dep_release();
+  if (ctl->overflow) return;
+  const int lane = threadIdx.x & 31;
   const long long rec = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (ctl->overflow || rec >= n_items) return;
-  const unsigned cnt = count[rec];
-  if (!cnt) return;
-  const unsigned long long off = offsets[rec], end = off + cnt;
-  for (unsigned long long b = (off + 255) >> 8; (b << 8) < end; ++b) block_owner[b] = (unsigned)rec;
+  const unsigned cnt = rec < n_items ? count[rec] : 0u;
+  const unsigned off = cnt ? offsets[rec] : 0u;
+  if (cnt <= kFillAlone) {
+    for (unsigned k = 0; k < cnt; ++k) inst_rec[(unsigned long long)off + k] = (unsigned)rec;
+  }
+  unsigned big = __ballot_sync(0xffffffffu, cnt > kFillAlone);
+  while (big) {
+    const int l = __ffs(big) - 1;
+    big &= big - 1u;
+    const unsigned r = __shfl_sync(0xffffffffu, (unsigned)rec, l);
+    const unsigned o = __shfl_sync(0xffffffffu, off, l);
+    const unsigned c = __shfl_sync(0xffffffffu, cnt, l);
+    for (unsigned k = lane; k < c; k += 32u) inst_rec[(unsigned long long)o + k] = r;
+  }
 }
 
 __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDev* __restrict__ views, int stride,
-                                              long long n_items, unsigned long long* __restrict__ keys0,
-                                              unsigned* __restrict__ vals0, unsigned long long* __restrict__ keys1,
-                                              unsigned* __restrict__ vals1, unsigned* __restrict__ inst_rec,
-                                              const unsigned* __restrict__ block_owner, unsigned* __restrict__ hist,
+                                              unsigned long long* __restrict__ keys0, unsigned* __restrict__ vals0,
+                                              unsigned long long* __restrict__ keys1, unsigned* __restrict__ vals1,
+                                              const unsigned* __restrict__ inst_rec, unsigned* __restrict__ hist,
                                               int tile_bits, const Control* __restrict__ ctl) {
   dep_wait();
   dep_release();
@@ -212,18 +223,9 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
   unsigned* __restrict__ vals = (passes & 1) ? vals1 : vals0;
   if (!ctl->overflow) {
     const unsigned long long M = ctl->m_total;
-    const unsigned long long nblk = (M + 255) >> 8;
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < M;
          e += (unsigned long long)gridDim.x * blockDim.x) {
-      const unsigned long long b = e >> 8;
-      unsigned lo = block_owner[b];
-      unsigned hi = b + 1 < nblk ? block_owner[b + 1] : (unsigned)(n_items - 1);
-      while (lo < hi) {
-        const unsigned mid = lo + ((hi - lo + 1) >> 1);
-        if (pb.offsets[mid] <= e) lo = mid;
-        else hi = mid - 1;
-      }
-      const unsigned rec = lo;
+      const unsigned rec = inst_rec[e];
       const unsigned k = (unsigned)(e - pb.offsets[rec]);
       const uint2 rc = pb.rect[rec];
       const unsigned db = __float_as_uint(pb.depth[rec]);
@@ -235,7 +237,6 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
       const unsigned long long key = (tile << kl.D) | (unsigned long long)(db - kl.dmin);
       keys[e] = key;
       vals[e] = rec;
-      inst_rec[e] = rec;
       for (int p = depth_passes; p < passes; ++p)
         atomicAdd(&s_hist[p][(key >> (p * kSortBits)) & (kSortBins - 1)], 1u);
       if (k == 0) {  // every instance of the record has the record's depth digits
@@ -253,13 +254,13 @@ __global__ void __launch_bounds__(256) k_emit(const ProjBuffers pb, const ViewDe
 }
 
 void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
-                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* block_owner,
-                 unsigned* hist, int tile_bits, int num_sms, const Control* ctl, cudaStream_t s) {
+                 unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* hist,
+                 int tile_bits, int num_sms, const Control* ctl, cudaStream_t s) {
   if (n_items <= 0) return;
-  launch_dep(k_block_owner, dim3((unsigned)((n_items + 255) / 256)), dim3(256), 0, s, pb.count, pb.offsets, n_items,
-      block_owner, ctl);
-  launch_dep(k_emit, dim3((unsigned)(num_sms * 8)), dim3(256), 0, s, pb, views, stride, n_items, keys0, vals0, keys1,
-      vals1, inst_rec, block_owner, hist, tile_bits, ctl);
+  launch_dep(k_fill_owner, dim3((unsigned)((n_items + 255) / 256)), dim3(256), 0, s, pb.count, pb.offsets, n_items,
+      inst_rec, ctl);
+  launch_dep(k_emit, dim3((unsigned)(num_sms * 8)), dim3(256), 0, s, pb, views, stride, keys0, vals0, keys1, vals1,
+      inst_rec, hist, tile_bits, ctl);
 }
 
 // ---------------------------------------------------------------------------------------------
