@@ -323,12 +323,16 @@ def run_gs(args):
 
     sampler = ClockSampler(local)
     sync_all()
-    field.set_timing(True)
     sampler.start()
     ms, acc = timed_loop(field, img, args.steps)
     launches = acc.pop("launches")
     sync_all()
     clocks = sampler.stop()
+    # per-kernel times from a second run of the same steps with an event around every kernel (the
+    # events sit between the kernels of the replayed graph, so that run is not the timed one)
+    field.set_timing(True)
+    timed_loop(field, img, args.steps)
+    sync_all()
     kms, ksteps = field.kernel_times()
     field.set_timing(False)
     tiling = field.stats()["last_tiling"]
