@@ -318,6 +318,10 @@ struct AdamArgs {
   float lr[6];
 };
 
+template <int N>
+__device__ __forceinline__ void apply_rows_mv(const AdamArgs& A, int c0, const int* grp, int i, const float* g,
+                                              const float* pcur, const float* m, const float* v);
+
 // Adam (or gradient write) for n consecutive component rows c0..c0+n-1 of Gaussian i, with
 // every load issued before the first store so the rows stream concurrently.
 template <int N>
@@ -336,6 +340,13 @@ __device__ __forceinline__ void apply_rows(const AdamArgs& A, int c0, const int*
     m[r] = A.m[k];
     v[r] = A.v[k];
   }
+  apply_rows_mv<N>(A, c0, grp, i, g, pcur, m, v);
+}
+
+// The update of apply_rows with the rows' moments already loaded (m, v).
+template <int N>
+__device__ __forceinline__ void apply_rows_mv(const AdamArgs& A, int c0, const int* grp, int i, const float* g,
+                                              const float* pcur, const float* m, const float* v) {
   const float ibc2s = 1.f / A.bc2s;
 #pragma unroll
   for (int r = 0; r < N; ++r) {
@@ -356,9 +367,15 @@ template <int K0, int MAXV>
 __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, unsigned vmask, float (&vdir)[MAXV][3],
                                          float (&vcol)[MAXV][3], float (&vdd)[MAXV][3]) {
   constexpr bool kSmall = MAXV <= 4;
-  float p[12];
+  // the group's parameter rows and (for Adam) their moments, all loads issued at once
+  float p[12], m[12], v[12];
 #pragma unroll
-  for (int r = 0; r < 12; ++r) p[r] = A.params[(long long)(11 + 3 * K0 + r) * A.stride + i];
+  for (int r = 0; r < 12; ++r) {
+    const long long k = (long long)(11 + 3 * K0 + r) * A.stride + i;
+    p[r] = A.params[k];
+    m[r] = A.adam == 1 ? A.m[k] : 0.f;
+    v[r] = A.adam == 1 ? A.v[k] : 0.f;
+  }
   float g[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) g[r] = 0.f;
@@ -390,7 +407,8 @@ __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, uns
   int grp[12];
 #pragma unroll
   for (int r = 0; r < 12; ++r) grp[r] = (K0 == 0 && r < 3) ? 4 : 5;
-  apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
+  if (A.adam == 1) apply_rows_mv<12>(A, 11 + 3 * K0, grp, i, g, p, m, v);
+  else apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
 }
 
 // K9a: per record (view, Gaussian), the sum of its instances' nine gradients (a reduce by key over
@@ -628,11 +646,12 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     if (kSmall && v >= n_views) break;
     const long long rec = (long long)v * stride + i;
     const unsigned cnt = count[rec];
-    if (cnt == 0u) continue;
-    const int slot = kSmall ? v : nvis;
+    // the record's sums are loaded with its count (read but unused for a record without instances)
     float g2[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) g2[k] = g2s[k * n_rec + rec];
+    if (cnt == 0u) continue;
+    const int slot = kSmall ? v : nvis;
     const ViewDev& V = views[v];
     Geo g;
     if (!geo_forward(V, mu, ls, q, g)) continue;
