@@ -136,20 +136,30 @@ def kernel_work(k, st, n, passes):
 def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
     per = [k / max(1, steps) for k in kernel_ms]
     dom = int(np.argmax(per))
-    t = per[dom] * 1e-3
-    bound, work = kernel_work(dom, st, n, passes)
-    if bound == "alu":
-        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-        ach = work / t / 1e12
-        unit, src = "Tops/s", f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived from unit counts and clock)"
-    else:
-        peak = peaks["hbm_gbs"]
-        ach = work / t / 1e9
-        unit, src = "GB/s", f"HBM copy, {peaks_kind}"
+
+    def frac_of(k):
+        t = per[k] * 1e-3
+        bound, work = kernel_work(k, st, n, passes)
+        if bound == "alu":
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+            unit, src = "Tops/s", f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived from unit counts and clock)"
+            ach = work / t / 1e12 if t > 0 else 0.0
+        else:
+            peak = peaks["hbm_gbs"]
+            unit, src = "GB/s", f"HBM copy, {peaks_kind}"
+            ach = work / t / 1e9 if t > 0 else 0.0
+        return bound, work, ach, peak, unit, src
+
+    bound, work, ach, peak, unit, src = frac_of(dom)
+    # every kernel against its own roofline (the same algorithmic-work definitions)
+    each = {}
+    for k, nm in enumerate(KERNELS):
+        b, _, a, pk, _, _ = frac_of(k)
+        each[nm] = {"bound": b, "frac": round(a / pk, 4)}
     return dict(kernel=KERNELS[dom], bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
                 traffic=traffic.get(KERNELS[dom]), peak_source=src, work_per_launch=work,
-                per_kernel_ms={nm: round(x, 4) for nm, x in zip(KERNELS, per)})
+                per_kernel_ms={nm: round(x, 4) for nm, x in zip(KERNELS, per)}, per_kernel_frac=each)
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed ncu
