@@ -4,7 +4,7 @@
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
 // views, the loss is the mean of the per-view losses.  The window is separable: each CTA stages
-// a 32 x 32 output block plus a 5-pixel halo in shared memory, blurs rows then columns.  The
+// a 32 x 48 output block plus a 5-pixel halo in shared memory, blurs rows then columns.  The
 // staging is asynchronous (cp.async, zero-filled outside the image) and double-buffered: the
 // next channel's block is in flight while the current one is blurred.
 //   pass 1 (k_loss_forward): the five window moments -> SSIM map, the three partial derivatives
@@ -20,8 +20,10 @@
 namespace gs {
 
 namespace {
-constexpr int kBX = 32, kBY = 32, kR = 5;
-constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // 42 x 42 staged block
+constexpr int kBX = 32, kBY = 48, kR = 5;
+constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // staged block with the halo
+constexpr int kVR = kBY / 8;  // column pass: 32 columns x 8 segments of kVR rows (256 threads)
+static_assert(kVR % 2 == 0, "column outputs are paired for the packed single-map blur");
 constexpr int kSXP = 44;                               // padded row: 16-byte aligned float4 reads
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
@@ -50,7 +52,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stage MAPS planes (W x H each) of the 42 x 42 block at (ox - 5, oy - 5) into dst[m] (rows of
+// Stage MAPS planes (W x H each) of the 42 x 58 block at (ox - 5, oy - 5) into dst[m] (rows of
 // kSXP floats); outside the image (and the pad columns) become 0.  A task is 4 consecutive
 // columns of one row (the rows of an image of any width are not 16-byte aligned, so the copies
 // are 4-byte ones; the row and bounds arithmetic is shared by the four).
@@ -188,23 +190,24 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
       }
     }
     __syncthreads();
-    // vertical: 32 columns x 8 segments of 4 rows
+    // vertical: 32 columns x 8 segments of kVR rows
     {
-      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * 4;
-      float2 mxy[4], mq[4], mc2[2];
+      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * kVR;
+      float2 mxy[kVR], mq[kVR], mc2[kVR / 2];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < kVR; ++o) {
         mxy[o] = make_float2(0.f, 0.f);
         mq[o] = make_float2(0.f, 0.f);
       }
-      mc2[0] = mc2[1] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 14; ++j) {
+      for (int k = 0; k < kVR / 2; ++k) mc2[k] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kVR + 10; ++j) {
         const float2 hxy = S.hxy[r0 + j][c], hq = S.hq[r0 + j][c];
         const float hc = S.hc[r0 + j][c];
         const float2 hcc = make_float2(hc, hc);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        for (int o = 0; o < kVR; ++o) {
           const int t = j - o;
           if (t >= 0 && t < 11) {
             mxy[o] = __ffma2_rn(c_w2[t], hxy, mxy[o]);
@@ -212,18 +215,18 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
           }
         }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kVR / 2; ++k) {
           const int t = j - 2 * k;
           if (t >= 0 && t <= 11) mc2[k] = __ffma2_rn(c_wp[t], hcc, mc2[k]);
         }
       }
-      const float mc[4] = {mc2[0].x, mc2[0].y, mc2[1].x, mc2[1].y};
-      float l1c = 0.f, ssc = 0.f;  // at most 4 terms per thread and channel: float is exact enough
+      float l1c = 0.f, ssc = 0.f;  // at most kVR terms per thread and channel: float is exact enough
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < kVR; ++o) {
         const int gy = oy + r0 + o, gx = ox + c;
         if (gx >= V.W || gy >= V.H) continue;
-        const float mx = mxy[o].x, my = mxy[o].y, exx = mq[o].x, eyy = mq[o].y, exy = mc[o];
+        const float mx = mxy[o].x, my = mxy[o].y, exx = mq[o].x, eyy = mq[o].y;
+        const float exy = (o & 1) ? mc2[o / 2].y : mc2[o / 2].x;
         const float N1 = 2.f * mx * my + kC1, N2 = 2.f * (exy - mx * my) + kC2;
         const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
         const float N = N1 * N2, D = D1 * D2;
@@ -365,10 +368,10 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
     }
     __syncthreads();
     // this thread's four output pixels: fetch the render and target now, used after the blur
-    const int vc = threadIdx.x % kBX, vr0 = (threadIdx.x / kBX) * 4;
-    float xo[4], yo[4];
+    const int vc = threadIdx.x % kBX, vr0 = (threadIdx.x / kBX) * kVR;
+    float xo[kVR], yo[kVR];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) {
+    for (int o = 0; o < kVR; ++o) {
       const int gy = oy + vr0 + o, gx = ox + vc;
       const bool in = gx < V.W && gy < V.H;
       const long long pix = in ? (long long)gy * V.W + gx : 0;
@@ -421,36 +424,37 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
     __syncthreads();
     {
       const int c = vc, r0 = vr0;
-      float2 bab[4], bc2[2];
+      float2 bab[kVR], bc2[kVR / 2];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) bab[o] = make_float2(0.f, 0.f);
-      bc2[0] = bc2[1] = make_float2(0.f, 0.f);
+      for (int o = 0; o < kVR; ++o) bab[o] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 14; ++j) {
+      for (int k = 0; k < kVR / 2; ++k) bc2[k] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kVR + 10; ++j) {
         const float2 h = S.hab[r0 + j][c];
         const float hc = S.hc[r0 + j][c];
         const float2 hcc = make_float2(hc, hc);
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        for (int o = 0; o < kVR; ++o) {
           const int t = j - o;
           if (t >= 0 && t < 11) bab[o] = __ffma2_rn(c_w2[t], h, bab[o]);
         }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kVR / 2; ++k) {
           const int t = j - 2 * k;
           if (t >= 0 && t <= 11) bc2[k] = __ffma2_rn(c_wp[t], hcc, bc2[k]);
         }
       }
-      const float bc[4] = {bc2[0].x, bc2[0].y, bc2[1].x, bc2[1].y};
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
+      for (int o = 0; o < kVR; ++o) {
         const int gy = oy + r0 + o, gx = ox + c;
         if (gx >= V.W || gy >= V.H) continue;
         const long long pix = (long long)gy * V.W + gx;
         const float xv = xo[o], yv = yo[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        dX[ch * HW + pix] = gl1 * sgn + gs * (bab[o].x + 2.f * xv * bab[o].y + yv * bc[o]);
+        const float bc = (o & 1) ? bc2[o / 2].y : bc2[o / 2].x;
+        dX[ch * HW + pix] = gl1 * sgn + gs * (bab[o].x + 2.f * xv * bab[o].y + yv * bc);
       }
     }
     __syncthreads();
