@@ -5,8 +5,9 @@
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
 // views, the loss is the mean of the per-view losses.  The window is separable: each CTA stages
 // a 32 x 48 output block plus a 5-pixel halo in shared memory, blurs rows then columns.  The
-// staging is asynchronous (cp.async, zero-filled outside the image) and double-buffered: the
-// next channel's block is in flight while the current one is blurred.
+// staging is asynchronous (cp.async, zero-filled outside the image) into one buffer, so that three
+// CTAs share an SM and overlap one another's staging (a second buffer with the next channel in
+// flight left room for two).
 //   pass 1 (k_loss_forward): the five window moments -> SSIM map, the three partial derivatives
 //          of SSIM with respect to (mu_x, E[x^2], E[xy]) per pixel, and per-CTA sums;
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
@@ -24,6 +25,7 @@ constexpr int kBX = 32, kBY = 48, kR = 5;
 constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // staged block with the halo
 constexpr int kVR = kBY / 8;  // column pass: 32 columns x 8 segments of kVR rows (256 threads)
 static_assert(kVR % 2 == 0, "column outputs are paired for the packed single-map blur");
+constexpr int kStageBufs = 1;  // staging buffers: 2 = the next channel in flight, 1 = more CTAs per SM
 constexpr int kSXP = 44;                               // padded row: 16-byte aligned float4 reads
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
@@ -84,18 +86,18 @@ long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * 
 // The row pass blurs 8 adjacent outputs per thread from 18 staged values per map, the column pass
 // 4 from 14, so a staged value is read once per 8 (4) outputs.
 struct LossFwdSmem {
-  float in[2][2][kSY][kSXP];  // [buffer][x / y][row][col]
+  float in[kStageBufs][2][kSY][kSXP];  // [buffer][x / y][row][col]
   float2 hxy[kSY][kBX + 1];   // row-blurred (E[x], E[y])
   float2 hq[kSY][kBX + 1];    // row-blurred (E[x^2], E[y^2])
   float hc[kSY][kBX + 1];     // row-blurred E[xy]
 };
 struct LossBwdSmem {
-  float in[2][3][kSY][kSXP];  // [buffer][partial][row][col]
+  float in[kStageBufs][3][kSY][kSXP];  // [buffer][partial][row][col]
   float2 hab[kSY][kBX + 1];   // row-blurred (dS/dmu_x, dS/dE[x^2])
   float hc[kSY][kBX + 1];     // row-blurred dS/dE[xy]
 };
 
-__global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
+__global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
                                                       long long n_blocks, const float* __restrict__ image,
                                                       const StepParams* __restrict__ sp,
                                                       float* __restrict__ partials, double* __restrict__ block_sums,
@@ -119,15 +121,19 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   float* P = partials + 9 * V.pix_base;
   const float* Yt = V.target;
   double l1 = 0.0, ss = 0.0;
-  {
+  if (kStageBufs == 2) {
     const float* const src[2] = {X, Yt};
     stage_block<2>(S.in[0], src, ox, oy, V.W, V.H);
   }
   for (int ch = 0; ch < 3; ++ch) {
-    const int cur = ch & 1;
-    if (ch < 2) {
+    const int cur = kStageBufs == 2 ? (ch & 1) : 0;
+    if (kStageBufs == 1) {
+      const float* const src[2] = {X + ch * HW, Yt + ch * HW};
+      stage_block<2>(S.in[0], src, ox, oy, V.W, V.H);
+      cp_async_wait<0>();
+    } else if (ch < 2) {
       const float* const src[2] = {X + (ch + 1) * HW, Yt + (ch + 1) * HW};
-      stage_block<2>(S.in[cur ^ 1], src, ox, oy, V.W, V.H);
+      stage_block<2>(S.in[(cur + 1) % kStageBufs], src, ox, oy, V.W, V.H);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(256) k_loss_forward(const ViewDev* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict__ views, int n_views,
+__global__ void __launch_bounds__(256, 3) k_loss_backward(const ViewDev* __restrict__ views, int n_views,
                                                        const float* __restrict__ image,
                                                        const StepParams* __restrict__ sp,
                                                        const float* __restrict__ partials,
@@ -353,15 +359,19 @@ __global__ void __launch_bounds__(256) k_loss_backward(const ViewDev* __restrict
   const float lam = sp->lambda_ssim;
   const float scale = 1.f / (3.f * (float)V.W * (float)V.H * (float)n_views);
   const float gl1 = sp->lambda_l1 * scale, gs = -lam * scale;
-  {
+  if (kStageBufs == 2) {
     const float* const src[3] = {P, P + HW, P + 2 * HW};
     stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);
   }
   for (int ch = 0; ch < 3; ++ch) {
-    const int cur = ch & 1;
-    if (ch < 2) {
+    const int cur = kStageBufs == 2 ? (ch & 1) : 0;
+    if (kStageBufs == 1) {
+      const float* const src[3] = {P + (3 * ch) * HW, P + (3 * ch + 1) * HW, P + (3 * ch + 2) * HW};
+      stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);
+      cp_async_wait<0>();
+    } else if (ch < 2) {
       const float* const src[3] = {P + (3 * ch + 3) * HW, P + (3 * ch + 4) * HW, P + (3 * ch + 5) * HW};
-      stage_block<3>(S.in[cur ^ 1], src, ox, oy, V.W, V.H);
+      stage_block<3>(S.in[(cur + 1) % kStageBufs], src, ox, oy, V.W, V.H);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
