@@ -25,8 +25,8 @@ struct ProjBuffers {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
 constexpr int kSortMinBlocks = 2;  // resident onesweep CTAs per SM the registers must allow
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep CTA
 constexpr int kSortBits = 8;

@@ -333,9 +333,14 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
     rank[r] = pre + __popc(peers & lt);
   }
   __syncthreads();
-  // Per digit: warp-exclusive prefix in place, CTA total, decoupled look-back across CTAs.
-  {
-    const int d = threadIdx.x;  // kSortThreads == kSortBins
+  // Per digit (thread d < 256; whole warps): warp-exclusive prefix in place, CTA total, decoupled
+  // look-back across CTAs, then the digit bases by a block-wide scan over the 256 digits.
+  static_assert(kSortThreads % kSortBins == 0, "the digit threads are whole warps");
+  __shared__ unsigned s_wa[kSortBins / 32], s_wb[kSortBins / 32];
+  const int d = threadIdx.x;
+  const bool digit = d < kSortBins;
+  unsigned total = 0u, excl = 0u, h = 0u, a = 0u, b = 0u;
+  if (digit) {
     unsigned run = 0;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) {
@@ -343,9 +348,8 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
       S.cnt[w][d] = run;
       run += c;
     }
-    const unsigned total = run;
+    total = run;
     unsigned* st = state + (unsigned long long)tile * kSortBins + d;
-    unsigned excl = 0;
     if (tile == 0) {
       st_relaxed_u32(st, kSortPrefix | total);
     } else {
@@ -383,9 +387,10 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
       st_relaxed_u32(st, kSortPrefix | (excl + total));
     }
     // digit base = exclusive scan of the global histogram; CTA digit start = exclusive scan of
-    // the CTA totals.  Both by a block-wide scan over the 256 digits.
-    const unsigned h = hist[pass * kSortBins + d];
-    unsigned a = h, b = total;
+    // the CTA totals
+    h = hist[pass * kSortBins + d];
+    a = h;
+    b = total;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned ya = __shfl_up_sync(0xffffffffu, a, o);
@@ -395,12 +400,13 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
         b += yb;
       }
     }
-    __shared__ unsigned s_wa[kSortThreads / 32], s_wb[kSortThreads / 32];
     if (lane == 31) {
       s_wa[warp] = a;
       s_wb[warp] = b;
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (digit) {
     unsigned pa = 0, pb = 0;
     for (int w = 0; w < warp; ++w) {
       pa += s_wa[w];
