@@ -366,7 +366,8 @@ template <int PIX>
 struct BwdWarp {
   float4 a[kChunk], b[kChunk], c[kChunk];  // the chunk's Gaussians (records A, B, C)
   uint2 act[PIX];                          // compacted (slot, mask) of the pixels to visit
-  float red[32][33];                       // per lane: the 27 terms of a group of 3 Gaussians
+  float red[kGroup * 9][36];               // per term of a group of 3 Gaussians: the 32 lanes' values
+                                           // (rows padded to 16-byte multiples for vector reads)
   float acc[kChunk][9];                    // per Gaussian of the chunk: running gradient sums
 };
 
@@ -569,13 +570,22 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
             }
           }
 #pragma unroll
-          for (int j = 0; j < 9; ++j) S.red[lane][9 * gi + j] = g[j];
+          for (int j = 0; j < 9; ++j) S.red[9 * gi + j][lane] = g[j];
         }
         __syncwarp();
         if (lane < 9 * ng) {
-          float sum = 0.f;
-#pragma unroll 8
-          for (int l = 0; l < 32; ++l) sum += S.red[l][lane];
+          // the term's 32 values: eight 16-byte reads, four running sums (fixed order)
+          const float4* row = reinterpret_cast<const float4*>(S.red[lane]);
+          float4 s4 = row[0];
+#pragma unroll
+          for (int k = 1; k < 8; ++k) {
+            const float4 x = row[k];
+            s4.x += x.x;
+            s4.y += x.y;
+            s4.z += x.z;
+            s4.w += x.w;
+          }
+          const float sum = (s4.x + s4.y) + (s4.z + s4.w);
           const int gi = lane / 9;
           const int q = gi == 0 ? qs[0] : (gi == 1 ? qs[1] : qs[2]);
           S.acc[q][lane - 9 * gi] += sum;
