@@ -112,7 +112,7 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic work per kernel launch (DESIGN.md): FP32 lane-operations for the blend kernels,
+# Algorithmic work per kernel launch: FP32 lane-operations for the blend kernels,
 # counted from the formulas they evaluate; bytes for the memory-bound kernels.
 def kernel_work(k, st, n, passes):
     P, B, M = st["pairs"], st["blended"], st["instances"]
@@ -200,7 +200,8 @@ def run_reference(args):
     val, sec, pairs = cpu_baseline_run(K_eff, W_eff)
     line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded ring scene; see DESIGN.md)",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
             "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",

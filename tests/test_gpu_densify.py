@@ -178,7 +178,7 @@ def test_checkpoint_keeps_statistics_and_the_split_round(tmp_path):
     ids = [f.add_image(c, t) for c, t in zip(cams, tg)]
     kw = dict(grad_thresh=1e-6, percent_dense=0.02, min_opacity=0.01, max_scale=0.5)
     f.optimize_step(ids)
-    f.densify(**kw)  # round 0
+    f.densify(**kw)  # the first densification (split counter 0)
     f.optimize_step(ids)
     f.save(tmp_path / "s.gsf")
     g = gs.Field.load(tmp_path / "s.gsf")
@@ -186,7 +186,7 @@ def test_checkpoint_keeps_statistics_and_the_split_round(tmp_path):
         x.optimize_step(ids)
     sa, sb = f.densify_stats(), g.densify_stats()
     assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
-    ra, rb = f.densify(**kw), g.densify(**kw)  # round 1 on both
+    ra, rb = f.densify(**kw), g.densify(**kw)  # the second one (counter 1) on both
     assert ra == rb
     for a, b in zip(f.get_gaussians(with_adam=True), g.get_gaussians(with_adam=True)):
         assert np.array_equal(a, b)
