@@ -397,3 +397,36 @@ def test_sparse_adam_updates_only_the_gaussians_a_step_sees():
     f.optimize_step([img])  # the unseen ones stay put on later steps too
     assert np.array_equal(f.get_gaussians()[:, ~seen], p[:, ~seen])
     f.close()
+
+
+def test_sparse_adam_over_several_views():
+    """sparse_adam in a step over three views: a Gaussian seen by any of them takes the dense
+    step's update, one seen by none keeps parameters and moments bit for bit."""
+    p = gi.cube_scene(3000, seed=13, stride=3008)
+    p[0, :3000:4] += 4.0  # a quarter far to the side: outside every view
+    cams = [gi.identity_camera(96, 64, 90.0), gi.identity_camera(70, 52, 60.0)]
+    R, t = gi.look_at([0.4, -0.3, -0.4], [0.0, 0.0, 3.0])
+    cams.append(gi.camera_dict(R, t, 70.0, 70.0, 40.0, 30.0, 81, 61))
+    tg = [gi.uniform_target(c["width"], c["height"], 30 + k) for k, c in enumerate(cams)]
+    f = make_field(use_graph=0, sparse_adam=1)
+    f.set_gaussians(p[:, :3000])
+    ids = [f.add_image(c, t) for c, t in zip(cams, tg)]
+    lr = float(np.mean([f.image_lr(i) for i in ids]))
+    f.optimize_step(ids)
+    got, gm, gv = f.get_gaussians(with_adam=True)
+    L, g, r = oracle.loss_and_grad(p, [ocam(c) for c in cams], tg, lam=0.2, prec="f32", n=3000)
+    seen = np.zeros(3000, bool)
+    for v in range(3):
+        rect = r["projs"][v]["rect"]
+        seen |= ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]) > 0) & (r["projs"][v]["radius"] > 0)
+    assert 0.3 < seen.mean() < 0.9
+    assert np.array_equal(got[:, ~seen], p[:, :3000][:, ~seen])
+    assert not gm[:, ~seen].any() and not gv[:, ~seen].any()
+    ref = p.copy()
+    oracle.adam(ref, g, np.zeros_like(p), np.zeros_like(p), [lr] + LRS_REST, 1, prec="f32", n=3000)
+    groups = [(0, 3, lr), (3, 6, 5e-3), (6, 10, 1e-3), (10, 11, 0.05), (11, 14, 2.5e-3), (14, 59, 1.25e-4)]
+    for a, b, lrg in groups:
+        d = np.abs(got[a:b, seen] - ref[a:b, :3000][:, seen])
+        bad = d > 1e-3 * lrg + 1e-6
+        assert bad.mean() < 2e-3, (a, b, bad.mean())
+    f.close()
