@@ -473,9 +473,17 @@ def run_batched(args):
         tot += ev0.elapsed_time(ev1)
         pairs += field.stats()["last_pairs"]
     tiling = field.stats()["last_tiling"]
+    # per-kernel times from the same steps run again with an event around every kernel
+    field.set_timing(True)
+    for _ in range(args.steps):
+        field.restore()
+        field.optimize_step(ids)
+    torch.cuda.synchronize()
+    kms, ksteps = field.kernel_times()
     field.close()
     print(json.dumps({"workload": "batched: 500k Gaussians, 9 views at mixed sizes, one graph", "ms_per_step":
                       tot / args.steps, "pairs_per_s": pairs / (tot * 1e-3),
+                      "kernel_ms_per_step": {nm: round(x / max(1, ksteps), 4) for nm, x in zip(KERNELS, kms)},
                       "sizes": [(c["width"], c["height"]) for c in cams],
                       "tiling": f"{tiling[0]}x{tiling[1]}/{tiling[2]}",
                       "autotune_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]}}))
