@@ -255,7 +255,10 @@ GS_API gs_status gs_integrate(gs_field* f, int32_t image_id, gs_integrate_stats*
  * seeded with seed ^ 0x5048415345310000, a draw in [0, n) is next() mod n).  The position rate is
  * 3DGS's exponential schedule, exp((1 - u) ln eta0 + u ln etaf) with u = min(step / max_steps, 1)
  * over the phase-1 steps (3DGS: max_steps 30000), times the scene extent; the other groups keep
- * their rates.  T_j counts these iterations (Eq. 7).  out_stats as for gs_integrate. */
+ * their rates.  T_j counts these iterations (Eq. 7).  out_stats as for gs_integrate.
+ * Called after the last arrival it is also the "rapid additional optimisation" of Phase 3
+ * (Sec. IV-A) over all registered images; refined poses, where a caller has them, are set first
+ * with gs_set_image. */
 GS_API gs_status gs_initial_training(gs_field* f, int32_t iterations, int32_t max_steps, gs_integrate_stats* out_stats);
 
 /* Render the field from any camera: out_rgb_chw (device, 3 x H x W), out_T (device, nullable). */
