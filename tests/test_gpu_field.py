@@ -430,3 +430,26 @@ def test_sparse_adam_over_several_views():
         bad = d > 1e-3 * lrg + 1e-6
         assert bad.mean() < 2e-3, (a, b, bad.mean())
     f.close()
+
+
+def test_phase3_refinement_takes_updated_poses():
+    """Phase 3 (Sec. IV-A) after the last arrival: a refined pose set with set_image is the one
+    the next step renders (its loss equals the oracle's for that pose and the field's current
+    state), and initial_training then runs the additional optimisation over the images."""
+    p, cams, tg = config1(seed=14)
+    f = make_field(use_graph=0)
+    f.set_gaussians(p)
+    img = f.add_image(cams[0], tg[0])
+    f.optimize_step([img])
+    refined = gi.camera_dict(cams[0]["R"], np.array([0.03, -0.02, 0.05]), cams[0]["fx"], cams[0]["fy"],
+                             cams[0]["cx"], cams[0]["cy"], cams[0]["width"], cams[0]["height"])
+    f.set_image(img, cam=refined)
+    state = f.get_gaussians()
+    loss = f.optimize_step([img])
+    L, _, _ = oracle.loss_and_grad(state, [ocam(refined)], tg, lam=0.2, prec="f32")
+    assert abs(loss - L) <= 1e-5 * max(1.0, abs(L))
+    L_old, _, _ = oracle.loss_and_grad(state, [ocam(cams[0])], tg, lam=0.2, prec="f32")
+    assert abs(L - L_old) > 1e-4  # the pose change is visible in the loss
+    st = f.initial_training(6, max_steps=30000)
+    assert st["iterations"] == 6 and np.isfinite(st["mean_loss"])
+    f.close()
