@@ -191,6 +191,20 @@ def cpu_baseline_run(steps, warmup, seed=0):
     return float(np.sum(pairs) / np.sum(times)), float(np.mean(times)), int(np.mean(pairs))
 
 
+def combine_ranks(ms, pairs, ws, device):
+    """Whole-job figures over the ranks' independent sessions: the slowest rank's time (max) and
+    the pairs of all ranks (sum).  One rank: unchanged."""
+    if ws <= 1:
+        return ms, pairs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, pairs], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t)
+    return float(tmax[0].item()), float(t[1].item())
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -347,13 +361,7 @@ def run_gs(args):
     kms, ksteps = field.kernel_times()
     field.set_timing(False)
     tiling = field.stats()["last_tiling"]
-    ms_max, pairs_total = ms, float(acc["pairs"])
-    if ws > 1:
-        t = torch.tensor([ms, float(acc["pairs"])], device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t)
-        ms_max, pairs_total = float(tmax[0].item()), float(t[1].item())
+    ms_max, pairs_total = combine_ranks(ms, float(acc["pairs"]), ws, "cuda")
     value = pairs_total / (ms_max * 1e-3)
 
     # end to end through the C ABI: host target (pinned) -> device, step, loss -> host
@@ -370,12 +378,7 @@ def run_gs(args):
         e2e_pairs += field.stats()["last_pairs"]
     sync_all()
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
-    if ws > 1:
-        t = torch.tensor([e2e_ms, float(e2e_pairs)], device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t)
-        e2e_ms, e2e_pairs = float(tmax[0].item()), float(t[1].item())
+    e2e_ms, e2e_pairs = combine_ranks(e2e_ms, float(e2e_pairs), ws, "cuda")
     field.close()
 
     steps = max(1, args.steps)
