@@ -681,6 +681,15 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
   }
   if (nvis == 0 && A.adam == 1 && sp->sparse) return;  // sparse Adam: not seen by the step
 
+  // log-scales, quaternion and opacity are complete here: update them before the SH rows so their
+  // gradients and values are not held through them (only the mean takes the direction gradient)
+  {
+    const float gg[8] = {gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
+    const float pc[8] = {ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
+    const int grp[8] = {1, 1, 1, 2, 2, 2, 2, 3};
+    apply_rows<8>(A, 3, grp, i, gg, pc);
+  }
+
   // SH rows, four coefficients (12 rows) at a time; accumulates the direction gradient.
   sh_group<0>(A, i, nvis, vmask, vdir, vcol, vdd);
   sh_group<4>(A, i, nvis, vmask, vdir, vcol, vdd);
@@ -695,10 +704,8 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
 #pragma unroll
     for (int a = 0; a < 3; ++a) gmu[a] += (vdd[j][a] - vdir[j][a] * dd) * vinv[j];
   }
-  const float gg[11] = {gmu[0], gmu[1], gmu[2], gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
-  const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
-  const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};
-  apply_rows<11>(A, 0, grp, i, gg, pc);
+  const int grp[3] = {0, 0, 0};
+  apply_rows<3>(A, 0, grp, i, gmu, mu);
 }
 
 // One SH coefficient K of one view: its three gradient rows (colour gradient x Y_K(dir)) into
