@@ -361,6 +361,24 @@ GS_API gs_status gs_field_autotune(gs_field* f, const int32_t* view_ids, int32_t
 GS_API gs_status gs_autotune_clear(void);
 
 /* ----------------------------------------------------------------------------------------
+ * Failure detection of the device-side waits.  The paper has no counterpart.
+ * ---------------------------------------------------------------------------------------- */
+
+/* The two inter-CTA waits of a step (the decoupled look-back of the K2 scan and of each K4 sort
+ * pass) spin a bounded number of times; a wait that gives up sets an error bit in the step's
+ * control block and its CTA finishes its work with the prefix it has, so the kernel returns and the
+ * context stays usable, and the step reports GS_ERR_TIMEOUT.  This call runs each wait once on a
+ * two-tile problem by a single CTA that holds the second tile: the first tile is never started,
+ * so the wait can only end by giving up.
+ *   spin_limit  rounds of the look-back before giving up; 0 = the limit the steps use
+ *   out_error   (host, 2 uint32) error bits of the scan's and the sort pass's run; bit 0 (value 1)
+ *               set = the wait gave up
+ *   out_ms      (host, 2 float, nullable) device time of each run
+ * Synchronous.  Allocates about 0.3 MB of device memory and frees it before returning.
+ * Returns GS_OK when both runs completed (whatever they report), GS_ERR_CUDA otherwise. */
+GS_API gs_status gs_wait_probe(uint32_t spin_limit, uint32_t out_error[2], float out_ms[2]);
+
+/* ----------------------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a deployment variant.
  * ---------------------------------------------------------------------------------------- */
 

@@ -153,6 +153,7 @@ SYMBOLS = {
     "gs_scan_noalloc": ([P, P, I64, P, P], I32),
     "gs_field_densify": ([P, P, P], I32),
     "gs_field_densify_stats": ([P, P, P], I32),
+    "gs_wait_probe": ([ctypes.c_uint32, P, P], I32),
 }
 
 KERNEL_NAMES = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss",
@@ -320,6 +321,17 @@ def tiling_candidates():
 def autotune_clear():
     """Forget every autotuned view-set class (the cache is shared by all sessions)."""
     _check(load().gs_autotune_clear())
+
+
+def wait_probe(spin_limit=0):
+    """Run the scan's and the sort pass's look-back wait once each with a predecessor that never
+    starts (spin_limit rounds, 0 = the steps' own limit).  Returns ((scan_error_bits, sort_error_bits),
+    (scan_ms, sort_ms)); bit 0 set = the wait gave up."""
+    _torch()
+    err = (ctypes.c_uint32 * 2)()
+    ms = (ctypes.c_float * 2)()
+    _check(load().gs_wait_probe(int(spin_limit), err, ms))
+    return (int(err[0]), int(err[1])), (float(ms[0]), float(ms[1]))
 
 
 def default_config(**kw):

@@ -147,8 +147,10 @@ __device__ __forceinline__ KeyLayout key_layout(const Control* ctl, int tile_bit
 }
 
 // Bounded spin limit for inter-CTA waits (decoupled look-back).  On expiry the waiting CTA sets
-// kErrTimeout and proceeds; the host reports GS_ERR_TIMEOUT.
-constexpr unsigned kSpinLimit = 1u << 24;
+// kErrTimeout and proceeds; the host reports GS_ERR_TIMEOUT.  A round of the scan's look-back takes
+// about 0.29 us on a GB300 and one of a sort pass's about 0.37 us, so a wait that nothing ends gives
+// up after about 1.2 / 1.6 s; a predecessor that is running publishes within microseconds.
+constexpr unsigned kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;

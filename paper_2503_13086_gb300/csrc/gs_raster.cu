@@ -382,6 +382,12 @@ extern "C" {
 const char* gs_last_error(void) { return gs::g_last_error.c_str(); }
 const char* gs_version(void) { return "gs-onthefly-gb300 0.1 (sm_103a)"; }
 
+gs_status gs_wait_probe(uint32_t spin_limit, uint32_t out_error[2], float out_ms[2]) {
+  if (!out_error) return fail(GS_ERR_INVALID_ARG, "out_error is NULL");
+  out_error[0] = out_error[1] = 0u;
+  return gs::run_wait_probe(spin_limit, out_error, out_ms);
+}
+
 gs_status gs_raster_create(gs_raster** out) {
   if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;

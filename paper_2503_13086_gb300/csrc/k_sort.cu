@@ -37,7 +37,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restrict__ in, unsigned* __restrict__ out,
                                                        long long n_items, unsigned long long* __restrict__ state,
                                                        Control* __restrict__ ctl, unsigned long long m_cap,
-                                                       Ledger* __restrict__ ledger, const float* __restrict__ depth) {
+                                                       Ledger* __restrict__ ledger, const float* __restrict__ depth,
+                                                       unsigned spin_limit) {
   dep_wait();
   dep_release();
   __shared__ unsigned s_tile;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const unsigned* __restric
         excl += v;
         if (first < 32 && ((isprefix >> first) & 1u)) break;
         j -= first;
-        if (first < 32 && ++spins > kSpinLimit) {
+        if (first < 32 && ++spins > spin_limit) {
           if (lane == 0) atomicOr(&ctl->error, kErrTimeout);
           break;
         }
@@ -169,7 +170,7 @@ void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned 
                  unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth) {
   const long long tiles = (n_items + kScanTile - 1) / kScanTile;
   launch_dep(k_scan, dim3((unsigned)tiles), dim3(kScanThreads), 0, s, in, out, n_items, state, ctl, m_cap, ledger,
-      depth);
+      depth, kSpinLimit);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
                                                             unsigned* __restrict__ vals1,
                                                             const unsigned* __restrict__ hist,
                                                             unsigned* __restrict__ state, int pass, int tile_bits,
-                                                            Control* __restrict__ ctl) {
+                                                            Control* __restrict__ ctl, unsigned spin_limit) {
   dep_wait();
   dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kSortThreads, kSortMinBlocks) k_sort_pass(unsi
           if (flag == kSortPrefix) done = true;
         }
         j -= used;
-        if (wait && ++spins > kSpinLimit) {
+        if (wait && ++spins > spin_limit) {
           atomicOr(&ctl->error, kErrTimeout);
           break;
         }
@@ -446,7 +447,7 @@ void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long 
                       cudaStream_t s) {
   const long long tiles = (m_cap + kSortTile - 1) / kSortTile;
   launch_dep(k_sort_pass, dim3((unsigned)(tiles > 0 ? tiles : 1)), dim3(kSortThreads), sizeof(SortSmem), s, keys0,
-      vals0, keys1, vals1, hist, state, pass, tile_bits, ctl);
+      vals0, keys1, vals1, hist, state, pass, tile_bits, ctl, kSpinLimit);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -474,6 +475,80 @@ void launch_ranges(const unsigned long long* keys, uint2* ranges, int tile_bits,
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
   launch_dep(k_ranges, dim3((unsigned)blocks), dim3(256), 0, s, keys, ranges, tile_bits, ctl);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Failure detection for the two inter-CTA waits.  Each wait is run once on a two-tile problem by a
+// single CTA that holds ticket 1: tile 0 is never started, so its status word stays 0 and the wait
+// can only end by giving up.  The problems are laid out so that the CTA's remaining work after
+// giving up (with a partial prefix of 0) stays inside its own buffers.
+// ---------------------------------------------------------------------------------------------
+gs_status run_wait_probe(unsigned spin_limit, unsigned out_error[2], float out_ms[2]) {
+  if (spin_limit == 0u) spin_limit = kSpinLimit;
+  init_sort_attributes();
+  const size_t n_scan = 2 * (size_t)kScanTile, n_sort = 2 * (size_t)kSortTile;
+  const size_t off_ctl_b = kCtlBytes, off_state_a = 2 * kCtlBytes;
+  const size_t off_state_b = off_state_a + 2 * sizeof(unsigned long long);
+  const size_t off_hist = off_state_b + 2 * kSortBins * sizeof(unsigned);
+  const size_t off_in = off_hist + (size_t)kMaxSortPasses * kSortBins * sizeof(unsigned);
+  const size_t off_out = off_in + n_scan * sizeof(unsigned);
+  const size_t off_k0 = off_out + n_scan * sizeof(unsigned);
+  const size_t off_k1 = off_k0 + n_sort * sizeof(unsigned long long);
+  const size_t off_v0 = off_k1 + n_sort * sizeof(unsigned long long);
+  const size_t off_v1 = off_v0 + n_sort * sizeof(unsigned);
+  const size_t bytes = off_v1 + n_sort * sizeof(unsigned);
+  char* d = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  gs_status status = GS_OK;
+  auto check = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && status == GS_OK) status = fail(GS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  if (check(cudaMalloc(&d, bytes), "cudaMalloc") && check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream") &&
+      check(cudaEventCreate(&ev[0]), "event") && check(cudaEventCreate(&ev[1]), "event") &&
+      check(cudaEventCreate(&ev[2]), "event") && check(cudaMemsetAsync(d, 0, bytes, st), "cudaMemsetAsync")) {
+    Control ca{}, cb{};
+    ca.scan_ticket = 1u;       // the CTA takes tile 1 of the scan
+    cb.sort_ticket[0] = 1u;    // and tile 1 of pass 0 of the sort
+    cb.m_total = n_sort;       // all keys 0: one pass, every key in digit 0
+    const unsigned h0 = (unsigned)n_sort;
+    Control* ctl_a = reinterpret_cast<Control*>(d);
+    Control* ctl_b = reinterpret_cast<Control*>(d + off_ctl_b);
+    unsigned* hist = reinterpret_cast<unsigned*>(d + off_hist);
+    if (check(cudaMemcpyAsync(ctl_a, &ca, sizeof(Control), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+        check(cudaMemcpyAsync(ctl_b, &cb, sizeof(Control), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+        check(cudaMemcpyAsync(hist, &h0, sizeof(unsigned), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync")) {
+      cudaEventRecord(ev[0], st);
+      k_scan<<<1, kScanThreads, 0, st>>>(reinterpret_cast<const unsigned*>(d + off_in),
+                                         reinterpret_cast<unsigned*>(d + off_out), (long long)n_scan,
+                                         reinterpret_cast<unsigned long long*>(d + off_state_a), ctl_a, ~0ull,
+                                         nullptr, nullptr, spin_limit);
+      cudaEventRecord(ev[1], st);
+      k_sort_pass<<<1, kSortThreads, sizeof(SortSmem), st>>>(
+          reinterpret_cast<unsigned long long*>(d + off_k0), reinterpret_cast<unsigned*>(d + off_v0),
+          reinterpret_cast<unsigned long long*>(d + off_k1), reinterpret_cast<unsigned*>(d + off_v1), hist,
+          reinterpret_cast<unsigned*>(d + off_state_b), 0, 8, ctl_b, spin_limit);
+      cudaEventRecord(ev[2], st);
+      check(cudaGetLastError(), "wait probe launch");
+      Control ra{}, rb{};
+      if (check(cudaMemcpyAsync(&ra, ctl_a, sizeof(Control), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") &&
+          check(cudaMemcpyAsync(&rb, ctl_b, sizeof(Control), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") &&
+          check(cudaStreamSynchronize(st), "cudaStreamSynchronize")) {
+        out_error[0] = ra.error;
+        out_error[1] = rb.error;
+        if (out_ms) {
+          cudaEventElapsedTime(&out_ms[0], ev[0], ev[1]);
+          cudaEventElapsedTime(&out_ms[1], ev[1], ev[2]);
+        }
+      }
+    }
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  return status;
 }
 
 }  // namespace gs
