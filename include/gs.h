@@ -62,7 +62,8 @@ typedef enum gs_status {
   GS_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
   GS_ERR_TIMEOUT = 6,     /* a bounded device-side wait expired */
   GS_ERR_STATE = 7,       /* call out of order (e.g. backward without a forward) */
-  GS_ERR_IO = 8           /* a file could not be written or read, or is not a saved field */
+  GS_ERR_IO = 8,          /* a file could not be written or read, or is not a saved field */
+  GS_ERR_INTERNAL = 9     /* a consistency check failed: a device buffer was written past its end */
 } gs_status;
 
 /* Pinhole camera.  R is the row-major world->camera rotation and t the translation
@@ -195,6 +196,11 @@ typedef struct gs_field_config {
   int32_t sparse_adam;      /* 1: a step's Adam updates only the Gaussians with instances in one of
                                its views (later 3DGS releases' sparse Adam; bias correction by the
                                field's step count); 0 (default): all, as the original dense Adam */
+  int32_t debug_canaries;   /* 1: after every run of steps, check the guard words behind every device
+                               buffer of the field (256 bytes of 0xA5 each, written when the buffer
+                               is allocated and never by a kernel) and fail with GS_ERR_INTERNAL,
+                               naming the buffer, if one changed.  Synchronises once per run of
+                               steps.  0 (default): off */
 } gs_field_config;
 
 /* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2
@@ -314,6 +320,15 @@ typedef struct gs_densify_result {
 GS_API gs_status gs_field_densify(gs_field* f, const gs_densify_params* p, gs_densify_result* out);
 /* The accumulated statistics (host arrays of n floats each; either may be NULL). */
 GS_API gs_status gs_field_densify_stats(gs_field* f, float* host_norm_sum, float* host_count);
+
+/* Host-side fault injection for the guard-word check (debug_canaries): overwrites one guard word
+ * behind the index-th allocated device buffer of the session (0 .. buffers - 1, a fixed order over
+ * the session's, its images' and its rasterizer's buffers) with 0, as a kernel writing past that
+ * buffer's end would.  The write lies inside the allocation.  out_name (host, name_cap bytes,
+ * nullable) receives the buffer's name.  The next run of steps with debug_canaries set fails with
+ * GS_ERR_INTERNAL naming it; the guard stays changed (the session is for testing only afterwards).
+ * Synchronous. */
+GS_API gs_status gs_field_corrupt_guard(gs_field* f, int32_t index, char* out_name, int32_t name_cap);
 
 /* Checkpoint / resume of a whole session in a file (the paper keeps the field and optimiser state
  * of a session; Sec. IV).  gs_field_save writes the configuration, the Gaussians with their Adam

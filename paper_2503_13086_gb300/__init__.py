@@ -81,7 +81,7 @@ class FieldConfig(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("hbm_budget_bytes", ctypes.c_uint64), ("initial_capacity", ctypes.c_int64),
                 ("tiling", Tiling), ("batch_scaling", ctypes.c_int32), ("lambda_l1", ctypes.c_float),
                 ("lambda_load", ctypes.c_float), ("densify_stats", ctypes.c_int32),
-                ("sparse_adam", ctypes.c_int32)]
+                ("sparse_adam", ctypes.c_int32), ("debug_canaries", ctypes.c_int32)]
 
 
 class DensifyParams(ctypes.Structure):
@@ -154,6 +154,7 @@ SYMBOLS = {
     "gs_field_densify": ([P, P, P], I32),
     "gs_field_densify_stats": ([P, P, P], I32),
     "gs_wait_probe": ([ctypes.c_uint32, P, P], I32),
+    "gs_field_corrupt_guard": ([P, I32, P, I32], I32),
 }
 
 KERNEL_NAMES = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss",
@@ -499,6 +500,13 @@ class Field:
         _check(self._lib.gs_field_densify_stats(self._h, a.ctypes.data_as(ctypes.c_void_p),
                                                 c.ctypes.data_as(ctypes.c_void_p)))
         return a[:n], c[:n]
+
+    def corrupt_guard(self, index):
+        """Overwrite one guard word behind the index-th allocated device buffer of the session (host-side
+        fault injection for the debug_canaries check); returns the buffer's name."""
+        name = ctypes.create_string_buffer(64)
+        _check(self._lib.gs_field_corrupt_guard(self._h, int(index), name, 64))
+        return name.value.decode()
 
     def render(self, cam, want_T=False):
         torch = _torch()

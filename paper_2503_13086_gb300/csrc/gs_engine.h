@@ -23,6 +23,11 @@ void init_sort_attributes();
 void init_blend_attributes();
 void init_loss_attributes();
 
+// Every DevBuf allocation carries kCanaryBytes of guard words (bytes 0xA5) behind its usable
+// `bytes`; no kernel writes them, so a changed word means a write past the end of the buffer.
+constexpr size_t kCanaryBytes = 256;
+constexpr unsigned kCanaryWord = 0xA5A5A5A5u;
+
 // A device allocation that only grows.
 struct DevBuf {
   void* p = nullptr;
@@ -30,6 +35,16 @@ struct DevBuf {
   gs_status reserve(size_t want, size_t* account);
   void release(size_t* account);
 };
+
+// One buffer whose guard words a check covers.
+struct CanaryRef {
+  const char* name;
+  const DevBuf* buf;
+};
+// Checks the guard words of `refs` (buffers without an allocation are skipped) on stream s and
+// waits for the result; `flags` is a device scratch of at least (n + 31) / 32 words.  On a changed
+// word returns GS_ERR_INTERNAL naming the first such buffer.
+gs_status check_canaries(const CanaryRef* refs, int n, unsigned* flags, cudaStream_t s);
 
 constexpr int kMaxViews = 32;
 // kernel launches of one optimisation step besides the sort passes: K1, K2, K3 x 2, K5 x 2, K6,

@@ -142,6 +142,7 @@ struct Field {
   size_t own_bytes = 0;
   // snapshot (gs_field_snapshot / gs_field_restore)
   DevBuf snap_p, snap_m, snap_v;
+  DevBuf canary_flags;  // scratch of the guard-word check
   int snap_n = -1, snap_stride = 0;
   long long snap_step = 0;
   std::vector<int> snap_T;
@@ -166,10 +167,45 @@ struct Field {
     snap_p.release(&own_bytes);
     snap_m.release(&own_bytes);
     snap_v.release(&own_bytes);
+    canary_flags.release(&own_bytes);
     DevBuf* pts[] = {&pts_xyz,   &pts_next,  &grid_keys,  &grid_head,   &new_rgb,
                      &far_flags, &far_off,   &far_count,  &pts_next_c,  &grid_keys_c, &grid_head_c};
     for (DevBuf* b : pts) b->release(&own_bytes);
     if (count_h) cudaFreeHost(count_h);
+  }
+
+  // Every device buffer of the session (its own, its images', its rasterizer's) for the guard-word
+  // check, in a fixed order.
+  std::vector<CanaryRef> canary_refs() const {
+    std::vector<CanaryRef> v = {
+        {"params", &params}, {"adam_m", &adam_m}, {"adam_v", &adam_v}, {"dstat", &dstat}, {"dens_tmp", &dens_tmp},
+        {"pts_xyz", &pts_xyz}, {"pts_next", &pts_next}, {"grid_keys", &grid_keys}, {"grid_head", &grid_head},
+        {"new_rgb", &new_rgb}, {"far_flags", &far_flags}, {"far_off", &far_off}, {"far_count", &far_count},
+        {"pts_next_c", &pts_next_c}, {"grid_keys_c", &grid_keys_c}, {"grid_head_c", &grid_head_c},
+        {"step_img", &step_img}, {"step_last", &step_last}, {"step_dimg", &step_dimg}, {"step_T", &step_T},
+        {"step_gp", &step_gp}, {"snap_p", &snap_p}, {"snap_m", &snap_m}, {"snap_v", &snap_v}};
+    for (const Image& im : images) v.push_back({"image rgb", &im.rgb});
+    if (r) {
+      const Raster& R = *r;
+      const CanaryRef rr[] = {
+          {"step params", &R.sp_d}, {"views", &R.views_d}, {"ledger", &R.ledger_d}, {"control + scan state", &R.zeroA},
+          {"histograms + sort state + ranges", &R.zeroB}, {"xyo", &R.xyo}, {"conic", &R.conic}, {"rgb", &R.rgb},
+          {"depth", &R.depth}, {"radius", &R.radius}, {"rect", &R.rect}, {"count", &R.count}, {"offsets", &R.offsets},
+          {"clamp", &R.clamp}, {"g2s", &R.g2s}, {"keys0", &R.keys0}, {"keys1", &R.keys1}, {"vals0", &R.vals0},
+          {"vals1", &R.vals1}, {"ginst", &R.ginst}, {"ckpt", &R.ckpt}, {"cmask", &R.cmask}, {"order", &R.order},
+          {"tile_chunks", &R.tile_chunks}, {"inst_rec", &R.inst_rec}, {"carry", &R.carry}, {"partials", &R.partials},
+          {"block_sums", &R.block_sums}, {"raster image", &R.own_image}, {"raster last", &R.own_last},
+          {"raster dimage", &R.own_dimage}};
+      v.insert(v.end(), std::begin(rr), std::end(rr));
+    }
+    return v;
+  }
+
+  gs_status check_guard_words() {
+    const std::vector<CanaryRef> refs = canary_refs();
+    gs_status s = canary_flags.reserve(((refs.size() + 31) / 32) * 4, &own_bytes);
+    if (s) return s;
+    return check_canaries(refs.data(), (int)refs.size(), static_cast<unsigned*>(canary_flags.p), stream);
   }
 
   PointGridDev grid_dev(bool coarse = false) const {
@@ -765,6 +801,7 @@ struct Field {
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     const Ledger& Lg = *R.ledger_h;
     if (Lg.error & kErrTimeout) return fail(GS_ERR_TIMEOUT, "a device-side wait (decoupled look-back) timed out");
+    if (cfg.debug_canaries && (s = check_guard_words())) return s;
     const size_t ok = std::min<size_t>(Lg.steps_ok, count);
     // commit the completed prefix only
     adam_step = step0 + (long long)ok;
@@ -1163,6 +1200,28 @@ gs_status gs_field_densify_stats(gs_field* ff, float* host_sum, float* host_coun
   return GS_OK;
 }
 
+gs_status gs_field_corrupt_guard(gs_field* ff, int32_t index, char* out_name, int32_t name_cap) {
+  Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "field is NULL");
+  cudaError_t e = cudaStreamSynchronize(f->stream);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  std::vector<gs::CanaryRef> allocated;
+  for (const gs::CanaryRef& c : f->canary_refs())
+    if (c.buf->p) allocated.push_back(c);
+  if (index < 0 || index >= (int32_t)allocated.size())
+    return fail(GS_ERR_INVALID_ARG, "index must be in 0.." + std::to_string((long long)allocated.size() - 1));
+  const gs::DevBuf* b = allocated[(size_t)index].buf;
+  // one guard word of the allocation (inside it: the bytes behind the usable size)
+  e = cudaMemset(static_cast<char*>(b->p) + b->bytes + 4 * (index % 64), 0, 4);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  if (out_name && name_cap > 0) {
+    std::strncpy(out_name, allocated[(size_t)index].name, (size_t)name_cap - 1);
+    out_name[name_cap - 1] = '\0';
+  }
+  return GS_OK;
+}
+
 gs_status gs_field_densify(gs_field* ff, const gs_densify_params* prm, gs_densify_result* out) {
   Field* f = F(ff);
   if (!f || !prm) return fail(GS_ERR_INVALID_ARG, "NULL argument");
@@ -1436,7 +1495,7 @@ extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
   if (!out.f) return fail(GS_ERR_IO, std::string("cannot write ") + path);
   FileHeader h;
   std::memcpy(h.magic, kMagic, 8);
-  h.version = 2;
+  h.version = 3;
   h.cfg_bytes = sizeof(gs_field_config);
   h.camera_bytes = sizeof(gs_camera);
   h.nparams = gs::kNumParams;
@@ -1490,7 +1549,7 @@ extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** ou
   if (!in.f) return fail(GS_ERR_IO, std::string("cannot read ") + path);
   FileHeader h;
   in.get(h);
-  if (!in.ok || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 2 || h.cfg_bytes != sizeof(gs_field_config) ||
+  if (!in.ok || std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 3 || h.cfg_bytes != sizeof(gs_field_config) ||
       h.camera_bytes != sizeof(gs_camera) || h.nparams != (uint32_t)gs::kNumParams)
     return fail(GS_ERR_IO, std::string(path) + " is not a saved field of this library");
   gs_field_config cfg;

@@ -38,11 +38,19 @@ gs_status DevBuf::reserve(size_t want, size_t* account) {
   }
   if (want == 0) return GS_OK;
   const size_t rounded = (want + 255) & ~size_t(255);
-  cudaError_t e = cudaMalloc(&p, rounded);
+  cudaError_t e = cudaMalloc(&p, rounded + kCanaryBytes);
   if (e != cudaSuccess) {
     p = nullptr;
     cudaGetLastError();
     return fail(GS_ERR_OOM, std::string("cudaMalloc(") + std::to_string(rounded) + "): " + cudaGetErrorString(e));
+  }
+  // guard words behind the usable bytes, complete before any stream can use the buffer
+  e = cudaMemset(static_cast<char*>(p) + rounded, 0xA5, kCanaryBytes);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    p = nullptr;
+    return fail(GS_ERR_CUDA, std::string("guard words: ") + cudaGetErrorString(e));
   }
   bytes = rounded;
   if (account) *account += bytes;
@@ -62,6 +70,51 @@ void DevBuf::release(size_t* account) {
   }
   p = nullptr;
   bytes = 0;
+}
+
+// Guard-word check: one CTA of 64 threads per buffer (64 x 4 B = kCanaryBytes).
+constexpr int kCanaryBatch = 64;
+struct CanaryList {
+  const unsigned* p[kCanaryBatch];
+  int n;
+};
+static_assert(kCanaryBytes == 64 * 4, "one thread per guard word");
+
+__global__ void k_canary_check(CanaryList L, int first, unsigned* __restrict__ flags) {
+  const int b = blockIdx.x;
+  if (b >= L.n) return;
+  if (L.p[b][threadIdx.x] != kCanaryWord) atomicOr(&flags[(first + b) >> 5], 1u << ((first + b) & 31));
+}
+
+gs_status check_canaries(const CanaryRef* refs, int n, unsigned* flags, cudaStream_t s) {
+  const int words = (n + 31) / 32;
+  cudaError_t e = words > 0 ? cudaMemsetAsync(flags, 0, (size_t)words * 4, s) : cudaSuccess;
+  // one launch per run of up to kCanaryBatch consecutive allocated buffers; flag bit = position in refs
+  int k = 0;
+  while (k < n && e == cudaSuccess) {
+    if (!refs[k].buf || !refs[k].buf->p) {
+      ++k;
+      continue;
+    }
+    CanaryList L{};
+    const int first = k;
+    while (k < n && L.n < kCanaryBatch && refs[k].buf && refs[k].buf->p) {
+      const DevBuf* d = refs[k].buf;
+      L.p[L.n++] = reinterpret_cast<const unsigned*>(static_cast<const char*>(d->p) + d->bytes);
+      ++k;
+    }
+    k_canary_check<<<L.n, 64, 0, s>>>(L, first, flags);
+    e = cudaGetLastError();
+  }
+  std::vector<unsigned> h((size_t)words, 0u);
+  if (e == cudaSuccess && words > 0) e = cudaMemcpyAsync(h.data(), flags, (size_t)words * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("guard-word check: ") + cudaGetErrorString(e));
+  for (int j = 0; j < n; ++j)
+    if ((h[(size_t)j >> 5] >> (j & 31)) & 1u)
+      return fail(GS_ERR_INTERNAL, std::string("device buffer '") + refs[j].name +
+                                       "' was written past its end (its guard words changed)");
+  return GS_OK;
 }
 
 static int bits_for(long long x) {  // bits needed to represent values 0..x
