@@ -61,3 +61,12 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.run_reference(argparse.Namespace(steps=3, warmup=3, gpus=2)) is None
+
+
+def test_all_cores_oracle_baseline_runs_its_steps_together():
+    """The host-cores baseline: one oracle step per process of a spawn pool, started at a common
+    barrier; the figure is all their pairs over the span from the first start to the last end."""
+    import bench
+    val, procs, span, pairs = bench.cpu_baseline_all_cores(2)
+    assert procs == 2 and span > 0 and pairs > 0
+    assert val == pytest.approx(2 * pairs / span, rel=1e-6)
