@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gs.h"
 #include "gs_device.cuh"
 #include "gs_kernels.h"
@@ -18,6 +20,16 @@ gs_status fail(gs_status s, const std::string& msg);
 // K2's and K4's look-back waits run once each with a predecessor that never starts (gs_wait_probe).
 gs_status run_wait_probe(unsigned spin_limit, unsigned out_error[2], float out_ms[2]);
 std::mutex& alloc_capture_mutex();
+
+// A named NVTX range over a scope (host-side phases of the session: steps, field update, graph
+// capture, densification...), for profilers that read NVTX (ncu --nvtx).  Costs nothing when no
+// tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 void init_sort_attributes();
 void init_blend_attributes();

@@ -605,6 +605,7 @@ struct Field {
     for (auto& g : graphs)
       if (g.key == key && g.timing == R.timing) ge = &g;
     if (!ge) {
+      TraceRange trace("graph capture");
       if (graphs.size() >= 8) drop_graphs();
       cudaGraph_t graph;
       std::unique_lock<std::mutex> lock(alloc_capture_mutex());
@@ -768,6 +769,7 @@ struct Field {
   // rest.  T_j and the Adam step count are advanced only for completed steps.
   gs_status run_steps(const std::vector<std::vector<int>>& groups, size_t first_group, size_t count, size_t* done,
                       double* loss_sum) {
+    TraceRange trace("run of steps");
     Raster& R = *r;
     gs_status s;
     const long long step0 = adam_step;
@@ -943,6 +945,7 @@ gs_status gs_field_destroy(gs_field* f) {
 }
 
 gs_status gs_field_set_gaussians(gs_field* ff, const float* host, int64_t n, int64_t src_stride) {
+  gs::TraceRange trace("gs_field_set_gaussians");
   Field* f = F(ff);
   if (!f || (!host && n > 0) || n < 0 || src_stride < n) return fail(GS_ERR_INVALID_ARG, "bad arguments");
   gs_status s = f->reserve_gaussians(std::max<int64_t>(n, 1));
@@ -983,6 +986,7 @@ gs_status gs_field_get_gaussians(gs_field* ff, float* host, float* host_m, float
 
 gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int on_device, const float* pts_xyz,
                        const float* pts_rgb, int32_t n_pts, const int64_t* tracks, int32_t* out_id) {
+  gs::TraceRange trace("gs_add_image");
   Field* f = F(ff);
   if (!f || !cam || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (n_pts < 0 || (n_pts > 0 && (!pts_xyz || !pts_rgb))) return fail(GS_ERR_INVALID_ARG, "bad sparse points");
@@ -1089,6 +1093,7 @@ gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int
 }
 
 gs_status gs_set_image(gs_field* ff, int32_t id, const gs_camera* cam, const float* rgb, int on_device) {
+  gs::TraceRange trace("gs_set_image");
   Field* f = F(ff);
   if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
   gs::Image& im = f->images[id];
@@ -1120,6 +1125,7 @@ gs_status gs_select_neighbors(gs_field* ff, int32_t id, int32_t k, int32_t* out_
 }
 
 gs_status gs_optimize_step(gs_field* ff, const int32_t* ids, int32_t nv, float* out_loss) {
+  gs::TraceRange trace("gs_optimize_step");
   Field* f = F(ff);
   if (!f || !ids) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   std::vector<int> v(ids, ids + nv);
@@ -1127,6 +1133,7 @@ gs_status gs_optimize_step(gs_field* ff, const int32_t* ids, int32_t nv, float* 
 }
 
 gs_status gs_integrate(gs_field* ff, int32_t id, gs_integrate_stats* st) {
+  gs::TraceRange trace("gs_integrate");
   Field* f = F(ff);
   if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
   int nk = 0;
@@ -1152,6 +1159,7 @@ gs_status gs_integrate(gs_field* ff, int32_t id, gs_integrate_stats* st) {
 }
 
 gs_status gs_initial_training(gs_field* ff, int32_t iterations, int32_t max_steps, gs_integrate_stats* st) {
+  gs::TraceRange trace("gs_initial_training");
   Field* f = F(ff);
   if (!f || iterations < 0 || max_steps <= 0) return fail(GS_ERR_INVALID_ARG, "bad arguments");
   if (f->images.empty()) return fail(GS_ERR_STATE, "no registered image");
@@ -1223,6 +1231,7 @@ gs_status gs_field_corrupt_guard(gs_field* ff, int32_t index, char* out_name, in
 }
 
 gs_status gs_field_densify(gs_field* ff, const gs_densify_params* prm, gs_densify_result* out) {
+  gs::TraceRange trace("gs_field_densify");
   Field* f = F(ff);
   if (!f || !prm) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (!(prm->grad_thresh >= 0.f) || !(prm->percent_dense > 0.f) || !(prm->min_opacity > 0.f) ||
@@ -1306,6 +1315,7 @@ gs_status gs_field_densify(gs_field* ff, const gs_densify_params* prm, gs_densif
 }
 
 gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* out_T) {
+  gs::TraceRange trace("gs_render");
   Field* f = F(ff);
   if (!f || !cam || !out_rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (f->n <= 0) return fail(GS_ERR_STATE, "the field has no Gaussians");
@@ -1371,6 +1381,7 @@ gs_status gs_image_lr(const gs_field* ff, int32_t id, float* out_lr) {
 }
 
 gs_status gs_field_snapshot(gs_field* ff) {
+  gs::TraceRange trace("gs_field_snapshot");
   Field* f = F(ff);
   if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
   const size_t bytes = (size_t)f->stride * gs::kNumParams * 4;
@@ -1397,6 +1408,7 @@ gs_status gs_field_snapshot(gs_field* ff) {
 }
 
 gs_status gs_field_restore(gs_field* ff) {
+  gs::TraceRange trace("gs_field_restore");
   Field* f = F(ff);
   if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
   if (f->snap_n < 0) return fail(GS_ERR_STATE, "no snapshot");
@@ -1427,6 +1439,7 @@ gs_status gs_field_set_timing(gs_field* ff, int enable) {
 }
 
 gs_status gs_field_autotune(gs_field* ff, const int32_t* ids, int32_t nv, int32_t reps, gs_autotune_result* out) {
+  gs::TraceRange trace("gs_field_autotune");
   Field* f = F(ff);
   if (!f || !ids) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   for (int k = 0; k < nv; ++k)
@@ -1486,6 +1499,7 @@ struct File {
 }  // namespace
 
 extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
+  gs::TraceRange trace("gs_field_save");
   Field* f = F(ff);
   if (!f || !path) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   cudaError_t e = cudaStreamSynchronize(f->stream);
@@ -1542,6 +1556,7 @@ extern "C" gs_status gs_field_save(gs_field* ff, const char* path) {
 }
 
 extern "C" gs_status gs_field_load(const char* path, void* stream, gs_field** out_field) {
+  gs::TraceRange trace("gs_field_load");
   if (!path || !out_field) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   *out_field = nullptr;
   File in;
