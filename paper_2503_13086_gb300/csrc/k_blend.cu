@@ -507,9 +507,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
 #pragma unroll
         for (int gi = 0; gi < kGroup; ++gi) {
           qs[gi] = 0;
-          float g[9];
+          // the nine terms summed over this lane's pixel pairs, both halves kept apart until the end
+          float2 g2[9];
 #pragma unroll
-          for (int j = 0; j < 9; ++j) g[j] = 0.f;
+          for (int j = 0; j < 9; ++j) g2[j] = make_float2(0.f, 0.f);
           if (uni) {
             const int q = __ffs(uni) - 1;
             uni &= uni - 1u;
@@ -546,31 +547,33 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
               float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T[pp], cd));
               dal.x = oG.x > kAlphaMax ? 0.f : dal.x;
               dal.y = oG.y > kAlphaMax ? 0.f : dal.y;
-              const float2 w0 = __fmul2_rn(w, d0[pp]), w1 = __fmul2_rn(w, d1[pp]), w2 = __fmul2_rn(w, d2[pp]);
-              const float2 g5 = __fmul2_rn(dal, G);
               const float2 dpow = __fmul2_rn(dal, alpha);
               const float2 ex = __ffma2_rn(A2x2, dx, __fmul2_rn(B2, dy));
               const float2 ey = __ffma2_rn(B2, dx, __fmul2_rn(C2x2, dy));
               const float2 pdx = __fmul2_rn(dpow, dx), pdy = __fmul2_rn(dpow, dy);
-              const float2 g0 = __fmul2_rn(dpow, ex), g1 = __fmul2_rn(dpow, ey);
-              const float2 g2 = __fmul2_rn(pdx, dx), g3 = __fmul2_rn(pdx, dy), g4 = __fmul2_rn(pdy, dy);
-              g[0] += g0.x + g0.y;
-              g[1] += g1.x + g1.y;
-              g[2] -= 0.5f * (g2.x + g2.y);
-              g[3] -= g3.x + g3.y;
-              g[4] -= 0.5f * (g4.x + g4.y);
-              g[5] += g5.x + g5.y;
-              g[6] += w0.x + w0.y;
-              g[7] += w1.x + w1.y;
-              g[8] += w2.x + w2.y;
+              g2[0] = __ffma2_rn(dpow, ex, g2[0]);
+              g2[1] = __ffma2_rn(dpow, ey, g2[1]);
+              g2[2] = __ffma2_rn(pdx, dx, g2[2]);
+              g2[3] = __ffma2_rn(pdx, dy, g2[3]);
+              g2[4] = __ffma2_rn(pdy, dy, g2[4]);
+              g2[5] = __ffma2_rn(dal, G, g2[5]);
+              g2[6] = __ffma2_rn(w, d0[pp], g2[6]);
+              g2[7] = __ffma2_rn(w, d1[pp], g2[7]);
+              g2[8] = __ffma2_rn(w, d2[pp], g2[8]);
               T[pp] = __fmul2_rn(T[pp], __ffma2_rn(alpha, neg2, one2));
               F0[pp] = n0;
               F1[pp] = n1;
               F2[pp] = n2;
             }
           }
+          // terms 2-4 of the conic: -1/2, -1, -1/2 times the accumulated products
+          S.red[9 * gi + 0][lane] = g2[0].x + g2[0].y;
+          S.red[9 * gi + 1][lane] = g2[1].x + g2[1].y;
+          S.red[9 * gi + 2][lane] = -0.5f * (g2[2].x + g2[2].y);
+          S.red[9 * gi + 3][lane] = -(g2[3].x + g2[3].y);
+          S.red[9 * gi + 4][lane] = -0.5f * (g2[4].x + g2[4].y);
 #pragma unroll
-          for (int j = 0; j < 9; ++j) S.red[9 * gi + j][lane] = g[j];
+          for (int j = 5; j < 9; ++j) S.red[9 * gi + j][lane] = g2[j].x + g2[j].y;
         }
         __syncwarp();
         if (lane < 9 * ng) {
