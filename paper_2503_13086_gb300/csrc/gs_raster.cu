@@ -32,7 +32,7 @@ gs_status DevBuf::reserve(size_t want, size_t* account) {
     // steps enqueued earlier may still use the old buffer
     cudaDeviceSynchronize();
     cudaFree(p);
-    if (account) *account -= bytes;
+    if (account) *account -= bytes + kCanaryBytes;
     p = nullptr;
     bytes = 0;
   }
@@ -53,7 +53,7 @@ gs_status DevBuf::reserve(size_t want, size_t* account) {
     return fail(GS_ERR_CUDA, std::string("guard words: ") + cudaGetErrorString(e));
   }
   bytes = rounded;
-  if (account) *account += bytes;
+  if (account) *account += bytes + kCanaryBytes;
   return GS_OK;
 }
 
@@ -66,7 +66,7 @@ void DevBuf::release(size_t* account) {
   if (p) {
     cudaDeviceSynchronize();
     cudaFree(p);
-    if (account) *account -= bytes;
+    if (account) *account -= bytes + kCanaryBytes;
   }
   p = nullptr;
   bytes = 0;
