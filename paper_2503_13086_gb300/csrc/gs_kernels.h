@@ -57,7 +57,7 @@ void launch_scan(const unsigned* in, unsigned* out, long long n_items, unsigned 
                  unsigned long long m_cap, Ledger* ledger, cudaStream_t s, const float* depth = nullptr);
 void launch_emit(const ProjBuffers& pb, const ViewDev* views, int stride, long long n_items, unsigned long long* keys0,
                  unsigned* vals0, unsigned long long* keys1, unsigned* vals1, unsigned* inst_rec, unsigned* hist,
-                 int tile_bits, int num_sms, const Control* ctl, cudaStream_t s);
+                 int tile_bits, long long m_cap, int num_sms, const Control* ctl, cudaStream_t s);
 void launch_sort_pass(unsigned long long* keys0, unsigned* vals0, unsigned long long* keys1, unsigned* vals1,
                       const unsigned* hist, unsigned* state, int pass, int tile_bits, long long m_cap, Control* ctl,
                       cudaStream_t s);

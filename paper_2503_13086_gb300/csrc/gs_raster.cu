@@ -364,7 +364,7 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
   unsigned* v0 = static_cast<unsigned*>(vals0.p);
   unsigned* v1 = static_cast<unsigned*>(vals1.p);
   launch_emit(proj(), vd(), stride, n_items, k0, v0, k1, v1, static_cast<unsigned*>(inst_rec.p),
-              hist(), tile_bits, num_sms, ctl(), s);
+              hist(), tile_bits, (long long)m_cap, num_sms, ctl(), s);
   mark(s, 3);
   const unsigned long long sort_tiles = (m_cap + kSortTile - 1) / kSortTile;
   for (int p = 0; p < passes; ++p)  // passes the step does not need return at once; the list ends in buffer 0
