@@ -28,15 +28,20 @@ class Scene:
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes, session_budget_bytes, max_active=4):
+    def __init__(self, hbm_budget_bytes, session_budget_bytes, max_active=4, session_factory=None, mem_info=None):
+        """session_factory(hbm_budget_bytes=..., **scene.config) makes a scene's session (default: a
+        StreamingSession); mem_info() -> (free, total) device bytes, sampled for the peak (default:
+        torch.cuda.mem_get_info).  Both are replaceable so that the admission policy runs without a GPU."""
         self.hbm_budget = int(hbm_budget_bytes)
         self.session_budget = int(session_budget_bytes)
         self.max_active = int(max_active)
+        self.session_factory = session_factory or StreamingSession
+        self.mem_info = mem_info
         self.log = []  # (time_s, event, scene id)
 
     def run(self, scenes, keep_fields=False, poll_s=0.0005):
         """Serve every scene; returns {sid: dict(results, latency, state)}."""
-        torch = _torch()
+        mem_info = self.mem_info or _torch().cuda.mem_get_info
         t_start = time.perf_counter()
         lock = threading.Lock()
         pending = sorted(scenes, key=lambda s: s.requests[0][0] if s.requests else 0.0)
@@ -50,7 +55,7 @@ class Server:
         def worker(scene):
             sess = None
             try:
-                sess = StreamingSession(hbm_budget_bytes=self.session_budget, **scene.config)
+                sess = self.session_factory(hbm_budget_bytes=self.session_budget, **scene.config)
                 for arrival, req in scene.requests:
                     wait = arrival - now()
                     if wait > 0:
@@ -87,7 +92,7 @@ class Server:
                         (len(active) >= self.max_active or reserved[0] + self.session_budget > self.hbm_budget):
                     if not self.log or self.log[-1][1:] != ("defer", pending[0].sid):
                         self.log.append((now(), "defer", pending[0].sid))
-            free, total = torch.cuda.mem_get_info()
+            free, total = mem_info()
             peak_used[0] = max(peak_used[0], total - free)
             time.sleep(poll_s)
         if errors:
