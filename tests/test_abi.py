@@ -41,6 +41,10 @@ def test_host_only_calls_without_a_gpu():
     # argument checks fail cleanly with a status and a message, no GPU touched
     assert lib.gs_field_init(None, None, None) == 1
     assert b"NULL" in lib.gs_last_error()
+    assert lib.gs_wait_probe(0, None, None) == 1
+    assert b"out_error" in lib.gs_last_error()
+    assert lib.gs_field_corrupt_guard(None, 0, None, 0) == 1
+    assert cfg.debug_canaries == 0 and cfg.sparse_adam == 0 and cfg.densify_stats == 0
 
 
 def test_tiling_candidates_on_the_host():
