@@ -1,6 +1,7 @@
 """Parity at the bench's full size (200k Gaussians in the ring scene, one 1297 x 840 view, L1 +
-0.2 D-SSIM), in the launch configuration the bench times: bit-exact binning, pixels, loss and
-gradients against the oracle, and the Eq. 9 G_p statistic."""
+0.2 D-SSIM): bit-exact binning, pixels, loss and gradients against the oracle, the session step in
+the launch configuration the bench times (graph replay, Adam fused) against the oracle's step, and
+the Eq. 9 G_p statistic."""
 import numpy as np
 import pytest
 
@@ -50,6 +51,24 @@ def test_scene_scale_parity():
     bad = grad_close(grads.cpu().numpy()[:, :n], g_ref[:, :n])
     assert bad.mean() < 1e-3, bad.sum(axis=1)
     ras.close()
+    # the session step the bench times (graph-captured, Adam fused into the projection backward):
+    # its loss, and one Adam step from zero moments applied to the oracle's gradients
+    f = gs.Field(scene_extent=7.0, lambda_ssim=0.2, use_graph=1, tiling=(16, 16, 256))
+    f.set_gaussians(p)
+    img_id = f.add_image(cam, tgt)
+    lr = f.image_lr(img_id)
+    step_loss = f.optimize_step([img_id])
+    got = f.get_gaussians()
+    f.close()
+    assert abs(step_loss - ref) <= 1e-5 * abs(ref)
+    rates = [lr * 7.0, 5e-3, 1e-3, 0.05, 2.5e-3, 2.5e-3 / 20]
+    upd = p.copy()
+    oracle.adam(upd, g_ref, np.zeros_like(p), np.zeros_like(p), rates, 1, prec="f32")
+    for (a, b), rate in zip([(0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 59)], rates):
+        # a first Adam step moves a parameter by about rate x sign(g); only gradients too small for a
+        # stable sign may differ
+        off = np.abs(got[a:b, :n] - upd[a:b, :n]) > 1e-3 * rate + 1e-6
+        assert off.mean() < 2e-3, (a, b, off.mean())
 
 
 def test_load_balance_statistic_matches_oracle():
