@@ -291,6 +291,21 @@ GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);
 /* Per-image bookkeeping: T_j (iterations trained, Eq. 7) and the overlap row M[image, :]. */
 GS_API gs_status gs_image_info(const gs_field* f, int32_t image_id, int32_t* out_T, float* out_M_row, int32_t row_len);
 
+/* The schedule of one arrival on the host, with no session and no GPU (planning, tests): for the
+ * arriving image new_id, given the overlap matrix M (host, n x n, row-major, M[i][j] in [0, 1]) and
+ * the images' iteration counts T (host, n, Eq. 7), the Eq. 3-4 weights, the N_m key images (highest
+ * weight first, ties to the lower id), the T_I view slots of Eq. 5 plus the semi-global half in
+ * their seeded order (cfg supplies T_I, N_m and seed), and Eq. 8's rate of every image (cfg supplies
+ * eta0, etaf and T_a) -- the computation gs_integrate runs for a session.
+ *   out_slots  (host, cfg->T_I int32)         the image of each iteration slot; *out_n_slots = T_I
+ *   out_keys   (host, cfg->N_m int32, nullable) the key images; *out_n_keys of them
+ *   out_w      (host, n float, nullable)       Eq. 3-4 weights (0 for images new_id cannot reach)
+ *   out_lr     (host, n float, nullable)       Eq. 8 rates
+ * GS_ERR_INVALID_ARG for n < 1, new_id outside [0, n), T_I or N_m < 1, or a NULL required pointer. */
+GS_API gs_status gs_schedule_plan(const gs_field_config* cfg, const float* M, const int32_t* T, int32_t n,
+                                  int32_t new_id, int32_t* out_slots, int32_t* out_n_slots, int32_t* out_keys,
+                                  int32_t* out_n_keys, float* out_w, float* out_lr);
+
 /* The learning rate of Eq. 8 for image_id under the current T_j (diagnostics and tests). */
 GS_API gs_status gs_image_lr(const gs_field* f, int32_t image_id, float* out_lr);
 

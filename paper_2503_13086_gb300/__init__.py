@@ -155,6 +155,7 @@ SYMBOLS = {
     "gs_field_densify_stats": ([P, P, P], I32),
     "gs_wait_probe": ([ctypes.c_uint32, P, P], I32),
     "gs_field_corrupt_guard": ([P, I32, P, I32], I32),
+    "gs_schedule_plan": ([P, P, P, I32, I32, P, P, P, P, P, P], I32),
 }
 
 KERNEL_NAMES = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges", "K6 blend fwd", "K7 loss",
@@ -333,6 +334,26 @@ def wait_probe(spin_limit=0):
     ms = (ctypes.c_float * 2)()
     _check(load().gs_wait_probe(int(spin_limit), err, ms))
     return (int(err[0]), int(err[1])), (float(ms[0]), float(ms[1]))
+
+
+def schedule_plan(M, T, new_id, **config):
+    """The schedule of one arrival computed on the host (no GPU): returns dict(slots, keys, w, lr) for
+    overlap matrix M (n x n), iteration counts T (n) and the arriving image new_id; config fields of
+    gs_field_config (T_I, N_m, seed, eta0, etaf, T_a) as keywords."""
+    lib = load()
+    cfg = default_config(**config)
+    M = np.ascontiguousarray(M, np.float32)
+    T = np.ascontiguousarray(T, np.int32)
+    n = int(M.shape[0])
+    slots = np.zeros(max(cfg.T_I, 1), np.int32)
+    keys = np.zeros(max(cfg.N_m, 1), np.int32)
+    w = np.zeros(n, np.float32)
+    lr = np.zeros(n, np.float32)
+    ns, nk = ctypes.c_int32(), ctypes.c_int32()
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    _check(lib.gs_schedule_plan(ctypes.byref(cfg), vp(M), vp(T), n, int(new_id), vp(slots), ctypes.byref(ns),
+                                vp(keys), ctypes.byref(nk), vp(w), vp(lr)))
+    return dict(slots=slots[:ns.value].tolist(), keys=keys[:nk.value].tolist(), w=w, lr=lr)
 
 
 def default_config(**kw):

@@ -105,6 +105,138 @@ TuneCache& tune_cache() {
   return c;
 }
 
+// The schedule of Sec. IV-C/IV-D on the host: Eq. 6-8 rates, Eq. 3-4 weights, the key images and
+// Eq. 5 with the semi-global half, over an overlap matrix M (n x n) and the images' iteration
+// counts T (Eq. 7).  The session and gs_schedule_plan both use it.
+struct Schedule {
+  const gs_field_config& cfg;
+  const std::vector<std::vector<float>>& M;
+  const std::vector<int>& T;
+  int n() const { return (int)M.size(); }
+
+  double lr_current(int Tj) const {
+    const double t = Tj > cfg.T_a ? 1.0 : (double)Tj / (double)cfg.T_a;
+    return std::exp(std::log((double)cfg.eta0) * (1.0 - t) + std::log((double)cfg.etaf) * t);
+  }
+  // Eq. 8
+  double lr_image(int j) const {
+    double acc = lr_current(T[j]);
+    int cnt = 0;
+    for (int i = 0; i < n(); ++i) {
+      if (i == j || !(M[i][j] > 0.f)) continue;
+      acc += (double)M[i][j] * lr_current(T[i]);
+      ++cnt;
+    }
+    return acc / (double)(cnt + 1);
+  }
+
+  // Eq. 3-4
+  void weights(int nw, std::vector<double>& w) const {
+    const int N = n();
+    w.assign(N, 0.0);
+    std::vector<int> layer(N, 0);
+    w[nw] = 1.0;
+    layer[nw] = 1;
+    std::vector<int> prev = {nw};
+    int k = 1;
+    while (!prev.empty()) {
+      ++k;
+      std::vector<int> next;
+      for (int i = 0; i < N; ++i) {
+        if (layer[i]) continue;
+        for (int j : prev)
+          if (M[j][i] > 0.f) {
+            next.push_back(i);
+            break;
+          }
+      }
+      for (int i : next) layer[i] = k;
+      for (int i : next) {
+        if (k == 2) {
+          w[i] = w[nw] * (double)M[i][nw];
+        } else {
+          double s = 0;
+          for (int j : prev) s += w[j] * (double)M[j][i];
+          w[i] = s / (double)prev.size();
+        }
+      }
+      prev = next;
+    }
+  }
+
+  static std::vector<int> key_images(const std::vector<double>& w, int n_m) {
+    std::vector<int> cand;
+    for (int i = 0; i < (int)w.size(); ++i)
+      if (w[i] > 0.0) cand.push_back(i);
+    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return w[a] != w[b] ? w[a] > w[b] : a < b; });
+    if ((int)cand.size() > n_m) cand.resize(n_m);
+    return cand;
+  }
+
+  static std::vector<int> largest_remainder(const std::vector<double>& shares, const std::vector<int>& ids, int total) {
+    double s = 0;
+    for (double x : shares) s += x;
+    std::vector<double> exact(shares.size());
+    std::vector<int> base(shares.size());
+    int used = 0;
+    for (size_t k = 0; k < shares.size(); ++k) {
+      exact[k] = (double)total * shares[k] / s;
+      base[k] = (int)std::floor(exact[k]);
+      used += base[k];
+    }
+    std::vector<size_t> order(shares.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+      const double ra = exact[a] - base[a], rb = exact[b] - base[b];
+      return ra != rb ? ra > rb : ids[a] < ids[b];
+    });
+    for (int q = 0; q < total - used && q < (int)order.size(); ++q) base[order[q]] += 1;
+    return base;
+  }
+
+  // Eq. 5 + the semi-global half; returns the shuffled view slots
+  std::vector<int> allocate(int nw, int* n_keys) const {
+    std::vector<double> w;
+    weights(nw, w);
+    std::vector<int> keys = key_images(w, cfg.N_m);
+    if (n_keys) *n_keys = (int)keys.size();
+    std::vector<double> shares;
+    for (int i : keys) shares.push_back(1.0 - std::exp(-w[i]));
+    std::vector<char> is_key((size_t)n(), 0);
+    for (int i : keys) is_key[i] = 1;
+    std::vector<int> others;
+    for (int i = 0; i < n(); ++i)
+      if (!is_key[i]) others.push_back(i);
+    SplitMix64 rng(cfg.seed ^ ((unsigned long long)(nw + 1) * 0x9E3779B97F4A7C15ull));
+    std::vector<int> iters((size_t)n(), 0);
+    const int T_I = cfg.T_I;
+    if (!others.empty()) {
+      std::vector<int> tk = largest_remainder(shares, keys, T_I / 2);
+      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
+      const int half = T_I - T_I / 2;
+      const int per = half / (int)others.size(), rem = half % (int)others.size();
+      std::vector<int> arr = others;
+      for (int i = 0; i < rem; ++i) {
+        const int j = i + (int)rng.below((unsigned long long)(arr.size() - i));
+        std::swap(arr[i], arr[j]);
+      }
+      for (int i : others) iters[i] = per;
+      for (int i = 0; i < rem; ++i) iters[arr[i]] += 1;
+    } else {
+      std::vector<int> tk = largest_remainder(shares, keys, T_I);
+      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
+    }
+    std::vector<int> slots;
+    for (int i = 0; i < n(); ++i)
+      for (int q = 0; q < iters[i]; ++q) slots.push_back(i);
+    for (int i = (int)slots.size() - 1; i > 0; --i) {
+      const int j = (int)rng.below((unsigned long long)(i + 1));
+      std::swap(slots[i], slots[j]);
+    }
+    return slots;
+  }
+};
+
 struct Field {
   gs_field_config cfg;
   cudaStream_t stream = nullptr;
@@ -377,126 +509,24 @@ struct Field {
   }
 
   // Eq. 6-7
-  double lr_current(int T) const {
-    const double t = T > cfg.T_a ? 1.0 : (double)T / (double)cfg.T_a;
-    return std::exp(std::log((double)cfg.eta0) * (1.0 - t) + std::log((double)cfg.etaf) * t);
+  std::vector<int> image_T() const {
+    std::vector<int> t;
+    t.reserve(images.size());
+    for (const Image& im : images) t.push_back(im.T);
+    return t;
   }
-  // Eq. 8
   double lr_image(int j) const {
-    double acc = lr_current(images[j].T);
-    int cnt = 0;
-    for (int i = 0; i < (int)images.size(); ++i) {
-      if (i == j || !(M[i][j] > 0.f)) continue;
-      acc += (double)M[i][j] * lr_current(images[i].T);
-      ++cnt;
-    }
-    return acc / (double)(cnt + 1);
+    const std::vector<int> t = image_T();
+    return Schedule{cfg, M, t}.lr_image(j);
   }
-
-  // Eq. 3-4
   void weights(int nw, std::vector<double>& w) const {
-    const int N = (int)images.size();
-    w.assign(N, 0.0);
-    std::vector<int> layer(N, 0);
-    w[nw] = 1.0;
-    layer[nw] = 1;
-    std::vector<int> prev = {nw};
-    int k = 1;
-    while (!prev.empty()) {
-      ++k;
-      std::vector<int> next;
-      for (int i = 0; i < N; ++i) {
-        if (layer[i]) continue;
-        for (int j : prev)
-          if (M[j][i] > 0.f) {
-            next.push_back(i);
-            break;
-          }
-      }
-      for (int i : next) layer[i] = k;
-      for (int i : next) {
-        if (k == 2) {
-          w[i] = w[nw] * (double)M[i][nw];
-        } else {
-          double s = 0;
-          for (int j : prev) s += w[j] * (double)M[j][i];
-          w[i] = s / (double)prev.size();
-        }
-      }
-      prev = next;
-    }
+    const std::vector<int> t = image_T();
+    Schedule{cfg, M, t}.weights(nw, w);
   }
-
-  std::vector<int> key_images(const std::vector<double>& w, int n_m) const {
-    std::vector<int> cand;
-    for (int i = 0; i < (int)w.size(); ++i)
-      if (w[i] > 0.0) cand.push_back(i);
-    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return w[a] != w[b] ? w[a] > w[b] : a < b; });
-    if ((int)cand.size() > n_m) cand.resize(n_m);
-    return cand;
-  }
-
-  static std::vector<int> largest_remainder(const std::vector<double>& shares, const std::vector<int>& ids, int total) {
-    double s = 0;
-    for (double x : shares) s += x;
-    std::vector<double> exact(shares.size());
-    std::vector<int> base(shares.size());
-    int used = 0;
-    for (size_t k = 0; k < shares.size(); ++k) {
-      exact[k] = (double)total * shares[k] / s;
-      base[k] = (int)std::floor(exact[k]);
-      used += base[k];
-    }
-    std::vector<size_t> order(shares.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-      const double ra = exact[a] - base[a], rb = exact[b] - base[b];
-      return ra != rb ? ra > rb : ids[a] < ids[b];
-    });
-    for (int q = 0; q < total - used && q < (int)order.size(); ++q) base[order[q]] += 1;
-    return base;
-  }
-
-  // Eq. 5 + the semi-global half; returns the shuffled view slots
+  std::vector<int> key_images(const std::vector<double>& w, int n_m) const { return Schedule::key_images(w, n_m); }
   std::vector<int> allocate(int nw, int* n_keys) const {
-    std::vector<double> w;
-    weights(nw, w);
-    std::vector<int> keys = key_images(w, cfg.N_m);
-    if (n_keys) *n_keys = (int)keys.size();
-    std::vector<double> shares;
-    for (int i : keys) shares.push_back(1.0 - std::exp(-w[i]));
-    std::vector<char> is_key(images.size(), 0);
-    for (int i : keys) is_key[i] = 1;
-    std::vector<int> others;
-    for (int i = 0; i < (int)images.size(); ++i)
-      if (!is_key[i]) others.push_back(i);
-    SplitMix64 rng(cfg.seed ^ ((unsigned long long)(nw + 1) * 0x9E3779B97F4A7C15ull));
-    std::vector<int> iters(images.size(), 0);
-    const int T_I = cfg.T_I;
-    if (!others.empty()) {
-      std::vector<int> tk = largest_remainder(shares, keys, T_I / 2);
-      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
-      const int half = T_I - T_I / 2;
-      const int per = half / (int)others.size(), rem = half % (int)others.size();
-      std::vector<int> arr = others;
-      for (int i = 0; i < rem; ++i) {
-        const int j = i + (int)rng.below((unsigned long long)(arr.size() - i));
-        std::swap(arr[i], arr[j]);
-      }
-      for (int i : others) iters[i] = per;
-      for (int i = 0; i < rem; ++i) iters[arr[i]] += 1;
-    } else {
-      std::vector<int> tk = largest_remainder(shares, keys, T_I);
-      for (size_t q = 0; q < keys.size(); ++q) iters[keys[q]] = tk[q];
-    }
-    std::vector<int> slots;
-    for (int i = 0; i < (int)images.size(); ++i)
-      for (int q = 0; q < iters[i]; ++q) slots.push_back(i);
-    for (int i = (int)slots.size() - 1; i > 0; --i) {
-      const int j = (int)rng.below((unsigned long long)(i + 1));
-      std::swap(slots[i], slots[j]);
-    }
-    return slots;
+    const std::vector<int> t = image_T();
+    return Schedule{cfg, M, t}.allocate(nw, n_keys);
   }
 
   gs_status ensure_step_buffers(long long pix) {
@@ -1370,6 +1400,37 @@ gs_status gs_image_info(const gs_field* ff, int32_t id, int32_t* out_T, float* r
   if (out_T) *out_T = f->images[id].T;
   if (row)
     for (int i = 0; i < row_len && i < (int)f->images.size(); ++i) row[i] = f->M[id][i];
+  return GS_OK;
+}
+
+gs_status gs_schedule_plan(const gs_field_config* cfg, const float* Mh, const int32_t* Th, int32_t n,
+                           int32_t new_id, int32_t* out_slots, int32_t* out_n_slots, int32_t* out_keys,
+                           int32_t* out_n_keys, float* out_w, float* out_lr) {
+  if (!cfg || !Mh || !Th || !out_slots || !out_n_slots || (out_keys && !out_n_keys))
+    return fail(GS_ERR_INVALID_ARG, "gs_schedule_plan: a required pointer is NULL");
+  if (n < 1 || new_id < 0 || new_id >= n || cfg->T_I < 1 || cfg->N_m < 1)
+    return fail(GS_ERR_INVALID_ARG, "gs_schedule_plan: need n >= 1, 0 <= new_id < n, T_I >= 1, N_m >= 1");
+  std::vector<std::vector<float>> M((size_t)n, std::vector<float>((size_t)n));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) M[i][j] = Mh[(size_t)i * n + j];
+  const std::vector<int> T(Th, Th + n);
+  const gs::Schedule sc{*cfg, M, T};
+  int nk = 0;
+  const std::vector<int> slots = sc.allocate(new_id, &nk);
+  if ((int)slots.size() > cfg->T_I) return fail(GS_ERR_INVALID_ARG, "gs_schedule_plan: more slots than T_I");
+  std::copy(slots.begin(), slots.end(), out_slots);
+  *out_n_slots = (int32_t)slots.size();
+  std::vector<double> w;
+  sc.weights(new_id, w);
+  if (out_keys) {
+    const std::vector<int> keys = gs::Schedule::key_images(w, cfg->N_m);
+    std::copy(keys.begin(), keys.end(), out_keys);
+    *out_n_keys = (int32_t)keys.size();
+  }
+  for (int i = 0; i < n; ++i) {
+    if (out_w) out_w[i] = (float)w[i];
+    if (out_lr) out_lr[i] = (float)sc.lr_image(i);
+  }
   return GS_OK;
 }
 
