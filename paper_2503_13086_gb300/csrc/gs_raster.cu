@@ -126,13 +126,15 @@ static int bits_for(long long x) {  // bits needed to represent values 0..x
   return b;
 }
 
+// Kernel attributes, occupancy figures and the loss window's constants, set once per process
+// (sessions may be created from several host threads at once).
 static void init_attributes_once() {
-  static bool done = false;
-  if (done) return;
-  init_sort_attributes();
-  init_blend_attributes();
-  init_loss_attributes();
-  done = true;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    init_sort_attributes();
+    init_blend_attributes();
+    init_loss_attributes();
+  });
 }
 
 Raster::Raster() {
