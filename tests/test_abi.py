@@ -1,8 +1,10 @@
-"""The C ABI library builds for sm_103a, loads, and exports every entry point include/gs.h declares
-(CPU only: no compute call is made)."""
+"""The C ABI library builds for sm_103a, loads, and exports every entry point include/gs.h declares;
+a C program compiles against the header and links the library (CPU only: no GPU call is made)."""
 import ctypes
 import os
 import re
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -70,3 +72,54 @@ def test_loading_a_file_that_is_not_a_field_fails_cleanly(tmp_path):
     assert b"not a saved field" in lib.gs_last_error()
     assert lib.gs_field_load(str(tmp_path / "missing.gsf").encode(), None, ctypes.byref(h)) == 8
     assert not h.value
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "gs.h"
+int main(void) {
+  gs_field_config c;
+  gs_field_config_default(&c);
+  if (c.T_I != 200 || c.N_m != 10) return 1;
+  /* three images in a chain 0 - 1 - 2, image 1 arriving */
+  float M[9] = {0.f, 0.5f, 0.f, 0.5f, 0.f, 0.25f, 0.f, 0.25f, 0.f};
+  int32_t T[3] = {10, 0, 300}, slots[200], keys[10], ns = 0, nk = 0;
+  float w[3], lr[3];
+  c.N_m = 2;
+  if (gs_schedule_plan(&c, M, T, 3, 1, slots, &ns, keys, &nk, w, lr) != GS_OK) return 2;
+  if (ns != 200 || nk != 2 || keys[0] != 1 || keys[1] != 0) return 3;
+  if (w[1] != 1.f || w[0] != 0.5f || w[2] != 0.25f) return 4;
+  int count[3] = {0, 0, 0};
+  for (int i = 0; i < ns; ++i) count[slots[i]]++;
+  if (count[0] + count[1] != 100 || count[2] != 100) return 5;  /* key half, semi-global half */
+  if (gs_schedule_plan(&c, M, T, 3, 7, slots, &ns, keys, &nk, w, lr) != GS_ERR_INVALID_ARG) return 6;
+  if (strlen(gs_last_error()) == 0) return 7;
+  printf("ok %d %d %d\n", count[0], count[1], count[2]);
+  return 0;
+}
+"""
+
+
+def test_a_c_program_uses_the_abi(tmp_path):
+    """The header is plain C (C99, pedantic) and a C program links the library and runs a host-side
+    entry point (the Eq. 3-5 schedule), no GPU needed."""
+    import shutil
+    import subprocess
+    import paper_2503_13086_gb300 as gs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = gs.library_path()
+    if not os.path.exists(lib):
+        gs.build()
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src), lib,
+                        "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.startswith("ok")
