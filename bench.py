@@ -602,19 +602,22 @@ def run_serve(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
-    ap.add_argument("--impl", default="gs", choices=["gs", "reference"])
-    ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve", "stream"])
-    ap.add_argument("--arrivals", type=int, default=20)
-    ap.add_argument("--serve-budget-gb", type=float, default=40.0)
-    ap.add_argument("--serve-session-gb", type=float, default=16.0)
-    ap.add_argument("--serve-points", type=int, default=150_000)
-    ap.add_argument("--serve-gt", type=int, default=4_000_000)
-    ap.add_argument("--serve-batch", type=int, default=3)
-    ap.add_argument("--serve-thresh", type=float, default=0.005)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs (one rank each under torchrun; independent sessions)")
+    ap.add_argument("--steps", type=int, default=200, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=10, help="untimed warm-up steps (at least 3)")
+    ap.add_argument("--impl", default="gs", choices=["gs", "reference"],
+                    help="gs: the CUDA library; reference: the CPU oracle on the same workload")
+    ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve", "stream"],
+                    help="scene: the headline step (+ streaming latency); batched: 9 views per step; "
+                         "serve: sessions under an HBM budget; stream: a full-length arrival stream")
+    ap.add_argument("--arrivals", type=int, default=20, help="arriving images of the streaming / serving runs")
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0, help="serve: the server's HBM budget")
+    ap.add_argument("--serve-session-gb", type=float, default=16.0, help="serve: HBM reserved per session")
+    ap.add_argument("--serve-points", type=int, default=150_000, help="serve: most sparse points per arrival (at least half as many)")
+    ap.add_argument("--serve-gt", type=int, default=4_000_000, help="serve: Gaussians of each hidden scene")
+    ap.add_argument("--serve-batch", type=int, default=3, help="serve: views per optimisation step")
+    ap.add_argument("--serve-thresh", type=float, default=0.005, help="serve: new-point distance threshold")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timings")
     ap.add_argument("--no-autotune-report", action="store_true",
                     help="skip the timed run of the autotuned session (profiling runs)")
     ap.add_argument("--tiling", default="16x16x256",
