@@ -33,23 +33,25 @@ def cam(W, H, f, cx=None, cy=None, R=None, t=None):
 
 
 # ------------------------------------------------------------------------------------------
-# Spherical harmonics: degree <= 3 real SH, each of our basis functions equal (up to the sign
-# convention) to scipy's real SH of the same (l, m), and the set orthonormal on the sphere.
+# Spherical harmonics: degree <= 3 real SH in the convention of 3DGS, whose basis the paper keeps
+# (Sec. V-A): Y_l^m of scipy carries the Condon-Shortley phase (-1)^m, and 3DGS's real basis is
+# sqrt(2) Re Y_l^m (m > 0), sqrt(2) Im Y_l^|m| (m < 0), Y_l^0 (m = 0), ordered m = -l .. l.  Each of
+# the oracle's 16 functions must equal that reference with its sign, and the set be orthonormal.
 # ------------------------------------------------------------------------------------------
-def _real_sh_scipy(l, m, polar, azim):
+def _real_sh_3dgs(l, m, polar, azim):
     import scipy.special as sp
     if hasattr(sp, "sph_harm_y"):
         Y = sp.sph_harm_y(l, abs(m), polar, azim)
     else:  # older scipy
         Y = sp.sph_harm(abs(m), l, azim, polar)
     if m > 0:
-        return math.sqrt(2.0) * (-1) ** m * Y.real
+        return math.sqrt(2.0) * Y.real
     if m < 0:
-        return math.sqrt(2.0) * (-1) ** m * Y.imag
+        return math.sqrt(2.0) * Y.imag
     return Y.real
 
 
-def test_sh_basis_matches_real_spherical_harmonics():
+def _sphere_quadrature():
     x, w = np.polynomial.legendre.leggauss(16)
     nphi = 32
     phi = 2 * np.pi * np.arange(nphi) / nphi
@@ -57,6 +59,11 @@ def test_sh_basis_matches_real_spherical_harmonics():
     ST = np.sqrt(1 - CT ** 2)
     dirs = np.stack([ST * np.cos(PH), ST * np.sin(PH), CT], -1).reshape(-1, 3)
     wt = (w[:, None] * np.ones((1, nphi)) * (2 * np.pi / nphi)).reshape(-1)
+    return dirs, wt
+
+
+def test_sh_basis_matches_real_spherical_harmonics():
+    dirs, wt = _sphere_quadrature()
     Y = oracle.sh_eval(dirs, "f64")
     G = (Y * wt[:, None]).T @ Y
     assert np.allclose(G, np.eye(16), atol=1e-12)
@@ -65,10 +72,38 @@ def test_sh_basis_matches_real_spherical_harmonics():
     k = 0
     for l in range(4):
         for m in range(-l, l + 1):
-            ref = _real_sh_scipy(l, m, polar, azim)
+            ref = _real_sh_3dgs(l, m, polar, azim)
+            # the projection onto the reference, sign included: +1 for the same function
             c = float(np.sum(wt * Y[:, k] * ref))
-            assert abs(abs(c) - 1.0) < 1e-10, (l, m, c)
+            assert abs(c - 1.0) < 1e-10, (l, m, c)
+            assert np.allclose(Y[:, k], ref, atol=1e-12), (l, m)
             k += 1
+
+
+def test_sh_basis_values_on_the_axes():
+    """Hand-evaluated values on the coordinate axes (x, y, z = one of the unit vectors), from the
+    normalisations sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) (times sqrt 2 for m != 0) and the
+    Legendre functions of each (l, m); zero wherever a factor x, y or z of the function vanishes."""
+    pi = math.pi
+    k1 = math.sqrt(3 / (4 * pi))                  # l = 1
+    k2 = 0.5 * math.sqrt(15 / pi)                 # l = 2, |m| = 1, 2 (xy, yz, xz)
+    k20 = 0.25 * math.sqrt(5 / pi)                # l = 2, m = 0: (3 z^2 - 1)
+    k22 = 0.25 * math.sqrt(15 / pi)               # l = 2, m = 2: (x^2 - y^2)
+    k33 = 0.25 * math.sqrt(35 / (2 * pi))         # l = 3, |m| = 3
+    k31 = 0.25 * math.sqrt(21 / (2 * pi))         # l = 3, |m| = 1
+    k30 = 0.25 * math.sqrt(7 / pi)                # l = 3, m = 0: z (5 z^2 - 3)
+    Y = oracle.sh_eval(np.eye(3), "f64")
+    want = np.zeros((3, 16))
+    want[:, 0] = 0.5 / math.sqrt(pi)
+    # +x: Y_1^1 = -k1 x; Y_2^0 = -k20; Y_2^2 = +k22; Y_3^1 = -k31 x (4z^2 - x^2 - y^2) = +k31;
+    #     Y_3^3 = -k33 x (x^2 - 3y^2) = -k33
+    want[0, 3], want[0, 6], want[0, 8], want[0, 13], want[0, 15] = -k1, -k20, k22, k31, -k33
+    # +y: Y_1^-1 = -k1 y; Y_2^0 = -k20; Y_2^2 = -k22; Y_3^-3 = -k33 y (3x^2 - y^2) = +k33;
+    #     Y_3^-1 = -k31 y (4z^2 - x^2 - y^2) = +k31
+    want[1, 1], want[1, 6], want[1, 8], want[1, 9], want[1, 11] = -k1, -k20, -k22, k33, k31
+    # +z: Y_1^0 = k1 z; Y_2^0 = 2 k20; Y_3^0 = k30 z (2z^2 - 3x^2 - 3y^2) = 2 k30
+    want[2, 2], want[2, 6], want[2, 12] = k1, 2 * k20, 2 * k30
+    assert np.allclose(Y, want, atol=1e-14), np.argwhere(~np.isclose(Y, want, atol=1e-14))
 
 
 # ------------------------------------------------------------------------------------------
