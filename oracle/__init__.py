@@ -61,6 +61,7 @@ def _declare(L):
         getattr(L, f"orc_project_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32] + [P] * 9
         getattr(L, f"orc_blend_forward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 12
         getattr(L, f"orc_blend_backward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 9
+        getattr(L, f"orc_blend_backward_magnitude_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 10
         getattr(L, f"orc_project_backward_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32, P, P]
         f = getattr(L, f"orc_loss_{suf}")
         f.argtypes = [I32, I32, P, P, F64, P, F64, P, P]
@@ -185,6 +186,27 @@ def blend_backward(cam_size, tile_base, ranges, vals, rec, dimg, grad2d, bg=(0, 
         W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
         _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(grad2d))
     return grad2d
+
+
+def blend_backward_magnitude(cam_size, tile_base, ranges, vals, rec, dimg, grad2d_mag, terms, bg=(0, 0, 0),
+                             tile=(16, 16), prec="f32"):
+    """The rounding scale of blend_backward's sums: accumulates into ``grad2d_mag`` (9 per record) the
+    sum of the magnitudes of every product that enters each 2D gradient, and into ``terms`` (uint32 per
+    record) the number of (pixel, contributor) terms.  |fl(g) - g| <= gamma_k * grad2d_mag for k
+    roundings in sequence (the componentwise bound of a floating-point sum)."""
+    dt = _dt(prec)
+    W, H = cam_size
+    m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
+    bgv = np.asarray(bg, dt)
+    d = _c(dimg, dt)
+    assert grad2d_mag.dtype == dt and grad2d_mag.flags.c_contiguous
+    assert terms.dtype == np.uint32 and terms.flags.c_contiguous
+    ranges = _c(ranges, np.uint32)
+    vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    getattr(lib(), f"orc_blend_backward_magnitude_{prec}")(
+        W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
+        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(grad2d_mag), _ptr(terms))
+    return grad2d_mag, terms
 
 
 def project_backward(params, cam: Camera, grad2d, grads, tile=(16, 16), prec="f32", n=None):

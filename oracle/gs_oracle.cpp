@@ -463,13 +463,22 @@ void blend_forward(int W, int H, int tw, int th, int64_t tile_base, const uint32
 // with its exact transmittance, then the contributors are visited back to front while the colour
 // behind them (including the background term) is accumulated.  The clamps and cutoffs act as
 // masks.  grad2d per record: d mean2d (2), d conic (a, b, c), d opacity, d rgb (3).
-template <class T>
-void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
-                    const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity,
-                    const T* rgb, const T* bg, const T* dimg, T* grad2d) {
+//
+// With kMagnitude the same walk accumulates, instead of each gradient, the sum of the absolute
+// values of every elementary product that enters it (|dL/dC| |c| T, the colour behind a
+// contributor as a sum of magnitudes, |a dx| + |b dy| for the mean, ...), and terms[rec] counts the
+// (pixel, contributor) terms summed into the record.  That is the scale of the componentwise
+// rounding-error bound of the sum (Higham, "Accuracy and Stability of Numerical Algorithms", Sec.
+// 4.2: |fl(sum) - sum| <= gamma_k sum |x_i| for k terms): a parity check uses it for the entries
+// whose terms cancel.
+template <class T, bool kMagnitude>
+void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
+                         const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity,
+                         const T* rgb, const T* bg, const T* dimg, T* grad2d, uint32_t* terms) {
   const int gx = (W + tw - 1) / tw;
   PixelWalk<T> w;
   const int64_t HW = (int64_t)W * H;
+  auto mag = [](T x) { return kMagnitude ? std::fabs(x) : x; };
   for (int py = 0; py < H; ++py)
     for (int px = 0; px < W; ++px) {
       const int64_t tile = tile_base + (int64_t)(py / th) * gx + px / tw;
@@ -478,31 +487,48 @@ void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint3
       const int64_t pix = (int64_t)py * W + px;
       T dC[3], S[3];
       for (int ch = 0; ch < 3; ++ch) {
-        dC[ch] = dimg[ch * HW + pix];
-        S[ch] = bg[ch] * w.trans;
+        dC[ch] = mag(dimg[ch * HW + pix]);
+        S[ch] = mag(bg[ch]) * w.trans;
       }
       for (int k = (int)w.contrib.size() - 1; k >= 0; --k) {
         const auto& e = w.contrib[k];
         T* g = grad2d + 9 * (int64_t)e.rec;
+        if (terms) terms[e.rec] += 1;
         const T wgt = e.alpha * e.Tb;
         T dalpha = 0;
         for (int ch = 0; ch < 3; ++ch) {
-          const T c = rgb[3 * e.rec + ch];
+          const T c = mag(rgb[3 * e.rec + ch]);
           g[6 + ch] += wgt * dC[ch];
-          dalpha += dC[ch] * (c * e.Tb - S[ch] / (1 - e.alpha));
+          if (kMagnitude)
+            dalpha += dC[ch] * (c * e.Tb + S[ch] / (1 - e.alpha));
+          else
+            dalpha += dC[ch] * (c * e.Tb - S[ch] / (1 - e.alpha));
           S[ch] += c * wgt;
         }
         if (e.clamped) continue;
         const T a = conic[3 * e.rec], b = conic[3 * e.rec + 1], c = conic[3 * e.rec + 2];
         g[5] += dalpha * e.G;
         const T dpower = dalpha * e.alpha;
-        g[0] += dpower * (-(a * e.dx + b * e.dy));
-        g[1] += dpower * (-(c * e.dy + b * e.dx));
-        g[2] += dpower * ((T)(-0.5) * e.dx * e.dx);
-        g[3] += dpower * (-(e.dx * e.dy));
-        g[4] += dpower * ((T)(-0.5) * e.dy * e.dy);
+        if (kMagnitude) {
+          g[0] += dpower * (std::fabs(a * e.dx) + std::fabs(b * e.dy));
+          g[1] += dpower * (std::fabs(c * e.dy) + std::fabs(b * e.dx));
+        } else {
+          g[0] += dpower * (-(a * e.dx + b * e.dy));
+          g[1] += dpower * (-(c * e.dy + b * e.dx));
+        }
+        g[2] += mag(dpower * ((T)(-0.5) * e.dx * e.dx));
+        g[3] += mag(dpower * (-(e.dx * e.dy)));
+        g[4] += mag(dpower * ((T)(-0.5) * e.dy * e.dy));
       }
     }
+}
+
+template <class T>
+void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
+                    const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity,
+                    const T* rgb, const T* bg, const T* dimg, T* grad2d) {
+  blend_backward_impl<T, false>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity, rgb, bg,
+                                dimg, grad2d, nullptr);
 }
 
 // Chain rule from the per-view 2D quantities back to the 59 parameters of each Gaussian,
@@ -771,6 +797,13 @@ extern "C" {
                                            const T* rgb, const T* bg, const T* dimg, T* grad2d) {   \
     blend_backward<T>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity, rgb, bg,      \
                       dimg, grad2d);                                                               \
+  }                                                                                                \
+  ORC_EXPORT void orc_blend_backward_magnitude_##SUF(                                             \
+      int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges, const uint32_t* vals, \
+      const T* mean2d, const T* conic, const T* opacity, const T* rgb, const T* bg, const T* dimg,   \
+      T* grad2d_mag, uint32_t* terms) {                                                            \
+    blend_backward_impl<T, true>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity,    \
+                                 rgb, bg, dimg, grad2d_mag, terms);                               \
   }                                                                                                \
   ORC_EXPORT void orc_project_backward_##SUF(const T* params, int64_t n, int64_t stride,            \
                                              const double* cam, int W, int H, int tw, int th,       \

@@ -516,6 +516,64 @@ def test_float_and_double_oracles_agree():
 
 
 # ------------------------------------------------------------------------------------------
+# The rounding scale of the blend backward (used by the GPU parity bounds): the sum of the
+# magnitudes of every product entering each 2D gradient.  Pinned by a case without sums (it is
+# then |gradient|), by the triangle inequality and the term count, and by the rounding it bounds:
+# the fp32 backward's error against the fp64 backward on the same records lies within
+# gamma_k x magnitude (k = terms + the longest per-pixel chain + 16 roundings per term).
+# ------------------------------------------------------------------------------------------
+def test_backward_magnitude_single_term_equals_abs_gradient():
+    p = blank(1)
+    p[0:3, 0] = [0.0, 0.0, 3.0]  # on the optical axis: J diagonal, so the axis-aligned conic has b = 0
+    p[3:6, 0] = [math.log(0.01), math.log(0.02), math.log(0.015)]
+    p[10, 0] = 0.4
+    p[11:14, 0] = [0.7, 0.2, 0.4]
+    c = cam(1, 1, 100.0, cx=0.3, cy=-0.2)  # the one pixel (0, 0) sits off the mean: dx, dy != 0
+    r = oracle.render(p, [c], prec="f64", n=1)
+    assert r["outs"][0]["gp"][0, 0] == 1 and abs(r["rec"]["conic"][0, 1]) < 1e-15
+    L = r["lists"]
+    d = np.array([0.3, 0.1, 0.2]).reshape(3, 1, 1)  # positive: no sign mixing across channels
+    g = np.zeros((1, 9))
+    oracle.blend_backward((1, 1), 0, L["ranges"], L["vals"], r["rec"], d, g, prec="f64")
+    mag = np.zeros((1, 9))
+    terms = np.zeros(1, np.uint32)
+    oracle.blend_backward_magnitude((1, 1), 0, L["ranges"], L["vals"], r["rec"], d, mag, terms, prec="f64")
+    assert terms[0] == 1
+    assert np.allclose(mag, np.abs(g), rtol=1e-14, atol=0) and (mag[0, :2] > 0).all()
+
+
+def test_backward_magnitude_bounds_fp32_rounding():
+    u = 2.0 ** -24
+    p = gi.cube_scene(300, seed=10, stride=320)
+    c = Camera(**gi.identity_camera(96, 80, 96.0))
+    r = oracle.render(p, [c], prec="f32", n=300)
+    o = r["outs"][0]
+    assert o["margin"].min() > 1e-4  # no threshold tie: fp32 and fp64 blend the same pairs
+    L = r["lists"]
+    d = np.random.default_rng(10).normal(size=(3, 80, 96)).astype(np.float32) * 1e-4
+    rec64 = {k: v.astype(np.float64) for k, v in r["rec"].items()}
+    g32 = np.zeros((300, 9), np.float32)
+    oracle.blend_backward((96, 80), 0, L["ranges"], L["vals"], r["rec"], d, g32, prec="f32")
+    g64 = np.zeros((300, 9))
+    oracle.blend_backward((96, 80), 0, L["ranges"], L["vals"], rec64, d.astype(np.float64), g64, prec="f64")
+    mag = np.zeros((300, 9))
+    terms = np.zeros(300, np.uint32)
+    oracle.blend_backward_magnitude((96, 80), 0, L["ranges"], L["vals"], rec64, d.astype(np.float64), mag, terms,
+                                    prec="f64")
+    assert int(terms.sum()) == int(o["gp"].astype(np.int64).sum())
+    assert (mag >= np.abs(g64) * (1 - 1e-12)).all()
+    mag_neg = np.zeros((300, 9))
+    oracle.blend_backward_magnitude((96, 80), 0, L["ranges"], L["vals"], rec64, -d.astype(np.float64), mag_neg,
+                                    np.zeros(300, np.uint32), prec="f64")
+    assert np.array_equal(mag, mag_neg)
+    k = terms[:, None].astype(np.float64) + float(o["gp"].max()) + 16
+    gamma = k * u / (1 - k * u)
+    assert (np.abs(g32 - g64) <= gamma * mag).all()
+    # and the bound is not vacuous: cancellation makes |g| much smaller than the scale somewhere
+    assert (np.abs(g64) < 0.1 * mag).any()
+
+
+# ------------------------------------------------------------------------------------------
 # Schedule (Eq. 3-8): a hand-computed example and invariants.
 # ------------------------------------------------------------------------------------------
 def test_schedule_hand_example():
