@@ -68,6 +68,7 @@ def _declare(L):
         f.restype = F64
         getattr(L, f"orc_adam_{suf}").argtypes = [P, P, P, P, I64, I64, P, F64, F64, F64, I64]
         getattr(L, f"orc_sh_eval_{suf}").argtypes = [P, I64, P]
+    L.orc_project_backward_magnitude.argtypes = [P, I64, I64, P, I32, I32, I32, I32, P, P]
     L.orc_build_lists.argtypes = [I32, I64, P, P, I32, I32, P, P, P, I64, P, P, P]
     L.orc_build_lists.restype = I64
 
@@ -221,6 +222,21 @@ def project_backward(params, cam: Camera, grad2d, grads, tile=(16, 16), prec="f3
     getattr(lib(), f"orc_project_backward_{prec}")(
         _ptr(params), n, stride, _ptr(camp), cam.width, cam.height, tile[0], tile[1], _ptr(g2), _ptr(grads))
     return grads
+
+
+def project_backward_magnitude(params, cam: Camera, grad2d, grads_mag, tile=(16, 16), n=None):
+    """The rounding scale of project_backward's chain rule: accumulates into ``grads_mag`` (59, stride)
+    float64 the sum of the magnitudes of the products that make up each parameter gradient (fp64
+    evaluation of the same chain; see ``Mag`` in gs_oracle.cpp)."""
+    params = _c(params, np.float64)
+    stride = params.shape[1]
+    n = stride if n is None else n
+    g2 = _c(grad2d, np.float64)
+    assert grads_mag.dtype == np.float64 and grads_mag.flags.c_contiguous and grads_mag.shape == params.shape
+    camp = cam.packed()
+    lib().orc_project_backward_magnitude(_ptr(params), n, stride, _ptr(camp), cam.width, cam.height, tile[0],
+                                         tile[1], _ptr(g2), _ptr(grads_mag))
+    return grads_mag
 
 
 def loss(img, target, lam=0.2, want_grad=True, grad_scale=1.0, prec="f32"):

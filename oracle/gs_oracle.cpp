@@ -137,6 +137,9 @@ struct SH {
 // square of half-side r around (u, v), clamped to the grid.  Evaluated in the scalar type T.
 template <class T>
 void rect_of(T u, T v, int r, int tw, int th, int gx, int gy, int rect[4], T* margin) {
+  using std::fabs;
+  using std::floor;
+  using std::round;
   const T rr = (T)r;
   T q[4];
   q[0] = (u - rr) / (T)tw;
@@ -145,13 +148,13 @@ void rect_of(T u, T v, int r, int tw, int th, int gx, int gy, int rect[4], T* ma
   q[3] = ((v + rr) + (T)(th - 1)) / (T)th;
   const int lim[4] = {gx, gy, gx, gy};
   for (int k = 0; k < 4; ++k) {
-    T f = std::floor(q[k]);
+    T f = floor(q[k]);
     long long iv = (long long)f;
     if (iv < 0) iv = 0;
     if (iv > lim[k]) iv = lim[k];
     rect[k] = (int)iv;
     if (margin) {
-      T d = std::fabs(q[k] - std::round(q[k]));
+      T d = fabs(q[k] - round(q[k]));
       if (d < *margin) *margin = d;
     }
   }
@@ -186,6 +189,12 @@ struct Proj {
 template <class T>
 Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& cam, int tw, int th,
                     const SH<T>& sh) {
+  using std::ceil;
+  using std::exp;
+  using std::fabs;
+  using std::isfinite;
+  using std::round;
+  using std::sqrt;
   Proj<T> f;
   auto P = [&](int c) { return params[(int64_t)c * stride + i]; };
   const T mu[3] = {P(0), P(1), P(2)};
@@ -196,7 +205,7 @@ Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& ca
 
   // Eq. 1: Sigma = R S S^T R^T from the (normalised) quaternion and exp(log-scale).
   for (int k = 0; k < 4; ++k) f.q[k] = P(6 + k);
-  f.qlen = std::sqrt(f.q[0] * f.q[0] + f.q[1] * f.q[1] + f.q[2] * f.q[2] + f.q[3] * f.q[3]);
+  f.qlen = sqrt(f.q[0] * f.q[0] + f.q[1] * f.q[1] + f.q[2] * f.q[2] + f.q[3] * f.q[3]);
   if (!(f.qlen > 0)) return f;
   for (int k = 0; k < 4; ++k) f.qn[k] = f.q[k] / f.qlen;
   const T w = f.qn[0], x = f.qn[1], y = f.qn[2], z = f.qn[3];
@@ -209,7 +218,7 @@ Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& ca
   f.Rq[6] = 2 * (x * z - w * y);
   f.Rq[7] = 2 * (y * z + w * x);
   f.Rq[8] = 1 - 2 * (x * x + y * y);
-  for (int k = 0; k < 3; ++k) f.s[k] = std::exp(P(3 + k));
+  for (int k = 0; k < 3; ++k) f.s[k] = exp(P(3 + k));
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) f.M[3 * r + c] = f.Rq[3 * r + c] * f.s[c];
   for (int r = 0; r < 3; ++r)
@@ -260,18 +269,18 @@ Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& ca
   f.u = cam.fx * f.p[0] / pz + cam.cx;
   f.v = cam.fy * f.p[1] / pz + cam.cy;
   const T mid = (T)0.5 * (f.cov[0] + f.cov[2]);
-  f.lam = mid + std::sqrt(std::max((T)0.1, mid * mid - f.det));
-  f.rf = 3 * std::sqrt(f.lam);
-  f.radius = (int)std::ceil(f.rf);
+  f.lam = mid + sqrt(std::max((T)0.1, mid * mid - f.det));
+  f.rf = 3 * sqrt(f.lam);
+  f.radius = (int)ceil(f.rf);
   {
-    T d = std::fabs(f.rf - std::round(f.rf));
+    T d = fabs(f.rf - round(f.rf));
     if (d < f.margin) f.margin = d;
   }
   const int gx = (cam.W + tw - 1) / tw, gy = (cam.H + th - 1) / th;
   rect_of<T>(f.u, f.v, f.radius, tw, th, gx, gy, f.rect, &f.margin);
   if ((f.rect[2] - f.rect[0]) * (f.rect[3] - f.rect[1]) == 0) return f;
-  if (!(std::isfinite(f.u) && std::isfinite(f.v) && std::isfinite(f.conic[0]) &&
-        std::isfinite(f.conic[1]) && std::isfinite(f.conic[2])))
+  if (!(isfinite(f.u) && isfinite(f.v) && isfinite(f.conic[0]) &&
+        isfinite(f.conic[1]) && isfinite(f.conic[2])))
     return f;
 
   // Colour from degree-3 SH at the view direction (mean minus camera centre), + 0.5, >= 0.
@@ -279,7 +288,7 @@ Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& ca
   for (int c = 0; c < 3; ++c)
     campos[c] = -(cam.R[0 * 3 + c] * cam.t[0] + cam.R[1 * 3 + c] * cam.t[1] + cam.R[2 * 3 + c] * cam.t[2]);
   for (int c = 0; c < 3; ++c) f.dvec[c] = mu[c] - campos[c];
-  f.dlen = std::sqrt(f.dvec[0] * f.dvec[0] + f.dvec[1] * f.dvec[1] + f.dvec[2] * f.dvec[2]);
+  f.dlen = sqrt(f.dvec[0] * f.dvec[0] + f.dvec[1] * f.dvec[1] + f.dvec[2] * f.dvec[2]);
   for (int c = 0; c < 3; ++c) f.dir[c] = f.dvec[c] / f.dlen;
   sh.eval(f.dir[0], f.dir[1], f.dir[2], f.Y);
   f.clampbits = 0;
@@ -290,7 +299,7 @@ Proj<T> project_one(const T* params, int64_t i, int64_t stride, const Cam<T>& ca
     if (f.raw[ch] < 0) f.clampbits |= (uint8_t)(1u << ch);
     f.rgb[ch] = std::max((T)0, f.raw[ch]);
   }
-  f.opacity = (T)1 / ((T)1 + std::exp(-P(10)));
+  f.opacity = (T)1 / ((T)1 + exp(-P(10)));
   f.visible = true;
   return f;
 }
@@ -465,9 +474,12 @@ void blend_forward(int W, int H, int tw, int th, int64_t tile_base, const uint32
 // masks.  grad2d per record: d mean2d (2), d conic (a, b, c), d opacity, d rgb (3).
 //
 // With kMagnitude the same walk accumulates, instead of each gradient, the sum of the absolute
-// values of every elementary product that enters it (|dL/dC| |c| T, the colour behind a
-// contributor as a sum of magnitudes, |a dx| + |b dy| for the mean, ...), and terms[rec] counts the
-// (pixel, contributor) terms summed into the record.  That is the scale of the componentwise
+// values of every elementary product that enters it (|dL/dC| |c| T, |a dx| + |b dy| for the mean,
+// ...), and terms[rec] counts the (pixel, contributor) terms summed into the record.  The colour
+// behind a contributor enters at the scale of the pixel's whole colour (sum of |c| alpha T over
+// all contributors plus |bg| T): it equals the pixel colour minus the colour in front, and a
+// front-to-back evaluation obtains it as that difference, whose rounding is relative to the
+// operands.  That is the scale of the componentwise
 // rounding-error bound of the sum (Higham, "Accuracy and Stability of Numerical Algorithms", Sec.
 // 4.2: |fl(sum) - sum| <= gamma_k sum |x_i| for k terms): a parity check uses it for the entries
 // whose terms cancel.
@@ -490,6 +502,9 @@ void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const 
         dC[ch] = mag(dimg[ch * HW + pix]);
         S[ch] = mag(bg[ch]) * w.trans;
       }
+      if (kMagnitude)  // the scale of the colour behind any contributor: the pixel's whole colour
+        for (const auto& e : w.contrib)
+          for (int ch = 0; ch < 3; ++ch) S[ch] += std::fabs(rgb[3 * e.rec + ch]) * e.alpha * e.Tb;
       for (int k = (int)w.contrib.size() - 1; k >= 0; --k) {
         const auto& e = w.contrib[k];
         T* g = grad2d + 9 * (int64_t)e.rec;
@@ -499,11 +514,12 @@ void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const 
         for (int ch = 0; ch < 3; ++ch) {
           const T c = mag(rgb[3 * e.rec + ch]);
           g[6 + ch] += wgt * dC[ch];
-          if (kMagnitude)
+          if (kMagnitude) {
             dalpha += dC[ch] * (c * e.Tb + S[ch] / (1 - e.alpha));
-          else
+          } else {
             dalpha += dC[ch] * (c * e.Tb - S[ch] / (1 - e.alpha));
-          S[ch] += c * wgt;
+            S[ch] += c * wgt;
+          }
         }
         if (e.clamped) continue;
         const T a = conic[3 * e.rec], b = conic[3 * e.rec + 1], c = conic[3 * e.rec + 2];
@@ -531,6 +547,116 @@ void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint3
                                 dimg, grad2d, nullptr);
 }
 
+// Chain rule of one visible Gaussian in one view: its 2D gradient g2 (9 values) back to its 59
+// parameters, accumulated through G(c); P(c) reads its parameters.
+template <class T, class PF, class GF>
+void chain_one(const Proj<T>& f, const Cam<T>& cam, const SH<T>& sh, const T* g2, PF P, GF G) {
+  T dmu[3] = {0, 0, 0};
+  T dp[3] = {0, 0, 0};
+
+  // opacity = sigmoid(logit)
+  G(10) += g2[5] * f.opacity * (1 - f.opacity);
+
+  // colour -> SH coefficients and view direction
+  T ddir[3] = {0, 0, 0};
+  T dY[16][3];
+  sh.grad(f.dir[0], f.dir[1], f.dir[2], dY);
+  for (int ch = 0; ch < 3; ++ch) {
+    if (f.clampbits & (1u << ch)) continue;
+    const T dcol = g2[6 + ch];
+    for (int k = 0; k < 16; ++k) {
+      G(11 + 3 * k + ch) += f.Y[k] * dcol;
+      for (int a = 0; a < 3; ++a) ddir[a] += dY[k][a] * P(11 + 3 * k + ch) * dcol;
+    }
+  }
+  const T dd = f.dir[0] * ddir[0] + f.dir[1] * ddir[1] + f.dir[2] * ddir[2];
+  for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - f.dir[a] * dd) / f.dlen;
+
+  // conic = inverse of the dilated covariance (a', b', c'), written out per entry
+  const T A = f.cov[0], B = f.cov[1], C = f.cov[2], det = f.det, det2 = det * det;
+  const T dA = g2[2], dB = g2[3], dC = g2[4];
+  const T da = dA * (-C * C / det2) + dB * (B * C / det2) + dC * (1 / det - A * C / det2);
+  const T db = dA * (2 * B * C / det2) + dB * (-1 / det - 2 * B * B / det2) + dC * (2 * A * B / det2);
+  const T dc = dA * (1 / det - A * C / det2) + dB * (A * B / det2) + dC * (-A * A / det2);
+
+  // (a, b, c) = entries of Tm Sigma Tm^T, Tm = J R_cam (2 x 3)
+  T dSig[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      dSig[3 * r + c] = da * f.Tm[r] * f.Tm[c] + db * f.Tm[r] * f.Tm[3 + c] + dc * f.Tm[3 + r] * f.Tm[3 + c];
+  T dTm[6] = {0, 0, 0, 0, 0, 0};
+  for (int r = 0; r < 3; ++r) {
+    T s00 = 0, s01 = 0, s10 = 0, s11 = 0;
+    for (int k = 0; k < 3; ++k) {
+      const T sym = f.Sig[3 * r + k] + f.Sig[3 * k + r];
+      s00 += sym * f.Tm[k];
+      s11 += sym * f.Tm[3 + k];
+      s01 += f.Sig[3 * r + k] * f.Tm[3 + k];
+      s10 += f.Sig[3 * k + r] * f.Tm[k];
+    }
+    dTm[r] += da * s00 + db * s01;
+    dTm[3 + r] += dc * s11 + db * s10;
+  }
+  T dJ[6];
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 3; ++c) {
+      T acc = 0;
+      for (int k = 0; k < 3; ++k) acc += dTm[3 * r + k] * cam.R[3 * c + k];
+      dJ[3 * r + c] = acc;
+    }
+  const T x = f.p[0], y = f.p[1], z = f.p[2], z2 = z * z, z3 = z2 * z;
+  dp[2] += dJ[0] * (-cam.fx / z2) + dJ[4] * (-cam.fy / z2);
+  if (f.xin) {
+    dp[0] += dJ[2] * (-cam.fx / z2);
+    dp[2] += dJ[2] * (2 * cam.fx * x / z3);
+  } else {
+    dp[2] += dJ[2] * (cam.fx * f.txz / z2);
+  }
+  if (f.yin) {
+    dp[1] += dJ[5] * (-cam.fy / z2);
+    dp[2] += dJ[5] * (2 * cam.fy * y / z3);
+  } else {
+    dp[2] += dJ[5] * (cam.fy * f.tyz / z2);
+  }
+  // mean2d = (fx x/z + cx, fy y/z + cy)
+  dp[0] += g2[0] * cam.fx / z;
+  dp[2] += g2[0] * (-cam.fx * x / z2);
+  dp[1] += g2[1] * cam.fy / z;
+  dp[2] += g2[1] * (-cam.fy * y / z2);
+  for (int a = 0; a < 3; ++a)
+    dmu[a] += cam.R[0 * 3 + a] * dp[0] + cam.R[1 * 3 + a] * dp[1] + cam.R[2 * 3 + a] * dp[2];
+  for (int a = 0; a < 3; ++a) G(a) += dmu[a];
+
+  // Sigma = M M^T, M = R_q diag(s)
+  T dM[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      T acc = 0;
+      for (int k = 0; k < 3; ++k) acc += (dSig[3 * r + k] + dSig[3 * k + r]) * f.M[3 * k + c];
+      dM[3 * r + c] = acc;
+    }
+  T dRq[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) dRq[3 * r + c] = dM[3 * r + c] * f.s[c];
+  for (int c = 0; c < 3; ++c) {
+    T ds = 0;
+    for (int r = 0; r < 3; ++r) ds += dM[3 * r + c] * f.Rq[3 * r + c];
+    G(3 + c) += ds * f.s[c];
+  }
+  const T w = f.qn[0], qx = f.qn[1], qy = f.qn[2], qz = f.qn[3];
+  T dqn[4];
+  dqn[0] = dRq[1] * (-2 * qz) + dRq[2] * (2 * qy) + dRq[3] * (2 * qz) + dRq[5] * (-2 * qx) +
+           dRq[6] * (-2 * qy) + dRq[7] * (2 * qx);
+  dqn[1] = dRq[1] * (2 * qy) + dRq[2] * (2 * qz) + dRq[3] * (2 * qy) + dRq[4] * (-4 * qx) +
+           dRq[5] * (-2 * w) + dRq[6] * (2 * qz) + dRq[7] * (2 * w) + dRq[8] * (-4 * qx);
+  dqn[2] = dRq[0] * (-4 * qy) + dRq[1] * (2 * qx) + dRq[2] * (2 * w) + dRq[3] * (2 * qx) +
+           dRq[5] * (2 * qz) + dRq[6] * (-2 * w) + dRq[7] * (2 * qz) + dRq[8] * (-4 * qy);
+  dqn[3] = dRq[0] * (-4 * qz) + dRq[1] * (-2 * w) + dRq[2] * (2 * qx) + dRq[3] * (2 * w) +
+           dRq[4] * (-4 * qz) + dRq[5] * (2 * qy) + dRq[6] * (2 * qx) + dRq[7] * (2 * qy);
+  const T qd = f.qn[0] * dqn[0] + f.qn[1] * dqn[1] + f.qn[2] * dqn[2] + f.qn[3] * dqn[3];
+  for (int k = 0; k < 4; ++k) G(6 + k) += (dqn[k] - f.qn[k] * qd) / f.qlen;
+}
+
 // Chain rule from the per-view 2D quantities back to the 59 parameters of each Gaussian,
 // accumulated into grads (component-major, same stride as params).
 template <class T>
@@ -541,113 +667,9 @@ void project_backward(const T* params, int64_t n, int64_t stride, const double* 
   for (int64_t i = 0; i < n; ++i) {
     const Proj<T> f = project_one<T>(params, i, stride, cam, tw, th, sh);
     if (!f.visible) continue;
-    const T* g2 = grad2d + 9 * i;
     auto G = [&](int c) -> T& { return grads[(int64_t)c * stride + i]; };
     auto P = [&](int c) { return params[(int64_t)c * stride + i]; };
-    T dmu[3] = {0, 0, 0};
-    T dp[3] = {0, 0, 0};
-
-    // opacity = sigmoid(logit)
-    G(10) += g2[5] * f.opacity * (1 - f.opacity);
-
-    // colour -> SH coefficients and view direction
-    T ddir[3] = {0, 0, 0};
-    T dY[16][3];
-    sh.grad(f.dir[0], f.dir[1], f.dir[2], dY);
-    for (int ch = 0; ch < 3; ++ch) {
-      if (f.clampbits & (1u << ch)) continue;
-      const T dcol = g2[6 + ch];
-      for (int k = 0; k < 16; ++k) {
-        G(11 + 3 * k + ch) += f.Y[k] * dcol;
-        for (int a = 0; a < 3; ++a) ddir[a] += dY[k][a] * P(11 + 3 * k + ch) * dcol;
-      }
-    }
-    const T dd = f.dir[0] * ddir[0] + f.dir[1] * ddir[1] + f.dir[2] * ddir[2];
-    for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - f.dir[a] * dd) / f.dlen;
-
-    // conic = inverse of the dilated covariance (a', b', c'), written out per entry
-    const T A = f.cov[0], B = f.cov[1], C = f.cov[2], det = f.det, det2 = det * det;
-    const T dA = g2[2], dB = g2[3], dC = g2[4];
-    const T da = dA * (-C * C / det2) + dB * (B * C / det2) + dC * (1 / det - A * C / det2);
-    const T db = dA * (2 * B * C / det2) + dB * (-1 / det - 2 * B * B / det2) + dC * (2 * A * B / det2);
-    const T dc = dA * (1 / det - A * C / det2) + dB * (A * B / det2) + dC * (-A * A / det2);
-
-    // (a, b, c) = entries of Tm Sigma Tm^T, Tm = J R_cam (2 x 3)
-    T dSig[9];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c)
-        dSig[3 * r + c] = da * f.Tm[r] * f.Tm[c] + db * f.Tm[r] * f.Tm[3 + c] + dc * f.Tm[3 + r] * f.Tm[3 + c];
-    T dTm[6] = {0, 0, 0, 0, 0, 0};
-    for (int r = 0; r < 3; ++r) {
-      T s00 = 0, s01 = 0, s10 = 0, s11 = 0;
-      for (int k = 0; k < 3; ++k) {
-        const T sym = f.Sig[3 * r + k] + f.Sig[3 * k + r];
-        s00 += sym * f.Tm[k];
-        s11 += sym * f.Tm[3 + k];
-        s01 += f.Sig[3 * r + k] * f.Tm[3 + k];
-        s10 += f.Sig[3 * k + r] * f.Tm[k];
-      }
-      dTm[r] += da * s00 + db * s01;
-      dTm[3 + r] += dc * s11 + db * s10;
-    }
-    T dJ[6];
-    for (int r = 0; r < 2; ++r)
-      for (int c = 0; c < 3; ++c) {
-        T acc = 0;
-        for (int k = 0; k < 3; ++k) acc += dTm[3 * r + k] * cam.R[3 * c + k];
-        dJ[3 * r + c] = acc;
-      }
-    const T x = f.p[0], y = f.p[1], z = f.p[2], z2 = z * z, z3 = z2 * z;
-    dp[2] += dJ[0] * (-cam.fx / z2) + dJ[4] * (-cam.fy / z2);
-    if (f.xin) {
-      dp[0] += dJ[2] * (-cam.fx / z2);
-      dp[2] += dJ[2] * (2 * cam.fx * x / z3);
-    } else {
-      dp[2] += dJ[2] * (cam.fx * f.txz / z2);
-    }
-    if (f.yin) {
-      dp[1] += dJ[5] * (-cam.fy / z2);
-      dp[2] += dJ[5] * (2 * cam.fy * y / z3);
-    } else {
-      dp[2] += dJ[5] * (cam.fy * f.tyz / z2);
-    }
-    // mean2d = (fx x/z + cx, fy y/z + cy)
-    dp[0] += g2[0] * cam.fx / z;
-    dp[2] += g2[0] * (-cam.fx * x / z2);
-    dp[1] += g2[1] * cam.fy / z;
-    dp[2] += g2[1] * (-cam.fy * y / z2);
-    for (int a = 0; a < 3; ++a)
-      dmu[a] += cam.R[0 * 3 + a] * dp[0] + cam.R[1 * 3 + a] * dp[1] + cam.R[2 * 3 + a] * dp[2];
-    for (int a = 0; a < 3; ++a) G(a) += dmu[a];
-
-    // Sigma = M M^T, M = R_q diag(s)
-    T dM[9];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) {
-        T acc = 0;
-        for (int k = 0; k < 3; ++k) acc += (dSig[3 * r + k] + dSig[3 * k + r]) * f.M[3 * k + c];
-        dM[3 * r + c] = acc;
-      }
-    T dRq[9];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) dRq[3 * r + c] = dM[3 * r + c] * f.s[c];
-    for (int c = 0; c < 3; ++c) {
-      T ds = 0;
-      for (int r = 0; r < 3; ++r) ds += dM[3 * r + c] * f.Rq[3 * r + c];
-      G(3 + c) += ds * f.s[c];
-    }
-    const T w = f.qn[0], qx = f.qn[1], qy = f.qn[2], qz = f.qn[3];
-    T dqn[4];
-    dqn[0] = dRq[1] * (-2 * qz) + dRq[2] * (2 * qy) + dRq[3] * (2 * qz) + dRq[5] * (-2 * qx) +
-             dRq[6] * (-2 * qy) + dRq[7] * (2 * qx);
-    dqn[1] = dRq[1] * (2 * qy) + dRq[2] * (2 * qz) + dRq[3] * (2 * qy) + dRq[4] * (-4 * qx) +
-             dRq[5] * (-2 * w) + dRq[6] * (2 * qz) + dRq[7] * (2 * w) + dRq[8] * (-4 * qx);
-    dqn[2] = dRq[0] * (-4 * qy) + dRq[1] * (2 * qx) + dRq[2] * (2 * w) + dRq[3] * (2 * qx) +
-             dRq[5] * (2 * qz) + dRq[6] * (-2 * w) + dRq[7] * (2 * qz) + dRq[8] * (-4 * qy);
-    dqn[3] = dRq[0] * (-4 * qz) + dRq[1] * (-2 * w) + dRq[2] * (2 * qx) + dRq[3] * (2 * w) +
-             dRq[4] * (-4 * qz) + dRq[5] * (2 * qy) + dRq[6] * (2 * qx) + dRq[7] * (2 * qy);
-    const T qd = f.qn[0] * dqn[0] + f.qn[1] * dqn[1] + f.qn[2] * dqn[2] + f.qn[3] * dqn[3];
-    for (int k = 0; k < 4; ++k) G(6 + k) += (dqn[k] - f.qn[k] * qd) / f.qlen;
+    chain_one<T>(f, cam, sh, grad2d + 9 * i, P, G);
   }
 }
 
@@ -768,6 +790,59 @@ void sh_eval_export(const T* dirs, int64_t n, T* out) {
   for (int64_t i = 0; i < n; ++i) sh.eval(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], out + 16 * i);
 }
 
+// The rounding scale of the projection and its chain rule: a value carried with the sum of the
+// magnitudes of the products it was built from (a sum or difference adds the magnitudes, a product
+// multiplies them, a quotient divides by the divisor's magnitude; an input, and the result of a
+// square root or an exponential, is its own magnitude).  Evaluating the projection and the chain
+// in this type gives, per parameter gradient, the sum of |products| of the componentwise
+// rounding-error bound (Higham, "Accuracy and Stability of Numerical Algorithms", Sec. 3.1-3.3):
+// |fl(g) - g| <= gamma_k x magnitude for an evaluation of depth k.  Branch decisions (clamps,
+// visibility, the tile rectangle) are taken on the values.
+struct Mag {
+  double v, m;
+  Mag(double x = 0.0) : v(x), m(std::fabs(x)) {}
+  Mag(double x, double mm) : v(x), m(mm) {}
+  explicit operator double() const { return v; }
+  explicit operator int() const { return (int)v; }
+  explicit operator long long() const { return (long long)v; }
+};
+inline Mag operator+(Mag a, Mag b) { return Mag(a.v + b.v, a.m + b.m); }
+inline Mag operator-(Mag a, Mag b) { return Mag(a.v - b.v, a.m + b.m); }
+inline Mag operator-(Mag a) { return Mag(-a.v, a.m); }
+inline Mag operator*(Mag a, Mag b) { return Mag(a.v * b.v, a.m * b.m); }
+inline Mag operator/(Mag a, Mag b) { return Mag(a.v / b.v, a.m / std::fabs(b.v)); }
+inline Mag& operator+=(Mag& a, Mag b) { return a = a + b; }
+inline bool operator<(Mag a, Mag b) { return a.v < b.v; }
+inline bool operator>(Mag a, Mag b) { return a.v > b.v; }
+inline bool operator<=(Mag a, Mag b) { return a.v <= b.v; }
+inline bool operator>=(Mag a, Mag b) { return a.v >= b.v; }
+inline Mag sqrt(Mag a) { return Mag(std::sqrt(a.v)); }
+inline Mag exp(Mag a) { return Mag(std::exp(a.v)); }
+inline Mag floor(Mag a) { return Mag(std::floor(a.v)); }
+inline Mag ceil(Mag a) { return Mag(std::ceil(a.v)); }
+inline Mag round(Mag a) { return Mag(std::round(a.v)); }
+inline Mag fabs(Mag a) { return Mag(std::fabs(a.v), a.m); }
+inline bool isfinite(Mag a) { return std::isfinite(a.v); }
+
+// Magnitudes of the products that make up each parameter gradient of the projection backward
+// (accumulated into grads_mag, component-major like params), for fp64 parameters and 2D gradients.
+void project_backward_magnitude(const double* params, int64_t n, int64_t stride, const double* camd, int W,
+                                int H, int tw, int th, const double* grad2d, double* grads_mag) {
+  const Cam<Mag> cam = load_cam<Mag>(camd, W, H);
+  const SH<Mag> sh;
+  for (int64_t i = 0; i < n; ++i) {
+    Mag pm[kParams], g2[9], acc[kParams];
+    for (int c = 0; c < kParams; ++c) pm[c] = Mag(params[(int64_t)c * stride + i]);
+    const Proj<Mag> f = project_one<Mag>(pm, 0, 1, cam, tw, th, sh);
+    if (!f.visible) continue;
+    for (int k = 0; k < 9; ++k) g2[k] = Mag(grad2d[9 * i + k]);
+    auto G = [&](int c) -> Mag& { return acc[c]; };
+    auto P = [&](int c) { return pm[c]; };
+    chain_one<Mag>(f, cam, sh, g2, P, G);
+    for (int c = 0; c < kParams; ++c) grads_mag[(int64_t)c * stride + i] += acc[c].m;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -825,6 +900,12 @@ extern "C" {
 
 ORC_INSTANTIATE(float, f32)
 ORC_INSTANTIATE(double, f64)
+
+ORC_EXPORT void orc_project_backward_magnitude(const double* params, int64_t n, int64_t stride,
+                                               const double* cam, int W, int H, int tw, int th,
+                                               const double* grad2d, double* grads_mag) {
+  project_backward_magnitude(params, n, stride, cam, W, H, tw, th, grad2d, grads_mag);
+}
 
 ORC_EXPORT int64_t orc_build_lists(int V, int64_t n, const int* Ws, const int* Hs, int tw, int th,
                                    const float* mean2d, const int32_t* radius, const float* depth,

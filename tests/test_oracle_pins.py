@@ -517,8 +517,8 @@ def test_float_and_double_oracles_agree():
 
 # ------------------------------------------------------------------------------------------
 # The rounding scale of the blend backward (used by the GPU parity bounds): the sum of the
-# magnitudes of every product entering each 2D gradient.  Pinned by a case without sums (it is
-# then |gradient|), by the triangle inequality and the term count, and by the rounding it bounds:
+# magnitudes of every product entering each 2D gradient.  Pinned by a one-term case (closed form),
+# by the triangle inequality and the term count, and by the rounding it bounds:
 # the fp32 backward's error against the fp64 backward on the same records lies within
 # gamma_k x magnitude (k = terms + the longest per-pixel chain + 16 roundings per term).
 # ------------------------------------------------------------------------------------------
@@ -539,7 +539,12 @@ def test_backward_magnitude_single_term_equals_abs_gradient():
     terms = np.zeros(1, np.uint32)
     oracle.blend_backward_magnitude((1, 1), 0, L["ranges"], L["vals"], r["rec"], d, mag, terms, prec="f64")
     assert terms[0] == 1
-    assert np.allclose(mag, np.abs(g), rtol=1e-14, atol=0) and (mag[0, :2] > 0).all()
+    # colour entries: one product each, the magnitude is |gradient|; the entries through alpha also
+    # carry the colour behind at the scale of the pixel's colour c alpha T (T = 1 in front), so
+    # d alpha's magnitude is dC c (1 + alpha / (1 - alpha)) = |d alpha| / (1 - alpha)
+    alpha = 1.0 - r["outs"][0]["T"][0, 0]
+    assert np.allclose(mag[0, 6:], np.abs(g[0, 6:]), rtol=1e-14, atol=0)
+    assert np.allclose(mag[0, :6], np.abs(g[0, :6]) / (1 - alpha), rtol=1e-13, atol=0) and (mag[0, :2] > 0).all()
 
 
 def test_backward_magnitude_bounds_fp32_rounding():
@@ -571,6 +576,51 @@ def test_backward_magnitude_bounds_fp32_rounding():
     assert (np.abs(g32 - g64) <= gamma * mag).all()
     # and the bound is not vacuous: cancellation makes |g| much smaller than the scale somewhere
     assert (np.abs(g64) < 0.1 * mag).any()
+
+
+def test_chain_magnitude_closed_forms():
+    """One Gaussian on the optical axis, camera centre at the origin: the view direction is exactly
+    +z, so the SH products are c0, c1 z, c2b (2 z z - x x - y y), c3d z (2 z z - 3 x x - 3 y y) with
+    x = y = 0: the SH rows' magnitudes are |dcol| x (c0, c1, 2 c2b, 2 c3d) for k = 0, 2, 6, 12 and 0
+    for the other coefficients; the opacity row g2[5] o (1 - o) has magnitude |g2[5]| o (1 + o)."""
+    p = blank(1, dtype=np.float64)
+    p[2, 0] = 3.0
+    p[3:6, 0] = math.log(0.05)
+    p[10, 0] = 0.3
+    p[11:14, 0] = 0.2
+    c = cam(32, 32, 40.0)
+    g2 = np.array([[0.1, -0.2, 0.3, 0.05, -0.4, 0.7, 0.25, -0.5, 0.125]])
+    mag = np.zeros((59, 32))
+    oracle.project_backward_magnitude(p, c, g2, mag, n=1)
+    pi = math.pi
+    mY = np.zeros(16)
+    mY[0] = 0.5 / math.sqrt(pi)
+    mY[2] = math.sqrt(3 / (4 * pi))
+    mY[6] = 2 * 0.25 * math.sqrt(5 / pi)
+    mY[12] = 2 * 0.25 * math.sqrt(7 / pi)
+    for k in range(16):
+        for ch in range(3):
+            assert mag[11 + 3 * k + ch, 0] == pytest.approx(abs(g2[0, 6 + ch]) * mY[k], rel=1e-14, abs=1e-300)
+    o = 1 / (1 + math.exp(-0.3))
+    assert mag[10, 0] == pytest.approx(0.7 * o * (1 + o), rel=1e-14)
+
+
+def test_chain_magnitude_bounds_fp32_rounding():
+    u = 2.0 ** -24
+    p = gi.cube_scene(2000, seed=3, stride=2016, logscale=(-2.5, 0.5))
+    p[11, ::7] = -3.0  # some clamped colour channels
+    c = Camera(**gi.identity_camera(96, 80, 96.0))
+    g2 = np.random.default_rng(0).normal(size=(2016, 9)).astype(np.float32)
+    g32 = np.zeros((59, 2016), np.float32)
+    oracle.project_backward(p, c, g2, g32, prec="f32", n=2000)
+    g64 = np.zeros((59, 2016))
+    oracle.project_backward(p.astype(np.float64), c, g2.astype(np.float64), g64, prec="f64", n=2000)
+    mag = np.zeros((59, 2016))
+    oracle.project_backward_magnitude(p, c, g2, mag, n=2000)
+    assert (mag >= np.abs(g64) * (1 - 1e-12)).all()
+    k = 64
+    assert (np.abs(g32 - g64) <= k * u / (1 - k * u) * mag).all()
+    assert (np.abs(g64) < 0.01 * mag).sum() > 1000  # cancellation: relative bounds alone would not hold
 
 
 # ------------------------------------------------------------------------------------------
