@@ -105,12 +105,19 @@ GS_API gs_status gs_raster_forward(gs_raster* r, void* stream, const float* para
                             const gs_camera* cams, int n_views, const float bg[3], float* out_image,
                             float* out_T, uint32_t* out_last, uint32_t* out_gp, uint64_t* out_pairs);
 
-/* K7 on the views of the last forward: L = mean over views of
- * (1 - lambda_ssim) mean|X - Y| + lambda_ssim (1 - mean SSIM(X, Y)) (11x11 Gaussian window,
- * sigma 1.5, zero padding).  image/target (device) are packed like out_image.  out_dimage
+/* Weights of the loss terms of Eq. 10: lambda_l1 L1 + lambda_ssim D-SSIM + lambda_load L_load. */
+typedef struct gs_loss_weights {
+  float lambda_l1, lambda_ssim, lambda_load;
+} gs_loss_weights;
+
+/* K7 on the views of the last forward (Eq. 10): L = mean over views of
+ * lambda_l1 mean|X - Y| + lambda_ssim (1 - mean SSIM(X, Y)) (11x11 Gaussian window, sigma 1.5,
+ * zero padding, C1 = 0.01^2, C2 = 0.03^2, means over 3 H W), plus lambda_load L_load when that weight
+ * is > 0.  w (host, nullable; NULL = 3DGS's 0.8 / 0.2 / 0) must hold weights >= 0
+ * (GS_ERR_INVALID_ARG otherwise).  image/target (device) are packed like out_image.  out_dimage
  * (device, nullable) receives dL/dimage.  out_loss (host, nullable) receives L and synchronises. */
-GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, const float* target, float lambda_ssim,
-                         float* out_dimage, double* out_loss);
+GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, const float* target,
+                                const gs_loss_weights* w, float* out_dimage, double* out_loss);
 
 /* K8 + K9: gradients of a scalar loss with respect to the parameters of the last forward,
  * given dL/dimage (device, packed like out_image).  image and last are the forward's outputs.

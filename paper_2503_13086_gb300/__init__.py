@@ -65,6 +65,10 @@ class Tiling(ctypes.Structure):
         return (self.tile_w, self.tile_h, self.batch)
 
 
+class LossWeights(ctypes.Structure):
+    _fields_ = [("lambda_l1", ctypes.c_float), ("lambda_ssim", ctypes.c_float), ("lambda_load", ctypes.c_float)]
+
+
 class AutotuneResult(ctypes.Structure):
     _fields_ = [("chosen", Tiling), ("n_candidates", ctypes.c_int32), ("candidates", Tiling * MAX_TILINGS),
                 ("ms", ctypes.c_float * MAX_TILINGS)]
@@ -119,7 +123,7 @@ SYMBOLS = {
     "gs_raster_create": ([P], I32),
     "gs_raster_destroy": ([P], I32),
     "gs_raster_forward": ([P, P, P, I64, I64, P, ctypes.c_int, P, P, P, P, P, P], I32),
-    "gs_raster_loss": ([P, P, P, P, F32, P, P], I32),
+    "gs_raster_loss": ([P, P, P, P, P, P, P], I32),
     "gs_raster_backward": ([P, P, P, P, P, P, P, P], I32),
     "gs_adam_step": ([P, P, P, P, P, I64, I64, P, F32, F32, F32, I64], I32),
     "gs_raster_read": ([P, ctypes.c_int, P, ctypes.c_size_t, P], I32),
@@ -265,12 +269,14 @@ class Raster:
         self.generation += 1
         return dict(image=image, T=T, last=last, gp=gp, pairs=int(pairs.value), sizes=sizes)
 
-    def loss(self, image, target, lambda_ssim=0.2, want_grad=True, stream=None):
+    def loss(self, image, target, lambda_ssim=0.2, want_grad=True, stream=None, lambda_l1=None, lambda_load=0.0):
+        """Eq. 10 on the last forward's views; lambda_l1 defaults to 1 - lambda_ssim."""
         torch = _torch()
         dimage = torch.empty_like(image) if want_grad else None
         out = ctypes.c_double()
+        w = LossWeights(1.0 - lambda_ssim if lambda_l1 is None else lambda_l1, lambda_ssim, lambda_load)
         _check(self._lib.gs_raster_loss(self._h, _stream(stream), _ptr(image), _ptr(target.contiguous()),
-                                        float(lambda_ssim), _ptr(dimage), ctypes.byref(out)))
+                                        ctypes.byref(w), _ptr(dimage), ctypes.byref(out)))
         return float(out.value), dimage
 
     def backward(self, params, image, last, dimage, want_grad2d=False, stream=None):

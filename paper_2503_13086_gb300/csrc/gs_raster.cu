@@ -501,8 +501,8 @@ gs_status gs_raster_forward(gs_raster* rr, void* stream, const float* params, in
   return GS_OK;
 }
 
-gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const float* target, float lambda_ssim,
-                         float* out_dimage, double* out_loss) {
+gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const float* target,
+                         const gs_loss_weights* w, float* out_dimage, double* out_loss) {
   gs::Raster* r = reinterpret_cast<gs::Raster*>(rr);
   if (!r || !image || !target) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (!r->have_forward) return fail(GS_ERR_STATE, "gs_raster_loss needs a forward first");
@@ -510,9 +510,12 @@ gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const 
   for (auto& V : r->views) V.target = target + 3 * V.pix_base;
   gs_status st;
   if ((st = r->stage(s))) return st;
-  r->sp_h->lambda_ssim = lambda_ssim;
-  r->sp_h->lambda_l1 = 1.f - lambda_ssim;
-  r->sp_h->lambda_load = 0.f;
+  const gs_loss_weights lw = w ? *w : gs_loss_weights{0.8f, 0.2f, 0.f};
+  if (!(lw.lambda_l1 >= 0.f) || !(lw.lambda_ssim >= 0.f) || !(lw.lambda_load >= 0.f))
+    return fail(GS_ERR_INVALID_ARG, "loss weights must be >= 0");
+  r->sp_h->lambda_ssim = lw.lambda_ssim;
+  r->sp_h->lambda_l1 = lw.lambda_l1;
+  r->sp_h->lambda_load = lw.lambda_load;
   r->upload(s);
   r->enqueue_loss(s, image, out_dimage);
   cudaError_t e = cudaGetLastError();

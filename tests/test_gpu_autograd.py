@@ -1,12 +1,12 @@
 """The hand-written backward behind torch.autograd: batched views at mixed sizes, gradients of a
 64-Gaussian subset against central finite differences of the same CUDA forward, and agreement
-with the oracle's gradient."""
+with the oracle's gradient (bounds and exemptions: tests/parity.py)."""
 import numpy as np
 import pytest
 
 import gsinputs as gi
-import oracle
-from helpers import ocam, grad_close
+from helpers import gpu_forward
+from parity import backward_parity, fd_check
 
 pytestmark = pytest.mark.gpu
 
@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 def test_autograd_matches_finite_differences_and_oracle():
     import torch
     import paper_2503_13086_gb300 as gs
-    from paper_2503_13086_gb300.autograd import rasterize, unpack
+    from paper_2503_13086_gb300.autograd import rasterize
     n = 600
     p = gi.cube_scene(n, seed=11, stride=608, logscale=(-2.6, 0.3))
     cams = [gi.identity_camera(72, 56, 70.0), gi.identity_camera(48, 40, 45.0)]
@@ -30,44 +30,14 @@ def test_autograd_matches_finite_differences_and_oracle():
     loss.backward()
     g = P.grad.detach().cpu().numpy()
 
-    # oracle gradient of the same linear loss
-    views = unpack(weights, cams)
-    r = oracle.render(p, [ocam(c) for c in cams], prec="f32", n=n)
-    g2 = np.zeros((len(cams) * n, 9), np.float32)  # oracle records are view * n + i
-    for v, c in enumerate(cams):
-        oracle.blend_backward((c["width"], c["height"]), r["lists"]["tile_base"][v], r["lists"]["ranges"],
-                              r["lists"]["vals"], r["rec"], views[v].cpu().numpy(), g2, prec="f32")
-    g_ref = np.zeros_like(p)
-    for v, c in enumerate(cams):
-        oracle.project_backward(p, ocam(c), g2[v * n:(v + 1) * n], g_ref, prec="f32", n=n)
-    assert grad_close(g[:, :n], g_ref[:, :n]).mean() < 1e-3
+    # the same linear loss through the stateless raster: each backward stage against the oracle
+    # on the same inputs (tests/parity.py), and the autograd result equal to it
+    gg = gpu_forward(ras, p, n, cams)
+    grads, _ = backward_parity("autograd three views", ras, gg, p, n, cams, weights)
+    assert np.array_equal(g[:, :n], grads[:, :n])
 
-    # central differences of the CUDA forward on a 64-Gaussian subset (fp32: step 1e-3)
+    # central differences of the CUDA forward on a 64-Gaussian subset (tests/parity.py: fd_check)
     subset = rng.choice(n, 64, replace=False)
-    rows = [0, 1, 2, 3, 6, 10, 11]
-    eps = 1e-3
-    checked = bad = 0
-    base = ras.forward(P.detach(), n, cams)
-    base_last, base_gp = base["last"].clone(), base["gp"].clone()
-    for i in subset:
-        for c in rows:
-            an = g[c, i]
-            if abs(an) < 1e-3 * np.abs(g[c, :n]).max():
-                continue
-            vals = []
-            same = True
-            for s in (1, -1):
-                q = P.detach().clone()
-                q[c, i] += s * eps
-                o = ras.forward(q, n, cams)
-                # skip perturbations that change a discrete decision (blend set or early stop)
-                same &= bool(torch.equal(o["last"], base_last)) and bool(torch.equal(o["gp"], base_gp))
-                vals.append(float((o["image"].double() * weights.double()).sum()))
-            if not same:
-                continue
-            fd = (vals[0] - vals[1]) / (2 * eps)
-            checked += 1
-            if abs(fd - an) > 0.05 * abs(an) + 1e-3 * np.abs(g[c, :n]).max():
-                bad += 1
-    assert checked >= 40 and bad <= max(1, checked // 20), (checked, bad)
+    fd_check("autograd three views", ras, P, n, cams, weights, g, subset, [0, 1, 2, 3, 6, 10, 11],
+             min_discriminating=100)
     ras.close()

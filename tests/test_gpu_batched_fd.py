@@ -6,11 +6,13 @@ torch.autograd wrapper, against central finite differences of the same CUDA forw
 The loss is a seeded random linear functional of all nine images, so a perturbation changes it
 only through the pixels the perturbed Gaussian reaches; the forward is deterministic, so every
 other pixel cancels exactly in the difference.  Perturbations that change a discrete decision
-anywhere (the set of Gaussians a pixel blends, or where it stops) are skipped."""
+anywhere (the set of Gaussians a pixel blends, or where it stops) are skipped and printed; every
+other entry must agree within the per-entry bound of tests/parity.py (fd_check)."""
 import numpy as np
 import pytest
 
 import gsinputs as gi
+from parity import fd_check
 
 pytestmark = pytest.mark.gpu
 
@@ -39,29 +41,5 @@ def test_batched_views_gradient_matches_finite_differences():
     op = np.abs(g[10, visible])
     cand = visible[op > 1e-2 * op.max()]
     subset = rng.choice(cand, 64, replace=False)
-    rows = [0, 1, 2, 3, 6, 10, 11]
-    base = ras.forward(P.detach(), n, cams)
-    base_last, base_gp = base["last"].clone(), base["gp"].clone()
-    wd = weights.double()
-    eps = 1e-3
-    checked = bad = 0
-    for i in subset:
-        for c in rows:
-            an = float(g[c, i])
-            if abs(an) < 1e-3 * np.abs(g[c]).max():
-                continue
-            vals, same = [], True
-            for s in (1, -1):
-                q = P.detach().clone()
-                q[c, i] += s * eps
-                o = ras.forward(q, n, cams)
-                same &= bool(torch.equal(o["last"], base_last)) and bool(torch.equal(o["gp"], base_gp))
-                vals.append(float((o["image"].double() * wd).sum()))
-            if not same:
-                continue
-            fd = (vals[0] - vals[1]) / (2 * eps)
-            checked += 1
-            if abs(fd - an) > 0.05 * abs(an) + 1e-3 * np.abs(g[c]).max():
-                bad += 1
-    assert checked >= 100 and bad <= max(1, checked // 20), (checked, bad)
+    fd_check("batched 9 views", ras, P, n, cams, weights, g, subset, [0, 1, 2, 3, 6, 10, 11], min_discriminating=90)
     ras.close()

@@ -1,13 +1,14 @@
 """Parity at the bench's full size (200k Gaussians in the ring scene, one 1297 x 840 view, L1 +
 0.2 D-SSIM): bit-exact binning, pixels, loss and gradients against the oracle, the session step in
-the launch configuration the bench times (graph replay, Adam fused) against the oracle's step, and
-the Eq. 9 G_p statistic."""
+the launch configuration the bench times (graph replay, Adam fused) against the oracle's Adam on the
+same gradients, and the Eq. 9 G_p statistic.  Bounds and exemptions: tests/parity.py."""
 import numpy as np
 import pytest
 
 import gsinputs as gi
 import oracle
-from helpers import gpu_forward, grad_close, ocam, split_views
+from helpers import gpu_forward, grad_close, ocam, split_views  # noqa: F401
+from parity import Exemptions, backward_parity, check_adam
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +32,10 @@ def test_scene_scale_parity():
     o = oracle.blend_forward((1297, 840), 0, L["ranges"], L["vals"], g["rec"], prec="f32")
     img = g["out"]["image"].cpu().numpy().reshape(3, 840, 1297)
     clean = o["margin"] > TIE
+    ex = Exemptions("scene 200k blend forward")
+    for py, px in np.argwhere(~clean):
+        ex.add(f"pixel ({py}, {px})", f"threshold tie (margin {o['margin'][py, px]:.1e})")
+    ex.report()
     assert clean.mean() > 0.999
     assert np.abs(img - o["image"])[:, clean].max() <= 1e-4
     gp = g["out"]["gp"].cpu().numpy().view(np.uint32).reshape(840, 1297)
@@ -41,18 +46,11 @@ def test_scene_scale_parity():
     ref, d_ref, _, _ = oracle.loss(img, tgt, 0.2, True, 1.0, prec="f32")
     assert abs(loss - ref) <= 1e-5 * abs(ref)
     assert grad_close(dimg.cpu().numpy().reshape(1, -1), d_ref.reshape(1, -1)).mean() == 0.0
-    # gradients
-    grads, _ = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg)
-    g2 = np.zeros((n, 9), np.float32)
-    oracle.blend_backward((1297, 840), 0, L["ranges"], L["vals"], g["rec"], dimg.cpu().numpy().reshape(3, 840, 1297),
-                          g2, prec="f32")
-    g_ref = np.zeros_like(p)
-    oracle.project_backward(p, ocam(cam), g2, g_ref, prec="f32", n=n)
-    bad = grad_close(grads.cpu().numpy()[:, :n], g_ref[:, :n])
-    assert bad.mean() < 1e-3, bad.sum(axis=1)
+    # gradients: the blend backward and the projection backward against the oracle on the same inputs
+    grads, _ = backward_parity("scene 200k", ras, g, p, n, [cam], dimg)
     ras.close()
     # the session step the bench times (graph-captured, Adam fused into the projection backward):
-    # its loss, and one Adam step from zero moments applied to the oracle's gradients
+    # its loss, and its Adam update against the oracle's Adam on the same gradients
     f = gs.Field(scene_extent=7.0, lambda_ssim=0.2, use_graph=1, tiling=(16, 16, 256))
     f.set_gaussians(p)
     img_id = f.add_image(cam, tgt)
@@ -62,13 +60,7 @@ def test_scene_scale_parity():
     f.close()
     assert abs(step_loss - ref) <= 1e-5 * abs(ref)
     rates = [lr * 7.0, 5e-3, 1e-3, 0.05, 2.5e-3, 2.5e-3 / 20]
-    upd = p.copy()
-    oracle.adam(upd, g_ref, np.zeros_like(p), np.zeros_like(p), rates, 1, prec="f32")
-    for (a, b), rate in zip([(0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 59)], rates):
-        # a first Adam step moves a parameter by about rate x sign(g); only gradients too small for a
-        # stable sign may differ
-        off = np.abs(got[a:b, :n] - upd[a:b, :n]) > 1e-3 * rate + 1e-6
-        assert off.mean() < 2e-3, (a, b, off.mean())
+    check_adam("scene 200k session step", got, p, grads, rates, 1, n=n)
 
 
 def test_load_balance_statistic_matches_oracle():

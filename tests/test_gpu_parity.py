@@ -2,10 +2,11 @@
 
 Bars: tile keys, sort order and per-tile ranges bit-exact (the oracle's binning is fed the
 kernel's projected positions, radii and depths, so both decide from the same fp32 values);
-pixels <= 1e-4 absolute; gradients elementwise <= 1e-3 relative with a floor of 1 % of the
-row's largest magnitude (float summation order differs).  Per-pixel integers (last index, G_p,
-entries evaluated) are exact except at recorded threshold ties: pixels where the oracle saw an
-alpha within 1e-5 (relative) of 1/255 or a transmittance within 1e-5 of 1e-4.
+pixels <= 1e-4 absolute; the projection's mean within 4 u of its rounding scale and the conic
+within its conditioning; gradients elementwise within 1e-3 relative plus the rounding scale of
+their products (tests/parity.py).  Per-pixel integers (last index, G_p, entries evaluated) are
+exact except at recorded threshold ties: pixels where the oracle saw an alpha within 1e-5
+(relative) of 1/255 or a transmittance within 1e-5 of 1e-4.  Every exemption is printed.
 """
 import numpy as np
 import pytest
@@ -13,6 +14,7 @@ import pytest
 import gsinputs as gi
 import oracle
 from helpers import config1, gpu_forward, grad_close, ocam, split_views
+from parity import U32, Exemptions, backward_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -79,10 +81,34 @@ def test_projection(run):
         assert ((vis_g == vis_o) | border).all()
         both = vis_g & vis_o & ~border
         assert both.sum() > 0
+        ex = Exemptions(f"{run['name']} view {v} projection")
+        for i in np.nonzero((vis_g != vis_o) & border)[0]:
+            ex.add(f"Gaussian {i}", f"visibility differs at a cull/rect threshold (margin {o['margin'][i]:.2e})")
+        ex.report()
         assert (run["radius"][sl][both] == o["radius"][both]).all()
-        assert np.allclose(run["rec"]["mean2d"][sl][both], o["mean2d"][both], rtol=1e-5, atol=1e-3)
+        # mean2d = f x/z + c: fp32 rounding of the camera transform (3-term dot products), the
+        # division and the affine map, each side within 2 u of the scale below
+        R = np.asarray(c["R"], np.float64).reshape(3, 3)
+        t = np.asarray(c["t"], np.float64)
+        mu = p[0:3, :n].astype(np.float64)
+        pc = R @ mu + t[:, None]
+        ax = np.abs(R) @ np.abs(mu) + np.abs(t)[:, None]
+        for k, (f, cc) in enumerate(((c["fx"], c["cx"]), (c["fy"], c["cy"]))):
+            uu = f * pc[k] / pc[2] + cc
+            scale = f * (ax[k] + np.abs(pc[k] / pc[2]) * ax[2]) / np.abs(pc[2]) + np.abs(uu)
+            err = np.abs(run["rec"]["mean2d"][sl][:, k].astype(np.float64) - o["mean2d"][:, k])
+            assert (err[both] <= 4 * U32 * scale[both]).all(), (k, float((err / scale)[both].max() / U32))
         assert np.allclose(run["depth"][sl][both], o["depth"][both], rtol=1e-6)
-        assert np.allclose(run["rec"]["conic"][sl][both], o["conic"][both], rtol=1e-4, atol=1e-6)
+        # the conic is the inverse of the 2D covariance: its fp32 error grows with the condition
+        # number kappa of that 2 x 2 matrix; bound 64 u kappa |conic| (+1e-5 |conic|)
+        co = o["conic"].astype(np.float64)
+        tr = co[:, 0] + co[:, 2]
+        disc = np.sqrt(np.maximum((co[:, 0] - co[:, 2]) ** 2 + 4 * co[:, 1] ** 2, 0))
+        lmax, lmin = 0.5 * (tr + disc), np.maximum(0.5 * (tr - disc), 1e-30)
+        nrm = np.abs(co).max(1)
+        cb = (64 * U32 * lmax / lmin + 1e-5) * nrm
+        cerr = np.abs(run["rec"]["conic"][sl].astype(np.float64) - co).max(1)
+        assert (cerr[both] <= cb[both]).all(), float((cerr / cb)[both].max())
         assert np.allclose(run["rec"]["opacity"][sl][both], o["opacity"][both], rtol=1e-6, atol=1e-7)
         assert np.allclose(run["rec"]["rgb"][sl][both], o["rgb"][both], atol=1e-5)
         assert (run["clamp"][sl][both] == o["clamp"][both]).all()
@@ -115,14 +141,18 @@ def test_blend_forward(run):
     gps = split_views(out["gp"].cpu().numpy().view(np.uint32), run["sizes"], 1)
     pairs_ref = 0
     ties = 0
+    ex = Exemptions(f"{run['name']} blend forward")
     for v, o in enumerate(outs):
         clean = o["margin"] > TIE
         ties += int((~clean).sum())
+        for py, px in np.argwhere(~clean):
+            ex.add(f"view {v} pixel ({py}, {px})", f"threshold tie (margin {o['margin'][py, px]:.1e})")
         assert np.abs(imgs[v] - o["image"])[:, clean].max() <= 1e-4
         assert np.abs(Ts[v] - o["T"])[clean].max() <= 1e-4
         assert np.array_equal(lasts[v][clean], o["last"][clean])
         assert np.array_equal(gps[v][clean], o["gp"][clean])
         pairs_ref += int(o["neval"].astype(np.int64).sum())
+    ex.report()
     if ties == 0:
         assert out["pairs"] == pairs_ref
     else:
@@ -130,12 +160,25 @@ def test_blend_forward(run):
 
 
 def test_forward_against_oracle_end_to_end(run):
+    """The GPU's pixels against the oracle's whole forward (its own projection and binning).  A pixel
+    may differ only where the oracle itself, walking the GPU's projected records instead of its own,
+    takes another decision (blend set, stop) or sits at a threshold tie: there the projection's
+    rounding decides the branch.  Each such pixel is printed; every other pixel is within 1e-4."""
     r = oracle.render(run["params"], [ocam(c) for c in run["cams"]], prec="f32", n=run["n"])
+    L, outs_g = _oracle_forward_on_gpu_records(run)
     imgs = split_views(run["out"]["image"].cpu().numpy(), run["sizes"], 3)
     for v, o in enumerate(r["outs"]):
+        og = outs_g[v]
+        flip = (o["last"] != og["last"]) | (o["gp"] != og["gp"]) | (o["neval"] != og["neval"])
+        tie = (o["margin"] <= TIE) | (og["margin"] <= TIE)
         d = np.abs(imgs[v] - o["image"]).max(0)
-        good = (d <= 1e-4) | (o["margin"] <= TIE)
-        assert good.mean() >= 0.999, (run["name"], v, good.mean(), d.max())
+        ex = Exemptions(f"{run['name']} view {v} end-to-end forward")
+        for py, px in np.argwhere((d > 1e-4) & (flip | tie)):
+            ex.add(f"pixel ({py}, {px}) |d| {d[py, px]:.1e}",
+                   "decision differs on the GPU's records" if flip[py, px] else "threshold tie")
+        ex.report()
+        bad = (d > 1e-4) & ~flip & ~tie
+        assert not bad.any(), (run["name"], v, np.argwhere(bad)[:10].tolist(), float(d[bad].max()))
 
 
 def test_loss(run, ras):
@@ -159,31 +202,11 @@ def test_loss(run, ras):
 
 def test_backward(run, ras):
     import torch
-    out = run["out"]
-    if "dimage" not in run:
-        tg = np.concatenate([t.reshape(-1) for t in run["targets"]]).astype(np.float32)
-        ras.loss(out["image"], torch.tensor(tg, device="cuda"), 0.2)
-    # re-run the forward so this test stands alone, then take a fresh dL/dimage
+    # a fresh forward and dL/dimage so this test stands alone
     g = gpu_forward(ras, run["params"], run["n"], run["cams"])
     tg = np.concatenate([t.reshape(-1) for t in run["targets"]]).astype(np.float32)
     _, dimg = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), 0.2)
-    grads, grad2d = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg, want_grad2d=True)
-    grads = grads.cpu().numpy()
-    grad2d = grad2d.cpu().numpy().reshape(-1, 9)
-    n, stride = run["n"], run["params"].shape[1]
-    L = oracle.build_lists(run["sizes"], g["rec"]["mean2d"], g["radius"], g["depth"])
-    ds = split_views(dimg.cpu().numpy(), run["sizes"], 3)
-    g2_ref = np.zeros((len(run["sizes"]) * stride, 9), np.float32)
-    for v, s in enumerate(run["sizes"]):
-        oracle.blend_backward(s, L["tile_base"][v], L["ranges"], L["vals"], g["rec"], ds[v], g2_ref, prec="f32")
-    vis = g["count"] > 0
-    bad2 = grad_close(grad2d[vis].T, g2_ref[vis].T)
-    assert bad2.mean() < 1e-3, (run["name"], bad2.sum(axis=1))
-    g_ref = np.zeros_like(run["params"])
-    for v, c in enumerate(run["cams"]):
-        oracle.project_backward(run["params"], ocam(c), g2_ref[v * stride:(v + 1) * stride], g_ref, prec="f32", n=n)
-    bad = grad_close(grads[:, :n], g_ref[:, :n])
-    assert bad.mean() < 1e-3, (run["name"], bad.sum(axis=1))
+    backward_parity(run["name"], ras, g, run["params"], run["n"], run["cams"], dimg)
 
 
 def test_adam_kernel():

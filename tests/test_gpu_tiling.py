@@ -4,7 +4,8 @@ the autotuner of the session.
 The tile shape is part of the result (the 3DGS rect rule bins by tile, and a Gaussian whose 1/255
 footprint reaches past its 3-sigma square can enter or miss a pixel's list depending on the grid),
 so each shape is compared with the oracle binning by the same shape: keys, order and ranges
-bit-exact, pixels <= 1e-4, gradients <= 1e-3 relative (floor 1 % of the row maximum).  The blend
+bit-exact, pixels <= 1e-4 (ties printed), gradients within 1e-3 relative plus their rounding scale
+(tests/parity.py).  The blend
 batch only changes how many sorted Gaussians K6 stages per round: results are bitwise the same.
 """
 import numpy as np
@@ -12,7 +13,8 @@ import pytest
 
 import gsinputs as gi
 import oracle
-from helpers import gpu_forward, grad_close, ocam, split_views
+from helpers import gpu_forward, ocam, split_views
+from parity import Exemptions, backward_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +41,9 @@ def case_dense():
     return p, 2500, [gi.identity_camera(64, 48, 200.0)], [gi.uniform_target(64, 48, 3)]
 
 
-def _run(ras, tl, case):
+def _run(ras, tl, case, check=False):
+    """One forward, loss and backward with tiling tl; with check, the backward's two stages against
+    the oracle run with the same tile shape (tests/parity.py)."""
     import torch
     p, n, cams, tg = case()
     ras.set_tiling(*tl)
@@ -47,10 +51,13 @@ def _run(ras, tl, case):
     sizes = [(c["width"], c["height"]) for c in cams]
     tgt = torch.tensor(np.concatenate([t.reshape(-1) for t in tg]).astype(np.float32), device="cuda")
     loss, dimg = ras.loss(g["out"]["image"], tgt, 0.2)
-    grads, grad2d = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg, want_grad2d=True)
+    if check:
+        grads, grad2d = backward_parity(f"{case.__name__} {tl}", ras, g, p, n, cams, dimg, tile=(tl[0], tl[1]))
+    else:
+        grads, grad2d = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg, want_grad2d=True)
+        grads, grad2d = grads.cpu().numpy(), grad2d.cpu().numpy().reshape(-1, 9)
     return dict(g=g, p=p, n=n, cams=cams, sizes=sizes, dimg=dimg.cpu().numpy(), loss=loss,
-                grads=grads.cpu().numpy(), grad2d=grad2d.cpu().numpy().reshape(-1, 9),
-                image=g["out"]["image"].cpu().numpy())
+                grads=grads, grad2d=grad2d, image=g["out"]["image"].cpu().numpy())
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +71,7 @@ def ras():
 @pytest.mark.parametrize("case", [case_ragged, case_dense], ids=["ragged_multiview", "dense_tile"])
 def test_every_tiling_matches_the_oracle(ras, case):
     for tl in _candidates():
-        r = _run(ras, tl, case)
+        r = _run(ras, tl, case, check=True)  # the backward's stages are checked inside
         g, tile = r["g"], (tl[0], tl[1])
         # binning: bit-exact against the oracle's enumeration with the same tile shape
         L = oracle.build_lists(r["sizes"], g["rec"]["mean2d"], g["radius"], g["depth"], tile)
@@ -74,25 +81,15 @@ def test_every_tiling_matches_the_oracle(ras, case):
         # blending
         imgs = split_views(r["image"], r["sizes"], 3)
         lasts = split_views(g["out"]["last"].cpu().numpy().view(np.uint32), r["sizes"], 1)
-        ds = split_views(r["dimg"], r["sizes"], 3)
-        stride = r["p"].shape[1]
-        g2_ref = np.zeros((len(r["sizes"]) * stride, 9), np.float32)
+        ex = Exemptions(f"{case.__name__} {tl} blend forward")
         for v, s in enumerate(r["sizes"]):
             o = oracle.blend_forward(s, L["tile_base"][v], L["ranges"], L["vals"], g["rec"], tile=tile, prec="f32")
             clean = o["margin"] > TIE
+            for py, px in np.argwhere(~clean):
+                ex.add(f"view {v} pixel ({py}, {px})", "threshold tie")
             assert np.abs(imgs[v] - o["image"])[:, clean].max() <= 1e-4, tl
             assert np.array_equal(lasts[v][clean], o["last"][clean]), tl
-            oracle.blend_backward(s, L["tile_base"][v], L["ranges"], L["vals"], g["rec"], ds[v], g2_ref, tile=tile,
-                                  prec="f32")
-        vis = g["count"] > 0
-        bad2 = grad_close(r["grad2d"][vis].T, g2_ref[vis].T)
-        assert bad2.mean() < 1e-3, (tl, bad2.sum(axis=1))
-        g_ref = np.zeros_like(r["p"])
-        for v, c in enumerate(r["cams"]):
-            oracle.project_backward(r["p"], ocam(c), g2_ref[v * stride:(v + 1) * stride], g_ref, tile=tile, prec="f32",
-                                    n=r["n"])
-        bad = grad_close(r["grads"][:, :r["n"]], g_ref[:, :r["n"]])
-        assert bad.mean() < 1e-3, (tl, bad.sum(axis=1))
+        ex.report()
 
 
 def test_blend_batch_does_not_change_results(ras):
