@@ -1,17 +1,21 @@
 """Benchmark of the On-the-Fly GS hot path on GB300.
 
-Default workload (one "step" = one pass of the whole hot path): the scene-scale single view --
-200k Gaussians in a ring-shaped outdoor-like volume, one 1297 x 840 view, SH degree 3, loss
+Headline (one "step" = one pass of the whole hot path): the scene-scale single view -- 200k
+Gaussians in a ring-shaped outdoor-like volume, one 1297 x 840 view, SH degree 3, loss
 0.8 L1 + 0.2 D-SSIM: projection, binning, sort, blend forward, loss, blend backward, projection
 backward and Adam with the per-image learning rate, through the session API (gs_optimize_step),
 replayed from a CUDA graph.  value = Gaussian-pixel pairs per second (P counted by the oracle's
-definition: per pixel, list entries evaluated up to its stop) / step time.  The same line carries
-the new-image integration latency p50/p99 of a streaming segment (arrivals on a random-walk
-trajectory, T_I = 200 iterations each), for the plain per-view eager path and the batched,
-graph-replayed path.
+definition: per pixel, list entries evaluated up to its stop) / step device time.  The same line
+carries, measured in the same run with the clocks sampled during each:
+  integration_latency_s  the streaming session at full length (150 arrivals, the field growing to
+                         about 1.5-1.9M Gaussians): p50/p99 new-image integration latency of the
+                         plain per-view, graph per-view and batched paths, PSNR against the targets
+                         and of the GPU's renders against the oracle's renders of the final field;
+  batched_step           500k Gaussians x 9 mixed-size views per step, per-kernel times;
+  serving                4 concurrent scenes admitted by HBM budget, p50/p99 per session.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gs|reference]
-                  [--workload scene|batched|serve] [--arrivals A]
+                  [--workload scene|batched|serve|stream] [--segments stream,batched,serve|none]
 
 --impl reference times the oracle (CPU, fp32, one thread) on the same workload.  Under torchrun
 each rank runs its own independent session (weak scaling, no data exchange); rank 0 prints one
@@ -40,6 +44,15 @@ W, H = 1297, 840
 WORKLOAD = "scene-scale single view: 200k Gaussians (ring volume), 1297x840, SH3, 0.8 L1 + 0.2 D-SSIM, fwd+bwd+Adam"
 KERNELS = ["K1 project", "K2 scan", "K3 emit", "K4 sort", "K5 ranges+order", "K6 blend fwd", "K7 loss", "K8 blend bwd",
            "K9+K10 project bwd + Adam"]
+
+
+def workload_config(ws=1):
+    """The workload as both arms name it (the same dict in the CUDA line and the reference line)."""
+    return {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H, "sh_degree": 3,
+            "loss": "0.8 L1 + 0.2 D-SSIM", "tiling": "16x16 tiles (3DGS), blend batch 256",
+            "l2": "flushed before every timed step (256 MiB write, untimed)",
+            "state": "every timed step starts from the same snapshot (device copy, untimed)",
+            "parallelism": f"{ws} independent session(s), one per GPU"}
 
 
 def make_workload(seed):
@@ -133,17 +146,37 @@ def kernel_work(k, st, n, passes):
     return "hbm", 8.0 * n
 
 
-def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
+# The per-pair instruction counts the scope table states for the two blend kernels (K6 "~16 FP32
+# instructions + 1 ex2 per pair" over the evaluated pairs; K8 "~55-65" over the pairs it walks, the
+# blended ones), reported beside the finer counts above.
+SURVEY_PER_PAIR = {5: ("pairs", 16.0), 7: ("blended", 60.0)}
+
+
+def device_sm_count(default=152):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    return default
+
+
+def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic, n_sms=None):
     per = [k / max(1, steps) for k in kernel_ms]
     dom = int(np.argmax(per))
+    n_sms = device_sm_count() if n_sms is None else int(n_sms)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = n_sms * 128 * sm_mhz * 1e6 / 1e12
 
     def frac_of(k):
         t = per[k] * 1e-3
         bound, work = kernel_work(k, st, n, passes)
         if bound == "alu":
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-            unit, src = "Tops/s", f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived from unit counts and clock)"
+            peak = alu_peak
+            unit = "Tops/s"
+            src = (f"{n_sms} SMs (cudaDeviceProp.multiProcessorCount) x 128 FP32 lanes x {sm_mhz:.0f} MHz "
+                   f"(sm_max_mhz, {peaks_kind}): derived from unit counts and clock")
             ach = work / t / 1e12 if t > 0 else 0.0
         else:
             peak = peaks["hbm_gbs"]
@@ -157,9 +190,16 @@ def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic):
     for k, nm in enumerate(KERNELS):
         b, _, a, pk, _, _ = frac_of(k)
         each[nm] = {"bound": b, "frac": round(a / pk, 4)}
-    return dict(kernel=KERNELS[dom], bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
-                traffic=traffic.get(KERNELS[dom]), peak_source=src, work_per_launch=work,
-                per_kernel_ms={nm: round(x, 4) for nm, x in zip(KERNELS, per)}, per_kernel_frac=each)
+    out = dict(kernel=KERNELS[dom], bound=bound, achieved=ach, peak=peak, unit=unit, frac=ach / peak,
+               traffic=traffic.get(KERNELS[dom]), peak_source=src, work_per_launch=work, n_sms=n_sms,
+               per_kernel_ms={nm: round(x, 4) for nm, x in zip(KERNELS, per)}, per_kernel_frac=each)
+    if dom in SURVEY_PER_PAIR and per[dom] > 0:
+        key, ops = SURVEY_PER_PAIR[dom]
+        w2 = ops * st[key]
+        a2 = w2 / (per[dom] * 1e-3) / 1e12
+        out["survey_count"] = {"ops_per_pair": ops, "pairs": key, "work_per_launch": w2, "achieved": a2,
+                               "frac": a2 / alu_peak}
+    return out
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed ncu
@@ -170,25 +210,41 @@ TRAFFIC = {"K8 blend bwd": 62.6e6, "K6 blend fwd": 21.8e6, "K9+K10 project bwd +
            "K4 sort": 5 * 4.1e6, "K7 loss": 94.4e6}
 
 
-def cpu_baseline_run(steps, warmup, seed=0):
-    """The oracle (fp32, one thread) doing full steps of the same workload."""
+def cpu_baseline_run(steps, warmup, seed=0, rows=None):
+    """The oracle (fp32, one thread) doing full steps of the same workload; with rows, each step
+    covers a horizontal band of that many rows in the middle of the view (the same camera, its
+    principal point moved), so that many steps stay within a bounded CPU time."""
     import oracle
     from oracle import Camera
     p, cam, tgt = make_workload(seed)
-    c = Camera(cam["R"], cam["t"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"])
+    h = H if rows is None else int(min(H, max(16, rows)))
+    y0 = (H - h) // 2
+    c = Camera(cam["R"], cam["t"], cam["fx"], cam["fy"], cam["cx"], cam["cy"] - y0, cam["width"], h)
+    tg = np.ascontiguousarray(tgt[:, y0:y0 + h, :])
     m = np.zeros_like(p)
     v = np.zeros_like(p)
     lrs = [1.6e-4 * 7.0, 5e-3, 1e-3, 0.05, 2.5e-3, 1.25e-4]
     times, pairs = [], []
     for s in range(warmup + steps):
         t0 = time.perf_counter()
-        L, g, r = oracle.loss_and_grad(p, [c], [tgt], lam=0.2, prec="f32")
+        L, g, r = oracle.loss_and_grad(p, [c], [tg], lam=0.2, prec="f32")
         oracle.adam(p, g, m, v, lrs, s + 1, prec="f32")
         dt = time.perf_counter() - t0
         if s >= warmup:
             times.append(dt)
             pairs.append(oracle.pairs(r))
     return float(np.sum(pairs) / np.sum(times)), float(np.mean(times)), int(np.mean(pairs))
+
+
+REFERENCE_BUDGET_S = 120.0  # the reference arm's CPU time for all its steps, about
+ORACLE_STEP_S = 2.5         # one full oracle step of the workload on one GPU-box host core
+
+
+def reference_rows(steps, warmup):
+    """Rows of the view each reference step covers: the whole view while K + W full steps fit the
+    budget, else a band small enough that they do."""
+    total = (steps + warmup) * ORACLE_STEP_S
+    return None if total <= REFERENCE_BUDGET_S else max(16, int(H * REFERENCE_BUDGET_S / total))
 
 
 _BARRIER = None
@@ -246,21 +302,24 @@ def combine_ranks(ms, pairs, ws, device):
 
 
 def run_reference(args):
+    """The oracle (fp32, one host thread) on the same workload: W untimed and K timed full steps
+    (about 2.3 s each on the GPU machine's Arm host), printed with the steps it actually ran."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    K_eff = min(args.steps, 6)  # each step is one full oracle step (~4-5 s on one core): bounded
-    W_eff = min(args.warmup, 1)
-    val, sec, pairs = cpu_baseline_run(K_eff, W_eff)
+    rows = reference_rows(args.steps, args.warmup)
+    val, sec, pairs = cpu_baseline_run(args.steps, args.warmup, rows=rows)
+    sample = (f"{args.steps} full oracle steps (after {args.warmup} untimed) of the workload, {pairs} pairs each"
+              if rows is None else
+              f"{args.steps} oracle steps (after {args.warmup} untimed), each over the middle {rows} of the view's "
+              f"{H} rows (all 200k Gaussians projected; {pairs} pairs each) to bound the CPU time")
     line = {"metric": METRIC, "value": val, "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
-            "impl": "reference",
-            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H},
+            "impl": "reference", "config": workload_config(ws),
             "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{K_eff} full oracle steps (after {W_eff} warm-up) of the workload, {pairs} "
-                                       f"pairs each; steps capped at 6 to bound CPU time"},
+                             "sample": sample + ", fp32, one thread"},
             "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -285,7 +344,7 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H, pts_range=(5000,
 
 
 def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False,
-               thresh=0.0, sparse=0):
+               thresh=0.0, sparse=0, keep_field=False):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
@@ -304,6 +363,7 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, 
     lat = sess.latency()
     psnr = sess.psnr(cams, targets)
     n = sess.field.stats()["n_gaussians"]
+    final = sess.field.get_gaussians() if keep_field else None
     kt = None
     if kernel_times:
         kms, ksteps = sess.field.kernel_times()
@@ -314,7 +374,7 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, 
                 pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn,
                 batch_scaling=scaling, sparse_adam=bool(sparse), add_image_mean_s=float(np.mean(add_s)),
                 integrate_mean_s=float(np.mean(int_s)),
-                **({"kernel_ms_per_step": kt} if kt else {}))
+                **({"kernel_ms_per_step": kt} if kt else {}), **({"field": final} if keep_field else {}))
 
 
 def run_gs(args):
@@ -338,9 +398,12 @@ def run_gs(args):
 
     def timed_loop(f, img, steps):
         """steps timed optimisation steps, each from the same snapshot (restored untimed) after an
-        untimed L2 flush; CUDA events on the session's stream."""
+        untimed L2 flush.  Two clocks, both CUDA events on the session's stream: the library's events
+        around the enqueued step (the step's device time; the step's own readback of its ledger and
+        loss follows them), and events recorded here around the call (which also cover that readback
+        and the host's return from it)."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        acc = dict(pairs=0, blended=0, instances=0, launches=0)
+        acc = dict(pairs=0, blended=0, instances=0, launches=0, device_ms=0.0)
         for k in range(steps):
             f.restore()
             with torch.cuda.stream(stream):
@@ -353,6 +416,7 @@ def run_gs(args):
             acc["blended"] += st["last_blended"]
             acc["instances"] += st["last_instances"]
             acc["launches"] += st["last_kernels"]
+            acc["device_ms"] += st["last_run_ms"]
         torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in ev)), acc
 
@@ -365,9 +429,10 @@ def run_gs(args):
         for _ in range(args.warmup):
             fa.optimize_step([img_a])
         fa.snapshot()
-        auto_ms, auto_acc = timed_loop(fa, img_a, args.steps)
+        _, auto_acc = timed_loop(fa, img_a, args.steps)
         auto_tiling = fa.stats()["last_tiling"]
         fa.close()
+        auto_ms = auto_acc["device_ms"]
         auto = {"tiling": f"{auto_tiling[0]}x{auto_tiling[1]}/{auto_tiling[2]}",
                 "ms_per_step": auto_ms / max(1, args.steps), "pairs_per_step": int(auto_acc["pairs"] / max(1, args.steps)),
                 "pairs_per_s": auto_acc["pairs"] / (auto_ms * 1e-3),
@@ -389,8 +454,9 @@ def run_gs(args):
     sampler = ClockSampler(local)
     sync_all()
     sampler.start()
-    ms, acc = timed_loop(field, img, args.steps)
+    call_ms, acc = timed_loop(field, img, args.steps)
     launches = acc.pop("launches")
+    ms = acc.pop("device_ms")
     sync_all()
     clocks = sampler.stop()
     # per-kernel times from a second run of the same steps with an event around every kernel (the
@@ -402,20 +468,26 @@ def run_gs(args):
     field.set_timing(False)
     tiling = field.stats()["last_tiling"]
     ms_max, pairs_total = combine_ranks(ms, float(acc["pairs"]), ws, "cuda")
+    call_ms_max, _ = combine_ranks(call_ms, 0.0, ws, "cuda")
     value = pairs_total / (ms_max * 1e-3)
 
-    # end to end through the C ABI: host target (pinned) -> device, step, loss -> host
-    tgt_pinned = torch.from_numpy(tgt.reshape(-1)).pin_memory()
+    # end to end through the C ABI, as a user calls it: the step's target as decoded (H x W x 3,
+    # pinned host memory) -> device (transposed there by gs_set_image's kernel), the step, and the
+    # library's readback of the step's ledger and loss; all inside the timed region
+    tgt_hwc = torch.from_numpy(np.ascontiguousarray(np.transpose(tgt, (1, 2, 0)))).pin_memory()
     e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    e2e_pairs = 0
+    e2e_pairs, e2e_h2d, e2e_d2h = 0, 0, 0
     sync_all()
     for k in range(args.steps):
         field.restore()
         e2e_ev[k][0].record(stream)
-        field.set_image(img, tgt_pinned)
+        field.set_image(img, tgt_hwc)
         field.optimize_step([img])
         e2e_ev[k][1].record(stream)
-        e2e_pairs += field.stats()["last_pairs"]
+        st = field.stats()
+        e2e_pairs += st["last_pairs"]
+        e2e_h2d += tgt_hwc.numel() * 4 + st["last_h2d_bytes"]
+        e2e_d2h += st["last_d2h_bytes"]
     sync_all()
     e2e_ms = float(sum(a.elapsed_time(b) for a, b in e2e_ev))
     e2e_ms, e2e_pairs = combine_ranks(e2e_ms, float(e2e_pairs), ws, "cuda")
@@ -427,58 +499,56 @@ def run_gs(args):
     passes = (32 + int(tiles - 1).bit_length() + 7) // 8
     # visible Gaussians of the view (for K1's algorithmic bytes)
     ras = gs.Raster()
-    fo = ras.forward(torch.tensor(p, device="cuda"), N_GAUSS, [cam])
+    ras.forward(torch.tensor(p, device="cuda"), N_GAUSS, [cam])
     st_mean["visible"] = int((ras.read(6, np.uint32) > 0).sum())
     ras.close()
+    del flush
+    torch.cuda.empty_cache()
 
-    lat = None
-    if ws == 1 and args.arrivals > 0:
-        cams, targets, pts = stream_inputs(args.arrivals, seed=rank)
-        # the autotuner's classes (a power of two of pixels per step) are tuned once per process, as a
-        # server would at start-up: untimed sessions over the first arrivals fill the cache
-        gs.autotune_clear()
-        warm = min(args.arrivals, 10)
-        for b in (1, 3, 9):
-            run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1)
-        plain = run_stream(cams, targets, pts, batch=1, graph=0, asyn=1)
-        graphed = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16)
-        graphed_k = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16, kernel_times=True)
-        batched = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16)
-        batched_s = run_stream(cams, targets, pts, batch=9, graph=1, asyn=16, scaling=1)
-        batched3_s = run_stream(cams, targets, pts, batch=3, graph=1, asyn=16, scaling=1)
-        lat = {"workload": f"{args.arrivals} arrivals, 1297x840, random walk with 60-80% overlap, 5k-20k sparse "
-                           f"points each, T_I = 200 over the new image + 8 neighbours, 1.5M-Gaussian hidden scene",
-               "autotune": f"tiling autotuned per class, cache filled by untimed sessions over the first {warm} arrivals",
-               "plain_per_view": plain, "graph_async_per_view": graphed,
-               "kernel_ms_per_step_graph_async": graphed_k["kernel_ms_per_step"], "batched_graph": batched,
-               "batched_graph_scaled": batched_s, "batched3_graph_scaled": batched3_s}
+    segments = {}
+    if ws == 1:
+        wanted = [x for x in args.segments.split(",") if x] if args.segments != "none" else []
+        for name in wanted:
+            fn = {"stream": segment_stream, "batched": segment_batched, "serve": segment_serve}[name]
+            smp = ClockSampler(local)
+            smp.start()
+            t0 = time.perf_counter()
+            res = fn(args)
+            res["wall_s"] = time.perf_counter() - t0
+            res["clocks"] = smp.stop()
+            segments[name] = res
+            torch.cuda.empty_cache()
 
     if rank == 0:
         peaks, kind = measured_peaks()
         rl = roofline(kms, ksteps, st_mean, N_GAUSS, passes, peaks, kind,
                       TRAFFIC if tuple(tiling) == TRAFFIC_TILING else {})
+        cfg = workload_config(ws)
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
-                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": W, "height": H,
-                           "instances": int(st_mean["instances"]), "pairs_per_step": int(st_mean["pairs"]),
+                "config": cfg,
+                "counts": {"instances": int(st_mean["instances"]), "pairs_per_step": int(st_mean["pairs"]),
                            "blended_pairs_per_step": int(st_mean["blended"]),
-                           "tiling": {"tile": f"{tiling[0]}x{tiling[1]}", "blend_batch": tiling[2],
-                                      "source": "autotuned" if args.tiling == "auto" else "fixed"},
-                           "l2": "flushed before every timed step (256 MiB write, untimed)",
-                           "state": "every timed step starts from the same snapshot (device copy, untimed)",
-                           "parallelism": f"{ws} independent session(s), one per GPU", "graph": True},
+                           "tiling": f"{tiling[0]}x{tiling[1]}/{tiling[2]}", "graph": True},
+                "timing": {"ms_per_step_device": ms_max / steps,
+                           "ms_per_step_with_readback": call_ms_max / steps,
+                           "note": "value: the library's CUDA events around each step's device work; the second "
+                                   "figure adds the step's readback of its ledger and loss and the host's return "
+                                   "(events recorded by the caller around gs_optimize_step)"},
                 "e2e": {"value": e2e_pairs / (e2e_ms * 1e-3), "unit": "pairs/s",
-                        "h2d_bytes_per_step": int(tgt.nbytes), "d2h_bytes_per_step": 1024},
+                        "h2d_bytes_per_step": int(e2e_h2d // steps), "d2h_bytes_per_step": int(e2e_d2h // steps)},
                 "gpu_launches": int(launches),
                 "autotuned": auto,
                 "roofline": rl, "clocks": clocks}
-        if lat is not None:
-            # headline: the per-view path (the paper's one-image-per-iteration semantics, so the same
-            # PSNR as the plain path) replayed from graphs with 16 steps between host syncs
-            line["integration_latency_s"] = {"p50": lat["graph_async_per_view"]["p50_s"],
-                                             "p99": lat["graph_async_per_view"]["p99_s"], "detail": lat}
+        if "stream" in segments:
+            sd = segments["stream"]
+            line["integration_latency_s"] = {"p50": sd["graph_async_per_view"]["p50_s"],
+                                             "p99": sd["graph_async_per_view"]["p99_s"], "detail": sd}
+        for nm in ("batched", "serve"):
+            if nm in segments:
+                line[{"batched": "batched_step", "serve": "serving"}[nm]] = segments[nm]
         if not args.no_cpu_baseline and ws == 1:
             val, sec, pp = cpu_baseline_run(3, 0)
             line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
@@ -493,8 +563,95 @@ def run_gs(args):
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args):
-    """Batched local & semi-global step: 500k Gaussians, 9 views at mixed sizes, one graph."""
+def _oracle_render_worker(job):
+    """Render one view of a saved field with the oracle (fp32); returns (view, image)."""
+    import oracle
+    from oracle import Camera
+    path, n, cam = job
+    prm = np.load(path, mmap_mode="r")
+    c = Camera(cam["R"], cam["t"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["width"], cam["height"])
+    r = oracle.render(np.ascontiguousarray(prm), [c], prec="f32", n=n)
+    return r["outs"][0]["image"]
+
+
+def oracle_psnr_of_field(params, cams, views):
+    """PSNR of the field's GPU renders against the oracle's renders of the same field, per view (a
+    spawn pool, one host process per view)."""
+    import multiprocessing as mp
+    import tempfile
+    import torch
+    import paper_2503_13086_gb300 as gs
+    n = params.shape[1]
+    stride = -(-n // 32) * 32
+    padded = np.zeros((59, stride), np.float32)
+    padded[:, :n] = params
+    f = gs.Field(scene_extent=7.0, tiling=(16, 16, 256))
+    f.set_gaussians(padded, n)
+    gpu = [f.render(cams[v]).cpu().numpy() for v in views]
+    f.close()
+    torch.cuda.synchronize()
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "field.npy")
+        np.save(path, padded)
+        with mp.get_context("spawn").Pool(len(views)) as pool:
+            ref = pool.map(_oracle_render_worker, [(path, n, cams[v]) for v in views], chunksize=1)
+    out = []
+    for g_img, o_img in zip(gpu, ref):
+        mse = float(np.mean((g_img.astype(np.float64) - o_img.astype(np.float64)) ** 2))
+        out.append(10.0 * np.log10(1.0 / max(mse, 1e-30)))
+    return out
+
+
+def segment_stream(args):
+    """The streaming session at full length (150 arrivals at 1297 x 840 on a random walk with 60-80 %
+    overlap, 5k-20k sparse points each, new points kept down to 0.005 from the field so it grows to
+    about 1.5-1.9M Gaussians, T_I = 200 over the new image + 8 neighbours): new-image integration
+    latency of the plain per-view eager path, the per-view path replayed from graphs, and the batched
+    path (3 views per step, large-batch rates); PSNR against the targets, and of the GPU's renders of
+    the final field against the oracle's renders of the same field."""
+    import gc
+    import paper_2503_13086_gb300 as gs
+    cams, targets, pts = stream_inputs(args.arrivals, seed=0, n_gt=4_000_000)
+    gs.autotune_clear()
+    warm = min(args.arrivals, 10)
+    for b in (1, 3):
+        run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1,
+                   thresh=0.005)
+    res = {}
+    final = None
+    for name, b, graph, asyn, scaling in (("plain_per_view", 1, 0, 1, 0), ("graph_async_per_view", 1, 1, 16, 0),
+                                          ("batched3_graph_scaled", 3, 1, 16, 1)):
+        r = run_stream(cams, targets, pts, batch=b, graph=graph, asyn=asyn, scaling=scaling, thresh=0.005,
+                       kernel_times=(name == "graph_async_per_view"), keep_field=(name == "graph_async_per_view"))
+        if "field" in r:
+            final = r.pop("field")
+        res[name] = r
+        gc.collect()
+    views = [int(x) for x in np.linspace(0, len(cams) - 1, 4).round()]
+    res["oracle_render_psnr_db"] = {
+        "views": views, "psnr_db": oracle_psnr_of_field(final, cams, views),
+        "note": "the per-view graph path's final field rendered by the GPU and by the oracle (fp32, one host "
+                "process per view) from 4 of the trajectory's cameras"}
+    res["workload"] = (f"{args.arrivals} arrivals, 1297x840, random walk 60-80% overlap, 5k-20k sparse points each, "
+                       f"new-point threshold 0.005, T_I = 200 over the new image + 8 neighbours, 4M-Gaussian hidden "
+                       f"scene")
+    res["autotune"] = f"tiling autotuned per class, cache filled by untimed sessions over the first {warm} arrivals"
+    return res
+
+
+def segment_batched(args):
+    """The batched local & semi-global step: 500k Gaussians, 9 views at mixed sizes, one graph."""
+    return batched_step(steps=max(3, min(args.steps, 20)), warmup=3)
+
+
+def segment_serve(args):
+    """Multi-session serving: 4 scenes at 1920x1080 / 1280x720, each growing to about 3M Gaussians."""
+    return serve(args)
+
+
+def batched_step(steps, warmup):
+    """Batched local & semi-global step: 500k Gaussians, 9 views at mixed sizes (960 x 540 to
+    1600 x 1060), autotuned tiling, one graph replay per step; device time from CUDA events."""
     import torch
     import paper_2503_13086_gb300 as gs
     torch.cuda.set_device(0)
@@ -506,12 +663,12 @@ def run_batched(args):
     field.set_gaussians(p)
     ids = [field.add_image(c, gi.uniform_target(c["width"], c["height"], k)) for k, c in enumerate(cams)]
     tune = field.autotune(ids, reps=3)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         field.optimize_step(ids)
     field.snapshot()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tot, pairs = 0.0, 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         field.restore()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -523,46 +680,29 @@ def run_batched(args):
     tiling = field.stats()["last_tiling"]
     # per-kernel times from the same steps run again with an event around every kernel
     field.set_timing(True)
-    for _ in range(args.steps):
+    for _ in range(steps):
         field.restore()
         field.optimize_step(ids)
     torch.cuda.synchronize()
     kms, ksteps = field.kernel_times()
     field.close()
-    print(json.dumps({"workload": "batched: 500k Gaussians, 9 views at mixed sizes, one graph", "ms_per_step":
-                      tot / args.steps, "pairs_per_s": pairs / (tot * 1e-3),
-                      "kernel_ms_per_step": {nm: round(x / max(1, ksteps), 4) for nm, x in zip(KERNELS, kms)},
-                      "sizes": [(c["width"], c["height"]) for c in cams],
-                      "tiling": f"{tiling[0]}x{tiling[1]}/{tiling[2]}",
-                      "autotune_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]}}))
+    return {"workload": "batched: 500k Gaussians, 9 views at mixed sizes, one graph", "steps": steps,
+            "ms_per_step": tot / steps, "pairs_per_step": pairs // steps, "pairs_per_s": pairs / (tot * 1e-3),
+            "kernel_ms_per_step": {nm: round(x / max(1, ksteps), 4) for nm, x in zip(KERNELS, kms)},
+            "sizes": [(c["width"], c["height"]) for c in cams],
+            "tiling": f"{tiling[0]}x{tiling[1]}/{tiling[2]}",
+            "autotune_ms": {f"{c[0]}x{c[1]}/{c[2]}": round(t, 4) for c, t in tune["candidates"]}}
+
+
+def run_batched(args):
+    print(json.dumps(batched_step(args.steps, args.warmup)))
 
 
 def run_stream_long(args):
-    """The streaming session at full length: 150 arrivals at 1297 x 840 on a random walk, 5k-20k
-    sparse points each, new points kept down to 0.005 from the field so it grows to ~1.5M Gaussians;
-    the per-view graph-replayed path (dense and sparse Adam; per-kernel times recorded by events in the
-    replayed graphs) and the 3-view batched path."""
-    import torch
-    import paper_2503_13086_gb300 as gs
-    torch.cuda.set_device(0)
-    cams, targets, pts = stream_inputs(args.arrivals, seed=0, n_gt=4_000_000)
-    gs.autotune_clear()
-    warm = min(args.arrivals, 10)
-    for b in (1, 3):
-        run_stream(cams[:warm], targets[:warm], pts[:warm], batch=b, graph=1, asyn=16, T_I=18, scaling=1,
-                   thresh=0.005)
-    res = {}
-    for name, b, sp in (("graph_async_per_view", 1, 0), ("batched3_graph_scaled", 3, 0),
-                        ("graph_async_per_view_sparse_adam", 1, 1)):
-        r = run_stream(cams, targets, pts, batch=b, graph=1, asyn=16, scaling=1, thresh=0.005, sparse=sp,
-                       kernel_times=(b == 1))
-        res[name] = r
-    print(json.dumps({"workload": f"streaming: {args.arrivals} arrivals, 1297x840, random walk 60-80% overlap, "
-                                  f"5k-20k sparse points each, new-point threshold 0.005, T_I = 200 over the new "
-                                  f"image + 8 neighbours, 4M-Gaussian hidden scene", **res}))
+    print(json.dumps(segment_stream(args)))
 
 
-def run_serve(args):
+def serve(args):
     """Multi-session serving: 4 scenes at 1920x1080 / 1280x720 arriving at 1-3 Hz (seeded Poisson),
     each growing by up to args.serve_points new Gaussians per arrival; sessions are admitted and
     deferred by the HBM budget."""
@@ -573,7 +713,7 @@ def run_serve(args):
     scenes = []
     for s in range(4):
         Wv, Hv = (1920, 1080) if s % 2 == 0 else (1280, 720)
-        cams, targets, pts = stream_inputs(args.arrivals, seed=10 + s, n_gt=args.serve_gt, Wv=Wv, Hv=Hv,
+        cams, targets, pts = stream_inputs(args.serve_arrivals, seed=10 + s, n_gt=args.serve_gt, Wv=Wv, Hv=Hv,
                                            pts_range=(args.serve_points // 2, args.serve_points + 1))
         rng = np.random.default_rng(s)
         t, reqs = 0.0, []
@@ -592,12 +732,16 @@ def run_serve(args):
                 deferred=sum(1 for _, e, _ in srv.log if e == "defer"),
                 n_gaussians={sid: r["stats"]["n_gaussians"] for sid, r in out.items()},
                 bytes_in_use={sid: r["stats"]["bytes_in_use"] for sid, r in out.items()},
-                config={"arrivals_per_scene": args.arrivals, "points_per_arrival": [args.serve_points // 2,
+                config={"arrivals_per_scene": args.serve_arrivals, "points_per_arrival": [args.serve_points // 2,
                                                                                      args.serve_points],
                         "gt_gaussians": args.serve_gt, "batch_views": args.serve_batch, "batch_scaling": 1,
                         "new_point_threshold": args.serve_thresh,
                         "hbm_budget_gb": args.serve_budget_gb, "session_budget_gb": args.serve_session_gb})
-    print(json.dumps({"workload": "serving: 4 scenes, 1920x1080 and 1280x720, 1-3 Hz arrivals", **summ}))
+    return {"workload": "serving: 4 scenes, 1920x1080 and 1280x720, 1-3 Hz arrivals", **summ}
+
+
+def run_serve(args):
+    print(json.dumps(serve(args)))
 
 
 def main():
@@ -610,7 +754,11 @@ def main():
     ap.add_argument("--workload", default="scene", choices=["scene", "batched", "serve", "stream"],
                     help="scene: the headline step (+ streaming latency); batched: 9 views per step; "
                          "serve: sessions under an HBM budget; stream: a full-length arrival stream")
-    ap.add_argument("--arrivals", type=int, default=20, help="arriving images of the streaming / serving runs")
+    ap.add_argument("--arrivals", type=int, default=150, help="arriving images of the streaming run")
+    ap.add_argument("--serve-arrivals", type=int, default=28, help="arriving images per scene of the serving run")
+    ap.add_argument("--segments", default="stream,batched,serve",
+                    help="scene workload: the measurements after the headline (comma list of stream, batched, "
+                         "serve; 'none' for the headline alone)")
     ap.add_argument("--serve-budget-gb", type=float, default=40.0, help="serve: the server's HBM budget")
     ap.add_argument("--serve-session-gb", type=float, default=16.0, help="serve: HBM reserved per session")
     ap.add_argument("--serve-points", type=int, default=150_000, help="serve: most sparse points per arrival (at least half as many)")

@@ -210,11 +210,21 @@ typedef struct gs_field_config {
                                steps.  0 (default): off */
 } gs_field_config;
 
-/* Paper defaults: T_I 200, N_m 10, T_a 200, batch 1, eta 1.6e-4 -> 1.6e-6, lambda_ssim 0.2
- * (3DGS), group rates 5e-3 / 1e-3 / 0.05 / 2.5e-3 / 1.25e-4, Adam (0.9, 0.999, 1e-15); tiling auto. */
+/* Paper defaults (Sec. V-A, implementation details): T_I 200, N_m 10, T_a 200, eta 1.6e-4 -> 1.6e-6;
+ * batch 1; loss weights 0.8 L1 + 0.2 D-SSIM (3DGS; the paper's 0.47 / 0.12 / 0.41 is a preset);
+ * group rates 5e-3 / 1e-3 / 0.05 / 2.5e-3 / 1.25e-4 and Adam (0.9, 0.999, 1e-15) of the original
+ * 3DGS ("all other settings"); tiling auto. */
 GS_API void gs_field_config_default(gs_field_config* cfg);
 
+/* A new session: the 3DGS field the paper trains while images arrive (Sec. III; the field of
+ * Phase 2, Sec. IV-A), empty, with its Adam state and image registry, on `stream` (a
+ * cudaStream_t; NULL = a non-blocking stream of the field's own, as graph capture needs one).
+ * cfg (host) is copied.  GS_ERR_INVALID_ARG for an invalid configuration (T_I, N_m, T_a,
+ * batch_views outside 1..32, non-positive rates, weights < 0, a tiling not among
+ * gs_tiling_candidates), GS_ERR_OOM / GS_ERR_BUDGET when initial_capacity cannot be reserved.
+ * *out (host) receives the field, owned by the caller until gs_field_destroy. */
 GS_API gs_status gs_field_init(const gs_field_config* cfg, void* stream, gs_field** out);
+/* Release every device and host resource of the field (waits for its stream); NULL is ignored. */
 GS_API gs_status gs_field_destroy(gs_field* f);
 
 /* Replace the field's Gaussians (host, component-major, src_stride >= n); Adam state is
@@ -224,27 +234,51 @@ GS_API gs_status gs_field_set_gaussians(gs_field* f, const float* host_params, i
 GS_API gs_status gs_field_get_gaussians(gs_field* f, float* host_params, float* host_m, float* host_v,
                                  int64_t dst_stride, int64_t* out_n);
 
-/* Register an arriving image (Sec. IV-B): pose and intrinsics, the target image (3 x H x W,
- * host or device per rgb_on_device), and its sparse points (host: xyz n_pts x 3, rgb n_pts x 3
- * in [0, 1], track ids n_pts; any may be NULL when n_pts == 0).  Points farther than
- * add_dist_thresh from every existing sparse point become new Gaussians (3DGS initialisation);
- * track ids shared with earlier images define the overlap matrix M (shared / min count).
- * GS_ERR_BUDGET when growing the field would exceed hbm_budget_bytes. */
-GS_API gs_status gs_add_image(gs_field* f, const gs_camera* cam, const float* rgb_chw, int rgb_on_device,
-                       const float* pts_xyz, const float* pts_rgb, int32_t n_pts, const int64_t* pt_track_ids,
-                       int32_t* out_image_id);
+/* Register an arriving image (Sec. IV-B; the inputs per image of Sec. III: its pose from the SfM,
+ * the image and its new sparse points with their matches): pose and intrinsics, the target image
+ * rgb_hwc (H x W x 3 interleaved fp32 in [0, 1], the layout image decoders produce; host or device
+ * per rgb_on_device; transposed on the device into the planar layout the loss reads), and its
+ * sparse points (host: xyz n_pts x 3, rgb n_pts x 3 in [0, 1], track ids n_pts; any may be NULL when
+ * n_pts == 0).  Points farther than add_dist_thresh from every existing sparse point become new
+ * Gaussians (3DGS initialisation); track ids (the co-visibility of Sec. IV-C: a track is one
+ * sparse point seen by several images) shared with earlier images define the overlap matrix M
+ * (shared / min count).  Synchronises the field's stream (the number of new Gaussians is read
+ * back), so every host input has been read when it returns.  *out_image_id (host, nullable)
+ * receives the image's id (0, 1, ... in arrival order).  GS_ERR_BUDGET when growing the field would
+ * exceed hbm_budget_bytes; GS_ERR_CAPACITY beyond 4096 images. */
+GS_API gs_status gs_add_image(gs_field* f, const gs_camera* cam, const float* rgb_hwc, int rgb_on_device,
+                              const float* pts_xyz, const float* pts_rgb, int32_t n_pts, const int32_t* pt_track_ids,
+                              int32_t* out_image_id);
+/* The same with the target already planar (3 x H x W), e.g. a render of another field. */
+GS_API gs_status gs_add_image_chw(gs_field* f, const gs_camera* cam, const float* rgb_chw, int rgb_on_device,
+                                  const float* pts_xyz, const float* pts_rgb, int32_t n_pts,
+                                  const int32_t* pt_track_ids, int32_t* out_image_id);
 
-/* Replace a registered image's target (and pose when cam != NULL), e.g. a refined pose. */
-GS_API gs_status gs_set_image(gs_field* f, int32_t image_id, const gs_camera* cam, const float* rgb_chw, int rgb_on_device);
+/* Replace a registered image's target (rgb_hwc, H x W x 3 interleaved, nullable) and/or its pose
+ * (cam, nullable; same size), e.g. a refined pose (Sec. IV-A, Phase 3).  Asynchronous on the
+ * field's stream: a host image in pinned memory is read by the copy the call enqueues, so it must
+ * stay unchanged until the field's next synchronising call (the next gs_optimize_step) returns;
+ * pageable host memory is read before the call returns. */
+GS_API gs_status gs_set_image(gs_field* f, int32_t image_id, const gs_camera* cam, const float* rgb_hwc,
+                              int rgb_on_device);
+/* The same with a planar (3 x H x W) target. */
+GS_API gs_status gs_set_image_chw(gs_field* f, int32_t image_id, const gs_camera* cam, const float* rgb_chw,
+                                  int rgb_on_device);
 
 /* Eq. 3-4: hierarchical weights from image_id over M; returns image_id first, then up to k
  * neighbours by decreasing weight (ties: lower id).  out_ids / out_w hold k + 1 entries. */
 GS_API gs_status gs_select_neighbors(gs_field* f, int32_t image_id, int32_t k, int32_t* out_ids, float* out_w,
                               int32_t* out_n);
 
-/* One optimisation step over n_views registered views (<= 32): render, loss (mean over
- * views), backward, Adam with the position rate = mean over the views of Eq. 8's rate x scene
- * extent; then T_j += 1 for every view.  out_loss (host, nullable). */
+/* One Local & Semi-Global optimisation iteration (Sec. IV-C; the 3DGS iteration of Sec. III, Eq.
+ * 1-2 forward, Eq. 10 loss, the splatting-parallel backward of Sec. IV-D) over n_views registered
+ * views (host array of ids, 1..32): render, loss (mean over views), backward, Adam with the
+ * position rate = mean over the views of Eq. 8's rate x scene extent; then T_j += 1 for every
+ * view (Eq. 7).  One view is the paper's iteration; several are the batched step.  out_loss (host,
+ * nullable) receives the loss.  Synchronises the field's stream once (it checks that the step
+ * completed: instance buffers that overflowed are grown and the step re-run).  Errors:
+ * GS_ERR_INVALID_ARG (bad ids), GS_ERR_CAPACITY (views), GS_ERR_STATE (no Gaussians),
+ * GS_ERR_TIMEOUT (a bounded device wait gave up), GS_ERR_CUDA. */
 GS_API gs_status gs_optimize_step(gs_field* f, const int32_t* view_ids, int32_t n_views, float* out_loss);
 
 typedef struct gs_integrate_stats {
@@ -274,10 +308,18 @@ GS_API gs_status gs_integrate(gs_field* f, int32_t image_id, gs_integrate_stats*
  * with gs_set_image. */
 GS_API gs_status gs_initial_training(gs_field* f, int32_t iterations, int32_t max_steps, gs_integrate_stats* out_stats);
 
-/* Render the field from any camera: out_rgb_chw (device, 3 x H x W), out_T (device, nullable). */
+/* Render the field from any camera (the forward of Eq. 1-2 without a loss; Sec. III's output,
+ * the trained field, viewed): out_rgb_chw (device, 3 x H x W fp32, written), out_T (device,
+ * H x W final transmittance, nullable).  Synchronises the field's stream.  GS_ERR_INVALID_ARG for a
+ * NULL or invalid camera, GS_ERR_STATE for an empty field. */
 GS_API gs_status gs_render(gs_field* f, const gs_camera* cam, float* out_rgb_chw, float* out_T);
 
-typedef struct gs_field_stats {
+/* The size of the field and the device memory it holds (Sec. III's output is the field; the
+ * memory is what admission by HBM budget counts): *n_gaussians and *bytes_in_use (host, each
+ * nullable).  Host-only. */
+GS_API gs_status gs_field_stats(const gs_field* f, size_t* n_gaussians, size_t* bytes_in_use);
+
+typedef struct gs_field_info {
   int64_t n_gaussians;
   int64_t capacity;
   int64_t n_images;
@@ -292,8 +334,14 @@ typedef struct gs_field_stats {
   double last_load_std;    /* Eq. 9 L_load of the last step's first view set: std of G_p over pixels with G_p > 0 */
   gs_tiling last_tiling;   /* tile shape and blend batch of the last step */
   int32_t pad2;
-} gs_field_stats;
-GS_API gs_status gs_field_stats_get(const gs_field* f, gs_field_stats* out);
+  double last_run_ms;      /* device time of the last run of steps: CUDA events on the field's stream before
+                              its first and after its last step (its own readback not included) */
+  int64_t last_run_steps;  /* steps of that run */
+  uint64_t last_h2d_bytes; /* host->device bytes the library staged for that run (step parameters, views) */
+  uint64_t last_d2h_bytes; /* device->host bytes it read back after that run (ledger, control block) */
+} gs_field_info;
+/* Everything gs_field_stats gives and the bookkeeping of the last step (host-only). */
+GS_API gs_status gs_field_info_get(const gs_field* f, gs_field_info* out);
 
 /* Per-image bookkeeping: T_j (iterations trained, Eq. 7) and the overlap row M[image, :]. */
 GS_API gs_status gs_image_info(const gs_field* f, int32_t image_id, int32_t* out_T, float* out_M_row, int32_t row_len);

@@ -103,12 +103,14 @@ class IntegrateStats(ctypes.Structure):
                 ("new_gaussians", ctypes.c_int32), ("mean_loss", ctypes.c_double), ("pairs", ctypes.c_uint64)]
 
 
-class FieldStats(ctypes.Structure):
+class FieldInfo(ctypes.Structure):
     _fields_ = [("n_gaussians", ctypes.c_int64), ("capacity", ctypes.c_int64), ("n_images", ctypes.c_int64),
                 ("adam_step", ctypes.c_int64), ("bytes_in_use", ctypes.c_uint64), ("last_pairs", ctypes.c_uint64),
                 ("last_blended", ctypes.c_uint64), ("last_instances", ctypes.c_int64), ("last_kernels", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("last_loss", ctypes.c_double), ("last_load_std", ctypes.c_double),
-                ("last_tiling", Tiling), ("pad2", ctypes.c_int32)]
+                ("last_tiling", Tiling), ("pad2", ctypes.c_int32), ("last_run_ms", ctypes.c_double),
+                ("last_run_steps", ctypes.c_int64), ("last_h2d_bytes", ctypes.c_uint64),
+                ("last_d2h_bytes", ctypes.c_uint64)]
 
 
 P = ctypes.c_void_p
@@ -137,13 +139,16 @@ SYMBOLS = {
     "gs_field_set_gaussians": ([P, P, I64, I64], I32),
     "gs_field_get_gaussians": ([P, P, P, P, I64, P], I32),
     "gs_add_image": ([P, P, P, ctypes.c_int, P, P, I32, P, P], I32),
+    "gs_add_image_chw": ([P, P, P, ctypes.c_int, P, P, I32, P, P], I32),
     "gs_set_image": ([P, I32, P, P, ctypes.c_int], I32),
+    "gs_set_image_chw": ([P, I32, P, P, ctypes.c_int], I32),
     "gs_select_neighbors": ([P, I32, I32, P, P, P], I32),
     "gs_optimize_step": ([P, P, I32, P], I32),
     "gs_integrate": ([P, I32, P], I32),
     "gs_initial_training": ([P, I32, I32, P], I32),
     "gs_render": ([P, P, P, P], I32),
-    "gs_field_stats_get": ([P, P], I32),
+    "gs_field_stats": ([P, P, P], I32),
+    "gs_field_info_get": ([P, P], I32),
     "gs_image_info": ([P, I32, P, P, I32], I32),
     "gs_image_lr": ([P, I32, P], I32),
     "gs_field_snapshot": ([P], I32),
@@ -445,47 +450,63 @@ class Field:
             return p, m[:, :n], v[:, :n]
         return p
 
-    def add_image(self, cam, rgb, pts_xyz=None, pts_rgb=None, tracks=None):
-        """rgb: numpy (3, H, W) float32 (host) or a CUDA tensor."""
-        cam_c = Camera.of(cam)
-        on_dev = 0
-        keep = None
-        if hasattr(rgb, "is_cuda") and rgb.is_cuda:
+    @staticmethod
+    def _image_arg(rgb, width, height):
+        """(pointer, on_device, interleaved, keep-alive) of a target image: (H, W, 3) is interleaved
+        (gs_add_image / gs_set_image), (3, H, W) or flat planar (the _chw entry points)."""
+        if hasattr(rgb, "data_ptr"):
             keep = rgb.contiguous()
             ptr = ctypes.c_void_p(keep.data_ptr())
-            on_dev = 1
-        elif hasattr(rgb, "data_ptr"):
-            keep = rgb.contiguous()
-            ptr = ctypes.c_void_p(keep.data_ptr())
+            on_dev = 1 if keep.is_cuda else 0
         else:
             keep = np.ascontiguousarray(rgb, np.float32)
             ptr = keep.ctypes.data_as(ctypes.c_void_p)
+            on_dev = 0
+        shape = tuple(keep.shape)
+        if width is None:  # size unknown here (a field loaded from a file): the shape decides
+            hwc = len(shape) == 3 and shape[2] == 3 and shape[0] != 3
+        elif shape == (height, width, 3):
+            hwc = True
+        elif shape == (3, height, width) or shape == (3 * height * width,):
+            hwc = False
+        else:
+            raise ValueError(f"image of shape {shape} is neither ({height}, {width}, 3) nor (3, {height}, {width})")
+        return ptr, on_dev, hwc, keep
+
+    def add_image(self, cam, rgb, pts_xyz=None, pts_rgb=None, tracks=None):
+        """rgb: (H, W, 3) interleaved or (3, H, W) planar float32, numpy (host) or a torch tensor."""
+        cam_c = Camera.of(cam)
+        ptr, on_dev, hwc, keep = self._image_arg(rgb, cam_c.width, cam_c.height)
         n_pts = 0 if pts_xyz is None else len(pts_xyz)
         xyz = np.ascontiguousarray(pts_xyz, np.float32) if n_pts else None
         prgb = np.ascontiguousarray(pts_rgb, np.float32) if n_pts else None
-        tr = np.ascontiguousarray(tracks, np.int64) if (n_pts and tracks is not None) else None
+        tr = np.ascontiguousarray(tracks, np.int32) if (n_pts and tracks is not None) else None
         out = ctypes.c_int32()
-        _check(self._lib.gs_add_image(self._h, ctypes.byref(cam_c), ptr, on_dev,
-                                      xyz.ctypes.data_as(ctypes.c_void_p) if xyz is not None else None,
-                                      prgb.ctypes.data_as(ctypes.c_void_p) if prgb is not None else None, n_pts,
-                                      tr.ctypes.data_as(ctypes.c_void_p) if tr is not None else None,
-                                      ctypes.byref(out)))
+        fn = self._lib.gs_add_image if hwc else self._lib.gs_add_image_chw
+        _check(fn(self._h, ctypes.byref(cam_c), ptr, on_dev,
+                  xyz.ctypes.data_as(ctypes.c_void_p) if xyz is not None else None,
+                  prgb.ctypes.data_as(ctypes.c_void_p) if prgb is not None else None, n_pts,
+                  tr.ctypes.data_as(ctypes.c_void_p) if tr is not None else None, ctypes.byref(out)))
+        del keep
+        if not hasattr(self, "_sizes"):
+            self._sizes = {}
+        self._sizes[out.value] = (cam_c.width, cam_c.height)
         return out.value
 
     def set_image(self, image_id, rgb=None, cam=None):
+        """Replace a registered image's target ((H, W, 3) or (3, H, W)) and/or pose.  A pinned host
+        tensor is read asynchronously (keep it unchanged until the next step returns)."""
         cam_c = Camera.of(cam) if cam is not None else None
-        ptr, on_dev = None, 0
-        keep = None
+        ptr, on_dev, hwc, keep = None, 0, False, None
         if rgb is not None:
-            if hasattr(rgb, "data_ptr"):
-                keep = rgb.contiguous()
-                ptr = ctypes.c_void_p(keep.data_ptr())
-                on_dev = 1 if keep.is_cuda else 0
+            if cam_c is not None:
+                W, H = cam_c.width, cam_c.height
             else:
-                keep = np.ascontiguousarray(rgb, np.float32)
-                ptr = keep.ctypes.data_as(ctypes.c_void_p)
-        _check(self._lib.gs_set_image(self._h, int(image_id), ctypes.byref(cam_c) if cam_c is not None else None, ptr,
-                                      on_dev))
+                W, H = getattr(self, "_sizes", {}).get(int(image_id), (None, None))
+            ptr, on_dev, hwc, keep = self._image_arg(rgb, W, H)
+        self._keep_image = keep  # the asynchronous copy reads it after this call returns
+        fn = self._lib.gs_set_image if hwc else self._lib.gs_set_image_chw
+        _check(fn(self._h, int(image_id), ctypes.byref(cam_c) if cam_c is not None else None, ptr, on_dev))
 
     def select_neighbors(self, image_id, k):
         ids = (ctypes.c_int32 * (k + 1))()
@@ -546,11 +567,18 @@ class Field:
         return (img, T) if want_T else img
 
     def stats(self):
-        st = FieldStats()
-        _check(self._lib.gs_field_stats_get(self._h, ctypes.byref(st)))
-        out = {k: getattr(st, k) for k, _ in FieldStats._fields_}
+        """gs_field_info_get as a dict (size, memory, and the last step's and run's bookkeeping)."""
+        st = FieldInfo()
+        _check(self._lib.gs_field_info_get(self._h, ctypes.byref(st)))
+        out = {k: getattr(st, k) for k, _ in FieldInfo._fields_}
         out["last_tiling"] = st.last_tiling.astuple()
         return out
+
+    def footprint(self):
+        """(Gaussians, device bytes in use) by gs_field_stats."""
+        n, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(self._lib.gs_field_stats(self._h, ctypes.byref(n), ctypes.byref(b)))
+        return int(n.value), int(b.value)
 
     def autotune(self, view_ids, reps=3):
         """Time every compiled tiling on these views; returns the choice and ms per candidate."""

@@ -271,6 +271,13 @@ struct Field {
   unsigned long long last_pairs = 0, last_blended = 0, last_instances = 0;
   double last_load_std = 0.0;
   int last_kernels = 0;
+  // the last run of steps: device time between events recorded before its first and after its last
+  // step (no readback inside), its steps, and the bytes staged to and read from the device
+  cudaEvent_t run_ev[2] = {nullptr, nullptr};
+  double last_run_ms = 0.0;
+  long long last_run_steps = 0;
+  unsigned long long last_h2d_bytes = 0, last_d2h_bytes = 0;
+  DevBuf hwc_stage;  // an interleaved host image on its way to the planar layout
   size_t own_bytes = 0;
   // snapshot (gs_field_snapshot / gs_field_restore)
   DevBuf snap_p, snap_m, snap_v;
@@ -300,6 +307,9 @@ struct Field {
     snap_m.release(&own_bytes);
     snap_v.release(&own_bytes);
     canary_flags.release(&own_bytes);
+    hwc_stage.release(&own_bytes);
+    for (cudaEvent_t& e : run_ev)
+      if (e) cudaEventDestroy(e);
     DevBuf* pts[] = {&pts_xyz,   &pts_next,  &grid_keys,  &grid_head,   &new_rgb,
                      &far_flags, &far_off,   &far_count,  &pts_next_c,  &grid_keys_c, &grid_head_c};
     for (DevBuf* b : pts) b->release(&own_bytes);
@@ -330,6 +340,7 @@ struct Field {
           {"raster dimage", &R.own_dimage}};
       v.insert(v.end(), std::begin(rr), std::end(rr));
     }
+    v.push_back({"hwc staging", &hwc_stage});
     return v;
   }
 
@@ -810,7 +821,10 @@ struct Field {
     }
     std::vector<int> T0;
     for (auto& im : images) T0.push_back(im.T);
+    for (cudaEvent_t& e : run_ev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return fail(GS_ERR_CUDA, "event creation failed");
     R.reset_ledger(stream);
+    cudaEventRecord(run_ev[0], stream);
     for (size_t k = 0; k < count; ++k) {
       const std::vector<int>& ids = groups[first_group + k];
       double lr_mean = 0;
@@ -825,10 +839,19 @@ struct Field {
       last_tiling = R.tiling;
       for (int id : ids) images[id].T += 1;  // tentative: Eq. 7 counts for the next steps' rates
     }
+    cudaEventRecord(run_ev[1], stream);
     R.read_ledger(stream);
     R.enqueue_readback(stream);
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step: ") + cudaGetErrorString(e));
+    {
+      float ms = 0.f;
+      last_run_ms = cudaEventElapsedTime(&ms, run_ev[0], run_ev[1]) == cudaSuccess ? (double)ms : 0.0;
+      last_run_steps = (long long)count;
+      // per step: the staged step parameters and views; per run: the ledger and control block
+      last_h2d_bytes = (unsigned long long)count * (sizeof(StepParams) + sizeof(ViewDev) * (size_t)R.views.size());
+      last_d2h_bytes = sizeof(Ledger) + sizeof(Control);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     const Ledger& Lg = *R.ledger_h;
@@ -1014,28 +1037,51 @@ gs_status gs_field_get_gaussians(gs_field* ff, float* host, float* host_m, float
   return GS_OK;
 }
 
-gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int on_device, const float* pts_xyz,
-                       const float* pts_rgb, int32_t n_pts, const int64_t* tracks, int32_t* out_id) {
-  gs::TraceRange trace("gs_add_image");
+// Copy an image into the planar device layout: straight for a planar source, through the transpose
+// kernel (and the staging buffer, for a host source) for an interleaved one.
+static gs_status upload_image(Field* f, float* dst, const float* rgb, int on_device, bool hwc, size_t npix) {
+  const size_t bytes = npix * 12;
+  cudaError_t e;
+  if (!hwc) {
+    e = cudaMemcpyAsync(dst, rgb, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, f->stream);
+    return e == cudaSuccess ? GS_OK : fail(GS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  const float* src = rgb;
+  if (!on_device) {
+    gs_status s = f->hwc_stage.reserve(bytes, &f->own_bytes);
+    if (s) return s;
+    e = cudaMemcpyAsync(f->hwc_stage.p, rgb, bytes, cudaMemcpyHostToDevice, f->stream);
+    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+    src = static_cast<const float*>(f->hwc_stage.p);
+  }
+  gs::launch_hwc_to_chw(src, dst, (long long)npix, f->stream);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GS_OK : fail(GS_ERR_CUDA, std::string("image layout: ") + cudaGetErrorString(e));
+}
+
+static gs_status add_image_impl(gs_field* ff, const gs_camera* cam, const float* rgb, int on_device, bool hwc,
+                                const float* pts_xyz, const float* pts_rgb, int32_t n_pts, const int32_t* tracks,
+                                int32_t* out_id) {
   Field* f = F(ff);
   if (!f || !cam || !rgb) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (n_pts < 0 || (n_pts > 0 && (!pts_xyz || !pts_rgb))) return fail(GS_ERR_INVALID_ARG, "bad sparse points");
   if (cam->width <= 0 || cam->height <= 0 || !(cam->fx > 0.f) || !(cam->fy > 0.f))
     return fail(GS_ERR_INVALID_ARG, "bad camera");
   if (f->images.size() >= 4096) return fail(GS_ERR_CAPACITY, "image registry full (4096)");
-  const size_t img_bytes = (size_t)cam->width * cam->height * 3 * 4;
-  if (f->cfg.hbm_budget_bytes && f->bytes_in_use() + img_bytes > f->cfg.hbm_budget_bytes)
+  const size_t npix = (size_t)cam->width * cam->height;
+  const size_t img_bytes = npix * 3 * 4;
+  const size_t stage_grow = (hwc && !on_device && f->hwc_stage.bytes < img_bytes) ? img_bytes - f->hwc_stage.bytes : 0;
+  if (f->cfg.hbm_budget_bytes && f->bytes_in_use() + img_bytes + stage_grow > f->cfg.hbm_budget_bytes)
     return fail(GS_ERR_BUDGET, "registering the image would exceed hbm_budget_bytes");
   gs::Image im;
   im.cam = *cam;
   gs_status s = im.rgb.reserve(img_bytes, &f->own_bytes);
   if (s) return s;
-  cudaError_t e = cudaMemcpyAsync(im.rgb.p, rgb, img_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  f->stream);
-  if (e != cudaSuccess) {
+  if ((s = upload_image(f, static_cast<float*>(im.rgb.p), rgb, on_device, hwc, npix))) {
     im.rgb.release(&f->own_bytes);
-    return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+    return s;
   }
+  cudaError_t e;
   if (tracks && n_pts > 0) {
     im.tracks.assign(tracks, tracks + n_pts);
     std::sort(im.tracks.begin(), im.tracks.end());
@@ -1122,8 +1168,21 @@ gs_status gs_add_image(gs_field* ff, const gs_camera* cam, const float* rgb, int
   return GS_OK;
 }
 
-gs_status gs_set_image(gs_field* ff, int32_t id, const gs_camera* cam, const float* rgb, int on_device) {
-  gs::TraceRange trace("gs_set_image");
+gs_status gs_add_image(gs_field* f, const gs_camera* cam, const float* rgb_hwc, int rgb_on_device, const float* pts_xyz,
+                       const float* pts_rgb, int32_t n_pts, const int32_t* pt_track_ids, int32_t* out_image_id) {
+  gs::TraceRange trace("gs_add_image");
+  return add_image_impl(f, cam, rgb_hwc, rgb_on_device, true, pts_xyz, pts_rgb, n_pts, pt_track_ids, out_image_id);
+}
+
+gs_status gs_add_image_chw(gs_field* f, const gs_camera* cam, const float* rgb_chw, int rgb_on_device,
+                           const float* pts_xyz, const float* pts_rgb, int32_t n_pts, const int32_t* pt_track_ids,
+                           int32_t* out_image_id) {
+  gs::TraceRange trace("gs_add_image");
+  return add_image_impl(f, cam, rgb_chw, rgb_on_device, false, pts_xyz, pts_rgb, n_pts, pt_track_ids, out_image_id);
+}
+
+static gs_status set_image_impl(gs_field* ff, int32_t id, const gs_camera* cam, const float* rgb, int on_device,
+                                bool hwc) {
   Field* f = F(ff);
   if (!f || id < 0 || id >= (int)f->images.size()) return fail(GS_ERR_INVALID_ARG, "bad image id");
   gs::Image& im = f->images[id];
@@ -1132,12 +1191,24 @@ gs_status gs_set_image(gs_field* ff, int32_t id, const gs_camera* cam, const flo
     im.cam = *cam;
   }
   if (rgb) {
-    const size_t bytes = (size_t)im.cam.width * im.cam.height * 12;
-    cudaError_t e = cudaMemcpyAsync(im.rgb.p, rgb, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    f->stream);
-    if (e != cudaSuccess) return fail(GS_ERR_CUDA, cudaGetErrorString(e));
+    const size_t npix = (size_t)im.cam.width * im.cam.height;
+    if (hwc && !on_device && f->cfg.hbm_budget_bytes && f->hwc_stage.bytes < npix * 12 &&
+        f->bytes_in_use() + (npix * 12 - f->hwc_stage.bytes) > f->cfg.hbm_budget_bytes)
+      return fail(GS_ERR_BUDGET, "the staging buffer would exceed hbm_budget_bytes");
+    gs_status s = upload_image(f, static_cast<float*>(im.rgb.p), rgb, on_device, hwc, npix);
+    if (s) return s;
   }
   return GS_OK;
+}
+
+gs_status gs_set_image(gs_field* f, int32_t id, const gs_camera* cam, const float* rgb_hwc, int rgb_on_device) {
+  gs::TraceRange trace("gs_set_image");
+  return set_image_impl(f, id, cam, rgb_hwc, rgb_on_device, true);
+}
+
+gs_status gs_set_image_chw(gs_field* f, int32_t id, const gs_camera* cam, const float* rgb_chw, int rgb_on_device) {
+  gs::TraceRange trace("gs_set_image");
+  return set_image_impl(f, id, cam, rgb_chw, rgb_on_device, false);
 }
 
 gs_status gs_select_neighbors(gs_field* ff, int32_t id, int32_t k, int32_t* out_ids, float* out_w, int32_t* out_n) {
@@ -1374,7 +1445,15 @@ gs_status gs_render(gs_field* ff, const gs_camera* cam, float* out_rgb, float* o
   return R.check_control();
 }
 
-gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
+gs_status gs_field_stats(const gs_field* ff, size_t* n_gaussians, size_t* bytes_in_use) {
+  const Field* f = F(ff);
+  if (!f) return fail(GS_ERR_INVALID_ARG, "NULL field");
+  if (n_gaussians) *n_gaussians = (size_t)f->n;
+  if (bytes_in_use) *bytes_in_use = f->bytes_in_use();
+  return GS_OK;
+}
+
+gs_status gs_field_info_get(const gs_field* ff, gs_field_info* out) {
   const Field* f = F(ff);
   if (!f || !out) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   out->n_gaussians = f->n;
@@ -1391,6 +1470,10 @@ gs_status gs_field_stats_get(const gs_field* ff, gs_field_stats* out) {
   out->last_load_std = f->last_load_std;
   out->last_tiling = gs_tiling{f->last_tiling.tw, f->last_tiling.th, f->last_tiling.batch};
   out->pad2 = 0;
+  out->last_run_ms = f->last_run_ms;
+  out->last_run_steps = f->last_run_steps;
+  out->last_h2d_bytes = f->last_h2d_bytes;
+  out->last_d2h_bytes = f->last_d2h_bytes;
   return GS_OK;
 }
 

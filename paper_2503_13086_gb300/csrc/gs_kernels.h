@@ -84,6 +84,7 @@ struct PointGridDev {
   unsigned mask;              // slots - 1 (slots a power of two, at least twice the points)
   float cell;                 // cell edge
 };
+void launch_hwc_to_chw(const float* src, float* dst, long long npix, cudaStream_t s);
 void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float thr2, int ring, unsigned* far,
                        cudaStream_t s);
 void launch_insert_points(const PointGridDev& g, int* next, long long first, long long count, cudaStream_t s);

@@ -234,6 +234,24 @@ __global__ void __launch_bounds__(128) k_init_gaussians(PointGridDev g, PointGri
   }
 }
 
+// An arriving image in the interleaved layout callers decode to (H x W x 3) into the planar layout
+// the loss reads (3 x H x W): one thread per pixel, 12 contiguous bytes read, three coalesced
+// planes written.
+__global__ void __launch_bounds__(256) k_hwc_to_chw(const float* __restrict__ src, float* __restrict__ dst,
+                                                    long long npix) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npix) return;
+  const float r = src[3 * p], g = src[3 * p + 1], b = src[3 * p + 2];
+  dst[p] = r;
+  dst[npix + p] = g;
+  dst[2 * npix + p] = b;
+}
+
+void launch_hwc_to_chw(const float* src, float* dst, long long npix, cudaStream_t s) {
+  if (npix <= 0) return;
+  k_hwc_to_chw<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(src, dst, npix);
+}
+
 void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float thr2, int ring, unsigned* far,
                        cudaStream_t s) {
   if (n_new <= 0) return;

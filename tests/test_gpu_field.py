@@ -420,3 +420,32 @@ def test_phase3_refinement_takes_updated_poses():
     st = f.initial_training(6, max_steps=30000)
     assert st["iterations"] == 6 and np.isfinite(st["mean_loss"])
     f.close()
+
+
+def test_interleaved_and_planar_targets_give_the_same_step():
+    """gs_add_image takes the interleaved H x W x 3 image decoders produce (host or device) and
+    transposes it on the device; the planar entry point takes 3 x H x W.  All three register the same
+    target: the steps after them are bitwise equal.  gs_field_stats reports the field's size and
+    memory like gs_field_info_get, and gs_set_image replaces a target in either layout."""
+    import torch
+    p, cams, tg = config1(seed=9)
+    hwc = np.ascontiguousarray(np.transpose(tg[0], (1, 2, 0)))
+    res = []
+    for kind in ("chw", "hwc_host", "hwc_device"):
+        f = make_field(use_graph=0)
+        f.set_gaussians(p)
+        src = {"chw": tg[0], "hwc_host": hwc, "hwc_device": torch.tensor(hwc, device="cuda")}[kind]
+        img = f.add_image(cams[0], src)
+        loss = f.optimize_step([img])
+        n, b = f.footprint()
+        st = f.stats()
+        assert n == st["n_gaussians"] == 4096 and b == st["bytes_in_use"] > 0
+        assert st["last_run_steps"] == 1 and st["last_run_ms"] > 0 and st["last_d2h_bytes"] > 0
+        res.append((loss, f.get_gaussians()))
+        # replacing the target with a zero image in the other layout changes the next loss
+        zero = np.zeros((3, 256, 256), np.float32) if kind != "chw" else np.zeros((256, 256, 3), np.float32)
+        f.set_image(img, zero)
+        assert f.optimize_step([img]) != loss
+        f.close()
+    for loss, g in res[1:]:
+        assert loss == res[0][0] and np.array_equal(g, res[0][1])
