@@ -60,8 +60,9 @@ def _declare(L):
     for suf in ("f32", "f64"):
         getattr(L, f"orc_project_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32] + [P] * 9
         getattr(L, f"orc_blend_forward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 12
-        getattr(L, f"orc_blend_backward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 9
-        getattr(L, f"orc_blend_backward_magnitude_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 10
+        getattr(L, f"orc_blend_backward_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 10
+        getattr(L, f"orc_blend_soft_count_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 7
+        getattr(L, f"orc_blend_backward_magnitude_{suf}").argtypes = [I32, I32, I32, I32, I64] + [P] * 11
         getattr(L, f"orc_project_backward_{suf}").argtypes = [P, I64, I64, P, I32, I32, I32, I32, P, P]
         f = getattr(L, f"orc_loss_{suf}")
         f.argtypes = [I32, I32, P, P, F64, P, F64, P, P]
@@ -173,8 +174,9 @@ def blend_forward(cam_size, tile_base, ranges, vals, rec, bg=(0, 0, 0), tile=(16
 
 
 def blend_backward(cam_size, tile_base, ranges, vals, rec, dimg, grad2d, bg=(0, 0, 0), tile=(16, 16),
-                   prec="f32"):
-    """Accumulate the per-record 2D gradients (9 per record) of one view into ``grad2d``."""
+                   prec="f32", load_w=None):
+    """Accumulate the per-record 2D gradients (9 per record) of one view into ``grad2d``.  load_w
+    (H, W), optional: dL/dG_p per pixel of the load term (Eq. 9-10, see ``load_weights``)."""
     dt = _dt(prec)
     W, H = cam_size
     m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
@@ -183,14 +185,57 @@ def blend_backward(cam_size, tile_base, ranges, vals, rec, dimg, grad2d, bg=(0, 
     assert grad2d.dtype == dt and grad2d.flags.c_contiguous
     ranges = _c(ranges, np.uint32)
     vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    lw = None if load_w is None else _c(load_w, dt)
     getattr(lib(), f"orc_blend_backward_{prec}")(
         W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
-        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(grad2d))
+        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(lw), _ptr(grad2d))
     return grad2d
 
 
+def blend_soft_count(cam_size, tile_base, ranges, vals, rec, tile=(16, 16), prec="f64"):
+    """Per pixel, the soft count of Eq. 9's G_p: the sum over its blended Gaussians of
+    255 alpha / (1 + 255 alpha)."""
+    dt = _dt(prec)
+    W, H = cam_size
+    m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
+    out = np.zeros((H, W), dt)
+    ranges = _c(ranges, np.uint32)
+    vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    getattr(lib(), f"orc_blend_soft_count_{prec}")(
+        W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
+        _ptr(rgb), _ptr(out))
+    return out
+
+
+def load_std(gps):
+    """Eq. 9: L_load = std of G_p over the pixels with G_p > 0 (the image's visible range), pooled
+    over the views of a step (``gps``: per-view integer arrays)."""
+    g = np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in gps])
+    g = g[g > 0]
+    return float(np.std(g)) if g.size else 0.0
+
+
+def load_weights(gps, lam):
+    """dL/dG_p of lam x L_load per view (float64 arrays shaped like ``gps``): the derivative of the
+    population standard deviation over the N pixels with G_p > 0, lam (G_p - mean) / (N std); zero
+    at pixels with G_p = 0 and everywhere when std = 0."""
+    g = np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in gps])
+    vis = g > 0
+    out = [np.zeros(np.shape(x), np.float64) for x in gps]
+    if vis.sum() == 0:
+        return out
+    mean = g[vis].mean()
+    std = np.sqrt(max(np.mean(g[vis] ** 2) - mean * mean, 0.0))
+    if std == 0:
+        return out
+    for k, x in enumerate(gps):
+        xv = np.asarray(x, np.float64)
+        out[k] = np.where(xv > 0, lam * (xv - mean) / (vis.sum() * std), 0.0)
+    return out
+
+
 def blend_backward_magnitude(cam_size, tile_base, ranges, vals, rec, dimg, grad2d_mag, terms, bg=(0, 0, 0),
-                             tile=(16, 16), prec="f32"):
+                             tile=(16, 16), prec="f32", load_w=None):
     """The rounding scale of blend_backward's sums: accumulates into ``grad2d_mag`` (9 per record) the
     sum of the magnitudes of every product that enters each 2D gradient, and into ``terms`` (uint32 per
     record) the number of (pixel, contributor) terms.  |fl(g) - g| <= gamma_k * grad2d_mag for k
@@ -204,9 +249,10 @@ def blend_backward_magnitude(cam_size, tile_base, ranges, vals, rec, dimg, grad2
     assert terms.dtype == np.uint32 and terms.flags.c_contiguous
     ranges = _c(ranges, np.uint32)
     vals = _c(vals, np.uint32) if len(vals) else np.zeros(1, np.uint32)
+    lw = None if load_w is None else _c(load_w, dt)
     getattr(lib(), f"orc_blend_backward_magnitude_{prec}")(
         W, H, tile[0], tile[1], int(tile_base), _ptr(ranges), _ptr(vals), _ptr(m2), _ptr(co), _ptr(op),
-        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(grad2d_mag), _ptr(terms))
+        _ptr(rgb), _ptr(bgv), _ptr(d), _ptr(lw), _ptr(grad2d_mag), _ptr(terms))
     return grad2d_mag, terms
 
 
@@ -281,20 +327,28 @@ def render(params, cams, tile=(16, 16), bg=(0, 0, 0), prec="f32", n=None):
     return dict(projs=projs, lists=lists, rec=rec, outs=outs, n=n)
 
 
-def loss_and_grad(params, cams, targets, lam=0.2, tile=(16, 16), bg=(0, 0, 0), prec="f32", n=None):
-    """Batched step semantics: loss = mean over views; returns (loss, grads (59, stride), render)."""
+def loss_and_grad(params, cams, targets, lam=0.2, tile=(16, 16), bg=(0, 0, 0), prec="f32", n=None, lambda_l1=None,
+                  lambda_load=0.0):
+    """Batched step semantics: loss = mean over views of lambda_l1 L1 + lam D-SSIM (lambda_l1 defaults
+    to 1 - lam), plus lambda_load L_load over all the views' pixels (Eq. 9-10); returns
+    (loss, grads (59, stride), render)."""
     dt = _dt(prec)
     params = _c(params, dt)
     r = render(params, cams, tile, bg, prec, n)
     n = r["n"]
     V = len(cams)
+    l1w = 1.0 - lam if lambda_l1 is None else lambda_l1
     grad2d = np.zeros((V * n, 9), dt)
-    total = 0.0
+    lws = load_weights([o["gp"] for o in r["outs"]], lambda_load) if lambda_load else [None] * V
+    total = lambda_load * load_std([o["gp"] for o in r["outs"]]) if lambda_load else 0.0
     for v, c in enumerate(cams):
-        val, d, _, _ = loss(r["outs"][v]["image"], targets[v], lam, True, 1.0 / V, prec)
-        total += val / V
+        # lambda_l1 L1 + lam D-SSIM = (lambda_l1 + lam) ((1 - lam') L1 + lam' D-SSIM), lam' = lam / (lambda_l1 + lam)
+        wsum = l1w + lam
+        lam_n = lam / wsum if wsum > 0 else 0.0
+        val, d, _, _ = loss(r["outs"][v]["image"], targets[v], lam_n, True, wsum / V, prec)
+        total += wsum * val / V
         blend_backward((c.width, c.height), r["lists"]["tile_base"][v], r["lists"]["ranges"], r["lists"]["vals"],
-                       r["rec"], d, grad2d, bg, tile, prec)
+                       r["rec"], d, grad2d, bg, tile, prec, load_w=lws[v])
     grads = np.zeros_like(params)
     for v, c in enumerate(cams):
         project_backward(params, c, grad2d[v * n:(v + 1) * n], grads, tile, prec, n)

@@ -471,7 +471,9 @@ void blend_forward(int W, int H, int tw, int th, int64_t tile_base, const uint32
 // Gradient of Eq. 2 in the natural per-pixel order: the forward walk keeps every contributor
 // with its exact transmittance, then the contributors are visited back to front while the colour
 // behind them (including the background term) is accumulated.  The clamps and cutoffs act as
-// masks.  grad2d per record: d mean2d (2), d conic (a, b, c), d opacity, d rgb (3).
+// masks.  grad2d per record: d mean2d (2), d conic (a, b, c), d opacity, d rgb (3).  load_w
+// (nullable) is dL/dG_p per pixel for the load-balancing term of Eq. 9-10; G_p is a count, and its
+// derivative is taken through the soft count of blend_soft_count below.
 //
 // With kMagnitude the same walk accumulates, instead of each gradient, the sum of the absolute
 // values of every elementary product that enters it (|dL/dC| |c| T, |a dx| + |b dy| for the mean,
@@ -486,7 +488,7 @@ void blend_forward(int W, int H, int tw, int th, int64_t tile_base, const uint32
 template <class T, bool kMagnitude>
 void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
                          const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity,
-                         const T* rgb, const T* bg, const T* dimg, T* grad2d, uint32_t* terms) {
+                         const T* rgb, const T* bg, const T* dimg, const T* load_w, T* grad2d, uint32_t* terms) {
   const int gx = (W + tw - 1) / tw;
   PixelWalk<T> w;
   const int64_t HW = (int64_t)W * H;
@@ -521,6 +523,12 @@ void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const 
             S[ch] += c * wgt;
           }
         }
+        // Eq. 9 through the soft count: dL_load/dG_p (load_w) x d s(alpha) / d alpha,
+        // s(alpha) = 255 alpha / (1 + 255 alpha)
+        if (load_w) {
+          const T q = 1 + (T)255 * e.alpha;
+          dalpha += mag(load_w[pix]) * ((T)255 / (q * q));
+        }
         if (e.clamped) continue;
         const T a = conic[3 * e.rec], b = conic[3 * e.rec + 1], c = conic[3 * e.rec + 2];
         g[5] += dalpha * e.G;
@@ -542,9 +550,29 @@ void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const 
 template <class T>
 void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
                     const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity,
-                    const T* rgb, const T* bg, const T* dimg, T* grad2d) {
+                    const T* rgb, const T* bg, const T* dimg, const T* load_w, T* grad2d) {
   blend_backward_impl<T, false>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity, rgb, bg,
-                                dimg, grad2d, nullptr);
+                                dimg, load_w, grad2d, nullptr);
+}
+
+// The soft count of Eq. 9's G_p: per pixel, the sum over the Gaussians it blends of
+// s(alpha) = 255 alpha / (1 + 255 alpha), a logistic step in log alpha centred on the 1/255 cutoff
+// (s = 1/2 there, -> 1 for alpha >> 1/255).  Its value is not used by the loss (L_load takes the
+// count itself); its derivative is the one the backward gives the count.
+template <class T>
+void blend_soft_count(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
+                      const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity, const T* rgb,
+                      T* soft) {
+  const int gx = (W + tw - 1) / tw;
+  PixelWalk<T> w;
+  for (int py = 0; py < H; ++py)
+    for (int px = 0; px < W; ++px) {
+      const int64_t tile = tile_base + (int64_t)(py / th) * gx + px / tw;
+      walk_pixel<T>(px, py, ranges[2 * tile], ranges[2 * tile + 1], vals, mean2d, conic, opacity, rgb, w, true);
+      T acc = 0;
+      for (const auto& e : w.contrib) acc += (T)255 * e.alpha / (1 + (T)255 * e.alpha);
+      soft[(int64_t)py * W + px] = acc;
+    }
 }
 
 // Chain rule of one visible Gaussian in one view: its 2D gradient g2 (9 values) back to its 59
@@ -869,16 +897,23 @@ extern "C" {
   ORC_EXPORT void orc_blend_backward_##SUF(int W, int H, int tw, int th, int64_t tile_base,         \
                                            const uint32_t* ranges, const uint32_t* vals,            \
                                            const T* mean2d, const T* conic, const T* opacity,       \
-                                           const T* rgb, const T* bg, const T* dimg, T* grad2d) {   \
+                                           const T* rgb, const T* bg, const T* dimg,                \
+                                           const T* load_w, T* grad2d) {                            \
     blend_backward<T>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity, rgb, bg,      \
-                      dimg, grad2d);                                                               \
+                      dimg, load_w, grad2d);                                                       \
+  }                                                                                                \
+  ORC_EXPORT void orc_blend_soft_count_##SUF(int W, int H, int tw, int th, int64_t tile_base,       \
+                                             const uint32_t* ranges, const uint32_t* vals,          \
+                                             const T* mean2d, const T* conic, const T* opacity,     \
+                                             const T* rgb, T* soft) {                               \
+    blend_soft_count<T>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity, rgb, soft); \
   }                                                                                                \
   ORC_EXPORT void orc_blend_backward_magnitude_##SUF(                                             \
       int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges, const uint32_t* vals, \
       const T* mean2d, const T* conic, const T* opacity, const T* rgb, const T* bg, const T* dimg,   \
-      T* grad2d_mag, uint32_t* terms) {                                                            \
+      const T* load_w, T* grad2d_mag, uint32_t* terms) {                                           \
     blend_backward_impl<T, true>(W, H, tw, th, tile_base, ranges, vals, mean2d, conic, opacity,    \
-                                 rgb, bg, dimg, grad2d_mag, terms);                               \
+                                 rgb, bg, dimg, load_w, grad2d_mag, terms);                       \
   }                                                                                                \
   ORC_EXPORT void orc_project_backward_##SUF(const T* params, int64_t n, int64_t stride,            \
                                              const double* cam, int W, int H, int tw, int th,       \

@@ -624,6 +624,81 @@ def test_chain_magnitude_bounds_fp32_rounding():
 
 
 # ------------------------------------------------------------------------------------------
+# Load balancing (Eq. 9-10).  L_load = std of G_p over the pixels with G_p > 0; the count's derivative
+# is taken through the soft count s(alpha) = 255 alpha / (1 + 255 alpha) summed over the blended
+# Gaussians.  Pinned by finite differences: of the standard deviation (its weights dL/dG_p), and of
+# the frozen-weight functional sum_p w_p soft_p(theta) through the whole projection, in fp64.
+# ------------------------------------------------------------------------------------------
+def test_load_weights_are_the_derivative_of_the_standard_deviation():
+    rng = np.random.default_rng(3)
+    gps = [rng.integers(0, 9, size=(5, 7)).astype(np.float64), rng.integers(0, 4, size=(3, 4)).astype(np.float64)]
+    lam = 0.41
+    w = oracle.load_weights(gps, lam)
+    flat = np.concatenate([g.reshape(-1) for g in gps])
+    vis = flat > 0
+
+    def f(x):
+        return lam * np.std(x[vis])
+
+    wf = np.concatenate([x.reshape(-1) for x in w])
+    h = 1e-6
+    for i in np.nonzero(vis)[0][:20]:
+        e = np.zeros_like(flat)
+        e[i] = h
+        assert (f(flat + e) - f(flat - e)) / (2 * h) == pytest.approx(wf[i], rel=1e-6, abs=1e-10)
+    assert (wf[~vis] == 0).all()
+    assert oracle.load_std(gps) == pytest.approx(np.std(flat[vis]), rel=1e-15)
+    # a uniform count has no spread and no gradient
+    same = [np.where(g > 0, 3.0, 0.0) for g in gps]
+    assert all((x == 0).all() for x in oracle.load_weights(same, lam))
+
+
+def test_load_gradient_matches_finite_differences_of_the_soft_count():
+    p, cams = _scene("two_views")
+    n = 5
+    rng = np.random.default_rng(4)
+    ws = [rng.normal(size=(c.height, c.width)) for c in cams]
+
+    def phi(q):
+        r = oracle.render(q, cams, prec="f64", n=n)
+        L = r["lists"]
+        return sum(float((ws[v] * oracle.blend_soft_count((c.width, c.height), L["tile_base"][v], L["ranges"],
+                                                          L["vals"], r["rec"], prec="f64")).sum())
+                   for v, c in enumerate(cams)), r
+
+    _, r0 = phi(p)
+    L = r0["lists"]
+    g2 = np.zeros((len(cams) * n, 9))
+    for v, c in enumerate(cams):
+        oracle.blend_backward((c.width, c.height), L["tile_base"][v], L["ranges"], L["vals"], r0["rec"],
+                              np.zeros((3, c.height, c.width)), g2, prec="f64", load_w=ws[v])
+    g = np.zeros_like(p)
+    for v, c in enumerate(cams):
+        oracle.project_backward(p, c, g2[v * n:(v + 1) * n], g, prec="f64", n=n)
+    assert np.abs(g[:, :n]).max() > 0
+    eps = 1e-6
+    keys = ("last", "gp", "neval")
+    checked = 0
+    for i in range(n):
+        for c in list(range(11)) + [11, 12, 13]:
+            vals, same = [], True
+            for sgn in (1, -1):
+                q = p.copy()
+                q[c, i] += sgn * eps
+                val, rq = phi(q)
+                vals.append(val)
+                same &= all((rq["outs"][v][k] == r0["outs"][v][k]).all() for v in range(len(cams)) for k in keys)
+            if not same:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * eps)
+            assert abs(fd - g[c, i]) <= 1e-6 * max(abs(fd), abs(g[c, i])) + 1e-9, (i, c, fd, g[c, i])
+            checked += 1
+    assert checked > 40
+    # the colour rows take no gradient from the count (s depends on alpha only)
+    assert (g[11:, :n] == 0).all()
+
+
+# ------------------------------------------------------------------------------------------
 # Schedule (Eq. 3-8): a hand-computed example and invariants.
 # ------------------------------------------------------------------------------------------
 def test_schedule_hand_example():
