@@ -344,12 +344,13 @@ def stream_inputs(n_images, seed=0, n_gt=1_500_000, Wv=W, Hv=H, pts_range=(5000,
 
 
 def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, scaling=0, kernel_times=False,
-               thresh=0.0, sparse=0, keep_field=False):
+               thresh=0.0, sparse=0, keep_field=False, weights=None, prune_opacity=None):
     import torch
     from paper_2503_13086_gb300.streaming import StreamingSession
+    w = {} if weights is None else dict(lambda_l1=weights[0], lambda_ssim=weights[1], lambda_load=weights[2])
     sess = StreamingSession(T_I=T_I, N_m=k_neighbours + 1, batch_views=batch, use_graph=graph, async_steps=asyn,
                             scene_extent=7.0, seed=3, batch_scaling=scaling, add_dist_thresh=thresh,
-                            sparse_adam=sparse)
+                            sparse_adam=sparse, prune_opacity=prune_opacity, **w)
     if kernel_times:
         sess.field.set_timing(True)
     pairs, add_s, int_s = 0, [], []
@@ -370,7 +371,10 @@ def run_stream(cams, targets, pts, batch, graph, asyn, T_I=200, k_neighbours=8, 
         kt = {nm: round(x / max(1, ksteps), 4) for nm, x in zip(KERNELS, kms)}
     torch.cuda.synchronize()
     sess.close()
+    steps = sum(r["steps"] for r in sess.results)
     return dict(p50_s=lat["p50"], p99_s=lat["p99"], psnr_db=psnr, n_gaussians=n, arrivals=len(cams),
+                ms_per_step=1e3 * float(np.sum(int_s)) / max(1, steps),
+                pruned=int(sum(r.get("pruned", 0) for r in sess.results)),
                 pairs_per_s=pairs / wall, batch_views=batch, graph=bool(graph), steps_between_syncs=asyn,
                 batch_scaling=scaling, sparse_adam=bool(sparse), add_image_mean_s=float(np.mean(add_s)),
                 integrate_mean_s=float(np.mean(int_s)),
@@ -509,11 +513,15 @@ def run_gs(args):
     if ws == 1:
         wanted = [x for x in args.segments.split(",") if x] if args.segments != "none" else []
         for name in wanted:
-            fn = {"stream": segment_stream, "batched": segment_batched, "serve": segment_serve}[name]
+            fn = {"stream": segment_stream, "load": segment_load, "batched": segment_batched,
+                  "serve": segment_serve}[name]
             smp = ClockSampler(local)
             smp.start()
             t0 = time.perf_counter()
-            res = fn(args)
+            try:
+                res = fn(args)
+            except Exception as exc:  # a failed measurement is reported, the others still run
+                res = {"error": f"{type(exc).__name__}: {exc}"}
             res["wall_s"] = time.perf_counter() - t0
             res["clocks"] = smp.stop()
             segments[name] = res
@@ -542,13 +550,13 @@ def run_gs(args):
                 "gpu_launches": int(launches),
                 "autotuned": auto,
                 "roofline": rl, "clocks": clocks}
-        if "stream" in segments:
+        if "stream" in segments and "graph_async_per_view" in segments["stream"]:
             sd = segments["stream"]
             line["integration_latency_s"] = {"p50": sd["graph_async_per_view"]["p50_s"],
                                              "p99": sd["graph_async_per_view"]["p99_s"], "detail": sd}
-        for nm in ("batched", "serve"):
+        for nm in ("load", "batched", "serve"):
             if nm in segments:
-                line[{"batched": "batched_step", "serve": "serving"}[nm]] = segments[nm]
+                line[{"load": "load_balance", "batched": "batched_step", "serve": "serving"}[nm]] = segments[nm]
         if not args.no_cpu_baseline and ws == 1:
             val, sec, pp = cpu_baseline_run(3, 0)
             line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
@@ -602,6 +610,41 @@ def oracle_psnr_of_field(params, cams, views):
     return out
 
 
+_STREAM_INPUTS = {}
+
+
+def cached_stream_inputs(n):
+    """The full-length stream's inputs, made once per process (the load-balance segment reuses them)."""
+    key = n
+    if key not in _STREAM_INPUTS:
+        _STREAM_INPUTS.clear()
+        _STREAM_INPUTS[key] = stream_inputs(n, seed=0, n_gt=4_000_000)
+    return _STREAM_INPUTS[key]
+
+
+def segment_load(args):
+    """The load-balancing term (Eq. 9-10) in a streaming session: the paper's weights 0.47 L1 +
+    0.12 D-SSIM + 0.41 L_load against the same without L_load (0.47 / 0.12 / 0), both pruning the
+    Gaussians whose opacity fell below 0.005 after every arrival (3DGS's opacity pruning), over the
+    first args.load_arrivals arrivals of the stream: Gaussian count, step time, latency, PSNR."""
+    import gc
+    import paper_2503_13086_gb300 as gs
+    cams, targets, pts = cached_stream_inputs(args.arrivals)
+    k = min(args.load_arrivals, len(cams))
+    cams, targets, pts = cams[:k], targets[:k], pts[:k]
+    gs.autotune_clear()
+    run_stream(cams[:5], targets[:5], pts[:5], batch=1, graph=1, asyn=16, T_I=18, thresh=0.005)
+    res = {}
+    for name, w in (("paper_weights", (0.47, 0.12, 0.41)), ("without_load", (0.47, 0.12, 0.0))):
+        res[name] = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16, thresh=0.005, weights=w,
+                               prune_opacity=0.005)
+        res[name]["weights_l1_ssim_load"] = list(w)
+        gc.collect()
+    res["workload"] = (f"the first {k} arrivals of the stream, per-view graph path, T_I = 200, opacity pruning "
+                       f"below 0.005 after every arrival")
+    return res
+
+
 def segment_stream(args):
     """The streaming session at full length (150 arrivals at 1297 x 840 on a random walk with 60-80 %
     overlap, 5k-20k sparse points each, new points kept down to 0.005 from the field so it grows to
@@ -611,7 +654,7 @@ def segment_stream(args):
     the final field against the oracle's renders of the same field."""
     import gc
     import paper_2503_13086_gb300 as gs
-    cams, targets, pts = stream_inputs(args.arrivals, seed=0, n_gt=4_000_000)
+    cams, targets, pts = cached_stream_inputs(args.arrivals)
     gs.autotune_clear()
     warm = min(args.arrivals, 10)
     for b in (1, 3):
@@ -727,16 +770,18 @@ def serve(args):
     srv = Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)),
                  session_budget_bytes=int(args.serve_session_gb * (1 << 30)), max_active=4)
     out = srv.run(scenes)
-    summ = summarize(out, srv.wall_s)
+    summ = summarize(out, srv.wall_s, srv.log)
     summ.update(peak_device_bytes=srv.peak_device_bytes, wall_s=srv.wall_s,
                 deferred=sum(1 for _, e, _ in srv.log if e == "defer"),
+                throttled=sum(1 for _, e, _ in srv.log if e == "throttle"),
+                admission="by measured bytes in use + 2 x the largest growth per request (estimate before the first)",
                 n_gaussians={sid: r["stats"]["n_gaussians"] for sid, r in out.items()},
                 bytes_in_use={sid: r["stats"]["bytes_in_use"] for sid, r in out.items()},
                 config={"arrivals_per_scene": args.serve_arrivals, "points_per_arrival": [args.serve_points // 2,
                                                                                      args.serve_points],
                         "gt_gaussians": args.serve_gt, "batch_views": args.serve_batch, "batch_scaling": 1,
                         "new_point_threshold": args.serve_thresh,
-                        "hbm_budget_gb": args.serve_budget_gb, "session_budget_gb": args.serve_session_gb})
+                        "hbm_budget_gb": args.serve_budget_gb, "session_estimate_gb": args.serve_session_gb})
     return {"workload": "serving: 4 scenes, 1920x1080 and 1280x720, 1-3 Hz arrivals", **summ}
 
 
@@ -756,11 +801,16 @@ def main():
                          "serve: sessions under an HBM budget; stream: a full-length arrival stream")
     ap.add_argument("--arrivals", type=int, default=150, help="arriving images of the streaming run")
     ap.add_argument("--serve-arrivals", type=int, default=28, help="arriving images per scene of the serving run")
-    ap.add_argument("--segments", default="stream,batched,serve",
-                    help="scene workload: the measurements after the headline (comma list of stream, batched, "
+    ap.add_argument("--segments", default="stream,load,batched,serve",
+                    help="scene workload: the measurements after the headline (comma list of stream, load, batched, "
                          "serve; 'none' for the headline alone)")
-    ap.add_argument("--serve-budget-gb", type=float, default=40.0, help="serve: the server's HBM budget")
-    ap.add_argument("--serve-session-gb", type=float, default=16.0, help="serve: HBM reserved per session")
+    ap.add_argument("--load-arrivals", type=int, default=40,
+                    help="load: arrivals of the load-balancing comparison (the stream's first ones)")
+    ap.add_argument("--serve-budget-gb", type=float, default=24.0,
+                    help="serve: the HBM the sessions may hold together (below 4 sessions' peak, so deferral and "
+                         "throttling are exercised)")
+    ap.add_argument("--serve-session-gb", type=float, default=4.0,
+                    help="serve: a new session's estimate, used for admission until it has measured its own use")
     ap.add_argument("--serve-points", type=int, default=150_000, help="serve: most sparse points per arrival (at least half as many)")
     ap.add_argument("--serve-gt", type=int, default=4_000_000, help="serve: Gaussians of each hidden scene")
     ap.add_argument("--serve-batch", type=int, default=3, help="serve: views per optimisation step")

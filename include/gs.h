@@ -121,6 +121,9 @@ GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, 
 
 /* K8 + K9: gradients of a scalar loss with respect to the parameters of the last forward,
  * given dL/dimage (device, packed like out_image).  image and last are the forward's outputs.
+ * With a load weight > 0 in the last gs_raster_loss, the gradient of lambda_load L_load (Eq. 9,
+ * through the soft count, see gs_field_config) is added; that needs the forward's out_gp
+ * (GS_ERR_STATE without it).
  * out_grads (device, 59 x stride, row stride = stride) is overwritten for i < n.  out_grad2d
  * (device, nullable, 9 floats per record, record = view * stride + i) receives per view the 2D
  * gradient (d mean2d x, y; d conic a, b, c; d opacity; d rgb). */
@@ -196,8 +199,10 @@ typedef struct gs_field_config {
                                2024 for 3DGS), which keeps per-view progress with B x fewer steps */
   float lambda_l1;          /* Eq. 10 L1 weight; -1 = 1 - lambda_ssim (3DGS: 0.8) */
   float lambda_load;        /* Eq. 10 weight of L_load (Eq. 9, std of G_p over the pixels some Gaussian
-                               reaches, all views of the step); G_p is a count, so the term enters the
-                               reported loss only and has no gradient.  The paper's preset:
+                               reaches, all views of the step).  The loss takes the count G_p; the
+                               gradient takes the count's derivative through the soft count
+                               sum 255 alpha / (1 + 255 alpha) over the pixel's blended Gaussians,
+                               times dL_load/dG_p = (G_p - mean) / (N std).  The paper's preset:
                                lambda_l1 0.47, lambda_ssim 0.12, lambda_load 0.41.  Default 0. */
   int32_t densify_stats;    /* 1: every step accumulates the statistics gs_field_densify uses */
   int32_t sparse_adam;      /* 1: a step's Adam updates only the Gaussians with instances in one of

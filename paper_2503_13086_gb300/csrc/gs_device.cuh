@@ -109,7 +109,7 @@ struct StepParams {
   float bg[3];
   float lambda_ssim;     // D-SSIM weight of the loss
   float lambda_l1;       // L1 weight of the loss
-  float lambda_load;     // weight of L_load (Eq. 9) in the reported loss (no gradient)
+  float lambda_load;     // weight of L_load (Eq. 9): added to the loss; its gradient through the soft count
   float lr[6];           // learning rate per parameter group
   float beta1, beta2, eps;
   float step_size_scale; // 1 / (1 - beta1^t)

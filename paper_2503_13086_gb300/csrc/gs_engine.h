@@ -80,6 +80,7 @@ struct Raster {
   int num_sms = 1;
   Tiling tiling;   // tile shape and K6 batch of the next step
   float* dstat = nullptr;  // densification statistics (2 rows of stride floats), nullptr: off
+  const unsigned* last_gp = nullptr;  // G_p of the last forward (the load term's input), nullptr: none
 
   // device buffers
   DevBuf sp_d, views_d;

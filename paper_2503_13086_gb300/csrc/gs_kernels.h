@@ -72,7 +72,8 @@ void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, l
 void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
-                           const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s);
+                           const int* tile_chunks, float4* ginst, const unsigned* gp, const StepParams* sp,
+                           int num_sms, cudaStream_t s);
 
 // Field update (Sec. IV-B): the registered sparse points, hashed by cubic cells.
 constexpr float kCoarseCells = 4.f;  // coarse grid cell edge in fine cells (3-NN search)

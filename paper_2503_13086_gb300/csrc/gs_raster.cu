@@ -358,6 +358,7 @@ gs_status Raster::enqueue_forward_head(cudaStream_t s, const float* params, int 
 }
 
 gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp) {
+  last_gp = gp;
   if (zeroB_pending) cudaMemsetAsync(zeroB.p, 0, zeroB_bytes, s);
   zeroB_pending = false;
   const long long n_items = (long long)n_views * stride;
@@ -392,7 +393,8 @@ void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
 void Raster::enqueue_blend_backward(cudaStream_t s, const float* image, const float* dimage) {
   launch_blend_backward(tiling, vd(), n_views, n_tiles, ranges(), static_cast<unsigned*>(vals0.p), proj(),
                         ctl(), image, dimage, static_cast<float4*>(ckpt.p), static_cast<unsigned*>(cmask.p),
-                        chunk_tile(), static_cast<int*>(tile_chunks.p), static_cast<float4*>(ginst.p), num_sms, s);
+                        chunk_tile(), static_cast<int*>(tile_chunks.p), static_cast<float4*>(ginst.p), last_gp, sp(),
+                        num_sms, s);
   mark(s, 8);
 }
 
@@ -535,6 +537,8 @@ gs_status gs_raster_backward(gs_raster* rr, void* stream, const float* params, c
   if (!r || !params || !image || !last || !dimage || !out_grads) return fail(GS_ERR_INVALID_ARG, "NULL argument");
   if (!r->have_forward) return fail(GS_ERR_STATE, "gs_raster_backward needs a forward first");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (r->sp_h->lambda_load > 0.f && !r->last_gp)
+    return fail(GS_ERR_STATE, "the load term (lambda_load > 0) needs the forward's out_gp");
   gs_status st;
   if ((st = r->stage(s))) return st;
   r->sp_h->adam = 0;

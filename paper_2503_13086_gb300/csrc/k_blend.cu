@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
     const unsigned* __restrict__ vals, const ProjBuffers pb, Control* __restrict__ ctl,
     const float* __restrict__ image, const float* __restrict__ dimage, const float4* __restrict__ ckpt,
     const unsigned* __restrict__ cmask, const int* __restrict__ chunk_tile, const int* __restrict__ tile_chunks,
-    float4* __restrict__ ginst) {
+    float4* __restrict__ ginst, const unsigned* __restrict__ gp, const StepParams* __restrict__ sp) {
   dep_wait();
   dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -386,6 +386,19 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
   constexpr int kPix = Sh::kPix;
   BwdWarp<kPix>& S = reinterpret_cast<BwdWarp<kPix>*>(smem_raw)[warp];
   if (ctl->overflow) return;
+  // Eq. 9-10: dL/dG_p = lambda_load (G_p - mean) / (N std) over the N pixels with G_p > 0 (K6's
+  // moments of all the step's views); it reaches alpha through the soft count's derivative
+  // 255 / (1 + 255 alpha)^2.  load_a = lambda_load / (N std), load_mu = mean; off without G_p.
+  float load_a = 0.f, load_mu = 0.f;
+  if (gp != nullptr && sp->lambda_load > 0.f && ctl->gp_pixels > 0ull) {
+    const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
+    const double var = (double)ctl->gp_sq / np - mean * mean;
+    if (var > 0.0) {
+      load_a = (float)((double)sp->lambda_load / (np * sqrt(var)));
+      load_mu = (float)mean;
+    }
+  }
+  const bool load = load_a != 0.f;
   const unsigned long long M = ctl->m_total;
   const long long n_ids = (long long)(M >> 5) + n_tiles + 1;
   const unsigned lt = (1u << lane) - 1u;
@@ -445,10 +458,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
       unsigned mk[2 * kBwdPairs];
       float2 d0[kBwdPairs], d1[kBwdPairs], d2[kBwdPairs], P0[kBwdPairs], P1[kBwdPairs], P2[kBwdPairs];
       float2 T[kBwdPairs], F0[kBwdPairs], F1[kBwdPairs], F2[kBwdPairs], npx[kBwdPairs], npy[kBwdPairs];
+      float2 LW[kBwdPairs];  // dL/dG_p of the load term per pixel (0 without it)
       unsigned any = 0u;
 #pragma unroll
       for (int pp = 0; pp < kBwdPairs; ++pp) {
-        float st[2][12];
+        float st[2][13];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int i = r0 + 32 * (2 * pp + h) + lane;
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
           float* q = st[h];
           q[0] = q[1] = q[2] = q[3] = q[4] = q[5] = 0.f;
           q[6] = 1.f;
-          q[7] = q[8] = q[9] = q[10] = q[11] = 0.f;
+          q[7] = q[8] = q[9] = q[10] = q[11] = q[12] = 0.f;
           if (pm.y) {
             int ox, oy;
             Sh::slot_xy((int)pm.x, ox, oy);
@@ -479,6 +493,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
             }
             q[10] = -(float)px;
             q[11] = -(float)py;
+            if (load) q[12] = load_a * ((float)gp[V.pix_base + pix] - load_mu);
           }
         }
         d0[pp] = make_float2(st[0][0], st[1][0]);
@@ -493,6 +508,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
         F2[pp] = make_float2(st[0][9], st[1][9]);
         npx[pp] = make_float2(st[0][10], st[1][10]);
         npy[pp] = make_float2(st[0][11], st[1][11]);
+        LW[pp] = make_float2(st[0][12], st[1][12]);
       }
       const float2 one2 = make_float2(1.f, 1.f), neg2 = make_float2(-1.f, -1.f);
       // The round's pixels walk the union of their Gaussians in list order, three at a time.  A
@@ -545,6 +561,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
               const float2 cd = __ffma2_rn(cx, d0[pp], __ffma2_rn(cy, d1[pp], __fmul2_rn(cz, d2[pp])));
               const float2 ninv = make_float2(-__fdividef(1.f, 1.f - alpha.x), -__fdividef(1.f, 1.f - alpha.y));
               float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T[pp], cd));
+              if (load) {  // + dL/dG_p x d/dalpha of 255 alpha / (1 + 255 alpha)
+                const float2 q1 = __ffma2_rn(make_float2(255.f, 255.f), alpha, one2);
+                const float2 q2 = __fmul2_rn(q1, q1);
+                dal = __ffma2_rn(LW[pp], make_float2(__fdividef(255.f, q2.x), __fdividef(255.f, q2.y)), dal);
+              }
               dal.x = oG.x > kAlphaMax ? 0.f : dal.x;
               dal.y = oG.y > kAlphaMax ? 0.f : dal.y;
               const float2 dpow = __fmul2_rn(dal, alpha);
@@ -631,10 +652,11 @@ template <int TW, int TH>
 void launch_backward_instance(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                               const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                               const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
-                              const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
+                              const int* tile_chunks, float4* ginst, const unsigned* gp, const StepParams* sp,
+                              int num_sms, cudaStream_t s) {
   launch_dep(k_blend_backward<TW, TH>, dim3(num_sms * bwd_occupancy<TW, TH>()), dim3(kBwdWarps * 32),
       sizeof(BwdWarp<TW * TH>) * kBwdWarps, s, views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt,
-      cmask, chunk_tile, tile_chunks, ginst);
+      cmask, chunk_tile, tile_chunks, ginst, gp, sp);
 }
 }  // namespace
 
@@ -649,12 +671,13 @@ void init_blend_attributes() {
 void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
-                           const int* tile_chunks, float4* ginst, int num_sms, cudaStream_t s) {
+                           const int* tile_chunks, float4* ginst, const unsigned* gp, const StepParams* sp,
+                           int num_sms, cudaStream_t s) {
   // the backward depends on the tile shape only
 #define GS_BWD(W, H, B)                                                                                          \
   if (tl.tw == W && tl.th == H) {                                                                               \
     launch_backward_instance<W, H>(views, n_views, n_tiles, ranges, vals, pb, ctl, image, dimage, ckpt, cmask, \
-                                   chunk_tile, tile_chunks, ginst, num_sms, s);                                \
+                                   chunk_tile, tile_chunks, ginst, gp, sp, num_sms, s);                        \
     return;                                                                                                    \
   }
   GS_TILINGS(GS_BWD)

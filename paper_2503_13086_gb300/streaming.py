@@ -22,10 +22,14 @@ def percentile(xs, q):
 class StreamingSession:
     """One scene: a Field on its own CUDA stream, fed one image at a time."""
 
-    def __init__(self, stream=None, **config):
+    def __init__(self, stream=None, prune_opacity=None, **config):
+        """config: gs_field_config fields.  prune_opacity: after each arrival's iterations, remove the
+        Gaussians whose opacity fell below it (3DGS's opacity pruning, gs_field_densify with no
+        clone or split), as the load-balancing term of Eq. 10 intends for redundant Gaussians."""
         torch = _torch()
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.field = Field(stream=self.stream, **config)
+        self.prune_opacity = prune_opacity
         self.results = []
 
     def close(self):
@@ -41,9 +45,13 @@ class StreamingSession:
         tb = time.perf_counter()
         st = self.field.integrate(img) if n1 > 0 else dict(iterations=0, steps=0, key_images=0, mean_loss=0.0,
                                                               pairs=0)
+        pruned = 0
+        if self.prune_opacity is not None and n1 > 0:
+            pruned = self.field.densify(grad_thresh=3.0e38, percent_dense=1.0, min_opacity=self.prune_opacity,
+                                        max_scale=1.0e30)["pruned"]
         t1 = time.perf_counter()
         rec = dict(image_id=img, latency_s=t1 - t0, add_image_s=tb - ta, integrate_s=t1 - tb, new_gaussians=n1 - n0,
-                   n_gaussians=n1, **st)
+                   n_gaussians=n1 - pruned, pruned=pruned, **st)
         self.results.append(rec)
         return rec
 

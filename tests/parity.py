@@ -105,9 +105,11 @@ def check_chain(label, got, ref, mag, n_views, rel=1e-3):
                                    for c, i in np.argwhere(bad)[:10]])
 
 
-def backward_parity(label, ras, g, params, n, cams, dimg, tile=(16, 16), bg=(0, 0, 0)):
+def backward_parity(label, ras, g, params, n, cams, dimg, tile=(16, 16), bg=(0, 0, 0), lambda_load=0.0):
     """K8 and K9 of the raster's last forward (``g`` from helpers.gpu_forward) against the oracle on
-    the same inputs; returns the GPU's parameter gradients (59, stride) and 2D gradients."""
+    the same inputs; returns the GPU's parameter gradients (59, stride) and 2D gradients.  With
+    lambda_load (the weight the raster's last loss call used) the oracle adds the load term's
+    gradient, its dL/dG_p taken from the oracle's G_p on the same records (oracle.load_weights)."""
     sizes = [(c["width"], c["height"]) for c in cams]
     stride = params.shape[1]
     grads, grad2d = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg, want_grad2d=True)
@@ -120,11 +122,14 @@ def backward_parity(label, ras, g, params, n, cams, dimg, tile=(16, 16), bg=(0, 
     mag2 = np.zeros((nrec, 9), np.float64)
     terms = np.zeros(nrec, np.uint32)
     rec64 = {k: v.astype(np.float64) for k, v in g["rec"].items()}
-    _, ties, gpmax = tie_pixels(sizes, L, g["rec"], tile, bg)
+    outs, ties, gpmax = tie_pixels(sizes, L, g["rec"], tile, bg)
+    lws = oracle.load_weights([o["gp"] for o in outs], lambda_load) if lambda_load else [None] * len(sizes)
     for v, s in enumerate(sizes):
-        oracle.blend_backward(s, L["tile_base"][v], L["ranges"], L["vals"], g["rec"], ds[v], ref2, bg, tile, "f32")
+        lw32 = None if lws[v] is None else lws[v].astype(np.float32)
+        oracle.blend_backward(s, L["tile_base"][v], L["ranges"], L["vals"], g["rec"], ds[v], ref2, bg, tile, "f32",
+                              load_w=lw32)
         oracle.blend_backward_magnitude(s, L["tile_base"][v], L["ranges"], L["vals"], rec64, ds[v].astype(np.float64),
-                                        mag2, terms, bg, tile, "f64")
+                                        mag2, terms, bg, tile, "f64", load_w=lws[v])
     check_grad2d(label, grad2d, ref2, mag2, terms, gpmax, ties)
     ref = np.zeros_like(params)
     mag = np.zeros(params.shape, np.float64)
@@ -136,7 +141,8 @@ def backward_parity(label, ras, g, params, n, cams, dimg, tile=(16, 16), bg=(0, 
     return grads, grad2d
 
 
-def raster_gradients(params, n, cams, targets, lam=0.2, tiling=(16, 16, 256), label="step", lambda_l1=None):
+def raster_gradients(params, n, cams, targets, lam=0.2, tiling=(16, 16, 256), label="step", lambda_l1=None,
+                     lambda_load=0.0):
     """The GPU's loss and parameter gradients of one step's views through the stateless raster (the
     kernels a session step runs), each stage checked against the oracle on the same inputs."""
     import torch
@@ -147,8 +153,9 @@ def raster_gradients(params, n, cams, targets, lam=0.2, tiling=(16, 16, 256), la
         ras.set_tiling(*tiling)
         g = gpu_forward(ras, params, n, cams)
         tg = np.concatenate([np.asarray(t, np.float32).reshape(-1) for t in targets])
-        loss, dimg = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), lam, lambda_l1=lambda_l1)
-        grads, _ = backward_parity(label, ras, g, params, n, cams, dimg, tiling[:2])
+        loss, dimg = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), lam, lambda_l1=lambda_l1,
+                              lambda_load=lambda_load)
+        grads, _ = backward_parity(label, ras, g, params, n, cams, dimg, tiling[:2], lambda_load=lambda_load)
         return loss, grads
     finally:
         ras.close()

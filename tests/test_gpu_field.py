@@ -253,8 +253,9 @@ def test_new_gaussians_start_with_zero_adam_moments_after_restore():
 
 def test_paper_loss_preset_with_the_load_term():
     """Eq. 10 with the paper's weights: 0.47 L1 + 0.12 D-SSIM + 0.41 L_load, L_load = std of G_p
-    over the pixels some Gaussian reaches (Eq. 9); G_p is a count, so the load term changes the
-    reported loss but not the gradient."""
+    over the pixels some Gaussian reaches (Eq. 9), its gradient through the soft count: the session
+    step's loss against the oracle's, its Adam update on the step's gradients (each stage of which
+    is checked against the oracle with the load term)."""
     p, cams, tg = config1(seed=7)
     f = make_field(use_graph=0, lambda_l1=0.47, lambda_ssim=0.12, lambda_load=0.41)
     f.set_gaussians(p)
@@ -262,11 +263,11 @@ def test_paper_loss_preset_with_the_load_term():
     lr = f.image_lr(img)
     loss = f.optimize_step([img])
     got = f.get_gaussians()
-    L, g, r = oracle.loss_and_grad(p, [ocam(cams[0])], tg, lam=0.12 / 0.59, prec="f32")
-    gp = r["outs"][0]["gp"].astype(np.float64)
-    ref_loss = 0.59 * L + 0.41 * float(np.std(gp[gp > 0]))
+    ref_loss, _, _ = oracle.loss_and_grad(p, [ocam(cams[0])], tg, lam=0.12, lambda_l1=0.47, lambda_load=0.41,
+                                          prec="f32")
     assert abs(loss - ref_loss) <= 1e-5 * max(1.0, abs(ref_loss)), (loss, ref_loss)
-    _, grads = raster_gradients(p, 4096, cams, tg, lam=0.12, lambda_l1=0.47, label="paper-weights step")
+    _, grads = raster_gradients(p, 4096, cams, tg, lam=0.12, lambda_l1=0.47, lambda_load=0.41,
+                                label="paper-weights step")
     check_adam("paper-weights step", got, p, grads, [lr] + LRS_REST, 1)
     f.close()
 

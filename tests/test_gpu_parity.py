@@ -209,6 +209,30 @@ def test_backward(run, ras):
     backward_parity(run["name"], ras, g, run["params"], run["n"], run["cams"], dimg)
 
 
+def test_backward_with_the_load_term(run, ras):
+    """Eq. 9-10 with the paper's weight 0.41: the raster's loss adds lambda_load std(G_p) and the
+    backward the load term's gradient through the soft count; both stages against the oracle on the
+    same records, and the loss value against the oracle's."""
+    import torch
+    g = gpu_forward(ras, run["params"], run["n"], run["cams"])
+    tg = np.concatenate([t.reshape(-1) for t in run["targets"]]).astype(np.float32)
+    loss, dimg = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), 0.12, lambda_l1=0.47, lambda_load=0.41)
+    L, outs = _oracle_forward_on_gpu_records(run)
+    imgs = split_views(g["out"]["image"].cpu().numpy(), run["sizes"], 3)
+    V = len(imgs)
+    ref = 0.41 * oracle.load_std([o["gp"] for o in outs])
+    for v in range(V):
+        val, _, _, _ = oracle.loss(imgs[v], run["targets"][v], 0.12 / 0.59, False, 1.0, prec="f32")
+        ref += 0.59 * val / V
+    assert abs(loss - ref) <= 1e-5 * max(1.0, abs(ref)), (loss, ref)
+    with_load, _ = backward_parity(run["name"] + " with L_load", ras, g, run["params"], run["n"], run["cams"], dimg,
+                                   lambda_load=0.41)
+    # the load term changes the gradient (it is not only in the reported loss)
+    _, dimg2 = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), 0.12, lambda_l1=0.47, lambda_load=0.0)
+    without, _ = ras.backward(g["P"], g["out"]["image"], g["out"]["last"], dimg2)
+    assert np.abs(with_load - without.cpu().numpy()).max() > 0
+
+
 def test_adam_kernel():
     import torch
     import paper_2503_13086_gb300 as gs
