@@ -479,13 +479,14 @@ GS_API gs_status gs_wait_probe(uint32_t spin_limit, uint32_t out_error[2], float
  * in the library's own device memory, which every GPU that loads the library keeps until exit.
  *   counts      (device, n uint32, 16-byte aligned)          input
  *   out_offsets (device, n uint32, 16-byte aligned)          out_offsets[i] = sum of counts[0..i)
- *   out_total   (device, one uint64, nullable)               sum of all counts
+ *   out_total   (device, one uint64, nullable)               sum of all counts (UINT64_MAX: see below)
  * n may be 0 .. 2^24 (GS_ERR_CAPACITY beyond); the sum must fit in 32 bits for the offsets.
  * Asynchronous on stream.  The first call on a device also looks up the scratch array's device
  * address; make that first call before any stream capture.  All calls share the one scratch
  * array: calls that can overlap on the GPU (other streams, other threads) race and give wrong
  * results, so serialise them.  The look-back waits are bounded; if one gives up, the offsets are
- * unspecified (no error is reported, as nothing is read back). */
+ * unspecified and *out_total is set to UINT64_MAX (a sum of 32-bit counts never reaches it), so a
+ * caller that passes out_total can tell; nothing is read back to the host. */
 GS_API gs_status gs_scan_noalloc(void* stream, const uint32_t* counts, int64_t n, uint32_t* out_offsets,
                                  uint64_t* out_total);
 

@@ -29,6 +29,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
+// The total, or UINT64_MAX when a look-back wait of the scan gave up (its offsets are then not
+// valid): the one result a caller reads, so a timeout is visible without a host readback.
+__global__ void k_noalloc_total(const Control* __restrict__ ctl, unsigned long long* __restrict__ out_total) {
+  *out_total = (ctl->error & kErrTimeout) ? ~0ull : ctl->m_total;
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -65,10 +71,7 @@ extern "C" GS_API gs_status gs_scan_noalloc(void* stream, const uint32_t* counts
   e = cudaMemsetAsync(base, 0, kCtlBytes + (size_t)tiles * 8, s);
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   if (n > 0) launch_scan(counts, out_offsets, n, state, ctl, ~0ull, nullptr, s);
-  if (out_total) {
-    e = cudaMemcpyAsync(out_total, &ctl->m_total, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-  }
+  if (out_total) k_noalloc_total<<<1, 1, 0, s>>>(ctl, reinterpret_cast<unsigned long long*>(out_total));
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("gs_scan_noalloc launch: ") + cudaGetErrorString(e));
   return GS_OK;
