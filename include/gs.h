@@ -115,7 +115,8 @@ typedef struct gs_loss_weights {
  * zero padding, C1 = 0.01^2, C2 = 0.03^2, means over 3 H W), plus lambda_load L_load when that weight
  * is > 0.  w (host, nullable; NULL = 3DGS's 0.8 / 0.2 / 0) must hold weights >= 0
  * (GS_ERR_INVALID_ARG otherwise).  image/target (device) are packed like out_image.  out_dimage
- * (device, nullable) receives dL/dimage.  out_loss (host, nullable) receives L and synchronises. */
+ * (device, nullable) receives dL/dimage.  out_loss (host, nullable) receives L and synchronises.
+ * May be called again on the same forward (e.g. with other weights). */
 GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, const float* target,
                                 const gs_loss_weights* w, float* out_dimage, double* out_loss);
 
@@ -126,7 +127,8 @@ GS_API gs_status gs_raster_loss(gs_raster* r, void* stream, const float* image, 
  * (GS_ERR_STATE without it).
  * out_grads (device, 59 x stride, row stride = stride) is overwritten for i < n.  out_grad2d
  * (device, nullable, 9 floats per record, record = view * stride + i) receives per view the 2D
- * gradient (d mean2d x, y; d conic a, b, c; d opacity; d rgb). */
+ * gradient (d mean2d x, y; d conic a, b, c; d opacity; d rgb).  May be called again on the same
+ * forward (another dL/dimage). */
 GS_API gs_status gs_raster_backward(gs_raster* r, void* stream, const float* params, const float* image,
                              const uint32_t* last, const float* dimage, float* out_grads, float* out_grad2d);
 

@@ -519,6 +519,8 @@ gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const 
   r->sp_h->lambda_l1 = lw.lambda_l1;
   r->sp_h->lambda_load = lw.lambda_load;
   r->upload(s);
+  // the loss may run again on the same forward (other weights): its CTA counter starts at 0
+  cudaMemsetAsync(&r->ctl()->loss_done, 0, sizeof(unsigned), s);
   r->enqueue_loss(s, image, out_dimage);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("loss launch: ") + cudaGetErrorString(e));
@@ -543,6 +545,8 @@ gs_status gs_raster_backward(gs_raster* rr, void* stream, const float* params, c
   if ((st = r->stage(s))) return st;
   r->sp_h->adam = 0;
   r->upload(s);
+  // the backward may run again on the same forward (another dL/dimage): its work counter starts at 0
+  cudaMemsetAsync(&r->ctl()->bwd_work, 0, sizeof(unsigned), s);
   r->enqueue_backward(s, const_cast<float*>(params), image, last, dimage, out_grads, nullptr, nullptr, out_grad2d);
   r->enqueue_readback(s);
   cudaError_t e = cudaStreamSynchronize(s);
