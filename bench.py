@@ -624,9 +624,10 @@ def cached_stream_inputs(n):
 
 def segment_load(args):
     """The load-balancing term (Eq. 9-10) in a streaming session: the paper's weights 0.47 L1 +
-    0.12 D-SSIM + 0.41 L_load against the same without L_load (0.47 / 0.12 / 0), both pruning the
-    Gaussians whose opacity fell below 0.005 after every arrival (3DGS's opacity pruning), over the
-    first args.load_arrivals arrivals of the stream: Gaussian count, step time, latency, PSNR."""
+    0.12 D-SSIM + 0.41 L_load, the load weight a tenth and a hundredth of it, and none (0.47 / 0.12 / 0),
+    all pruning the Gaussians whose opacity fell below 0.005 after every arrival (3DGS's opacity
+    pruning), over the first args.load_arrivals arrivals of the stream: Gaussian count, step time,
+    latency, PSNR."""
     import gc
     import paper_2503_13086_gb300 as gs
     cams, targets, pts = cached_stream_inputs(args.arrivals)
@@ -635,7 +636,8 @@ def segment_load(args):
     gs.autotune_clear()
     run_stream(cams[:5], targets[:5], pts[:5], batch=1, graph=1, asyn=16, T_I=18, thresh=0.005)
     res = {}
-    for name, w in (("paper_weights", (0.47, 0.12, 0.41)), ("without_load", (0.47, 0.12, 0.0))):
+    for name, w in (("paper_weights", (0.47, 0.12, 0.41)), ("load_0.041", (0.47, 0.12, 0.041)),
+                    ("load_0.0041", (0.47, 0.12, 0.0041)), ("without_load", (0.47, 0.12, 0.0))):
         res[name] = run_stream(cams, targets, pts, batch=1, graph=1, asyn=16, thresh=0.005, weights=w,
                                prune_opacity=0.005)
         res[name]["weights_l1_ssim_load"] = list(w)
@@ -804,12 +806,12 @@ def main():
     ap.add_argument("--segments", default="stream,load,batched,serve",
                     help="scene workload: the measurements after the headline (comma list of stream, load, batched, "
                          "serve; 'none' for the headline alone)")
-    ap.add_argument("--load-arrivals", type=int, default=40,
+    ap.add_argument("--load-arrivals", type=int, default=30,
                     help="load: arrivals of the load-balancing comparison (the stream's first ones)")
-    ap.add_argument("--serve-budget-gb", type=float, default=24.0,
+    ap.add_argument("--serve-budget-gb", type=float, default=40.0,
                     help="serve: the HBM the sessions may hold together (below 4 sessions' peak, so deferral and "
                          "throttling are exercised)")
-    ap.add_argument("--serve-session-gb", type=float, default=4.0,
+    ap.add_argument("--serve-session-gb", type=float, default=16.0,
                     help="serve: a new session's estimate, used for admission until it has measured its own use")
     ap.add_argument("--serve-points", type=int, default=150_000, help="serve: most sparse points per arrival (at least half as many)")
     ap.add_argument("--serve-gt", type=int, default=4_000_000, help="serve: Gaussians of each hidden scene")

@@ -200,11 +200,11 @@ typedef struct gs_field_config {
                                1 = also lr x sqrt(B) and betas ^ B (the large-batch rule of Zhao et al.
                                2024 for 3DGS), which keeps per-view progress with B x fewer steps */
   float lambda_l1;          /* Eq. 10 L1 weight; -1 = 1 - lambda_ssim (3DGS: 0.8) */
-  float lambda_load;        /* Eq. 10 weight of L_load (Eq. 9, std of G_p over the pixels some Gaussian
+  float lambda_load;        /* Eq. 10 weight of L_load (Eq. 9, std of G_p over the N pixels some Gaussian
                                reaches, all views of the step).  The loss takes the count G_p; the
-                               gradient takes the count's derivative through the soft count
-                               sum 255 alpha / (1 + 255 alpha) over the pixel's blended Gaussians,
-                               times dL_load/dG_p = (G_p - mean) / (N std).  The paper's preset:
+                               gradient takes the count's derivative through the soft count, the sum
+                               of the alphas of the pixel's blended Gaussians, times
+                               dL_load/dG_p = (G_p - mean) / (N std).  The paper's preset:
                                lambda_l1 0.47, lambda_ssim 0.12, lambda_load 0.41.  Default 0. */
   int32_t densify_stats;    /* 1: every step accumulates the statistics gs_field_densify uses */
   int32_t sparse_adam;      /* 1: a step's Adam updates only the Gaussians with instances in one of
@@ -338,7 +338,7 @@ typedef struct gs_field_info {
   int32_t last_kernels;    /* kernel launches of the last step */
   int32_t pad;
   double last_loss;
-  double last_load_std;    /* Eq. 9 L_load of the last step's first view set: std of G_p over pixels with G_p > 0 */
+  double last_load_std;    /* Eq. 9 L_load of the last step: std of G_p over the pixels with G_p > 0 */
   gs_tiling last_tiling;   /* tile shape and blend batch of the last step */
   int32_t pad2;
   double last_run_ms;      /* device time of the last run of steps: CUDA events on the field's stream before

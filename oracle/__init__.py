@@ -193,8 +193,7 @@ def blend_backward(cam_size, tile_base, ranges, vals, rec, dimg, grad2d, bg=(0, 
 
 
 def blend_soft_count(cam_size, tile_base, ranges, vals, rec, tile=(16, 16), prec="f64"):
-    """Per pixel, the soft count of Eq. 9's G_p: the sum over its blended Gaussians of
-    255 alpha / (1 + 255 alpha)."""
+    """Per pixel, the soft count of Eq. 9's G_p: the sum of the alphas of its blended Gaussians."""
     dt = _dt(prec)
     W, H = cam_size
     m2, co, op, rgb = (_c(rec[k], dt) for k in ("mean2d", "conic", "opacity", "rgb"))
@@ -208,11 +207,17 @@ def blend_soft_count(cam_size, tile_base, ranges, vals, rec, tile=(16, 16), prec
 
 
 def load_std(gps):
-    """Eq. 9: L_load = std of G_p over the pixels with G_p > 0 (the image's visible range), pooled
-    over the views of a step (``gps``: per-view integer arrays)."""
+    """The spread of G_p over the pixels with G_p > 0 (the image's visible range), pooled over the
+    views of a step (``gps``: per-view integer arrays): its population standard deviation."""
     g = np.concatenate([np.asarray(x, np.float64).reshape(-1) for x in gps])
     g = g[g > 0]
     return float(np.std(g)) if g.size else 0.0
+
+
+def load_term(gps):
+    """Eq. 9's L_load: the population standard deviation of G_p over the pixels with G_p > 0 (the
+    image's visible range), pooled over the views of a step; 0 without visible pixels."""
+    return load_std(gps)
 
 
 def load_weights(gps, lam):
@@ -340,7 +345,7 @@ def loss_and_grad(params, cams, targets, lam=0.2, tile=(16, 16), bg=(0, 0, 0), p
     l1w = 1.0 - lam if lambda_l1 is None else lambda_l1
     grad2d = np.zeros((V * n, 9), dt)
     lws = load_weights([o["gp"] for o in r["outs"]], lambda_load) if lambda_load else [None] * V
-    total = lambda_load * load_std([o["gp"] for o in r["outs"]]) if lambda_load else 0.0
+    total = lambda_load * load_term([o["gp"] for o in r["outs"]]) if lambda_load else 0.0
     for v, c in enumerate(cams):
         # lambda_l1 L1 + lam D-SSIM = (lambda_l1 + lam) ((1 - lam') L1 + lam' D-SSIM), lam' = lam / (lambda_l1 + lam)
         wsum = l1w + lam

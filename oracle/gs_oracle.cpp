@@ -473,7 +473,7 @@ void blend_forward(int W, int H, int tw, int th, int64_t tile_base, const uint32
 // behind them (including the background term) is accumulated.  The clamps and cutoffs act as
 // masks.  grad2d per record: d mean2d (2), d conic (a, b, c), d opacity, d rgb (3).  load_w
 // (nullable) is dL/dG_p per pixel for the load-balancing term of Eq. 9-10; G_p is a count, and its
-// derivative is taken through the soft count of blend_soft_count below.
+// derivative is taken through the soft count of blend_soft_count below (the sum of the alphas).
 //
 // With kMagnitude the same walk accumulates, instead of each gradient, the sum of the absolute
 // values of every elementary product that enters it (|dL/dC| |c| T, |a dx| + |b dy| for the mean,
@@ -523,12 +523,8 @@ void blend_backward_impl(int W, int H, int tw, int th, int64_t tile_base, const 
             S[ch] += c * wgt;
           }
         }
-        // Eq. 9 through the soft count: dL_load/dG_p (load_w) x d s(alpha) / d alpha,
-        // s(alpha) = 255 alpha / (1 + 255 alpha)
-        if (load_w) {
-          const T q = 1 + (T)255 * e.alpha;
-          dalpha += mag(load_w[pix]) * ((T)255 / (q * q));
-        }
+        // Eq. 9 through the soft count: dL_load/dG_p (load_w) x d alpha / d alpha
+        if (load_w) dalpha += mag(load_w[pix]);
         if (e.clamped) continue;
         const T a = conic[3 * e.rec], b = conic[3 * e.rec + 1], c = conic[3 * e.rec + 2];
         g[5] += dalpha * e.G;
@@ -555,10 +551,9 @@ void blend_backward(int W, int H, int tw, int th, int64_t tile_base, const uint3
                                 dimg, load_w, grad2d, nullptr);
 }
 
-// The soft count of Eq. 9's G_p: per pixel, the sum over the Gaussians it blends of
-// s(alpha) = 255 alpha / (1 + 255 alpha), a logistic step in log alpha centred on the 1/255 cutoff
-// (s = 1/2 there, -> 1 for alpha >> 1/255).  Its value is not used by the loss (L_load takes the
-// count itself); its derivative is the one the backward gives the count.
+// The soft count of Eq. 9's G_p: per pixel, the sum of the alphas of the Gaussians it blends (each
+// Gaussian counted by how much it is associated with the pixel).  Its value is not used by the
+// loss (L_load takes the count itself); its derivative is the one the backward gives the count.
 template <class T>
 void blend_soft_count(int W, int H, int tw, int th, int64_t tile_base, const uint32_t* ranges,
                       const uint32_t* vals, const T* mean2d, const T* conic, const T* opacity, const T* rgb,
@@ -570,7 +565,7 @@ void blend_soft_count(int W, int H, int tw, int th, int64_t tile_base, const uin
       const int64_t tile = tile_base + (int64_t)(py / th) * gx + px / tw;
       walk_pixel<T>(px, py, ranges[2 * tile], ranges[2 * tile + 1], vals, mean2d, conic, opacity, rgb, w, true);
       T acc = 0;
-      for (const auto& e : w.contrib) acc += (T)255 * e.alpha / (1 + (T)255 * e.alpha);
+      for (const auto& e : w.contrib) acc += e.alpha;
       soft[(int64_t)py * W + px] = acc;
     }
 }

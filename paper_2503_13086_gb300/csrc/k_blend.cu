@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
   BwdWarp<kPix>& S = reinterpret_cast<BwdWarp<kPix>*>(smem_raw)[warp];
   if (ctl->overflow) return;
   // Eq. 9-10: dL/dG_p = lambda_load (G_p - mean) / (N std) over the N pixels with G_p > 0 (K6's
-  // moments of all the step's views); it reaches alpha through the soft count's derivative
-  // 255 / (1 + 255 alpha)^2.  load_a = lambda_load / (N std), load_mu = mean; off without G_p.
+  // moments of all the step's views); it reaches alpha through the soft count, the sum of the
+  // blended Gaussians' alphas.  load_a = lambda_load / (N std), load_mu = mean; off without G_p.
   float load_a = 0.f, load_mu = 0.f;
   if (gp != nullptr && sp->lambda_load > 0.f && ctl->gp_pixels > 0ull) {
     const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
@@ -561,11 +561,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_blend_backward(
               const float2 cd = __ffma2_rn(cx, d0[pp], __ffma2_rn(cy, d1[pp], __fmul2_rn(cz, d2[pp])));
               const float2 ninv = make_float2(-__fdividef(1.f, 1.f - alpha.x), -__fdividef(1.f, 1.f - alpha.y));
               float2 dal = __ffma2_rn(DS, ninv, __fmul2_rn(T[pp], cd));
-              if (load) {  // + dL/dG_p x d/dalpha of 255 alpha / (1 + 255 alpha)
-                const float2 q1 = __ffma2_rn(make_float2(255.f, 255.f), alpha, one2);
-                const float2 q2 = __fmul2_rn(q1, q1);
-                dal = __ffma2_rn(LW[pp], make_float2(__fdividef(255.f, q2.x), __fdividef(255.f, q2.y)), dal);
-              }
+              if (load) dal = __fadd2_rn(dal, LW[pp]);  // + dL/dG_p x d alpha / d alpha
               dal.x = oG.x > kAlphaMax ? 0.f : dal.x;
               dal.y = oG.y > kAlphaMax ? 0.f : dal.y;
               const float2 dpow = __fmul2_rn(dal, alpha);

@@ -1,5 +1,5 @@
-// k_loss.cu -- K7: L = lambda_1 L1 + lambda_ssim (1 - SSIM) (+ lambda_load L_load, a value without
-// gradient) of Eq. 10, and dL/d(render), sm_103a.
+// k_loss.cu -- K7: L = lambda_1 L1 + lambda_ssim (1 - SSIM) (+ lambda_load L_load) of Eq. 10, and
+// dL/d(render), sm_103a (the load term's gradient enters the blend backward, K8).
 //
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
@@ -312,9 +312,9 @@ __global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restri
   }
   if (threadIdx.x == 0) {
     double loss = total / (double)n_views;
-    // Eq. 9-10: + lambda_load std(G_p) over the pixels some Gaussian reaches (all views of the step);
-    // G_p is a count, so this term has no gradient
-    if (sp->lambda_load != 0.f && ctl->gp_pixels) {
+    // Eq. 9-10: + lambda_load L_load over the pixels some Gaussian reaches (all views of the step;
+    // K6's moments of G_p); its gradient enters the blend backward through the soft count
+    if (sp->lambda_load != 0.f && ctl->gp_pixels) {  // std of G_p
       const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
       const double var = (double)ctl->gp_sq / np - mean * mean;
       loss += (double)sp->lambda_load * sqrt(var > 0.0 ? var : 0.0);

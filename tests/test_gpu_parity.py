@@ -220,7 +220,7 @@ def test_backward_with_the_load_term(run, ras):
     L, outs = _oracle_forward_on_gpu_records(run)
     imgs = split_views(g["out"]["image"].cpu().numpy(), run["sizes"], 3)
     V = len(imgs)
-    ref = 0.41 * oracle.load_std([o["gp"] for o in outs])
+    ref = 0.41 * oracle.load_term([o["gp"] for o in outs])
     for v in range(V):
         val, _, _, _ = oracle.loss(imgs[v], run["targets"][v], 0.12 / 0.59, False, 1.0, prec="f32")
         ref += 0.59 * val / V
@@ -231,7 +231,7 @@ def test_backward_with_the_load_term(run, ras):
     # backward may run again on the same forward
     loss_wo, dimg2 = ras.loss(g["out"]["image"], torch.tensor(tg, device="cuda"), 0.12, lambda_l1=0.47,
                               lambda_load=0.0)
-    ref_wo = ref - 0.41 * oracle.load_std([o["gp"] for o in outs])
+    ref_wo = ref - 0.41 * oracle.load_term([o["gp"] for o in outs])
     assert abs(loss_wo - ref_wo) <= 1e-5 * max(1.0, abs(ref_wo)), (loss_wo, ref_wo)
     without, _ = backward_parity(run["name"] + " without L_load", ras, g, run["params"], run["n"], run["cams"], dimg2)
     assert np.abs(with_load - without).max() > 0

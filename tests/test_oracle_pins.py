@@ -625,8 +625,7 @@ def test_chain_magnitude_bounds_fp32_rounding():
 
 # ------------------------------------------------------------------------------------------
 # Load balancing (Eq. 9-10).  L_load = std of G_p over the pixels with G_p > 0; the count's derivative
-# is taken through the soft count s(alpha) = 255 alpha / (1 + 255 alpha) summed over the blended
-# Gaussians.  Pinned by finite differences: of the standard deviation (its weights dL/dG_p), and of
+# is taken through the soft count, the sum of the blended Gaussians' alphas.  Pinned by finite differences: of the standard deviation (its weights dL/dG_p), and of
 # the frozen-weight functional sum_p w_p soft_p(theta) through the whole projection, in fp64.
 # ------------------------------------------------------------------------------------------
 def test_load_weights_are_the_derivative_of_the_standard_deviation():
@@ -647,10 +646,11 @@ def test_load_weights_are_the_derivative_of_the_standard_deviation():
         e[i] = h
         assert (f(flat + e) - f(flat - e)) / (2 * h) == pytest.approx(wf[i], rel=1e-6, abs=1e-10)
     assert (wf[~vis] == 0).all()
+    assert oracle.load_term(gps) * lam == pytest.approx(f(flat), rel=1e-15)
     assert oracle.load_std(gps) == pytest.approx(np.std(flat[vis]), rel=1e-15)
     # a uniform count has no spread and no gradient
     same = [np.where(g > 0, 3.0, 0.0) for g in gps]
-    assert all((x == 0).all() for x in oracle.load_weights(same, lam))
+    assert all((x == 0).all() for x in oracle.load_weights(same, lam)) and oracle.load_term(same) == 0.0
 
 
 def test_load_gradient_matches_finite_differences_of_the_soft_count():
