@@ -104,6 +104,51 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
 // ---------------------------------------------------------------------------------------------
 // K6
 // ---------------------------------------------------------------------------------------------
+// Work flows through the CTA as jobs: a job is one staged batch (up to BATCH sorted entries) of one
+// tile, and two jobs are in shared memory at a time.  Each warp walks every job in order (its 8 x 4
+// block of the job's tile); the warp that finishes job j first stages job j + 1 into the other
+// buffer -- the next batch of the same tile while any warp of it still blends, else the first batch
+// of the next tile in the longest-first order -- so staging overlaps the slower warps' walk and a
+// warp waits only when it has caught up with the staging, not for the tile's slowest block.  A job
+// is published by an mbarrier (`full`, 32 arrivals: the staging warp's lanes) and released by
+// another (`empty`, one arrival per warp).  Every wait is bounded: a wait that gives up sets
+// kErrTimeout and its warp leaves (the host reports GS_ERR_TIMEOUT; the outputs are then unspecified).
+namespace {
+struct FwdJob {
+  long long t;      // global tile
+  unsigned start;   // first entry of the tile's list
+  int L;            // list length
+  int b0;           // first entry of this batch
+  int seq;          // tile sequence number within the CTA
+  int end;          // 1: no more work
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase of the given parity to complete; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned k = 0; k < limit; ++k) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+}  // namespace
+
 template <int TW, int TH, int BATCH>
 __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     const ViewDev* __restrict__ views, int n_views, long long n_tiles, const uint2* __restrict__ ranges,
@@ -116,61 +161,105 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   using S = Shape<TW, TH>;
   constexpr int kPix = S::kPix;
   static_assert(BATCH % kChunk == 0, "batches hold whole chunks");
-  __shared__ float4 s_xyo[BATCH];
-  __shared__ float4 s_con[BATCH];
-  __shared__ float4 s_rgb[BATCH];
-  __shared__ unsigned char s_bm[BATCH];  // per entry: the warp blocks its cutoff box reaches
-  __shared__ unsigned long long s_pairs[S::kWarps];
-  __shared__ unsigned long long s_blend[S::kWarps];
-  __shared__ unsigned long long s_gpn[S::kWarps], s_gpsq[S::kWarps];
-  __shared__ int s_item;
+  __shared__ float4 s_xyo[2][BATCH];
+  __shared__ float4 s_con[2][BATCH];
+  __shared__ float4 s_rgb[2][BATCH];
+  __shared__ unsigned char s_bm[2][BATCH];  // per entry: the warp blocks its cutoff box reaches
+  __shared__ FwdJob s_job[2];
+  __shared__ __align__(8) unsigned long long s_full[2], s_empty[2];
+  __shared__ int s_next;     // the next job to be staged (the stager of job j + 1 is elected on it)
+  __shared__ int s_live[2];  // per tile (sequence parity): warps with pixels still blending
+  // the stager's progress through the tiles (only the warp staging the next job reads or writes it;
+  // jobs are staged one after another)
+  __shared__ long long s_cur_t;
+  __shared__ unsigned s_cur_start;
+  __shared__ int s_cur_L, s_cur_nb, s_cur_seq;
   if (ctl->overflow) return;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const float bg0 = sp->bg[0], bg1 = sp->bg[1], bg2 = sp->bg[2];
-  unsigned long long my_pairs = 0, my_blend = 0, my_gpn = 0, my_gpsq = 0;
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) s_item = (int)atomicAdd(&ctl->fwd_work, 1u);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= n_tiles) break;
-    const long long t = order[item];
-    const int v = view_of_tile(views, n_views, t);
-    const ViewDev& V = views[v];
-    const long long local = t - V.tile_base;
-    const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
-    int ox, oy;
-    S::slot_xy(tid, ox, oy);
-    const int px = tx * TW + ox;
-    const int py = ty * TH + oy;
-    const bool inside = px < V.W && py < V.H;
-    const float pxf = (float)px, pyf = (float)py;
-    const int warp = tid >> 5, lane = tid & 31;
-    const float tx0 = (float)(tx * TW), ty0 = (float)(ty * TH);
+  unsigned my_pairs = 0, my_blend = 0, my_gpn = 0, my_gpsq = 0;  // this thread's pixels (fit 32 bits)
 
-    const uint2 rg = ranges[t];
-    const unsigned start = rg.x;
-    const int L = (int)(rg.y - rg.x);
-    const long long cb = chunk_base(start, t);
-    for (int k = tid; k < (L + kChunk - 1) / kChunk; k += kPix) chunk_tile[cb + k] = (int)(t + 1);
-
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    unsigned last = 0u, gp = 0u;
-    unsigned neval = (unsigned)L;
-    bool done = !inside;
-    int batches = 0;
-    for (int b0 = 0; b0 < L; b0 += BATCH) {
-      if (__syncthreads_count(done) == kPix) break;
-      ++batches;
+  // Stage job j (one warp): decide what it is, then load its entries into buffer j & 1.
+  auto stage = [&](int j) -> bool {
+    const int buf = j & 1;
+    if (j >= 2 && !mbar_wait(&s_empty[buf], ((j - 2) >> 1) & 1, kSpinLimit)) return false;
+    if (lane == 0) {
+      FwdJob jb;
+      jb.end = 0;
+      if (s_cur_seq >= 0 && s_cur_nb * BATCH < s_cur_L && s_live[s_cur_seq & 1] > 0) {
+        jb.t = s_cur_t;  // the tile's next batch
+        jb.start = s_cur_start;
+        jb.L = s_cur_L;
+        jb.b0 = s_cur_nb * BATCH;
+        jb.seq = s_cur_seq;
+        ++s_cur_nb;
+      } else {
+        // chunks whose masks every pixel of the finished tile received (the backward reads those)
+        if (s_cur_seq >= 0)
+          tile_chunks[s_cur_t] = min((s_cur_L + kChunk - 1) / kChunk, s_cur_nb * (BATCH / kChunk));
+        const int item = (int)atomicAdd(&ctl->fwd_work, 1u);
+        if (item >= n_tiles) {
+          jb.end = 1;
+          jb.t = 0;
+          jb.start = 0;
+          jb.L = 0;
+          jb.b0 = 0;
+          jb.seq = s_cur_seq + 1;
+        } else {
+          const long long t = order[item];
+          const uint2 rg = ranges[t];
+          s_cur_t = t;
+          s_cur_start = rg.x;
+          s_cur_L = (int)(rg.y - rg.x);
+          s_cur_nb = 1;
+          s_cur_seq += 1;
+          s_live[s_cur_seq & 1] = S::kWarps;
+          jb.t = t;
+          jb.start = rg.x;
+          jb.L = s_cur_L;
+          jb.b0 = 0;
+          jb.seq = s_cur_seq;
+        }
+      }
+      s_job[buf] = jb;
+    }
+    __syncwarp();
+    const FwdJob jb = s_job[buf];
+    if (!jb.end) {
+      if (jb.b0 == 0) {  // a new tile: map its chunks back to it for the backward
+        const long long cb = chunk_base(jb.start, jb.t);
+        for (int k = lane; k < (jb.L + kChunk - 1) / kChunk; k += 32) chunk_tile[cb + k] = (int)(jb.t + 1);
+      }
+      const int v = view_of_tile(views, n_views, jb.t);
+      const ViewDev& V = views[v];
+      const long long local = jb.t - V.tile_base;
+      const float tx0 = (float)((int)(local % V.gx) * TW), ty0 = (float)((int)(local / V.gx) * TH);
+      const int nb = min(BATCH, jb.L - jb.b0);
+      // all of the lane's record indices in flight at once, then its records copied straight into
+      // shared memory by asynchronous 16-byte copies (no registers held), then the block masks
+      constexpr int kPer = BATCH / 32;
+      unsigned recs[kPer];
 #pragma unroll
-      for (int jj = tid; jj < BATCH; jj += kPix) {
-        const int j = b0 + jj;
-        if (j >= L) break;
-        const unsigned rec = vals[start + j];
-        const float4 xy = pb.xyo[rec];
-        s_xyo[jj] = xy;
-        s_con[jj] = pb.conic[rec];
-        s_rgb[jj] = pb.rgb[rec];
+      for (int k = 0; k < kPer; ++k) {
+        const int jj = lane + 32 * k;
+        recs[k] = jj < nb ? __ldg(vals + jb.start + jb.b0 + jj) : 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int jj = lane + 32 * k;
+        if (jj < nb) {
+          cp_async16(&s_xyo[buf][jj], pb.xyo + recs[k]);
+          cp_async16(&s_con[buf][jj], pb.conic + recs[k]);
+          cp_async16(&s_rgb[buf][jj], pb.rgb + recs[k]);
+        }
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const int jj = lane + 32 * k;
+        if (jj >= nb) break;
+        const float4 xy = s_xyo[buf][jj];
         // which 8 x 4 warp blocks (warp w at (8 (w % BX), 4 (w / BX))) the cutoff box of this
         // Gaussian reaches; block centres are 3.5 / 1.5 px from their edge pixels
         unsigned xm = 0u, ym = 0u;
@@ -184,102 +273,159 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
 #pragma unroll
         for (int by = 0; by < S::kBY; ++by)
           if (ym & (1u << by)) bm |= xm << (S::kBX * by);
-        s_bm[jj] = (unsigned char)bm;
-      }
-      __syncthreads();
-      const int nb = min(BATCH, L - b0);
-      for (int c0 = 0; c0 < nb; c0 += kChunk) {
-        const int jg0 = b0 + c0;
-        const long long chunk = cb + (jg0 >> 5);
-        const int ce = min(kChunk, nb - c0);
-        // entries of this chunk whose cutoff box reaches this warp's block (warp-uniform)
-        const unsigned rel = __ballot_sync(0xffffffffu, lane < ce && ((s_bm[c0 + lane] >> warp) & 1u));
-        if (done) {  // stopped pixels still record an empty mask: the backward reads every chunk
-          cmask[chunk * kPix + tid] = 0u;
-          continue;
-        }
-        if (jg0 > 0) ckpt[chunk * kPix + tid] = make_float4(T, C0, C1, C2);
-        unsigned cand = rel;
-        unsigned mask = 0u;
-        while (cand) {
-          const int q = __ffs(cand) - 1;
-          cand &= cand - 1u;
-          const float4 xy = s_xyo[c0 + q];
-          const float4 co = s_con[c0 + q];
-          const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
-          if (power > 0.f || !(power >= co.w)) continue;
-          const float4 c = s_rgb[c0 + q];
-          const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, splat_exp(power)));
-          if (alpha < kAlphaMin) continue;
-          const float testT = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (testT < kTransMin) {
-            done = true;
-            neval = (unsigned)(jg0 + q) + 1u;
-            break;
-          }
-          const float w = __fmul_rn(alpha, T);
-          C0 = __fmaf_rn(c.x, w, C0);
-          C1 = __fmaf_rn(c.y, w, C1);
-          C2 = __fmaf_rn(c.z, w, C2);
-          T = testT;
-          last = (unsigned)(jg0 + q) + 1u;
-          ++gp;
-          mask |= 1u << q;
-        }
-        cmask[chunk * kPix + tid] = mask;
+        s_bm[buf][jj] = (unsigned char)bm;
       }
     }
-    // chunks whose masks K6 wrote for every pixel of the tile (the rest the backward skips)
-    if (tid == 0) tile_chunks[t] = min((L + kChunk - 1) / kChunk, batches * (BATCH / kChunk));
-    if (inside) {
-      const long long HW = (long long)V.W * V.H;
-      const long long pix = (long long)py * V.W + px;
-      float* img = image + 3 * V.pix_base;
-      img[pix] = C0 + T * bg0;
-      img[HW + pix] = C1 + T * bg1;
-      img[2 * HW + pix] = C2 + T * bg2;
-      const long long gpix = V.pix_base + pix;
-      if (Tout) Tout[gpix] = T;
-      last_out[gpix] = last;
-      if (gp_out) gp_out[gpix] = gp;
-      my_pairs += neval;
-      my_blend += gp;
-      if (gp) {
-        my_gpn += 1;
-        my_gpsq += (unsigned long long)gp * gp;
-      }
-    }
+    mbar_arrive(&s_full[buf]);  // every lane: its own writes are published with it
+    return true;
+  };
+
+  if (tid == 0) {
+    mbar_init(&s_full[0], 32);
+    mbar_init(&s_full[1], 32);
+    mbar_init(&s_empty[0], S::kWarps);
+    mbar_init(&s_empty[1], S::kWarps);
+    s_next = 1;
+    s_cur_seq = -1;
+    s_cur_nb = 0;
+    s_cur_L = 0;
+    s_live[0] = s_live[1] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+  bool ok = warp != 0 || stage(0);
+
+  // this thread's pixel of the current tile
+  int my_seq = -1;
+  long long pix_base = 0;
+  int px = 0, py = 0, Wv = 0;
+  long long HWv = 0, cb = 0;
+  bool inside = false, done = true, counted = true;
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  unsigned last = 0u, gp = 0u, neval = 0u;
+  float pxf = 0.f, pyf = 0.f;
+  auto finish_tile = [&]() {
+    if (my_seq < 0 || !inside) return;
+    const long long pix = (long long)py * Wv + px;
+    float* img = image + 3 * pix_base;
+    img[pix] = C0 + T * bg0;
+    img[HWv + pix] = C1 + T * bg1;
+    img[2 * HWv + pix] = C2 + T * bg2;
+    const long long gpix = pix_base + pix;
+    if (Tout) Tout[gpix] = T;
+    last_out[gpix] = last;
+    if (gp_out) gp_out[gpix] = gp;
+    my_pairs += neval;
+    my_blend += gp;
+    if (gp) {
+      my_gpn += 1;
+      my_gpsq += gp * gp;
+    }
+  };
+
+  for (int j = 0; ok; ++j) {
+    const int buf = j & 1;
+    if (!mbar_wait(&s_full[buf], (j >> 1) & 1, kSpinLimit)) {
+      ok = false;
+      break;
+    }
+    const FwdJob jb = s_job[buf];
+    if (jb.seq != my_seq) {  // a new tile (or the end)
+      finish_tile();
+      if (jb.end) break;
+      my_seq = jb.seq;
+      const int v = view_of_tile(views, n_views, jb.t);
+      const ViewDev& V = views[v];
+      const long long local = jb.t - V.tile_base;
+      const int tx = (int)(local % V.gx), ty = (int)(local / V.gx);
+      int ox, oy;
+      S::slot_xy(tid, ox, oy);
+      px = tx * TW + ox;
+      py = ty * TH + oy;
+      Wv = V.W;
+      HWv = (long long)V.W * V.H;
+      pix_base = V.pix_base;
+      inside = px < V.W && py < V.H;
+      pxf = (float)px;
+      pyf = (float)py;
+      cb = chunk_base(jb.start, jb.t);
+      T = 1.f;
+      C0 = C1 = C2 = 0.f;
+      last = gp = 0u;
+      neval = (unsigned)jb.L;
+      done = !inside;
+      counted = false;
+    }
+    // walk this job's chunks (a warp whose pixels have all stopped still records empty masks)
+    const int nb = min(BATCH, jb.L - jb.b0);
+    for (int c0 = 0; c0 < nb; c0 += kChunk) {
+      const int jg0 = jb.b0 + c0;
+      const long long chunk = cb + (jg0 >> 5);
+      const int ce = min(kChunk, nb - c0);
+      // entries of this chunk whose cutoff box reaches this warp's block (warp-uniform)
+      const unsigned rel = __ballot_sync(0xffffffffu, lane < ce && ((s_bm[buf][c0 + lane] >> warp) & 1u));
+      if (done) {
+        cmask[chunk * kPix + tid] = 0u;
+        continue;
+      }
+      if (jg0 > 0) ckpt[chunk * kPix + tid] = make_float4(T, C0, C1, C2);
+      unsigned cand = rel;
+      unsigned mask = 0u;
+      while (cand) {
+        const int q = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        const float4 xy = s_xyo[buf][c0 + q];
+        const float4 co = s_con[buf][c0 + q];
+        const float power = splat_power(co.x, co.y, co.z, __fsub_rn(xy.x, pxf), __fsub_rn(xy.y, pyf));
+        if (power > 0.f || !(power >= co.w)) continue;
+        const float4 c = s_rgb[buf][c0 + q];
+        const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, splat_exp(power)));
+        if (alpha < kAlphaMin) continue;
+        const float testT = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        if (testT < kTransMin) {
+          done = true;
+          neval = (unsigned)(jg0 + q) + 1u;
+          break;
+        }
+        const float w = __fmul_rn(alpha, T);
+        C0 = __fmaf_rn(c.x, w, C0);
+        C1 = __fmaf_rn(c.y, w, C1);
+        C2 = __fmaf_rn(c.z, w, C2);
+        T = testT;
+        last = (unsigned)(jg0 + q) + 1u;
+        ++gp;
+        mask |= 1u << q;
+      }
+      cmask[chunk * kPix + tid] = mask;
+    }
+    // this warp's pixels have all stopped: the stager need not stage more of the tile for it
+    if (!counted && __all_sync(0xffffffffu, done)) {
+      counted = true;
+      if (lane == 0) atomicSub(&s_live[my_seq & 1], 1);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_empty[buf]);
+    // the first warp to finish job j stages job j + 1
+    int mine = 0;
+    if (lane == 0) mine = atomicCAS(&s_next, j + 1, j + 2) == j + 1;
+    if (__shfl_sync(0xffffffffu, mine, 0) && !stage(j + 1)) ok = false;
+  }
+  if (!ok && lane == 0) atomicOr(&ctl->error, kErrTimeout);
   // Gaussian-pixel pairs by definition: entries evaluated per pixel up to its termination.
+  unsigned long long sp_ = my_pairs, sb = my_blend, sn = my_gpn, sq = my_gpsq;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
-    my_blend += __shfl_down_sync(0xffffffffu, my_blend, o);
-    my_gpn += __shfl_down_sync(0xffffffffu, my_gpn, o);
-    my_gpsq += __shfl_down_sync(0xffffffffu, my_gpsq, o);
+    sp_ += __shfl_down_sync(0xffffffffu, sp_, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+    sn += __shfl_down_sync(0xffffffffu, sn, o);
+    sq += __shfl_down_sync(0xffffffffu, sq, o);
   }
-  __syncthreads();
-  if ((tid & 31) == 0) {
-    s_pairs[tid >> 5] = my_pairs;
-    s_blend[tid >> 5] = my_blend;
-    s_gpn[tid >> 5] = my_gpn;
-    s_gpsq[tid >> 5] = my_gpsq;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    unsigned long long s = 0, b = 0, gn = 0, gq = 0;
-#pragma unroll
-    for (int w = 0; w < S::kWarps; ++w) {
-      s += s_pairs[w];
-      b += s_blend[w];
-      gn += s_gpn[w];
-      gq += s_gpsq[w];
-    }
-    if (s) atomicAdd(&ctl->pairs, s);
-    if (b) atomicAdd(&ctl->blended, b);
-    if (gn) {
-      atomicAdd(&ctl->gp_pixels, gn);
-      atomicAdd(&ctl->gp_sq, gq);
+  if (lane == 0) {
+    if (sp_) atomicAdd(&ctl->pairs, sp_);
+    if (sb) atomicAdd(&ctl->blended, sb);
+    if (sn) {
+      atomicAdd(&ctl->gp_pixels, sn);
+      atomicAdd(&ctl->gp_sq, sq);
     }
   }
 }
