@@ -4,18 +4,20 @@
 // Both are templates over the tile shape TW x TH (a multiple of the 8 x 4 warp block, at most 256
 // pixels) and K6 over the staged batch; the autotuner of the session picks the instance.
 //
-// K6: persistent CTAs of TW x TH threads (one tile at a time, one pixel per thread, each warp an
-// 8 x 4 pixel block) take tiles longest-list first, so the few very long tiles do not end up as
-// the tail of the launch.  The tile's sorted Gaussians are staged through shared memory in
-// batches of BATCH and walked in chunks of 32.  A warp skips a Gaussian outright when the
-// bounding box of its 1/255 cutoff ellipse misses the warp's block (warp-uniform); for the others
-// each pixel tests its exponent against -ln(255 opacity) and only then evaluates exp, alpha, the
-// early stop and the blending.  (A separate, pipelined candidate pass before the sequential walk
-// computed the exponent twice for every candidate: equal on sparse views, 6-10 % slower on dense
-// ones.)
+// K6: persistent CTAs of TW x TH threads (one pixel per thread, each warp an 8 x 4 pixel block)
+// take tiles longest-list first, so the few very long tiles do not end up as the tail of the
+// launch.  A tile's sorted Gaussians come through shared memory as jobs of up to BATCH entries, two
+// jobs resident at a time: the warp that finishes a job first stages the next one (the next batch
+// of the same tile while a warp of it still blends, else the next tile) with asynchronous copies,
+// and publishes it on an mbarrier, so staging overlaps the other warps' walk and a fast warp can run
+// a job ahead of the tile's slowest block instead of waiting for it at a CTA barrier.  Jobs are
+// walked in chunks of 32.  A warp skips a Gaussian outright when the bounding box of its 1/255 cutoff
+// ellipse misses the warp's block (warp-uniform); for the others each pixel tests its exponent
+// against -ln(255 opacity) and only then evaluates exp, alpha, the early stop and the blending.  (A
+// separate, pipelined candidate pass before the sequential walk computed the exponent twice for
+// every candidate: equal on sparse views, 6-10 % slower on dense ones.)
 // Per (pixel, chunk) K6 stores the transmittance and colour at the chunk start and a 32-bit mask
-// of the Gaussians actually blended; the CTA leaves the batch loop once every pixel has stopped
-// (__syncthreads_count).
+// of the Gaussians actually blended; a tile gets no more batches once every warp's pixels stopped.
 //
 // K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =
@@ -105,15 +107,17 @@ __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ r
 // K6
 // ---------------------------------------------------------------------------------------------
 // Work flows through the CTA as jobs: a job is one staged batch (up to BATCH sorted entries) of one
-// tile, and two jobs are in shared memory at a time.  Each warp walks every job in order (its 8 x 4
+// tile, and kFwdBufs jobs are in shared memory at a time.  Each warp walks every job in order (its 8 x 4
 // block of the job's tile); the warp that finishes job j first stages job j + 1 into the other
-// buffer -- the next batch of the same tile while any warp of it still blends, else the first batch
+// buffer of job j + 1 - kFwdBufs once every warp is through that job -- the next batch of the same tile while any warp of it still blends, else the first batch
 // of the next tile in the longest-first order -- so staging overlaps the slower warps' walk and a
 // warp waits only when it has caught up with the staging, not for the tile's slowest block.  A job
 // is published by an mbarrier (`full`, 32 arrivals: the staging warp's lanes) and released by
 // another (`empty`, one arrival per warp).  Every wait is bounded: a wait that gives up sets
 // kErrTimeout and its warp leaves (the host reports GS_ERR_TIMEOUT; the outputs are then unspecified).
 namespace {
+constexpr int kFwdBufs = 2;  // jobs in shared memory at a time (3 measured 112 against 107 us)
+
 struct FwdJob {
   long long t;      // global tile
   unsigned start;   // first entry of the tile's list
@@ -161,14 +165,14 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   using S = Shape<TW, TH>;
   constexpr int kPix = S::kPix;
   static_assert(BATCH % kChunk == 0, "batches hold whole chunks");
-  __shared__ float4 s_xyo[2][BATCH];
-  __shared__ float4 s_con[2][BATCH];
-  __shared__ float4 s_rgb[2][BATCH];
-  __shared__ unsigned char s_bm[2][BATCH];  // per entry: the warp blocks its cutoff box reaches
-  __shared__ FwdJob s_job[2];
-  __shared__ __align__(8) unsigned long long s_full[2], s_empty[2];
+  __shared__ float4 s_xyo[kFwdBufs][BATCH];
+  __shared__ float4 s_con[kFwdBufs][BATCH];
+  __shared__ float4 s_rgb[kFwdBufs][BATCH];
+  __shared__ unsigned char s_bm[kFwdBufs][BATCH];  // per entry: the warp blocks its cutoff box reaches
+  __shared__ FwdJob s_job[kFwdBufs];
+  __shared__ __align__(8) unsigned long long s_full[kFwdBufs], s_empty[kFwdBufs];
   __shared__ int s_next;     // the next job to be staged (the stager of job j + 1 is elected on it)
-  __shared__ int s_live[2];  // per tile (sequence parity): warps with pixels still blending
+  __shared__ int s_live[kFwdBufs];  // per tile (sequence mod kFwdBufs): warps with pixels still blending
   // the stager's progress through the tiles (only the warp staging the next job reads or writes it;
   // jobs are staged one after another)
   __shared__ long long s_cur_t;
@@ -180,14 +184,14 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   const float bg0 = sp->bg[0], bg1 = sp->bg[1], bg2 = sp->bg[2];
   unsigned my_pairs = 0, my_blend = 0, my_gpn = 0, my_gpsq = 0;  // this thread's pixels (fit 32 bits)
 
-  // Stage job j (one warp): decide what it is, then load its entries into buffer j & 1.
+  // Stage job j (one warp): decide what it is, then load its entries into buffer j % kFwdBufs.
   auto stage = [&](int j) -> bool {
-    const int buf = j & 1;
-    if (j >= 2 && !mbar_wait(&s_empty[buf], ((j - 2) >> 1) & 1, kSpinLimit)) return false;
+    const int buf = j % kFwdBufs;
+    if (j >= kFwdBufs && !mbar_wait(&s_empty[buf], ((j - kFwdBufs) / kFwdBufs) & 1, kSpinLimit)) return false;
     if (lane == 0) {
       FwdJob jb;
       jb.end = 0;
-      if (s_cur_seq >= 0 && s_cur_nb * BATCH < s_cur_L && s_live[s_cur_seq & 1] > 0) {
+      if (s_cur_seq >= 0 && s_cur_nb * BATCH < s_cur_L && s_live[s_cur_seq % kFwdBufs] > 0) {
         jb.t = s_cur_t;  // the tile's next batch
         jb.start = s_cur_start;
         jb.L = s_cur_L;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
           s_cur_L = (int)(rg.y - rg.x);
           s_cur_nb = 1;
           s_cur_seq += 1;
-          s_live[s_cur_seq & 1] = S::kWarps;
+          s_live[s_cur_seq % kFwdBufs] = S::kWarps;
           jb.t = t;
           jb.start = rg.x;
           jb.L = s_cur_L;
@@ -281,15 +285,15 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   };
 
   if (tid == 0) {
-    mbar_init(&s_full[0], 32);
-    mbar_init(&s_full[1], 32);
-    mbar_init(&s_empty[0], S::kWarps);
-    mbar_init(&s_empty[1], S::kWarps);
+    for (int b = 0; b < kFwdBufs; ++b) {
+      mbar_init(&s_full[b], 32);
+      mbar_init(&s_empty[b], S::kWarps);
+    }
     s_next = 1;
     s_cur_seq = -1;
     s_cur_nb = 0;
     s_cur_L = 0;
-    s_live[0] = s_live[1] = 0;
+    for (int b = 0; b < kFwdBufs; ++b) s_live[b] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -324,8 +328,8 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   };
 
   for (int j = 0; ok; ++j) {
-    const int buf = j & 1;
-    if (!mbar_wait(&s_full[buf], (j >> 1) & 1, kSpinLimit)) {
+    const int buf = j % kFwdBufs;
+    if (!mbar_wait(&s_full[buf], (j / kFwdBufs) & 1, kSpinLimit)) {
       ok = false;
       break;
     }
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     // this warp's pixels have all stopped: the stager need not stage more of the tile for it
     if (!counted && __all_sync(0xffffffffu, done)) {
       counted = true;
-      if (lane == 0) atomicSub(&s_live[my_seq & 1], 1);
+      if (lane == 0) atomicSub(&s_live[my_seq % kFwdBufs], 1);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&s_empty[buf]);
