@@ -139,8 +139,9 @@ def kernel_work(k, st, n, passes):
         return "hbm", 24.0 * M * passes
     if k == 0:   # K1: geometry of every Gaussian, SH of the visible ones, the records written
         return "hbm", 44.0 * n + st["visible"] * (192.0 + 80.0)
-    if k == 6:   # K7: two reads + one write of 3 H W per pass, partial maps written and re-read
-        return "hbm", 4.0 * W * H * (3 * 3 + 9 * 2 + 3)
+    if k == 6:   # K7: forward reads render + target (6 H W floats) and writes the 9 partial maps;
+        # backward reads the partials, render and target and writes dL/dimage (3 H W)
+        return "hbm", 4.0 * W * H * (6 + 9 + 9 + 6 + 3)
     if k == 2:
         return "hbm", 12.0 * M + 24.0 * n
     return "hbm", 8.0 * n
@@ -207,7 +208,7 @@ def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic, n_sms=
 # changed since its capture.
 TRAFFIC_TILING = (16, 16, 256)
 TRAFFIC = {"K8 blend bwd": 62.5e6, "K6 blend fwd": 21.9e6, "K9+K10 project bwd + Adam": 251.9e6,
-           "K4 sort": 5 * 4.1e6, "K7 loss": 94.4e6}
+           "K4 sort": 5 * 4.1e6, "K7 loss": 94.3e6}
 
 
 def cpu_baseline_run(steps, warmup, seed=0, rows=None):

@@ -258,7 +258,7 @@ gs_status Raster::ensure_records(int stride_) {
   const long long scan_tiles = (recs + kScanTile - 1) / kScanTile;
   if ((s = zeroA.reserve(kCtlBytes + scan_tiles * 8, &bytes_in_use))) return s;
   zeroA_bytes = kCtlBytes + scan_tiles * 8;
-  if ((s = partials.reserve(n_pix * 9 * 4, &bytes_in_use)) || (s = block_sums.reserve(n_loss_blocks * 16, &bytes_in_use)))
+  if ((s = partials.reserve(n_pix * 10 * 4, &bytes_in_use)) || (s = block_sums.reserve(n_loss_blocks * 16, &bytes_in_use)))
     return s;
   return GS_OK;
 }

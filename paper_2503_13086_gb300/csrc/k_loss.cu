@@ -3,16 +3,21 @@
 //
 // SSIM uses the 11 x 11 Gaussian window (sigma 1.5) of 3DGS, zero padding and "same" output
 // size, C1 = 0.01^2, C2 = 0.03^2, per colour channel; means run over 3 H W and, for a batch of
-// views, the loss is the mean of the per-view losses.  The window is separable: each CTA stages
-// a 32 x 48 output block plus a 5-pixel halo in shared memory, blurs rows then columns.  The
-// staging is asynchronous (cp.async, zero-filled outside the image) into one buffer, so that three
-// CTAs share an SM and overlap one another's staging (a second buffer with the next channel in
-// flight left room for two).
-//   pass 1 (k_loss_forward): the five window moments -> SSIM map, the three partial derivatives
-//          of SSIM with respect to (mu_x, E[x^2], E[xy]) per pixel, and per-CTA sums;
+// views, the loss is the mean of the per-view losses.  E[x^2] and E[y^2] enter SSIM only through
+// sigma_x^2 + sigma_y^2, so their window means are taken as one map E[x^2 + y^2] (the window is
+// linear): the forward blurs two pair maps, (x, y) and (x^2 + y^2, xy), with the packed FP32x2 FMA
+// of sm_100+ and no register shuffling, and the backward the pair (dS/dmu_x, dS/dE[x^2 + y^2]) and
+// the single map dS/dE[xy], two adjacent outputs per packed FMA.  The window is separable and
+// symmetric (six distinct weights).  Each CTA stages a 32 x 48 output block plus a 5-pixel halo in
+// shared memory (cp.async, zero-filled outside the image, consecutive threads on consecutive
+// columns; blocks inside the image skip the bounds tests) and blurs rows, then columns:
+//   pass 1 (k_loss_forward): the window moments -> SSIM map, the three partial derivatives of SSIM
+//          per pixel (an (a, b) pair plane and a c plane per channel), and per-CTA sums;
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
 //          symmetric, so the adjoint of the blur is the blur) gives dL/dx.
-// The last CTA of pass 1 reduces the per-CTA sums in a fixed order: the loss is deterministic.
+// Both passes run three 256-thread CTAs per SM (80 registers): their shared memory would fit four,
+// but at four (64 registers) the optimisation step that contains them measured 20 us slower.  The
+// last CTA of pass 1 reduces the per-CTA sums in a fixed order: the loss is deterministic.
 #include <cmath>
 
 #include "gs_device.cuh"
@@ -22,19 +27,18 @@ namespace gs {
 
 namespace {
 constexpr int kBX = 32, kBY = 48, kR = 5;
-constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // staged block with the halo
-constexpr int kVR = kBY / 8;  // column pass: 32 columns x 8 segments of kVR rows (256 threads)
-static_assert(kVR % 2 == 0, "column outputs are paired for the packed single-map blur");
-constexpr int kStageBufs = 1;  // staging buffers: 2 = the next channel in flight, 1 = more CTAs per SM
-constexpr int kSXP = 44;                               // padded row: 16-byte aligned float4 reads
+constexpr int kSX = kBX + 2 * kR, kSY = kBY + 2 * kR;  // staged block with the halo (42 x 58)
+constexpr int kVR = kBY / 8;                           // column pass: 32 columns x 8 segments of 6 rows
+constexpr int kSXP = 42;                               // staged pair rows (336 B)
+constexpr int kSCP = 44;                               // staged single-map rows (176 B)
+constexpr int kHP = kBX + 1;                           // row-blurred rows, padded
+constexpr int kThreads = 256;
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
-// The normalised window w[k] = exp(-d^2 / (2 1.5^2)) / sum, d = k - 5, set once by the host (in
-// double, rounded to float), held twice for the packed FP32x2 FMAs: c_w2[k] = (w[k], w[k]).
-__constant__ float2 c_w2[11];
-// (w[t], w[t - 1]) for t = 0..11 (0 outside the window): the weights of one input at two adjacent
-// outputs, for blurring a single map two outputs per packed FMA
-__constant__ float2 c_wp[12];
+// (w[t], w[t]) for t = 0..5 of the normalised window w[k] = exp(-(k - 5)^2 / (2 1.5^2)) / sum, set
+// once by the host (in double, rounded to float); w[t] = w[10 - t].
+__constant__ float2 c_w6[6];
+__device__ __forceinline__ float2 wgt(int t) { return c_w6[t <= kR ? t : 2 * kR - t]; }
 
 __device__ __forceinline__ int view_of_block(const ViewDev* __restrict__ views, int n_views, long long b) {
   int v = 0;
@@ -42,38 +46,59 @@ __device__ __forceinline__ int view_of_block(const ViewDev* __restrict__ views, 
   return v;
 }
 
-// 4-byte asynchronous copy global -> shared; ok == false writes 0 (reads nothing).
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+// The staged block: element e -> (row e / 42, column e % 42), image pixel (ox - 5 + col, oy - 5 +
+// row), 0 outside the image.
+constexpr int kStageN = kSY * kSX;
+
+__device__ __forceinline__ bool block_inside(int ox, int oy, int W, int H) {
+  return ox >= kR && oy >= kR && ox + kBX + kR <= W && oy + kBY + kR <= H;
+}
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = ok ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Stage MAPS planes (W x H each) of the 42 x 58 block at (ox - 5, oy - 5) into dst[m] (rows of
-// kSXP floats); outside the image (and the pad columns) become 0.  A task is 4 consecutive
-// columns of one row (the rows of an image of any width are not 16-byte aligned, so the copies
-// are 4-byte ones; the row and bounds arithmetic is shared by the four).
-template <int MAPS>
-__device__ __forceinline__ void stage_block(float (*dst)[kSY][kSXP], const float* const (&src)[MAPS], int ox, int oy,
-                                            int W, int H) {
-  constexpr int kGroups = kSXP / 4;
-  for (int task = threadIdx.x; task < kSY * kGroups; task += blockDim.x) {
-    const int r = task / kGroups, c0 = (task - r * kGroups) * 4;
-    const int gy = oy + r - kR, gx0 = ox + c0 - kR;
-    const bool row_ok = gy >= 0 && gy < H;
-    const long long rowbase = row_ok ? (long long)gy * W : 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int gx = gx0 + i;
-      const bool ok = row_ok && c0 + i < kSX && gx >= 0 && gx < W;
-      const long long pix = ok ? rowbase + gx : 0;
-#pragma unroll
-      for (int m = 0; m < MAPS; ++m) cp_async4(&dst[m][r][c0 + i], src[m] + pix, ok);
+// Asynchronous staging: thread t takes elements t, t + 256, ...; element e is (row e / 42,
+// column e % 42), so consecutive threads take consecutive columns.  A block whose staged window
+// lies inside the image (most of them) skips the bounds tests.
+template <typename Copy>
+__device__ __forceinline__ void stage_async(int ox, int oy, int W, int H, Copy copy) {
+  int r = threadIdx.x / kSX, col = threadIdx.x - r * kSX;
+  constexpr int kDr = kThreads / kSX, kDc = kThreads % kSX;
+  if (block_inside(ox, oy, W, H)) {
+    int pix = (oy + r - kR) * W + (ox + col - kR);
+#pragma unroll 2
+    for (int e = threadIdx.x; e < kStageN; e += kThreads) {
+      copy(r, col, pix, true);
+      col += kDc;
+      r += kDr;
+      pix += kDr * W + kDc;
+      if (col >= kSX) {
+        col -= kSX;
+        ++r;
+        pix += W - kSX;
+      }
+    }
+  } else {
+#pragma unroll 2
+    for (int e = threadIdx.x; e < kStageN; e += kThreads) {
+      const int gy = oy + r - kR, gx = ox + col - kR;
+      const bool ok = (unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W;
+      copy(r, col, ok ? gy * W + gx : 0, ok);
+      col += kDc;
+      r += kDr;
+      if (col >= kSX) {
+        col -= kSX;
+        ++r;
+      }
     }
   }
   cp_async_commit();
@@ -83,25 +108,25 @@ __device__ __forceinline__ void stage_block(float (*dst)[kSY][kSXP], const float
 
 long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * ((H + kBY - 1) / kBY); }
 
-// The row pass blurs 8 adjacent outputs per thread from 18 staged values per map, the column pass
-// 4 from 14, so a staged value is read once per 8 (4) outputs.
+// Forward 50.1 KB, backward 52.7 KB.
 struct LossFwdSmem {
-  float in[kStageBufs][2][kSY][kSXP];  // [buffer][x / y][row][col]
-  float2 hxy[kSY][kBX + 1];   // row-blurred (E[x], E[y])
-  float2 hq[kSY][kBX + 1];    // row-blurred (E[x^2], E[y^2])
-  float hc[kSY][kBX + 1];     // row-blurred E[xy]
+  float2 xy[kSY][kSXP];  // staged (x, y)
+  float2 hA[kSY][kHP];   // row-blurred (E[x], E[y])
+  float2 hB[kSY][kHP];   // row-blurred (E[x^2 + y^2], E[xy])
 };
 struct LossBwdSmem {
-  float in[kStageBufs][3][kSY][kSXP];  // [buffer][partial][row][col]
-  float2 hab[kSY][kBX + 1];   // row-blurred (dS/dmu_x, dS/dE[x^2])
-  float hc[kSY][kBX + 1];     // row-blurred dS/dE[xy]
+  float2 ab[kSY][kSXP];  // staged (dS/dmu_x, dS/dE[x^2 + y^2])
+  float c[kSY][kSCP];    // staged dS/dE[xy]
+  float2 hab[kSY][kHP];
+  float hc[kSY][kHP];
 };
 
-__global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
-                                                      long long n_blocks, const float* __restrict__ image,
-                                                      const StepParams* __restrict__ sp,
-                                                      float* __restrict__ partials, double* __restrict__ block_sums,
-                                                      Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
+__global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __restrict__ views, int n_views,
+                                                           long long n_blocks, const float* __restrict__ image,
+                                                           const StepParams* __restrict__ sp,
+                                                           float* __restrict__ partials,
+                                                           double* __restrict__ block_sums,
+                                                           Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
   dep_wait();
   dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -118,140 +143,102 @@ __global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restri
   const int ox = bx * kBX, oy = by * kBY;
   const long long HW = (long long)V.W * V.H;
   const float* X = image + 3 * V.pix_base;
-  float* P = partials + 9 * V.pix_base;
+  // per view 10 floats per pixel (so that every view's pair planes are 8-byte aligned): the three
+  // channels' (a, b) pair planes, then their c planes
+  float* Q = partials + 10 * V.pix_base;
+  float2* Pab = reinterpret_cast<float2*>(Q);
+  float* Pc = Q + 6 * HW;
   const float* Yt = V.target;
   double l1 = 0.0, ss = 0.0;
-  if (kStageBufs == 2) {
-    const float* const src[2] = {X, Yt};
-    stage_block<2>(S.in[0], src, ox, oy, V.W, V.H);
-  }
   for (int ch = 0; ch < 3; ++ch) {
-    const int cur = kStageBufs == 2 ? (ch & 1) : 0;
-    if (kStageBufs == 1) {
-      const float* const src[2] = {X + ch * HW, Yt + ch * HW};
-      stage_block<2>(S.in[0], src, ox, oy, V.W, V.H);
-      cp_async_wait<0>();
-    } else if (ch < 2) {
-      const float* const src[2] = {X + (ch + 1) * HW, Yt + (ch + 1) * HW};
-      stage_block<2>(S.in[(cur + 1) % kStageBufs], src, ox, oy, V.W, V.H);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    {
+      const float* Xc = X + ch * HW;
+      const float* Yc = Yt + ch * HW;
+      stage_async(ox, oy, V.W, V.H, [&](int r, int col, int pix, bool ok) {
+        cp_async4(&S.xy[r][col].x, Xc + pix, ok);
+        cp_async4(&S.xy[r][col].y, Yc + pix, ok);
+      });
     }
+    cp_async_wait<0>();
     __syncthreads();
-    float (*sx)[kSXP] = S.in[cur][0];
-    float (*sy)[kSXP] = S.in[cur][1];
-    // horizontal: 42 rows x 4 segments of 8 columns, one per thread.  x and y (and x^2 and y^2)
-    // share the window weights, so they are blurred as pairs with the packed FP32x2 FMA of sm_100+;
-    // xy is blurred two adjacent outputs per packed FMA.
-    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += blockDim.x) {
-      const int r = task >> 2, c0 = (task & 3) * 8;
-      const float* rx = sx[r] + c0;
-      const float* ry = sy[r] + c0;
-      float2 axy[8], aq[8], ac[4];
+    // row pass: 58 rows x 4 segments of 8 outputs, consecutive threads on consecutive rows (so the
+    // 16-byte reads of a quarter warp hit distinct banks)
+    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += kThreads) {
+      const int seg = task / kSY, r = task - seg * kSY, c0 = seg * 8;
+      float2 a1[8], a2[8];
 #pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        axy[o] = make_float2(0.f, 0.f);
-        aq[o] = make_float2(0.f, 0.f);
-      }
+      for (int o = 0; o < 8; ++o) a1[o] = a2[o] = make_float2(0.f, 0.f);
+      const float4* s4 = reinterpret_cast<const float4*>(&S.xy[r][c0]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) ac[k] = make_float2(0.f, 0.f);
+      for (int q = 0; q < 9; ++q) {
+        const float4 f = s4[q];
 #pragma unroll
-      for (int j4 = 0; j4 < 20; j4 += 4) {  // inputs c0 .. c0 + 17 (+ 2 zero pad columns)
-        const float4 X4 = *reinterpret_cast<const float4*>(rx + j4);
-        const float4 Y4 = *reinterpret_cast<const float4*>(ry + j4);
-        const float xs[4] = {X4.x, X4.y, X4.z, X4.w}, ys[4] = {Y4.x, Y4.y, Y4.z, Y4.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = j4 + u;
-          if (j >= 18) break;
-          const float2 v = make_float2(xs[u], ys[u]);
-          const float2 v2 = __fmul2_rn(v, v);
-          const float c = xs[u] * ys[u];
-          const float2 cc = make_float2(c, c);
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * q + h;
+          const float x = h ? f.z : f.x, y = h ? f.w : f.y;
+          const float2 v1 = make_float2(x, y);
+          const float2 v2 = make_float2(fmaf(x, x, y * y), x * y);
 #pragma unroll
           for (int o = 0; o < 8; ++o) {
             const int t = j - o;
-            if (t >= 0 && t < 11) {
-              axy[o] = __ffma2_rn(c_w2[t], v, axy[o]);
-              aq[o] = __ffma2_rn(c_w2[t], v2, aq[o]);
+            if (t >= 0 && t <= 2 * kR) {
+              a1[o] = __ffma2_rn(wgt(t), v1, a1[o]);
+              a2[o] = __ffma2_rn(wgt(t), v2, a2[o]);
             }
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int t = j - 2 * k;
-            if (t >= 0 && t <= 11) ac[k] = __ffma2_rn(c_wp[t], cc, ac[k]);
           }
         }
       }
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
-        S.hxy[r][c0 + o] = axy[o];
-        S.hq[r][c0 + o] = aq[o];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        S.hc[r][c0 + 2 * k] = ac[k].x;
-        S.hc[r][c0 + 2 * k + 1] = ac[k].y;
+        S.hA[r][c0 + o] = a1[o];
+        S.hB[r][c0 + o] = a2[o];
       }
     }
     __syncthreads();
-    // vertical: 32 columns x 8 segments of kVR rows
     {
       const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * kVR;
-      float2 mxy[kVR], mq[kVR], mc2[kVR / 2];
+      float2 mA[kVR], mB[kVR];
 #pragma unroll
-      for (int o = 0; o < kVR; ++o) {
-        mxy[o] = make_float2(0.f, 0.f);
-        mq[o] = make_float2(0.f, 0.f);
-      }
+      for (int o = 0; o < kVR; ++o) mA[o] = mB[o] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < kVR / 2; ++k) mc2[k] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kVR + 10; ++j) {
-        const float2 hxy = S.hxy[r0 + j][c], hq = S.hq[r0 + j][c];
-        const float hc = S.hc[r0 + j][c];
-        const float2 hcc = make_float2(hc, hc);
+      for (int j = 0; j < kVR + 2 * kR; ++j) {
+        const float2 hA = S.hA[r0 + j][c], hB = S.hB[r0 + j][c];
 #pragma unroll
         for (int o = 0; o < kVR; ++o) {
           const int t = j - o;
-          if (t >= 0 && t < 11) {
-            mxy[o] = __ffma2_rn(c_w2[t], hxy, mxy[o]);
-            mq[o] = __ffma2_rn(c_w2[t], hq, mq[o]);
+          if (t >= 0 && t <= 2 * kR) {
+            mA[o] = __ffma2_rn(wgt(t), hA, mA[o]);
+            mB[o] = __ffma2_rn(wgt(t), hB, mB[o]);
           }
         }
-#pragma unroll
-        for (int k = 0; k < kVR / 2; ++k) {
-          const int t = j - 2 * k;
-          if (t >= 0 && t <= 11) mc2[k] = __ffma2_rn(c_wp[t], hcc, mc2[k]);
-        }
       }
-      float l1c = 0.f, ssc = 0.f;  // at most kVR terms per thread and channel: float is exact enough
+      float l1c = 0.f, ssc = 0.f;
+      const int gx = ox + c;
 #pragma unroll
       for (int o = 0; o < kVR; ++o) {
-        const int gy = oy + r0 + o, gx = ox + c;
+        const int gy = oy + r0 + o;
         if (gx >= V.W || gy >= V.H) continue;
-        const float mx = mxy[o].x, my = mxy[o].y, exx = mq[o].x, eyy = mq[o].y;
-        const float exy = (o & 1) ? mc2[o / 2].y : mc2[o / 2].x;
-        const float N1 = 2.f * mx * my + kC1, N2 = 2.f * (exy - mx * my) + kC2;
-        const float D1 = mx * mx + my * my + kC1, D2 = (exx - mx * mx) + (eyy - my * my) + kC2;
+        const float mx = mA[o].x, my = mA[o].y, eq = mB[o].x, exy = mB[o].y;
+        const float mxmy = mx * my, m2 = fmaf(mx, mx, my * my);
+        const float N1 = 2.f * mxmy + kC1, N2 = 2.f * (exy - mxmy) + kC2;
+        const float D1 = m2 + kC1, D2 = (eq - m2) + kC2;
         const float N = N1 * N2, D = D1 * D2;
-        const float iD = 1.f / D;
-        ssc += N * iD;
-        const float dN = 2.f * my * N2 - 2.f * my * N1;
-        const float dD = 2.f * mx * D2 - 2.f * mx * D1;
-        const long long pix = (long long)gy * V.W + gx;
-        P[(3 * ch + 0) * HW + pix] = (dN * D - N * dD) * iD * iD;  // dS/dmu_x
-        P[(3 * ch + 1) * HW + pix] = -N * D1 * iD * iD;             // dS/dE[x^2]
-        P[(3 * ch + 2) * HW + pix] = 2.f * N1 * iD;                 // dS/dE[xy]
-        l1c += fabsf(sx[r0 + o + kR][c + kR] - sy[r0 + o + kR][c + kR]);
+        const float iD = __fdividef(1.f, D);  // C1 C2 <= D < 4: within 2 ulp
+        const float Sv = N * iD;
+        ssc += Sv;
+        const float dN = 2.f * my * (N2 - N1), dD = 2.f * mx * (D2 - D1);
+        const long long pix = ch * HW + (long long)gy * V.W + gx;
+        Pab[pix] = make_float2((dN - Sv * dD) * iD,  // dS/dmu_x
+                               -(Sv * D1) * iD);     // dS/dE[x^2 + y^2]
+        Pc[pix] = 2.f * N1 * iD;                     // dS/dE[xy]
+        const float2 xy = S.xy[r0 + o + kR][c + kR];
+        l1c += fabsf(xy.x - xy.y);
       }
       l1 += (double)l1c;
       ss += (double)ssc;
     }
     __syncthreads();
   }
-  // per-CTA sums (fixed-order tree), then the last CTA reduces all CTAs in index order
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     l1 += __shfl_down_sync(0xffffffffu, l1, o);
@@ -283,7 +270,7 @@ __global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restri
     const long long b0 = U.loss_block_base;
     const long long b1 = (vv + 1 < n_views) ? views[vv + 1].loss_block_base : n_blocks;
     double a = 0.0, c = 0.0;
-    for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
+    for (long long k = b0 + threadIdx.x; k < b1; k += kThreads) {
       a += ((volatile double*)block_sums)[2 * k];
       c += ((volatile double*)block_sums)[2 * k + 1];
     }
@@ -312,15 +299,13 @@ __global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restri
   }
   if (threadIdx.x == 0) {
     double loss = total / (double)n_views;
-    // Eq. 9-10: + lambda_load L_load over the pixels some Gaussian reaches (all views of the step;
-    // K6's moments of G_p); its gradient enters the blend backward through the soft count
-    if (sp->lambda_load != 0.f && ctl->gp_pixels) {  // std of G_p
+    if (sp->lambda_load != 0.f && ctl->gp_pixels) {
       const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
       const double var = (double)ctl->gp_sq / np - mean * mean;
       loss += (double)sp->lambda_load * sqrt(var > 0.0 ? var : 0.0);
     }
     ctl->loss = loss;
-    if (ledger) {  // this step is complete up to Adam, which cannot fail any more
+    if (ledger) {
       ledger->loss_sum += ctl->loss;
       ledger->pairs += ctl->pairs;
       ledger->blended += ctl->blended;
@@ -334,11 +319,12 @@ __global__ void __launch_bounds__(256, 3) k_loss_forward(const ViewDev* __restri
   }
 }
 
-__global__ void __launch_bounds__(256, 3) k_loss_backward(const ViewDev* __restrict__ views, int n_views,
-                                                       const float* __restrict__ image,
-                                                       const StepParams* __restrict__ sp,
-                                                       const float* __restrict__ partials,
-                                                       const Control* __restrict__ ctl, float* __restrict__ dimage) {
+__global__ void __launch_bounds__(kThreads, 3) k_loss_backward(const ViewDev* __restrict__ views, int n_views,
+                                                            const float* __restrict__ image,
+                                                            const StepParams* __restrict__ sp,
+                                                            const float* __restrict__ partials,
+                                                            const Control* __restrict__ ctl,
+                                                            float* __restrict__ dimage) {
   dep_wait();
   dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -354,73 +340,64 @@ __global__ void __launch_bounds__(256, 3) k_loss_backward(const ViewDev* __restr
   const long long HW = (long long)V.W * V.H;
   const float* X = image + 3 * V.pix_base;
   const float* Yt = V.target;
-  const float* P = partials + 9 * V.pix_base;
+  const float* Q = partials + 10 * V.pix_base;
+  const float2* Pab = reinterpret_cast<const float2*>(Q);
+  const float* Pc = Q + 6 * HW;
   float* dX = dimage + 3 * V.pix_base;
   const float lam = sp->lambda_ssim;
   const float scale = 1.f / (3.f * (float)V.W * (float)V.H * (float)n_views);
   const float gl1 = sp->lambda_l1 * scale, gs = -lam * scale;
-  if (kStageBufs == 2) {
-    const float* const src[3] = {P, P + HW, P + 2 * HW};
-    stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);
-  }
   for (int ch = 0; ch < 3; ++ch) {
-    const int cur = kStageBufs == 2 ? (ch & 1) : 0;
-    if (kStageBufs == 1) {
-      const float* const src[3] = {P + (3 * ch) * HW, P + (3 * ch + 1) * HW, P + (3 * ch + 2) * HW};
-      stage_block<3>(S.in[0], src, ox, oy, V.W, V.H);
-      cp_async_wait<0>();
-    } else if (ch < 2) {
-      const float* const src[3] = {P + (3 * ch + 3) * HW, P + (3 * ch + 4) * HW, P + (3 * ch + 5) * HW};
-      stage_block<3>(S.in[(cur + 1) % kStageBufs], src, ox, oy, V.W, V.H);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    {
+      const float2* ABc = Pab + ch * HW;
+      const float* Cc = Pc + ch * HW;
+      stage_async(ox, oy, V.W, V.H, [&](int r, int col, int pix, bool ok) {
+        cp_async8(&S.ab[r][col], ABc + pix, ok);
+        cp_async4(&S.c[r][col], Cc + pix, ok);
+      });
     }
+    cp_async_wait<0>();
     __syncthreads();
-    // this thread's four output pixels: fetch the render and target now, used after the blur
-    const int vc = threadIdx.x % kBX, vr0 = (threadIdx.x / kBX) * kVR;
-    float xo[kVR], yo[kVR];
-#pragma unroll
-    for (int o = 0; o < kVR; ++o) {
-      const int gy = oy + vr0 + o, gx = ox + vc;
-      const bool in = gx < V.W && gy < V.H;
-      const long long pix = in ? (long long)gy * V.W + gx : 0;
-      xo[o] = in ? X[ch * HW + pix] : 0.f;
-      yo[o] = in ? Yt[ch * HW + pix] : 0.f;
-    }
-    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += blockDim.x) {
-      const int r = task >> 2, c0 = (task & 3) * 8;
-      const float* ra = S.in[cur][0][r] + c0;
-      const float* rb = S.in[cur][1][r] + c0;
-      const float* rc = S.in[cur][2][r] + c0;
+    for (int task = threadIdx.x; task < kSY * (kBX / 8); task += kThreads) {
+      const int seg = task / kSY, r = task - seg * kSY, c0 = seg * 8;
       float2 aab[8], ac[4];
 #pragma unroll
       for (int o = 0; o < 8; ++o) aab[o] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < 4; ++k) ac[k] = make_float2(0.f, 0.f);
+      const float4* s4 = reinterpret_cast<const float4*>(&S.ab[r][c0]);
 #pragma unroll
-      for (int j4 = 0; j4 < 20; j4 += 4) {
-        const float4 A4 = *reinterpret_cast<const float4*>(ra + j4);
-        const float4 B4 = *reinterpret_cast<const float4*>(rb + j4);
-        const float4 C4 = *reinterpret_cast<const float4*>(rc + j4);
-        const float as[4] = {A4.x, A4.y, A4.z, A4.w}, bs[4] = {B4.x, B4.y, B4.z, B4.w};
-        const float cs[4] = {C4.x, C4.y, C4.z, C4.w};
+      for (int q = 0; q < 9; ++q) {
+        const float4 f = s4[q];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = j4 + u;
-          if (j >= 18) break;
-          const float2 v = make_float2(as[u], bs[u]);
-          const float2 cc = make_float2(cs[u], cs[u]);
+        for (int h = 0; h < 2; ++h) {
+          const int j = 2 * q + h;
+          const float2 v1 = h ? make_float2(f.z, f.w) : make_float2(f.x, f.y);
 #pragma unroll
           for (int o = 0; o < 8; ++o) {
             const int t = j - o;
-            if (t >= 0 && t < 11) aab[o] = __ffma2_rn(c_w2[t], v, aab[o]);
+            if (t >= 0 && t <= 2 * kR) aab[o] = __ffma2_rn(wgt(t), v1, aab[o]);
           }
+        }
+      }
+      // the single map: output pairs (2k, 2k + 1) from input pairs (c[m], c[m + 1]), m = 2k + t
+      const float4* c4 = reinterpret_cast<const float4*>(&S.c[r][c0]);
+      float cv[20];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int t = j - 2 * k;
-            if (t >= 0 && t <= 11) ac[k] = __ffma2_rn(c_wp[t], cc, ac[k]);
-          }
+      for (int q = 0; q < 5; ++q) {
+        const float4 f = c4[q];
+        cv[4 * q] = f.x;
+        cv[4 * q + 1] = f.y;
+        cv[4 * q + 2] = f.z;
+        cv[4 * q + 3] = f.w;
+      }
+#pragma unroll
+      for (int m = 0; m <= 16; ++m) {
+        const float2 p = make_float2(cv[m], cv[m + 1]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int t = m - 2 * k;
+          if (t >= 0 && t <= 2 * kR) ac[k] = __ffma2_rn(wgt(t), p, ac[k]);
         }
       }
 #pragma unroll
@@ -433,38 +410,51 @@ __global__ void __launch_bounds__(256, 3) k_loss_backward(const ViewDev* __restr
     }
     __syncthreads();
     {
-      const int c = vc, r0 = vr0;
-      float2 bab[kVR], bc2[kVR / 2];
+      const int c = threadIdx.x % kBX, r0 = (threadIdx.x / kBX) * kVR;
+      const int gx = ox + c;
+      float xo[kVR], yo[kVR];
+#pragma unroll
+      for (int o = 0; o < kVR; ++o) {
+        const int gy = oy + r0 + o;
+        const bool in = gx < V.W && gy < V.H;
+        const long long pix = in ? ch * HW + (long long)gy * V.W + gx : 0;
+        xo[o] = in ? X[pix] : 0.f;
+        yo[o] = in ? Yt[pix] : 0.f;
+      }
+      float2 bab[kVR], bc[kVR / 2];
 #pragma unroll
       for (int o = 0; o < kVR; ++o) bab[o] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < kVR / 2; ++k) bc2[k] = make_float2(0.f, 0.f);
+      for (int k = 0; k < kVR / 2; ++k) bc[k] = make_float2(0.f, 0.f);
+      float hv[kVR + 2 * kR];
 #pragma unroll
-      for (int j = 0; j < kVR + 10; ++j) {
+      for (int j = 0; j < kVR + 2 * kR; ++j) {
         const float2 h = S.hab[r0 + j][c];
-        const float hc = S.hc[r0 + j][c];
-        const float2 hcc = make_float2(hc, hc);
+        hv[j] = S.hc[r0 + j][c];
 #pragma unroll
         for (int o = 0; o < kVR; ++o) {
           const int t = j - o;
-          if (t >= 0 && t < 11) bab[o] = __ffma2_rn(c_w2[t], h, bab[o]);
+          if (t >= 0 && t <= 2 * kR) bab[o] = __ffma2_rn(wgt(t), h, bab[o]);
         }
+      }
+#pragma unroll
+      for (int m = 0; m <= kVR - 2 + 2 * kR; ++m) {
+        const float2 p = make_float2(hv[m], hv[m + 1]);
 #pragma unroll
         for (int k = 0; k < kVR / 2; ++k) {
-          const int t = j - 2 * k;
-          if (t >= 0 && t <= 11) bc2[k] = __ffma2_rn(c_wp[t], hcc, bc2[k]);
+          const int t = m - 2 * k;
+          if (t >= 0 && t <= 2 * kR) bc[k] = __ffma2_rn(wgt(t), p, bc[k]);
         }
       }
 #pragma unroll
       for (int o = 0; o < kVR; ++o) {
-        const int gy = oy + r0 + o, gx = ox + c;
+        const int gy = oy + r0 + o;
         if (gx >= V.W || gy >= V.H) continue;
-        const long long pix = (long long)gy * V.W + gx;
         const float xv = xo[o], yv = yo[o];
         const float diff = xv - yv;
         const float sgn = diff > 0.f ? 1.f : (diff < 0.f ? -1.f : 0.f);
-        const float bc = (o & 1) ? bc2[o / 2].y : bc2[o / 2].x;
-        dX[ch * HW + pix] = gl1 * sgn + gs * (bab[o].x + 2.f * xv * bab[o].y + yv * bc);
+        const float bcv = (o & 1) ? bc[o / 2].y : bc[o / 2].x;
+        dX[ch * HW + (long long)gy * V.W + gx] = gl1 * sgn + gs * (bab[o].x + 2.f * xv * bab[o].y + yv * bcv);
       }
     }
     __syncthreads();
@@ -472,22 +462,18 @@ __global__ void __launch_bounds__(256, 3) k_loss_backward(const ViewDev* __restr
 }
 
 void init_loss_attributes() {
-  float w[11];
-  float2 w2[11];
   double sum = 0.0, e[11];
   for (int k = 0; k < 11; ++k) {
     const double d = (double)(k - kR);
     e[k] = std::exp(-d * d / (2.0 * 1.5 * 1.5));
     sum += e[k];
   }
-  for (int k = 0; k < 11; ++k) {
-    w[k] = (float)(e[k] / sum);
-    w2[k] = make_float2(w[k], w[k]);
+  float2 w6[6];
+  for (int t = 0; t <= kR; ++t) {
+    const float w = (float)(e[t] / sum);
+    w6[t] = make_float2(w, w);
   }
-  float2 wp[12];
-  for (int t = 0; t < 12; ++t) wp[t] = make_float2(t <= 10 ? w[t] : 0.f, t >= 1 ? w[t - 1] : 0.f);
-  cudaMemcpyToSymbol(c_w2, w2, sizeof(w2));
-  cudaMemcpyToSymbol(c_wp, wp, sizeof(wp));
+  cudaMemcpyToSymbol(c_w6, w6, sizeof(w6));
   cudaFuncSetAttribute(k_loss_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossFwdSmem));
   cudaFuncSetAttribute(k_loss_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LossBwdSmem));
 }
@@ -495,11 +481,11 @@ void init_loss_attributes() {
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
                  float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s) {
   if (n_blocks <= 0) return;
-  launch_dep(k_loss_forward, dim3((unsigned)n_blocks), dim3(256), sizeof(LossFwdSmem), s, views, n_views, n_blocks,
-      image, sp, partials, block_sums, ctl, ledger);
+  launch_dep(k_loss_forward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossFwdSmem), s, views, n_views,
+      n_blocks, image, sp, partials, block_sums, ctl, ledger);
   if (dimage)
-    launch_dep(k_loss_backward, dim3((unsigned)n_blocks), dim3(256), sizeof(LossBwdSmem), s, views, n_views, image, sp,
-        partials, ctl, dimage);
+    launch_dep(k_loss_backward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossBwdSmem), s, views, n_views,
+        image, sp, partials, ctl, dimage);
 }
 
 }  // namespace gs

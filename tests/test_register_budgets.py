@@ -3,7 +3,7 @@ GPU needed): the blend forward must fit four 256-thread CTAs per SM (<= 64 regis
 backward four 4-warp CTAs (<= 128), the projection backward two 256-thread CTAs (<= 128), the loss
 kernels three 256-thread CTAs (<= 85), the key emission 1024-thread CTAs (<= 64); none of the hot
 kernels spills more than a few words (the projection backward's 80 bytes and the loss kernels'
-12-20 bytes are the measured state)."""
+4-20 bytes are the measured state)."""
 import os
 import re
 import shutil
