@@ -82,7 +82,7 @@ struct Control {
   unsigned int bwd_work;
   unsigned int fwd_work;
   unsigned int loss_done;
-  unsigned int pad;
+  unsigned int fwd_done;        // blend-forward warps past their last counter update
   unsigned int order_count[32];  // tiles per list-length bucket (long-first schedule)
   double loss_view[32];         // per-view loss of the last step
   double loss;                  // batch loss (mean over views)
@@ -186,6 +186,9 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
 }
 __device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 }  // namespace gs

@@ -85,7 +85,7 @@ struct Raster {
   // device buffers
   DevBuf sp_d, views_d;
   DevBuf zeroA;  // Control + scan look-back state (cleared before K1)
-  DevBuf zeroB;  // histograms + sort look-back state + ranges + chunk map (cleared before K3)
+  DevBuf zeroB;  // histograms + sort look-back state + ranges + chunk map + tile counts (cleared before K3)
   size_t zeroA_bytes = 0, zeroB_bytes = 0, sort_state_bytes = 0, ranges_bytes = 0, chunk_bytes = 0;
   bool zeroB_pending = true;  // zeroB still to be cleared by the forward tail
   DevBuf xyo, conic, rgb, depth, radius, rect, count, offsets, clamp, g2s;
@@ -116,6 +116,7 @@ struct Raster {
   unsigned* sort_state() const;
   uint2* ranges() const;
   int* chunk_tile() const;
+  unsigned* tile_done() const;  // per tile: blend-forward warps that finished it
   ProjBuffers proj() const;
   const StepParams* sp() const { return static_cast<const StepParams*>(sp_d.p); }
   const ViewDev* vd() const { return static_cast<const ViewDev*>(views_d.p); }
@@ -128,7 +129,9 @@ struct Raster {
   void mark(cudaStream_t s, int k);
   gs_status enqueue_forward_head(cudaStream_t s, const float* params, int stride_, bool size_exactly);
   gs_status enqueue_forward_tail(cudaStream_t s, float* image, float* T, unsigned* last, unsigned* gp);
-  void enqueue_loss(cudaStream_t s, const float* image, float* dimage);
+  // after_forward: the loss follows this step's blend forward directly in the stream (its blocks then
+  // start as the forward completes the tiles under them)
+  void enqueue_loss(cudaStream_t s, const float* image, float* dimage, bool after_forward);
   void enqueue_blend_backward(cudaStream_t s, const float* image, const float* dimage);
   void enqueue_backward(cudaStream_t s, float* params, const float* image, const unsigned* last, const float* dimage,
                         float* grads, float* m, float* v, float* grad2d);

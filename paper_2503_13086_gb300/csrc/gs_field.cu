@@ -559,7 +559,7 @@ struct Field {
     if ((s = R.enqueue_forward_tail(stream, static_cast<float*>(step_img.p), static_cast<float*>(step_T.p),
                                     static_cast<unsigned*>(step_last.p), static_cast<unsigned*>(step_gp.p))))
       return s;
-    R.enqueue_loss(stream, static_cast<float*>(step_img.p), static_cast<float*>(step_dimg.p));
+    R.enqueue_loss(stream, static_cast<float*>(step_img.p), static_cast<float*>(step_dimg.p), true);
     R.enqueue_backward(stream, static_cast<float*>(params.p), static_cast<float*>(step_img.p),
                        static_cast<unsigned*>(step_last.p), static_cast<float*>(step_dimg.p), nullptr,
                        static_cast<float*>(adam_m.p), static_cast<float*>(adam_v.p), nullptr);
@@ -738,7 +738,7 @@ struct Field {
         if ((s = R.enqueue_forward_tail(stream, img, static_cast<float*>(step_T.p), static_cast<unsigned*>(step_last.p),
                                         static_cast<unsigned*>(step_gp.p))))
           break;
-        R.enqueue_loss(stream, img, dimg);
+        R.enqueue_loss(stream, img, dimg, true);
         R.enqueue_backward(stream, static_cast<float*>(params.p), img, static_cast<unsigned*>(step_last.p), dimg,
                            nullptr, static_cast<float*>(adam_m.p), static_cast<float*>(adam_v.p), nullptr);
         if (rep == reps) {

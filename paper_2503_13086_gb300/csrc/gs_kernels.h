@@ -68,7 +68,10 @@ void launch_tile_order(const uint2* ranges, long long n_tiles, int* order, const
 void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
-                          unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s);
+                          unsigned* cmask, int* chunk_tile, int* tile_chunks, unsigned* tile_done, int num_sms,
+                          cudaStream_t s);
+// Warps the blend forward launches for this problem (each adds 1 to Control::fwd_done at its end).
+long long forward_warps(const Tiling& tl, long long n_tiles, int num_sms);
 void launch_blend_backward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                            const unsigned* vals, const ProjBuffers& pb, Control* ctl, const float* image,
                            const float* dimage, const float4* ckpt, const unsigned* cmask, const int* chunk_tile,
@@ -113,7 +116,12 @@ void launch_densify_write(int n, int stride, const float* params, const float* m
 
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);
+// tile_done (nullable): the blend forward's per-tile warp counts; with it the loss forward follows the
+// blend forward directly and starts each block once the tiles under its window are complete (and its
+// last CTA once fwd_warps warps have counted themselves in Control::fwd_done) instead of waiting for
+// the whole forward.  Null: the image is complete before the launch (it waits for its predecessor).
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
-                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s);
+                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage,
+                 const unsigned* tile_done, long long fwd_warps, cudaStream_t s);
 
 }  // namespace gs

@@ -187,6 +187,10 @@ uint2* Raster::ranges() const {
 int* Raster::chunk_tile() const {
   return reinterpret_cast<int*>(static_cast<char*>(zeroB.p) + kHistBytes + sort_state_bytes + ranges_bytes);
 }
+unsigned* Raster::tile_done() const {
+  return reinterpret_cast<unsigned*>(static_cast<char*>(zeroB.p) + kHistBytes + sort_state_bytes + ranges_bytes +
+                                     chunk_bytes);
+}
 ProjBuffers Raster::proj() const {
   ProjBuffers p;
   p.xyo = static_cast<float4*>(xyo.p);
@@ -294,7 +298,7 @@ gs_status Raster::ensure_instances(unsigned long long m) {
   sort_state_bytes = (size_t)passes * sort_tiles * kSortBins * 4;
   ranges_bytes = (size_t)n_tiles * 8;
   chunk_bytes = (size_t)n_ids * 4;
-  zeroB_bytes = kHistBytes + sort_state_bytes + ranges_bytes + chunk_bytes;
+  zeroB_bytes = kHistBytes + sort_state_bytes + ranges_bytes + chunk_bytes + (size_t)n_tiles * 4;
   if ((s = zeroB.reserve(zeroB_bytes, &bytes_in_use))) return s;
   return GS_OK;
 }
@@ -379,14 +383,16 @@ gs_status Raster::enqueue_forward_tail(cudaStream_t s, float* image, float* T, u
   mark(s, 5);
   launch_blend_forward(tiling, vd(), n_views, n_tiles, ranges(), v0, proj(), sp(), ctl(),
                        static_cast<const int*>(order.p), image, T, last, gp, static_cast<float4*>(ckpt.p),
-                       static_cast<unsigned*>(cmask.p), chunk_tile(), static_cast<int*>(tile_chunks.p), num_sms, s);
+                       static_cast<unsigned*>(cmask.p), chunk_tile(), static_cast<int*>(tile_chunks.p), tile_done(),
+                       num_sms, s);
   mark(s, 6);
   return GS_OK;
 }
 
-void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage) {
+void Raster::enqueue_loss(cudaStream_t s, const float* image, float* dimage, bool after_forward) {
   launch_loss(vd(), n_views, n_loss_blocks, image, sp(), static_cast<float*>(partials.p),
-              static_cast<double*>(block_sums.p), ctl(), ledger(), dimage, s);
+              static_cast<double*>(block_sums.p), ctl(), ledger(), dimage, after_forward ? tile_done() : nullptr,
+              forward_warps(tiling, n_tiles, num_sms), s);
   mark(s, 7);
 }
 
@@ -521,7 +527,7 @@ gs_status gs_raster_loss(gs_raster* rr, void* stream, const float* image, const 
   r->upload(s);
   // the loss may run again on the same forward (other weights): its CTA counter starts at 0
   cudaMemsetAsync(&r->ctl()->loss_done, 0, sizeof(unsigned), s);
-  r->enqueue_loss(s, image, out_dimage);
+  r->enqueue_loss(s, image, out_dimage, false);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(GS_ERR_CUDA, std::string("loss launch: ") + cudaGetErrorString(e));
   if (out_loss) {

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     const unsigned* __restrict__ vals, const ProjBuffers pb, const StepParams* __restrict__ sp,
     Control* __restrict__ ctl, const int* __restrict__ order, float* __restrict__ image, float* __restrict__ Tout,
     unsigned* __restrict__ last_out, unsigned* __restrict__ gp_out, float4* __restrict__ ckpt,
-    unsigned* __restrict__ cmask, int* __restrict__ chunk_tile, int* __restrict__ tile_chunks) {
+    unsigned* __restrict__ cmask, int* __restrict__ chunk_tile, int* __restrict__ tile_chunks,
+    unsigned* __restrict__ tile_done) {
   dep_wait();
   dep_release();
   using S = Shape<TW, TH>;
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
 
   // this thread's pixel of the current tile
   int my_seq = -1;
+  long long my_t = 0;
   long long pix_base = 0;
   int px = 0, py = 0, Wv = 0;
   long long HWv = 0, cb = 0;
@@ -308,23 +310,31 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
   unsigned last = 0u, gp = 0u, neval = 0u;
   float pxf = 0.f, pyf = 0.f;
+  // (warp-uniform: every lane of the warp leaves the tile at the same job)
   auto finish_tile = [&]() {
-    if (my_seq < 0 || !inside) return;
-    const long long pix = (long long)py * Wv + px;
-    float* img = image + 3 * pix_base;
-    img[pix] = C0 + T * bg0;
-    img[HWv + pix] = C1 + T * bg1;
-    img[2 * HWv + pix] = C2 + T * bg2;
-    const long long gpix = pix_base + pix;
-    if (Tout) Tout[gpix] = T;
-    last_out[gpix] = last;
-    if (gp_out) gp_out[gpix] = gp;
-    my_pairs += neval;
-    my_blend += gp;
-    if (gp) {
-      my_gpn += 1;
-      my_gpsq += gp * gp;
+    if (my_seq < 0) return;
+    if (inside) {
+      const long long pix = (long long)py * Wv + px;
+      float* img = image + 3 * pix_base;
+      img[pix] = C0 + T * bg0;
+      img[HWv + pix] = C1 + T * bg1;
+      img[2 * HWv + pix] = C2 + T * bg2;
+      const long long gpix = pix_base + pix;
+      if (Tout) Tout[gpix] = T;
+      last_out[gpix] = last;
+      if (gp_out) gp_out[gpix] = gp;
+      my_pairs += neval;
+      my_blend += gp;
+      if (gp) {
+        my_gpn += 1;
+        my_gpsq += gp * gp;
+      }
     }
+    // this warp's pixels of the tile are final: count the warp on the tile.  The warp barrier
+    // orders every lane's writes before lane 0's release, so a reader that acquires the count
+    // sees them (the loss forward starts a block once all tiles under its window are counted).
+    __syncwarp();
+    if (lane == 0) red_release_add_u32(tile_done + my_t, 1u);
   };
 
   for (int j = 0; ok; ++j) {
@@ -338,6 +348,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
       finish_tile();
       if (jb.end) break;
       my_seq = jb.seq;
+      my_t = jb.t;
       const int v = view_of_tile(views, n_views, jb.t);
       const ViewDev& V = views[v];
       const long long local = jb.t - V.tile_base;
@@ -431,6 +442,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
       atomicAdd(&ctl->gp_pixels, sn);
       atomicAdd(&ctl->gp_sq, sq);
     }
+    red_release_add_u32(&ctl->fwd_done, 1u);  // after this warp's counters (the loss's last CTA waits)
   }
 }
 
@@ -457,15 +469,22 @@ void init_forward_instance() {
   fwd_occupancy<TW, TH, BATCH>() = occ > 0 ? occ : 1;
 }
 
+// Persistent grid of one K6 instance: every resident CTA, at most one per tile.
+template <int TW, int TH, int BATCH>
+long long forward_grid(long long n_tiles, int num_sms) {
+  long long grid = (long long)num_sms * fwd_occupancy<TW, TH, BATCH>();
+  return grid > n_tiles ? n_tiles : grid;
+}
+
 template <int TW, int TH, int BATCH>
 void launch_forward_instance(const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                              const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                              const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
-                             unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
-  long long grid = (long long)num_sms * fwd_occupancy<TW, TH, BATCH>();
-  if (grid > n_tiles) grid = n_tiles;
-  launch_dep(k_blend_forward<TW, TH, BATCH>, dim3((unsigned)grid), dim3(TW * TH), 0, s, views, n_views, n_tiles, ranges,
-      vals, pb, sp, ctl, order, image, T, last, gp, ckpt, cmask, chunk_tile, tile_chunks);
+                             unsigned* cmask, int* chunk_tile, int* tile_chunks, unsigned* tile_done, int num_sms,
+                             cudaStream_t s) {
+  launch_dep(k_blend_forward<TW, TH, BATCH>, dim3((unsigned)forward_grid<TW, TH, BATCH>(n_tiles, num_sms)),
+      dim3(TW * TH), 0, s, views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image, T, last, gp, ckpt, cmask,
+      chunk_tile, tile_chunks, tile_done);
 }
 }  // namespace
 
@@ -493,16 +512,26 @@ bool tiling_supported(const Tiling& t) {
 void launch_blend_forward(const Tiling& tl, const ViewDev* views, int n_views, long long n_tiles, const uint2* ranges,
                           const unsigned* vals, const ProjBuffers& pb, const StepParams* sp, Control* ctl,
                           const int* order, float* image, float* T, unsigned* last, unsigned* gp, float4* ckpt,
-                          unsigned* cmask, int* chunk_tile, int* tile_chunks, int num_sms, cudaStream_t s) {
+                          unsigned* cmask, int* chunk_tile, int* tile_chunks, unsigned* tile_done, int num_sms,
+                          cudaStream_t s) {
   if (n_tiles <= 0) return;
 #define GS_FWD(W, H, B)                                                                                              \
   if (tl.tw == W && tl.th == H && tl.batch == B) {                                                                  \
     launch_forward_instance<W, H, B>(views, n_views, n_tiles, ranges, vals, pb, sp, ctl, order, image, T, last, gp, \
-                                     ckpt, cmask, chunk_tile, tile_chunks, num_sms, s);                           \
+                                     ckpt, cmask, chunk_tile, tile_chunks, tile_done, num_sms, s);                \
     return;                                                                                                        \
   }
   GS_TILINGS(GS_FWD)
 #undef GS_FWD
+}
+
+long long forward_warps(const Tiling& tl, long long n_tiles, int num_sms) {
+  if (n_tiles <= 0) return 0;
+#define GS_FWDW(W, H, B) \
+  if (tl.tw == W && tl.th == H && tl.batch == B) return forward_grid<W, H, B>(n_tiles, num_sms) * (W * H / 32);
+  GS_TILINGS(GS_FWDW)
+#undef GS_FWDW
+  return 0;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -104,6 +104,40 @@ __device__ __forceinline__ void stage_async(int ox, int oy, int W, int H, Copy c
   cp_async_commit();
 }
 
+// Synchronous staging of the render through L2 (ld.global.cg) for a block that starts while the blend
+// forward still runs: a neighbour tile may have been incomplete when this SM's L1 last held a sector
+// of it, so the render must not be read through L1.  All of a thread's loads are in flight together.
+__device__ __forceinline__ void stage_render_l2(float2 (*xy)[kSXP], const float* __restrict__ Xc, int ox, int oy,
+                                                int W, int H) {
+  constexpr int kPer = (kStageN + kThreads - 1) / kThreads;
+  float v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = threadIdx.x + k * kThreads;
+    const int r = e / kSX, col = e - r * kSX;
+    const int gy = oy + r - kR, gx = ox + col - kR;
+    const bool ok = e < kStageN && (unsigned)gy < (unsigned)H && (unsigned)gx < (unsigned)W;
+    v[k] = ok ? __ldcg(Xc + (long long)gy * W + gx) : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = threadIdx.x + k * kThreads;
+    if (e < kStageN) {
+      const int r = e / kSX;
+      xy[r][e - r * kSX].x = v[k];
+    }
+  }
+}
+
+// Bounded wait (one thread) until *p >= need; false when it gave up.
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need) {
+  for (unsigned k = 0; k < kSpinLimit; ++k) {
+    if (ld_acquire_u32(p) >= need) return true;
+    __nanosleep(128);
+  }
+  return false;
+}
+
 }  // namespace
 
 long long loss_blocks(int W, int H) { return (long long)((W + kBX - 1) / kBX) * ((H + kBY - 1) / kBY); }
@@ -126,14 +160,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
                                                            const StepParams* __restrict__ sp,
                                                            float* __restrict__ partials,
                                                            double* __restrict__ block_sums,
-                                                           Control* __restrict__ ctl, Ledger* __restrict__ ledger) {
-  dep_wait();
+                                                           Control* __restrict__ ctl, Ledger* __restrict__ ledger,
+                                                           const unsigned* __restrict__ tile_done,
+                                                           unsigned long long fwd_warps) {
+  // Directly after the blend forward (tile_done given) this grid does not wait for the forward to
+  // complete: its CTAs are scheduled once every forward CTA is running (the forward is persistent,
+  // so every one of them is resident and makes progress), and each block waits only for the tiles
+  // under its window.  What the forward writes (render, counters) is then read through L2.
+  if (!tile_done) dep_wait();
   dep_release();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LossFwdSmem& S = *reinterpret_cast<LossFwdSmem*>(smem_raw);
   __shared__ double s_red[2][8];
   __shared__ bool s_last;
-  if (ctl->overflow) return;
+  if (ld_relaxed_u32(&ctl->overflow)) return;
   const long long b = blockIdx.x;
   const int v = view_of_block(views, n_views, b);
   const ViewDev& V = views[v];
@@ -141,6 +181,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
   const long long lb = b - V.loss_block_base;
   const int bx = (int)(lb % bxn), by = (int)(lb / bxn);
   const int ox = bx * kBX, oy = by * kBY;
+  if (tile_done) {
+    if (threadIdx.x < 32) {
+      // the tiles under the staged window (clipped to the image), one lane per tile
+      const int tx0 = max(0, ox - kR) / V.tw, tx1 = min(V.W - 1, ox + kBX + kR - 1) / V.tw;
+      const int ty0 = max(0, oy - kR) / V.th, ty1 = min(V.H - 1, oy + kBY + kR - 1) / V.th;
+      const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+      const unsigned need = (unsigned)(V.tw * V.th / 32);  // warps per tile
+      bool ok = true;
+      for (int k = threadIdx.x; k < nt && ok; k += 32)
+        ok = wait_count(tile_done + V.tile_base + (long long)(ty0 + k / ntx) * V.gx + (tx0 + k % ntx), need);
+      if (!ok) atomicOr(&ctl->error, kErrTimeout);
+    }
+    __syncthreads();
+  }
   const long long HW = (long long)V.W * V.H;
   const float* X = image + 3 * V.pix_base;
   // per view 10 floats per pixel (so that every view's pair planes are 8-byte aligned): the three
@@ -154,10 +208,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
     {
       const float* Xc = X + ch * HW;
       const float* Yc = Yt + ch * HW;
-      stage_async(ox, oy, V.W, V.H, [&](int r, int col, int pix, bool ok) {
-        cp_async4(&S.xy[r][col].x, Xc + pix, ok);
-        cp_async4(&S.xy[r][col].y, Yc + pix, ok);
-      });
+      if (tile_done) {
+        stage_async(ox, oy, V.W, V.H,
+                    [&](int r, int col, int pix, bool ok) { cp_async4(&S.xy[r][col].y, Yc + pix, ok); });
+        stage_render_l2(S.xy, Xc, ox, oy, V.W, V.H);
+      } else {
+        stage_async(ox, oy, V.W, V.H, [&](int r, int col, int pix, bool ok) {
+          cp_async4(&S.xy[r][col].x, Xc + pix, ok);
+          cp_async4(&S.xy[r][col].y, Yc + pix, ok);
+        });
+      }
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -298,23 +358,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
     }
   }
   if (threadIdx.x == 0) {
+    // the forward's counters: complete once every forward warp has counted itself (when this grid
+    // did not wait for the forward), read through L2
+    if (tile_done && !wait_count(&ctl->fwd_done, (unsigned)fwd_warps)) atomicOr(&ctl->error, kErrTimeout);
+    const unsigned long long gp_pixels = ld_relaxed_u64(&ctl->gp_pixels), blended = ld_relaxed_u64(&ctl->blended);
+    const unsigned long long gp_sq = ld_relaxed_u64(&ctl->gp_sq), pairs = ld_relaxed_u64(&ctl->pairs);
     double loss = total / (double)n_views;
-    if (sp->lambda_load != 0.f && ctl->gp_pixels) {
-      const double np = (double)ctl->gp_pixels, mean = (double)ctl->blended / np;
-      const double var = (double)ctl->gp_sq / np - mean * mean;
+    if (sp->lambda_load != 0.f && gp_pixels) {
+      const double np = (double)gp_pixels, mean = (double)blended / np;
+      const double var = (double)gp_sq / np - mean * mean;
       loss += (double)sp->lambda_load * sqrt(var > 0.0 ? var : 0.0);
     }
     ctl->loss = loss;
     if (ledger) {
-      ledger->loss_sum += ctl->loss;
-      ledger->pairs += ctl->pairs;
-      ledger->blended += ctl->blended;
-      ledger->instances += ctl->m_total;
+      ledger->loss_sum += loss;
+      ledger->pairs += pairs;
+      ledger->blended += blended;
+      ledger->instances += ld_relaxed_u64(&ctl->m_total);
       ledger->steps_ok += 1u;
-      ledger->error |= ctl->error;
-      ledger->last_gp_sum = ctl->blended;
-      ledger->last_gp_pixels = ctl->gp_pixels;
-      ledger->last_gp_sq = ctl->gp_sq;
+      ledger->error |= ld_relaxed_u32(&ctl->error);
+      ledger->last_gp_sum = blended;
+      ledger->last_gp_pixels = gp_pixels;
+      ledger->last_gp_sq = gp_sq;
     }
   }
 }
@@ -479,10 +544,11 @@ void init_loss_attributes() {
 }
 
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
-                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage, cudaStream_t s) {
+                 float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage,
+                 const unsigned* tile_done, long long fwd_warps, cudaStream_t s) {
   if (n_blocks <= 0) return;
   launch_dep(k_loss_forward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossFwdSmem), s, views, n_views,
-      n_blocks, image, sp, partials, block_sums, ctl, ledger);
+      n_blocks, image, sp, partials, block_sums, ctl, ledger, tile_done, (unsigned long long)fwd_warps);
   if (dimage)
     launch_dep(k_loss_backward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossBwdSmem), s, views, n_views,
         image, sp, partials, ctl, dimage);

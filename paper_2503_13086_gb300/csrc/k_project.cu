@@ -361,12 +361,28 @@ __device__ __forceinline__ void apply_rows_mv(const AdamArgs& A, int c0, const i
   }
 }
 
+// L2 prefetch of rows c0 .. c0 + nrows - 1 of Gaussian i (the parameters too if pmv), so that their
+// DRAM reads are under way while the thread works on the rows before them.  Holds no register.
+__device__ __forceinline__ void l2_prefetch(const float* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void l2_prefetch_rows(const AdamArgs& A, int c0, int nrows, int i, bool pmv) {
+  for (int r = 0; r < nrows; ++r) {
+    const long long k = (long long)(c0 + r) * A.stride + i;
+    if (pmv) l2_prefetch(A.params + k);
+    l2_prefetch(A.m + k);
+    l2_prefetch(A.v + k);
+  }
+}
+
 // Four SH coefficients (12 rows) K0..K0+3: gradient sum over the visible views, the direction
 // gradient they feed, and the update.
 template <int K0, int MAXV>
 __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, unsigned vmask, float (&vdir)[MAXV][3],
                                          float (&vcol)[MAXV][3], float (&vdd)[MAXV][3]) {
   constexpr bool kSmall = MAXV <= 4;
+  if (A.adam == 1) {  // the next group's rows (after the last group, the mean's moments)
+    if (K0 < 12) l2_prefetch_rows(A, 11 + 3 * (K0 + 4), 12, i, true);
+    else l2_prefetch_rows(A, 0, 3, i, false);
+  }
   // the group's parameter rows and (for Adam) their moments, all loads issued at once
   float p[12], m[12], v[12];
 #pragma unroll
@@ -629,6 +645,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
 #pragma unroll
   for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
   const float logit = params[10 * stride + i];
+  if (A.adam == 1 && !sp->sparse) l2_prefetch_rows(A, 3, 8, i, false);  // moments of the rows after the chain
 
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gop = 0.f;
@@ -680,6 +697,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     geo_backward(V, g, g2, gmu, gls, gq);
   }
   if (nvis == 0 && A.adam == 1 && sp->sparse) return;  // sparse Adam: not seen by the step
+  if (A.adam == 1) l2_prefetch_rows(A, 11, 12, i, true);  // the first SH group
 
   // log-scales, quaternion and opacity are complete here: update them before the SH rows so their
   // gradients and values are not held through them (only the mean takes the direction gradient)
@@ -777,6 +795,7 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
   for (int k = 0; k < 4; ++k) q[k] = params[(6 + k) * stride + i];
   const float logit = params[10 * stride + i];
   const float o = 1.f / (1.f + __expf(-logit));
+  if (A.adam == 1 && !sp->sparse) l2_prefetch_rows(A, 0, 11, i, false);  // moments of the geometry rows
 
   float gmu[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
   float gop = 0.f;
@@ -809,12 +828,14 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
     geo_backward(V, g, g2, gmu, gls, gq);
   }
   if (!seen && A.adam == 1 && sp->sparse) return;  // sparse Adam: not seen by the step
+  if (A.adam == 1) l2_prefetch_rows(A, 11, 12, i, false);  // the first SH group's moments
   const float gg[11] = {gmu[0], gmu[1], gmu[2], gls[0], gls[1], gls[2], gq[0], gq[1], gq[2], gq[3], gop};
   const float pc[11] = {mu[0], mu[1], mu[2], ls[0], ls[1], ls[2], q[0], q[1], q[2], q[3], logit};
   const int grp[11] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3};
   apply_rows<11>(A, 0, grp, i, gg, pc);
 #pragma unroll
   for (int g0 = 0; g0 < 48; g0 += 12) {
+    if (A.adam == 1 && g0 + 12 < 48) l2_prefetch_rows(A, 11 + g0 + 12, 12, i, false);  // the next group's
     float p12[12], g12[12];
     int grp12[12];
 #pragma unroll
