@@ -116,7 +116,7 @@ struct Raster {
   unsigned* sort_state() const;
   uint2* ranges() const;
   int* chunk_tile() const;
-  unsigned* tile_done() const;  // per tile: blend-forward warps that finished it
+  unsigned* tile_done() const;  // per tile: 1 once the blend forward finished it
   ProjBuffers proj() const;
   const StepParams* sp() const { return static_cast<const StepParams*>(sp_d.p); }
   const ViewDev* vd() const { return static_cast<const ViewDev*>(views_d.p); }

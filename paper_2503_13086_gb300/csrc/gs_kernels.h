@@ -116,10 +116,10 @@ void launch_densify_write(int n, int stride, const float* params, const float* m
 
 // Loss: per-view partial maps, the loss value in ctl->loss, dL/dimage.
 long long loss_blocks(int W, int H);
-// tile_done (nullable): the blend forward's per-tile warp counts; with it the loss forward follows the
-// blend forward directly and starts each block once the tiles under its window are complete (and its
-// last CTA once fwd_warps warps have counted themselves in Control::fwd_done) instead of waiting for
-// the whole forward.  Null: the image is complete before the launch (it waits for its predecessor).
+// tile_done (nullable): the blend forward's per-tile completion flags; with it the loss forward follows
+// the blend forward directly and starts each block once the tiles under its window are complete (and
+// its last CTA once fwd_warps warps have counted themselves in Control::fwd_done) instead of waiting
+// for the whole forward.  Null: the image is complete before the launch (it waits for its predecessor).
 void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const float* image, const StepParams* sp,
                  float* partials, double* block_sums, Control* ctl, Ledger* ledger, float* dimage,
                  const unsigned* tile_done, long long fwd_warps, cudaStream_t s);

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   __shared__ __align__(8) unsigned long long s_full[kFwdBufs], s_empty[kFwdBufs];
   __shared__ int s_next;     // the next job to be staged (the stager of job j + 1 is elected on it)
   __shared__ int s_live[kFwdBufs];  // per tile (sequence mod kFwdBufs): warps with pixels still blending
+  __shared__ unsigned s_fin[4];     // per tile (sequence mod 4): warps that left it (at most 2 tiles open)
   // the stager's progress through the tiles (only the warp staging the next job reads or writes it;
   // jobs are staged one after another)
   __shared__ long long s_cur_t;
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     s_cur_nb = 0;
     s_cur_L = 0;
     for (int b = 0; b < kFwdBufs; ++b) s_live[b] = 0;
+    for (int b = 0; b < 4; ++b) s_fin[b] = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -330,11 +332,21 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
         my_gpsq += gp * gp;
       }
     }
-    // this warp's pixels of the tile are final: count the warp on the tile.  The warp barrier
-    // orders every lane's writes before lane 0's release, so a reader that acquires the count
-    // sees them (the loss forward starts a block once all tiles under its window are counted).
+    // this warp's pixels of the tile are final.  The warp barrier orders its lanes' writes before
+    // lane 0's CTA-scope release on the tile's arrival count; the last warp to arrive acquires them
+    // all and publishes the tile with one GPU-scope release, so a reader that acquires the flag sees
+    // every pixel of the tile (the loss forward starts a block once the tiles under it are flagged).
+    // A warp is at most one job ahead of the slowest, so at most two tiles are open at a time.
     __syncwarp();
-    if (lane == 0) red_release_add_u32(tile_done + my_t, 1u);
+    if (lane == 0) {
+      unsigned* fin = &s_fin[my_seq & 3];
+      unsigned old;
+      asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(smem_u32(fin)) : "memory");
+      if (old == (unsigned)(S::kWarps - 1)) {
+        *fin = 0u;
+        red_release_add_u32(tile_done + my_t, 1u);
+      }
+    }
   };
 
   for (int j = 0; ok; ++j) {

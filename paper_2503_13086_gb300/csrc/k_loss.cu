@@ -187,10 +187,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
       const int tx0 = max(0, ox - kR) / V.tw, tx1 = min(V.W - 1, ox + kBX + kR - 1) / V.tw;
       const int ty0 = max(0, oy - kR) / V.th, ty1 = min(V.H - 1, oy + kBY + kR - 1) / V.th;
       const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
-      const unsigned need = (unsigned)(V.tw * V.th / 32);  // warps per tile
       bool ok = true;
       for (int k = threadIdx.x; k < nt && ok; k += 32)
-        ok = wait_count(tile_done + V.tile_base + (long long)(ty0 + k / ntx) * V.gx + (tx0 + k % ntx), need);
+        ok = wait_count(tile_done + V.tile_base + (long long)(ty0 + k / ntx) * V.gx + (tx0 + k % ntx), 1u);
       if (!ok) atomicOr(&ctl->error, kErrTimeout);
     }
     __syncthreads();
