@@ -427,6 +427,71 @@ __device__ __forceinline__ void sh_group(const AdamArgs& A, int i, int nvis, uns
   else apply_rows<12>(A, 11 + 3 * K0, grp, i, g, p);
 }
 
+// A warp whose 32 Gaussians had no instance in any view of the step (none past n): their gradients
+// are all zero.  In the streaming fields Gaussians are appended per arriving image, so a view's
+// visible set comes in long runs and most warps outside it qualify.
+__device__ __forceinline__ bool warp_unseen(const unsigned* __restrict__ count, int n_views, int stride, int i, int n) {
+  bool seen = i >= n;
+  for (int v = 0; v < n_views && !seen; ++v) seen = count[(long long)v * stride + i] != 0u;
+  return __all_sync(0xffffffffu, !seen);
+}
+
+// Adam with a zero gradient (or the zero gradient itself) over the 59 rows of such a warp's Gaussians
+// i0 .. i0 + 31, in 16-byte accesses: eight lanes per 32-Gaussian row segment, four rows per pass.
+// The update is the expression apply_rows_mv evaluates, with g = 0, so the result is the same bits.
+__device__ __forceinline__ void unseen_rows(const AdamArgs& A, int i0, int lane) {
+  if (A.adam == 2) return;
+  const int sub = lane >> 3, c4 = (lane & 7) * 4;
+  if (!A.adam) {
+    for (int r = sub; r < kNumParams; r += 4)
+      *reinterpret_cast<float4*>(A.grads_out + (long long)r * A.stride + i0 + c4) = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float ibc2s = 1.f / A.bc2s;
+  const float g = 0.f;
+  // rows sub, sub + 4, ..., five at a time with every load issued before the first store (the
+  // stores could alias the next rows' loads as far as the compiler knows, so it would not hoist them)
+  constexpr int kU = 5;
+  for (int r0 = sub; r0 < kNumParams; r0 += 4 * kU) {
+    float4 p[kU], m[kU], v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int r = r0 + 4 * u;
+      if (r < kNumParams) {
+        const long long k = (long long)r * A.stride + i0 + c4;
+        p[u] = *reinterpret_cast<const float4*>(A.params + k);
+        m[u] = *reinterpret_cast<const float4*>(A.m + k);
+        v[u] = *reinterpret_cast<const float4*>(A.v + k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int r = r0 + 4 * u;
+      if (r >= kNumParams) continue;
+      // the row's group rate, selected among registers (a computed index would put A.lr in local memory)
+      const float lr = r < 3 ? A.lr[0] : (r < 6 ? A.lr[1] : (r < 10 ? A.lr[2] : (r < 11 ? A.lr[3] : (r < 14 ? A.lr[4] : A.lr[5]))));
+      auto upd = [&](float& pp, float& mm, float& vv) {
+        mm = A.b1 * mm + (1.f - A.b1) * g;
+        vv = A.b2 * vv + (1.f - A.b2) * g * g;
+        pp = pp - __fdividef((lr * A.ssc) * mm, __fsqrt_rn(vv) * ibc2s + A.eps);
+      };
+      upd(p[u].x, m[u].x, v[u].x);
+      upd(p[u].y, m[u].y, v[u].y);
+      upd(p[u].z, m[u].z, v[u].z);
+      upd(p[u].w, m[u].w, v[u].w);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int r = r0 + 4 * u;
+      if (r >= kNumParams) continue;
+      const long long k = (long long)r * A.stride + i0 + c4;
+      *reinterpret_cast<float4*>(A.m + k) = m[u];
+      *reinterpret_cast<float4*>(A.v + k) = v[u];
+      *reinterpret_cast<float4*>(A.params + k) = p[u];
+    }
+  }
+}
+
 // K9a: per record (view, Gaussian), the sum of its instances' nine gradients (a reduce by key over
 // the instances, whose records are non-decreasing in emission order).  Warps take 32-instance
 // chunks (coalesced) and sum each record's run inside the chunk by a segmented scan over the
@@ -613,13 +678,14 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
     float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
     const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
-    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v, int vec_ok) {
   dep_wait();
   dep_release();
   const long long n_rec = (long long)n_views * stride;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= sp->n) return;
   if (ctl->overflow) return;  // the step was skipped; the host re-runs it with more capacity
+  const bool unseen = vec_ok && warp_unseen(count, n_views, stride, i, sp->n);
+  if (i >= sp->n) return;
 
   AdamArgs A;
   A.params = params;
@@ -635,6 +701,10 @@ __global__ void __launch_bounds__(256, 2) k_project_backward(
   A.bc2s = sp->bc2_sqrt;
 #pragma unroll
   for (int k = 0; k < 6; ++k) A.lr[k] = sp->lr[k];
+  if (unseen) {  // sparse Adam leaves such Gaussians as they are
+    if (!(A.adam == 1 && sp->sparse)) unseen_rows(A, i - (int)(threadIdx.x & 31), threadIdx.x & 31);
+    return;
+  }
 
   float mu[3], ls[3], q[4];
 #pragma unroll
@@ -758,17 +828,16 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
     float* __restrict__ params, int stride, const StepParams* __restrict__ sp,
     const ViewDev* __restrict__ views, int n_views, const unsigned* __restrict__ count,
     const unsigned char* __restrict__ clampbits, const float* __restrict__ g2s, const Control* __restrict__ ctl,
-    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v) {
+    float* __restrict__ grads_out, float* __restrict__ adam_m, float* __restrict__ adam_v, int vec_ok) {
   dep_wait();
   dep_release();
   const long long n_rec = (long long)n_views * stride;
   __shared__ float s_gsh[48 * 256];  // [row][thread]
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= sp->n) return;
   if (ctl->overflow) return;
+  const bool unseen = vec_ok && warp_unseen(count, n_views, stride, i, sp->n);
+  if (i >= sp->n) return;
   float* gsh = s_gsh + threadIdx.x;
-#pragma unroll
-  for (int r = 0; r < 48; ++r) gsh[r * 256] = 0.f;
 
   AdamArgs A;
   A.params = params;
@@ -784,6 +853,12 @@ __global__ void __launch_bounds__(256, 2) k_project_backward_views(
   A.bc2s = sp->bc2_sqrt;
 #pragma unroll
   for (int k = 0; k < 6; ++k) A.lr[k] = sp->lr[k];
+  if (unseen) {  // sparse Adam leaves such Gaussians as they are
+    if (!(A.adam == 1 && sp->sparse)) unseen_rows(A, i - (int)(threadIdx.x & 31), threadIdx.x & 31);
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 48; ++r) gsh[r * 256] = 0.f;
 
   float mu[3], ls[3], q[4];
 #pragma unroll
@@ -900,12 +975,15 @@ void launch_project_backward(float* params, int stride, int n_views, const StepP
         head, tail, g2s, grad2d_out);
   }
   const unsigned grid = (unsigned)((stride + 255) / 256);
+  // 16-byte row accesses for warps no view saw: rows of a multiple-of-4 stride from 16-byte aligned bases
+  const auto al16 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const int vec_ok = (stride % 4 == 0) && al16(params) && al16(m) && al16(v) && al16(grads_out);
   if (n_views <= 1)
     launch_dep(k_project_backward<1>, dim3(grid), dim3(256), 0, s, params, stride, sp, views, n_views, pb.count,
-        pb.clamp, g2s, ctl, grads_out, m, v);
+        pb.clamp, g2s, ctl, grads_out, m, v, vec_ok);
   else
     launch_dep(k_project_backward_views, dim3(grid), dim3(256), 0, s, params, stride, sp, views, n_views, pb.count,
-        pb.clamp, g2s, ctl, grads_out, m, v);
+        pb.clamp, g2s, ctl, grads_out, m, v, vec_ok);
 }
 
 void launch_adam(float* params, const float* grads, float* m, float* v, int n, int stride, const StepParams* sp,
