@@ -176,7 +176,7 @@ __device__ __forceinline__ bool geo_forward(const ViewDev& V, const float mu[3],
 // ---------------------------------------------------------------------------------------------
 // K1: projection forward.  grid = (ceil(stride / 256), views); one thread per (view, Gaussian).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_project(const float* __restrict__ params, int stride,
+__global__ void __launch_bounds__(256, 6) k_project(const float* __restrict__ params, int stride,
                                                  const StepParams* __restrict__ sp,
                                                  const ViewDev* __restrict__ views, ProjBuffers out) {
   dep_wait();
@@ -234,6 +234,15 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ param
   d0 *= dl;
   d1 *= dl;
   d2 *= dl;
+  // the 48 SH coefficient rows and the opacity logit on their way to L2 at once (no register held):
+  // the loads below, which the compiler issues a few at a time (40 registers keep six CTAs per SM,
+  // so a 200k-Gaussian view is one wave), then find them there instead of making one DRAM round
+  // trip per batch
+  {
+    const float* pf = params + 10ll * stride + i;
+#pragma unroll 1
+    for (int k = 0; k < 49; ++k, pf += stride) asm volatile("prefetch.global.L2 [%0];" ::"l"(pf));
+  }
   float Y[16];
   sh_basis(d0, d1, d2, Y);
   float col[3];
