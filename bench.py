@@ -207,7 +207,7 @@ def roofline(kernel_ms, steps, st, n, passes, peaks, peaks_kind, traffic, n_sms=
 # summaries of the current kernels (profiles/), taken with the tiling below; None for a kernel
 # changed since its capture.
 TRAFFIC_TILING = (16, 16, 256)
-TRAFFIC = {"K8 blend bwd": 62.5e6, "K6 blend fwd": 21.9e6, "K9+K10 project bwd + Adam": 251.9e6,
+TRAFFIC = {"K8 blend bwd": 62.5e6, "K6 blend fwd": 21.7e6, "K9+K10 project bwd + Adam": 253.5e6,
            "K4 sort": 5 * 4.1e6, "K7 loss": 94.3e6}
 
 
