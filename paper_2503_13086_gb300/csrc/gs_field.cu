@@ -1048,6 +1048,15 @@ static gs_status upload_image(Field* f, float* dst, const float* rgb, int on_dev
   }
   const float* src = rgb;
   if (!on_device) {
+    // Page-locked host memory the device can address: the layout kernel reads it over the host
+    // link itself (NVLink-C2C on Grace-Blackwell), with no staging copy in device memory.
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, rgb) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+      gs::launch_hwc_to_chw_host(static_cast<const float*>(pa.devicePointer), dst, (long long)npix, f->stream);
+      e = cudaGetLastError();
+      return e == cudaSuccess ? GS_OK : fail(GS_ERR_CUDA, std::string("image layout: ") + cudaGetErrorString(e));
+    }
+    cudaGetLastError();  // an unregistered pointer is not an error here
     gs_status s = f->hwc_stage.reserve(bytes, &f->own_bytes);
     if (s) return s;
     e = cudaMemcpyAsync(f->hwc_stage.p, rgb, bytes, cudaMemcpyHostToDevice, f->stream);

@@ -89,6 +89,8 @@ struct PointGridDev {
   float cell;                 // cell edge
 };
 void launch_hwc_to_chw(const float* src, float* dst, long long npix, cudaStream_t s);
+// src: the device address of page-locked host memory (read by the kernel over the host link).
+void launch_hwc_to_chw_host(const float* src, float* dst, long long npix, cudaStream_t s);
 void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float thr2, int ring, unsigned* far,
                        cudaStream_t s);
 void launch_insert_points(const PointGridDev& g, int* next, long long first, long long count, cudaStream_t s);

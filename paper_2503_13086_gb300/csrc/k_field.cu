@@ -247,9 +247,52 @@ __global__ void __launch_bounds__(256) k_hwc_to_chw(const float* __restrict__ sr
   dst[2 * npix + p] = b;
 }
 
+// The same from page-locked host memory read directly over the host link (a 16-byte aligned source):
+// a CTA moves 1024 pixels (12 KB of the interleaved stream) with consecutive 16-byte loads into
+// shared memory, then writes its part of the three planes, so the link sees whole contiguous
+// requests and no staging copy is made.
+constexpr int kHostPix = 1024;
+__global__ void __launch_bounds__(256) k_hwc_to_chw_host(const float* __restrict__ src, float* __restrict__ dst,
+                                                         long long npix) {
+  __shared__ float4 s[kHostPix * 3 / 4];
+  const long long p0 = (long long)blockIdx.x * kHostPix;
+  const long long f0 = 3 * p0;  // first float of the CTA's span (a multiple of 4: 16-byte aligned)
+  const long long nf = 3 * min((long long)kHostPix, npix - p0);
+  const float4* s4 = reinterpret_cast<const float4*>(src + f0);
+  for (int k = threadIdx.x; k < kHostPix * 3 / 4; k += blockDim.x) {
+    if (4ll * k + 4 <= nf) {
+      s[k] = s4[k];
+    } else {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (4ll * k < nf) v.x = src[f0 + 4 * k];
+      if (4ll * k + 1 < nf) v.y = src[f0 + 4 * k + 1];
+      if (4ll * k + 2 < nf) v.z = src[f0 + 4 * k + 2];
+      s[k] = v;
+    }
+  }
+  __syncthreads();
+  const float* sf = reinterpret_cast<const float*>(s);
+  for (int q = threadIdx.x; q < kHostPix; q += blockDim.x) {
+    const long long p = p0 + q;
+    if (p < npix) {
+      dst[p] = sf[3 * q];
+      dst[npix + p] = sf[3 * q + 1];
+      dst[2 * npix + p] = sf[3 * q + 2];
+    }
+  }
+}
+
 void launch_hwc_to_chw(const float* src, float* dst, long long npix, cudaStream_t s) {
   if (npix <= 0) return;
   k_hwc_to_chw<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(src, dst, npix);
+}
+
+void launch_hwc_to_chw_host(const float* src, float* dst, long long npix, cudaStream_t s) {
+  if (npix <= 0) return;
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)
+    k_hwc_to_chw_host<<<(unsigned)((npix + kHostPix - 1) / kHostPix), 256, 0, s>>>(src, dst, npix);
+  else
+    k_hwc_to_chw<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(src, dst, npix);
 }
 
 void launch_far_points(const PointGridDev& g, const float* xyz, int n_new, float thr2, int ring, unsigned* far,

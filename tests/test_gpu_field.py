@@ -426,16 +426,25 @@ def test_phase3_refinement_takes_updated_poses():
 def test_interleaved_and_planar_targets_give_the_same_step():
     """gs_add_image takes the interleaved H x W x 3 image decoders produce (host or device) and
     transposes it on the device; the planar entry point takes 3 x H x W.  All three register the same
-    target: the steps after them are bitwise equal.  gs_field_stats reports the field's size and
-    memory like gs_field_info_get, and gs_set_image replaces a target in either layout."""
+    target: the steps after them are bitwise equal.  A page-locked host image is read by the layout
+    kernel directly (16-byte aligned, and at a 4-byte offset, which takes the per-pixel kernel).
+    gs_field_stats reports the field's size and memory like gs_field_info_get, and gs_set_image
+    replaces a target in either layout."""
     import torch
     p, cams, tg = config1(seed=9)
     hwc = np.ascontiguousarray(np.transpose(tg[0], (1, 2, 0)))
+    pinned = torch.tensor(hwc).pin_memory()
+    assert pinned.is_pinned() and pinned.data_ptr() % 16 == 0
+    spare = torch.empty(hwc.size + 1, dtype=torch.float32).pin_memory()  # the same image 4 bytes in
+    spare[1:] = torch.from_numpy(hwc.reshape(-1))
+    pinned_off = spare[1:].view(hwc.shape)
+    assert pinned_off.is_pinned() and pinned_off.data_ptr() % 16 == 4
     res = []
-    for kind in ("chw", "hwc_host", "hwc_device"):
+    for kind in ("chw", "hwc_host", "hwc_device", "hwc_pinned", "hwc_pinned_offset"):
         f = make_field(use_graph=0)
         f.set_gaussians(p)
-        src = {"chw": tg[0], "hwc_host": hwc, "hwc_device": torch.tensor(hwc, device="cuda")}[kind]
+        src = {"chw": tg[0], "hwc_host": hwc, "hwc_device": torch.tensor(hwc, device="cuda"), "hwc_pinned": pinned,
+               "hwc_pinned_offset": pinned_off}[kind]
         img = f.add_image(cams[0], src)
         loss = f.optimize_step([img])
         n, b = f.footprint()
