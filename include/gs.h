@@ -244,7 +244,9 @@ GS_API gs_status gs_field_get_gaussians(gs_field* f, float* host_params, float* 
 /* Register an arriving image (Sec. IV-B; the inputs per image of Sec. III: its pose from the SfM,
  * the image and its new sparse points with their matches): pose and intrinsics, the target image
  * rgb_hwc (H x W x 3 interleaved fp32 in [0, 1], the layout image decoders produce; host or device
- * per rgb_on_device; transposed on the device into the planar layout the loss reads), and its
+ * per rgb_on_device; transposed on the device into the planar layout the loss reads; a page-locked
+ * host image is read by that layout kernel directly over the host link, other host memory is first
+ * copied to a device staging buffer), and its
  * sparse points (host: xyz n_pts x 3, rgb n_pts x 3 in [0, 1], track ids n_pts; any may be NULL when
  * n_pts == 0).  Points farther than add_dist_thresh from every existing sparse point become new
  * Gaussians (3DGS initialisation); track ids (the co-visibility of Sec. IV-C: a track is one
@@ -263,7 +265,7 @@ GS_API gs_status gs_add_image_chw(gs_field* f, const gs_camera* cam, const float
 
 /* Replace a registered image's target (rgb_hwc, H x W x 3 interleaved, nullable) and/or its pose
  * (cam, nullable; same size), e.g. a refined pose (Sec. IV-A, Phase 3).  Asynchronous on the
- * field's stream: a host image in pinned memory is read by the copy the call enqueues, so it must
+ * field's stream: a host image in pinned memory is read by the kernel the call enqueues, so it must
  * stay unchanged until the field's next synchronising call (the next gs_optimize_step) returns;
  * pageable host memory is read before the call returns. */
 GS_API gs_status gs_set_image(gs_field* f, int32_t image_id, const gs_camera* cam, const float* rgb_hwc,
