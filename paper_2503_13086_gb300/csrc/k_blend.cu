@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
   __shared__ __align__(8) unsigned long long s_full[kFwdBufs], s_empty[kFwdBufs];
   __shared__ int s_next;     // the next job to be staged (the stager of job j + 1 is elected on it)
   __shared__ int s_live[kFwdBufs];  // per tile (sequence mod kFwdBufs): warps with pixels still blending
-  __shared__ unsigned s_fin[4];     // per tile (sequence mod 4): warps that left it (at most 2 tiles open)
+  __shared__ unsigned s_fin[4];     // per tile (sequence mod 4): warps that left it (at most 3 tiles open)
   // the stager's progress through the tiles (only the warp staging the next job reads or writes it;
   // jobs are staged one after another)
   __shared__ long long s_cur_t;
@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(TW * TH, 1024 / (TW * TH)) k_blend_forward(
     // lane 0's CTA-scope release on the tile's arrival count; the last warp to arrive acquires them
     // all and publishes the tile with one GPU-scope release, so a reader that acquires the flag sees
     // every pixel of the tile (the loss forward starts a block once the tiles under it are flagged).
-    // A warp is at most one job ahead of the slowest, so at most two tiles are open at a time.
+    // Job j + 1 is staged only once every warp is through job j - 1, so the warps that have not left
+    // a tile are on the tiles of three consecutive jobs at most: four counters are never shared.
     __syncwarp();
     if (lane == 0) {
       unsigned* fin = &s_fin[my_seq & 3];
