@@ -472,6 +472,19 @@ GS_API gs_status gs_autotune_clear(void);
  * Returns GS_OK when both runs completed (whatever they report), GS_ERR_CUDA otherwise. */
 GS_API gs_status gs_wait_probe(uint32_t spin_limit, uint32_t out_error[2], float out_ms[2]);
 
+/* The loss forward that follows the blend forward in a step starts each block once the tiles under
+ * its window are flagged complete, and its last CTA once every blend-forward warp has counted its
+ * pair and G_p totals; both waits poll a bounded number of times, and one that gives up sets the
+ * same error bit (the step reports GS_ERR_TIMEOUT) and lets the kernel finish.  This call runs the
+ * loss forward once on a one-block 32 x 48 view whose tiles are never flagged and whose forward
+ * warps never count themselves, so both waits can only end by giving up.
+ *   spin_limit  polls of each wait before giving up; 0 = the limit the steps use
+ *   out_error   (host, 1 uint32) the run's error bits; bit 0 (value 1) set = a wait gave up
+ *   out_ms      (host, 1 float, nullable) device time of the run
+ * Synchronous.  Allocates about 90 KB of device memory and frees it before returning.  Returns
+ * GS_OK when the run completed (whatever it reports), GS_ERR_CUDA otherwise. */
+GS_API gs_status gs_loss_wait_probe(uint32_t spin_limit, uint32_t* out_error, float* out_ms);
+
 /* ----------------------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a deployment variant.
  * ---------------------------------------------------------------------------------------- */

@@ -163,6 +163,7 @@ SYMBOLS = {
     "gs_field_densify": ([P, P, P], I32),
     "gs_field_densify_stats": ([P, P, P], I32),
     "gs_wait_probe": ([ctypes.c_uint32, P, P], I32),
+    "gs_loss_wait_probe": ([ctypes.c_uint32, P, P], I32),
     "gs_field_corrupt_guard": ([P, I32, P, I32], I32),
     "gs_schedule_plan": ([P, P, P, I32, I32, P, P, P, P, P, P], I32),
 }
@@ -345,6 +346,17 @@ def wait_probe(spin_limit=0):
     ms = (ctypes.c_float * 2)()
     _check(load().gs_wait_probe(int(spin_limit), err, ms))
     return (int(err[0]), int(err[1])), (float(ms[0]), float(ms[1]))
+
+
+def loss_wait_probe(spin_limit=0):
+    """Run the loss forward's two waits of a step (tile flags, blend-forward warp count) once with
+    nothing that ever ends them (spin_limit polls each, 0 = the steps' own limit).  Returns
+    (error_bits, ms); bit 0 set = a wait gave up."""
+    _torch()
+    err = ctypes.c_uint32()
+    ms = ctypes.c_float()
+    _check(load().gs_loss_wait_probe(int(spin_limit), ctypes.byref(err), ctypes.byref(ms)))
+    return int(err.value), float(ms.value)
 
 
 def schedule_plan(M, T, new_id, **config):

@@ -19,6 +19,7 @@ extern thread_local std::string g_last_error;
 gs_status fail(gs_status s, const std::string& msg);
 // K2's and K4's look-back waits run once each with a predecessor that never starts (gs_wait_probe).
 gs_status run_wait_probe(unsigned spin_limit, unsigned out_error[2], float out_ms[2]);
+gs_status run_loss_wait_probe(unsigned spin_limit, unsigned* out_error, float* out_ms);
 std::mutex& alloc_capture_mutex();
 
 // A named NVTX range over a scope (host-side phases of the session: steps, field update, graph

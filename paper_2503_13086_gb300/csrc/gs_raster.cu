@@ -451,6 +451,12 @@ gs_status gs_wait_probe(uint32_t spin_limit, uint32_t out_error[2], float out_ms
   return gs::run_wait_probe(spin_limit, out_error, out_ms);
 }
 
+gs_status gs_loss_wait_probe(uint32_t spin_limit, uint32_t* out_error, float* out_ms) {
+  if (!out_error) return fail(GS_ERR_INVALID_ARG, "out_error is NULL");
+  *out_error = 0u;
+  return gs::run_loss_wait_probe(spin_limit, out_error, out_ms);
+}
+
 gs_status gs_raster_create(gs_raster** out) {
   if (!out) return fail(GS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;

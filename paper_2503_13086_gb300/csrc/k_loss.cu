@@ -129,9 +129,9 @@ __device__ __forceinline__ void stage_render_l2(float2 (*xy)[kSXP], const float*
   }
 }
 
-// Bounded wait (one thread) until *p >= need; false when it gave up.
-__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need) {
-  for (unsigned k = 0; k < kSpinLimit; ++k) {
+// Bounded wait (one thread) until *p >= need, at most `limit` polls; false when it gave up.
+__device__ __forceinline__ bool wait_count(const unsigned* p, unsigned need, unsigned limit) {
+  for (unsigned k = 0; k < limit; ++k) {
     if (ld_acquire_u32(p) >= need) return true;
     __nanosleep(128);
   }
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
                                                            double* __restrict__ block_sums,
                                                            Control* __restrict__ ctl, Ledger* __restrict__ ledger,
                                                            const unsigned* __restrict__ tile_done,
-                                                           unsigned long long fwd_warps) {
+                                                           unsigned long long fwd_warps, unsigned spin_limit) {
   // Directly after the blend forward (tile_done given) this grid does not wait for the forward to
   // complete: its CTAs are scheduled once every forward CTA is running (the forward is persistent,
   // so every one of them is resident and makes progress), and each block waits only for the tiles
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
       const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
       bool ok = true;
       for (int k = threadIdx.x; k < nt && ok; k += 32)
-        ok = wait_count(tile_done + V.tile_base + (long long)(ty0 + k / ntx) * V.gx + (tx0 + k % ntx), 1u);
+        ok = wait_count(tile_done + V.tile_base + (long long)(ty0 + k / ntx) * V.gx + (tx0 + k % ntx), 1u, spin_limit);
       if (!ok) atomicOr(&ctl->error, kErrTimeout);
     }
     __syncthreads();
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_loss_forward(const ViewDev* __r
   if (threadIdx.x == 0) {
     // the forward's counters: complete once every forward warp has counted itself (when this grid
     // did not wait for the forward), read through L2
-    if (tile_done && !wait_count(&ctl->fwd_done, (unsigned)fwd_warps)) atomicOr(&ctl->error, kErrTimeout);
+    if (tile_done && !wait_count(&ctl->fwd_done, (unsigned)fwd_warps, spin_limit)) atomicOr(&ctl->error, kErrTimeout);
     const unsigned long long gp_pixels = ld_relaxed_u64(&ctl->gp_pixels), blended = ld_relaxed_u64(&ctl->blended);
     const unsigned long long gp_sq = ld_relaxed_u64(&ctl->gp_sq), pairs = ld_relaxed_u64(&ctl->pairs);
     double loss = total / (double)n_views;
@@ -547,10 +547,71 @@ void launch_loss(const ViewDev* views, int n_views, long long n_blocks, const fl
                  const unsigned* tile_done, long long fwd_warps, cudaStream_t s) {
   if (n_blocks <= 0) return;
   launch_dep(k_loss_forward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossFwdSmem), s, views, n_views,
-      n_blocks, image, sp, partials, block_sums, ctl, ledger, tile_done, (unsigned long long)fwd_warps);
+      n_blocks, image, sp, partials, block_sums, ctl, ledger, tile_done, (unsigned long long)fwd_warps, kSpinLimit);
   if (dimage)
     launch_dep(k_loss_backward, dim3((unsigned)n_blocks), dim3(kThreads), sizeof(LossBwdSmem), s, views, n_views,
         image, sp, partials, ctl, dimage);
+}
+
+// Failure detection for the loss forward's waits when it runs under the blend forward: a one-block
+// view (32 x 48 pixels, six 16 x 16 tiles) whose tiles are never flagged and whose forward warps never
+// count themselves, so the tile wait and the last CTA's wait can only end by giving up.
+gs_status run_loss_wait_probe(unsigned spin_limit, unsigned* out_error, float* out_ms) {
+  if (spin_limit == 0u) spin_limit = kSpinLimit;
+  init_loss_attributes();
+  constexpr int W = kBX, H = kBY;
+  const size_t npix = (size_t)W * H;
+  const size_t off_views = 0, off_sp = 1024, off_ctl = 2048, off_sums = off_ctl + kCtlBytes;
+  const size_t off_done = off_sums + 64, off_img = off_done + 64;
+  const size_t off_tgt = off_img + 3 * npix * 4, off_part = off_tgt + 3 * npix * 4;
+  const size_t bytes = off_part + 10 * npix * 4;
+  char* d = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  gs_status status = GS_OK;
+  auto check = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && status == GS_OK) status = fail(GS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaSuccess;
+  };
+  if (check(cudaMalloc(&d, bytes), "cudaMalloc") && check(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream") &&
+      check(cudaEventCreate(&ev[0]), "event") && check(cudaEventCreate(&ev[1]), "event") &&
+      check(cudaMemsetAsync(d, 0, bytes, st), "cudaMemsetAsync")) {
+    ViewDev v{};
+    v.W = W;
+    v.H = H;
+    v.tw = 16;
+    v.th = 16;
+    v.gx = 2;
+    v.gy = 3;
+    v.target = reinterpret_cast<const float*>(d + off_tgt);
+    StepParams sp{};
+    sp.n_views = 1;
+    sp.lambda_ssim = 0.2f;
+    sp.lambda_l1 = 0.8f;
+    if (check(cudaMemcpyAsync(d + off_views, &v, sizeof(v), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync") &&
+        check(cudaMemcpyAsync(d + off_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, st), "cudaMemcpyAsync")) {
+      Control* ctl = reinterpret_cast<Control*>(d + off_ctl);
+      cudaEventRecord(ev[0], st);
+      k_loss_forward<<<1, kThreads, sizeof(LossFwdSmem), st>>>(
+          reinterpret_cast<const ViewDev*>(d + off_views), 1, 1, reinterpret_cast<const float*>(d + off_img),
+          reinterpret_cast<const StepParams*>(d + off_sp), reinterpret_cast<float*>(d + off_part),
+          reinterpret_cast<double*>(d + off_sums), ctl, nullptr, reinterpret_cast<const unsigned*>(d + off_done), 1ull,
+          spin_limit);
+      cudaEventRecord(ev[1], st);
+      check(cudaGetLastError(), "loss wait probe launch");
+      Control r{};
+      if (check(cudaMemcpyAsync(&r, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync") &&
+          check(cudaStreamSynchronize(st), "cudaStreamSynchronize")) {
+        *out_error = r.error;
+        if (out_ms) cudaEventElapsedTime(out_ms, ev[0], ev[1]);
+      }
+    }
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  return status;
 }
 
 }  // namespace gs

@@ -45,6 +45,8 @@ def test_host_only_calls_without_a_gpu():
     assert b"NULL" in lib.gs_last_error()
     assert lib.gs_wait_probe(0, None, None) == 1
     assert b"out_error" in lib.gs_last_error()
+    assert lib.gs_loss_wait_probe(0, None, None) == 1
+    assert b"out_error" in lib.gs_last_error()
     assert lib.gs_field_corrupt_guard(None, 0, None, 0) == 1
     assert cfg.debug_canaries == 0 and cfg.sparse_adam == 0 and cfg.densify_stats == 0
 

@@ -1,5 +1,6 @@
 """Failure detection without a GPU fault: the bounded inter-CTA waits of the scan (K2) and of the
-sort passes (K4).  Each wait runs once with a predecessor tile that never starts, so it can only end
+sort passes (K4), and the loss forward's waits for the blend forward's tile flags and warp count.
+Each wait runs once with a predecessor that never starts (or a flag nothing sets), so it can only end
 by giving up; it must report that through the control block, return, and leave the context usable
 for the next step."""
 import numpy as np
@@ -55,3 +56,35 @@ def test_the_steps_own_limit_gives_up_within_a_few_seconds():
     (e_scan, e_sort), (ms_scan, ms_sort) = gs.wait_probe(spin_limit=0)
     assert e_scan & 1 and e_sort & 1
     assert 100.0 < ms_scan < 5000.0 and 100.0 < ms_sort < 5000.0
+
+
+def test_the_loss_waits_give_up_and_report_it():
+    import paper_2503_13086_gb300 as gs
+    err, ms = gs.loss_wait_probe(spin_limit=4096)
+    assert err & 1, "the loss forward's waits did not report giving up"
+    assert 0.0 < ms < 1000.0
+
+
+def test_the_loss_waits_are_bounded_by_their_limit():
+    import paper_2503_13086_gb300 as gs
+    _, a = gs.loss_wait_probe(spin_limit=1 << 10)
+    _, b = gs.loss_wait_probe(spin_limit=1 << 14)
+    assert b > 4.0 * a
+
+
+def test_the_context_stays_usable_after_the_loss_waits_gave_up():
+    import paper_2503_13086_gb300 as gs
+    before = small_step()
+    err, _ = gs.loss_wait_probe(spin_limit=2048)
+    assert err & 1
+    after = small_step()
+    assert before[0] == after[0]
+    for a, b in zip(before[1], after[1]):
+        assert np.array_equal(a, b)
+
+
+def test_the_steps_own_loss_wait_limit_gives_up_within_seconds():
+    import paper_2503_13086_gb300 as gs
+    err, ms = gs.loss_wait_probe(spin_limit=0)
+    assert err & 1
+    assert 100.0 < ms < 10000.0
