@@ -18,6 +18,8 @@
 // every candidate: equal on sparse views, 6-10 % slower on dense ones.)
 // Per (pixel, chunk) K6 stores the transmittance and colour at the chunk start and a 32-bit mask
 // of the Gaussians actually blended; a tile gets no more batches once every warp's pixels stopped.
+// When the last of a tile's warps leaves it, the tile is flagged complete (a GPU-scope release), so
+// the loss that follows can start on the image blocks over finished tiles while K6 still runs.
 //
 // K8: gradient accumulation per Gaussian (the splatting-based parallelism the paper adopts from
 // Taming 3DGS to remove the serialized per-pixel atomics of the original backward).  Work item =

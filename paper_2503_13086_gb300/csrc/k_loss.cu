@@ -15,6 +15,8 @@
 //          per pixel (an (a, b) pair plane and a c plane per channel), and per-CTA sums;
 //   pass 2 (k_loss_backward): the same window applied to those partials (the window is
 //          symmetric, so the adjoint of the blur is the blur) gives dL/dx.
+// In a step, pass 1 follows the blend forward without waiting for it to complete: each block waits
+// for the completion flags of the tiles under its window and reads the render through L2.
 // Both passes run three 256-thread CTAs per SM (80 registers): their shared memory would fit four,
 // but at four (64 registers) the optimisation step that contains them measured 20 us slower.  The
 // last CTA of pass 1 reduces the per-CTA sums in a fixed order: the loss is deterministic.
