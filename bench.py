@@ -302,6 +302,31 @@ def combine_ranks(ms, pairs, ws, device):
     return float(tmax[0].item()), float(t[1].item())
 
 
+def host_cpu():
+    """The host the oracle runs on: logical CPUs and the CPU model (lscpu's "Model name", else
+    /proc/cpuinfo's "model name", else the machine type)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def run_reference(args):
     """The oracle (fp32, one host thread) on the same workload: W untimed and K timed full steps
     (about 2.3 s each on the GPU machine's Arm host), printed with the steps it actually ran."""
@@ -320,7 +345,7 @@ def run_reference(args):
             "data": "synthetic (seeded ring scene, uniform target; the paper's scenes are not available)",
             "impl": "reference", "config": workload_config(ws),
             "cpu_baseline": {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": sample + ", fp32, one thread"},
+                             "sample": sample + ", fp32, one thread", "host": host_cpu()},
             "e2e": {"value": val, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -561,12 +586,14 @@ def run_gs(args):
         if not args.no_cpu_baseline and ws == 1:
             val, sec, pp = cpu_baseline_run(3, 0)
             line["cpu_baseline"] = {"value": val, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                                    "sample": f"3 full oracle steps of the workload ({pp} pairs each), fp32, one thread"}
+                                    "sample": f"3 full oracle steps of the workload ({pp} pairs each), fp32, one thread",
+                                    "host": host_cpu()}
             aval, procs, span, app = cpu_baseline_all_cores()
             line["cpu_baseline_all_cores"] = {
                 "value": aval, "unit": "pairs/s", "cores": procs, "kind": "oracle",
                 "sample": f"{procs} processes (one per host core), one full oracle step each ({app} pairs), "
-                          f"started together; pairs / {span:.2f} s from the first start to the last end"}
+                          f"started together; pairs / {span:.2f} s from the first start to the last end",
+                "host": host_cpu()}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
